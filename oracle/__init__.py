@@ -1,0 +1,267 @@
+"""CPU FP64 oracle of the per-frame SIR particle-filter step (test infrastructure only).
+
+The arithmetic lives in ``pf_oracle.c`` (plain C, FP64, no FMA contraction); this
+module compiles it with gcc into ``oracle/_build/liborc.so`` and exposes numpy-level
+wrappers.  Only the tests, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
+leg import it.  It shares no code with the CUDA library.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pf_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "liborc.so")
+_lock = threading.Lock()
+_lib = None
+
+_I64 = ctypes.c_int64
+_U32 = ctypes.c_uint32
+_U64 = ctypes.c_uint64
+_D = ctypes.c_double
+_P = ctypes.c_void_p
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (plain C) if the library is missing or older than its source."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+               "-shared", "-o", tmp, _SRC, "-lm", "-lpthread"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        sig = {
+            "orc_philox_batch": (None, [_I64, _P, _U64, _P]),
+            "orc_uniform_batch": (None, [_I64, _P, _P]),
+            "orc_box_muller_batch": (None, [_I64, _P, _P, _P, _P]),
+            "orc_round_pixel_batch": (None, [_I64, _P, _P]),
+            "orc_resample_u0": (_D, [_U64, _U32, _U32]),
+            "orc_disk_count": (ctypes.c_int, [ctypes.c_int]),
+            "orc_likelihood_at": (_D, [_P, ctypes.c_int, ctypes.c_int, _I64, ctypes.c_int,
+                                       _D, _D, _I64, _I64]),
+            "orc_disk_sum": (_I64, [_P, ctypes.c_int, ctypes.c_int, _I64, ctypes.c_int,
+                                    _I64, _I64]),
+            "orc_propagate": (None, [_I64, _U32, _U64, _U32, _P, _P, _P, _D, _D, _D, _D,
+                                     _D, _D, _P, _P, ctypes.c_int]),
+            "orc_likelihood_all": (None, [_I64, _P, _P, _P, ctypes.c_int, ctypes.c_int, _I64,
+                                          ctypes.c_int, _D, _D, _P, ctypes.c_int]),
+            "orc_weights": (_D, [_I64, _P, _P]),
+            "orc_normalise": (_D, [_I64, _P, _P, _P, _P, _P]),
+            "orc_cdf": (None, [_I64, _P, _D, _P]),
+            "orc_resample_f64": (None, [_I64, _P, _D, _P]),
+            "orc_resample_f32": (None, [_I64, _P, ctypes.c_float, _P]),
+            "orc_run": (ctypes.c_int, [_P, _I64, ctypes.c_int, ctypes.c_int, ctypes.c_int, _I64,
+                                       _I64, ctypes.c_int, _D, _D, _D, _D, _D, _D, _D, _D,
+                                       _U64, _U32, ctypes.c_int, _P, _P, _P]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+# --------------------------------------------------------------------------- RNG
+def philox(ctrs, seed: int) -> np.ndarray:
+    """Philox4x32-10 of each counter row (n, 4) under the 64-bit key ``seed``."""
+    c = np.ascontiguousarray(np.asarray(ctrs, dtype=np.uint32).reshape(-1, 4))
+    out = np.empty_like(c)
+    _load().orc_philox_batch(c.shape[0], _ptr(c), seed & 0xFFFFFFFFFFFFFFFF, _ptr(out))
+    return out
+
+
+def uniform(words) -> np.ndarray:
+    w = np.ascontiguousarray(np.asarray(words, dtype=np.uint32).ravel())
+    u = np.empty(w.shape, dtype=np.float64)
+    _load().orc_uniform_batch(w.size, _ptr(w), _ptr(u))
+    return u
+
+
+def box_muller(ua, ub):
+    a = np.ascontiguousarray(np.asarray(ua, dtype=np.float64).ravel())
+    b = np.ascontiguousarray(np.asarray(ub, dtype=np.float64).ravel())
+    nx = np.empty_like(a)
+    ny = np.empty_like(a)
+    _load().orc_box_muller_batch(a.size, _ptr(a), _ptr(b), _ptr(nx), _ptr(ny))
+    return nx, ny
+
+
+def normals(seed: int, t: int, n: int, tracker: int = 0, start: int = 0):
+    """The propagation draws (n_x, n_y) of particles start..start+n-1 at frame t."""
+    j = np.arange(start, start + n, dtype=np.uint64).astype(np.uint32)
+    ctr = np.stack([j, np.full(n, t, np.uint32), np.zeros(n, np.uint32),
+                    np.full(n, tracker, np.uint32)], axis=1)
+    w = philox(ctr, seed)
+    return box_muller(uniform(w[:, 0]), uniform(w[:, 1]))
+
+
+def resample_u0(seed: int, t: int, tracker: int = 0) -> float:
+    return float(_load().orc_resample_u0(seed & 0xFFFFFFFFFFFFFFFF, t, tracker))
+
+
+# --------------------------------------------------------------------------- template / pixels
+def disk_count(r: int) -> int:
+    return int(_load().orc_disk_count(r))
+
+
+def round_pixel(v) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(v, dtype=np.float64).ravel())
+    p = np.empty(a.shape, dtype=np.int64)
+    _load().orc_round_pixel_batch(a.size, _ptr(a), _ptr(p))
+    return p
+
+
+def _frame_args(frame: np.ndarray):
+    f = np.ascontiguousarray(frame, dtype=np.uint8)
+    H, W = f.shape
+    return f, W, H, W
+
+
+def likelihood_at(frame: np.ndarray, r: int, px: int, py: int, bg=100.0, fg=228.0) -> float:
+    f, W, H, pitch = _frame_args(frame)
+    return float(_load().orc_likelihood_at(_ptr(f), W, H, pitch, r, bg, fg, px, py))
+
+
+def disk_sum(frame: np.ndarray, r: int, px: int, py: int) -> int:
+    f, W, H, pitch = _frame_args(frame)
+    return int(_load().orc_disk_sum(_ptr(f), W, H, pitch, r, px, py))
+
+
+# --------------------------------------------------------------------------- phases
+def propagate(N, t, seed, xa, ya, anc, init=(0.0, 0.0), drift=(0.0, 0.0), sigma=(1.0, 1.0),
+              tracker=0, nthreads=1):
+    x = np.empty(N, np.float64)
+    y = np.empty(N, np.float64)
+    if anc is None:
+        pa = pxa = pya = None
+    else:
+        xa = np.ascontiguousarray(xa, np.float64)
+        ya = np.ascontiguousarray(ya, np.float64)
+        anc = np.ascontiguousarray(anc, np.int64)
+        pa, pxa, pya = _ptr(anc), _ptr(xa), _ptr(ya)
+    _load().orc_propagate(N, t, seed & 0xFFFFFFFFFFFFFFFF, tracker, pxa, pya, pa,
+                          init[0], init[1], drift[0], drift[1], sigma[0], sigma[1],
+                          _ptr(x), _ptr(y), nthreads)
+    return x, y
+
+
+def likelihood_all(x, y, frame, r, bg=100.0, fg=228.0, nthreads=1):
+    x = np.ascontiguousarray(x, np.float64)
+    y = np.ascontiguousarray(y, np.float64)
+    f, W, H, pitch = _frame_args(frame)
+    L = np.empty(x.size, np.float64)
+    _load().orc_likelihood_all(x.size, _ptr(x), _ptr(y), _ptr(f), W, H, pitch, r, bg, fg,
+                               _ptr(L), nthreads)
+    return L
+
+
+def weights(L):
+    L = np.ascontiguousarray(L, np.float64)
+    e = np.empty_like(L)
+    M = _load().orc_weights(L.size, _ptr(L), _ptr(e))
+    return float(M), e
+
+
+def normalise(e, x, y):
+    e = np.ascontiguousarray(e, np.float64)
+    x = np.ascontiguousarray(x, np.float64)
+    y = np.ascontiguousarray(y, np.float64)
+    xh = ctypes.c_double()
+    yh = ctypes.c_double()
+    S = _load().orc_normalise(e.size, _ptr(e), _ptr(x), _ptr(y), ctypes.byref(xh), ctypes.byref(yh))
+    return float(S), float(xh.value), float(yh.value)
+
+
+def cdf(e, S):
+    e = np.ascontiguousarray(e, np.float64)
+    C = np.empty_like(e)
+    _load().orc_cdf(e.size, _ptr(e), float(S), _ptr(C))
+    return C
+
+
+def resample(C, u0, precision: str = "f64"):
+    """Systematic-resampling ancestors of CDF ``C`` with offset ``u0``, the decision taken
+    in FP64 (``precision='f64'``) or FP32 (``'f32'``; C and u0 are rounded to FP32)."""
+    if precision == "f64":
+        Cc = np.ascontiguousarray(C, np.float64)
+        a = np.empty(Cc.size, np.int64)
+        _load().orc_resample_f64(Cc.size, _ptr(Cc), float(u0), _ptr(a))
+    elif precision == "f32":
+        Cc = np.ascontiguousarray(C, np.float32)
+        a = np.empty(Cc.size, np.int64)
+        _load().orc_resample_f32(Cc.size, _ptr(Cc), float(np.float32(u0)), _ptr(a))
+    else:
+        raise ValueError(precision)
+    return a
+
+
+# --------------------------------------------------------------------------- whole tracker
+@dataclass
+class FrameRecord:
+    """What one frame of the oracle produced (all FP64)."""
+    x: np.ndarray
+    y: np.ndarray
+    L: np.ndarray
+    M: float
+    S: float
+    est: tuple
+    C: np.ndarray
+    u0: float
+    anc: np.ndarray
+    anc_in: np.ndarray | None = field(default=None)
+
+
+def track_steps(frames: np.ndarray, N: int, r: int, *, init, sigma=(1.0, 1.0), drift=(0.0, 0.0),
+                seed: int = 1, tracker: int = 0, bg=100.0, fg=228.0, nthreads=1):
+    """Run the tracker phase by phase (Fig. 1), yielding a FrameRecord per frame.
+    Same arithmetic as :func:`track`, with every intermediate array exposed."""
+    anc = None
+    xa = ya = None
+    for t in range(frames.shape[0]):
+        x, y = propagate(N, t, seed, xa, ya, anc, init=init, drift=drift, sigma=sigma,
+                         tracker=tracker, nthreads=nthreads)
+        L = likelihood_all(x, y, frames[t], r, bg, fg, nthreads=nthreads)
+        M, e = weights(L)
+        S, xh, yh = normalise(e, x, y)
+        C = cdf(e, S)
+        u0 = resample_u0(seed, t, tracker)
+        a = resample(C, u0, "f64")
+        yield FrameRecord(x=x, y=y, L=L, M=M, S=S, est=(xh, yh), C=C, u0=u0, anc=a, anc_in=anc)
+        xa, ya, anc = x, y, a
+
+
+def track(frames: np.ndarray, N: int, r: int, *, init, sigma=(1.0, 1.0), drift=(0.0, 0.0),
+          seed: int = 1, tracker: int = 0, bg=100.0, fg=228.0, nthreads=1):
+    """Whole FP64 track in C.  Returns (est (T,2), M (T,), S (T,))."""
+    f = np.ascontiguousarray(frames, dtype=np.uint8)
+    T, H, W = f.shape
+    est = np.empty((T, 2), np.float64)
+    M = np.empty(T, np.float64)
+    S = np.empty(T, np.float64)
+    rc = _load().orc_run(_ptr(f), H * W, T, W, H, W, N, r, bg, fg, init[0], init[1],
+                         sigma[0], sigma[1], drift[0], drift[1], seed & 0xFFFFFFFFFFFFFFFF,
+                         tracker, nthreads, _ptr(est), _ptr(M), _ptr(S))
+    if rc != 0:
+        raise MemoryError("oracle could not allocate its arrays")
+    return est, M, S

@@ -1,0 +1,91 @@
+"""Seeded synthetic monochrome video: the tracking input of the particle filter.
+
+The paper evaluates on a synthetic video in the style of the Rodinia particle-filter
+application (Sec. 4, "Verification & Accuracy Results"): one disk-shaped object of a
+single foreground intensity on a background of a single intensity, Gaussian noise
+added to every pixel, and the object bouncing specularly off the frame walls.  Neither
+that generator nor its data is available, so this module stands in for it with the
+same shapes: W x H uint8 frames, a disk of radius r, constant velocity v, intensity
+levels 100 / 228 (the two constants of Eq. 3) and additive noise of std ``noise``.
+
+This module is an *input generator only*.  It is shared by the CUDA path, the bench and
+the CPU oracle, and it holds none of the filter's arithmetic: no random draw of the
+method (those come from each side's own Philox4x32-10), no likelihood, no weighting,
+no resampling.  Its noise comes from numpy's PCG64 stream, seeded per video.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+__all__ = ["Video", "reflect", "centre_track", "make_video"]
+
+
+@dataclass
+class Video:
+    """T frames of H x W uint8 pixels plus the ground-truth disk centre of each frame."""
+
+    frames: np.ndarray   # (T, H, W) uint8, C-contiguous, row-major (y = row, x = column)
+    centres: np.ndarray  # (T, 2) float64, (x, y) of the disk centre in pixel units
+    radius: int
+    noise: float
+    seed: int
+
+    @property
+    def T(self) -> int:
+        return int(self.frames.shape[0])
+
+    @property
+    def H(self) -> int:
+        return int(self.frames.shape[1])
+
+    @property
+    def W(self) -> int:
+        return int(self.frames.shape[2])
+
+
+def reflect(p: np.ndarray, lo: float, hi: float) -> np.ndarray:
+    """Fold an unconstrained coordinate into [lo, hi] by specular reflection at both walls."""
+    p = np.asarray(p, dtype=np.float64)
+    span = hi - lo
+    if span <= 0:
+        return np.full_like(p, lo)
+    q = np.mod(p - lo, 2.0 * span)
+    q = np.where(q > span, 2.0 * span - q, q)
+    return lo + q
+
+
+def centre_track(W: int, H: int, T: int, r: int, v=(1.0, -2.0), c0=None,
+                 bounce: bool = True) -> np.ndarray:
+    """Centre of the disk in frames 0..T-1: c0 + t*v, folded into [r, W-1-r] x [r, H-1-r]."""
+    if c0 is None:
+        c0 = (W / 2.0, H / 2.0)
+    t = np.arange(T, dtype=np.float64)
+    cx = c0[0] + t * float(v[0])
+    cy = c0[1] + t * float(v[1])
+    if bounce:
+        cx = reflect(cx, float(r), float(W - 1 - r))
+        cy = reflect(cy, float(r), float(H - 1 - r))
+    return np.stack([cx, cy], axis=1)
+
+
+def make_video(W: int, H: int, T: int, r: int, *, v=(1.0, -2.0), c0=None,
+               noise: float = 5.0, bg: int = 100, fg: int = 228, seed: int = 1,
+               bounce: bool = True) -> Video:
+    """Render T frames: bg everywhere, fg inside the disk (x-cx)^2 + (y-cy)^2 <= r^2,
+    plus noise * N(0, 1) per pixel, rounded half up and clamped to [0, 255]."""
+    centres = centre_track(W, H, T, r, v=v, c0=c0, bounce=bounce)
+    rng = np.random.default_rng(seed)
+    ys = np.arange(H, dtype=np.float64)[:, None]
+    xs = np.arange(W, dtype=np.float64)[None, :]
+    frames = np.empty((T, H, W), dtype=np.uint8)
+    r2 = float(r) * float(r)
+    for t in range(T):
+        cx, cy = centres[t]
+        inside = (xs - cx) ** 2 + (ys - cy) ** 2 <= r2
+        img = np.where(inside, float(fg), float(bg))
+        if noise > 0:
+            img = img + noise * rng.standard_normal((H, W))
+        frames[t] = np.clip(np.floor(img + 0.5), 0, 255).astype(np.uint8)
+    return Video(frames=frames, centres=centres, radius=int(r), noise=float(noise), seed=int(seed))

@@ -1,0 +1,375 @@
+"""Pins of the CPU FP64 oracle to things other than itself (no GPU needed).
+
+Each test checks the oracle against what the paper or mathematics fixes: a library run
+as a black box (cuRAND's host Philox generator, numpy, scipy), closed forms of Eq. 3,
+invariants of systematic resampling (Sec. 3), brute force on tiny inputs, and recovery
+of the known ground-truth trajectory of the synthetic video (Sec. 4, verification).
+"""
+import ctypes
+import ctypes.util
+import glob
+import json
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2308_00763_gb300 import synth
+from conftest import GOLDEN
+
+
+# ----------------------------------------------------------------------------- Philox
+def _curand():
+    cands = []
+    for d in (os.environ.get("CUDA_HOME", ""), "/usr/local/cuda"):
+        if d:
+            cands += sorted(glob.glob(os.path.join(d, "lib64", "libcurand.so*")))
+            cands += sorted(glob.glob(os.path.join(d, "targets", "*", "lib", "libcurand.so*")))
+    found = ctypes.util.find_library("curand")
+    if found:
+        cands.append(found)
+    for c in cands:
+        try:
+            return ctypes.CDLL(c)
+        except OSError:
+            continue
+    return None
+
+
+def _curand_host_words(lib, seed, n_words, offset=0):
+    gen = ctypes.c_void_p()
+    CURAND_RNG_PSEUDO_PHILOX4_32_10 = 161
+    assert lib.curandCreateGeneratorHost(ctypes.byref(gen), CURAND_RNG_PSEUDO_PHILOX4_32_10) == 0
+    try:
+        assert lib.curandSetPseudoRandomGeneratorSeed(gen, ctypes.c_ulonglong(seed)) == 0
+        assert lib.curandSetGeneratorOffset(gen, ctypes.c_ulonglong(offset)) == 0
+        out = np.zeros(n_words, dtype=np.uint32)
+        assert lib.curandGenerate(gen, out.ctypes.data_as(ctypes.c_void_p), ctypes.c_size_t(n_words)) == 0
+        return out
+    finally:
+        lib.curandDestroyGenerator(gen)
+
+
+@pytest.mark.parametrize("seed", [1, 0x0123456789ABCDEF, 0xFFFFFFFFFFFFFFFF])
+@pytest.mark.parametrize("offset_blocks", [0, 65536 * 3 + 17, 1 << 48])
+def test_philox_matches_curand_host_generator(seed, offset_blocks):
+    """cuRAND's host Philox4x32-10 generator (run on the CPU as a black box) emits, in its
+    default ordering, block B of four words = Philox(ctr = (B >> 16 as a 64-bit value in
+    words 0-1, B & 0xffff in word 2, 0), key = seed).  That layout was read off the
+    library's output; the oracle must reproduce every block bit for bit."""
+    lib = _curand()
+    if lib is None:
+        pytest.skip("libcurand not found")
+    nblk = 4096
+    words = _curand_host_words(lib, seed, 4 * nblk, offset=4 * offset_blocks).reshape(nblk, 4)
+    B = np.arange(offset_blocks, offset_blocks + nblk, dtype=np.uint64)
+    hi = B >> np.uint64(16)
+    ctr = np.stack([(hi & np.uint64(0xFFFFFFFF)).astype(np.uint32),
+                    (hi >> np.uint64(32)).astype(np.uint32),
+                    (B & np.uint64(0xFFFF)).astype(np.uint32),
+                    np.zeros(nblk, np.uint32)], axis=1)
+    got = oracle.philox(ctr, seed)
+    assert np.array_equal(got, words)
+
+
+def test_philox_counter_words_all_matter():
+    base = np.array([[5, 6, 7, 8]], np.uint32)
+    ref = oracle.philox(base, 42)
+    for i in range(4):
+        c = base.copy()
+        c[0, i] ^= 1
+        assert not np.array_equal(oracle.philox(c, 42), ref)
+    assert not np.array_equal(oracle.philox(base, 43), ref)
+    assert not np.array_equal(oracle.philox(base, 42 | (1 << 40)), ref)
+
+
+# ----------------------------------------------------------------------------- uniforms / normals
+def test_uniform_grid_exact_in_fp32():
+    w = np.array([0, 511, 512, 1 << 31, 0xFFFFFFFF, 0xFFFFFE00, 0x12345678], np.uint32)
+    u = oracle.uniform(w)
+    assert u[0] == 2.0 ** -24 and u[1] == 2.0 ** -24          # low 9 bits dropped
+    assert u[2] == 3 * 2.0 ** -24
+    assert u[3] == 0.5 + 2.0 ** -24
+    assert u[4] == 1.0 - 2.0 ** -24 and u[5] == u[4]
+    ctr = np.stack([np.arange(200000, dtype=np.uint32)] + [np.zeros(200000, np.uint32)] * 3, 1)
+    uu = oracle.uniform(oracle.philox(ctr, 7).ravel())
+    assert np.all(uu.astype(np.float32).astype(np.float64) == uu)   # every value exact in FP32
+    assert uu.min() > 0.0 and uu.max() < 1.0
+    # uniformity: chi-square over 64 equal bins (scipy as the reference)
+    stats = pytest.importorskip("scipy.stats")
+    counts, _ = np.histogram(uu, bins=64, range=(0, 1))
+    assert stats.chisquare(counts).pvalue > 1e-4
+
+
+def test_box_muller_normals():
+    stats = pytest.importorskip("scipy.stats")
+    n = 1 << 20
+    nx, ny = oracle.normals(seed=1, t=3, n=n)
+    for v in (nx, ny):
+        assert abs(v.mean()) < 5.0 / math.sqrt(n)
+        assert abs(v.var() - 1.0) < 5.0 * math.sqrt(2.0 / n)
+        assert stats.kstest(v, "norm").pvalue > 1e-4
+    assert abs(np.corrcoef(nx, ny)[0, 1]) < 5.0 / math.sqrt(n)
+    # the 23-bit uniforms bound every draw by sqrt(-2 ln 2^-24)
+    assert np.abs(nx).max() <= math.sqrt(48 * math.log(2)) + 1e-12
+    # closed form of the transform: n_x^2 + n_y^2 = -2 ln u_a, atan2 gives 2 pi u_b
+    ua = np.array([0.25, 0.5, 0.75, 2.0 ** -24])
+    ub = np.array([0.0, 0.125, 0.5, 0.75])
+    bx, by = oracle.box_muller(ua, ub)
+    np.testing.assert_allclose(bx * bx + by * by, -2.0 * np.log(ua), rtol=1e-14)
+    np.testing.assert_allclose(np.mod(np.arctan2(by, bx), 2 * np.pi), 2 * np.pi * ub, atol=1e-14)
+
+
+# ----------------------------------------------------------------------------- template / rounding
+def test_disk_counts_golden():
+    with open(os.path.join(GOLDEN, "disk_counts.json")) as f:
+        counts = json.load(f)["counts"]
+    for r, n in counts.items():
+        assert oracle.disk_count(int(r)) == n
+
+
+def test_round_pixel_special_values():
+    v = np.array([2.5, np.nextafter(2.5, 0), -0.5, np.nextafter(-0.5, -1), 7.0, -7.0,
+                  1e6 + 0.5, 0.49999999999999994, 3.75, -3.25])
+    want = np.array([3, 2, 0, -1, 7, -7, 1000001, 0, 4, -3])
+    assert np.array_equal(oracle.round_pixel(v), want)
+    # away from the half-way points it is numpy's rounding
+    rng = np.random.default_rng(0)
+    x = rng.uniform(-600, 600, 100000)
+    x = x[np.abs(x - np.floor(x) - 0.5) > 1e-6]
+    assert np.array_equal(oracle.round_pixel(x), np.rint(x).astype(np.int64))
+
+
+# ----------------------------------------------------------------------------- likelihood, Eq. 3
+def _golden_L():
+    with open(os.path.join(GOLDEN, "likelihood_closed_forms.json")) as f:
+        return json.load(f)
+
+
+def test_likelihood_uniform_frame_closed_form():
+    g = _golden_L()
+    for case in g["uniform_frame"]:
+        frame = np.full((40, 50), case["c"], np.uint8)
+        for r in (1, 3, 5, 10):
+            for (px, py) in [(25, 20), (0, 0), (49, 39), (3, 37)]:
+                got = oracle.likelihood_at(frame, r, px, py)
+                assert abs(got - float(Fraction(case["L"]))) < 1e-12
+
+
+def test_likelihood_half_plane_closed_form():
+    g = _golden_L()["half_plane"]["cases"]
+    X0 = 30
+    frame = np.full((64, 64), 100, np.uint8)
+    frame[:, :X0] = 228
+    for case in g:
+        assert oracle.disk_count(case["r"]) == case["D"]
+        got = oracle.likelihood_at(frame, case["r"], X0, 32)
+        assert abs(got - float(Fraction(case["L"]))) < 1e-12
+        # the transposed frame needs the transposed position (x = column, y = row)
+        got_t = oracle.likelihood_at(frame.T.copy(), case["r"], 20, X0)
+        assert abs(got_t - float(Fraction(case["L"]))) < 1e-12
+        # r columns left of the edge the template is all foreground
+        assert abs(oracle.likelihood_at(frame, case["r"], X0 - 1 - case["r"], 32) - 327.68) < 1e-12
+
+
+def test_likelihood_corner_clamp_closed_form():
+    g = _golden_L()["corner_clamp"]
+    frame = np.full((16, 16), 100, np.uint8)
+    frame[0, 0] = 228
+    assert abs(oracle.likelihood_at(frame, g["r"], 0, 0) - float(Fraction(g["L"]))) < 1e-12
+    # the opposite corner clamps the same way
+    frame2 = np.full((16, 20), 100, np.uint8)
+    frame2[15, 19] = 228
+    assert abs(oracle.likelihood_at(frame2, 1, 19, 15) - float(Fraction(g["L"]))) < 1e-12
+
+
+def test_likelihood_noiseless_disk_video():
+    v = synth.make_video(96, 80, 6, 5, v=(1, -2), noise=0.0, seed=3)
+    for t in range(v.T):
+        cx, cy = (int(c) for c in v.centres[t])
+        assert oracle.likelihood_at(v.frames[t], 5, cx, cy) == pytest.approx(327.68, abs=1e-12)
+        # shifted by one column: the closed form with m counted by brute force on the frame
+        m = 0
+        for dy in range(-5, 6):
+            for dx in range(-5, 6):
+                if dx * dx + dy * dy <= 25 and v.frames[t][cy + dy, cx + 1 + dx] == 100:
+                    m += 1
+        want = 8192.0 * (81 - 2 * m) / (25.0 * 81)
+        assert oracle.likelihood_at(v.frames[t], 5, cx + 1, cy) == pytest.approx(want, abs=1e-12)
+    # far from the disk: pure background
+    assert oracle.likelihood_at(v.frames[0], 5, 10, 70) == pytest.approx(-327.68, abs=1e-12)
+
+
+def test_likelihood_integer_form_identity():
+    """(256 * sum(I) - 41984 |D|) / (50 |D|) equals the per-pixel Eq. 3 sum exactly: the
+    integer disk sum is a second, independent calculation of the same value."""
+    rng = np.random.default_rng(5)
+    frame = rng.integers(0, 256, size=(37, 53), dtype=np.uint8)
+    for r in (1, 3, 5, 12):
+        D = oracle.disk_count(r)
+        for _ in range(200):
+            px, py = int(rng.integers(-3, 56)), int(rng.integers(-3, 40))
+            s = oracle.disk_sum(frame, r, px, py)
+            assert oracle.likelihood_at(frame, r, px, py) == (256.0 * s - 41984.0 * D) / (50.0 * D)
+
+
+# ----------------------------------------------------------------------------- weights, normalisation, CDF
+def test_weights_shift_invariance_and_dominance():
+    rng = np.random.default_rng(1)
+    L = np.round(rng.uniform(-300, 300, 1000) * 8) / 8
+    M, e = oracle.weights(L)
+    assert M == L.max() and e.max() == 1.0 and np.all(e >= 0)
+    M2, e2 = oracle.weights(L + 1024.0)
+    assert M2 == M + 1024.0 and np.array_equal(e, e2)
+    M3, e3 = oracle.weights(np.array([-1000.0, 0.0, -1000.0]))
+    assert M3 == 0.0 and np.array_equal(e3, [0.0, 1.0, 0.0])
+
+
+def test_normalise_invariants():
+    rng = np.random.default_rng(2)
+    e = rng.uniform(0, 1, 5000)
+    x = rng.uniform(0, 512, 5000)
+    y = rng.uniform(0, 512, 5000)
+    S, xh, yh = oracle.normalise(e, x, y)
+    assert abs(S - math.fsum(e)) <= 4 * np.finfo(float).eps * S
+    assert abs(math.fsum(e / S) - 1.0) < 5000 * np.finfo(float).eps
+    assert abs(xh - math.fsum(e * x) / math.fsum(e)) < 1e-12
+    assert x.min() <= xh <= x.max() and y.min() <= yh <= y.max()
+    S1, xh1, yh1 = oracle.normalise(np.array([0.25]), np.array([3.5]), np.array([-7.25]))
+    assert (S1, xh1, yh1) == (0.25, 3.5, -7.25)
+    S2, xh2, yh2 = oracle.normalise(e[:100], np.full(100, 123.375), np.full(100, 9.0625))
+    assert abs(xh2 - 123.375) < 1e-12 and abs(yh2 - 9.0625) < 1e-12
+
+
+def test_cdf_matches_cumsum_and_is_monotone():
+    rng = np.random.default_rng(3)
+    for n in (1, 2, 7, 1000, 100003):
+        e = rng.exponential(size=n) * (rng.uniform(size=n) < 0.3)
+        e[rng.integers(n)] = 1.0
+        S, _, _ = oracle.normalise(e, np.zeros(n), np.zeros(n))
+        C = oracle.cdf(e, S)
+        assert C[-1] == 1.0
+        assert np.all(np.diff(C) >= 0)
+        np.testing.assert_allclose(C, np.cumsum(e) / e.sum(), rtol=0, atol=n * np.finfo(float).eps)
+
+
+# ----------------------------------------------------------------------------- systematic resampling
+def _counts(a, n):
+    return np.bincount(a, minlength=n)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_resample_uniform_weights_identity(prec):
+    for n in (1, 2, 8, 1024, 1 << 16):
+        C = (np.arange(n, dtype=np.float64) + 1) / n     # exact for powers of two
+        # in FP32, j + u0 must itself be exact (u0 = 2^-24 vanishes next to j >= 1)
+        offsets = (2.0 ** -24, 0.5, 1 - 2.0 ** -24) if prec == "f64" else (0.25, 0.5, 0.75)
+        for u0 in offsets:
+            a = oracle.resample(C, u0, prec)
+            assert np.array_equal(a, np.arange(n))
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_resample_offspring_counts_floor_ceil(prec):
+    rng = np.random.default_rng(4)
+    for n in (1, 2, 3, 7, 100, 1000, 4097):
+        for trial in range(5):
+            e = rng.exponential(size=n) ** 3
+            S, _, _ = oracle.normalise(e, np.zeros(n), np.zeros(n))
+            C = oracle.cdf(e, S)
+            if prec == "f32":
+                C = C.astype(np.float32).astype(np.float64)
+            u0 = float(oracle.uniform([rng.integers(0, 2 ** 32, dtype=np.uint64)])[0])
+            a = oracle.resample(C, u0, prec)
+            assert np.all(np.diff(a) >= 0) and a.min() >= 0 and a.max() < n
+            cnt = _counts(a, n)
+            assert cnt.sum() == n
+            w = np.diff(np.concatenate([[0.0], C]))
+            if prec == "f64":   # the FP32 strata are themselves rounded; the bound is for exact u_j
+                assert np.all(cnt >= np.floor(n * w - 1e-9)) and np.all(cnt <= np.ceil(n * w + 1e-9))
+
+
+def test_resample_brute_force_expectation():
+    """N <= 8: averaged over a fine grid of offsets u0, the offspring count of particle k
+    equals N * w_k (systematic resampling is unbiased)."""
+    rng = np.random.default_rng(6)
+    for n in (1, 2, 3, 5, 8):
+        e = rng.uniform(0.01, 1.0, n)
+        S, _, _ = oracle.normalise(e, np.zeros(n), np.zeros(n))
+        C = oracle.cdf(e, S)
+        w = np.diff(np.concatenate([[0.0], C]))
+        G = 20000
+        tot = np.zeros(n)
+        for g in range(G):
+            u0 = (g + 0.5) / G
+            tot += _counts(oracle.resample(C, u0, "f64"), n)
+        np.testing.assert_allclose(tot / G, n * w, atol=n / G * 2)
+
+
+def test_resample_dominant_and_clamp():
+    C = np.array([0.0, 0.0, 1.0, 1.0])
+    assert np.array_equal(oracle.resample(C, 0.3, "f64"), [2, 2, 2, 2])
+    C2 = np.array([0.2, 0.5, 0.9])     # no entry reaches the last strata: clamp to N-1
+    assert np.array_equal(oracle.resample(C2, 0.9, "f64"), [1, 2, 2])
+    # ties: a stratum point equal to a CDF entry belongs to that entry (first C_k >= u_j)
+    C3 = np.array([0.25, 0.5, 0.75, 1.0])
+    for prec in ("f64", "f32"):
+        assert np.array_equal(oracle.resample(C3, 1.0, prec), [0, 1, 2, 3])
+        assert np.array_equal(oracle.resample(C3, 0.0, prec), [0, 0, 1, 2])
+
+
+# ----------------------------------------------------------------------------- propagation, Eq. 1-2
+def test_propagation_moments_paper_motion():
+    """Eq. 1-2: x ~ N(1 + x_anc, 5^2), y ~ N(2 + y_anc, 2^2)."""
+    n = 200000
+    x, y = oracle.propagate(n, 4, 9, None, None, None, init=(100.0, 50.0), drift=(1.0, 2.0),
+                            sigma=(5.0, 2.0))
+    assert abs(x.mean() - 101.0) < 5 * 5.0 / math.sqrt(n)
+    assert abs(y.mean() - 52.0) < 5 * 2.0 / math.sqrt(n)
+    assert abs(x.std() - 5.0) < 0.05 and abs(y.std() - 2.0) < 0.02
+
+
+def test_propagation_gathers_ancestors():
+    n = 1000
+    rng = np.random.default_rng(8)
+    xa = rng.uniform(0, 100, n)
+    ya = rng.uniform(0, 100, n)
+    anc = np.sort(rng.integers(0, n, n))
+    x, y = oracle.propagate(n, 2, 5, xa, ya, anc, drift=(0.5, -1.5), sigma=(0.0, 0.0))
+    assert np.array_equal(x, xa[anc] + 0.5) and np.array_equal(y, ya[anc] - 1.5)
+    # the noise is keyed by (particle, frame): other frames draw other numbers
+    x1, _ = oracle.propagate(n, 2, 5, xa, ya, anc, sigma=(1.0, 1.0))
+    x2, _ = oracle.propagate(n, 3, 5, xa, ya, anc, sigma=(1.0, 1.0))
+    assert not np.allclose(x1, x2)
+
+
+# ----------------------------------------------------------------------------- whole tracker
+def test_track_recovers_ground_truth_config1():
+    """128x128, 10 frames, r = 5, noise 5, 1000 particles, sigma 1, seed 1: the FP64 track
+    stays within a pixel of the true disk centre (Sec. 4, verification)."""
+    v = synth.make_video(128, 128, 10, 5, noise=5.0, seed=1)
+    est, M, S = oracle.track(v.frames, 1000, 5, init=tuple(v.centres[0]), seed=1)
+    err = np.sqrt(np.sum((est - v.centres) ** 2, axis=1))
+    assert np.sqrt(np.mean(err ** 2)) < 1.0 and err.max() < 1.5
+    assert np.all(S >= 1.0) and np.all(M <= 11648 / 25)
+
+
+def test_track_noiseless_recovers_integer_centres():
+    v = synth.make_video(128, 128, 12, 5, noise=0.0, seed=2)
+    est, _, _ = oracle.track(v.frames, 4000, 5, init=tuple(v.centres[0]), seed=11)
+    assert np.array_equal(oracle.round_pixel(est[:, 0]), v.centres[:, 0].astype(np.int64))
+    assert np.array_equal(oracle.round_pixel(est[:, 1]), v.centres[:, 1].astype(np.int64))
+
+
+def test_track_phases_equal_whole_and_thread_count_invariant():
+    v = synth.make_video(128, 96, 6, 3, noise=8.0, seed=4, v=(2, 1))
+    kw = dict(init=tuple(v.centres[0]), seed=21, tracker=3)
+    est1, M1, S1 = oracle.track(v.frames, 5000, 3, nthreads=1, **kw)
+    est4, M4, S4 = oracle.track(v.frames, 5000, 3, nthreads=4, **kw)
+    assert np.array_equal(est1, est4) and np.array_equal(M1, M4) and np.array_equal(S1, S4)
+    recs = list(oracle.track_steps(v.frames, 5000, 3, **kw))
+    assert np.array_equal(np.array([r.est for r in recs]), est1)
+    assert np.array_equal(np.array([r.M for r in recs]), M1)
