@@ -1,0 +1,371 @@
+#!/usr/bin/env python
+"""Particle-steps/s of the per-frame SIR tracker step on GB300 (one JSON line on rank 0).
+
+Workload (single tracker at scale): a 512x512 synthetic video of 100 frames, a disk of
+radius 5 moving (+1, -2) px/frame with noise sigma 5, tracked by 2^20 particles (random
+walk sigma 1 px, init at the true start, Philox seed 1).  One bench step = the whole
+100-frame track through the C ABI (pf_reset + 100 x pf_step_frame), frames resident in
+HBM; L2 is flushed (a 512 MiB write) between timed steps, outside the timed events.
+The headline arithmetic is FP16 (half2 propagation and likelihood, FP32 weights / scan);
+REF64, F32 and BF16 are timed beside it on the same Philox stream, with their track
+RMSE against the REF64 GPU track.
+
+--impl reference times the CPU FP64 oracle (oracle/) on the host cores instead, each
+step a bounded sample of the same workload (its first frames at full N).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+W_, H_, T_, R_, N_, NOISE_, SEED_ = 512, 512, 100, 5, 1 << 20, 5.0, 1
+WORKLOAD = ("single tracker at scale: 512x512 uint8 synthetic video, 100 frames, disk r=5 "
+            "moving (+1,-2) px/frame, noise sigma 5, 2^20 particles, random walk sigma 1 px, Philox seed 1")
+METRIC = "particle-steps/s"
+# algorithmic HBM bytes per particle-step of the fused step kernel: read L + x,y of the
+# previous frame, write x,y + L of the new frame (the frame's template pixels are L2/L1 hits)
+BYTES_PER_PSTEP = {"ref64": 48, "f32": 24, "f16": 12, "bf16": 12}
+DTYPE_NAME = {"ref64": "f64", "f32": "f32", "f16": "f16", "bf16": "bf16"}
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=30)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--precision", default="f16", choices=["ref64", "f32", "f16", "bf16"])
+    p.add_argument("--only", action="store_true", help="time the headline precision only")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--frames", type=int, default=T_)
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------------------- distributed
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 50 ms while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,utilization.gpu")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            if self.thread:
+                self.thread.join(timeout=2)
+
+    def summary(self, t0=None, t1=None):
+        sm, mx, reasons, n_all = [], [], set(), 0
+        for ts, line in self.lines:
+            if t0 is not None and not (t0 <= ts <= t1):
+                continue
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 10:
+                continue
+            n_all += 1
+            try:
+                s, m, util = float(f[1]), float(f[2]), float(f[9])
+            except ValueError:
+                continue
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+            mx.append(m)
+            if util > 0:
+                sm.append(s)
+        if not mx:
+            return None
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": n_all, "samples_under_load": len(sm)}
+
+
+# ---------------------------------------------------------------------------- helpers
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def _kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2308_00763_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(prec):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary, if it was
+    taken on the current kernel source; else None."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "step_kernel_traffic.json")) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if d.get("source_sha") != _kernel_source_hash():
+        return None
+    v = d.get("dram_bytes_per_launch", {}).get(prec)
+    return float(v) if v is not None else None
+
+
+def _rmse(a, b):
+    import numpy as np
+    return float(math.sqrt(np.mean(np.sum((np.asarray(a) - np.asarray(b)) ** 2, axis=1))))
+
+
+# ---------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import numpy as np
+    import oracle
+    from paper_2308_00763_gb300 import synth
+    oracle.build()
+    cores = os.cpu_count() or 1
+    frames_per_step = 2
+    v = synth.make_video(W_, H_, frames_per_step, R_, noise=NOISE_, seed=SEED_)
+    init = tuple(v.centres[0])
+    for _ in range(args.warmup):
+        oracle.track(v.frames, N_, R_, init=init, seed=SEED_, nthreads=cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.track(v.frames, N_, R_, init=init, seed=SEED_, nthreads=cores)
+    dt = time.perf_counter() - t0
+    val = N_ * frames_per_step * args.steps / dt
+    sample = "first %d frames of the workload at full N = 2^20 per step (FP64 oracle, %d threads)" % (
+        frames_per_step, cores)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": METRIC, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "step": "oracle sample: " + sample},
+        "cpu_baseline": {"value": val, "unit": METRIC, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": val, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------- our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_2308_00763_gb300 as pf
+    from paper_2308_00763_gb300 import synth
+    pf.lib(build_if_missing=True)
+
+    T = args.frames
+    v = synth.make_video(W_, H_, T, R_, noise=NOISE_, seed=SEED_)
+    init = tuple(v.centres[0])
+    frames_dev = torch.from_numpy(v.frames).to(dev)
+    frames_pin = torch.from_numpy(v.frames).pin_memory()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    precs = [args.precision] if args.only else ["ref64", "f32", "f16", "bf16"]
+    if args.precision in precs:
+        precs.remove(args.precision)
+    precs.append(args.precision)     # headline last (clock sampling window)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    def max_over_ranks(x):
+        if ws == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    clocks = ClockSampler(local)
+    results = {}
+    tracks = {}
+    for prec in precs:
+        f = pf.Filter(W_, H_, N_, R_, prec, init=init, seed=SEED_ + rank, tracker_id=rank, stream=stream)
+        for _ in range(args.warmup):
+            f.reset()
+            f.run(frames_dev)
+        barrier()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        headline = prec == args.precision
+        if headline:
+            clocks.start()
+            time.sleep(0.3)
+        wall0 = time.time()
+        for k in range(args.steps):
+            flush.zero_()                       # L2 flush, outside the timed events
+            ev[k][0].record(stream)
+            f.reset()
+            f.run(frames_dev)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+        wall1 = time.time()
+        if headline:
+            clocks.stop()
+        total_ms = sum(a.elapsed_time(b) for a, b in ev)
+        total_ms = max_over_ranks(total_ms)
+        value = N_ * T * args.steps * ws / (total_ms * 1e-3)
+        tracks[prec] = f.estimates(0, T)
+        # per-launch duration of the step kernel (events between launches on its stream)
+        f.reset()
+        lev = [torch.cuda.Event(enable_timing=True) for _ in range(T + 1)]
+        flush.zero_()
+        lev[0].record(stream)
+        for t in range(T):
+            f.step(frames_dev[t])
+            lev[t + 1].record(stream)
+        torch.cuda.synchronize(dev)
+        launch_ms = [lev[t].elapsed_time(lev[t + 1]) for t in range(T)]
+        # end to end: pinned host frames through the C ABI, estimates read back
+        barrier()
+        e2e_times = []
+        for k in range(max(1, min(args.steps, 10))):
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            f.reset()
+            f.run(frames_pin)
+            est = f.estimates(0, T)            # synchronises + D2H of the per-frame estimates
+            e2e_times.append(time.perf_counter() - t0)
+        e2e_s = max_over_ranks(sum(e2e_times)) / len(e2e_times)
+        results[prec] = {
+            "value": value, "ms_per_step": total_ms / args.steps,
+            "launch_us_mean": 1e3 * statistics.mean(launch_ms),
+            "launch_us_median": 1e3 * statistics.median(launch_ms),
+            "e2e_value": N_ * T * ws / e2e_s, "wall": (wall0, wall1),
+        }
+        f.close()
+        del est
+
+    # accuracy of every precision against the REF64 GPU track
+    ref = tracks.get("ref64")
+    for prec in results:
+        results[prec]["rmse_px_vs_ref64_gpu"] = _rmse(tracks[prec], ref) if ref is not None else None
+    results_truth = {p: _rmse(tracks[p], v.centres) for p in tracks}
+
+    hp = args.precision
+    head = results[hp]
+    hbm, peak_kind = _peaks()
+    achieved_gbs = BYTES_PER_PSTEP[hp] * N_ / (head["launch_us_median"] * 1e-6) / 1e9
+    traffic = _traffic(hp)
+    line = {
+        "metric": METRIC, "value": head["value"], "unit": METRIC, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": DTYPE_NAME[hp], "data": "synthetic",
+        "config": {"workload": WORKLOAD, "frames_per_step": T, "particles": N_, "precision": hp,
+                   "l2": "flushed between timed steps (512 MiB write); state stays L2-resident across the frames of a step",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved_gbs / hbm, "traffic": traffic,
+                     "kernel": "step_kernel<%s>" % hp, "peak_source": peak_kind,
+                     "bytes_per_particle_step": BYTES_PER_PSTEP[hp],
+                     "launch_us_median": head["launch_us_median"]},
+        "e2e": {"value": head["e2e_value"], "unit": METRIC, "h2d_bytes_per_step": int(W_ * H_ * T),
+                "d2h_bytes_per_step": int(16 * T)},
+        "gpu_launches": args.steps * T,
+        "accuracy": {"rmse_px_vs_ref64_gpu": head["rmse_px_vs_ref64_gpu"],
+                     "rmse_px_vs_ground_truth": results_truth.get(hp)},
+        "per_precision": {p: {k: r[k] for k in ("value", "ms_per_step", "launch_us_median", "e2e_value",
+                                                "rmse_px_vs_ref64_gpu")}
+                          for p, r in results.items()},
+    }
+    cs = clocks.summary(*head["wall"]) or clocks.summary()
+    line["clocks"] = cs
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = _cpu_baseline(v, tracks)
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
+def _cpu_baseline(v, tracks):
+    """The FP64 oracle as it stands, on the host cores, over the first frames of the same
+    workload at full N (bounded to ~10-30 s); also the GPU tracks' error on those frames."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    frames = 4
+    t0 = time.perf_counter()
+    est, _, _ = oracle.track(v.frames[:frames], N_, R_, init=tuple(v.centres[0]), seed=SEED_, nthreads=cores)
+    dt = time.perf_counter() - t0
+    out = {"value": N_ * frames / dt, "unit": METRIC, "cores": cores, "kind": "oracle",
+           "sample": "first %d frames of the workload at full N = 2^20, FP64 oracle, %d threads" % (frames, cores),
+           "seconds": dt}
+    out["gpu_rmse_px_vs_oracle_on_sample"] = {p: _rmse(tr[:frames], est) for p, tr in tracks.items()}
+    return out
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,186 @@
+/*
+ * pf.h -- C ABI of the GB300 (sm_103a) particle-filter library: the per-frame SIR
+ * (sequential importance resampling) step of a video object tracker, after
+ * Schieffer et al., "Boosting the Performance of Object Tracking with a
+ * Half-Precision Particle Filter on GPU" (arXiv 2308.00763).
+ *
+ * The problem (Sec. 1 and Sec. 3): track one object in a monochrome video.  Each
+ * frame, every particle is propagated around its ancestor (Eq. 1-2), scored against
+ * the frame under a disk template (Eq. 3, in its overflow-safe scaled form Eq. 4 for
+ * half precision), weighted by exp(L - max L) (Eq. 5, log-sum-exp), normalised, summed
+ * into a cumulative distribution by an inclusive prefix sum, and resampled
+ * systematically (Sec. 3, "Resampling").  The paper switches the whole filter between
+ * double, single and half precision by a template argument (Sec. 3, "Implementation");
+ * here the precision is a field of the configuration.
+ *
+ * Conventions for every entry point:
+ *  - Pointers are plain host or device addresses, as each argument states; sizes are
+ *    in bytes unless stated otherwise.  No entry point takes ownership of a caller's
+ *    buffer.  Handles (pf_filter, pf_batch) are owned by the library and released only
+ *    by their destroy call.
+ *  - Every call returns a pf_status; nothing is thrown across the ABI.  A handle whose
+ *    device work has failed (a CUDA error, or a device wait that gave up) keeps that
+ *    status and answers PF_ERR_STATE to every later call except get/destroy.
+ *  - Work is enqueued on the handle's CUDA stream and is asynchronous unless the entry
+ *    point says it synchronises.  One host thread at a time per handle.
+ *  - Frames: width x height uint8 pixels, row-major (x = column, y = row), rows
+ *    pitch_bytes apart (pitch_bytes >= width).
+ */
+#ifndef PF_GB300_H
+#define PF_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PF_OK = 0,
+    PF_ERR_ARG = 1,        /* an argument is out of range or NULL */
+    PF_ERR_OOM = 2,        /* device or pinned memory could not be allocated */
+    PF_ERR_CUDA = 3,       /* a CUDA runtime call or kernel launch failed */
+    PF_ERR_TIMEOUT = 4,    /* a bounded device-side wait gave up (results of that step are invalid) */
+    PF_ERR_STATE = 5,      /* the handle failed earlier, or the call does not fit its state */
+    PF_ERR_ADMISSION = 6   /* serving: a stream was refused by the memory or compute budget */
+} pf_status;
+
+/* Arithmetic of the filter (Sec. 3: double / float / half specialisations). */
+typedef enum {
+    PF_REF64 = 0,  /* FP64 everywhere: the reference mode */
+    PF_F32 = 1,    /* FP32 everywhere */
+    PF_F16 = 2,    /* half2 propagation and likelihood (Eq. 4 form, half accumulation),
+                      half positions as offsets from an integer anchor, FP32 weights, sums, CDF */
+    PF_BF16 = 3    /* as PF_F16 in bfloat16, with the likelihood accumulated in FP32 */
+} pf_precision;
+
+/* pf_config.flags */
+#define PF_FLAG_DEBUG_ARRAYS 0x1u  /* keep the last step's CDF and ancestor indices (pf_get_debug) */
+#define PF_FLAG_ACCUM32      0x2u  /* PF_F16: accumulate the likelihood in FP32 instead of half */
+
+typedef struct {
+    int32_t width, height;     /* frame size in pixels, each in [1, 65535] */
+    int64_t num_particles;     /* N, in [1, 2^31 - 1] */
+    int32_t disk_radius;       /* r, in [0, 64]: template = {(dx,dy): dx^2 + dy^2 <= r^2} */
+    int32_t precision;         /* pf_precision */
+    double  bg_level, fg_level;/* background / foreground intensity of Eq. 3 (100, 228) */
+    double  init_x, init_y;    /* every particle starts here (pixel units) */
+    double  sigma_x, sigma_y;  /* std of the transition noise, Eq. 1-2 (paper: 5, 2) */
+    double  drift_x, drift_y;  /* mean displacement per frame, Eq. 1-2 (paper: 1, 2) */
+    uint64_t seed;             /* Philox4x32-10 key */
+    uint32_t tracker_id;       /* Philox counter word 3: separates trackers sharing a seed */
+    uint32_t flags;            /* PF_FLAG_* */
+    int32_t est_capacity;      /* frames of estimates kept on the device; 0 = 4096 */
+    int32_t reserved;          /* must be 0 */
+} pf_config;
+
+typedef struct pf_filter pf_filter;
+typedef struct pf_batch pf_batch;
+
+/* Human-readable name of a status code (static storage; never NULL). */
+const char *pf_status_string(pf_status s);
+
+/* Create one tracker (Sec. 3, Fig. 1 "initialisation"): validates *cfg, allocates its
+ * device buffers on the current CUDA device and binds it to `cuda_stream` (a
+ * cudaStream_t; NULL = the legacy default stream).  *out receives the handle.
+ * Errors: PF_ERR_ARG (bad field, NULL pointer), PF_ERR_OOM, PF_ERR_CUDA. */
+pf_status pf_create(const pf_config *cfg, void *cuda_stream, pf_filter **out);
+
+/* One frame of the filter (Sec. 3, Fig. 1: propagation, likelihood, max finding,
+ * weighting, normalising, resampling).  `frame` is a host pointer if frame_on_device
+ * is 0 (copied to the library's device buffer on the handle's stream before the
+ * call returns for pageable memory; pinned memory must stay unchanged until the step
+ * has run) or a device pointer if 1 (must stay valid until the step has run).
+ * Resampling of the previous frame's particles happens at the start of this step;
+ * the estimate of this frame is available to pf_estimate afterwards.  Asynchronous.
+ * Errors: PF_ERR_ARG, PF_ERR_STATE, PF_ERR_CUDA. */
+pf_status pf_step_frame(pf_filter *f, const uint8_t *frame, int64_t pitch_bytes,
+                        int32_t frame_on_device);
+
+/* Run `count` frames in one call: frame i at frames + i * frame_stride (bytes), rows
+ * pitch_bytes apart, all on the host (frames_on_device = 0) or all on the device (1).
+ * Equivalent to `count` calls of pf_step_frame.  Asynchronous. */
+pf_status pf_run_frames(pf_filter *f, const uint8_t *frames, int64_t pitch_bytes,
+                        int64_t frame_stride, int32_t count, int32_t frames_on_device);
+
+/* State estimate of frame `frame_index` (the weighted mean of the propagated
+ * particles before resampling).  Synchronises the handle's stream; checks the sticky
+ * device status.  Only the last est_capacity frames are kept.  x, y: host pointers.
+ * Errors: PF_ERR_ARG (index not stepped yet or overwritten), PF_ERR_TIMEOUT,
+ * PF_ERR_STATE, PF_ERR_CUDA. */
+pf_status pf_estimate(pf_filter *f, int64_t frame_index, double *x, double *y);
+
+/* Estimates of frames first .. first+count-1 into xy[2*count] (host), plus, if
+ * max_and_sum is not NULL, (max L, sum of exp(L - max L)) of each frame into
+ * max_and_sum[2*count].  Synchronises like pf_estimate. */
+pf_status pf_estimates(pf_filter *f, int64_t first, int32_t count, double *xy,
+                       double *max_and_sum);
+
+/* Restart the tracker at frame 0 with every particle back at (init_x, init_y), as
+ * after pf_create, without reallocating.  Enqueued on the handle's stream (asynchronous);
+ * estimates of earlier frames become unavailable.  Errors: PF_ERR_STATE, PF_ERR_CUDA. */
+pf_status pf_reset(pf_filter *f);
+
+/* Number of frames stepped so far (host-side count; no synchronisation). */
+int64_t pf_frames_done(const pf_filter *f);
+
+/* Release the handle and every device buffer it owns (synchronises its stream first).
+ * NULL is accepted. */
+pf_status pf_destroy(pf_filter *f);
+
+/* Checkpoint.  The state that the next step reads: the particles of the last frame
+ * (positions before resampling and their log-likelihoods) and the frame scalars.
+ * Layout (all little-endian, host memory):
+ *   pf_state_header, then x[N], y[N], L[N] in the precision's storage type:
+ *   REF64: double, double, double   F32: float, float, float
+ *   F16:   half,   half,   half     BF16: bfloat16 x3
+ *   (F16/BF16 positions are offsets from the integer anchor (anchor_x, anchor_y)).
+ * pf_get_state: with host_buf NULL, writes the size to *bytes; otherwise *bytes must
+ * be at least that size.  Synchronises.  pf_set_state: replaces the state (same
+ * precision and N required); the next step resamples from it. */
+typedef struct {
+    uint32_t magic;            /* 'PFS1' = 0x31534650 */
+    int32_t  precision;
+    int64_t  num_particles;
+    int64_t  t;                /* index of the next frame to step (frames done) */
+    double   max_l;            /* M = max L of the stored frame */
+    double   sum_e;            /* S = sum exp(L - M) */
+    double   anchor_x, anchor_y;       /* anchor of the stored positions (integers) */
+    double   next_anchor_x, next_anchor_y; /* anchor the next step writes against */
+    double   est_x, est_y;     /* estimate of the stored frame */
+} pf_state_header;
+
+pf_status pf_get_state(pf_filter *f, void *host_buf, size_t *bytes);
+pf_status pf_set_state(pf_filter *f, const void *host_buf, size_t bytes);
+
+/* Test hooks (flags & PF_FLAG_DEBUG_ARRAYS): after a step, `which` = 0 copies the
+ * ancestor index a_j of every particle j of that step (int32[N]; undefined at frame
+ * 0), `which` = 1 the CDF C_k of the previous frame as the step computed it (double[N]
+ * for REF64, float[N] otherwise).  Synchronises.  host_buf: host pointer of `bytes`. */
+pf_status pf_get_debug(pf_filter *f, int32_t which, void *host_buf, size_t bytes);
+
+/* Test hook: Philox4x32-10 on the device, the same generator the step uses: for each
+ * of the n counters ctrs[4*i..4*i+3] (host) with key = seed, writes four words to
+ * out[4*i..] (host).  Synchronises the legacy default stream. */
+pf_status pf_debug_philox(const uint32_t *ctrs, int64_t n, uint64_t seed, uint32_t *out);
+
+/* ---------------------------------------------------------------- batches
+ * Many independent trackers (different N, frame sizes, radii, seeds), stepped together
+ * by one persistent segmented launch per frame.  All trackers of a batch share one
+ * precision.  Frames: frames[i] is tracker i's frame (device pointers), rows
+ * pitches[i] bytes apart; a tracker whose active_mask[i] is 0 is not stepped (its
+ * frame pointer may be NULL).  active_mask NULL = all active. */
+pf_status pf_batch_create(const pf_config *cfgs, int32_t n, void *cuda_stream, pf_batch **out);
+pf_status pf_batch_step(pf_batch *b, const uint8_t *const *frames, const int64_t *pitches,
+                        const uint8_t *active_mask);
+/* Estimates of frame `frame_index` of every tracker into xy[2*n] (host); trackers that
+ * have not stepped that frame get NaN.  Synchronises. */
+pf_status pf_batch_estimates(pf_batch *b, int64_t frame_index, double *xy);
+pf_status pf_batch_destroy(pf_batch *b);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PF_GB300_H */

@@ -1,0 +1,417 @@
+"""ctypes binding of the C ABI in ``include/pf.h`` (argument marshalling only).
+
+Every function of the header is exposed under its own name; :class:`Filter` and
+:class:`Batch` wrap the handles for numpy / torch callers.  All filter arithmetic runs
+in the sm_103a library ``_build/libpf_gb300.so``; there is no fallback: if the library
+is missing or cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "PF_OK", "PF_ERR_ARG", "PF_ERR_OOM", "PF_ERR_CUDA", "PF_ERR_TIMEOUT", "PF_ERR_STATE",
+    "PF_ERR_ADMISSION", "PF_REF64", "PF_F32", "PF_F16", "PF_BF16", "PF_FLAG_DEBUG_ARRAYS",
+    "PF_FLAG_ACCUM32", "PfConfig", "PfStateHeader", "PfError", "lib", "library_path",
+    "pf_status_string", "pf_create", "pf_step_frame", "pf_run_frames", "pf_estimate",
+    "pf_estimates", "pf_frames_done", "pf_reset", "pf_destroy", "pf_get_state", "pf_set_state", "pf_get_debug",
+    "pf_debug_philox", "pf_batch_create", "pf_batch_step", "pf_batch_estimates",
+    "pf_batch_destroy", "Filter", "Batch", "PRECISIONS", "EXPORTED",
+]
+
+PF_OK, PF_ERR_ARG, PF_ERR_OOM, PF_ERR_CUDA, PF_ERR_TIMEOUT, PF_ERR_STATE, PF_ERR_ADMISSION = range(7)
+PF_REF64, PF_F32, PF_F16, PF_BF16 = range(4)
+PF_FLAG_DEBUG_ARRAYS = 0x1
+PF_FLAG_ACCUM32 = 0x2
+PRECISIONS = {"ref64": PF_REF64, "f64": PF_REF64, "f32": PF_F32, "f16": PF_F16, "bf16": PF_BF16}
+_POS_DTYPE = {PF_REF64: np.float64, PF_F32: np.float32, PF_F16: np.float16, PF_BF16: None}
+
+
+class PfConfig(ctypes.Structure):
+    _fields_ = [
+        ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+        ("num_particles", ctypes.c_int64),
+        ("disk_radius", ctypes.c_int32), ("precision", ctypes.c_int32),
+        ("bg_level", ctypes.c_double), ("fg_level", ctypes.c_double),
+        ("init_x", ctypes.c_double), ("init_y", ctypes.c_double),
+        ("sigma_x", ctypes.c_double), ("sigma_y", ctypes.c_double),
+        ("drift_x", ctypes.c_double), ("drift_y", ctypes.c_double),
+        ("seed", ctypes.c_uint64), ("tracker_id", ctypes.c_uint32), ("flags", ctypes.c_uint32),
+        ("est_capacity", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    ]
+
+
+class PfStateHeader(ctypes.Structure):
+    _fields_ = [
+        ("magic", ctypes.c_uint32), ("precision", ctypes.c_int32),
+        ("num_particles", ctypes.c_int64), ("t", ctypes.c_int64),
+        ("max_l", ctypes.c_double), ("sum_e", ctypes.c_double),
+        ("anchor_x", ctypes.c_double), ("anchor_y", ctypes.c_double),
+        ("next_anchor_x", ctypes.c_double), ("next_anchor_y", ctypes.c_double),
+        ("est_x", ctypes.c_double), ("est_y", ctypes.c_double),
+    ]
+
+
+class PfError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__("%s: %s (status %d)" % (what, _status_name(status), status))
+
+
+_P = ctypes.c_void_p
+_I32 = ctypes.c_int32
+_I64 = ctypes.c_int64
+_SIG = {
+    "pf_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "pf_create": (ctypes.c_int, [ctypes.POINTER(PfConfig), _P, ctypes.POINTER(_P)]),
+    "pf_step_frame": (ctypes.c_int, [_P, _P, _I64, _I32]),
+    "pf_run_frames": (ctypes.c_int, [_P, _P, _I64, _I64, _I32, _I32]),
+    "pf_estimate": (ctypes.c_int, [_P, _I64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "pf_estimates": (ctypes.c_int, [_P, _I64, _I32, _P, _P]),
+    "pf_frames_done": (_I64, [_P]),
+    "pf_reset": (ctypes.c_int, [_P]),
+    "pf_destroy": (ctypes.c_int, [_P]),
+    "pf_get_state": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_size_t)]),
+    "pf_set_state": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
+    "pf_get_debug": (ctypes.c_int, [_P, _I32, _P, ctypes.c_size_t]),
+    "pf_debug_philox": (ctypes.c_int, [_P, _I64, ctypes.c_uint64, _P]),
+    "pf_batch_create": (ctypes.c_int, [ctypes.POINTER(PfConfig), _I32, _P, ctypes.POINTER(_P)]),
+    "pf_batch_step": (ctypes.c_int, [_P, _P, _P, _P]),
+    "pf_batch_estimates": (ctypes.c_int, [_P, _I64, _P]),
+    "pf_batch_destroy": (ctypes.c_int, [_P]),
+}
+EXPORTED = tuple(_SIG)
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = False):
+    """The loaded library.  Raises if it is missing (no CPU fallback exists)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = library_path()
+        if not os.path.exists(path):
+            if build_if_missing:
+                _build.build()
+            else:
+                raise RuntimeError("the CUDA library %s is not built; run "
+                                   "`python -c 'import __graft_entry__ as g; g.build()'`" % path)
+        handle = ctypes.CDLL(path)
+        for name, (res, args) in _SIG.items():
+            fn = getattr(handle, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = handle
+        return _lib
+
+
+def _status_name(status: int) -> str:
+    names = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error",
+             4: "device wait timed out", 5: "failed or wrong state", 6: "admission refused"}
+    return names.get(status, "unknown")
+
+
+def _check(status: int, what: str):
+    if status != PF_OK:
+        raise PfError(status, what)
+
+
+# ------------------------------------------------------------------ raw C ABI, same names
+def pf_status_string(s: int) -> str:
+    return lib().pf_status_string(s).decode()
+
+
+def pf_create(cfg: PfConfig, stream=None):
+    h = _P()
+    _check(lib().pf_create(ctypes.byref(cfg), _P(stream or 0), ctypes.byref(h)), "pf_create")
+    return h
+
+
+def pf_step_frame(h, frame_ptr: int, pitch: int, on_device: int):
+    return lib().pf_step_frame(h, _P(frame_ptr), pitch, on_device)
+
+
+def pf_run_frames(h, frames_ptr: int, pitch: int, stride: int, count: int, on_device: int):
+    return lib().pf_run_frames(h, _P(frames_ptr), pitch, stride, count, on_device)
+
+
+def pf_estimate(h, t: int):
+    x = ctypes.c_double()
+    y = ctypes.c_double()
+    _check(lib().pf_estimate(h, t, ctypes.byref(x), ctypes.byref(y)), "pf_estimate")
+    return x.value, y.value
+
+
+def pf_estimates(h, first: int, count: int, with_stats: bool = False):
+    xy = np.empty((count, 2), np.float64)
+    ms = np.empty((count, 2), np.float64) if with_stats else None
+    _check(lib().pf_estimates(h, first, count, xy.ctypes.data_as(_P),
+                              ms.ctypes.data_as(_P) if ms is not None else None), "pf_estimates")
+    return (xy, ms) if with_stats else xy
+
+
+def pf_reset(h):
+    return lib().pf_reset(h)
+
+
+def pf_frames_done(h) -> int:
+    return int(lib().pf_frames_done(h))
+
+
+def pf_destroy(h):
+    return lib().pf_destroy(h)
+
+
+def pf_get_state(h) -> bytes:
+    n = ctypes.c_size_t(0)
+    _check(lib().pf_get_state(h, None, ctypes.byref(n)), "pf_get_state")
+    buf = ctypes.create_string_buffer(n.value)
+    _check(lib().pf_get_state(h, buf, ctypes.byref(n)), "pf_get_state")
+    return buf.raw
+
+
+def pf_set_state(h, blob: bytes):
+    _check(lib().pf_set_state(h, blob, len(blob)), "pf_set_state")
+
+
+def pf_get_debug(h, which: int, n: int, dtype):
+    out = np.empty(n, dtype)
+    _check(lib().pf_get_debug(h, which, out.ctypes.data_as(_P), out.nbytes), "pf_get_debug")
+    return out
+
+
+def pf_debug_philox(ctrs, seed: int) -> np.ndarray:
+    c = np.ascontiguousarray(np.asarray(ctrs, np.uint32).reshape(-1, 4))
+    out = np.empty_like(c)
+    _check(lib().pf_debug_philox(c.ctypes.data_as(_P), c.shape[0], seed & 0xFFFFFFFFFFFFFFFF,
+                                 out.ctypes.data_as(_P)), "pf_debug_philox")
+    return out
+
+
+def pf_batch_create(cfgs, stream=None):
+    arr = (PfConfig * len(cfgs))(*cfgs)
+    h = _P()
+    _check(lib().pf_batch_create(arr, len(cfgs), _P(stream or 0), ctypes.byref(h)), "pf_batch_create")
+    return h
+
+
+def pf_batch_step(h, frame_ptrs, pitches, active=None):
+    n = len(frame_ptrs)
+    fp = (ctypes.c_void_p * n)(*[p or 0 for p in frame_ptrs])
+    pp = (ctypes.c_int64 * n)(*pitches)
+    am = (ctypes.c_uint8 * n)(*active) if active is not None else None
+    return lib().pf_batch_step(h, fp, pp, am)
+
+
+def pf_batch_estimates(h, n: int, t: int) -> np.ndarray:
+    xy = np.empty((n, 2), np.float64)
+    _check(lib().pf_batch_estimates(h, t, xy.ctypes.data_as(_P)), "pf_batch_estimates")
+    return xy
+
+
+def pf_batch_destroy(h):
+    return lib().pf_batch_destroy(h)
+
+
+# ------------------------------------------------------------------ convenience wrappers
+def make_config(width, height, num_particles, disk_radius, precision="f32", *, init=(0.0, 0.0),
+                sigma=(1.0, 1.0), drift=(0.0, 0.0), seed=1, tracker_id=0, bg=100.0, fg=228.0,
+                flags=0, est_capacity=0) -> PfConfig:
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    return PfConfig(width=width, height=height, num_particles=num_particles, disk_radius=disk_radius,
+                    precision=prec, bg_level=bg, fg_level=fg, init_x=init[0], init_y=init[1],
+                    sigma_x=sigma[0], sigma_y=sigma[1], drift_x=drift[0], drift_y=drift[1],
+                    seed=seed & 0xFFFFFFFFFFFFFFFF, tracker_id=tracker_id, flags=flags,
+                    est_capacity=est_capacity, reserved=0)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        torch = _torch()
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+        return 0
+    return getattr(stream, "cuda_stream", stream)
+
+
+def _frame_ptr(frame):
+    """(pointer, pitch, on_device, keepalive) of a frame: torch CUDA tensor or host array."""
+    if hasattr(frame, "data_ptr") and hasattr(frame, "is_cuda"):
+        if frame.dtype.itemsize != 1 or frame.dim() < 2 or frame.stride(-1) != 1:
+            raise ValueError("frame must be a uint8 tensor with unit column stride")
+        if frame.is_cuda:
+            return frame.data_ptr(), frame.stride(-2), 1, frame
+        arr = frame.numpy()
+    else:
+        arr = frame
+    arr = np.ascontiguousarray(arr, dtype=np.uint8)
+    return arr.ctypes.data, arr.strides[-2], 0, arr
+
+
+class Filter:
+    """One tracker (pf_create / pf_step_frame / pf_estimate / pf_destroy)."""
+
+    def __init__(self, width, height, num_particles, disk_radius, precision="f32", *, stream=None, **kw):
+        self.cfg = make_config(width, height, num_particles, disk_radius, precision, **kw)
+        self.precision = self.cfg.precision
+        self.N = int(num_particles)
+        self.h = pf_create(self.cfg, _stream_ptr(stream))
+
+    # -- stepping
+    def step(self, frame):
+        ptr, pitch, dev, keep = _frame_ptr(frame)
+        _check(pf_step_frame(self.h, ptr, pitch, dev), "pf_step_frame")
+        return keep
+
+    def run(self, frames):
+        """Step every frame of a (T, H, W) uint8 array/tensor (host or CUDA)."""
+        if hasattr(frames, "is_cuda") and frames.is_cuda:
+            if frames.stride(-1) != 1:
+                raise ValueError("frames must have unit column stride")
+            _check(pf_run_frames(self.h, frames.data_ptr(), frames.stride(-2), frames.stride(0),
+                                 frames.shape[0], 1), "pf_run_frames")
+            return frames
+        arr = np.ascontiguousarray(frames.numpy() if hasattr(frames, "numpy") else frames, np.uint8)
+        _check(pf_run_frames(self.h, arr.ctypes.data, arr.strides[1], arr.strides[0], arr.shape[0], 0),
+               "pf_run_frames")
+        return arr
+
+    # -- results
+    def estimate(self, t):
+        return pf_estimate(self.h, t)
+
+    def estimates(self, first=0, count=None, with_stats=False):
+        if count is None:
+            count = self.frames_done - first
+        return pf_estimates(self.h, first, count, with_stats)
+
+    def reset(self):
+        _check(pf_reset(self.h), "pf_reset")
+
+    @property
+    def frames_done(self):
+        return pf_frames_done(self.h)
+
+    # -- checkpoint
+    def _pos_dtype(self):
+        return _POS_DTYPE[self.precision]
+
+    def get_state(self) -> dict:
+        blob = pf_get_state(self.h)
+        hdr = PfStateHeader.from_buffer_copy(blob[:ctypes.sizeof(PfStateHeader)])
+        body = np.frombuffer(blob, dtype=np.uint8, offset=ctypes.sizeof(PfStateHeader))
+        esz = {PF_REF64: 8, PF_F32: 4, PF_F16: 2, PF_BF16: 2}[self.precision]
+        raw = body.reshape(3, self.N * esz)
+        out = {k: getattr(hdr, k) for k, _ in PfStateHeader._fields_}
+        for i, name in enumerate(("x", "y", "L")):
+            out[name] = _decode(raw[i], self.precision)
+        return out
+
+    def set_state(self, st: dict):
+        hdr = PfStateHeader(magic=0x31534650, precision=self.precision, num_particles=self.N)
+        for k, _ in PfStateHeader._fields_:
+            if k not in ("magic", "precision", "num_particles") and k in st:
+                setattr(hdr, k, st[k])
+        body = b"".join(_encode(np.asarray(st[n], np.float64), self.precision) for n in ("x", "y", "L"))
+        pf_set_state(self.h, bytes(hdr) + body)
+
+    def debug(self, which):
+        if which == 0:
+            return pf_get_debug(self.h, 0, self.N, np.int32)
+        return pf_get_debug(self.h, 1, self.N, np.float64 if self.precision == PF_REF64 else np.float32)
+
+    def close(self):
+        if getattr(self, "h", None):
+            pf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Batch:
+    """Many trackers stepped by one launch per frame (pf_batch_*)."""
+
+    def __init__(self, cfgs, *, stream=None):
+        self.cfgs = list(cfgs)
+        self.n = len(self.cfgs)
+        self.h = pf_batch_create(self.cfgs, _stream_ptr(stream))
+
+    def step(self, frames, active=None):
+        """frames: list of CUDA uint8 tensors (H_i, W_i) (None where inactive)."""
+        ptrs = [f.data_ptr() if f is not None else 0 for f in frames]
+        pitches = [f.stride(0) if f is not None else 0 for f in frames]
+        _check(pf_batch_step(self.h, ptrs, pitches, active), "pf_batch_step")
+
+    def estimates(self, t):
+        return pf_batch_estimates(self.h, self.n, t)
+
+    def close(self):
+        if getattr(self, "h", None):
+            pf_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _bf16_to_f64(u16: np.ndarray) -> np.ndarray:
+    return (u16.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+
+
+def _f64_to_bf16(x: np.ndarray) -> np.ndarray:
+    f = np.asarray(x, np.float32)
+    b = f.view(np.uint32).astype(np.uint64)
+    # round to nearest even on the dropped 16 bits
+    b = (b + 0x7FFF + ((b >> 16) & 1)) >> 16
+    return b.astype(np.uint16)
+
+
+def _decode(raw: np.ndarray, prec: int) -> np.ndarray:
+    if prec == PF_REF64:
+        return raw.view(np.float64).copy()
+    if prec == PF_F32:
+        return raw.view(np.float32).astype(np.float64)
+    if prec == PF_F16:
+        return raw.view(np.float16).astype(np.float64)
+    return _bf16_to_f64(raw.view(np.uint16))
+
+
+def _encode(x: np.ndarray, prec: int) -> bytes:
+    if prec == PF_REF64:
+        return np.ascontiguousarray(x, np.float64).tobytes()
+    if prec == PF_F32:
+        return np.ascontiguousarray(x, np.float32).tobytes()
+    if prec == PF_F16:
+        return np.ascontiguousarray(x, np.float16).tobytes()
+    return _f64_to_bf16(x).tobytes()

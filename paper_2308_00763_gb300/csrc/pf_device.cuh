@@ -1,0 +1,162 @@
+// pf_device.cuh -- device building blocks of the SIR step (sm_103a, CUDA cores only).
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace pfk {
+
+// ----------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): a counter-based generator, so the
+// draw of particle j at frame t is a pure function of (seed, j, t, tag, tracker) and no
+// generator state is stored (the paper draws with cuRAND, Sec. 3 after Eq. 2).
+// ----------------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        if (round < 9) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+    }
+    return c;
+}
+
+// Uniform on (0,1) from the top 23 bits: ((w >> 9) + 1/2) * 2^-23, exact in FP32 and
+// FP64, so every precision sees the same uniforms.
+__device__ __forceinline__ float uniform_f32(uint32_t w) {
+    return (static_cast<float>(w >> 9) + 0.5f) * 1.1920928955078125e-07f;
+}
+__device__ __forceinline__ double uniform_f64(uint32_t w) {
+    return (static_cast<double>(w >> 9) + 0.5) * 1.1920928955078125e-07;
+}
+
+// Box-Muller: two N(0,1) draws from two uniforms.
+__device__ __forceinline__ void box_muller(double ua, double ub, double &nx, double &ny) {
+    const double rad = sqrt(-2.0 * log(ua));
+    double s, c;
+    sincospi(2.0 * ub, &s, &c);
+    nx = rad * c;
+    ny = rad * s;
+}
+__device__ __forceinline__ void box_muller(float ua, float ub, float &nx, float &ny) {
+    const float rad = sqrtf(-2.0f * logf(ua));
+    float s, c;
+    sincospif(2.0f * ub, &s, &c);
+    nx = rad * c;
+    ny = rad * s;
+}
+
+// ----------------------------------------------------------------------------------
+// Explicitly rounded arithmetic (no contraction), used where the result must equal the
+// same expression evaluated elsewhere.
+// ----------------------------------------------------------------------------------
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+
+__device__ __forceinline__ double exp_acc(double x) { return exp(x); }
+__device__ __forceinline__ float exp_acc(float x) { return expf(x); }
+
+template <typename A> __device__ __forceinline__ A neg_inf();
+template <> __device__ __forceinline__ double neg_inf<double>() { return -__longlong_as_double(0x7ff0000000000000ll); }
+template <> __device__ __forceinline__ float neg_inf<float>() { return -__int_as_float(0x7f800000); }
+
+// ----------------------------------------------------------------------------------
+// Systematic resampling (Sec. 3, "Resampling"): stratum j is sampled at
+// u_j = (j + u0) * (1/N), evaluated in the CDF's precision A.  count_le(c) is the number
+// of strata with u_j <= c; particle k receives strata [count_le(C_{k-1}), count_le(C_k)),
+// which is exactly a_j = min{k : C_k >= u_j} for a non-decreasing C.  u_j is
+// non-decreasing in j (both roundings are monotone), so the count is found from an
+// arithmetic estimate and a short galloping search.
+// ----------------------------------------------------------------------------------
+template <typename A>
+__device__ __forceinline__ A stratum_point(int64_t j, A u0, A inv_n) {
+    return mul_rn(add_rn(static_cast<A>(j), u0), inv_n);
+}
+
+template <typename A>
+__device__ int64_t count_le(A c, A u0, A inv_n, int64_t n) {
+    if (!(stratum_point<A>(0, u0, inv_n) <= c)) return 0;   // also NaN
+    if (stratum_point<A>(n - 1, u0, inv_n) <= c) return n;
+    // invariant wanted: u(lo) <= c < u(hi), 0 <= lo < hi <= n - 1
+    const A est = c * static_cast<A>(n) - u0;
+    int64_t j = (est > static_cast<A>(0)) ? static_cast<int64_t>(est) : 0;
+    if (j > n - 2) j = n - 2;
+    int64_t lo, hi;
+    if (stratum_point<A>(j, u0, inv_n) <= c) {
+        lo = j;
+        hi = j + 1;
+        int64_t step = 1;
+        while (hi < n - 1 && stratum_point<A>(hi, u0, inv_n) <= c) {
+            lo = hi;
+            step <<= 1;
+            hi = (hi + step < n - 1) ? hi + step : n - 1;
+        }
+    } else {
+        hi = j;
+        lo = j - 1;
+        int64_t step = 1;
+        while (lo > 0 && !(stratum_point<A>(lo, u0, inv_n) <= c)) {
+            hi = lo;
+            step <<= 1;
+            lo = (lo - step > 0) ? lo - step : 0;
+        }
+    }
+    while (hi - lo > 1) {
+        const int64_t mid = lo + ((hi - lo) >> 1);
+        if (stratum_point<A>(mid, u0, inv_n) <= c) lo = mid; else hi = mid;
+    }
+    return lo + 1;
+}
+
+// ----------------------------------------------------------------------------------
+// Memory-model helpers for the decoupled lookback and the last-block-done finalise.
+// ----------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ double ld_relaxed_f64(const double *p) {
+    double v;
+    asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// ----------------------------------------------------------------------------------
+// Precision traits.  acc_t is the precision of the weights, sums, scan and CDF.
+// ----------------------------------------------------------------------------------
+template <int P> struct Prec;
+template <> struct Prec<0> {   // PF_REF64
+    using pos_t = double; using lik_t = double; using acc_t = double;
+    static constexpr bool kHalf = false;
+};
+template <> struct Prec<1> {   // PF_F32
+    using pos_t = float; using lik_t = float; using acc_t = float;
+    static constexpr bool kHalf = false;
+};
+template <> struct Prec<2> {   // PF_F16
+    using pos_t = __half; using lik_t = __half; using acc_t = float;
+    static constexpr bool kHalf = true;
+};
+template <> struct Prec<3> {   // PF_BF16
+    using pos_t = __nv_bfloat16; using lik_t = __nv_bfloat16; using acc_t = float;
+    static constexpr bool kHalf = true;
+};
+
+__device__ __forceinline__ double to_acc(double v) { return v; }
+__device__ __forceinline__ float to_acc(float v) { return v; }
+__device__ __forceinline__ float to_acc(__half v) { return __half2float(v); }
+__device__ __forceinline__ float to_acc(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+}  // namespace pfk

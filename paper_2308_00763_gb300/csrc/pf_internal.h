@@ -1,0 +1,100 @@
+// pf_internal.h -- data shared by the host runtime and the sm_103a kernels.
+//
+// Layout in HBM (one tracker; a batch is an array of these):
+//   positions  x[2][N], y[2][N]   ping-pong: step t reads slot (t+1)&1, writes slot t&1
+//   likelihood L[2][N]            same ping-pong
+//     REF64: double  F32: float  F16: __half  BF16: __nv_bfloat16 (positions are offsets
+//     from an integer anchor in F16/BF16)
+//   per tile  LookbackDesc[ntiles]  decoupled-lookback status of the CDF scan
+//             TilePartial[ntiles]   (max L, sum e, sum e*dx, sum e*dy) of the tile's outputs
+//   per tracker TrackerState      frame counter, M, S, 1/S, anchors, last estimate, status
+//               est ring [cap][2], stat ring [cap][2] (M, S) in double
+#pragma once
+#include <stdint.h>
+
+namespace pfk {
+
+constexpr int kThreads = 256;             // threads per CTA of the step kernel
+constexpr int kItems = 8;                 // CDF elements per thread
+constexpr int kTile = kThreads * kItems;  // particles of the resampled frame per tile
+constexpr int kMaxRadius = 64;
+
+// Device status bits (sticky, per tracker).
+constexpr uint32_t kStatusTimeout = 0x1u;
+
+struct alignas(16) LookbackDesc {
+    uint32_t flag;      // (epoch << 2) | state, state: 0 empty, 1 aggregate, 2 inclusive
+    uint32_t pad;
+    double agg;         // tile aggregate of e (scan precision, stored exactly in double)
+    double incl;        // inclusive prefix through this tile
+    double pad2;
+};
+
+struct alignas(16) TilePartial {
+    double m, s, sx, sy;   // running max of L, sum exp(L-m), sum exp(L-m)*dx, *dy
+};
+
+struct alignas(16) TrackerState {
+    int64_t t;             // index of the frame the next step processes
+    uint32_t epoch;        // launch counter of this tracker (lookback flag tag), never reset
+    uint32_t status;       // sticky kStatus* bits
+    double M;              // max L of frame t-1
+    double S;              // sum exp(L - M) of frame t-1
+    double invS;           // 1 / S
+    double ax, ay;         // integer anchor of the stored positions (frame t-1)
+    double nx, ny;         // integer anchor the next step writes against
+    double est_x, est_y;   // estimate of frame t-1
+};
+
+struct FrameRef {
+    const uint8_t *base;   // frame pointer (device)
+    int64_t pitch;         // bytes between rows
+    int64_t stride;        // if nonzero, frame of step t is base + t * stride
+    int32_t active;        // 0: tracker not stepped this launch
+    int32_t pad;
+};
+
+struct TrackerDev {
+    int64_t N;
+    int32_t W, H;
+    int32_t r, D;              // radius and |D|
+    int32_t tile_begin, ntiles;
+    uint32_t key_lo, key_hi, tracker_id, flags;
+    int32_t est_cap, pad0;
+    // likelihood constants: L = c1 * (2 s - c2 * D) / den  (exact-integer form of Eq. 3)
+    double c1, c2, den;
+    float kappa, bg_f, fg_f, pad1;   // Eq. 4 scaled form: kappa = 1 / sqrt(50 |D|)
+    double init_x, init_y, sigma_x, sigma_y, drift_x, drift_y;
+    double inv_n;              // 1.0 / N
+    float inv_n_f;             // 1.0f / (float)N
+    float pad2;
+    void *px[2], *py[2], *pl[2];
+    int32_t *dbg_anc;          // NULL unless PF_FLAG_DEBUG_ARRAYS
+    void *dbg_cdf;
+    LookbackDesc *look;
+    TilePartial *part;
+    uint32_t *done;
+    TrackerState *state;
+    double *est_ring;          // [est_cap][2]
+    double *stat_ring;         // [est_cap][2] = (M, S)
+};
+
+// Launch of one step over a batch of trackers of one precision.
+struct StepLaunch {
+    const TrackerDev *trk;     // device array [ntrk]
+    const FrameRef *frames;    // device array [ntrk]
+    const int32_t *tile_trk;   // device array [total_tiles]: tracker of each tile
+    uint32_t *ticket;          // device counter, 0 between launches
+    int32_t ntrk;
+    int32_t total_tiles;
+    const uint8_t *frame_override;  // single tracker: frame pointer passed by the call
+    int64_t pitch_override;
+};
+
+// Host entry points into the kernel translation unit.
+int launch_step(int precision, const StepLaunch &L, int grid, void *stream);
+int step_grid_size(int precision, int total_tiles);
+int launch_debug_philox(const uint32_t *d_ctrs, int64_t n, uint64_t seed, uint32_t *d_out,
+                        void *stream);
+
+}  // namespace pfk

@@ -1,0 +1,588 @@
+// pf_runtime.cu -- host runtime behind the C ABI of include/pf.h: handles, device
+// buffers, frame staging, launches, estimates, checkpoints.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdlib.h>
+#include <stddef.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "../../include/pf.h"
+#include "pf_internal.h"
+
+using namespace pfk;
+
+namespace {
+
+size_t pos_bytes(int prec) { return prec == PF_REF64 ? 8 : prec == PF_F32 ? 4 : 2; }
+
+double round_half_up(double v) { return floor(v) + ((v - floor(v)) >= 0.5 ? 1.0 : 0.0); }
+
+int disk_count(int r) {
+    int n = 0;
+    for (int dy = -r; dy <= r; ++dy)
+        for (int dx = -r; dx <= r; ++dx)
+            if (dx * dx + dy * dy <= r * r) ++n;
+    return n;
+}
+
+pf_status check_config(const pf_config *c) {
+    if (!c) return PF_ERR_ARG;
+    if (c->width < 1 || c->width > 65535 || c->height < 1 || c->height > 65535) return PF_ERR_ARG;
+    if (c->num_particles < 1 || c->num_particles > 2147483647ll) return PF_ERR_ARG;
+    if (c->disk_radius < 0 || c->disk_radius > kMaxRadius) return PF_ERR_ARG;
+    if (c->precision < PF_REF64 || c->precision > PF_BF16) return PF_ERR_ARG;
+    if (!(c->sigma_x >= 0) || !(c->sigma_y >= 0)) return PF_ERR_ARG;
+    if (!isfinite(c->init_x) || !isfinite(c->init_y) || !isfinite(c->drift_x) || !isfinite(c->drift_y))
+        return PF_ERR_ARG;
+    if (!isfinite(c->bg_level) || !isfinite(c->fg_level) || !isfinite(c->sigma_x) || !isfinite(c->sigma_y))
+        return PF_ERR_ARG;
+    if (fabs(c->init_x) > 1.0e6 || fabs(c->init_y) > 1.0e6) return PF_ERR_ARG;
+    if (c->est_capacity < 0 || c->reserved != 0) return PF_ERR_ARG;
+    if (c->flags & ~(PF_FLAG_DEBUG_ARRAYS | PF_FLAG_ACCUM32)) return PF_ERR_ARG;
+    return PF_OK;
+}
+
+// One allocation carved into aligned pieces.
+struct Arena {
+    char *base = nullptr;
+    size_t size = 0, used = 0;
+    size_t take(size_t bytes) {
+        const size_t off = (used + 255) & ~size_t(255);
+        used = off + bytes;
+        return off;
+    }
+};
+
+}  // namespace
+
+// A set of trackers of one precision, stepped by one launch.
+struct Engine {
+    int prec = 0;
+    int n = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<pf_config> cfg;
+    std::vector<TrackerDev> h_trk;     // host copy; device pointers inside
+    std::vector<FrameRef> h_frames;
+    std::vector<int64_t> done_frames;  // per tracker
+    TrackerDev *d_trk = nullptr;
+    FrameRef *d_frames = nullptr;
+    FrameRef *h_frames_pinned = nullptr;
+    int32_t *d_tile_trk = nullptr;
+    uint32_t *d_ticket = nullptr;
+    char *d_arena = nullptr;
+    int total_tiles = 0;
+    int grid = 0;
+    pf_status sticky = PF_OK;
+    uint8_t *d_frame_buf = nullptr;    // single tracker: staging of host frames
+    TrackerState *h_init_pinned = nullptr;  // initial state of every tracker (pf_reset)
+    int64_t frame_buf_pitch = 0;
+
+    pf_status fail(pf_status s) {
+        if (sticky == PF_OK) sticky = s;
+        return s;
+    }
+};
+
+struct pf_filter {
+    Engine e;
+};
+
+struct pf_batch {
+    Engine e;
+};
+
+static void engine_free(Engine &e) {
+    if (e.stream || true) cudaStreamSynchronize(e.stream);
+    cudaFree(e.d_trk);
+    cudaFree(e.d_frames);
+    cudaFree(e.d_tile_trk);
+    cudaFree(e.d_ticket);
+    cudaFree(e.d_arena);
+    cudaFree(e.d_frame_buf);
+    if (e.h_frames_pinned) cudaFreeHost(e.h_frames_pinned);
+    if (e.h_init_pinned) cudaFreeHost(e.h_init_pinned);
+    e.h_init_pinned = nullptr;
+    e.d_trk = nullptr; e.d_frames = nullptr; e.d_tile_trk = nullptr; e.d_ticket = nullptr;
+    e.d_arena = nullptr; e.d_frame_buf = nullptr; e.h_frames_pinned = nullptr;
+}
+
+static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stream, bool stage_frames) {
+    if (n < 1 || !cfgs) return PF_ERR_ARG;
+    for (int i = 0; i < n; ++i) {
+        pf_status s = check_config(&cfgs[i]);
+        if (s != PF_OK) return s;
+        if (cfgs[i].precision != cfgs[0].precision) return PF_ERR_ARG;
+    }
+    e.prec = cfgs[0].precision;
+    e.n = n;
+    e.stream = static_cast<cudaStream_t>(stream);
+    e.cfg.assign(cfgs, cfgs + n);
+    e.h_trk.assign(n, TrackerDev{});
+    e.h_frames.assign(n, FrameRef{});
+    e.done_frames.assign(n, 0);
+
+    // sizes
+    const size_t pb = pos_bytes(e.prec);
+    const size_t cdf_b = e.prec == PF_REF64 ? 8 : 4;
+    Arena a;
+    struct Off { size_t px[2], py[2], pl[2], look, part, done, state, est, stat, dbga, dbgc; };
+    std::vector<Off> off(n);
+    int64_t tiles = 0;
+    for (int i = 0; i < n; ++i) {
+        const pf_config &c = cfgs[i];
+        const int64_t N = c.num_particles;
+        const int nt = static_cast<int>((N + kTile - 1) / kTile);
+        if (tiles + nt > 0x7fffffff) return PF_ERR_ARG;
+        const int cap = c.est_capacity ? c.est_capacity : 4096;
+        Off &o = off[i];
+        for (int s = 0; s < 2; ++s) {
+            o.px[s] = a.take(N * pb + 16);
+            o.py[s] = a.take(N * pb + 16);
+            o.pl[s] = a.take(N * pb + 16);
+        }
+        o.look = a.take(sizeof(LookbackDesc) * nt);
+        o.part = a.take(sizeof(TilePartial) * nt);
+        o.done = a.take(sizeof(uint32_t));
+        o.state = a.take(sizeof(TrackerState));
+        o.est = a.take(sizeof(double) * 2 * cap);
+        o.stat = a.take(sizeof(double) * 2 * cap);
+        if (c.flags & PF_FLAG_DEBUG_ARRAYS) {
+            o.dbga = a.take(sizeof(int32_t) * N);
+            o.dbgc = a.take(cdf_b * N);
+        }
+        TrackerDev &T = e.h_trk[i];
+        T.N = N;
+        T.W = c.width;
+        T.H = c.height;
+        T.r = c.disk_radius;
+        T.D = disk_count(c.disk_radius);
+        T.tile_begin = static_cast<int32_t>(tiles);
+        T.ntiles = nt;
+        T.key_lo = static_cast<uint32_t>(c.seed & 0xffffffffu);
+        T.key_hi = static_cast<uint32_t>(c.seed >> 32);
+        T.tracker_id = c.tracker_id;
+        T.flags = c.flags;
+        T.est_cap = cap;
+        T.c1 = c.fg_level - c.bg_level;
+        T.c2 = c.bg_level + c.fg_level;
+        T.den = 50.0 * T.D;
+        T.kappa = static_cast<float>(1.0 / sqrt(50.0 * T.D));
+        T.bg_f = static_cast<float>(c.bg_level);
+        T.fg_f = static_cast<float>(c.fg_level);
+        T.init_x = c.init_x; T.init_y = c.init_y;
+        T.sigma_x = c.sigma_x; T.sigma_y = c.sigma_y;
+        T.drift_x = c.drift_x; T.drift_y = c.drift_y;
+        T.inv_n = 1.0 / static_cast<double>(N);
+        T.inv_n_f = 1.0f / static_cast<float>(N);
+        tiles += nt;
+    }
+    e.total_tiles = static_cast<int>(tiles);
+    a.size = a.used + 256;
+
+    cudaError_t err = cudaMalloc(reinterpret_cast<void **>(&e.d_arena), a.size);
+    if (err != cudaSuccess) { cudaGetLastError(); engine_free(e); return PF_ERR_OOM; }
+    err = cudaMemsetAsync(e.d_arena, 0, a.size, e.stream);
+    if (err == cudaSuccess) err = cudaMalloc(reinterpret_cast<void **>(&e.d_trk), sizeof(TrackerDev) * n);
+    if (err == cudaSuccess) err = cudaMalloc(reinterpret_cast<void **>(&e.d_frames), sizeof(FrameRef) * n);
+    if (err == cudaSuccess) err = cudaMalloc(reinterpret_cast<void **>(&e.d_tile_trk), sizeof(int32_t) * e.total_tiles);
+    if (err == cudaSuccess) err = cudaMalloc(reinterpret_cast<void **>(&e.d_ticket), sizeof(uint32_t));
+    if (err == cudaSuccess) err = cudaMallocHost(reinterpret_cast<void **>(&e.h_frames_pinned), sizeof(FrameRef) * n);
+    if (err == cudaSuccess) err = cudaMallocHost(reinterpret_cast<void **>(&e.h_init_pinned), sizeof(TrackerState) * n);
+    if (err == cudaSuccess && stage_frames) {
+        e.frame_buf_pitch = (cfgs[0].width + 15) & ~15;
+        err = cudaMalloc(reinterpret_cast<void **>(&e.d_frame_buf), static_cast<size_t>(e.frame_buf_pitch) * cfgs[0].height);
+    }
+    if (err != cudaSuccess) {
+        cudaGetLastError();
+        engine_free(e);
+        return err == cudaErrorMemoryAllocation ? PF_ERR_OOM : PF_ERR_CUDA;
+    }
+    std::vector<int32_t> tile_trk(e.total_tiles);
+    std::vector<TrackerState> st(n);
+    for (int i = 0; i < n; ++i) {
+        TrackerDev &T = e.h_trk[i];
+        const Off &o = off[i];
+        for (int s = 0; s < 2; ++s) {
+            T.px[s] = e.d_arena + o.px[s];
+            T.py[s] = e.d_arena + o.py[s];
+            T.pl[s] = e.d_arena + o.pl[s];
+        }
+        T.look = reinterpret_cast<LookbackDesc *>(e.d_arena + o.look);
+        T.part = reinterpret_cast<TilePartial *>(e.d_arena + o.part);
+        T.done = reinterpret_cast<uint32_t *>(e.d_arena + o.done);
+        T.state = reinterpret_cast<TrackerState *>(e.d_arena + o.state);
+        T.est_ring = reinterpret_cast<double *>(e.d_arena + o.est);
+        T.stat_ring = reinterpret_cast<double *>(e.d_arena + o.stat);
+        if (e.cfg[i].flags & PF_FLAG_DEBUG_ARRAYS) {
+            T.dbg_anc = reinterpret_cast<int32_t *>(e.d_arena + o.dbga);
+            T.dbg_cdf = e.d_arena + o.dbgc;
+        }
+        for (int k = 0; k < T.ntiles; ++k) tile_trk[T.tile_begin + k] = i;
+        TrackerState &s = st[i];
+        memset(&s, 0, sizeof s);
+        s.t = 0;
+        s.epoch = 1;
+        s.M = 0.0;
+        s.S = 1.0;
+        s.invS = 1.0;
+        s.ax = s.nx = round_half_up(e.cfg[i].init_x);
+        s.ay = s.ny = round_half_up(e.cfg[i].init_y);
+        s.est_x = e.cfg[i].init_x;
+        s.est_y = e.cfg[i].init_y;
+        e.h_frames[i].active = 1;
+    }
+    err = cudaMemcpyAsync(e.d_trk, e.h_trk.data(), sizeof(TrackerDev) * n, cudaMemcpyHostToDevice, e.stream);
+    if (err == cudaSuccess)
+        err = cudaMemcpyAsync(e.d_tile_trk, tile_trk.data(), sizeof(int32_t) * e.total_tiles,
+                              cudaMemcpyHostToDevice, e.stream);
+    if (err == cudaSuccess) err = cudaMemsetAsync(e.d_ticket, 0, sizeof(uint32_t), e.stream);
+    memcpy(e.h_init_pinned, st.data(), sizeof(TrackerState) * n);
+    for (int i = 0; i < n && err == cudaSuccess; ++i)
+        err = cudaMemcpyAsync(e.h_trk[i].state, &e.h_init_pinned[i], sizeof(TrackerState), cudaMemcpyHostToDevice,
+                              e.stream);
+    if (err == cudaSuccess) {
+        memcpy(e.h_frames_pinned, e.h_frames.data(), sizeof(FrameRef) * n);
+        err = cudaMemcpyAsync(e.d_frames, e.h_frames_pinned, sizeof(FrameRef) * n, cudaMemcpyHostToDevice, e.stream);
+    }
+    if (err == cudaSuccess) err = cudaStreamSynchronize(e.stream);   // host vectors go out of scope
+    if (err != cudaSuccess) { cudaGetLastError(); engine_free(e); return PF_ERR_CUDA; }
+    e.grid = step_grid_size(e.prec, e.total_tiles);
+    return PF_OK;
+}
+
+static pf_status engine_launch(Engine &e, const uint8_t *override_frame, int64_t override_pitch) {
+    StepLaunch L;
+    L.trk = e.d_trk;
+    L.frames = e.d_frames;
+    L.tile_trk = e.d_tile_trk;
+    L.ticket = e.d_ticket;
+    L.ntrk = e.n;
+    L.total_tiles = e.total_tiles;
+    L.frame_override = override_frame;
+    L.pitch_override = override_pitch;
+    const int rc = launch_step(e.prec, L, e.grid, e.stream);
+    if (rc != 0) { cudaGetLastError(); return e.fail(PF_ERR_CUDA); }
+    return PF_OK;
+}
+
+static pf_status engine_sync_status(Engine &e) {
+    if (e.sticky != PF_OK) return e.sticky;
+    cudaError_t err = cudaStreamSynchronize(e.stream);
+    if (err != cudaSuccess) { cudaGetLastError(); return e.fail(PF_ERR_CUDA); }
+    for (int i = 0; i < e.n; ++i) {
+        uint32_t status = 0;
+        err = cudaMemcpy(&status, &e.h_trk[i].state->status, sizeof status, cudaMemcpyDeviceToHost);
+        if (err != cudaSuccess) { cudaGetLastError(); return e.fail(PF_ERR_CUDA); }
+        if (status & kStatusTimeout) return e.fail(PF_ERR_TIMEOUT);
+    }
+    return PF_OK;
+}
+
+static pf_status engine_read_frame(Engine &e, int i, int64_t idx, double *xy, double *ms) {
+    const TrackerDev &T = e.h_trk[i];
+    if (idx < 0 || idx >= e.done_frames[i] || idx < e.done_frames[i] - T.est_cap) return PF_ERR_ARG;
+    const int64_t slot = idx % T.est_cap;
+    cudaError_t err = cudaMemcpy(xy, T.est_ring + 2 * slot, 2 * sizeof(double), cudaMemcpyDeviceToHost);
+    if (err == cudaSuccess && ms) err = cudaMemcpy(ms, T.stat_ring + 2 * slot, 2 * sizeof(double), cudaMemcpyDeviceToHost);
+    if (err != cudaSuccess) { cudaGetLastError(); return e.fail(PF_ERR_CUDA); }
+    return PF_OK;
+}
+
+// ---------------------------------------------------------------------------- C ABI
+extern "C" {
+
+const char *pf_status_string(pf_status s) {
+    switch (s) {
+        case PF_OK: return "ok";
+        case PF_ERR_ARG: return "invalid argument";
+        case PF_ERR_OOM: return "out of memory";
+        case PF_ERR_CUDA: return "CUDA error";
+        case PF_ERR_TIMEOUT: return "device wait timed out";
+        case PF_ERR_STATE: return "handle in failed state or wrong state";
+        case PF_ERR_ADMISSION: return "admission refused";
+    }
+    return "unknown status";
+}
+
+pf_status pf_create(const pf_config *cfg, void *cuda_stream, pf_filter **out) {
+    if (!cfg || !out) return PF_ERR_ARG;
+    *out = nullptr;
+    pf_filter *f = new (std::nothrow) pf_filter();
+    if (!f) return PF_ERR_OOM;
+    pf_status s = engine_init(f->e, cfg, 1, cuda_stream, true);
+    if (s != PF_OK) { delete f; return s; }
+    *out = f;
+    return PF_OK;
+}
+
+pf_status pf_step_frame(pf_filter *f, const uint8_t *frame, int64_t pitch_bytes, int32_t frame_on_device) {
+    if (!f || !frame) return PF_ERR_ARG;
+    Engine &e = f->e;
+    if (e.sticky != PF_OK) return PF_ERR_STATE;
+    const pf_config &c = e.cfg[0];
+    if (pitch_bytes < c.width) return PF_ERR_ARG;
+    const uint8_t *dev = frame;
+    int64_t pitch = pitch_bytes;
+    if (!frame_on_device) {
+        cudaError_t err = cudaMemcpy2DAsync(e.d_frame_buf, e.frame_buf_pitch, frame, pitch_bytes, c.width,
+                                            c.height, cudaMemcpyHostToDevice, e.stream);
+        if (err != cudaSuccess) { cudaGetLastError(); return e.fail(PF_ERR_CUDA); }
+        dev = e.d_frame_buf;
+        pitch = e.frame_buf_pitch;
+    }
+    pf_status s = engine_launch(e, dev, pitch);
+    if (s != PF_OK) return s;
+    e.done_frames[0] += 1;
+    return PF_OK;
+}
+
+pf_status pf_run_frames(pf_filter *f, const uint8_t *frames, int64_t pitch_bytes, int64_t frame_stride,
+                        int32_t count, int32_t frames_on_device) {
+    if (!f || !frames || count < 0) return PF_ERR_ARG;
+    for (int32_t i = 0; i < count; ++i) {
+        pf_status s = pf_step_frame(f, frames + static_cast<int64_t>(i) * frame_stride, pitch_bytes, frames_on_device);
+        if (s != PF_OK) return s;
+    }
+    return PF_OK;
+}
+
+pf_status pf_estimate(pf_filter *f, int64_t frame_index, double *x, double *y) {
+    if (!f || !x || !y) return PF_ERR_ARG;
+    Engine &e = f->e;
+    pf_status s = engine_sync_status(e);
+    if (s != PF_OK) return s;
+    double xy[2];
+    s = engine_read_frame(e, 0, frame_index, xy, nullptr);
+    if (s != PF_OK) return s;
+    *x = xy[0];
+    *y = xy[1];
+    return PF_OK;
+}
+
+pf_status pf_estimates(pf_filter *f, int64_t first, int32_t count, double *xy, double *max_and_sum) {
+    if (!f || !xy || count < 0) return PF_ERR_ARG;
+    Engine &e = f->e;
+    pf_status s = engine_sync_status(e);
+    if (s != PF_OK) return s;
+    const TrackerDev &T = e.h_trk[0];
+    const int64_t done = e.done_frames[0];
+    if (count == 0) return PF_OK;
+    if (first < 0 || first + count > done || first < done - T.est_cap) return PF_ERR_ARG;
+    // copy in at most two contiguous pieces of the ring
+    int64_t idx = first;
+    int32_t left = count;
+    while (left > 0) {
+        const int64_t slot = idx % T.est_cap;
+        int64_t run = T.est_cap - slot;
+        if (run > left) run = left;
+        cudaError_t err = cudaMemcpy(xy + 2 * (idx - first), T.est_ring + 2 * slot, run * 2 * sizeof(double),
+                                     cudaMemcpyDeviceToHost);
+        if (err == cudaSuccess && max_and_sum)
+            err = cudaMemcpy(max_and_sum + 2 * (idx - first), T.stat_ring + 2 * slot, run * 2 * sizeof(double),
+                             cudaMemcpyDeviceToHost);
+        if (err != cudaSuccess) { cudaGetLastError(); return e.fail(PF_ERR_CUDA); }
+        idx += run;
+        left -= static_cast<int32_t>(run);
+    }
+    return PF_OK;
+}
+
+int64_t pf_frames_done(const pf_filter *f) { return f ? f->e.done_frames[0] : -1; }
+
+pf_status pf_reset(pf_filter *f) {
+    if (!f) return PF_ERR_ARG;
+    Engine &e = f->e;
+    if (e.sticky != PF_OK) return PF_ERR_STATE;
+    // Rewrite every field of the state except the launch counter (epoch) and the status
+    // word: lookback flags written by earlier launches must stay stale.
+    TrackerState *d = e.h_trk[0].state;
+    const TrackerState *h = &e.h_init_pinned[0];
+    const size_t tail = sizeof(TrackerState) - offsetof(TrackerState, M);
+    cudaError_t err = cudaMemcpyAsync(&d->t, &h->t, sizeof(int64_t), cudaMemcpyHostToDevice, e.stream);
+    if (err == cudaSuccess) err = cudaMemcpyAsync(&d->M, &h->M, tail, cudaMemcpyHostToDevice, e.stream);
+    if (err != cudaSuccess) { cudaGetLastError(); return e.fail(PF_ERR_CUDA); }
+    e.done_frames[0] = 0;
+    return PF_OK;
+}
+
+pf_status pf_destroy(pf_filter *f) {
+    if (!f) return PF_OK;
+    engine_free(f->e);
+    delete f;
+    return PF_OK;
+}
+
+pf_status pf_get_state(pf_filter *f, void *host_buf, size_t *bytes) {
+    if (!f || !bytes) return PF_ERR_ARG;
+    Engine &e = f->e;
+    const TrackerDev &T = e.h_trk[0];
+    const size_t pb = pos_bytes(e.prec);
+    const size_t need = sizeof(pf_state_header) + 3 * pb * static_cast<size_t>(T.N);
+    if (!host_buf) { *bytes = need; return PF_OK; }
+    if (*bytes < need) return PF_ERR_ARG;
+    cudaError_t err = cudaStreamSynchronize(e.stream);
+    TrackerState st;
+    if (err == cudaSuccess) err = cudaMemcpy(&st, T.state, sizeof st, cudaMemcpyDeviceToHost);
+    if (err != cudaSuccess) { cudaGetLastError(); return e.fail(PF_ERR_CUDA); }
+    pf_state_header h;
+    memset(&h, 0, sizeof h);
+    h.magic = 0x31534650u;
+    h.precision = e.prec;
+    h.num_particles = T.N;
+    h.t = st.t;
+    h.max_l = st.M;
+    h.sum_e = st.S;
+    h.anchor_x = st.ax;
+    h.anchor_y = st.ay;
+    h.next_anchor_x = st.nx;
+    h.next_anchor_y = st.ny;
+    h.est_x = st.est_x;
+    h.est_y = st.est_y;
+    char *p = static_cast<char *>(host_buf);
+    memcpy(p, &h, sizeof h);
+    p += sizeof h;
+    const int slot = static_cast<int>((st.t + 1) & 1);
+    const size_t nb = pb * static_cast<size_t>(T.N);
+    err = cudaMemcpy(p, T.px[slot], nb, cudaMemcpyDeviceToHost);
+    if (err == cudaSuccess) err = cudaMemcpy(p + nb, T.py[slot], nb, cudaMemcpyDeviceToHost);
+    if (err == cudaSuccess) err = cudaMemcpy(p + 2 * nb, T.pl[slot], nb, cudaMemcpyDeviceToHost);
+    if (err != cudaSuccess) { cudaGetLastError(); return e.fail(PF_ERR_CUDA); }
+    *bytes = need;
+    return PF_OK;
+}
+
+pf_status pf_set_state(pf_filter *f, const void *host_buf, size_t bytes) {
+    if (!f || !host_buf) return PF_ERR_ARG;
+    Engine &e = f->e;
+    if (e.sticky != PF_OK) return PF_ERR_STATE;
+    const TrackerDev &T = e.h_trk[0];
+    const size_t pb = pos_bytes(e.prec);
+    const size_t need = sizeof(pf_state_header) + 3 * pb * static_cast<size_t>(T.N);
+    if (bytes < need) return PF_ERR_ARG;
+    pf_state_header h;
+    memcpy(&h, host_buf, sizeof h);
+    if (h.magic != 0x31534650u || h.precision != e.prec || h.num_particles != T.N || h.t < 0) return PF_ERR_ARG;
+    if (!(h.sum_e > 0) || !isfinite(h.max_l)) return PF_ERR_ARG;
+    cudaError_t err = cudaStreamSynchronize(e.stream);
+    TrackerState st;
+    if (err == cudaSuccess) err = cudaMemcpy(&st, T.state, sizeof st, cudaMemcpyDeviceToHost);
+    if (err != cudaSuccess) { cudaGetLastError(); return e.fail(PF_ERR_CUDA); }
+    st.t = h.t;
+    st.M = h.max_l;
+    st.S = h.sum_e;
+    st.invS = e.prec == PF_REF64 ? 1.0 / h.sum_e
+                                 : static_cast<double>(1.0f / static_cast<float>(h.sum_e));
+    st.ax = h.anchor_x;
+    st.ay = h.anchor_y;
+    st.nx = h.next_anchor_x;
+    st.ny = h.next_anchor_y;
+    st.est_x = h.est_x;
+    st.est_y = h.est_y;
+    const char *p = static_cast<const char *>(host_buf) + sizeof h;
+    const int slot = static_cast<int>((h.t + 1) & 1);
+    const size_t nb = pb * static_cast<size_t>(T.N);
+    err = cudaMemcpy(T.state, &st, sizeof st, cudaMemcpyHostToDevice);
+    if (err == cudaSuccess) err = cudaMemcpy(T.px[slot], p, nb, cudaMemcpyHostToDevice);
+    if (err == cudaSuccess) err = cudaMemcpy(T.py[slot], p + nb, nb, cudaMemcpyHostToDevice);
+    if (err == cudaSuccess) err = cudaMemcpy(T.pl[slot], p + 2 * nb, nb, cudaMemcpyHostToDevice);
+    if (err != cudaSuccess) { cudaGetLastError(); return e.fail(PF_ERR_CUDA); }
+    e.done_frames[0] = h.t;
+    return PF_OK;
+}
+
+pf_status pf_get_debug(pf_filter *f, int32_t which, void *host_buf, size_t bytes) {
+    if (!f || !host_buf) return PF_ERR_ARG;
+    Engine &e = f->e;
+    const TrackerDev &T = e.h_trk[0];
+    if (!T.dbg_anc) return PF_ERR_STATE;
+    const size_t elem = which == 0 ? 4 : (e.prec == PF_REF64 ? 8 : 4);
+    if (which < 0 || which > 1 || bytes < elem * static_cast<size_t>(T.N)) return PF_ERR_ARG;
+    cudaError_t err = cudaStreamSynchronize(e.stream);
+    if (err == cudaSuccess)
+        err = cudaMemcpy(host_buf, which == 0 ? static_cast<void *>(T.dbg_anc) : T.dbg_cdf,
+                         elem * static_cast<size_t>(T.N), cudaMemcpyDeviceToHost);
+    if (err != cudaSuccess) { cudaGetLastError(); return e.fail(PF_ERR_CUDA); }
+    return PF_OK;
+}
+
+pf_status pf_debug_philox(const uint32_t *ctrs, int64_t n, uint64_t seed, uint32_t *out) {
+    if (!ctrs || !out || n < 0) return PF_ERR_ARG;
+    if (n == 0) return PF_OK;
+    uint32_t *d = nullptr;
+    cudaError_t err = cudaMalloc(reinterpret_cast<void **>(&d), static_cast<size_t>(n) * 32);
+    if (err != cudaSuccess) { cudaGetLastError(); return PF_ERR_OOM; }
+    err = cudaMemcpy(d, ctrs, static_cast<size_t>(n) * 16, cudaMemcpyHostToDevice);
+    if (err == cudaSuccess && launch_debug_philox(d, n, seed, d + 4 * n, nullptr) != 0) err = cudaErrorLaunchFailure;
+    if (err == cudaSuccess) err = cudaMemcpy(out, d + 4 * n, static_cast<size_t>(n) * 16, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (err != cudaSuccess) { cudaGetLastError(); return PF_ERR_CUDA; }
+    return PF_OK;
+}
+
+// ---------------------------------------------------------------------------- batches
+pf_status pf_batch_create(const pf_config *cfgs, int32_t n, void *cuda_stream, pf_batch **out) {
+    if (!cfgs || !out || n < 1) return PF_ERR_ARG;
+    *out = nullptr;
+    pf_batch *b = new (std::nothrow) pf_batch();
+    if (!b) return PF_ERR_OOM;
+    pf_status s = engine_init(b->e, cfgs, n, cuda_stream, false);
+    if (s != PF_OK) { delete b; return s; }
+    *out = b;
+    return PF_OK;
+}
+
+pf_status pf_batch_step(pf_batch *b, const uint8_t *const *frames, const int64_t *pitches,
+                        const uint8_t *active_mask) {
+    if (!b || !frames || !pitches) return PF_ERR_ARG;
+    Engine &e = b->e;
+    if (e.sticky != PF_OK) return PF_ERR_STATE;
+    // the pinned staging copy of the frame table may still be read by the previous copy
+    cudaError_t err = cudaStreamSynchronize(e.stream);
+    if (err != cudaSuccess) { cudaGetLastError(); return e.fail(PF_ERR_CUDA); }
+    for (int i = 0; i < e.n; ++i) {
+        const int act = active_mask ? (active_mask[i] != 0) : 1;
+        if (act && (!frames[i] || pitches[i] < e.cfg[i].width)) return PF_ERR_ARG;
+        FrameRef &fr = e.h_frames_pinned[i];
+        fr.base = act ? frames[i] : nullptr;
+        fr.pitch = act ? pitches[i] : 0;
+        fr.stride = 0;
+        fr.active = act;
+    }
+    err = cudaMemcpyAsync(e.d_frames, e.h_frames_pinned, sizeof(FrameRef) * e.n, cudaMemcpyHostToDevice, e.stream);
+    if (err != cudaSuccess) { cudaGetLastError(); return e.fail(PF_ERR_CUDA); }
+    pf_status s = engine_launch(e, nullptr, 0);
+    if (s != PF_OK) return s;
+    for (int i = 0; i < e.n; ++i)
+        if (e.h_frames_pinned[i].active) e.done_frames[i] += 1;
+    return PF_OK;
+}
+
+pf_status pf_batch_estimates(pf_batch *b, int64_t frame_index, double *xy) {
+    if (!b || !xy) return PF_ERR_ARG;
+    Engine &e = b->e;
+    pf_status s = engine_sync_status(e);
+    if (s != PF_OK) return s;
+    for (int i = 0; i < e.n; ++i) {
+        double v[2];
+        if (engine_read_frame(e, i, frame_index, v, nullptr) == PF_OK) {
+            xy[2 * i] = v[0];
+            xy[2 * i + 1] = v[1];
+        } else {
+            xy[2 * i] = NAN;
+            xy[2 * i + 1] = NAN;
+        }
+    }
+    return e.sticky;
+}
+
+pf_status pf_batch_destroy(pf_batch *b) {
+    if (!b) return PF_OK;
+    engine_free(b->e);
+    delete b;
+    return PF_OK;
+}
+
+}  // extern "C"

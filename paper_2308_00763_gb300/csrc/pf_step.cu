@@ -1,0 +1,721 @@
+// pf_step.cu -- the fused per-frame SIR step for sm_103a.
+//
+// One launch per frame for a whole batch of trackers.  A tile is kTile consecutive
+// particles k of one tracker's previous frame.  Per tile (dynamic ticket order):
+//   1. resampling of the previous frame (Sec. 3, "Normalizing" and "Resampling"):
+//      e_k = exp(L_k - M) (Eq. 5 with the max of the previous step), a block scan, and a
+//      decoupled lookback over the tracker's earlier tiles give the inclusive prefix
+//      P_k; C_k = P_k * (1/S) (the reciprocal saved by the previous step); the strata
+//      j with C_{k-1} < u_j <= C_k are the offspring of k.  The tile's offspring form a
+//      contiguous range of j, and their ancestors all lie in the tile, so the gather of
+//      ancestor positions is a read of the tile's own particles staged in shared memory.
+//   2. propagation (Eq. 1-2) of every offspring j with Philox draws keyed (j, t),
+//   3. likelihood (Eq. 3; Eq. 4 scaled half form in F16/BF16) on the new frame,
+//   4. per-tile (max L, sum e, sum e*dx, sum e*dy), merged with rescaling,
+//   5. the tile that completes a tracker merges its tiles' partials in index order:
+//      M, S, 1/S and the estimate of the frame (the weighted mean, Sec. 4 Fig. 4).
+// Frame t = 0 has no resampling: every particle starts at the initial position.
+//
+// The scan is made order-independent so that neighbouring tiles agree bit for bit on
+// their common boundary: a tile's exclusive prefix is the left-to-right chain sum of the
+// earlier tiles' aggregates (the lookback folds the aggregates it collects in that
+// order), and within a tile the prefix is made non-decreasing by a running max.  Hence
+// C is non-decreasing, the strata ranges of consecutive tiles meet exactly, and every j
+// is written by exactly one tile.
+#include <cuda_runtime.h>
+#include <float.h>
+#include <math.h>
+
+#include "pf_device.cuh"
+#include "pf_internal.h"
+
+namespace pfk {
+
+namespace {
+
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxWin = 8;               // lookback windows of 32 tiles kept for the chain sum
+constexpr uint32_t kSpinLimit = 1u << 22;  // bounded waits: ~1 s with backoff
+
+__device__ __forceinline__ bool flag_ready(uint32_t f, uint32_t ep) {
+    return (f >> 2) == (ep & 0x3fffffffu) && (f & 3u) != 0u;
+}
+
+// Wait (bounded) until the lookback descriptor of a tile carries this epoch.  Returns the
+// flag, or 0 on timeout (and raises the tracker's timeout bit).
+__device__ __forceinline__ bool timed_out(const TrackerState *st) {
+    return (ld_acquire_u32(&st->status) & kStatusTimeout) != 0u;
+}
+
+__device__ uint32_t wait_flag(const LookbackDesc *d, uint32_t ep, TrackerState *st) {
+    uint32_t ns = 8;
+    for (uint32_t it = 0; it < kSpinLimit; ++it) {
+        const uint32_t f = ld_acquire_u32(&d->flag);
+        if (flag_ready(f, ep)) return f;
+        if ((it & 1023u) == 1023u && timed_out(st)) return 0u;   // another wait already gave up
+        __nanosleep(ns);
+        if (ns < 256) ns <<= 1;
+    }
+    atomicOr(&st->status, kStatusTimeout);
+    return 0u;
+}
+
+template <typename A>
+struct Stats {
+    A m, s, sx, sy;
+};
+
+template <typename A>
+__device__ __forceinline__ void stats_merge(Stats<A> &a, const Stats<A> &b) {
+    if (b.m == neg_inf<A>()) return;
+    if (a.m == neg_inf<A>()) { a = b; return; }
+    if (b.m > a.m) {
+        const A sc = exp_acc(a.m - b.m);
+        a.s = a.s * sc + b.s;
+        a.sx = a.sx * sc + b.sx;
+        a.sy = a.sy * sc + b.sy;
+        a.m = b.m;
+    } else {
+        const A sc = exp_acc(b.m - a.m);
+        a.s += b.s * sc;
+        a.sx += b.sx * sc;
+        a.sy += b.sy * sc;
+    }
+}
+
+template <typename A>
+__device__ __forceinline__ void stats_add(Stats<A> &a, A L, A dx, A dy) {
+    if (L > a.m) {
+        const A sc = exp_acc(a.m - L);   // exp(-inf) = 0 on the first element
+        a.s *= sc; a.sx *= sc; a.sy *= sc;
+        a.m = L;
+    }
+    const A e = exp_acc(L - a.m);
+    a.s += e;
+    a.sx += e * dx;
+    a.sy += e * dy;
+}
+
+template <typename A>
+__device__ __forceinline__ Stats<A> stats_shfl_xor(const Stats<A> &a, int o) {
+    Stats<A> b;
+    b.m = __shfl_xor_sync(0xffffffffu, a.m, o);
+    b.s = __shfl_xor_sync(0xffffffffu, a.s, o);
+    b.sx = __shfl_xor_sync(0xffffffffu, a.sx, o);
+    b.sy = __shfl_xor_sync(0xffffffffu, a.sy, o);
+    return b;
+}
+
+// Block-wide merge of per-thread stats in a fixed order; result valid in thread 0.
+template <typename A>
+__device__ Stats<A> block_stats(Stats<A> v, Stats<A> *s_red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        Stats<A> w = stats_shfl_xor(v, o);
+        if ((lane & o) == 0) stats_merge(v, w); else { stats_merge(w, v); v = w; }
+    }
+    if (lane == 0) s_red[warp] = v;
+    __syncthreads();
+    Stats<A> r;
+    if (threadIdx.x == 0) {
+        r = s_red[0];
+        for (int w = 1; w < kWarps; ++w) stats_merge(r, s_red[w]);
+    }
+    __syncthreads();
+    return r;
+}
+
+// Pixel of a position (reading C3): floor(v) + (v - floor(v) >= 0.5), clamped into a
+// range that keeps the integer arithmetic safe (the template is clamped to the frame).
+template <typename A>
+__device__ __forceinline__ int pixel_of(A v) {
+    if (!(v > static_cast<A>(-1.0e9) && v < static_cast<A>(1.0e9))) return -1000000000;
+    const A f = floor(v);
+    return static_cast<int>(f) + ((v - f) >= static_cast<A>(0.5) ? 1 : 0);
+}
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+// Integer sum of the template pixels around (px, py) (exact form of Eq. 3; reading C4
+// clamps template pixels to the frame).
+__device__ __forceinline__ uint32_t disk_sum(const uint8_t *__restrict__ frame, int64_t pitch, int W,
+                                             int H, int r, const int8_t *s_w, int px, int py) {
+    uint32_t s = 0;
+    if (px - r >= 0 && px + r < W && py - r >= 0 && py + r < H) {
+        const uint8_t *row = frame + static_cast<int64_t>(py - r) * pitch + px;
+        for (int dy = 0; dy <= 2 * r; ++dy, row += pitch) {
+            const int w = s_w[dy];
+            for (int dx = -w; dx <= w; ++dx) s += __ldg(row + dx);
+        }
+    } else {
+        for (int dy = -r; dy <= r; ++dy) {
+            const int w = s_w[dy + r];
+            const uint8_t *row = frame + static_cast<int64_t>(clampi(py + dy, 0, H - 1)) * pitch;
+            for (int dx = -w; dx <= w; ++dx) s += __ldg(row + clampi(px + dx, 0, W - 1));
+        }
+    }
+    return s;
+}
+
+// Eq. 4 per-pixel scaled form on two particles at once (half2 lanes), accumulated in
+// the lane type (F16, the paper's form) or in FP32 (BF16 and PF_FLAG_ACCUM32).
+template <typename H2>
+struct HalfLik;
+
+template <>
+struct HalfLik<__half2> {
+    // (1024 + I) has the bit pattern 0x6400 | I in binary16, so the pixel arrives in a
+    // half2 lane without a conversion instruction: h - (1024 + level) is exact.
+    __device__ static __forceinline__ __half2 pix(uint32_t i0, uint32_t i1) {
+        const uint32_t bits = (0x6400u | i0) | ((0x6400u | i1) << 16);
+        return *reinterpret_cast<const __half2 *>(&bits);
+    }
+    __device__ static __forceinline__ __half2 term(__half2 h, __half2 bgo, __half2 fgo, __half2 kap) {
+        const __half2 a = __hmul2(__hsub2(h, bgo), kap);
+        const __half2 b = __hmul2(__hsub2(h, fgo), kap);
+        return __hfma2(a, a, __hneg2(__hmul2(b, b)));
+    }
+};
+
+template <>
+struct HalfLik<__nv_bfloat162> {
+    __device__ static __forceinline__ __nv_bfloat162 pix(uint32_t i0, uint32_t i1) {
+        return __floats2bfloat162_rn(static_cast<float>(i0), static_cast<float>(i1));
+    }
+    __device__ static __forceinline__ __nv_bfloat162 term(__nv_bfloat162 h, __nv_bfloat162 bgo,
+                                                          __nv_bfloat162 fgo, __nv_bfloat162 kap) {
+        const __nv_bfloat162 a = __hmul2(__hsub2(h, bgo), kap);
+        const __nv_bfloat162 b = __hmul2(__hsub2(h, fgo), kap);
+        return __hfma2(a, a, __hneg2(__hmul2(b, b)));
+    }
+};
+
+template <typename T> struct Vec2;
+template <> struct Vec2<__half> { using type = __half2; };
+template <> struct Vec2<__nv_bfloat16> { using type = __nv_bfloat162; };
+
+__device__ __forceinline__ __half2 make2(__half a, __half b) { return __halves2half2(a, b); }
+__device__ __forceinline__ __nv_bfloat162 make2(__nv_bfloat16 a, __nv_bfloat16 b) { return __halves2bfloat162(a, b); }
+__device__ __forceinline__ __half2 f2_to2(float a, float b, __half2 *) { return __floats2half2_rn(a, b); }
+__device__ __forceinline__ __nv_bfloat162 f2_to2(float a, float b, __nv_bfloat162 *) { return __floats2bfloat162_rn(a, b); }
+__device__ __forceinline__ float lo_f(__half2 v) { return __low2float(v); }
+__device__ __forceinline__ float hi_f(__half2 v) { return __high2float(v); }
+__device__ __forceinline__ float lo_f(__nv_bfloat162 v) { return __low2float(v); }
+__device__ __forceinline__ float hi_f(__nv_bfloat162 v) { return __high2float(v); }
+__device__ __forceinline__ __half lo_h(__half2 v) { return __low2half(v); }
+__device__ __forceinline__ __half hi_h(__half2 v) { return __high2half(v); }
+__device__ __forceinline__ __nv_bfloat16 lo_h(__nv_bfloat162 v) { return __low2bfloat16(v); }
+__device__ __forceinline__ __nv_bfloat16 hi_h(__nv_bfloat162 v) { return __high2bfloat16(v); }
+
+// Shared memory of the step kernel.
+template <int P>
+struct __align__(16) StepSmem {
+    using pos_t = typename Prec<P>::pos_t;
+    using acc_t = typename Prec<P>::acc_t;
+    pos_t ax[kTile];          // ancestor positions of the tile (previous frame)
+    pos_t ay[kTile];
+    int32_t J[kTile];         // J[e] = number of strata assigned to particles k0..k0+e
+    acc_t warp_sum[kWarps];
+    acc_t warp_max[kWarps];
+    acc_t stack[kMaxWin * 32];
+    Stats<acc_t> red[kWarps];
+    acc_t agg;
+    acc_t excl;
+    int64_t jbeg, jend;
+    int8_t w[2 * kMaxRadius + 1];
+    uint32_t ticket;
+    uint32_t last;
+};
+
+// Exclusive chain-order prefix of tile lt from the earlier tiles' descriptors (warp 0).
+template <typename A>
+__device__ A lookback_chain(const LookbackDesc *look, int lt, uint32_t ep, A *stack,
+                            TrackerState *st) {
+    const int lane = threadIdx.x & 31;
+    int base = lt - 1;
+    for (int w = 0; w < kMaxWin; ++w, base -= 32) {
+        const int idx = base - lane;
+        uint32_t f = 0;
+        A val = static_cast<A>(0);
+        if (idx >= 0) {
+            f = wait_flag(&look[idx], ep, st);
+            if (f == 0u) f = 2u;   // timed out: treat as an inclusive zero (result invalid, flagged)
+            else val = static_cast<A>(ld_relaxed_f64((f & 3u) == 2u ? &look[idx].incl : &look[idx].agg));
+        }
+        stack[w * 32 + lane] = val;
+        const unsigned incl = __ballot_sync(0xffffffffu, idx >= 0 && (f & 3u) == 2u);
+        __syncwarp();
+        if (incl) {
+            const int q = __ffs(incl) - 1;   // nearest tile with its inclusive prefix
+            A acc = static_cast<A>(0);
+            if (lane == 0) {
+                acc = stack[w * 32 + q];
+                for (int l = q - 1; l >= 0; --l) acc = add_rn(acc, stack[w * 32 + l]);
+                for (int ww = w - 1; ww >= 0; --ww)
+                    for (int l = 31; l >= 0; --l) acc = add_rn(acc, stack[ww * 32 + l]);
+            }
+            return __shfl_sync(0xffffffffu, acc, 0);
+        }
+    }
+    // Far lookback: the immediate predecessor's inclusive prefix is the chain sum itself.
+    A acc = static_cast<A>(0);
+    if (lane == 0) {
+        uint32_t ns = 32;
+        uint32_t it = 0;
+        for (; it < kSpinLimit; ++it) {
+            const uint32_t f = ld_acquire_u32(&look[lt - 1].flag);
+            if (flag_ready(f, ep) && (f & 3u) == 2u) {
+                acc = static_cast<A>(ld_relaxed_f64(&look[lt - 1].incl));
+                break;
+            }
+            if ((it & 1023u) == 1023u && timed_out(st)) break;
+            __nanosleep(ns);
+            if (ns < 512) ns <<= 1;
+        }
+        if (it >= kSpinLimit) atomicOr(&st->status, kStatusTimeout);
+    }
+    return __shfl_sync(0xffffffffu, acc, 0);
+}
+
+// First index e in [0, n) with J[e] > j (J non-decreasing, J[n-1] > j).
+__device__ __forceinline__ int upper_index(const int32_t *J, int n, int64_t j) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (static_cast<int64_t>(J[mid]) > j) hi = mid; else lo = mid + 1;
+    }
+    return lo;
+}
+
+template <int P>
+__device__ void finalize_tracker(const TrackerDev &T, TrackerState *st, StepSmem<P> &sm) {
+    using acc_t = typename Prec<P>::acc_t;
+    __threadfence();
+    Stats<acc_t> v{neg_inf<acc_t>(), 0, 0, 0};
+    for (int i = threadIdx.x; i < T.ntiles; i += kThreads) {
+        const double *p = &T.part[i].m;
+        Stats<acc_t> w;
+        w.m = static_cast<acc_t>(__ldcg(p + 0));
+        w.s = static_cast<acc_t>(__ldcg(p + 1));
+        w.sx = static_cast<acc_t>(__ldcg(p + 2));
+        w.sy = static_cast<acc_t>(__ldcg(p + 3));
+        stats_merge(v, w);
+    }
+    const Stats<acc_t> r = block_stats(v, sm.red);
+    if (threadIdx.x == 0) {
+        const int64_t t = st->t;
+        const double M = static_cast<double>(r.m);
+        const double S = static_cast<double>(r.s);
+        const double ex = st->nx + static_cast<double>(r.sx) / S;
+        const double ey = st->ny + static_cast<double>(r.sy) / S;
+        st->M = M;
+        st->S = S;
+        st->invS = static_cast<double>(static_cast<acc_t>(1) / r.s);
+        st->ax = st->nx;
+        st->ay = st->ny;
+        if (isfinite(ex) && fabs(ex) < 1.0e9) st->nx = floor(ex) + ((ex - floor(ex)) >= 0.5 ? 1.0 : 0.0);
+        if (isfinite(ey) && fabs(ey) < 1.0e9) st->ny = floor(ey) + ((ey - floor(ey)) >= 0.5 ? 1.0 : 0.0);
+        st->est_x = ex;
+        st->est_y = ey;
+        const int64_t slot = t % T.est_cap;
+        T.est_ring[2 * slot] = ex;
+        T.est_ring[2 * slot + 1] = ey;
+        T.stat_ring[2 * slot] = M;
+        T.stat_ring[2 * slot + 1] = S;
+        st->t = t + 1;
+        st->epoch = st->epoch + 1u;
+        __threadfence();
+        atomicExch(T.done, 0u);
+    }
+}
+
+template <int P>
+__device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
+    using Tr = Prec<P>;
+    using pos_t = typename Tr::pos_t;
+    using lik_t = typename Tr::lik_t;
+    using acc_t = typename Tr::acc_t;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int ti = Lp.tile_trk[g];
+    const TrackerDev &T = Lp.trk[ti];
+    const FrameRef fr = Lp.frames[ti];
+    if (!fr.active) return;
+    TrackerState *st = T.state;
+    if (timed_out(st)) return;   // a failed step: results are invalid, skip without waiting
+
+    const int64_t N = T.N;
+    const int lt = g - T.tile_begin;
+    const int64_t k0 = static_cast<int64_t>(lt) * kTile;
+    const int cnt = static_cast<int>((N - k0) < kTile ? (N - k0) : kTile);
+    const int64_t t = __ldcg(&st->t);
+    const uint32_t ep = __ldcg(&st->epoch);
+    const int in = static_cast<int>((t + 1) & 1), out = static_cast<int>(t & 1);
+
+    const int W = T.W, H = T.H, r = T.r;
+    const uint8_t *frame;
+    int64_t pitch;
+    if (Lp.frame_override) { frame = Lp.frame_override; pitch = Lp.pitch_override; }
+    else { frame = fr.base + (fr.stride ? t * fr.stride : 0); pitch = fr.pitch; }
+    for (int i = tid; i <= 2 * r; i += kThreads) {
+        const int dy = i - r;
+        int w = 0;
+        while ((w + 1) * (w + 1) + dy * dy <= r * r) ++w;
+        sm.w[i] = static_cast<int8_t>(w);
+    }
+
+    // Anchor the offspring are written against (F16/BF16 offsets; estimate sums).
+    const double nxa = __ldcg(&st->nx), nya = __ldcg(&st->ny);
+
+    // ------------------------------------------------------------ 1. resampling
+    if (t > 0) {
+        const lik_t *Lin = static_cast<const lik_t *>(T.pl[in]);
+        const pos_t *Xin = static_cast<const pos_t *>(T.px[in]);
+        const pos_t *Yin = static_cast<const pos_t *>(T.py[in]);
+        const acc_t M = static_cast<acc_t>(__ldcg(&st->M));
+        const acc_t invS = static_cast<acc_t>(__ldcg(&st->invS));
+        for (int e = tid; e < cnt; e += kThreads) {
+            sm.ax[e] = Xin[k0 + e];
+            sm.ay[e] = Yin[k0 + e];
+        }
+        // blocked arrangement: thread tid owns elements tid*kItems .. +kItems-1
+        acc_t s[kItems];
+        acc_t run = static_cast<acc_t>(0);
+#pragma unroll
+        for (int m = 0; m < kItems; ++m) {
+            const int e = tid * kItems + m;
+            acc_t v = static_cast<acc_t>(0);
+            if (e < cnt) v = exp_acc(to_acc(Lin[k0 + e]) - M);
+            run = (m == 0) ? v : run + v;
+            s[m] = run;
+        }
+        // block exclusive scan of the thread totals
+        acc_t x = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const acc_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) sm.warp_sum[warp] = x;
+        acc_t xex = __shfl_up_sync(0xffffffffu, x, 1);
+        if (lane == 0) xex = static_cast<acc_t>(0);
+        __syncthreads();
+        acc_t wpre = static_cast<acc_t>(0);
+        for (int w = 0; w < warp; ++w) wpre += sm.warp_sum[w];
+        const acc_t off = wpre + xex;
+        acc_t loc[kItems];
+#pragma unroll
+        for (int m = 0; m < kItems; ++m) loc[m] = (tid == 0) ? s[m] : off + s[m];
+        // running max across threads: makes the tile-local prefix non-decreasing
+        acc_t mx = loc[kItems - 1];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const acc_t y = __shfl_up_sync(0xffffffffu, mx, o);
+            if (lane >= o) mx = fmax(mx, y);
+        }
+        if (lane == 31) sm.warp_max[warp] = mx;
+        acc_t mex = __shfl_up_sync(0xffffffffu, mx, 1);
+        __syncthreads();
+        acc_t wmax = static_cast<acc_t>(0);
+        for (int w = 0; w < warp; ++w) wmax = fmax(wmax, sm.warp_max[w]);
+        if (lane == 0) mex = wmax; else mex = fmax(mex, wmax);
+#pragma unroll
+        for (int m = 0; m < kItems; ++m) loc[m] = fmax(loc[m], mex);
+        // the tile aggregate is the clamped prefix at its last particle
+        {
+            const int el = cnt - 1;
+            if (el / kItems == tid) {
+#pragma unroll
+                for (int m = 0; m < kItems; ++m)
+                    if (m == el % kItems) sm.agg = loc[m];
+            }
+        }
+        __syncthreads();
+        const acc_t agg = sm.agg;
+        LookbackDesc *look = T.look;
+        if (tid == 0) {
+            if (lt == 0) {
+                look[0].incl = static_cast<double>(agg);
+                st_release_u32(&look[0].flag, ((ep & 0x3fffffffu) << 2) | 2u);
+                sm.excl = static_cast<acc_t>(0);
+            } else {
+                look[lt].agg = static_cast<double>(agg);
+                st_release_u32(&look[lt].flag, ((ep & 0x3fffffffu) << 2) | 1u);
+            }
+        }
+        if (lt > 0 && warp == 0) {
+            const acc_t ex = lookback_chain<acc_t>(look, lt, ep, sm.stack, st);
+            if (lane == 0) {
+                sm.excl = ex;
+                look[lt].incl = static_cast<double>(add_rn(ex, agg));
+                st_release_u32(&look[lt].flag, ((ep & 0x3fffffffu) << 2) | 2u);
+            }
+        }
+        __syncthreads();
+        const acc_t excl = sm.excl;
+        // CDF and strata counts
+        acc_t u0;
+        {
+            const uint4 w = philox4x32_10(make_uint4(0u, static_cast<uint32_t>(t - 1), 1u, T.tracker_id),
+                                          T.key_lo, T.key_hi);
+            u0 = static_cast<acc_t>(uniform_f64(w.x));
+        }
+        const acc_t inv_n = sizeof(acc_t) == 8 ? static_cast<acc_t>(T.inv_n) : static_cast<acc_t>(T.inv_n_f);
+#pragma unroll
+        for (int m = 0; m < kItems; ++m) {
+            const int e = tid * kItems + m;
+            if (e < cnt) {
+                const int64_t k = k0 + e;
+                acc_t C = mul_rn(add_rn(excl, loc[m]), invS);
+                int64_t J;
+                if (k == N - 1) { C = static_cast<acc_t>(1); J = N; }
+                else J = count_le<acc_t>(C, u0, inv_n, N);
+                sm.J[e] = static_cast<int32_t>(J);
+                if (T.dbg_cdf) static_cast<acc_t *>(T.dbg_cdf)[k] = C;
+            }
+        }
+        if (tid == 0) {
+            sm.jbeg = (lt == 0) ? 0 : count_le<acc_t>(mul_rn(excl, invS), u0, inv_n, N);
+        }
+        __syncthreads();
+        if (tid == 0) sm.jend = sm.J[cnt - 1];
+        __syncthreads();
+    } else {
+        if (tid == 0) { sm.jbeg = k0; sm.jend = k0 + cnt; }
+        __syncthreads();
+    }
+
+    // ------------------------------------------------------------ 2-4. offspring
+    const int64_t jbeg = sm.jbeg, jend = sm.jend;
+    pos_t *Xout = static_cast<pos_t *>(T.px[out]);
+    pos_t *Yout = static_cast<pos_t *>(T.py[out]);
+    lik_t *Lout = static_cast<lik_t *>(T.pl[out]);
+    const uint32_t tctr = static_cast<uint32_t>(t);
+    Stats<acc_t> stats{neg_inf<acc_t>(), 0, 0, 0};
+
+    // ancestor shift for offsets (previous anchor minus the current one)
+    const double shx = __ldcg(&st->ax) - nxa, shy = __ldcg(&st->ay) - nya;
+
+    for (int64_t q = (jbeg >> 1) + tid; q < ((jend + 1) >> 1); q += kThreads) {
+        const int64_t j0 = 2 * q, j1 = j0 + 1;
+        const bool v0 = j0 >= jbeg && j0 < jend;
+        const bool v1 = j1 >= jbeg && j1 < jend;
+        int e0 = 0, e1 = 0;
+        if (t > 0) {
+            if (v0) e0 = upper_index(sm.J, cnt, j0);
+            if (v1) e1 = (v0 && static_cast<int64_t>(sm.J[e0]) > j1) ? e0 : upper_index(sm.J, cnt, j1);
+            if (!v0) e0 = e1;
+            if (!v1) e1 = e0;
+            if (T.dbg_anc) {
+                if (v0) T.dbg_anc[j0] = static_cast<int32_t>(k0 + e0);
+                if (v1) T.dbg_anc[j1] = static_cast<int32_t>(k0 + e1);
+            }
+        }
+        const uint4 w0 = philox4x32_10(make_uint4(static_cast<uint32_t>(j0), tctr, 0u, T.tracker_id), T.key_lo, T.key_hi);
+        const uint4 w1 = philox4x32_10(make_uint4(static_cast<uint32_t>(j1), tctr, 0u, T.tracker_id), T.key_lo, T.key_hi);
+
+        if constexpr (!Tr::kHalf) {
+            // ---------------- REF64 / F32: absolute positions, exact-integer likelihood
+            acc_t xa0, ya0, xa1, ya1;
+            if (t > 0) { xa0 = sm.ax[e0]; ya0 = sm.ay[e0]; xa1 = sm.ax[e1]; ya1 = sm.ay[e1]; }
+            else {
+                xa0 = xa1 = static_cast<acc_t>(T.init_x);
+                ya0 = ya1 = static_cast<acc_t>(T.init_y);
+            }
+            acc_t n0x, n0y, n1x, n1y;
+            if (sizeof(acc_t) == 8) {
+                double a, b, c, d;
+                box_muller(uniform_f64(w0.x), uniform_f64(w0.y), a, b);
+                box_muller(uniform_f64(w1.x), uniform_f64(w1.y), c, d);
+                n0x = static_cast<acc_t>(a); n0y = static_cast<acc_t>(b);
+                n1x = static_cast<acc_t>(c); n1y = static_cast<acc_t>(d);
+            } else {
+                float a, b, c, d;
+                box_muller(uniform_f32(w0.x), uniform_f32(w0.y), a, b);
+                box_muller(uniform_f32(w1.x), uniform_f32(w1.y), c, d);
+                n0x = a; n0y = b; n1x = c; n1y = d;
+            }
+            const acc_t dxm = static_cast<acc_t>(T.drift_x), dym = static_cast<acc_t>(T.drift_y);
+            const acc_t sgx = static_cast<acc_t>(T.sigma_x), sgy = static_cast<acc_t>(T.sigma_y);
+            const acc_t x0 = add_rn(add_rn(xa0, dxm), mul_rn(sgx, n0x));
+            const acc_t y0 = add_rn(add_rn(ya0, dym), mul_rn(sgy, n0y));
+            const acc_t x1 = add_rn(add_rn(xa1, dxm), mul_rn(sgx, n1x));
+            const acc_t y1 = add_rn(add_rn(ya1, dym), mul_rn(sgy, n1y));
+            acc_t L0 = static_cast<acc_t>(0), L1 = static_cast<acc_t>(0);
+            const acc_t c1 = static_cast<acc_t>(T.c1), c2D = static_cast<acc_t>(T.c2 * T.D);
+            const acc_t den = static_cast<acc_t>(T.den);
+            if (v0) {
+                const uint32_t s0 = disk_sum(frame, pitch, W, H, r, sm.w, pixel_of(x0), pixel_of(y0));
+                L0 = (c1 * (static_cast<acc_t>(2) * static_cast<acc_t>(s0) - c2D)) / den;
+            }
+            if (v1) {
+                const uint32_t s1 = disk_sum(frame, pitch, W, H, r, sm.w, pixel_of(x1), pixel_of(y1));
+                L1 = (c1 * (static_cast<acc_t>(2) * static_cast<acc_t>(s1) - c2D)) / den;
+            }
+            if (v0 && v1) {
+                if constexpr (sizeof(acc_t) == 8) {
+                    reinterpret_cast<double2 *>(Xout)[q] = make_double2(x0, x1);
+                    reinterpret_cast<double2 *>(Yout)[q] = make_double2(y0, y1);
+                    reinterpret_cast<double2 *>(Lout)[q] = make_double2(L0, L1);
+                } else {
+                    reinterpret_cast<float2 *>(Xout)[q] = make_float2(x0, x1);
+                    reinterpret_cast<float2 *>(Yout)[q] = make_float2(y0, y1);
+                    reinterpret_cast<float2 *>(Lout)[q] = make_float2(L0, L1);
+                }
+            } else if (v0) {
+                Xout[j0] = x0; Yout[j0] = y0; Lout[j0] = L0;
+            } else if (v1) {
+                Xout[j1] = x1; Yout[j1] = y1; Lout[j1] = L1;
+            }
+            if (v0) stats_add(stats, L0, x0 - static_cast<acc_t>(nxa), y0 - static_cast<acc_t>(nya));
+            if (v1) stats_add(stats, L1, x1 - static_cast<acc_t>(nxa), y1 - static_cast<acc_t>(nya));
+        } else {
+            // ---------------- F16 / BF16: half2 lanes = particles (j0, j1)
+            using h2 = typename Vec2<pos_t>::type;
+            h2 ox, oy;
+            if (t > 0) {
+                ox = make2(sm.ax[e0], sm.ax[e1]);
+                oy = make2(sm.ay[e0], sm.ay[e1]);
+                const float sx = static_cast<float>(shx), sy = static_cast<float>(shy);
+                if (sx != 0.0f || sy != 0.0f) {
+                    ox = __hadd2(ox, f2_to2(sx, sx, (h2 *)nullptr));
+                    oy = __hadd2(oy, f2_to2(sy, sy, (h2 *)nullptr));
+                }
+            } else {
+                const float ix = static_cast<float>(T.init_x - nxa), iy = static_cast<float>(T.init_y - nya);
+                ox = f2_to2(ix, ix, (h2 *)nullptr);
+                oy = f2_to2(iy, iy, (h2 *)nullptr);
+            }
+            float a, b, c, d;
+            box_muller(uniform_f32(w0.x), uniform_f32(w0.y), a, b);
+            box_muller(uniform_f32(w1.x), uniform_f32(w1.y), c, d);
+            const float dxm = static_cast<float>(T.drift_x), dym = static_cast<float>(T.drift_y);
+            const float sgx = static_cast<float>(T.sigma_x), sgy = static_cast<float>(T.sigma_y);
+            ox = __hadd2(ox, f2_to2(dxm + sgx * a, dxm + sgx * c, (h2 *)nullptr));
+            oy = __hadd2(oy, f2_to2(dym + sgy * b, dym + sgy * d, (h2 *)nullptr));
+            const int axi = static_cast<int>(nxa), ayi = static_cast<int>(nya);
+            const int px0 = axi + pixel_of(lo_f(ox)), py0 = ayi + pixel_of(lo_f(oy));
+            const int px1 = axi + pixel_of(hi_f(ox)), py1 = ayi + pixel_of(hi_f(oy));
+            const h2 kap = f2_to2(T.kappa, T.kappa, (h2 *)nullptr);
+            const bool half_acc = std::is_same<pos_t, __half>::value && !(T.flags & 0x2u);
+            const float lvl_b = std::is_same<pos_t, __half>::value ? 1024.0f + T.bg_f : T.bg_f;
+            const float lvl_f = std::is_same<pos_t, __half>::value ? 1024.0f + T.fg_f : T.fg_f;
+            const h2 bgo = f2_to2(lvl_b, lvl_b, (h2 *)nullptr);
+            const h2 fgo = f2_to2(lvl_f, lvl_f, (h2 *)nullptr);
+            h2 hacc = f2_to2(0.0f, 0.0f, (h2 *)nullptr);
+            float facc0 = 0.0f, facc1 = 0.0f;
+            const bool inside = px0 - r >= 0 && px0 + r < W && py0 - r >= 0 && py0 + r < H &&
+                                px1 - r >= 0 && px1 + r < W && py1 - r >= 0 && py1 + r < H;
+            for (int dy = -r; dy <= r; ++dy) {
+                const int w = sm.w[dy + r];
+                const uint8_t *row0 = frame + static_cast<int64_t>(inside ? py0 + dy : clampi(py0 + dy, 0, H - 1)) * pitch;
+                const uint8_t *row1 = frame + static_cast<int64_t>(inside ? py1 + dy : clampi(py1 + dy, 0, H - 1)) * pitch;
+                for (int dx = -w; dx <= w; ++dx) {
+                    const uint32_t i0 = __ldg(row0 + (inside ? px0 + dx : clampi(px0 + dx, 0, W - 1)));
+                    const uint32_t i1 = __ldg(row1 + (inside ? px1 + dx : clampi(px1 + dx, 0, W - 1)));
+                    const h2 tm = HalfLik<h2>::term(HalfLik<h2>::pix(i0, i1), bgo, fgo, kap);
+                    if (half_acc) hacc = __hadd2(hacc, tm);
+                    else { facc0 += lo_f(tm); facc1 += hi_f(tm); }
+                }
+            }
+            h2 L2 = half_acc ? hacc : f2_to2(facc0, facc1, (h2 *)nullptr);
+            if (v0 && v1) {
+                reinterpret_cast<h2 *>(Xout)[q] = ox;
+                reinterpret_cast<h2 *>(Yout)[q] = oy;
+                reinterpret_cast<h2 *>(Lout)[q] = L2;
+            } else if (v0) {
+                Xout[j0] = lo_h(ox); Yout[j0] = lo_h(oy); Lout[j0] = lo_h(L2);
+            } else if (v1) {
+                Xout[j1] = hi_h(ox); Yout[j1] = hi_h(oy); Lout[j1] = hi_h(L2);
+            }
+            if (v0) stats_add(stats, lo_f(L2), lo_f(ox), lo_f(oy));
+            if (v1) stats_add(stats, hi_f(L2), hi_f(ox), hi_f(oy));
+        }
+    }
+
+    // ------------------------------------------------------------ 5. tile partial + finalise
+    const Stats<acc_t> tot = block_stats(stats, sm.red);
+    if (tid == 0) {
+        TilePartial *p = &T.part[lt];
+        p->m = static_cast<double>(tot.m);
+        p->s = static_cast<double>(tot.s);
+        p->sx = static_cast<double>(tot.sx);
+        p->sy = static_cast<double>(tot.sy);
+        __threadfence();
+        const uint32_t prev = atomicAdd(T.done, 1u);
+        sm.last = (prev == static_cast<uint32_t>(T.ntiles - 1)) ? 1u : 0u;
+    }
+    __syncthreads();
+    if (sm.last) finalize_tracker<P>(T, st, sm);
+}
+
+template <int P>
+__global__ void __launch_bounds__(kThreads) step_kernel(const StepLaunch Lp) {
+    __shared__ StepSmem<P> sm;
+    for (;;) {
+        if (threadIdx.x == 0) sm.ticket = atomicAdd(Lp.ticket, 1u);
+        __syncthreads();
+        const uint32_t g = sm.ticket;
+        __syncthreads();
+        if (g >= static_cast<uint32_t>(Lp.total_tiles)) {
+            if (threadIdx.x == 0 && g == static_cast<uint32_t>(Lp.total_tiles) + gridDim.x - 1u)
+                atomicExch(Lp.ticket, 0u);
+            return;
+        }
+        run_tile<P>(Lp, static_cast<int>(g), sm);
+        __syncthreads();
+    }
+}
+
+__global__ void philox_kernel(const uint4 *ctrs, int64_t n, uint32_t k0, uint32_t k1, uint4 *out) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = philox4x32_10(ctrs[i], k0, k1);
+}
+
+template <int P>
+int occupancy_grid(int total_tiles) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel<P>, kThreads, 0);
+    if (per_sm < 1) per_sm = 1;
+    const int g = sms * per_sm;
+    return total_tiles < g ? total_tiles : g;
+}
+
+}  // namespace
+
+int step_grid_size(int precision, int total_tiles) {
+    switch (precision) {
+        case 0: return occupancy_grid<0>(total_tiles);
+        case 1: return occupancy_grid<1>(total_tiles);
+        case 2: return occupancy_grid<2>(total_tiles);
+        case 3: return occupancy_grid<3>(total_tiles);
+    }
+    return 0;
+}
+
+int launch_step(int precision, const StepLaunch &L, int grid, void *stream) {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (grid < 1) grid = 1;
+    switch (precision) {
+        case 0: step_kernel<0><<<grid, kThreads, 0, s>>>(L); break;
+        case 1: step_kernel<1><<<grid, kThreads, 0, s>>>(L); break;
+        case 2: step_kernel<2><<<grid, kThreads, 0, s>>>(L); break;
+        case 3: step_kernel<3><<<grid, kThreads, 0, s>>>(L); break;
+        default: return -1;
+    }
+    return static_cast<int>(cudaGetLastError());
+}
+
+int launch_debug_philox(const uint32_t *d_ctrs, int64_t n, uint64_t seed, uint32_t *d_out, void *stream) {
+    if (n <= 0) return 0;
+    const int64_t blocks = (n + 255) / 256;
+    philox_kernel<<<static_cast<unsigned>(blocks), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        reinterpret_cast<const uint4 *>(d_ctrs), n, static_cast<uint32_t>(seed & 0xffffffffu),
+        static_cast<uint32_t>(seed >> 32), reinterpret_cast<uint4 *>(d_out));
+    return static_cast<int>(cudaGetLastError());
+}
+
+}  // namespace pfk

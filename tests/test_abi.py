@@ -1,0 +1,80 @@
+"""The C-ABI library builds, loads on a machine without a GPU, and exports every entry
+point that include/pf.h declares (no compute call is made here)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from conftest import ROOT
+
+HEADER = os.path.join(ROOT, "include", "pf.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pf_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2308_00763_gb300 import build
+    return build.build()
+
+
+def test_header_compiles_as_c():
+    out = os.path.join(ROOT, "paper_2308_00763_gb300", "_build", "hdr_check.o")
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-x", "c", "-c", "-o", out, "-"],
+                   input=b'#include "pf.h"\nint pf_check_sizes(void){return (int)sizeof(pf_config);}\n',
+                   cwd=os.path.join(ROOT, "include"), check=True)
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    declared = _declared()
+    assert "pf_create" in declared and "pf_step_frame" in declared and "pf_estimate" in declared
+    missing = [name for name in declared if not hasattr(lib, name)]
+    assert not missing, missing
+
+
+def test_binding_covers_the_header(libpath):
+    import paper_2308_00763_gb300 as pf
+    for name in _declared():
+        assert name in pf.EXPORTED and callable(getattr(pf, name)), name
+    assert pf.pf_status_string(pf.PF_ERR_TIMEOUT) == "device wait timed out"
+
+
+def test_struct_layouts_match_c(libpath):
+    import paper_2308_00763_gb300 as pf
+    src = ('#include <stdio.h>\n#include <stddef.h>\n#include "pf.h"\nint main(void){printf("%zu %zu %zu %zu %zu",'
+           ' sizeof(pf_config), offsetof(pf_config, seed), offsetof(pf_config, est_capacity),'
+           ' sizeof(pf_state_header), offsetof(pf_state_header, est_y)); return 0;}\n')
+    exe = os.path.join(ROOT, "paper_2308_00763_gb300", "_build", "layout_check")
+    subprocess.run(["gcc", "-x", "c", "-o", exe, "-", "-I", os.path.join(ROOT, "include")],
+                   input=src.encode(), check=True)
+    got = list(map(int, subprocess.run([exe], capture_output=True, check=True).stdout.split()))
+    want = [ctypes.sizeof(pf.PfConfig), pf.PfConfig.seed.offset, pf.PfConfig.est_capacity.offset,
+            ctypes.sizeof(pf.PfStateHeader), pf.PfStateHeader.est_y.offset]
+    assert got == want
+
+
+def test_invalid_configs_rejected_without_gpu(libpath):
+    """Argument validation happens on the host before any CUDA call."""
+    import paper_2308_00763_gb300 as pf
+    bad = [dict(num_particles=0), dict(disk_radius=-1), dict(disk_radius=65), dict(width=0),
+           dict(precision=7), dict(sigma=(-1.0, 1.0)), dict(init=(float("nan"), 0.0))]
+    for b in bad:
+        kw = dict(width=64, height=64, num_particles=100, disk_radius=3, precision="f32")
+        kw.update({k: v for k, v in b.items() if k in kw})
+        extra = {k: v for k, v in b.items() if k not in kw}
+        cfg = pf.make_config(kw["width"], kw["height"], kw["num_particles"], kw["disk_radius"],
+                             kw["precision"], **extra)
+        h = ctypes.c_void_p()
+        rc = pf.lib().pf_create(ctypes.byref(cfg), None, ctypes.byref(h))
+        assert rc == pf.PF_ERR_ARG, b
+        assert not h.value
+    assert pf.lib().pf_create(None, None, None) == pf.PF_ERR_ARG
+    assert pf.lib().pf_destroy(None) == pf.PF_OK

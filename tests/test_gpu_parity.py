@@ -1,0 +1,299 @@
+"""GPU parity: the sm_103a library against the CPU FP64 oracle, through the C ABI.
+
+Bit-exact on the integer work (Philox words, resampled ancestor indices given the CDF the
+step computed, pixel rounding / disk sums via the exact REF64 likelihood), within the
+stated tolerances on floating point: REF64 track within 1e-9 px, FP32 within 1e-3 px,
+FP16/BF16 track RMSE within 0.5 px of the oracle's FP64 track.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2308_00763_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TILE = 2048  # particles per tile of the step kernel (resampling side)
+
+
+@pytest.fixture(scope="module")
+def pf():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2308_00763_gb300 as m
+    m.lib(build_if_missing=True)
+    return m
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _abs_positions(st, prec):
+    if prec in ("f16", "bf16"):
+        return st["x"] + st["anchor_x"], st["y"] + st["anchor_y"]
+    return st["x"], st["y"]
+
+
+def _run_gpu(pf, video, N, prec, *, seed=1, r=None, flags=0, init=None, sigma=(1.0, 1.0),
+             drift=(0.0, 0.0), tracker=0, on_device=True):
+    r = video.radius if r is None else r
+    init = tuple(video.centres[0]) if init is None else init
+    f = pf.Filter(video.W, video.H, N, r, prec, init=init, seed=seed, flags=flags, sigma=sigma,
+                  drift=drift, tracker_id=tracker)
+    torch = _torch()
+    frames = torch.from_numpy(video.frames).cuda() if on_device else video.frames
+    f.run(frames)
+    est, ms = f.estimates(0, video.T, with_stats=True)
+    return f, est, ms
+
+
+# ----------------------------------------------------------------------------- RNG
+def test_philox_device_bit_exact(pf):
+    rng = np.random.default_rng(0)
+    ctr = rng.integers(0, 2 ** 32, size=(100000, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[:10] = 0
+    ctr[10:20] = 0xFFFFFFFF
+    for seed in (1, 0xDEADBEEFCAFEF00D, 2 ** 64 - 1):
+        assert np.array_equal(pf.pf_debug_philox(ctr, seed), oracle.philox(ctr, seed))
+
+
+# ----------------------------------------------------------------------------- whole tracks
+def test_config1_ref64_track_within_1e9(pf):
+    """128x128, 10 frames, r = 5, noise 5, N = 1000, sigma 1 px, init at the true start,
+    Philox seed 1: the FP64 GPU track equals the oracle's within 1e-9 px."""
+    v = synth.make_video(128, 128, 10, 5, noise=5.0, seed=1)
+    est_o, M_o, S_o = oracle.track(v.frames, 1000, 5, init=tuple(v.centres[0]), seed=1)
+    _, est, ms = _run_gpu(pf, v, 1000, "ref64")
+    assert np.abs(est - est_o).max() <= 1e-9
+    assert np.array_equal(ms[:, 0], M_o)           # max L is exact (integer disk sums)
+    np.testing.assert_allclose(ms[:, 1], S_o, rtol=1e-12)
+
+
+def test_config1_f32_track_within_1e3(pf):
+    v = synth.make_video(128, 128, 10, 5, noise=5.0, seed=1)
+    est_o, _, _ = oracle.track(v.frames, 1000, 5, init=tuple(v.centres[0]), seed=1)
+    _, est, _ = _run_gpu(pf, v, 1000, "f32")
+    assert np.abs(est - est_o).max() <= 1e-3
+
+
+@pytest.mark.parametrize("prec,flags", [("f16", 0), ("f16", 2), ("bf16", 0)])
+def test_config1_half_track_rmse(pf, prec, flags):
+    v = synth.make_video(128, 128, 10, 5, noise=5.0, seed=1)
+    est_o, _, _ = oracle.track(v.frames, 1000, 5, init=tuple(v.centres[0]), seed=1)
+    _, est, _ = _run_gpu(pf, v, 1000, prec, flags=flags)
+    rmse = math.sqrt(np.mean(np.sum((est - est_o) ** 2, axis=1)))
+    assert rmse <= 0.5, rmse
+
+
+def test_host_and_device_frames_agree(pf):
+    v = synth.make_video(96, 80, 6, 4, noise=5.0, seed=7, v=(1.5, 1.0))
+    _, e1, _ = _run_gpu(pf, v, 3000, "f32", on_device=True)
+    _, e2, _ = _run_gpu(pf, v, 3000, "f32", on_device=False)
+    assert np.array_equal(e1, e2)
+
+
+def test_deterministic_bits(pf):
+    v = synth.make_video(128, 128, 8, 5, noise=5.0, seed=3)
+    for prec in ("ref64", "f32", "f16"):
+        _, a, _ = _run_gpu(pf, v, 50000, prec)
+        _, b, _ = _run_gpu(pf, v, 50000, prec)
+        assert np.array_equal(a, b), prec
+
+
+# ----------------------------------------------------------------------------- teacher-forced step
+def _check_step(pf, prec, N, video, t_check, *, seed=5, r=None, sample=None):
+    """Run the GPU to frame t_check-1, read its state, run frame t_check with debug arrays
+    and check every stage against the oracle applied to the GPU's own inputs."""
+    r = video.radius if r is None else r
+    f = pf.Filter(video.W, video.H, N, r, prec, init=tuple(video.centres[0]), seed=seed,
+                  flags=pf.PF_FLAG_DEBUG_ARRAYS)
+    torch = _torch()
+    frames = torch.from_numpy(video.frames).cuda()
+    f.run(frames[:t_check])
+    st0 = f.get_state()
+    f.step(frames[t_check])
+    st1 = f.get_state()
+    anc = f.debug(0).astype(np.int64)
+    C = f.debug(1).astype(np.float64)
+    xs0, ys0 = _abs_positions(st0, prec)
+    xs1, ys1 = _abs_positions(st1, prec)
+    dec = "f64" if prec == "ref64" else "f32"
+
+    # CDF of the previous frame from the GPU's L: oracle cumulative sum
+    M, e = oracle.weights(st0["L"])
+    assert M == st0["max_l"]
+    S, _, _ = oracle.normalise(e, xs0, ys0)
+    C_o = oracle.cdf(e, S)
+    assert np.all(np.diff(C) >= 0), "CDF not monotone"
+    assert C[-1] == 1.0
+    ntiles = (N + TILE - 1) // TILE
+    tol = 1e-12 if prec == "ref64" else 4e-6 + ntiles * 1.2e-7   # FP32 chain over the tiles
+    assert np.abs(C - C_o).max() <= tol
+
+    # ancestors: bit-exact given the CDF the step used
+    u0 = oracle.resample_u0(seed, t_check - 1)
+    a_o = oracle.resample(C, u0, dec)
+    assert np.array_equal(anc, a_o)
+
+    # propagation of the ancestors (Eq. 1-2) and likelihood (Eq. 3)
+    idx = np.arange(N) if sample is None else sample
+    x_o, y_o = oracle.propagate(N, t_check, seed, xs0, ys0, anc)
+    if prec == "ref64":
+        assert np.abs(xs1[idx] - x_o[idx]).max() <= 1e-12
+        assert np.abs(ys1[idx] - y_o[idx]).max() <= 1e-12
+    elif prec == "f32":
+        assert np.abs(xs1[idx] - x_o[idx]).max() <= 1e-4
+    else:   # two roundings of an offset below 16 px: half ulp <= 2^-7, bfloat16 ulp <= 2^-4
+        assert np.abs(xs1[idx] - x_o[idx]).max() <= (0.02 if prec == "f16" else 0.15)
+    L_o = oracle.likelihood_all(xs1[idx], ys1[idx], video.frames[t_check], r)
+    if prec == "ref64":
+        assert np.array_equal(st1["L"][idx], L_o)
+    elif prec == "f32":
+        np.testing.assert_allclose(st1["L"][idx], L_o, rtol=2 ** -23, atol=1e-4)
+    else:
+        D = oracle.disk_count(r)
+        assert np.abs(st1["L"][idx] - L_o).max() <= D * 0.25 + 1.0
+
+    # estimate of the new frame from the GPU's own L and positions
+    M1, e1 = oracle.weights(st1["L"])
+    S1, xh, yh = oracle.normalise(e1, xs1, ys1)
+    tol_e = 1e-9 if prec == "ref64" else (1e-3 if prec == "f32" else 2e-2)
+    assert abs(st1["est_x"] - xh) <= tol_e and abs(st1["est_y"] - yh) <= tol_e
+    assert st1["max_l"] == M1
+    f.close()
+
+
+@pytest.mark.parametrize("prec", ["ref64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("N", [1, 2, 3, TILE - 1, TILE, TILE + 1, 3 * TILE + 17])
+def test_teacher_forced_step(pf, prec, N):
+    v = synth.make_video(128, 128, 4, 5, noise=5.0, seed=11)
+    _check_step(pf, prec, N, v, 3)
+
+
+@pytest.mark.parametrize("prec", ["ref64", "f32", "f16"])
+def test_teacher_forced_step_wide_cloud_many_tiles(pf, prec):
+    """A wide cloud (sigma 6 px, flat weights) spreads offspring over every tile."""
+    v = synth.make_video(200, 160, 4, 3, noise=20.0, seed=12)
+    f_kw = dict(seed=9)
+    N = 40 * TILE + 5
+    f = pf.Filter(v.W, v.H, N, 3, prec, init=tuple(v.centres[0]), sigma=(6.0, 6.0),
+                  flags=pf.PF_FLAG_DEBUG_ARRAYS, **f_kw)
+    torch = _torch()
+    fr = torch.from_numpy(v.frames).cuda()
+    f.run(fr[:2])
+    st0 = f.get_state()
+    f.step(fr[2])
+    anc = f.debug(0).astype(np.int64)
+    C = f.debug(1).astype(np.float64)
+    assert np.all(np.diff(C) >= 0) and C[-1] == 1.0
+    a_o = oracle.resample(C, oracle.resample_u0(9, 1), "f64" if prec == "ref64" else "f32")
+    assert np.array_equal(anc, a_o)
+    assert len(np.unique(anc)) > 1000
+
+
+@pytest.mark.parametrize("prec", ["ref64", "f32"])
+def test_edge_of_frame_and_radius_extremes(pf, prec):
+    """Particles whose template leaves the frame (clamped, reading C4), r = 0 and r = 12,
+    a non-square frame."""
+    v = synth.make_video(70, 45, 4, 3, noise=5.0, seed=13, c0=(2.0, 43.0), v=(0.0, 0.0))
+    for r in (0, 1, 12):
+        _check_step(pf, prec, 5000, v, 2, r=r)
+
+
+def test_pitched_device_frames(pf):
+    torch = _torch()
+    v = synth.make_video(100, 64, 5, 4, noise=5.0, seed=14)
+    padded = torch.zeros((v.T, v.H, 128), dtype=torch.uint8, device="cuda")
+    padded[:, :, :v.W] = torch.from_numpy(v.frames).cuda()
+    f1 = pf.Filter(v.W, v.H, 4000, 4, "ref64", init=tuple(v.centres[0]), seed=3)
+    for t in range(v.T):
+        f1.step(padded[t, :, :v.W])
+    _, e2, _ = _run_gpu(pf, v, 4000, "ref64", seed=3)
+    assert np.array_equal(f1.estimates(0, v.T), e2)
+
+
+def test_dominant_particle(pf):
+    """One particle far better than all others receives every offspring."""
+    f = pf.Filter(64, 64, 5000, 2, "f32", init=(32.0, 32.0), seed=2, flags=pf.PF_FLAG_DEBUG_ARRAYS)
+    st = {"t": 1, "max_l": 0.0, "sum_e": 1.0, "anchor_x": 32.0, "anchor_y": 32.0,
+          "next_anchor_x": 32.0, "next_anchor_y": 32.0, "est_x": 32.0, "est_y": 32.0}
+    x = np.full(5000, 10.0)
+    y = np.full(5000, 10.0)
+    L = np.full(5000, -500.0)
+    x[3777], y[3777], L[3777] = 40.25, 20.5, 0.0
+    st.update(x=x, y=y, L=L)
+    f.set_state(st)
+    f.step(np.full((64, 64), 100, np.uint8))
+    assert np.all(f.debug(0) == 3777)
+
+
+def test_checkpoint_resume_bit_identical(pf):
+    v = synth.make_video(128, 128, 10, 5, noise=5.0, seed=15)
+    torch = _torch()
+    fr = torch.from_numpy(v.frames).cuda()
+    for prec in ("ref64", "f32", "f16", "bf16"):
+        a = pf.Filter(v.W, v.H, 9000, 5, prec, init=tuple(v.centres[0]), seed=4)
+        a.run(fr)
+        full = a.estimates(0, v.T)
+        b = pf.Filter(v.W, v.H, 9000, 5, prec, init=tuple(v.centres[0]), seed=4)
+        b.run(fr[:6])
+        st = b.get_state()
+        c = pf.Filter(v.W, v.H, 9000, 5, prec, init=tuple(v.centres[0]), seed=4)
+        c.set_state(st)
+        c.run(fr[6:])
+        assert np.array_equal(c.estimates(6, 4), full[6:]), prec
+
+
+# ----------------------------------------------------------------------------- batches
+def test_batch_equals_single_trackers(pf):
+    torch = _torch()
+    vids = [synth.make_video(96, 96, 6, 3, noise=5.0, seed=20),
+            synth.make_video(160, 120, 6, 5, noise=5.0, seed=21, v=(-1, 1)),
+            synth.make_video(64, 64, 6, 2, noise=5.0, seed=22, v=(0.5, 0.5))]
+    Ns = [1000, 3 * TILE + 7, 17]
+    for prec in ("ref64", "f32", "f16"):
+        cfgs = [pf.make_config(v.W, v.H, n, v.radius, prec, init=tuple(v.centres[0]), seed=30 + i,
+                               tracker_id=i) for i, (v, n) in enumerate(zip(vids, Ns))]
+        b = pf.Batch(cfgs)
+        fr = [torch.from_numpy(v.frames).cuda() for v in vids]
+        got = []
+        for t in range(6):
+            b.step([f[t] for f in fr])
+            got.append(b.estimates(t))
+        got = np.stack(got, axis=1)
+        for i, (v, n) in enumerate(zip(vids, Ns)):
+            s = pf.Filter(v.W, v.H, n, v.radius, prec, init=tuple(v.centres[0]), seed=30 + i, tracker_id=i)
+            s.run(fr[i])
+            assert np.array_equal(s.estimates(0, 6), got[i]), (prec, i)
+
+
+def test_batch_inactive_trackers_hold_state(pf):
+    torch = _torch()
+    v = synth.make_video(64, 64, 4, 3, noise=5.0, seed=23)
+    fr = torch.from_numpy(v.frames).cuda()
+    cfgs = [pf.make_config(64, 64, 500, 3, "f32", init=tuple(v.centres[0]), seed=1, tracker_id=i)
+            for i in range(2)]
+    b = pf.Batch(cfgs)
+    b.step([fr[0], fr[0]])
+    b.step([fr[1], None], active=[1, 0])
+    e = b.estimates(1)
+    assert np.isfinite(e[0]).all() and np.isnan(e[1]).all()
+    b.step([fr[2], fr[1]])
+    e2 = b.estimates(1)
+    assert np.isfinite(e2).all()
+
+
+# ----------------------------------------------------------------------------- full size (sampled)
+@pytest.mark.parametrize("prec", ["ref64", "f32", "f16"])
+def test_full_size_config2_step_sampled(pf, prec):
+    """512x512, r = 5, N = 2^20 (the bench's launch configuration): one teacher-forced
+    step with every ancestor checked and the propagation / likelihood sampled."""
+    v = synth.make_video(512, 512, 3, 5, noise=5.0, seed=1)
+    rng = np.random.default_rng(0)
+    sample = np.unique(np.concatenate([rng.integers(0, 1 << 20, 4000), [0, (1 << 20) - 1]]))
+    _check_step(pf, prec, 1 << 20, v, 2, seed=1, sample=sample)
