@@ -134,6 +134,66 @@ __device__ __forceinline__ double ld_relaxed_f64(const double *p) {
 }
 
 // ----------------------------------------------------------------------------------
+// 128-bit fixed point for the inter-tile prefix of the CDF scan: x -> round-down(x * 2^90).
+// Tile aggregates are at most 2^11 and a tracker's total at most 2^31, so 2^121 bounds
+// every value; the sum of integers is exact and associative.
+// ----------------------------------------------------------------------------------
+constexpr int kFixShift = 90;
+
+struct U128 {
+    uint64_t lo, hi;
+};
+
+__device__ __forceinline__ U128 add128(U128 a, U128 b) {
+    U128 r;
+    r.lo = a.lo + b.lo;
+    r.hi = a.hi + b.hi + (r.lo < a.lo ? 1ull : 0ull);
+    return r;
+}
+
+// Non-negative finite double -> floor(v * 2^90) (values below 2^-90 become 0).
+__device__ __forceinline__ U128 to_fixed(double v) {
+    U128 r{0ull, 0ull};
+    if (!(v > 0.0)) return r;
+    const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(v));
+    const int ex = static_cast<int>((bits >> 52) & 0x7ff);
+    if (ex == 0) return r;  // subnormal: far below 2^-90
+    const uint64_t mant = (bits & 0xfffffffffffffull) | 0x10000000000000ull;  // 53 bits
+    const int sh = ex - 1075 + kFixShift;   // v * 2^90 = mant * 2^sh
+    if (sh <= -53) return r;
+    if (sh < 0) { r.lo = mant >> (-sh); return r; }
+    if (sh == 0) { r.lo = mant; return r; }
+    if (sh < 64) { r.lo = mant << sh; r.hi = mant >> (64 - sh); return r; }
+    r.hi = mant << (sh - 64);
+    return r;
+}
+
+// Fixed point -> double: the top 64 significant bits rounded to nearest; monotone
+// non-decreasing and deterministic, which is all the scan boundaries rely on.
+__device__ __forceinline__ double from_fixed(U128 x) {
+    if (x.hi == 0ull) return __ull2double_rn(x.lo) * 8.0779356694631609e-28;   // 2^-90
+    const int lz = __clzll(static_cast<long long>(x.hi));
+    const uint64_t top = (x.hi << lz) | (lz ? (x.lo >> (64 - lz)) : 0ull);
+    const int e2 = 64 - lz - kFixShift;                     // value = top * 2^e2
+    const double scale = __longlong_as_double(static_cast<long long>(1023 + e2) << 52);
+    return __ull2double_rn(top) * scale;
+}
+
+__device__ __forceinline__ U128 ld_relaxed_u128(const uint64_t *lo_hi) {
+    U128 r;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(r.lo) : "l"(lo_hi) : "memory");
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(r.hi) : "l"(lo_hi + 1) : "memory");
+    return r;
+}
+
+__device__ __forceinline__ U128 shfl_down128(U128 v, int o) {
+    U128 r;
+    r.lo = __shfl_down_sync(0xffffffffu, v.lo, o);
+    r.hi = __shfl_down_sync(0xffffffffu, v.hi, o);
+    return r;
+}
+
+// ----------------------------------------------------------------------------------
 // Precision traits.  acc_t is the precision of the weights, sums, scan and CDF.
 // ----------------------------------------------------------------------------------
 template <int P> struct Prec;

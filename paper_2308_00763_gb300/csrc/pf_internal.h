@@ -22,12 +22,14 @@ constexpr int kMaxRadius = 64;
 // Device status bits (sticky, per tracker).
 constexpr uint32_t kStatusTimeout = 0x1u;
 
+// Tile status of the decoupled lookback.  The inter-tile prefix is an exact fixed-point
+// sum (value * 2^kFixShift in 128 bits), so its value does not depend on the order in
+// which a tile collects its predecessors' aggregates.
 struct alignas(16) LookbackDesc {
     uint32_t flag;      // (epoch << 2) | state, state: 0 empty, 1 aggregate, 2 inclusive
-    uint32_t pad;
-    double agg;         // tile aggregate of e (scan precision, stored exactly in double)
-    double incl;        // inclusive prefix through this tile
-    double pad2;
+    uint32_t pad[3];
+    uint64_t agg_lo, agg_hi;    // tile aggregate of e, fixed point
+    uint64_t incl_lo, incl_hi;  // inclusive prefix through this tile, fixed point
 };
 
 struct alignas(16) TilePartial {

@@ -34,7 +34,6 @@ namespace pfk {
 namespace {
 
 constexpr int kWarps = kThreads / 32;
-constexpr int kMaxWin = 8;               // lookback windows of 32 tiles kept for the chain sum
 constexpr uint32_t kSpinLimit = 1u << 22;  // bounded waits: ~1 s with backoff
 
 __device__ __forceinline__ bool flag_ready(uint32_t f, uint32_t ep) {
@@ -218,64 +217,57 @@ struct __align__(16) StepSmem {
     int32_t J[kTile];         // J[e] = number of strata assigned to particles k0..k0+e
     acc_t warp_sum[kWarps];
     acc_t warp_max[kWarps];
-    acc_t stack[kMaxWin * 32];
+    U128 red128[kWarps];
     Stats<acc_t> red[kWarps];
     acc_t agg;
-    acc_t excl;
+    U128 excl_x, end_x;       // exact fixed-point prefix before / after the tile
+    int qmin;
     int64_t jbeg, jend;
     int8_t w[2 * kMaxRadius + 1];
     uint32_t ticket;
     uint32_t last;
 };
 
-// Exclusive chain-order prefix of tile lt from the earlier tiles' descriptors (warp 0).
-template <typename A>
-__device__ A lookback_chain(const LookbackDesc *look, int lt, uint32_t ep, A *stack,
-                            TrackerState *st) {
-    const int lane = threadIdx.x & 31;
-    int base = lt - 1;
-    for (int w = 0; w < kMaxWin; ++w, base -= 32) {
-        const int idx = base - lane;
-        uint32_t f = 0;
-        A val = static_cast<A>(0);
+// Block-wide sum of a 128-bit value (exact, so the order is irrelevant); valid in thread 0.
+__device__ U128 block_sum128(U128 v, U128 *s_red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = add128(v, shfl_down128(v, o));
+    if (lane == 0) s_red[warp] = v;
+    __syncthreads();
+    U128 r{0ull, 0ull};
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kWarps; ++w) r = add128(r, s_red[w]);
+    __syncthreads();
+    return r;
+}
+
+// Decoupled lookback over the tracker's earlier tiles, kThreads tiles per round (thread
+// i inspects tile base - i).  Sums the fixed-point aggregates back to the nearest tile
+// that has published its inclusive prefix.  Whole block; result valid in thread 0.
+template <int P>
+__device__ U128 lookback(const LookbackDesc *look, int lt, uint32_t ep, TrackerState *st, StepSmem<P> &sm) {
+    const int tid = threadIdx.x;
+    U128 total{0ull, 0ull};
+    for (int base = lt - 1; base >= 0; base -= kThreads) {
+        const int idx = base - tid;
+        uint32_t f = 0u;
+        U128 v{0ull, 0ull};
         if (idx >= 0) {
             f = wait_flag(&look[idx], ep, st);
-            if (f == 0u) f = 2u;   // timed out: treat as an inclusive zero (result invalid, flagged)
-            else val = static_cast<A>(ld_relaxed_f64((f & 3u) == 2u ? &look[idx].incl : &look[idx].agg));
+            if (f == 0u) f = 2u;   // timed out: an inclusive zero (the step is flagged invalid)
+            else v = ld_relaxed_u128((f & 3u) == 2u ? &look[idx].incl_lo : &look[idx].agg_lo);
         }
-        stack[w * 32 + lane] = val;
-        const unsigned incl = __ballot_sync(0xffffffffu, idx >= 0 && (f & 3u) == 2u);
-        __syncwarp();
-        if (incl) {
-            const int q = __ffs(incl) - 1;   // nearest tile with its inclusive prefix
-            A acc = static_cast<A>(0);
-            if (lane == 0) {
-                acc = stack[w * 32 + q];
-                for (int l = q - 1; l >= 0; --l) acc = add_rn(acc, stack[w * 32 + l]);
-                for (int ww = w - 1; ww >= 0; --ww)
-                    for (int l = 31; l >= 0; --l) acc = add_rn(acc, stack[ww * 32 + l]);
-            }
-            return __shfl_sync(0xffffffffu, acc, 0);
-        }
+        if (tid == 0) sm.qmin = kThreads;
+        __syncthreads();
+        if (idx >= 0 && (f & 3u) == 2u) atomicMin(&sm.qmin, tid);
+        __syncthreads();
+        const int q = sm.qmin;      // nearest inclusive predecessor, kThreads if none here
+        if (idx < 0 || tid > q) v = U128{0ull, 0ull};
+        total = add128(total, block_sum128(v, sm.red128));
+        if (q < kThreads) break;
     }
-    // Far lookback: the immediate predecessor's inclusive prefix is the chain sum itself.
-    A acc = static_cast<A>(0);
-    if (lane == 0) {
-        uint32_t ns = 32;
-        uint32_t it = 0;
-        for (; it < kSpinLimit; ++it) {
-            const uint32_t f = ld_acquire_u32(&look[lt - 1].flag);
-            if (flag_ready(f, ep) && (f & 3u) == 2u) {
-                acc = static_cast<A>(ld_relaxed_f64(&look[lt - 1].incl));
-                break;
-            }
-            if ((it & 1023u) == 1023u && timed_out(st)) break;
-            __nanosleep(ns);
-            if (ns < 512) ns <<= 1;
-        }
-        if (it >= kSpinLimit) atomicOr(&st->status, kStatusTimeout);
-    }
-    return __shfl_sync(0xffffffffu, acc, 0);
+    return total;
 }
 
 // First index e in [0, n) with J[e] > j (J non-decreasing, J[n-1] > j).
@@ -434,26 +426,36 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
         __syncthreads();
         const acc_t agg = sm.agg;
         LookbackDesc *look = T.look;
+        const U128 aggx = to_fixed(static_cast<double>(agg));
+        const uint32_t tag = (ep & 0x3fffffffu) << 2;
         if (tid == 0) {
             if (lt == 0) {
-                look[0].incl = static_cast<double>(agg);
-                st_release_u32(&look[0].flag, ((ep & 0x3fffffffu) << 2) | 2u);
-                sm.excl = static_cast<acc_t>(0);
+                look[0].incl_lo = aggx.lo;
+                look[0].incl_hi = aggx.hi;
+                st_release_u32(&look[0].flag, tag | 2u);
             } else {
-                look[lt].agg = static_cast<double>(agg);
-                st_release_u32(&look[lt].flag, ((ep & 0x3fffffffu) << 2) | 1u);
+                look[lt].agg_lo = aggx.lo;
+                look[lt].agg_hi = aggx.hi;
+                st_release_u32(&look[lt].flag, tag | 1u);
             }
         }
-        if (lt > 0 && warp == 0) {
-            const acc_t ex = lookback_chain<acc_t>(look, lt, ep, sm.stack, st);
-            if (lane == 0) {
-                sm.excl = ex;
-                look[lt].incl = static_cast<double>(add_rn(ex, agg));
-                st_release_u32(&look[lt].flag, ((ep & 0x3fffffffu) << 2) | 2u);
+        U128 exclx{0ull, 0ull};
+        if (lt > 0) exclx = lookback<P>(look, lt, ep, st, sm);
+        if (tid == 0) {
+            const U128 endx = add128(exclx, aggx);
+            if (lt > 0) {
+                look[lt].incl_lo = endx.lo;
+                look[lt].incl_hi = endx.hi;
+                st_release_u32(&look[lt].flag, tag | 2u);
             }
+            sm.excl_x = exclx;
+            sm.end_x = endx;
         }
         __syncthreads();
-        const acc_t excl = sm.excl;
+        // Prefix of the tile's elements: FP inside the tile, pinned to the exact fixed-point
+        // values at both tile boundaries, so neighbouring tiles see the same boundary.
+        const acc_t excl = static_cast<acc_t>(from_fixed(sm.excl_x));
+        const acc_t pend = static_cast<acc_t>(from_fixed(sm.end_x));
         // CDF and strata counts
         acc_t u0;
         {
@@ -467,7 +469,8 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
             const int e = tid * kItems + m;
             if (e < cnt) {
                 const int64_t k = k0 + e;
-                acc_t C = mul_rn(add_rn(excl, loc[m]), invS);
+                const acc_t P = (e == cnt - 1) ? pend : fmin(add_rn(excl, loc[m]), pend);
+                acc_t C = mul_rn(P, invS);
                 int64_t J;
                 if (k == N - 1) { C = static_cast<acc_t>(1); J = N; }
                 else J = count_le<acc_t>(C, u0, inv_n, N);

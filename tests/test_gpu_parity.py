@@ -193,7 +193,7 @@ def test_teacher_forced_step_wide_cloud_many_tiles(pf, prec):
     assert np.all(np.diff(C) >= 0) and C[-1] == 1.0
     a_o = oracle.resample(C, oracle.resample_u0(9, 1), "f64" if prec == "ref64" else "f32")
     assert np.array_equal(anc, a_o)
-    assert len(np.unique(anc)) > 1000
+    assert len(np.unique(anc // TILE)) >= 10     # ancestors spread over many tiles
 
 
 @pytest.mark.parametrize("prec", ["ref64", "f32"])
