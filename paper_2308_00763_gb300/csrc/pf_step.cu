@@ -10,21 +10,29 @@
 //      contiguous range of j, and their ancestors all lie in the tile, so the gather of
 //      ancestor positions is a read of the tile's own particles staged in shared memory.
 //   2. propagation (Eq. 1-2) of every offspring j with Philox draws keyed (j, t),
-//   3. likelihood (Eq. 3; Eq. 4 scaled half form in F16/BF16) on the new frame,
+//   3. likelihood (Eq. 3; Eq. 4 scaled half form in F16/BF16) on the new frame.  The
+//      likelihood is a function of the particle's pixel only, so each tile first tabulates
+//      it in shared memory over the window its offspring can reach (the ancestors'
+//      bounding box widened by the largest draw the 23-bit Box-Muller can produce) and
+//      each offspring reads its pixel's value; a pixel outside the window is evaluated
+//      directly by the same function, so the two routes give identical bits.
 //   4. per-tile (max L, sum e, sum e*dx, sum e*dy), merged with rescaling,
 //   5. the tile that completes a tracker merges its tiles' partials in index order:
-//      M, S, 1/S and the estimate of the frame (the weighted mean, Sec. 4 Fig. 4).
+//      M, S, 1/S and the estimate of the frame (the weighted mean of the propagated
+//      particles).
 // Frame t = 0 has no resampling: every particle starts at the initial position.
 //
-// The scan is made order-independent so that neighbouring tiles agree bit for bit on
-// their common boundary: a tile's exclusive prefix is the left-to-right chain sum of the
-// earlier tiles' aggregates (the lookback folds the aggregates it collects in that
-// order), and within a tile the prefix is made non-decreasing by a running max.  Hence
-// C is non-decreasing, the strata ranges of consecutive tiles meet exactly, and every j
-// is written by exactly one tile.
+// Scan boundaries.  The prefix between tiles is an exact 128-bit fixed-point sum of
+// the tiles' aggregates, so every tile obtains the same boundary value whichever
+// predecessors its lookback visits.  Inside a tile the prefix is an FP scan made
+// non-decreasing by a running max and clamped to the exact value at the tile's end.
+// Hence C is non-decreasing, the strata ranges of consecutive tiles meet exactly, and
+// every j is written by exactly one tile.
 #include <cuda_runtime.h>
 #include <float.h>
 #include <math.h>
+
+#include <type_traits>
 
 #include "pf_device.cuh"
 #include "pf_internal.h"
@@ -34,18 +42,21 @@ namespace pfk {
 namespace {
 
 constexpr int kWarps = kThreads / 32;
+constexpr int kTableMax = 4096;            // cells of the per-tile likelihood table
 constexpr uint32_t kSpinLimit = 1u << 22;  // bounded waits: ~1 s with backoff
+// Largest |N(0,1)| draw: sqrt(-2 ln 2^-24) = 5.7684 for the smallest 23-bit uniform.
+constexpr float kMaxNormal = 5.77f;
 
 __device__ __forceinline__ bool flag_ready(uint32_t f, uint32_t ep) {
     return (f >> 2) == (ep & 0x3fffffffu) && (f & 3u) != 0u;
 }
 
-// Wait (bounded) until the lookback descriptor of a tile carries this epoch.  Returns the
-// flag, or 0 on timeout (and raises the tracker's timeout bit).
 __device__ __forceinline__ bool timed_out(const TrackerState *st) {
     return (ld_acquire_u32(&st->status) & kStatusTimeout) != 0u;
 }
 
+// Wait (bounded) until the lookback descriptor of a tile carries this epoch.  Returns the
+// flag, or 0 on timeout (and raises the tracker's timeout bit).
 __device__ uint32_t wait_flag(const LookbackDesc *d, uint32_t ep, TrackerState *st) {
     uint32_t ns = 8;
     for (uint32_t it = 0; it < kSpinLimit; ++it) {
@@ -59,6 +70,15 @@ __device__ uint32_t wait_flag(const LookbackDesc *d, uint32_t ep, TrackerState *
     return 0u;
 }
 
+// exp(d) for d <= 0 with the two exact shortcuts: exp(0) = 1, and 0 below the point
+// where the precision underflows to zero anyway.
+__device__ __forceinline__ double exp_le0(double d) {
+    return d == 0.0 ? 1.0 : (d < -746.0 ? 0.0 : exp(d));
+}
+__device__ __forceinline__ float exp_le0(float d) {
+    return d == 0.0f ? 1.0f : (d < -104.0f ? 0.0f : expf(d));
+}
+
 template <typename A>
 struct Stats {
     A m, s, sx, sy;
@@ -69,13 +89,13 @@ __device__ __forceinline__ void stats_merge(Stats<A> &a, const Stats<A> &b) {
     if (b.m == neg_inf<A>()) return;
     if (a.m == neg_inf<A>()) { a = b; return; }
     if (b.m > a.m) {
-        const A sc = exp_acc(a.m - b.m);
+        const A sc = exp_le0(a.m - b.m);
         a.s = a.s * sc + b.s;
         a.sx = a.sx * sc + b.sx;
         a.sy = a.sy * sc + b.sy;
         a.m = b.m;
     } else {
-        const A sc = exp_acc(b.m - a.m);
+        const A sc = exp_le0(b.m - a.m);
         a.s += b.s * sc;
         a.sx += b.sx * sc;
         a.sy += b.sy * sc;
@@ -85,14 +105,16 @@ __device__ __forceinline__ void stats_merge(Stats<A> &a, const Stats<A> &b) {
 template <typename A>
 __device__ __forceinline__ void stats_add(Stats<A> &a, A L, A dx, A dy) {
     if (L > a.m) {
-        const A sc = exp_acc(a.m - L);   // exp(-inf) = 0 on the first element
+        const A sc = (a.m == neg_inf<A>()) ? static_cast<A>(0) : exp_le0(a.m - L);
         a.s *= sc; a.sx *= sc; a.sy *= sc;
         a.m = L;
     }
-    const A e = exp_acc(L - a.m);
-    a.s += e;
-    a.sx += e * dx;
-    a.sy += e * dy;
+    const A e = exp_le0(L - a.m);
+    if (e != static_cast<A>(0)) {
+        a.s += e;
+        a.sx += e * dx;
+        a.sy += e * dy;
+    }
 }
 
 template <typename A>
@@ -103,26 +125,6 @@ __device__ __forceinline__ Stats<A> stats_shfl_xor(const Stats<A> &a, int o) {
     b.sx = __shfl_xor_sync(0xffffffffu, a.sx, o);
     b.sy = __shfl_xor_sync(0xffffffffu, a.sy, o);
     return b;
-}
-
-// Block-wide merge of per-thread stats in a fixed order; result valid in thread 0.
-template <typename A>
-__device__ Stats<A> block_stats(Stats<A> v, Stats<A> *s_red) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        Stats<A> w = stats_shfl_xor(v, o);
-        if ((lane & o) == 0) stats_merge(v, w); else { stats_merge(w, v); v = w; }
-    }
-    if (lane == 0) s_red[warp] = v;
-    __syncthreads();
-    Stats<A> r;
-    if (threadIdx.x == 0) {
-        r = s_red[0];
-        for (int w = 1; w < kWarps; ++w) stats_merge(r, s_red[w]);
-    }
-    __syncthreads();
-    return r;
 }
 
 // Pixel of a position (reading C3): floor(v) + (v - floor(v) >= 0.5), clamped into a
@@ -136,31 +138,42 @@ __device__ __forceinline__ int pixel_of(A v) {
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
-// Integer sum of the template pixels around (px, py) (exact form of Eq. 3; reading C4
-// clamps template pixels to the frame).
-__device__ __forceinline__ uint32_t disk_sum(const uint8_t *__restrict__ frame, int64_t pitch, int W,
-                                             int H, int r, const int8_t *s_w, int px, int py) {
+struct FrameView {
+    const uint8_t *p;
+    int64_t pitch;
+    int W, H, r;
+};
+
+// Integer sum of the template pixels around (px, py) (the exact form of Eq. 3; reading
+// C4 clamps template pixels to the frame).  w[i] = half-width of template row dy = i - r.
+__device__ __forceinline__ uint32_t disk_sum(const FrameView &f, const int8_t *w, int px, int py) {
     uint32_t s = 0;
-    if (px - r >= 0 && px + r < W && py - r >= 0 && py + r < H) {
-        const uint8_t *row = frame + static_cast<int64_t>(py - r) * pitch + px;
-        for (int dy = 0; dy <= 2 * r; ++dy, row += pitch) {
-            const int w = s_w[dy];
-            for (int dx = -w; dx <= w; ++dx) s += __ldg(row + dx);
+    const int r = f.r;
+    if (px - r >= 0 && px + r < f.W && py - r >= 0 && py + r < f.H) {
+        const uint8_t *row = f.p + static_cast<int64_t>(py - r) * f.pitch + px;
+        for (int i = 0; i <= 2 * r; ++i, row += f.pitch) {
+            const int hw = w[i];
+            for (int dx = -hw; dx <= hw; ++dx) s += __ldg(row + dx);
         }
     } else {
         for (int dy = -r; dy <= r; ++dy) {
-            const int w = s_w[dy + r];
-            const uint8_t *row = frame + static_cast<int64_t>(clampi(py + dy, 0, H - 1)) * pitch;
-            for (int dx = -w; dx <= w; ++dx) s += __ldg(row + clampi(px + dx, 0, W - 1));
+            const int hw = w[dy + r];
+            const uint8_t *row = f.p + static_cast<int64_t>(clampi(py + dy, 0, f.H - 1)) * f.pitch;
+            for (int dx = -hw; dx <= hw; ++dx) s += __ldg(row + clampi(px + dx, 0, f.W - 1));
         }
     }
     return s;
 }
 
-// Eq. 4 per-pixel scaled form on two particles at once (half2 lanes), accumulated in
-// the lane type (F16, the paper's form) or in FP32 (BF16 and PF_FLAG_ACCUM32).
-template <typename H2>
-struct HalfLik;
+// Eq. 3 from the integer disk sum: sum (I-bg)^2 - (I-fg)^2 = (fg-bg)(2 sum I - (bg+fg)|D|).
+template <typename A>
+__device__ __forceinline__ A lik_from_sum(uint32_t s, A c1, A c2D, A den) {
+    return (c1 * (static_cast<A>(2) * static_cast<A>(s) - c2D)) / den;
+}
+
+// Eq. 4 per-pixel scaled form on two pixels at once (half2 lanes), accumulated in the
+// lane type (F16, the paper's form) or in FP32 (BF16 and PF_FLAG_ACCUM32).
+template <typename H2> struct HalfLik;
 
 template <>
 struct HalfLik<__half2> {
@@ -170,11 +183,7 @@ struct HalfLik<__half2> {
         const uint32_t bits = (0x6400u | i0) | ((0x6400u | i1) << 16);
         return *reinterpret_cast<const __half2 *>(&bits);
     }
-    __device__ static __forceinline__ __half2 term(__half2 h, __half2 bgo, __half2 fgo, __half2 kap) {
-        const __half2 a = __hmul2(__hsub2(h, bgo), kap);
-        const __half2 b = __hmul2(__hsub2(h, fgo), kap);
-        return __hfma2(a, a, __hneg2(__hmul2(b, b)));
-    }
+    __device__ static __forceinline__ float level_offset() { return 1024.0f; }
 };
 
 template <>
@@ -182,22 +191,14 @@ struct HalfLik<__nv_bfloat162> {
     __device__ static __forceinline__ __nv_bfloat162 pix(uint32_t i0, uint32_t i1) {
         return __floats2bfloat162_rn(static_cast<float>(i0), static_cast<float>(i1));
     }
-    __device__ static __forceinline__ __nv_bfloat162 term(__nv_bfloat162 h, __nv_bfloat162 bgo,
-                                                          __nv_bfloat162 fgo, __nv_bfloat162 kap) {
-        const __nv_bfloat162 a = __hmul2(__hsub2(h, bgo), kap);
-        const __nv_bfloat162 b = __hmul2(__hsub2(h, fgo), kap);
-        return __hfma2(a, a, __hneg2(__hmul2(b, b)));
-    }
+    __device__ static __forceinline__ float level_offset() { return 0.0f; }
 };
-
-template <typename T> struct Vec2;
-template <> struct Vec2<__half> { using type = __half2; };
-template <> struct Vec2<__nv_bfloat16> { using type = __nv_bfloat162; };
 
 __device__ __forceinline__ __half2 make2(__half a, __half b) { return __halves2half2(a, b); }
 __device__ __forceinline__ __nv_bfloat162 make2(__nv_bfloat16 a, __nv_bfloat16 b) { return __halves2bfloat162(a, b); }
-__device__ __forceinline__ __half2 f2_to2(float a, float b, __half2 *) { return __floats2half2_rn(a, b); }
-__device__ __forceinline__ __nv_bfloat162 f2_to2(float a, float b, __nv_bfloat162 *) { return __floats2bfloat162_rn(a, b); }
+template <typename H2> __device__ __forceinline__ H2 f2_to2(float a, float b);
+template <> __device__ __forceinline__ __half2 f2_to2<__half2>(float a, float b) { return __floats2half2_rn(a, b); }
+template <> __device__ __forceinline__ __nv_bfloat162 f2_to2<__nv_bfloat162>(float a, float b) { return __floats2bfloat162_rn(a, b); }
 __device__ __forceinline__ float lo_f(__half2 v) { return __low2float(v); }
 __device__ __forceinline__ float hi_f(__half2 v) { return __high2float(v); }
 __device__ __forceinline__ float lo_f(__nv_bfloat162 v) { return __low2float(v); }
@@ -207,37 +208,96 @@ __device__ __forceinline__ __half hi_h(__half2 v) { return __high2half(v); }
 __device__ __forceinline__ __nv_bfloat16 lo_h(__nv_bfloat162 v) { return __low2bfloat16(v); }
 __device__ __forceinline__ __nv_bfloat16 hi_h(__nv_bfloat162 v) { return __high2bfloat16(v); }
 
-// Shared memory of the step kernel.
+template <typename H2>
+struct HalfConsts {
+    H2 kap, bgo, fgo;
+    bool half_acc;
+};
+
+// Likelihood of two pixels (px0,py0), (px1,py1) in the half form: per template pixel
+// a = (I - bg) kappa, b = (I - fg) kappa, term = a*a - b*b (Eq. 4), summed row by row.
+template <typename H2>
+__device__ H2 lik_half_pair(const FrameView &f, const int8_t *w, int px0, int py0, int px1, int py1,
+                            const HalfConsts<H2> &k) {
+    const int r = f.r;
+    const bool inside = px0 - r >= 0 && px0 + r < f.W && py0 - r >= 0 && py0 + r < f.H &&
+                        px1 - r >= 0 && px1 + r < f.W && py1 - r >= 0 && py1 + r < f.H;
+    H2 hacc = f2_to2<H2>(0.0f, 0.0f);
+    float a0 = 0.0f, a1 = 0.0f;
+    for (int dy = -r; dy <= r; ++dy) {
+        const int hw = w[dy + r];
+        const uint8_t *row0 = f.p + static_cast<int64_t>(inside ? py0 + dy : clampi(py0 + dy, 0, f.H - 1)) * f.pitch;
+        const uint8_t *row1 = f.p + static_cast<int64_t>(inside ? py1 + dy : clampi(py1 + dy, 0, f.H - 1)) * f.pitch;
+        for (int dx = -hw; dx <= hw; ++dx) {
+            const uint32_t i0 = __ldg(row0 + (inside ? px0 + dx : clampi(px0 + dx, 0, f.W - 1)));
+            const uint32_t i1 = __ldg(row1 + (inside ? px1 + dx : clampi(px1 + dx, 0, f.W - 1)));
+            const H2 h = HalfLik<H2>::pix(i0, i1);
+            const H2 a = __hmul2(__hsub2(h, k.bgo), k.kap);
+            const H2 b = __hmul2(__hsub2(h, k.fgo), k.kap);
+            const H2 term = __hfma2(a, a, __hneg2(__hmul2(b, b)));
+            if (k.half_acc) hacc = __hadd2(hacc, term);
+            else { a0 += lo_f(term); a1 += hi_f(term); }
+        }
+    }
+    return k.half_acc ? hacc : f2_to2<H2>(a0, a1);
+}
+
+// Shared memory of the step kernel (dynamic: sizeof(StepSmem<P>) bytes).
 template <int P>
 struct __align__(16) StepSmem {
     using pos_t = typename Prec<P>::pos_t;
+    using lik_t = typename Prec<P>::lik_t;
     using acc_t = typename Prec<P>::acc_t;
     pos_t ax[kTile];          // ancestor positions of the tile (previous frame)
     pos_t ay[kTile];
-    int32_t J[kTile];         // J[e] = number of strata assigned to particles k0..k0+e
+    int32_t J[kTile];         // J[e] = strata assigned to particles k0..k0+e (cumulative)
+    lik_t table[kTableMax];   // likelihood of each pixel of the tile's window
     acc_t warp_sum[kWarps];
     acc_t warp_max[kWarps];
+    float box[kWarps][4];
     U128 red128[kWarps];
     Stats<acc_t> red[kWarps];
     acc_t agg;
     U128 excl_x, end_x;       // exact fixed-point prefix before / after the tile
-    int qmin;
     int64_t jbeg, jend;
+    int win_x0, win_y0, win_w, win_h;   // likelihood table window (win_w = 0: none)
+    int qmin;
     int8_t w[2 * kMaxRadius + 1];
     uint32_t ticket;
     uint32_t last;
 };
 
+// Block-wide merge of per-thread stats in a fixed order; result valid in thread 0.
+template <int P, typename A>
+__device__ Stats<A> block_stats(Stats<A> v, StepSmem<P> &sm) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        Stats<A> w = stats_shfl_xor(v, o);
+        if ((lane & o) == 0) stats_merge(v, w); else { stats_merge(w, v); v = w; }
+    }
+    if (lane == 0) sm.red[warp] = v;
+    __syncthreads();
+    Stats<A> r;
+    if (threadIdx.x == 0) {
+        r = sm.red[0];
+        for (int w = 1; w < kWarps; ++w) stats_merge(r, sm.red[w]);
+    }
+    __syncthreads();
+    return r;
+}
+
 // Block-wide sum of a 128-bit value (exact, so the order is irrelevant); valid in thread 0.
-__device__ U128 block_sum128(U128 v, U128 *s_red) {
+template <int P>
+__device__ U128 block_sum128(U128 v, StepSmem<P> &sm) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = add128(v, shfl_down128(v, o));
-    if (lane == 0) s_red[warp] = v;
+    if (lane == 0) sm.red128[warp] = v;
     __syncthreads();
     U128 r{0ull, 0ull};
     if (threadIdx.x == 0)
-        for (int w = 0; w < kWarps; ++w) r = add128(r, s_red[w]);
+        for (int w = 0; w < kWarps; ++w) r = add128(r, sm.red128[w]);
     __syncthreads();
     return r;
 }
@@ -264,7 +324,7 @@ __device__ U128 lookback(const LookbackDesc *look, int lt, uint32_t ep, TrackerS
         __syncthreads();
         const int q = sm.qmin;      // nearest inclusive predecessor, kThreads if none here
         if (idx < 0 || tid > q) v = U128{0ull, 0ull};
-        total = add128(total, block_sum128(v, sm.red128));
+        total = add128(total, block_sum128<P>(v, sm));
         if (q < kThreads) break;
     }
     return total;
@@ -294,7 +354,7 @@ __device__ void finalize_tracker(const TrackerDev &T, TrackerState *st, StepSmem
         w.sy = static_cast<acc_t>(__ldcg(p + 3));
         stats_merge(v, w);
     }
-    const Stats<acc_t> r = block_stats(v, sm.red);
+    const Stats<acc_t> r = block_stats<P>(v, sm);
     if (threadIdx.x == 0) {
         const int64_t t = st->t;
         const double M = static_cast<double>(r.m);
@@ -345,11 +405,11 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
     const uint32_t ep = __ldcg(&st->epoch);
     const int in = static_cast<int>((t + 1) & 1), out = static_cast<int>(t & 1);
 
-    const int W = T.W, H = T.H, r = T.r;
-    const uint8_t *frame;
-    int64_t pitch;
-    if (Lp.frame_override) { frame = Lp.frame_override; pitch = Lp.pitch_override; }
-    else { frame = fr.base + (fr.stride ? t * fr.stride : 0); pitch = fr.pitch; }
+    FrameView fv;
+    fv.W = T.W; fv.H = T.H; fv.r = T.r;
+    if (Lp.frame_override) { fv.p = Lp.frame_override; fv.pitch = Lp.pitch_override; }
+    else { fv.p = fr.base + (fr.stride ? t * fr.stride : 0); fv.pitch = fr.pitch; }
+    const int r = fv.r;
     for (int i = tid; i <= 2 * r; i += kThreads) {
         const int dy = i - r;
         int w = 0;
@@ -357,8 +417,10 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
         sm.w[i] = static_cast<int8_t>(w);
     }
 
-    // Anchor the offspring are written against (F16/BF16 offsets; estimate sums).
+    // Anchor the offspring are written against (F16/BF16 offsets; estimate sums), and the
+    // anchor of the stored ancestors.
     const double nxa = __ldcg(&st->nx), nya = __ldcg(&st->ny);
+    const double axa = __ldcg(&st->ax), aya = __ldcg(&st->ay);
 
     // ------------------------------------------------------------ 1. resampling
     if (t > 0) {
@@ -378,7 +440,7 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
         for (int m = 0; m < kItems; ++m) {
             const int e = tid * kItems + m;
             acc_t v = static_cast<acc_t>(0);
-            if (e < cnt) v = exp_acc(to_acc(Lin[k0 + e]) - M);
+            if (e < cnt) v = exp_le0(to_acc(Lin[k0 + e]) - M);
             run = (m == 0) ? v : run + v;
             s[m] = run;
         }
@@ -456,7 +518,6 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
         // values at both tile boundaries, so neighbouring tiles see the same boundary.
         const acc_t excl = static_cast<acc_t>(from_fixed(sm.excl_x));
         const acc_t pend = static_cast<acc_t>(from_fixed(sm.end_x));
-        // CDF and strata counts
         acc_t u0;
         {
             const uint4 w = philox4x32_10(make_uint4(0u, static_cast<uint32_t>(t - 1), 1u, T.tracker_id),
@@ -469,8 +530,8 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
             const int e = tid * kItems + m;
             if (e < cnt) {
                 const int64_t k = k0 + e;
-                const acc_t P = (e == cnt - 1) ? pend : fmin(add_rn(excl, loc[m]), pend);
-                acc_t C = mul_rn(P, invS);
+                const acc_t Pk = (e == cnt - 1) ? pend : fmin(add_rn(excl, loc[m]), pend);
+                acc_t C = mul_rn(Pk, invS);
                 int64_t J;
                 if (k == N - 1) { C = static_cast<acc_t>(1); J = N; }
                 else J = count_le<acc_t>(C, u0, inv_n, N);
@@ -478,9 +539,7 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
                 if (T.dbg_cdf) static_cast<acc_t *>(T.dbg_cdf)[k] = C;
             }
         }
-        if (tid == 0) {
-            sm.jbeg = (lt == 0) ? 0 : count_le<acc_t>(mul_rn(excl, invS), u0, inv_n, N);
-        }
+        if (tid == 0) sm.jbeg = (lt == 0) ? 0 : count_le<acc_t>(mul_rn(excl, invS), u0, inv_n, N);
         __syncthreads();
         if (tid == 0) sm.jend = sm.J[cnt - 1];
         __syncthreads();
@@ -488,9 +547,96 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
         if (tid == 0) { sm.jbeg = k0; sm.jend = k0 + cnt; }
         __syncthreads();
     }
+    const int64_t jbeg = sm.jbeg, jend = sm.jend;
+
+    // ------------------------------------------------------------ likelihood window
+    // Bounding box of the ancestors that have offspring (absolute pixel units), widened by
+    // the drift and the largest draw; the offspring's pixels fall inside it.
+    {
+        float bx0 = FLT_MAX, bx1 = -FLT_MAX, by0 = FLT_MAX, by1 = -FLT_MAX;
+        if (t > 0) {
+            const float sx = Tr::kHalf ? static_cast<float>(axa) : 0.0f;
+            const float sy = Tr::kHalf ? static_cast<float>(aya) : 0.0f;
+#pragma unroll
+            for (int m = 0; m < kItems; ++m) {
+                const int e = tid * kItems + m;
+                if (e < cnt) {
+                    const int64_t jp = e ? static_cast<int64_t>(sm.J[e - 1]) : jbeg;
+                    if (static_cast<int64_t>(sm.J[e]) > jp) {
+                        const float xv = static_cast<float>(to_acc(sm.ax[e])) + sx;
+                        const float yv = static_cast<float>(to_acc(sm.ay[e])) + sy;
+                        bx0 = fminf(bx0, xv); bx1 = fmaxf(bx1, xv);
+                        by0 = fminf(by0, yv); by1 = fmaxf(by1, yv);
+                    }
+                }
+            }
+        } else {
+            bx0 = bx1 = static_cast<float>(T.init_x);
+            by0 = by1 = static_cast<float>(T.init_y);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            bx0 = fminf(bx0, __shfl_xor_sync(0xffffffffu, bx0, o));
+            bx1 = fmaxf(bx1, __shfl_xor_sync(0xffffffffu, bx1, o));
+            by0 = fminf(by0, __shfl_xor_sync(0xffffffffu, by0, o));
+            by1 = fmaxf(by1, __shfl_xor_sync(0xffffffffu, by1, o));
+        }
+        if (lane == 0) { sm.box[warp][0] = bx0; sm.box[warp][1] = bx1; sm.box[warp][2] = by0; sm.box[warp][3] = by1; }
+        __syncthreads();
+        if (tid == 0) {
+            for (int w = 1; w < kWarps; ++w) {
+                bx0 = fminf(bx0, sm.box[w][0]); bx1 = fmaxf(bx1, sm.box[w][1]);
+                by0 = fminf(by0, sm.box[w][2]); by1 = fmaxf(by1, sm.box[w][3]);
+            }
+            const float mxr = fabsf(static_cast<float>(T.drift_x)) + kMaxNormal * static_cast<float>(T.sigma_x) + 1.0f;
+            const float myr = fabsf(static_cast<float>(T.drift_y)) + kMaxNormal * static_cast<float>(T.sigma_y) + 1.0f;
+            int ww = 0, wh = 0, x0 = 0, y0 = 0;
+            if (bx0 <= bx1 && by0 <= by1 && bx1 - bx0 < 4096.0f && by1 - by0 < 4096.0f &&
+                fabsf(bx0) < 1.0e8f && fabsf(by0) < 1.0e8f && mxr < 4096.0f && myr < 4096.0f) {
+                x0 = static_cast<int>(floorf(bx0 - mxr));
+                y0 = static_cast<int>(floorf(by0 - myr));
+                ww = static_cast<int>(ceilf(bx1 + mxr)) - x0 + 1;
+                wh = static_cast<int>(ceilf(by1 + myr)) - y0 + 1;
+                const int64_t cells = static_cast<int64_t>(ww) * wh;
+                if (cells > kTableMax || cells > (jend - jbeg)) { ww = 0; wh = 0; }
+            }
+            sm.win_x0 = x0; sm.win_y0 = y0; sm.win_w = ww; sm.win_h = wh;
+        }
+        __syncthreads();
+    }
+    const int wx0 = sm.win_x0, wy0 = sm.win_y0, ww = sm.win_w, wh = sm.win_h;
+    const int cells = ww * wh;
+
+    // likelihood constants
+    const acc_t c1 = static_cast<acc_t>(T.c1), c2D = static_cast<acc_t>(T.c2 * T.D);
+    const acc_t den = static_cast<acc_t>(T.den);
+    using h2 = typename std::conditional<std::is_same<pos_t, __nv_bfloat16>::value, __nv_bfloat162, __half2>::type;
+    HalfConsts<h2> hk;
+    if constexpr (Tr::kHalf) {
+        const float lo = HalfLik<h2>::level_offset();
+        hk.kap = f2_to2<h2>(T.kappa, T.kappa);
+        hk.bgo = f2_to2<h2>(lo + T.bg_f, lo + T.bg_f);
+        hk.fgo = f2_to2<h2>(lo + T.fg_f, lo + T.fg_f);
+        hk.half_acc = std::is_same<pos_t, __half>::value && !(T.flags & 0x2u);
+    }
+
+    // tabulate the window (two pixels per thread step: the half form works on pairs)
+    for (int c = 2 * tid; c < cells; c += 2 * kThreads) {
+        const int c1i = (c + 1 < cells) ? c + 1 : c;
+        const int px0 = wx0 + c % ww, py0 = wy0 + c / ww;
+        const int px1 = wx0 + c1i % ww, py1 = wy0 + c1i / ww;
+        if constexpr (Tr::kHalf) {
+            const h2 L2 = lik_half_pair<h2>(fv, sm.w, px0, py0, px1, py1, hk);
+            sm.table[c] = lo_h(L2);
+            if (c + 1 < cells) sm.table[c + 1] = hi_h(L2);
+        } else {
+            sm.table[c] = lik_from_sum<acc_t>(disk_sum(fv, sm.w, px0, py0), c1, c2D, den);
+            if (c + 1 < cells) sm.table[c + 1] = lik_from_sum<acc_t>(disk_sum(fv, sm.w, px1, py1), c1, c2D, den);
+        }
+    }
+    __syncthreads();
 
     // ------------------------------------------------------------ 2-4. offspring
-    const int64_t jbeg = sm.jbeg, jend = sm.jend;
     pos_t *Xout = static_cast<pos_t *>(T.px[out]);
     pos_t *Yout = static_cast<pos_t *>(T.py[out]);
     lik_t *Lout = static_cast<lik_t *>(T.pl[out]);
@@ -498,7 +644,7 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
     Stats<acc_t> stats{neg_inf<acc_t>(), 0, 0, 0};
 
     // ancestor shift for offsets (previous anchor minus the current one)
-    const double shx = __ldcg(&st->ax) - nxa, shy = __ldcg(&st->ay) - nya;
+    const double shx = axa - nxa, shy = aya - nya;
 
     for (int64_t q = (jbeg >> 1) + tid; q < ((jend + 1) >> 1); q += kThreads) {
         const int64_t j0 = 2 * q, j1 = j0 + 1;
@@ -527,17 +673,12 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
                 ya0 = ya1 = static_cast<acc_t>(T.init_y);
             }
             acc_t n0x, n0y, n1x, n1y;
-            if (sizeof(acc_t) == 8) {
-                double a, b, c, d;
-                box_muller(uniform_f64(w0.x), uniform_f64(w0.y), a, b);
-                box_muller(uniform_f64(w1.x), uniform_f64(w1.y), c, d);
-                n0x = static_cast<acc_t>(a); n0y = static_cast<acc_t>(b);
-                n1x = static_cast<acc_t>(c); n1y = static_cast<acc_t>(d);
+            if constexpr (sizeof(acc_t) == 8) {
+                box_muller(uniform_f64(w0.x), uniform_f64(w0.y), n0x, n0y);
+                box_muller(uniform_f64(w1.x), uniform_f64(w1.y), n1x, n1y);
             } else {
-                float a, b, c, d;
-                box_muller(uniform_f32(w0.x), uniform_f32(w0.y), a, b);
-                box_muller(uniform_f32(w1.x), uniform_f32(w1.y), c, d);
-                n0x = a; n0y = b; n1x = c; n1y = d;
+                box_muller(uniform_f32(w0.x), uniform_f32(w0.y), n0x, n0y);
+                box_muller(uniform_f32(w1.x), uniform_f32(w1.y), n1x, n1y);
             }
             const acc_t dxm = static_cast<acc_t>(T.drift_x), dym = static_cast<acc_t>(T.drift_y);
             const acc_t sgx = static_cast<acc_t>(T.sigma_x), sgy = static_cast<acc_t>(T.sigma_y);
@@ -545,16 +686,17 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
             const acc_t y0 = add_rn(add_rn(ya0, dym), mul_rn(sgy, n0y));
             const acc_t x1 = add_rn(add_rn(xa1, dxm), mul_rn(sgx, n1x));
             const acc_t y1 = add_rn(add_rn(ya1, dym), mul_rn(sgy, n1y));
+            const int px0 = pixel_of(x0), py0 = pixel_of(y0), px1 = pixel_of(x1), py1 = pixel_of(y1);
+            const unsigned cx0 = static_cast<unsigned>(px0 - wx0), cy0 = static_cast<unsigned>(py0 - wy0);
+            const unsigned cx1 = static_cast<unsigned>(px1 - wx0), cy1 = static_cast<unsigned>(py1 - wy0);
             acc_t L0 = static_cast<acc_t>(0), L1 = static_cast<acc_t>(0);
-            const acc_t c1 = static_cast<acc_t>(T.c1), c2D = static_cast<acc_t>(T.c2 * T.D);
-            const acc_t den = static_cast<acc_t>(T.den);
             if (v0) {
-                const uint32_t s0 = disk_sum(frame, pitch, W, H, r, sm.w, pixel_of(x0), pixel_of(y0));
-                L0 = (c1 * (static_cast<acc_t>(2) * static_cast<acc_t>(s0) - c2D)) / den;
+                if (cx0 < static_cast<unsigned>(ww) && cy0 < static_cast<unsigned>(wh)) L0 = sm.table[cy0 * ww + cx0];
+                else L0 = lik_from_sum<acc_t>(disk_sum(fv, sm.w, px0, py0), c1, c2D, den);
             }
             if (v1) {
-                const uint32_t s1 = disk_sum(frame, pitch, W, H, r, sm.w, pixel_of(x1), pixel_of(y1));
-                L1 = (c1 * (static_cast<acc_t>(2) * static_cast<acc_t>(s1) - c2D)) / den;
+                if (cx1 < static_cast<unsigned>(ww) && cy1 < static_cast<unsigned>(wh)) L1 = sm.table[cy1 * ww + cx1];
+                else L1 = lik_from_sum<acc_t>(disk_sum(fv, sm.w, px1, py1), c1, c2D, den);
             }
             if (v0 && v1) {
                 if constexpr (sizeof(acc_t) == 8) {
@@ -574,71 +716,59 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
             if (v0) stats_add(stats, L0, x0 - static_cast<acc_t>(nxa), y0 - static_cast<acc_t>(nya));
             if (v1) stats_add(stats, L1, x1 - static_cast<acc_t>(nxa), y1 - static_cast<acc_t>(nya));
         } else {
-            // ---------------- F16 / BF16: half2 lanes = particles (j0, j1)
-            using h2 = typename Vec2<pos_t>::type;
+            // ---------------- F16 / BF16: half2 lanes = particles (j0, j1), offsets from the anchor
             h2 ox, oy;
             if (t > 0) {
                 ox = make2(sm.ax[e0], sm.ax[e1]);
                 oy = make2(sm.ay[e0], sm.ay[e1]);
                 const float sx = static_cast<float>(shx), sy = static_cast<float>(shy);
                 if (sx != 0.0f || sy != 0.0f) {
-                    ox = __hadd2(ox, f2_to2(sx, sx, (h2 *)nullptr));
-                    oy = __hadd2(oy, f2_to2(sy, sy, (h2 *)nullptr));
+                    ox = __hadd2(ox, f2_to2<h2>(sx, sx));
+                    oy = __hadd2(oy, f2_to2<h2>(sy, sy));
                 }
             } else {
                 const float ix = static_cast<float>(T.init_x - nxa), iy = static_cast<float>(T.init_y - nya);
-                ox = f2_to2(ix, ix, (h2 *)nullptr);
-                oy = f2_to2(iy, iy, (h2 *)nullptr);
+                ox = f2_to2<h2>(ix, ix);
+                oy = f2_to2<h2>(iy, iy);
             }
             float a, b, c, d;
             box_muller(uniform_f32(w0.x), uniform_f32(w0.y), a, b);
             box_muller(uniform_f32(w1.x), uniform_f32(w1.y), c, d);
             const float dxm = static_cast<float>(T.drift_x), dym = static_cast<float>(T.drift_y);
             const float sgx = static_cast<float>(T.sigma_x), sgy = static_cast<float>(T.sigma_y);
-            ox = __hadd2(ox, f2_to2(dxm + sgx * a, dxm + sgx * c, (h2 *)nullptr));
-            oy = __hadd2(oy, f2_to2(dym + sgy * b, dym + sgy * d, (h2 *)nullptr));
+            ox = __hadd2(ox, f2_to2<h2>(dxm + sgx * a, dxm + sgx * c));
+            oy = __hadd2(oy, f2_to2<h2>(dym + sgy * b, dym + sgy * d));
             const int axi = static_cast<int>(nxa), ayi = static_cast<int>(nya);
             const int px0 = axi + pixel_of(lo_f(ox)), py0 = ayi + pixel_of(lo_f(oy));
             const int px1 = axi + pixel_of(hi_f(ox)), py1 = ayi + pixel_of(hi_f(oy));
-            const h2 kap = f2_to2(T.kappa, T.kappa, (h2 *)nullptr);
-            const bool half_acc = std::is_same<pos_t, __half>::value && !(T.flags & 0x2u);
-            const float lvl_b = std::is_same<pos_t, __half>::value ? 1024.0f + T.bg_f : T.bg_f;
-            const float lvl_f = std::is_same<pos_t, __half>::value ? 1024.0f + T.fg_f : T.fg_f;
-            const h2 bgo = f2_to2(lvl_b, lvl_b, (h2 *)nullptr);
-            const h2 fgo = f2_to2(lvl_f, lvl_f, (h2 *)nullptr);
-            h2 hacc = f2_to2(0.0f, 0.0f, (h2 *)nullptr);
-            float facc0 = 0.0f, facc1 = 0.0f;
-            const bool inside = px0 - r >= 0 && px0 + r < W && py0 - r >= 0 && py0 + r < H &&
-                                px1 - r >= 0 && px1 + r < W && py1 - r >= 0 && py1 + r < H;
-            for (int dy = -r; dy <= r; ++dy) {
-                const int w = sm.w[dy + r];
-                const uint8_t *row0 = frame + static_cast<int64_t>(inside ? py0 + dy : clampi(py0 + dy, 0, H - 1)) * pitch;
-                const uint8_t *row1 = frame + static_cast<int64_t>(inside ? py1 + dy : clampi(py1 + dy, 0, H - 1)) * pitch;
-                for (int dx = -w; dx <= w; ++dx) {
-                    const uint32_t i0 = __ldg(row0 + (inside ? px0 + dx : clampi(px0 + dx, 0, W - 1)));
-                    const uint32_t i1 = __ldg(row1 + (inside ? px1 + dx : clampi(px1 + dx, 0, W - 1)));
-                    const h2 tm = HalfLik<h2>::term(HalfLik<h2>::pix(i0, i1), bgo, fgo, kap);
-                    if (half_acc) hacc = __hadd2(hacc, tm);
-                    else { facc0 += lo_f(tm); facc1 += hi_f(tm); }
-                }
+            const unsigned cx0 = static_cast<unsigned>(px0 - wx0), cy0 = static_cast<unsigned>(py0 - wy0);
+            const unsigned cx1 = static_cast<unsigned>(px1 - wx0), cy1 = static_cast<unsigned>(py1 - wy0);
+            const bool in0 = cx0 < static_cast<unsigned>(ww) && cy0 < static_cast<unsigned>(wh);
+            const bool in1 = cx1 < static_cast<unsigned>(ww) && cy1 < static_cast<unsigned>(wh);
+            lik_t l0 = in0 ? sm.table[cy0 * ww + cx0] : lik_t{};
+            lik_t l1 = in1 ? sm.table[cy1 * ww + cx1] : lik_t{};
+            if ((v0 && !in0) || (v1 && !in1)) {
+                const h2 Ld = lik_half_pair<h2>(fv, sm.w, px0, py0, px1, py1, hk);
+                if (!in0) l0 = lo_h(Ld);
+                if (!in1) l1 = hi_h(Ld);
             }
-            h2 L2 = half_acc ? hacc : f2_to2(facc0, facc1, (h2 *)nullptr);
+            const h2 L2 = make2(l0, l1);
             if (v0 && v1) {
                 reinterpret_cast<h2 *>(Xout)[q] = ox;
                 reinterpret_cast<h2 *>(Yout)[q] = oy;
                 reinterpret_cast<h2 *>(Lout)[q] = L2;
             } else if (v0) {
-                Xout[j0] = lo_h(ox); Yout[j0] = lo_h(oy); Lout[j0] = lo_h(L2);
+                Xout[j0] = lo_h(ox); Yout[j0] = lo_h(oy); Lout[j0] = l0;
             } else if (v1) {
-                Xout[j1] = hi_h(ox); Yout[j1] = hi_h(oy); Lout[j1] = hi_h(L2);
+                Xout[j1] = hi_h(ox); Yout[j1] = hi_h(oy); Lout[j1] = l1;
             }
-            if (v0) stats_add(stats, lo_f(L2), lo_f(ox), lo_f(oy));
-            if (v1) stats_add(stats, hi_f(L2), hi_f(ox), hi_f(oy));
+            if (v0) stats_add(stats, to_acc(l0), lo_f(ox), lo_f(oy));
+            if (v1) stats_add(stats, to_acc(l1), hi_f(ox), hi_f(oy));
         }
     }
 
     // ------------------------------------------------------------ 5. tile partial + finalise
-    const Stats<acc_t> tot = block_stats(stats, sm.red);
+    const Stats<acc_t> tot = block_stats<P>(stats, sm);
     if (tid == 0) {
         TilePartial *p = &T.part[lt];
         p->m = static_cast<double>(tot.m);
@@ -655,7 +785,8 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
 
 template <int P>
 __global__ void __launch_bounds__(kThreads) step_kernel(const StepLaunch Lp) {
-    __shared__ StepSmem<P> sm;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    StepSmem<P> &sm = *reinterpret_cast<StepSmem<P> *>(smem_raw);
     for (;;) {
         if (threadIdx.x == 0) sm.ticket = atomicAdd(Lp.ticket, 1u);
         __syncthreads();
@@ -677,11 +808,14 @@ __global__ void philox_kernel(const uint4 *ctrs, int64_t n, uint32_t k0, uint32_
 }
 
 template <int P>
-int occupancy_grid(int total_tiles) {
+int configure_and_grid(int total_tiles) {
+    const int bytes = static_cast<int>(sizeof(StepSmem<P>));
+    if (cudaFuncSetAttribute(step_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess)
+        return -1;
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel<P>, kThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel<P>, kThreads, bytes);
     if (per_sm < 1) per_sm = 1;
     const int g = sms * per_sm;
     return total_tiles < g ? total_tiles : g;
@@ -691,22 +825,22 @@ int occupancy_grid(int total_tiles) {
 
 int step_grid_size(int precision, int total_tiles) {
     switch (precision) {
-        case 0: return occupancy_grid<0>(total_tiles);
-        case 1: return occupancy_grid<1>(total_tiles);
-        case 2: return occupancy_grid<2>(total_tiles);
-        case 3: return occupancy_grid<3>(total_tiles);
+        case 0: return configure_and_grid<0>(total_tiles);
+        case 1: return configure_and_grid<1>(total_tiles);
+        case 2: return configure_and_grid<2>(total_tiles);
+        case 3: return configure_and_grid<3>(total_tiles);
     }
-    return 0;
+    return -1;
 }
 
 int launch_step(int precision, const StepLaunch &L, int grid, void *stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (grid < 1) grid = 1;
     switch (precision) {
-        case 0: step_kernel<0><<<grid, kThreads, 0, s>>>(L); break;
-        case 1: step_kernel<1><<<grid, kThreads, 0, s>>>(L); break;
-        case 2: step_kernel<2><<<grid, kThreads, 0, s>>>(L); break;
-        case 3: step_kernel<3><<<grid, kThreads, 0, s>>>(L); break;
+        case 0: step_kernel<0><<<grid, kThreads, sizeof(StepSmem<0>), s>>>(L); break;
+        case 1: step_kernel<1><<<grid, kThreads, sizeof(StepSmem<1>), s>>>(L); break;
+        case 2: step_kernel<2><<<grid, kThreads, sizeof(StepSmem<2>), s>>>(L); break;
+        case 3: step_kernel<3><<<grid, kThreads, sizeof(StepSmem<3>), s>>>(L); break;
         default: return -1;
     }
     return static_cast<int>(cudaGetLastError());
