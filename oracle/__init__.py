@@ -52,6 +52,7 @@ def _load():
             "orc_box_muller_batch": (None, [_I64, _P, _P, _P, _P]),
             "orc_round_pixel_batch": (None, [_I64, _P, _P]),
             "orc_resample_u0": (_D, [_U64, _U32, _U32]),
+            "orc_normal2_batch": (None, [_U64, _U32, _U32, _I64, _I64, _P, _P]),
             "orc_disk_count": (ctypes.c_int, [ctypes.c_int]),
             "orc_likelihood_at": (_D, [_P, ctypes.c_int, ctypes.c_int, _I64, ctypes.c_int,
                                        _D, _D, _I64, _I64]),
@@ -109,11 +110,10 @@ def box_muller(ua, ub):
 
 def normals(seed: int, t: int, n: int, tracker: int = 0, start: int = 0):
     """The propagation draws (n_x, n_y) of particles start..start+n-1 at frame t."""
-    j = np.arange(start, start + n, dtype=np.uint64).astype(np.uint32)
-    ctr = np.stack([j, np.full(n, t, np.uint32), np.zeros(n, np.uint32),
-                    np.full(n, tracker, np.uint32)], axis=1)
-    w = philox(ctr, seed)
-    return box_muller(uniform(w[:, 0]), uniform(w[:, 1]))
+    nx = np.empty(n, np.float64)
+    ny = np.empty(n, np.float64)
+    _load().orc_normal2_batch(seed & 0xFFFFFFFFFFFFFFFF, t, tracker, start, n, _ptr(nx), _ptr(ny))
+    return nx, ny
 
 
 def resample_u0(seed: int, t: int, tracker: int = 0) -> float:

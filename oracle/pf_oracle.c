@@ -29,7 +29,9 @@
  *   C12 at t = 0 every ancestor sits at (init_x, init_y).
  * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), written here
  * from that paper's description, keyed by the 64-bit seed with the counter
- * (particle j, frame t, tag, tracker id); tag 0 = propagation, 1 = resampling u0.
+ * (index, frame t, tag, tracker id); tag 0 = propagation, 1 = resampling u0.  One
+ * propagation block (four words) serves the particle pair (2i, 2i+1): counter index i,
+ * words 0-1 for particle 2i and words 2-3 for particle 2i+1.
  *
  * Build: gcc -O2 -ffp-contract=off -fno-fast-math -fPIC -shared (no FMA contraction,
  * so x86-64 and aarch64 produce the same bits).
@@ -114,12 +116,20 @@ void orc_box_muller_batch(int64_t n, const double *ua, const double *ub, double 
     for (int64_t i = 0; i < n; ++i) orc_box_muller(ua[i], ub[i], nx + i, ny + i);
 }
 
-/* The propagation draw of particle j at frame t (tag 0). */
+/* The propagation draw of particle j at frame t (tag 0): block j/2, words 2(j%2), 2(j%2)+1. */
 void orc_normal2(uint64_t seed, uint32_t j, uint32_t t, uint32_t tracker, double *nx, double *ny)
 {
     uint32_t w[4];
-    orc_philox_draw(seed, j, t, 0u, tracker, w);
-    orc_box_muller(orc_uniform(w[0]), orc_uniform(w[1]), nx, ny);
+    orc_philox_draw(seed, j >> 1, t, 0u, tracker, w);
+    const uint32_t h = 2u * (j & 1u);
+    orc_box_muller(orc_uniform(w[h]), orc_uniform(w[h + 1]), nx, ny);
+}
+
+void orc_normal2_batch(uint64_t seed, uint32_t t, uint32_t tracker, int64_t start, int64_t n,
+                       double *nx, double *ny)
+{
+    for (int64_t i = 0; i < n; ++i)
+        orc_normal2(seed, (uint32_t)(start + i), t, tracker, nx + i, ny + i);
 }
 
 /* The systematic-resampling offset u0 of frame t (tag 1, particle word 0). */

@@ -52,6 +52,19 @@ __device__ __forceinline__ void box_muller(float ua, float ub, float &nx, float 
     ny = rad * s;
 }
 
+// Box-Muller with the hardware approximations (log2, sqrt, sin/cos special-function
+// units), for the FP16/BF16 filters whose positions keep ~11 bits anyway.  The angle
+// is taken in [-pi, pi), where the sin/cos approximations are most accurate:
+// (cos, sin)(2 pi u - pi) = -(cos, sin)(2 pi u).
+__device__ __forceinline__ void box_muller_fast(float ua, float ub, float &nx, float &ny) {
+    const float rad = __fsqrt_rn(-1.3862943611198906f * __log2f(ua));   // -2 ln u = -2 ln2 log2 u
+    const float ang = 6.2831853071795865f * (ub - 0.5f);
+    float s, c;
+    __sincosf(ang, &s, &c);
+    nx = -rad * c;
+    ny = -rad * s;
+}
+
 // ----------------------------------------------------------------------------------
 // Explicitly rounded arithmetic (no contraction), used where the result must equal the
 // same expression evaluated elsewhere.
@@ -77,44 +90,56 @@ template <> __device__ __forceinline__ float neg_inf<float>() { return -__int_as
 // arithmetic estimate and a short galloping search.
 // ----------------------------------------------------------------------------------
 template <typename A>
-__device__ __forceinline__ A stratum_point(int64_t j, A u0, A inv_n) {
+__device__ __forceinline__ A stratum_point32(int j, A u0, A inv_n) {
     return mul_rn(add_rn(static_cast<A>(j), u0), inv_n);
 }
 
+// Strata of one tracker's frame: n = N, u0, 1/N, and the first / last stratum points.
 template <typename A>
-__device__ int64_t count_le(A c, A u0, A inv_n, int64_t n) {
-    if (!(stratum_point<A>(0, u0, inv_n) <= c)) return 0;   // also NaN
-    if (stratum_point<A>(n - 1, u0, inv_n) <= c) return n;
-    // invariant wanted: u(lo) <= c < u(hi), 0 <= lo < hi <= n - 1
-    const A est = c * static_cast<A>(n) - u0;
-    int64_t j = (est > static_cast<A>(0)) ? static_cast<int64_t>(est) : 0;
-    if (j > n - 2) j = n - 2;
-    int64_t lo, hi;
-    if (stratum_point<A>(j, u0, inv_n) <= c) {
-        lo = j;
-        hi = j + 1;
-        int64_t step = 1;
-        while (hi < n - 1 && stratum_point<A>(hi, u0, inv_n) <= c) {
-            lo = hi;
-            step <<= 1;
-            hi = (hi + step < n - 1) ? hi + step : n - 1;
-        }
-    } else {
-        hi = j;
-        lo = j - 1;
-        int64_t step = 1;
-        while (lo > 0 && !(stratum_point<A>(lo, u0, inv_n) <= c)) {
-            hi = lo;
-            step <<= 1;
-            lo = (lo - step > 0) ? lo - step : 0;
-        }
+struct Strata {
+    A u0, inv_n, first, last, nf;
+    int n;
+    __device__ __forceinline__ void init(int n_, A u0_, A inv_n_) {
+        n = n_; u0 = u0_; inv_n = inv_n_;
+        first = stratum_point32<A>(0, u0, inv_n);
+        last = stratum_point32<A>(n - 1, u0, inv_n);
+        nf = static_cast<A>(n);
     }
-    while (hi - lo > 1) {
-        const int64_t mid = lo + ((hi - lo) >> 1);
-        if (stratum_point<A>(mid, u0, inv_n) <= c) lo = mid; else hi = mid;
+    // number of strata j with u_j <= c
+    __device__ int count_le(A c) const {
+        if (!(first <= c)) return 0;   // also NaN
+        if (last <= c) return n;
+        // invariant wanted: u(lo) <= c < u(hi), 0 <= lo < hi <= n - 1
+        const A est = c * nf - u0;
+        int j = (est > static_cast<A>(0)) ? static_cast<int>(est) : 0;
+        if (j > n - 2) j = n - 2;
+        int lo, hi;
+        if (stratum_point32<A>(j, u0, inv_n) <= c) {
+            lo = j;
+            hi = j + 1;
+            long long step = 1;
+            while (hi < n - 1 && stratum_point32<A>(hi, u0, inv_n) <= c) {
+                lo = hi;
+                step <<= 1;
+                hi = (hi + step < n - 1) ? static_cast<int>(hi + step) : n - 1;
+            }
+        } else {
+            hi = j;
+            lo = j - 1;
+            long long step = 1;
+            while (lo > 0 && !(stratum_point32<A>(lo, u0, inv_n) <= c)) {
+                hi = lo;
+                step <<= 1;
+                lo = (lo > step) ? static_cast<int>(lo - step) : 0;
+            }
+        }
+        while (hi - lo > 1) {
+            const int mid = lo + ((hi - lo) >> 1);
+            if (stratum_point32<A>(mid, u0, inv_n) <= c) lo = mid; else hi = mid;
+        }
+        return lo + 1;
     }
-    return lo + 1;
-}
+};
 
 // ----------------------------------------------------------------------------------
 // Memory-model helpers for the decoupled lookback and the last-block-done finalise.

@@ -9,7 +9,7 @@
 #include <new>
 #include <vector>
 
-#include "../../include/pf.h"
+#include "pf.h"
 #include "pf_internal.h"
 
 using namespace pfk;

@@ -9,13 +9,15 @@
 //      j with C_{k-1} < u_j <= C_k are the offspring of k.  The tile's offspring form a
 //      contiguous range of j, and their ancestors all lie in the tile, so the gather of
 //      ancestor positions is a read of the tile's own particles staged in shared memory.
-//   2. propagation (Eq. 1-2) of every offspring j with Philox draws keyed (j, t),
+//   2. propagation (Eq. 1-2) of every offspring j with Philox draws keyed by (j, t),
 //   3. likelihood (Eq. 3; Eq. 4 scaled half form in F16/BF16) on the new frame.  The
 //      likelihood is a function of the particle's pixel only, so each tile first tabulates
 //      it in shared memory over the window its offspring can reach (the ancestors'
-//      bounding box widened by the largest draw the 23-bit Box-Muller can produce) and
-//      each offspring reads its pixel's value; a pixel outside the window is evaluated
-//      directly by the same function, so the two routes give identical bits.
+//      bounding box widened by the drift and the largest draw the 23-bit Box-Muller can
+//      produce), from a copy of the frame region staged in shared memory, and each
+//      offspring reads its pixel's value; a pixel outside the window is evaluated directly
+//      from global memory by the same arithmetic in the same order, so the two routes
+//      give identical bits.
 //   4. per-tile (max L, sum e, sum e*dx, sum e*dy), merged with rescaling,
 //   5. the tile that completes a tracker merges its tiles' partials in index order:
 //      M, S, 1/S and the estimate of the frame (the weighted mean of the propagated
@@ -42,7 +44,9 @@ namespace pfk {
 namespace {
 
 constexpr int kWarps = kThreads / 32;
-constexpr int kTableMax = 4096;            // cells of the per-tile likelihood table
+constexpr int kTableMax = 4096;            // pixels of the per-tile likelihood table
+constexpr int kRoiMax = 8192;              // staged frame pixels (window + template margin)
+constexpr int kMapMax = 8192;              // offspring of a tile served by the ancestor map
 constexpr uint32_t kSpinLimit = 1u << 22;  // bounded waits: ~1 s with backoff
 // Largest |N(0,1)| draw: sqrt(-2 ln 2^-24) = 5.7684 for the smallest 23-bit uniform.
 constexpr float kMaxNormal = 5.77f;
@@ -51,8 +55,20 @@ __device__ __forceinline__ bool flag_ready(uint32_t f, uint32_t ep) {
     return (f >> 2) == (ep & 0x3fffffffu) && (f & 3u) != 0u;
 }
 
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ uint32_t atom_add_acq_rel(uint32_t *p, uint32_t v) {
+    uint32_t old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
 __device__ __forceinline__ bool timed_out(const TrackerState *st) {
-    return (ld_acquire_u32(&st->status) & kStatusTimeout) != 0u;
+    return (ld_relaxed_u32(&st->status) & kStatusTimeout) != 0u;
 }
 
 // Wait (bounded) until the lookback descriptor of a tile carries this epoch.  Returns the
@@ -127,13 +143,16 @@ __device__ __forceinline__ Stats<A> stats_shfl_xor(const Stats<A> &a, int o) {
     return b;
 }
 
-// Pixel of a position (reading C3): floor(v) + (v - floor(v) >= 0.5), clamped into a
-// range that keeps the integer arithmetic safe (the template is clamped to the frame).
-template <typename A>
-__device__ __forceinline__ int pixel_of(A v) {
-    if (!(v > static_cast<A>(-1.0e9) && v < static_cast<A>(1.0e9))) return -1000000000;
-    const A f = floor(v);
-    return static_cast<int>(f) + ((v - f) >= static_cast<A>(0.5) ? 1 : 0);
+// Pixel of a position (reading C3): floor(v) + (v - floor(v) >= 0.5).  For |v| below
+// 2^22 (float) or 2^51 (double) this equals floor(v + 0.5): adding 1/2 is exact unless
+// it crosses into the next binade, which happens only when the fraction is >= 1/2 and
+// then rounds to the same integer.  Positions are first clamped to +-2^20, far outside
+// any frame (template pixels are clamped to the frame, reading C4).
+__device__ __forceinline__ int pixel_of(float v) {
+    return __float2int_rd(fminf(fmaxf(v, -1048576.0f), 1048576.0f) + 0.5f);
+}
+__device__ __forceinline__ int pixel_of(double v) {
+    return __double2int_rd(fmin(fmax(v, -1048576.0), 1048576.0) + 0.5);
 }
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
@@ -142,11 +161,14 @@ struct FrameView {
     const uint8_t *p;
     int64_t pitch;
     int W, H, r;
+    __device__ __forceinline__ uint32_t at(int x, int y) const {
+        return __ldg(p + static_cast<int64_t>(clampi(y, 0, H - 1)) * pitch + clampi(x, 0, W - 1));
+    }
 };
 
 // Integer sum of the template pixels around (px, py) (the exact form of Eq. 3; reading
 // C4 clamps template pixels to the frame).  w[i] = half-width of template row dy = i - r.
-__device__ __forceinline__ uint32_t disk_sum(const FrameView &f, const int8_t *w, int px, int py) {
+__device__ uint32_t disk_sum(const FrameView &f, const int8_t *w, int px, int py) {
     uint32_t s = 0;
     const int r = f.r;
     if (px - r >= 0 && px + r < f.W && py - r >= 0 && py + r < f.H) {
@@ -158,8 +180,7 @@ __device__ __forceinline__ uint32_t disk_sum(const FrameView &f, const int8_t *w
     } else {
         for (int dy = -r; dy <= r; ++dy) {
             const int hw = w[dy + r];
-            const uint8_t *row = f.p + static_cast<int64_t>(clampi(py + dy, 0, f.H - 1)) * f.pitch;
-            for (int dx = -hw; dx <= hw; ++dx) s += __ldg(row + clampi(px + dx, 0, f.W - 1));
+            for (int dx = -hw; dx <= hw; ++dx) s += f.at(px + dx, py + dy);
         }
     }
     return s;
@@ -171,100 +192,117 @@ __device__ __forceinline__ A lik_from_sum(uint32_t s, A c1, A c2D, A den) {
     return (c1 * (static_cast<A>(2) * static_cast<A>(s) - c2D)) / den;
 }
 
-// Eq. 4 per-pixel scaled form on two pixels at once (half2 lanes), accumulated in the
-// lane type (F16, the paper's form) or in FP32 (BF16 and PF_FLAG_ACCUM32).
-template <typename H2> struct HalfLik;
+// ----------------------------------------------------------------------------------
+// Eq. 4 per-pixel scaled form in half precision: a = (I - bg) kappa, b = (I - fg) kappa,
+// term = a*a - b*b, summed over the template row by row, left to right, in the lane type
+// (F16, the paper's form) or in FP32 (BF16 and PF_FLAG_ACCUM32).
+// ----------------------------------------------------------------------------------
+template <typename H> struct HalfOps;
 
 template <>
-struct HalfLik<__half2> {
-    // (1024 + I) has the bit pattern 0x6400 | I in binary16, so the pixel arrives in a
-    // half2 lane without a conversion instruction: h - (1024 + level) is exact.
-    __device__ static __forceinline__ __half2 pix(uint32_t i0, uint32_t i1) {
-        const uint32_t bits = (0x6400u | i0) | ((0x6400u | i1) << 16);
-        return *reinterpret_cast<const __half2 *>(&bits);
-    }
-    __device__ static __forceinline__ float level_offset() { return 1024.0f; }
+struct HalfOps<__half> {
+    using h2 = __half2;
+    // (1024 + I) has the bit pattern 0x6400 | I in binary16, so the pixel enters the
+    // half arithmetic without a conversion instruction: h - (1024 + level) is exact.
+    static constexpr float kLevelOffset = 1024.0f;
+    __device__ static __forceinline__ __half pix(uint32_t i) { return __ushort_as_half(static_cast<unsigned short>(0x6400u | i)); }
+    __device__ static __forceinline__ __half from_f(float v) { return __float2half_rn(v); }
+    __device__ static __forceinline__ float to_f(__half v) { return __half2float(v); }
+    __device__ static __forceinline__ h2 pack(__half a, __half b) { return __halves2half2(a, b); }
+    __device__ static __forceinline__ h2 from_f2(float a, float b) { return __floats2half2_rn(a, b); }
+    __device__ static __forceinline__ float lo(h2 v) { return __low2float(v); }
+    __device__ static __forceinline__ float hi(h2 v) { return __high2float(v); }
+    __device__ static __forceinline__ __half lo_h(h2 v) { return __low2half(v); }
+    __device__ static __forceinline__ __half hi_h(h2 v) { return __high2half(v); }
 };
 
 template <>
-struct HalfLik<__nv_bfloat162> {
-    __device__ static __forceinline__ __nv_bfloat162 pix(uint32_t i0, uint32_t i1) {
-        return __floats2bfloat162_rn(static_cast<float>(i0), static_cast<float>(i1));
-    }
-    __device__ static __forceinline__ float level_offset() { return 0.0f; }
+struct HalfOps<__nv_bfloat16> {
+    using h2 = __nv_bfloat162;
+    static constexpr float kLevelOffset = 0.0f;
+    __device__ static __forceinline__ __nv_bfloat16 pix(uint32_t i) { return __float2bfloat16_rn(static_cast<float>(i)); }
+    __device__ static __forceinline__ __nv_bfloat16 from_f(float v) { return __float2bfloat16_rn(v); }
+    __device__ static __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+    __device__ static __forceinline__ h2 pack(__nv_bfloat16 a, __nv_bfloat16 b) { return __halves2bfloat162(a, b); }
+    __device__ static __forceinline__ h2 from_f2(float a, float b) { return __floats2bfloat162_rn(a, b); }
+    __device__ static __forceinline__ float lo(h2 v) { return __low2float(v); }
+    __device__ static __forceinline__ float hi(h2 v) { return __high2float(v); }
+    __device__ static __forceinline__ __nv_bfloat16 lo_h(h2 v) { return __low2bfloat16(v); }
+    __device__ static __forceinline__ __nv_bfloat16 hi_h(h2 v) { return __high2bfloat16(v); }
 };
 
-__device__ __forceinline__ __half2 make2(__half a, __half b) { return __halves2half2(a, b); }
-__device__ __forceinline__ __nv_bfloat162 make2(__nv_bfloat16 a, __nv_bfloat16 b) { return __halves2bfloat162(a, b); }
-template <typename H2> __device__ __forceinline__ H2 f2_to2(float a, float b);
-template <> __device__ __forceinline__ __half2 f2_to2<__half2>(float a, float b) { return __floats2half2_rn(a, b); }
-template <> __device__ __forceinline__ __nv_bfloat162 f2_to2<__nv_bfloat162>(float a, float b) { return __floats2bfloat162_rn(a, b); }
-__device__ __forceinline__ float lo_f(__half2 v) { return __low2float(v); }
-__device__ __forceinline__ float hi_f(__half2 v) { return __high2float(v); }
-__device__ __forceinline__ float lo_f(__nv_bfloat162 v) { return __low2float(v); }
-__device__ __forceinline__ float hi_f(__nv_bfloat162 v) { return __high2float(v); }
-__device__ __forceinline__ __half lo_h(__half2 v) { return __low2half(v); }
-__device__ __forceinline__ __half hi_h(__half2 v) { return __high2half(v); }
-__device__ __forceinline__ __nv_bfloat16 lo_h(__nv_bfloat162 v) { return __low2bfloat16(v); }
-__device__ __forceinline__ __nv_bfloat16 hi_h(__nv_bfloat162 v) { return __high2bfloat16(v); }
-
-template <typename H2>
-struct HalfConsts {
-    H2 kap, bgo, fgo;
+template <typename H>
+struct HalfLik {
+    H kap, bgo, fgo;
     bool half_acc;
-};
-
-// Likelihood of two pixels (px0,py0), (px1,py1) in the half form: per template pixel
-// a = (I - bg) kappa, b = (I - fg) kappa, term = a*a - b*b (Eq. 4), summed row by row.
-template <typename H2>
-__device__ H2 lik_half_pair(const FrameView &f, const int8_t *w, int px0, int py0, int px1, int py1,
-                            const HalfConsts<H2> &k) {
-    const int r = f.r;
-    const bool inside = px0 - r >= 0 && px0 + r < f.W && py0 - r >= 0 && py0 + r < f.H &&
-                        px1 - r >= 0 && px1 + r < f.W && py1 - r >= 0 && py1 + r < f.H;
-    H2 hacc = f2_to2<H2>(0.0f, 0.0f);
-    float a0 = 0.0f, a1 = 0.0f;
-    for (int dy = -r; dy <= r; ++dy) {
-        const int hw = w[dy + r];
-        const uint8_t *row0 = f.p + static_cast<int64_t>(inside ? py0 + dy : clampi(py0 + dy, 0, f.H - 1)) * f.pitch;
-        const uint8_t *row1 = f.p + static_cast<int64_t>(inside ? py1 + dy : clampi(py1 + dy, 0, f.H - 1)) * f.pitch;
-        for (int dx = -hw; dx <= hw; ++dx) {
-            const uint32_t i0 = __ldg(row0 + (inside ? px0 + dx : clampi(px0 + dx, 0, f.W - 1)));
-            const uint32_t i1 = __ldg(row1 + (inside ? px1 + dx : clampi(px1 + dx, 0, f.W - 1)));
-            const H2 h = HalfLik<H2>::pix(i0, i1);
-            const H2 a = __hmul2(__hsub2(h, k.bgo), k.kap);
-            const H2 b = __hmul2(__hsub2(h, k.fgo), k.kap);
-            const H2 term = __hfma2(a, a, __hneg2(__hmul2(b, b)));
-            if (k.half_acc) hacc = __hadd2(hacc, term);
-            else { a0 += lo_f(term); a1 += hi_f(term); }
-        }
+    __device__ __forceinline__ H term(uint32_t i) const {
+        const H h = HalfOps<H>::pix(i);
+        const H a = __hmul(__hsub(h, bgo), kap);
+        const H b = __hmul(__hsub(h, fgo), kap);
+        return __hfma(a, a, __hneg(__hmul(b, b)));
     }
-    return k.half_acc ? hacc : f2_to2<H2>(a0, a1);
-}
+    // direct evaluation from the frame (same terms, same order as the tabulated route)
+    __device__ H at(const FrameView &f, const int8_t *w, int px, int py) const {
+        H hacc = HalfOps<H>::from_f(0.0f);
+        float facc = 0.0f;
+        for (int dy = -f.r; dy <= f.r; ++dy) {
+            const int hw = w[dy + f.r];
+            for (int dx = -hw; dx <= hw; ++dx) {
+                const H tm = term(f.at(px + dx, py + dy));
+                if (half_acc) hacc = __hadd(hacc, tm); else facc += HalfOps<H>::to_f(tm);
+            }
+        }
+        return half_acc ? hacc : HalfOps<H>::from_f(facc);
+    }
+    // from per-pixel terms staged in shared memory (row pitch rw, template centred at
+    // column cx + r, row cy + r)
+    __device__ H from_terms(const H *tm, int rw, const int8_t *w, int r, int cx, int cy) const {
+        H hacc = HalfOps<H>::from_f(0.0f);
+        float facc = 0.0f;
+        for (int i = 0; i <= 2 * r; ++i) {
+            const int hw = w[i];
+            const H *row = tm + (cy + i) * rw + cx + r;
+            for (int dx = -hw; dx <= hw; ++dx) {
+                if (half_acc) hacc = __hadd(hacc, row[dx]); else facc += HalfOps<H>::to_f(row[dx]);
+            }
+        }
+        return half_acc ? hacc : HalfOps<H>::from_f(facc);
+    }
+};
 
 // Shared memory of the step kernel (dynamic: sizeof(StepSmem<P>) bytes).
 template <int P>
 struct __align__(16) StepSmem {
-    using pos_t = typename Prec<P>::pos_t;
-    using lik_t = typename Prec<P>::lik_t;
-    using acc_t = typename Prec<P>::acc_t;
+    using Tr = Prec<P>;
+    using pos_t = typename Tr::pos_t;
+    using lik_t = typename Tr::lik_t;
+    using acc_t = typename Tr::acc_t;
+    static constexpr int kPixBytes = Tr::kHalf ? 16 : kRoiMax;
     pos_t ax[kTile];          // ancestor positions of the tile (previous frame)
     pos_t ay[kTile];
     int32_t J[kTile];         // J[e] = strata assigned to particles k0..k0+e (cumulative)
     lik_t table[kTableMax];   // likelihood of each pixel of the tile's window
+    union {
+        uint16_t pre[kRoiMax];      // integer form: row prefix sums of the staged region
+        lik_t term[kRoiMax];        // half form: per-pixel Eq. 4 terms of the staged region
+        uint16_t map[kMapMax];      // ancestor (tile element + 1) of each offspring
+    } u;
+    uint8_t pix[kPixBytes];   // integer form: staged frame region
     acc_t warp_sum[kWarps];
     acc_t warp_max[kWarps];
     float box[kWarps][4];
+    int warp_imax[kWarps];
     U128 red128[kWarps];
     Stats<acc_t> red[kWarps];
     acc_t agg;
     U128 excl_x, end_x;       // exact fixed-point prefix before / after the tile
-    int64_t jbeg, jend;
+    int jbeg, jend;
     int win_x0, win_y0, win_w, win_h;   // likelihood table window (win_w = 0: none)
     int qmin;
     int8_t w[2 * kMaxRadius + 1];
     uint32_t ticket;
     uint32_t last;
+    uint32_t skip;
 };
 
 // Block-wide merge of per-thread stats in a fixed order; result valid in thread 0.
@@ -331,11 +369,11 @@ __device__ U128 lookback(const LookbackDesc *look, int lt, uint32_t ep, TrackerS
 }
 
 // First index e in [0, n) with J[e] > j (J non-decreasing, J[n-1] > j).
-__device__ __forceinline__ int upper_index(const int32_t *J, int n, int64_t j) {
+__device__ __forceinline__ int upper_index(const int32_t *J, int n, int j) {
     int lo = 0, hi = n - 1;
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if (static_cast<int64_t>(J[mid]) > j) hi = mid; else lo = mid + 1;
+        if (J[mid] > j) hi = mid; else lo = mid + 1;
     }
     return lo;
 }
@@ -343,7 +381,6 @@ __device__ __forceinline__ int upper_index(const int32_t *J, int n, int64_t j) {
 template <int P>
 __device__ void finalize_tracker(const TrackerDev &T, TrackerState *st, StepSmem<P> &sm) {
     using acc_t = typename Prec<P>::acc_t;
-    __threadfence();
     Stats<acc_t> v{neg_inf<acc_t>(), 0, 0, 0};
     for (int i = threadIdx.x; i < T.ntiles; i += kThreads) {
         const double *p = &T.part[i].m;
@@ -390,19 +427,37 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
     using acc_t = typename Tr::acc_t;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int ti = Lp.tile_trk[g];
+    const int ti = (Lp.ntrk == 1) ? 0 : __ldg(&Lp.tile_trk[g]);
     const TrackerDev &T = Lp.trk[ti];
     const FrameRef fr = Lp.frames[ti];
     if (!fr.active) return;
-    TrackerState *st = T.state;
-    if (timed_out(st)) return;   // a failed step: results are invalid, skip without waiting
+    TrackerState *const st = T.state;
 
-    const int64_t N = T.N;
+    // ---- parameters into registers (the output stores must not force reloads)
+    const int N = static_cast<int>(T.N);
     const int lt = g - T.tile_begin;
-    const int64_t k0 = static_cast<int64_t>(lt) * kTile;
-    const int cnt = static_cast<int>((N - k0) < kTile ? (N - k0) : kTile);
+    const int ntiles = T.ntiles;
+    const int k0 = lt * kTile;
+    const int cnt = (N - k0) < kTile ? (N - k0) : kTile;
+    const uint32_t key_lo = T.key_lo, key_hi = T.key_hi, trk_id = T.tracker_id, flags = T.flags;
+    int32_t *const dbg_anc = T.dbg_anc;
+    acc_t *const dbg_cdf = static_cast<acc_t *>(T.dbg_cdf);
+    const double init_x = T.init_x, init_y = T.init_y;
+    const acc_t dxm = static_cast<acc_t>(T.drift_x), dym = static_cast<acc_t>(T.drift_y);
+    const acc_t sgx = static_cast<acc_t>(T.sigma_x), sgy = static_cast<acc_t>(T.sigma_y);
+    const acc_t c1 = static_cast<acc_t>(T.c1), c2D = static_cast<acc_t>(T.c2 * T.D);
+    const acc_t den = static_cast<acc_t>(T.den);
+    const acc_t inv_n = sizeof(acc_t) == 8 ? static_cast<acc_t>(T.inv_n) : static_cast<acc_t>(T.inv_n_f);
+    LookbackDesc *const look = T.look;
+
+    // a failed step: results are invalid, skip without waiting (decided once per block)
+    if (tid == 0) sm.skip = timed_out(st) ? 1u : 0u;
+    __syncthreads();
+    if (sm.skip) return;
     const int64_t t = __ldcg(&st->t);
     const uint32_t ep = __ldcg(&st->epoch);
+    const double nxa = __ldcg(&st->nx), nya = __ldcg(&st->ny);   // anchor of the offspring
+    const double axa = __ldcg(&st->ax), aya = __ldcg(&st->ay);   // anchor of the ancestors
     const int in = static_cast<int>((t + 1) & 1), out = static_cast<int>(t & 1);
 
     FrameView fv;
@@ -417,16 +472,11 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
         sm.w[i] = static_cast<int8_t>(w);
     }
 
-    // Anchor the offspring are written against (F16/BF16 offsets; estimate sums), and the
-    // anchor of the stored ancestors.
-    const double nxa = __ldcg(&st->nx), nya = __ldcg(&st->ny);
-    const double axa = __ldcg(&st->ax), aya = __ldcg(&st->ay);
-
     // ------------------------------------------------------------ 1. resampling
     if (t > 0) {
-        const lik_t *Lin = static_cast<const lik_t *>(T.pl[in]);
-        const pos_t *Xin = static_cast<const pos_t *>(T.px[in]);
-        const pos_t *Yin = static_cast<const pos_t *>(T.py[in]);
+        const lik_t *__restrict__ Lin = static_cast<const lik_t *>(T.pl[in]);
+        const pos_t *__restrict__ Xin = static_cast<const pos_t *>(T.px[in]);
+        const pos_t *__restrict__ Yin = static_cast<const pos_t *>(T.py[in]);
         const acc_t M = static_cast<acc_t>(__ldcg(&st->M));
         const acc_t invS = static_cast<acc_t>(__ldcg(&st->invS));
         for (int e = tid; e < cnt; e += kThreads) {
@@ -434,13 +484,28 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
             sm.ay[e] = Yin[k0 + e];
         }
         // blocked arrangement: thread tid owns elements tid*kItems .. +kItems-1
+        lik_t lv[kItems];
+        if (tid * kItems + kItems <= cnt) {
+            // kItems consecutive values, 16-byte aligned (k0 and tid*kItems are multiples of 8)
+            constexpr int kVec = sizeof(lik_t) * kItems / 16;
+            const uint4 *src = reinterpret_cast<const uint4 *>(Lin + k0 + tid * kItems);
+            uint4 *dst = reinterpret_cast<uint4 *>(lv);
+#pragma unroll
+            for (int v = 0; v < kVec; ++v) dst[v] = src[v];
+        } else {
+#pragma unroll
+            for (int m = 0; m < kItems; ++m) {
+                const int e = tid * kItems + m;
+                lv[m] = (e < cnt) ? Lin[k0 + e] : lik_t{};
+            }
+        }
         acc_t s[kItems];
         acc_t run = static_cast<acc_t>(0);
 #pragma unroll
         for (int m = 0; m < kItems; ++m) {
             const int e = tid * kItems + m;
             acc_t v = static_cast<acc_t>(0);
-            if (e < cnt) v = exp_le0(to_acc(Lin[k0 + e]) - M);
+            if (e < cnt) v = exp_le0(to_acc(lv[m]) - M);
             run = (m == 0) ? v : run + v;
             s[m] = run;
         }
@@ -487,7 +552,6 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
         }
         __syncthreads();
         const acc_t agg = sm.agg;
-        LookbackDesc *look = T.look;
         const U128 aggx = to_fixed(static_cast<double>(agg));
         const uint32_t tag = (ep & 0x3fffffffu) << 2;
         if (tid == 0) {
@@ -518,28 +582,31 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
         // values at both tile boundaries, so neighbouring tiles see the same boundary.
         const acc_t excl = static_cast<acc_t>(from_fixed(sm.excl_x));
         const acc_t pend = static_cast<acc_t>(from_fixed(sm.end_x));
-        acc_t u0;
-        {
-            const uint4 w = philox4x32_10(make_uint4(0u, static_cast<uint32_t>(t - 1), 1u, T.tracker_id),
-                                          T.key_lo, T.key_hi);
-            u0 = static_cast<acc_t>(uniform_f64(w.x));
-        }
-        const acc_t inv_n = sizeof(acc_t) == 8 ? static_cast<acc_t>(T.inv_n) : static_cast<acc_t>(T.inv_n_f);
+        const acc_t u0 = static_cast<acc_t>(uniform_f64(
+            philox4x32_10(make_uint4(0u, static_cast<uint32_t>(t - 1), 1u, trk_id), key_lo, key_hi).x));
+        Strata<acc_t> str;
+        str.init(N, u0, inv_n);
+        acc_t cprev = static_cast<acc_t>(-1);
+        int jprev = 0;
 #pragma unroll
         for (int m = 0; m < kItems; ++m) {
             const int e = tid * kItems + m;
             if (e < cnt) {
-                const int64_t k = k0 + e;
+                const int k = k0 + e;
                 const acc_t Pk = (e == cnt - 1) ? pend : fmin(add_rn(excl, loc[m]), pend);
-                acc_t C = mul_rn(Pk, invS);
-                int64_t J;
+                // the normalised CDF cannot exceed 1; the FP32 scan can round above it
+                acc_t C = fmin(mul_rn(Pk, invS), static_cast<acc_t>(1));
+                int J;
                 if (k == N - 1) { C = static_cast<acc_t>(1); J = N; }
-                else J = count_le<acc_t>(C, u0, inv_n, N);
-                sm.J[e] = static_cast<int32_t>(J);
-                if (T.dbg_cdf) static_cast<acc_t *>(T.dbg_cdf)[k] = C;
+                else if (C == cprev) J = jprev;          // same CDF value, same count
+                else J = str.count_le(C);
+                cprev = C;
+                jprev = J;
+                sm.J[e] = J;
+                if (dbg_cdf) dbg_cdf[k] = C;
             }
         }
-        if (tid == 0) sm.jbeg = (lt == 0) ? 0 : count_le<acc_t>(mul_rn(excl, invS), u0, inv_n, N);
+        if (tid == 0) sm.jbeg = (lt == 0) ? 0 : str.count_le(fmin(mul_rn(excl, invS), static_cast<acc_t>(1)));
         __syncthreads();
         if (tid == 0) sm.jend = sm.J[cnt - 1];
         __syncthreads();
@@ -547,7 +614,8 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
         if (tid == 0) { sm.jbeg = k0; sm.jend = k0 + cnt; }
         __syncthreads();
     }
-    const int64_t jbeg = sm.jbeg, jend = sm.jend;
+    const int jb = sm.jbeg, je = sm.jend;
+    const int nout = je - jb;
 
     // ------------------------------------------------------------ likelihood window
     // Bounding box of the ancestors that have offspring (absolute pixel units), widened by
@@ -561,8 +629,8 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
             for (int m = 0; m < kItems; ++m) {
                 const int e = tid * kItems + m;
                 if (e < cnt) {
-                    const int64_t jp = e ? static_cast<int64_t>(sm.J[e - 1]) : jbeg;
-                    if (static_cast<int64_t>(sm.J[e]) > jp) {
+                    const int jp = e ? sm.J[e - 1] : jb;
+                    if (sm.J[e] > jp) {
                         const float xv = static_cast<float>(to_acc(sm.ax[e])) + sx;
                         const float yv = static_cast<float>(to_acc(sm.ay[e])) + sy;
                         bx0 = fminf(bx0, xv); bx1 = fmaxf(bx1, xv);
@@ -571,8 +639,8 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
                 }
             }
         } else {
-            bx0 = bx1 = static_cast<float>(T.init_x);
-            by0 = by1 = static_cast<float>(T.init_y);
+            bx0 = bx1 = static_cast<float>(init_x);
+            by0 = by1 = static_cast<float>(init_y);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -588,17 +656,18 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
                 bx0 = fminf(bx0, sm.box[w][0]); bx1 = fmaxf(bx1, sm.box[w][1]);
                 by0 = fminf(by0, sm.box[w][2]); by1 = fmaxf(by1, sm.box[w][3]);
             }
-            const float mxr = fabsf(static_cast<float>(T.drift_x)) + kMaxNormal * static_cast<float>(T.sigma_x) + 1.0f;
-            const float myr = fabsf(static_cast<float>(T.drift_y)) + kMaxNormal * static_cast<float>(T.sigma_y) + 1.0f;
+            const float mxr = fabsf(static_cast<float>(dxm)) + kMaxNormal * static_cast<float>(sgx) + 1.0f;
+            const float myr = fabsf(static_cast<float>(dym)) + kMaxNormal * static_cast<float>(sgy) + 1.0f;
             int ww = 0, wh = 0, x0 = 0, y0 = 0;
             if (bx0 <= bx1 && by0 <= by1 && bx1 - bx0 < 4096.0f && by1 - by0 < 4096.0f &&
-                fabsf(bx0) < 1.0e8f && fabsf(by0) < 1.0e8f && mxr < 4096.0f && myr < 4096.0f) {
+                fabsf(bx0) < 1.0e6f && fabsf(by0) < 1.0e6f && mxr < 4096.0f && myr < 4096.0f) {
                 x0 = static_cast<int>(floorf(bx0 - mxr));
                 y0 = static_cast<int>(floorf(by0 - myr));
                 ww = static_cast<int>(ceilf(bx1 + mxr)) - x0 + 1;
                 wh = static_cast<int>(ceilf(by1 + myr)) - y0 + 1;
                 const int64_t cells = static_cast<int64_t>(ww) * wh;
-                if (cells > kTableMax || cells > (jend - jbeg)) { ww = 0; wh = 0; }
+                const int64_t roi = static_cast<int64_t>(ww + 2 * r + 1) * (wh + 2 * r);
+                if (cells > kTableMax || cells > nout || roi > kRoiMax) { ww = 0; wh = 0; }
             }
             sm.win_x0 = x0; sm.win_y0 = y0; sm.win_w = ww; sm.win_h = wh;
         }
@@ -607,81 +676,145 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
     const int wx0 = sm.win_x0, wy0 = sm.win_y0, ww = sm.win_w, wh = sm.win_h;
     const int cells = ww * wh;
 
-    // likelihood constants
-    const acc_t c1 = static_cast<acc_t>(T.c1), c2D = static_cast<acc_t>(T.c2 * T.D);
-    const acc_t den = static_cast<acc_t>(T.den);
-    using h2 = typename std::conditional<std::is_same<pos_t, __nv_bfloat16>::value, __nv_bfloat162, __half2>::type;
-    HalfConsts<h2> hk;
+    using H = typename std::conditional<Tr::kHalf, pos_t, __half>::type;
+    HalfLik<H> hk;
     if constexpr (Tr::kHalf) {
-        const float lo = HalfLik<h2>::level_offset();
-        hk.kap = f2_to2<h2>(T.kappa, T.kappa);
-        hk.bgo = f2_to2<h2>(lo + T.bg_f, lo + T.bg_f);
-        hk.fgo = f2_to2<h2>(lo + T.fg_f, lo + T.fg_f);
-        hk.half_acc = std::is_same<pos_t, __half>::value && !(T.flags & 0x2u);
+        const float lo = HalfOps<H>::kLevelOffset;
+        hk.kap = HalfOps<H>::from_f(T.kappa);
+        hk.bgo = HalfOps<H>::from_f(lo + T.bg_f);
+        hk.fgo = HalfOps<H>::from_f(lo + T.fg_f);
+        hk.half_acc = std::is_same<pos_t, __half>::value && !(flags & 0x2u);
     }
 
-    // tabulate the window (two pixels per thread step: the half form works on pairs)
-    for (int c = 2 * tid; c < cells; c += 2 * kThreads) {
-        const int c1i = (c + 1 < cells) ? c + 1 : c;
-        const int px0 = wx0 + c % ww, py0 = wy0 + c / ww;
-        const int px1 = wx0 + c1i % ww, py1 = wy0 + c1i / ww;
-        if constexpr (Tr::kHalf) {
-            const h2 L2 = lik_half_pair<h2>(fv, sm.w, px0, py0, px1, py1, hk);
-            sm.table[c] = lo_h(L2);
-            if (c + 1 < cells) sm.table[c + 1] = hi_h(L2);
-        } else {
-            sm.table[c] = lik_from_sum<acc_t>(disk_sum(fv, sm.w, px0, py0), c1, c2D, den);
-            if (c + 1 < cells) sm.table[c + 1] = lik_from_sum<acc_t>(disk_sum(fv, sm.w, px1, py1), c1, c2D, den);
+    // ------------------------------------------------------------ likelihood table
+    if (cells > 0) {
+        // stage the frame region the window's templates cover (clamped to the frame)
+        const int rx0 = wx0 - r, ry0 = wy0 - r, rw = ww + 2 * r, rh = wh + 2 * r;
+        for (int i = tid; i < rw * rh; i += kThreads) {
+            const int yy = i / rw, xx = i - yy * rw;
+            const uint32_t I = fv.at(rx0 + xx, ry0 + yy);
+            if constexpr (Tr::kHalf) sm.u.term[i] = hk.term(I);
+            else sm.pix[i] = static_cast<uint8_t>(I);
         }
-    }
-    __syncthreads();
-
-    // ------------------------------------------------------------ 2-4. offspring
-    pos_t *Xout = static_cast<pos_t *>(T.px[out]);
-    pos_t *Yout = static_cast<pos_t *>(T.py[out]);
-    lik_t *Lout = static_cast<lik_t *>(T.pl[out]);
-    const uint32_t tctr = static_cast<uint32_t>(t);
-    Stats<acc_t> stats{neg_inf<acc_t>(), 0, 0, 0};
-
-    // ancestor shift for offsets (previous anchor minus the current one)
-    const double shx = axa - nxa, shy = aya - nya;
-
-    for (int64_t q = (jbeg >> 1) + tid; q < ((jend + 1) >> 1); q += kThreads) {
-        const int64_t j0 = 2 * q, j1 = j0 + 1;
-        const bool v0 = j0 >= jbeg && j0 < jend;
-        const bool v1 = j1 >= jbeg && j1 < jend;
-        int e0 = 0, e1 = 0;
-        if (t > 0) {
-            if (v0) e0 = upper_index(sm.J, cnt, j0);
-            if (v1) e1 = (v0 && static_cast<int64_t>(sm.J[e0]) > j1) ? e0 : upper_index(sm.J, cnt, j1);
-            if (!v0) e0 = e1;
-            if (!v1) e1 = e0;
-            if (T.dbg_anc) {
-                if (v0) T.dbg_anc[j0] = static_cast<int32_t>(k0 + e0);
-                if (v1) T.dbg_anc[j1] = static_cast<int32_t>(k0 + e1);
+        __syncthreads();
+        if constexpr (!Tr::kHalf) {
+            // exclusive row prefix sums: pre[y * (rw + 1) + x] = sum of pix[y][0..x-1]
+            for (int yy = tid; yy < rh; yy += kThreads) {
+                uint32_t acc = 0;
+                uint16_t *p = sm.u.pre + yy * (rw + 1);
+                const uint8_t *q = sm.pix + yy * rw;
+                p[0] = 0;
+                for (int xx = 0; xx < rw; ++xx) { acc += q[xx]; p[xx + 1] = static_cast<uint16_t>(acc); }
+            }
+            __syncthreads();
+        }
+        for (int c = tid; c < cells; c += kThreads) {
+            const int cy = c / ww, cx = c - cy * ww;
+            if constexpr (Tr::kHalf) {
+                sm.table[c] = hk.from_terms(sm.u.term, rw, sm.w, r, cx, cy);
+            } else {
+                uint32_t ssum = 0;
+                for (int i = 0; i <= 2 * r; ++i) {
+                    const uint16_t *p = sm.u.pre + (cy + i) * (rw + 1) + cx + r;
+                    const int hw = sm.w[i];
+                    ssum += static_cast<uint32_t>(static_cast<uint16_t>(p[hw + 1] - p[-hw]));
+                }
+                sm.table[c] = lik_from_sum<acc_t>(ssum, c1, c2D, den);
             }
         }
-        const uint4 w0 = philox4x32_10(make_uint4(static_cast<uint32_t>(j0), tctr, 0u, T.tracker_id), T.key_lo, T.key_hi);
-        const uint4 w1 = philox4x32_10(make_uint4(static_cast<uint32_t>(j1), tctr, 0u, T.tracker_id), T.key_lo, T.key_hi);
+        __syncthreads();
+    }
+
+    // ------------------------------------------------------------ ancestor map
+    // map[j - jb] = 1 + tile element that is the ancestor of offspring j: a head at the
+    // first offspring of every element with offspring, then a running max fills the gaps.
+    const bool use_map = (t > 0) && nout <= kMapMax;
+    if (use_map) {
+        for (int i = tid; i < nout; i += kThreads) sm.u.map[i] = 0;
+        __syncthreads();
+#pragma unroll
+        for (int m = 0; m < kItems; ++m) {
+            const int e = tid * kItems + m;
+            if (e < cnt) {
+                const int jp = e ? sm.J[e - 1] : jb;
+                if (sm.J[e] > jp) sm.u.map[jp - jb] = static_cast<uint16_t>(e + 1);
+            }
+        }
+        __syncthreads();
+        const int ch = (nout + kThreads - 1) / kThreads;
+        const int i0 = tid * ch, i1 = min(nout, i0 + ch);
+        int run = 0;
+        for (int i = i0; i < i1; ++i) run = max(run, static_cast<int>(sm.u.map[i]));
+        int xm = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, xm, o);
+            if (lane >= o) xm = max(xm, y);
+        }
+        if (lane == 31) sm.warp_imax[warp] = xm;
+        int xex = __shfl_up_sync(0xffffffffu, xm, 1);
+        if (lane == 0) xex = 0;
+        __syncthreads();
+        for (int w = 0; w < warp; ++w) xex = max(xex, sm.warp_imax[w]);
+        run = xex;
+        for (int i = i0; i < i1; ++i) {
+            run = max(run, static_cast<int>(sm.u.map[i]));
+            sm.u.map[i] = static_cast<uint16_t>(run);
+        }
+        __syncthreads();
+    }
+
+    // ------------------------------------------------------------ 2-4. offspring
+    pos_t *__restrict__ Xout = static_cast<pos_t *>(T.px[out]);
+    pos_t *__restrict__ Yout = static_cast<pos_t *>(T.py[out]);
+    lik_t *__restrict__ Lout = static_cast<lik_t *>(T.pl[out]);
+    const uint32_t tctr = static_cast<uint32_t>(t);
+    Stats<acc_t> stats{neg_inf<acc_t>(), 0, 0, 0};
+    const acc_t nxa_a = static_cast<acc_t>(nxa), nya_a = static_cast<acc_t>(nya);
+    const int axi = static_cast<int>(nxa), ayi = static_cast<int>(nya);
+    // offsets: the ancestors' anchor minus the offspring's anchor (integers)
+    const float shx = static_cast<float>(axa - nxa), shy = static_cast<float>(aya - nya);
+    const float ix0 = static_cast<float>(init_x - nxa), iy0 = static_cast<float>(init_y - nya);
+
+    for (int q = (jb >> 1) + tid; q < ((je + 1) >> 1); q += kThreads) {
+        const int j0 = 2 * q, j1 = j0 + 1;
+        const bool v0 = j0 >= jb && j0 < je;
+        const bool v1 = j1 >= jb && j1 < je;
+        int e0 = 0, e1 = 0;
+        if (t > 0) {
+            if (use_map) {
+                e0 = v0 ? static_cast<int>(sm.u.map[j0 - jb]) - 1 : 0;
+                e1 = v1 ? static_cast<int>(sm.u.map[j1 - jb]) - 1 : 0;
+            } else {
+                if (v0) e0 = upper_index(sm.J, cnt, j0);
+                if (v1) e1 = (v0 && sm.J[e0] > j1) ? e0 : upper_index(sm.J, cnt, j1);
+            }
+            if (!v0) e0 = e1;
+            if (!v1) e1 = e0;
+            if (dbg_anc) {
+                if (v0) dbg_anc[j0] = k0 + e0;
+                if (v1) dbg_anc[j1] = k0 + e1;
+            }
+        }
+        // one Philox block per particle pair: words (x, y) for j0, (z, w) for j1
+        const uint4 wd = philox4x32_10(make_uint4(static_cast<uint32_t>(q), tctr, 0u, trk_id), key_lo, key_hi);
 
         if constexpr (!Tr::kHalf) {
             // ---------------- REF64 / F32: absolute positions, exact-integer likelihood
             acc_t xa0, ya0, xa1, ya1;
             if (t > 0) { xa0 = sm.ax[e0]; ya0 = sm.ay[e0]; xa1 = sm.ax[e1]; ya1 = sm.ay[e1]; }
             else {
-                xa0 = xa1 = static_cast<acc_t>(T.init_x);
-                ya0 = ya1 = static_cast<acc_t>(T.init_y);
+                xa0 = xa1 = static_cast<acc_t>(init_x);
+                ya0 = ya1 = static_cast<acc_t>(init_y);
             }
             acc_t n0x, n0y, n1x, n1y;
             if constexpr (sizeof(acc_t) == 8) {
-                box_muller(uniform_f64(w0.x), uniform_f64(w0.y), n0x, n0y);
-                box_muller(uniform_f64(w1.x), uniform_f64(w1.y), n1x, n1y);
+                box_muller(uniform_f64(wd.x), uniform_f64(wd.y), n0x, n0y);
+                box_muller(uniform_f64(wd.z), uniform_f64(wd.w), n1x, n1y);
             } else {
-                box_muller(uniform_f32(w0.x), uniform_f32(w0.y), n0x, n0y);
-                box_muller(uniform_f32(w1.x), uniform_f32(w1.y), n1x, n1y);
+                box_muller(uniform_f32(wd.x), uniform_f32(wd.y), n0x, n0y);
+                box_muller(uniform_f32(wd.z), uniform_f32(wd.w), n1x, n1y);
             }
-            const acc_t dxm = static_cast<acc_t>(T.drift_x), dym = static_cast<acc_t>(T.drift_y);
-            const acc_t sgx = static_cast<acc_t>(T.sigma_x), sgy = static_cast<acc_t>(T.sigma_y);
             const acc_t x0 = add_rn(add_rn(xa0, dxm), mul_rn(sgx, n0x));
             const acc_t y0 = add_rn(add_rn(ya0, dym), mul_rn(sgy, n0y));
             const acc_t x1 = add_rn(add_rn(xa1, dxm), mul_rn(sgx, n1x));
@@ -713,57 +846,50 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
             } else if (v1) {
                 Xout[j1] = x1; Yout[j1] = y1; Lout[j1] = L1;
             }
-            if (v0) stats_add(stats, L0, x0 - static_cast<acc_t>(nxa), y0 - static_cast<acc_t>(nya));
-            if (v1) stats_add(stats, L1, x1 - static_cast<acc_t>(nxa), y1 - static_cast<acc_t>(nya));
+            if (v0) stats_add(stats, L0, x0 - nxa_a, y0 - nya_a);
+            if (v1) stats_add(stats, L1, x1 - nxa_a, y1 - nya_a);
         } else {
             // ---------------- F16 / BF16: half2 lanes = particles (j0, j1), offsets from the anchor
+            using OPS = HalfOps<H>;
+            using h2 = typename OPS::h2;
             h2 ox, oy;
             if (t > 0) {
-                ox = make2(sm.ax[e0], sm.ax[e1]);
-                oy = make2(sm.ay[e0], sm.ay[e1]);
-                const float sx = static_cast<float>(shx), sy = static_cast<float>(shy);
-                if (sx != 0.0f || sy != 0.0f) {
-                    ox = __hadd2(ox, f2_to2<h2>(sx, sx));
-                    oy = __hadd2(oy, f2_to2<h2>(sy, sy));
+                ox = OPS::pack(sm.ax[e0], sm.ax[e1]);
+                oy = OPS::pack(sm.ay[e0], sm.ay[e1]);
+                if (shx != 0.0f || shy != 0.0f) {
+                    ox = __hadd2(ox, OPS::from_f2(shx, shx));
+                    oy = __hadd2(oy, OPS::from_f2(shy, shy));
                 }
             } else {
-                const float ix = static_cast<float>(T.init_x - nxa), iy = static_cast<float>(T.init_y - nya);
-                ox = f2_to2<h2>(ix, ix);
-                oy = f2_to2<h2>(iy, iy);
+                ox = OPS::from_f2(ix0, ix0);
+                oy = OPS::from_f2(iy0, iy0);
             }
             float a, b, c, d;
-            box_muller(uniform_f32(w0.x), uniform_f32(w0.y), a, b);
-            box_muller(uniform_f32(w1.x), uniform_f32(w1.y), c, d);
-            const float dxm = static_cast<float>(T.drift_x), dym = static_cast<float>(T.drift_y);
-            const float sgx = static_cast<float>(T.sigma_x), sgy = static_cast<float>(T.sigma_y);
-            ox = __hadd2(ox, f2_to2<h2>(dxm + sgx * a, dxm + sgx * c));
-            oy = __hadd2(oy, f2_to2<h2>(dym + sgy * b, dym + sgy * d));
-            const int axi = static_cast<int>(nxa), ayi = static_cast<int>(nya);
-            const int px0 = axi + pixel_of(lo_f(ox)), py0 = ayi + pixel_of(lo_f(oy));
-            const int px1 = axi + pixel_of(hi_f(ox)), py1 = ayi + pixel_of(hi_f(oy));
+            box_muller_fast(uniform_f32(wd.x), uniform_f32(wd.y), a, b);
+            box_muller_fast(uniform_f32(wd.z), uniform_f32(wd.w), c, d);
+            ox = __hadd2(ox, OPS::from_f2(dxm + sgx * a, dxm + sgx * c));
+            oy = __hadd2(oy, OPS::from_f2(dym + sgy * b, dym + sgy * d));
+            const int px0 = axi + pixel_of(OPS::lo(ox)), py0 = ayi + pixel_of(OPS::lo(oy));
+            const int px1 = axi + pixel_of(OPS::hi(ox)), py1 = ayi + pixel_of(OPS::hi(oy));
             const unsigned cx0 = static_cast<unsigned>(px0 - wx0), cy0 = static_cast<unsigned>(py0 - wy0);
             const unsigned cx1 = static_cast<unsigned>(px1 - wx0), cy1 = static_cast<unsigned>(py1 - wy0);
             const bool in0 = cx0 < static_cast<unsigned>(ww) && cy0 < static_cast<unsigned>(wh);
             const bool in1 = cx1 < static_cast<unsigned>(ww) && cy1 < static_cast<unsigned>(wh);
-            lik_t l0 = in0 ? sm.table[cy0 * ww + cx0] : lik_t{};
-            lik_t l1 = in1 ? sm.table[cy1 * ww + cx1] : lik_t{};
-            if ((v0 && !in0) || (v1 && !in1)) {
-                const h2 Ld = lik_half_pair<h2>(fv, sm.w, px0, py0, px1, py1, hk);
-                if (!in0) l0 = lo_h(Ld);
-                if (!in1) l1 = hi_h(Ld);
-            }
-            const h2 L2 = make2(l0, l1);
+            H l0 = in0 ? sm.table[cy0 * ww + cx0] : OPS::from_f(0.0f);
+            H l1 = in1 ? sm.table[cy1 * ww + cx1] : OPS::from_f(0.0f);
+            if (v0 && !in0) l0 = hk.at(fv, sm.w, px0, py0);
+            if (v1 && !in1) l1 = hk.at(fv, sm.w, px1, py1);
             if (v0 && v1) {
                 reinterpret_cast<h2 *>(Xout)[q] = ox;
                 reinterpret_cast<h2 *>(Yout)[q] = oy;
-                reinterpret_cast<h2 *>(Lout)[q] = L2;
+                reinterpret_cast<h2 *>(Lout)[q] = OPS::pack(l0, l1);
             } else if (v0) {
-                Xout[j0] = lo_h(ox); Yout[j0] = lo_h(oy); Lout[j0] = l0;
+                Xout[j0] = OPS::lo_h(ox); Yout[j0] = OPS::lo_h(oy); Lout[j0] = l0;
             } else if (v1) {
-                Xout[j1] = hi_h(ox); Yout[j1] = hi_h(oy); Lout[j1] = l1;
+                Xout[j1] = OPS::hi_h(ox); Yout[j1] = OPS::hi_h(oy); Lout[j1] = l1;
             }
-            if (v0) stats_add(stats, to_acc(l0), lo_f(ox), lo_f(oy));
-            if (v1) stats_add(stats, to_acc(l1), hi_f(ox), hi_f(oy));
+            if (v0) stats_add(stats, OPS::to_f(l0), OPS::lo(ox), OPS::lo(oy));
+            if (v1) stats_add(stats, OPS::to_f(l1), OPS::hi(ox), OPS::hi(oy));
         }
     }
 
@@ -775,16 +901,20 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
         p->s = static_cast<double>(tot.s);
         p->sx = static_cast<double>(tot.sx);
         p->sy = static_cast<double>(tot.sy);
-        __threadfence();
-        const uint32_t prev = atomicAdd(T.done, 1u);
-        sm.last = (prev == static_cast<uint32_t>(T.ntiles - 1)) ? 1u : 0u;
+        // release: the partial is visible before the count; acquire: the last tile sees all
+        const uint32_t prev = atom_add_acq_rel(T.done, 1u);
+        sm.last = (prev == static_cast<uint32_t>(ntiles - 1)) ? 1u : 0u;
     }
     __syncthreads();
     if (sm.last) finalize_tracker<P>(T, st, sm);
 }
 
+#ifndef PF_STEP_MIN_BLOCKS
+#define PF_STEP_MIN_BLOCKS 2   // CTAs per SM the register allocation must allow
+#endif
+
 template <int P>
-__global__ void __launch_bounds__(kThreads) step_kernel(const StepLaunch Lp) {
+__global__ void __launch_bounds__(kThreads, PF_STEP_MIN_BLOCKS) step_kernel(const StepLaunch Lp) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StepSmem<P> &sm = *reinterpret_cast<StepSmem<P> *>(smem_raw);
     for (;;) {

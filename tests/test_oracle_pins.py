@@ -75,6 +75,23 @@ def test_philox_matches_curand_host_generator(seed, offset_blocks):
     assert np.array_equal(got, words)
 
 
+def test_propagation_draw_mapping():
+    """One Philox block per particle pair: particle j uses block j // 2 (counter word 0),
+    words 2(j % 2) and 2(j % 2) + 1, frame t in word 1, tag 0, tracker id in word 3."""
+    seed, t, trk = 77, 5, 3
+    n = 1001
+    nx, ny = oracle.normals(seed, t, n, tracker=trk, start=10)
+    j = np.arange(10, 10 + n)
+    ctr = np.stack([(j // 2).astype(np.uint32), np.full(n, t, np.uint32), np.zeros(n, np.uint32),
+                    np.full(n, trk, np.uint32)], axis=1)
+    w = oracle.philox(ctr, seed)
+    h = 2 * (j % 2)
+    ua = oracle.uniform(w[np.arange(n), h])
+    ub = oracle.uniform(w[np.arange(n), h + 1])
+    bx, by = oracle.box_muller(ua, ub)
+    assert np.array_equal(nx, bx) and np.array_equal(ny, by)
+
+
 def test_philox_counter_words_all_matter():
     base = np.array([[5, 6, 7, 8]], np.uint32)
     ref = oracle.philox(base, 42)
