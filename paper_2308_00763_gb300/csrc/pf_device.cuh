@@ -193,6 +193,33 @@ __device__ __forceinline__ U128 to_fixed(double v) {
     return r;
 }
 
+// Non-negative finite float -> floor(v * 2^90).
+__device__ __forceinline__ U128 to_fixed(float v) {
+    U128 r{0ull, 0ull};
+    if (!(v > 0.0f)) return r;
+    const uint32_t bits = __float_as_uint(v);
+    const int ex = static_cast<int>((bits >> 23) & 0xff);
+    if (ex == 0) return r;  // subnormal: far below 2^-90
+    const uint64_t mant = (bits & 0x7fffffu) | 0x800000u;  // 24 bits
+    const int sh = ex - 150 + kFixShift;   // v * 2^90 = mant * 2^sh
+    if (sh <= -24) return r;
+    if (sh < 0) { r.lo = mant >> (-sh); return r; }
+    if (sh == 0) { r.lo = mant; return r; }
+    if (sh < 64) { r.lo = mant << sh; r.hi = mant >> (64 - sh); return r; }
+    r.hi = mant << (sh - 64);
+    return r;
+}
+
+// Fixed point -> float: the top 64 significant bits rounded to nearest (monotone,
+// deterministic); no FP64 instruction.
+__device__ __forceinline__ float from_fixed_f(U128 x) {
+    if (x.hi == 0ull) return __ull2float_rn(x.lo) * 8.0779356694631609e-28f;   // 2^-90
+    const int lz = __clzll(static_cast<long long>(x.hi));
+    const uint64_t top = (x.hi << lz) | (lz ? (x.lo >> (64 - lz)) : 0ull);
+    const int e2 = 64 - lz - kFixShift;                     // value = top * 2^e2, e2 in [-26, 38]
+    return __ull2float_rn(top) * __int_as_float((127 + e2) << 23);
+}
+
 // Fixed point -> double: the top 64 significant bits rounded to nearest; monotone
 // non-decreasing and deterministic, which is all the scan boundaries rely on.
 __device__ __forceinline__ double from_fixed(U128 x) {

@@ -46,6 +46,9 @@ struct alignas(16) TrackerState {
     double ax, ay;         // integer anchor of the stored positions (frame t-1)
     double nx, ny;         // integer anchor the next step writes against
     double est_x, est_y;   // estimate of frame t-1
+    // the same scalars for the FP32 kernels (no FP64 instruction on their path)
+    float M_f, invS_f;
+    int32_t axi, ayi, nxi, nyi;
 };
 
 struct FrameRef {
@@ -70,6 +73,9 @@ struct TrackerDev {
     double inv_n;              // 1.0 / N
     float inv_n_f;             // 1.0f / (float)N
     float pad2;
+    // FP32 copies for the FP32 kernels
+    float init_xf, init_yf, drift_xf, drift_yf, sigma_xf, sigma_yf;
+    float c1f, c2Df, denf, pad3;
     void *px[2], *py[2], *pl[2];
     int32_t *dbg_anc;          // NULL unless PF_FLAG_DEBUG_ARRAYS
     void *dbg_cdf;
@@ -84,6 +90,7 @@ struct TrackerDev {
 // Launch of one step over a batch of trackers of one precision.
 struct StepLaunch {
     const TrackerDev *trk;     // device array [ntrk]
+    TrackerState *states;      // device array [ntrk] (trk[i].state == states + i)
     const FrameRef *frames;    // device array [ntrk]
     const int32_t *tile_trk;   // device array [total_tiles]: tracker of each tile
     uint32_t *ticket;          // device counter, 0 between launches

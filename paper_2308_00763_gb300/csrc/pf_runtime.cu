@@ -56,6 +56,16 @@ struct Arena {
     }
 };
 
+// Fill the FP32 / integer copies of the state scalars from the FP64 ones.
+void state_copies(TrackerState &s) {
+    s.M_f = static_cast<float>(s.M);
+    s.invS_f = static_cast<float>(s.invS);
+    s.axi = static_cast<int32_t>(s.ax);
+    s.ayi = static_cast<int32_t>(s.ay);
+    s.nxi = static_cast<int32_t>(s.nx);
+    s.nyi = static_cast<int32_t>(s.ny);
+}
+
 }  // namespace
 
 // A set of trackers of one precision, stepped by one launch.
@@ -130,6 +140,8 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
     Arena a;
     struct Off { size_t px[2], py[2], pl[2], look, part, done, state, est, stat, dbga, dbgc; };
     std::vector<Off> off(n);
+    // the trackers' states form one array (the kernel indexes it by tracker)
+    const size_t states_off = a.take(sizeof(TrackerState) * n);
     int64_t tiles = 0;
     for (int i = 0; i < n; ++i) {
         const pf_config &c = cfgs[i];
@@ -146,7 +158,7 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
         o.look = a.take(sizeof(LookbackDesc) * nt);
         o.part = a.take(sizeof(TilePartial) * nt);
         o.done = a.take(sizeof(uint32_t));
-        o.state = a.take(sizeof(TrackerState));
+        o.state = states_off + sizeof(TrackerState) * i;
         o.est = a.take(sizeof(double) * 2 * cap);
         o.stat = a.take(sizeof(double) * 2 * cap);
         if (c.flags & PF_FLAG_DEBUG_ARRAYS) {
@@ -177,6 +189,12 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
         T.drift_x = c.drift_x; T.drift_y = c.drift_y;
         T.inv_n = 1.0 / static_cast<double>(N);
         T.inv_n_f = 1.0f / static_cast<float>(N);
+        T.init_xf = static_cast<float>(c.init_x); T.init_yf = static_cast<float>(c.init_y);
+        T.drift_xf = static_cast<float>(c.drift_x); T.drift_yf = static_cast<float>(c.drift_y);
+        T.sigma_xf = static_cast<float>(c.sigma_x); T.sigma_yf = static_cast<float>(c.sigma_y);
+        T.c1f = static_cast<float>(T.c1);
+        T.c2Df = static_cast<float>(T.c2 * T.D);
+        T.denf = static_cast<float>(T.den);
         tiles += nt;
     }
     e.total_tiles = static_cast<int>(tiles);
@@ -232,6 +250,7 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
         s.ay = s.ny = round_half_up(e.cfg[i].init_y);
         s.est_x = e.cfg[i].init_x;
         s.est_y = e.cfg[i].init_y;
+        state_copies(s);
         e.h_frames[i].active = 1;
     }
     err = cudaMemcpyAsync(e.d_trk, e.h_trk.data(), sizeof(TrackerDev) * n, cudaMemcpyHostToDevice, e.stream);
@@ -256,6 +275,7 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
 static pf_status engine_launch(Engine &e, const uint8_t *override_frame, int64_t override_pitch) {
     StepLaunch L;
     L.trk = e.d_trk;
+    L.states = e.h_trk[0].state;
     L.frames = e.d_frames;
     L.tile_trk = e.d_tile_trk;
     L.ticket = e.d_ticket;
@@ -481,6 +501,7 @@ pf_status pf_set_state(pf_filter *f, const void *host_buf, size_t bytes) {
     st.ny = h.next_anchor_y;
     st.est_x = h.est_x;
     st.est_y = h.est_y;
+    state_copies(st);
     const char *p = static_cast<const char *>(host_buf) + sizeof h;
     const int slot = static_cast<int>((h.t + 1) & 1);
     const size_t nb = pb * static_cast<size_t>(T.N);

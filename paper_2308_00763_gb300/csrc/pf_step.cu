@@ -302,7 +302,10 @@ struct __align__(16) StepSmem {
     int8_t w[2 * kMaxRadius + 1];
     uint32_t ticket;
     uint32_t last;
-    uint32_t skip;
+    int cached;               // tracker whose descriptor / state / frame are loaded below
+    TrackerDev trk;
+    TrackerState st;
+    FrameRef fr;
 };
 
 // Block-wide merge of per-thread stats in a fixed order; result valid in thread 0.
@@ -403,8 +406,14 @@ __device__ void finalize_tracker(const TrackerDev &T, TrackerState *st, StepSmem
         st->invS = static_cast<double>(static_cast<acc_t>(1) / r.s);
         st->ax = st->nx;
         st->ay = st->ny;
-        if (isfinite(ex) && fabs(ex) < 1.0e9) st->nx = floor(ex) + ((ex - floor(ex)) >= 0.5 ? 1.0 : 0.0);
-        if (isfinite(ey) && fabs(ey) < 1.0e9) st->ny = floor(ey) + ((ey - floor(ey)) >= 0.5 ? 1.0 : 0.0);
+        if (isfinite(ex) && fabs(ex) < 1.0e6) st->nx = floor(ex) + ((ex - floor(ex)) >= 0.5 ? 1.0 : 0.0);
+        if (isfinite(ey) && fabs(ey) < 1.0e6) st->ny = floor(ey) + ((ey - floor(ey)) >= 0.5 ? 1.0 : 0.0);
+        st->M_f = static_cast<float>(r.m);
+        st->invS_f = static_cast<float>(static_cast<acc_t>(1) / r.s);
+        st->axi = st->nxi;
+        st->ayi = st->nyi;
+        st->nxi = static_cast<int32_t>(st->nx);
+        st->nyi = static_cast<int32_t>(st->ny);
         st->est_x = ex;
         st->est_y = ey;
         const int64_t slot = t % T.est_cap;
@@ -428,42 +437,48 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int ti = (Lp.ntrk == 1) ? 0 : __ldg(&Lp.tile_trk[g]);
-    const TrackerDev &T = Lp.trk[ti];
-    const FrameRef fr = Lp.frames[ti];
-    if (!fr.active) return;
-    TrackerState *const st = T.state;
+    TrackerState *const st = Lp.states + ti;
 
-    // ---- parameters into registers (the output stores must not force reloads)
+    // ---- the tracker's descriptor, state and frame reference, loaded in one round trip
+    // and kept for the CTA's later tiles of the same tracker (none of them changes
+    // before the tracker's last tile of this launch has finished)
+    if (ti != sm.cached) {
+        const uint32_t *src_t = reinterpret_cast<const uint32_t *>(Lp.trk + ti);
+        const uint32_t *src_s = reinterpret_cast<const uint32_t *>(st);
+        const uint32_t *src_f = reinterpret_cast<const uint32_t *>(Lp.frames + ti);
+        uint32_t *dt = reinterpret_cast<uint32_t *>(&sm.trk);
+        uint32_t *ds = reinterpret_cast<uint32_t *>(&sm.st);
+        uint32_t *df = reinterpret_cast<uint32_t *>(&sm.fr);
+        constexpr int nt = sizeof(TrackerDev) / 4, ns = sizeof(TrackerState) / 4, nf = sizeof(FrameRef) / 4;
+        for (int i = tid; i < nt + ns + nf; i += kThreads) {
+            if (i < nt) dt[i] = __ldg(src_t + i);
+            else if (i < nt + ns) ds[i - nt] = __ldcg(src_s + i - nt);
+            else df[i - nt - ns] = __ldcg(src_f + i - nt - ns);
+        }
+        __syncthreads();
+        if (tid == 0) sm.cached = ti;
+    }
+    const TrackerDev &T = sm.trk;
+    if (!sm.fr.active) return;
+    if (sm.st.status & kStatusTimeout) return;   // a failed step: results are invalid
+
     const int N = static_cast<int>(T.N);
     const int lt = g - T.tile_begin;
-    const int ntiles = T.ntiles;
     const int k0 = lt * kTile;
     const int cnt = (N - k0) < kTile ? (N - k0) : kTile;
-    const uint32_t key_lo = T.key_lo, key_hi = T.key_hi, trk_id = T.tracker_id, flags = T.flags;
-    int32_t *const dbg_anc = T.dbg_anc;
-    acc_t *const dbg_cdf = static_cast<acc_t *>(T.dbg_cdf);
-    const double init_x = T.init_x, init_y = T.init_y;
-    const acc_t dxm = static_cast<acc_t>(T.drift_x), dym = static_cast<acc_t>(T.drift_y);
-    const acc_t sgx = static_cast<acc_t>(T.sigma_x), sgy = static_cast<acc_t>(T.sigma_y);
-    const acc_t c1 = static_cast<acc_t>(T.c1), c2D = static_cast<acc_t>(T.c2 * T.D);
-    const acc_t den = static_cast<acc_t>(T.den);
-    const acc_t inv_n = sizeof(acc_t) == 8 ? static_cast<acc_t>(T.inv_n) : static_cast<acc_t>(T.inv_n_f);
-    LookbackDesc *const look = T.look;
-
-    // a failed step: results are invalid, skip without waiting (decided once per block)
-    if (tid == 0) sm.skip = timed_out(st) ? 1u : 0u;
-    __syncthreads();
-    if (sm.skip) return;
-    const int64_t t = __ldcg(&st->t);
-    const uint32_t ep = __ldcg(&st->epoch);
-    const double nxa = __ldcg(&st->nx), nya = __ldcg(&st->ny);   // anchor of the offspring
-    const double axa = __ldcg(&st->ax), aya = __ldcg(&st->ay);   // anchor of the ancestors
+    const int64_t t = sm.st.t;
+    const uint32_t ep = sm.st.epoch;
+    constexpr bool kF64 = sizeof(acc_t) == 8;    // REF64; the other kernels use no FP64
+    const int nxi = sm.st.nxi, nyi = sm.st.nyi;     // anchor of the offspring
+    const int axi_anc = sm.st.axi, ayi_anc = sm.st.ayi;   // anchor of the ancestors
     const int in = static_cast<int>((t + 1) & 1), out = static_cast<int>(t & 1);
+    acc_t *const dbg_cdf = static_cast<acc_t *>(T.dbg_cdf);
+    LookbackDesc *const look = T.look;
 
     FrameView fv;
     fv.W = T.W; fv.H = T.H; fv.r = T.r;
     if (Lp.frame_override) { fv.p = Lp.frame_override; fv.pitch = Lp.pitch_override; }
-    else { fv.p = fr.base + (fr.stride ? t * fr.stride : 0); fv.pitch = fr.pitch; }
+    else { fv.p = sm.fr.base + (sm.fr.stride ? t * sm.fr.stride : 0); fv.pitch = sm.fr.pitch; }
     const int r = fv.r;
     for (int i = tid; i <= 2 * r; i += kThreads) {
         const int dy = i - r;
@@ -472,13 +487,15 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
         sm.w[i] = static_cast<int8_t>(w);
     }
 
-    // ------------------------------------------------------------ 1. resampling
+    // ------------------------------------------------------------ 1a. local scan of e
+    acc_t loc[kItems];
+    uint32_t heavy = 0u;          // bit m: element tid*kItems+m carries a non-negligible weight
+    U128 aggx{0ull, 0ull};
     if (t > 0) {
         const lik_t *__restrict__ Lin = static_cast<const lik_t *>(T.pl[in]);
         const pos_t *__restrict__ Xin = static_cast<const pos_t *>(T.px[in]);
         const pos_t *__restrict__ Yin = static_cast<const pos_t *>(T.py[in]);
-        const acc_t M = static_cast<acc_t>(__ldcg(&st->M));
-        const acc_t invS = static_cast<acc_t>(__ldcg(&st->invS));
+        const acc_t M = kF64 ? static_cast<acc_t>(sm.st.M) : static_cast<acc_t>(sm.st.M_f);
         for (int e = tid; e < cnt; e += kThreads) {
             sm.ax[e] = Xin[k0 + e];
             sm.ay[e] = Yin[k0 + e];
@@ -499,15 +516,15 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
                 lv[m] = (e < cnt) ? Lin[k0 + e] : lik_t{};
             }
         }
-        acc_t s[kItems];
         acc_t run = static_cast<acc_t>(0);
 #pragma unroll
         for (int m = 0; m < kItems; ++m) {
             const int e = tid * kItems + m;
             acc_t v = static_cast<acc_t>(0);
             if (e < cnt) v = exp_le0(to_acc(lv[m]) - M);
+            if (v > static_cast<acc_t>(9.3132257461547852e-10)) heavy |= 1u << m;   // 2^-30
             run = (m == 0) ? v : run + v;
-            s[m] = run;
+            loc[m] = run;
         }
         // block exclusive scan of the thread totals
         acc_t x = run;
@@ -523,9 +540,10 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
         acc_t wpre = static_cast<acc_t>(0);
         for (int w = 0; w < warp; ++w) wpre += sm.warp_sum[w];
         const acc_t off = wpre + xex;
-        acc_t loc[kItems];
+        if (tid != 0) {
 #pragma unroll
-        for (int m = 0; m < kItems; ++m) loc[m] = (tid == 0) ? s[m] : off + s[m];
+            for (int m = 0; m < kItems; ++m) loc[m] = off + loc[m];
+        }
         // running max across threads: makes the tile-local prefix non-decreasing
         acc_t mx = loc[kItems - 1];
 #pragma unroll
@@ -551,8 +569,7 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
             }
         }
         __syncthreads();
-        const acc_t agg = sm.agg;
-        const U128 aggx = to_fixed(static_cast<double>(agg));
+        aggx = to_fixed(sm.agg);
         const uint32_t tag = (ep & 0x3fffffffu) << 2;
         if (tid == 0) {
             if (lt == 0) {
@@ -565,82 +582,30 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
                 st_release_u32(&look[lt].flag, tag | 1u);
             }
         }
-        U128 exclx{0ull, 0ull};
-        if (lt > 0) exclx = lookback<P>(look, lt, ep, st, sm);
-        if (tid == 0) {
-            const U128 endx = add128(exclx, aggx);
-            if (lt > 0) {
-                look[lt].incl_lo = endx.lo;
-                look[lt].incl_hi = endx.hi;
-                st_release_u32(&look[lt].flag, tag | 2u);
-            }
-            sm.excl_x = exclx;
-            sm.end_x = endx;
-        }
-        __syncthreads();
-        // Prefix of the tile's elements: FP inside the tile, pinned to the exact fixed-point
-        // values at both tile boundaries, so neighbouring tiles see the same boundary.
-        const acc_t excl = static_cast<acc_t>(from_fixed(sm.excl_x));
-        const acc_t pend = static_cast<acc_t>(from_fixed(sm.end_x));
-        const acc_t u0 = static_cast<acc_t>(uniform_f64(
-            philox4x32_10(make_uint4(0u, static_cast<uint32_t>(t - 1), 1u, trk_id), key_lo, key_hi).x));
-        Strata<acc_t> str;
-        str.init(N, u0, inv_n);
-        acc_t cprev = static_cast<acc_t>(-1);
-        int jprev = 0;
-#pragma unroll
-        for (int m = 0; m < kItems; ++m) {
-            const int e = tid * kItems + m;
-            if (e < cnt) {
-                const int k = k0 + e;
-                const acc_t Pk = (e == cnt - 1) ? pend : fmin(add_rn(excl, loc[m]), pend);
-                // the normalised CDF cannot exceed 1; the FP32 scan can round above it
-                acc_t C = fmin(mul_rn(Pk, invS), static_cast<acc_t>(1));
-                int J;
-                if (k == N - 1) { C = static_cast<acc_t>(1); J = N; }
-                else if (C == cprev) J = jprev;          // same CDF value, same count
-                else J = str.count_le(C);
-                cprev = C;
-                jprev = J;
-                sm.J[e] = J;
-                if (dbg_cdf) dbg_cdf[k] = C;
-            }
-        }
-        if (tid == 0) sm.jbeg = (lt == 0) ? 0 : str.count_le(fmin(mul_rn(excl, invS), static_cast<acc_t>(1)));
-        __syncthreads();
-        if (tid == 0) sm.jend = sm.J[cnt - 1];
-        __syncthreads();
-    } else {
-        if (tid == 0) { sm.jbeg = k0; sm.jend = k0 + cnt; }
-        __syncthreads();
     }
-    const int jb = sm.jbeg, je = sm.jend;
-    const int nout = je - jb;
 
-    // ------------------------------------------------------------ likelihood window
-    // Bounding box of the ancestors that have offspring (absolute pixel units), widened by
-    // the drift and the largest draw; the offspring's pixels fall inside it.
+    // ------------------------------------------------------------ 1b. likelihood window
+    // Bounding box of the ancestors with non-negligible weight (absolute pixel units),
+    // widened by the drift and the largest draw: their offspring's pixels fall inside it.
+    // Computed before the lookback, so that the predecessors publish meanwhile.
     {
         float bx0 = FLT_MAX, bx1 = -FLT_MAX, by0 = FLT_MAX, by1 = -FLT_MAX;
         if (t > 0) {
-            const float sx = Tr::kHalf ? static_cast<float>(axa) : 0.0f;
-            const float sy = Tr::kHalf ? static_cast<float>(aya) : 0.0f;
+            const float sx = Tr::kHalf ? static_cast<float>(axi_anc) : 0.0f;
+            const float sy = Tr::kHalf ? static_cast<float>(ayi_anc) : 0.0f;
 #pragma unroll
             for (int m = 0; m < kItems; ++m) {
-                const int e = tid * kItems + m;
-                if (e < cnt) {
-                    const int jp = e ? sm.J[e - 1] : jb;
-                    if (sm.J[e] > jp) {
-                        const float xv = static_cast<float>(to_acc(sm.ax[e])) + sx;
-                        const float yv = static_cast<float>(to_acc(sm.ay[e])) + sy;
-                        bx0 = fminf(bx0, xv); bx1 = fmaxf(bx1, xv);
-                        by0 = fminf(by0, yv); by1 = fmaxf(by1, yv);
-                    }
+                if (heavy & (1u << m)) {
+                    const int e = tid * kItems + m;
+                    const float xv = static_cast<float>(to_acc(sm.ax[e])) + sx;
+                    const float yv = static_cast<float>(to_acc(sm.ay[e])) + sy;
+                    bx0 = fminf(bx0, xv); bx1 = fmaxf(bx1, xv);
+                    by0 = fminf(by0, yv); by1 = fmaxf(by1, yv);
                 }
             }
         } else {
-            bx0 = bx1 = static_cast<float>(init_x);
-            by0 = by1 = static_cast<float>(init_y);
+            bx0 = bx1 = T.init_xf;
+            by0 = by1 = T.init_yf;
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -656,8 +621,8 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
                 bx0 = fminf(bx0, sm.box[w][0]); bx1 = fmaxf(bx1, sm.box[w][1]);
                 by0 = fminf(by0, sm.box[w][2]); by1 = fmaxf(by1, sm.box[w][3]);
             }
-            const float mxr = fabsf(static_cast<float>(dxm)) + kMaxNormal * static_cast<float>(sgx) + 1.0f;
-            const float myr = fabsf(static_cast<float>(dym)) + kMaxNormal * static_cast<float>(sgy) + 1.0f;
+            const float mxr = fabsf(T.drift_xf) + kMaxNormal * T.sigma_xf + 1.0f;
+            const float myr = fabsf(T.drift_yf) + kMaxNormal * T.sigma_yf + 1.0f;
             int ww = 0, wh = 0, x0 = 0, y0 = 0;
             if (bx0 <= bx1 && by0 <= by1 && bx1 - bx0 < 4096.0f && by1 - by0 < 4096.0f &&
                 fabsf(bx0) < 1.0e6f && fabsf(by0) < 1.0e6f && mxr < 4096.0f && myr < 4096.0f) {
@@ -667,7 +632,7 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
                 wh = static_cast<int>(ceilf(by1 + myr)) - y0 + 1;
                 const int64_t cells = static_cast<int64_t>(ww) * wh;
                 const int64_t roi = static_cast<int64_t>(ww + 2 * r + 1) * (wh + 2 * r);
-                if (cells > kTableMax || cells > nout || roi > kRoiMax) { ww = 0; wh = 0; }
+                if (cells > kTableMax || cells > cnt || roi > kRoiMax) { ww = 0; wh = 0; }
             }
             sm.win_x0 = x0; sm.win_y0 = y0; sm.win_w = ww; sm.win_h = wh;
         }
@@ -683,10 +648,13 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
         hk.kap = HalfOps<H>::from_f(T.kappa);
         hk.bgo = HalfOps<H>::from_f(lo + T.bg_f);
         hk.fgo = HalfOps<H>::from_f(lo + T.fg_f);
-        hk.half_acc = std::is_same<pos_t, __half>::value && !(flags & 0x2u);
+        hk.half_acc = std::is_same<pos_t, __half>::value && !(T.flags & 0x2u);
     }
+    const acc_t c1 = kF64 ? static_cast<acc_t>(T.c1) : static_cast<acc_t>(T.c1f);
+    const acc_t c2D = kF64 ? static_cast<acc_t>(T.c2 * T.D) : static_cast<acc_t>(T.c2Df);
+    const acc_t den = kF64 ? static_cast<acc_t>(T.den) : static_cast<acc_t>(T.denf);
 
-    // ------------------------------------------------------------ likelihood table
+    // ------------------------------------------------------------ 1c. likelihood table
     if (cells > 0) {
         // stage the frame region the window's templates cover (clamped to the frame)
         const int rx0 = wx0 - r, ry0 = wy0 - r, rw = ww + 2 * r, rh = wh + 2 * r;
@@ -725,7 +693,64 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
         __syncthreads();
     }
 
-    // ------------------------------------------------------------ ancestor map
+    // ------------------------------------------------------------ 1d. lookback, CDF, strata
+    if (t > 0) {
+        const acc_t invS = kF64 ? static_cast<acc_t>(sm.st.invS) : static_cast<acc_t>(sm.st.invS_f);
+        const uint32_t w0 =
+            philox4x32_10(make_uint4(0u, static_cast<uint32_t>(t - 1), 1u, T.tracker_id), T.key_lo, T.key_hi).x;
+        const acc_t u0 = kF64 ? static_cast<acc_t>(uniform_f64(w0)) : static_cast<acc_t>(uniform_f32(w0));
+        Strata<acc_t> str;
+        str.init(N, u0, sizeof(acc_t) == 8 ? static_cast<acc_t>(T.inv_n) : static_cast<acc_t>(T.inv_n_f));
+        U128 exclx{0ull, 0ull};
+        if (lt > 0) exclx = lookback<P>(look, lt, ep, st, sm);
+        if (tid == 0) {
+            const U128 endx = add128(exclx, aggx);
+            if (lt > 0) {
+                look[lt].incl_lo = endx.lo;
+                look[lt].incl_hi = endx.hi;
+                st_release_u32(&look[lt].flag, ((ep & 0x3fffffffu) << 2) | 2u);
+            }
+            sm.excl_x = exclx;
+            sm.end_x = endx;
+        }
+        __syncthreads();
+        // Prefix of the tile's elements: FP inside the tile, pinned to the exact fixed-point
+        // values at both tile boundaries, so neighbouring tiles see the same boundary.
+        acc_t excl, pend;
+        if constexpr (kF64) { excl = from_fixed(sm.excl_x); pend = from_fixed(sm.end_x); }
+        else { excl = from_fixed_f(sm.excl_x); pend = from_fixed_f(sm.end_x); }
+        acc_t cprev = static_cast<acc_t>(-1);
+        int jprev = 0;
+#pragma unroll
+        for (int m = 0; m < kItems; ++m) {
+            const int e = tid * kItems + m;
+            if (e < cnt) {
+                const int k = k0 + e;
+                const acc_t Pk = (e == cnt - 1) ? pend : fmin(add_rn(excl, loc[m]), pend);
+                // the normalised CDF cannot exceed 1; the FP32 scan can round above it
+                acc_t C = fmin(mul_rn(Pk, invS), static_cast<acc_t>(1));
+                int J;
+                if (k == N - 1) { C = static_cast<acc_t>(1); J = N; }
+                else if (C == cprev) J = jprev;          // same CDF value, same count
+                else J = str.count_le(C);
+                cprev = C;
+                jprev = J;
+                sm.J[e] = J;
+                if (dbg_cdf) dbg_cdf[k] = C;
+            }
+        }
+        if (tid == 0) sm.jbeg = (lt == 0) ? 0 : str.count_le(fmin(mul_rn(excl, invS), static_cast<acc_t>(1)));
+        __syncthreads();
+        if (tid == 0) sm.jend = sm.J[cnt - 1];
+        __syncthreads();
+    } else {
+        if (tid == 0) { sm.jbeg = k0; sm.jend = k0 + cnt; }
+        __syncthreads();
+    }
+    const int jb = sm.jbeg, je = sm.jend;
+    const int nout = je - jb;
+
+    // ------------------------------------------------------------ 1e. ancestor map
     // map[j - jb] = 1 + tile element that is the ancestor of offspring j: a head at the
     // first offspring of every element with offspring, then a running max fills the gaps.
     const bool use_map = (t > 0) && nout <= kMapMax;
@@ -768,13 +793,19 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
     pos_t *__restrict__ Xout = static_cast<pos_t *>(T.px[out]);
     pos_t *__restrict__ Yout = static_cast<pos_t *>(T.py[out]);
     lik_t *__restrict__ Lout = static_cast<lik_t *>(T.pl[out]);
+    int32_t *__restrict__ dbg_anc = T.dbg_anc;
     const uint32_t tctr = static_cast<uint32_t>(t);
+    const uint32_t trk_id = T.tracker_id, key_lo = T.key_lo, key_hi = T.key_hi;
     Stats<acc_t> stats{neg_inf<acc_t>(), 0, 0, 0};
-    const acc_t nxa_a = static_cast<acc_t>(nxa), nya_a = static_cast<acc_t>(nya);
-    const int axi = static_cast<int>(nxa), ayi = static_cast<int>(nya);
+    const acc_t nxa_a = static_cast<acc_t>(nxi), nya_a = static_cast<acc_t>(nyi);
+    const int axi = nxi, ayi = nyi;
+    const acc_t dxm = kF64 ? static_cast<acc_t>(T.drift_x) : static_cast<acc_t>(T.drift_xf);
+    const acc_t dym = kF64 ? static_cast<acc_t>(T.drift_y) : static_cast<acc_t>(T.drift_yf);
+    const acc_t sgx = kF64 ? static_cast<acc_t>(T.sigma_x) : static_cast<acc_t>(T.sigma_xf);
+    const acc_t sgy = kF64 ? static_cast<acc_t>(T.sigma_y) : static_cast<acc_t>(T.sigma_yf);
     // offsets: the ancestors' anchor minus the offspring's anchor (integers)
-    const float shx = static_cast<float>(axa - nxa), shy = static_cast<float>(aya - nya);
-    const float ix0 = static_cast<float>(init_x - nxa), iy0 = static_cast<float>(init_y - nya);
+    const float shx = static_cast<float>(axi_anc - nxi), shy = static_cast<float>(ayi_anc - nyi);
+    const float ix0 = T.init_xf - static_cast<float>(nxi), iy0 = T.init_yf - static_cast<float>(nyi);
 
     for (int q = (jb >> 1) + tid; q < ((je + 1) >> 1); q += kThreads) {
         const int j0 = 2 * q, j1 = j0 + 1;
@@ -804,8 +835,8 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
             acc_t xa0, ya0, xa1, ya1;
             if (t > 0) { xa0 = sm.ax[e0]; ya0 = sm.ay[e0]; xa1 = sm.ax[e1]; ya1 = sm.ay[e1]; }
             else {
-                xa0 = xa1 = static_cast<acc_t>(init_x);
-                ya0 = ya1 = static_cast<acc_t>(init_y);
+                xa0 = xa1 = kF64 ? static_cast<acc_t>(T.init_x) : static_cast<acc_t>(T.init_xf);
+                ya0 = ya1 = kF64 ? static_cast<acc_t>(T.init_y) : static_cast<acc_t>(T.init_yf);
             }
             acc_t n0x, n0y, n1x, n1y;
             if constexpr (sizeof(acc_t) == 8) {
@@ -903,20 +934,24 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
         p->sy = static_cast<double>(tot.sy);
         // release: the partial is visible before the count; acquire: the last tile sees all
         const uint32_t prev = atom_add_acq_rel(T.done, 1u);
-        sm.last = (prev == static_cast<uint32_t>(ntiles - 1)) ? 1u : 0u;
+        sm.last = (prev == static_cast<uint32_t>(T.ntiles - 1)) ? 1u : 0u;
     }
     __syncthreads();
     if (sm.last) finalize_tracker<P>(T, st, sm);
 }
 
-#ifndef PF_STEP_MIN_BLOCKS
-#define PF_STEP_MIN_BLOCKS 2   // CTAs per SM the register allocation must allow
-#endif
+// CTAs per SM the register allocation must allow (measured best per precision on GB300:
+// the step is latency-bound, so the FP16/BF16 kernels trade a few spills for 4 CTAs/SM).
+template <int P> struct MinBlocks { static constexpr int value = 2; };
+template <> struct MinBlocks<1> { static constexpr int value = 3; };
+template <> struct MinBlocks<2> { static constexpr int value = 4; };
+template <> struct MinBlocks<3> { static constexpr int value = 4; };
 
 template <int P>
-__global__ void __launch_bounds__(kThreads, PF_STEP_MIN_BLOCKS) step_kernel(const StepLaunch Lp) {
+__global__ void __launch_bounds__(kThreads, MinBlocks<P>::value) step_kernel(const StepLaunch Lp) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StepSmem<P> &sm = *reinterpret_cast<StepSmem<P> *>(smem_raw);
+    if (threadIdx.x == 0) sm.cached = -1;
     for (;;) {
         if (threadIdx.x == 0) sm.ticket = atomicAdd(Lp.ticket, 1u);
         __syncthreads();
