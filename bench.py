@@ -134,13 +134,16 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+KERNEL_SOURCES = ("pf_step.cu", "pf_device.cuh", "pf_internal.h")
+
+
 def _kernel_source_hash():
+    """Hash of the sources that define the step kernel (the runtime does not change it)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2308_00763_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(f.read())
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 

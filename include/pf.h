@@ -100,7 +100,9 @@ pf_status pf_step_frame(pf_filter *f, const uint8_t *frame, int64_t pitch_bytes,
 
 /* Run `count` frames in one call: frame i at frames + i * frame_stride (bytes), rows
  * pitch_bytes apart, all on the host (frames_on_device = 0) or all on the device (1).
- * Equivalent to `count` calls of pf_step_frame.  Asynchronous. */
+ * Equivalent to `count` calls of pf_step_frame.  With device frames the `count` steps
+ * are replayed from a CUDA graph captured on the first call with this count.
+ * Asynchronous. */
 pf_status pf_run_frames(pf_filter *f, const uint8_t *frames, int64_t pitch_bytes,
                         int64_t frame_stride, int32_t count, int32_t frames_on_device);
 
@@ -174,6 +176,17 @@ pf_status pf_debug_philox(const uint32_t *ctrs, int64_t n, uint64_t seed, uint32
 pf_status pf_batch_create(const pf_config *cfgs, int32_t n, void *cuda_stream, pf_batch **out);
 pf_status pf_batch_step(pf_batch *b, const uint8_t *const *frames, const int64_t *pitches,
                         const uint8_t *active_mask);
+/* Resident videos: tracker i reads its next frame at videos[i] (device), later frames
+ * frame_strides[i] bytes apart, rows pitches[i] bytes apart (every video must hold all
+ * the frames that pf_batch_run will step).  Asynchronous. */
+pf_status pf_batch_set_videos(pf_batch *b, const uint8_t *const *videos, const int64_t *pitches,
+                              const int64_t *frame_strides);
+/* Step every tracker `count` frames through its resident video: one launch per frame,
+ * replayed from a CUDA graph captured on the first call with this count.  Asynchronous. */
+pf_status pf_batch_run(pf_batch *b, int32_t count);
+/* Restart every tracker at frame 0 (as after pf_batch_create); resident videos restart
+ * at their first frame.  Asynchronous. */
+pf_status pf_batch_reset(pf_batch *b);
 /* Estimates of frame `frame_index` of every tracker into xy[2*n] (host); trackers that
  * have not stepped that frame get NaN.  Synchronises. */
 pf_status pf_batch_estimates(pf_batch *b, int64_t frame_index, double *xy);

@@ -22,6 +22,7 @@ __all__ = [
     "pf_status_string", "pf_create", "pf_step_frame", "pf_run_frames", "pf_estimate",
     "pf_estimates", "pf_frames_done", "pf_reset", "pf_destroy", "pf_get_state", "pf_set_state", "pf_get_debug",
     "pf_debug_philox", "pf_batch_create", "pf_batch_step", "pf_batch_estimates",
+    "pf_batch_set_videos", "pf_batch_run", "pf_batch_reset",
     "pf_batch_destroy", "Filter", "Batch", "PRECISIONS", "EXPORTED",
 ]
 
@@ -84,6 +85,9 @@ _SIG = {
     "pf_batch_create": (ctypes.c_int, [ctypes.POINTER(PfConfig), _I32, _P, ctypes.POINTER(_P)]),
     "pf_batch_step": (ctypes.c_int, [_P, _P, _P, _P]),
     "pf_batch_estimates": (ctypes.c_int, [_P, _I64, _P]),
+    "pf_batch_set_videos": (ctypes.c_int, [_P, _P, _P, _P]),
+    "pf_batch_run": (ctypes.c_int, [_P, _I32]),
+    "pf_batch_reset": (ctypes.c_int, [_P]),
     "pf_batch_destroy": (ctypes.c_int, [_P]),
 }
 EXPORTED = tuple(_SIG)
@@ -220,6 +224,22 @@ def pf_batch_estimates(h, n: int, t: int) -> np.ndarray:
     xy = np.empty((n, 2), np.float64)
     _check(lib().pf_batch_estimates(h, t, xy.ctypes.data_as(_P)), "pf_batch_estimates")
     return xy
+
+
+def pf_batch_set_videos(h, video_ptrs, pitches, strides):
+    n = len(video_ptrs)
+    vp = (ctypes.c_void_p * n)(*video_ptrs)
+    pp = (ctypes.c_int64 * n)(*pitches)
+    sp = (ctypes.c_int64 * n)(*strides)
+    return lib().pf_batch_set_videos(h, vp, pp, sp)
+
+
+def pf_batch_run(h, count: int):
+    return lib().pf_batch_run(h, count)
+
+
+def pf_batch_reset(h):
+    return lib().pf_batch_reset(h)
 
 
 def pf_batch_destroy(h):
@@ -369,6 +389,18 @@ class Batch:
         ptrs = [f.data_ptr() if f is not None else 0 for f in frames]
         pitches = [f.stride(0) if f is not None else 0 for f in frames]
         _check(pf_batch_step(self.h, ptrs, pitches, active), "pf_batch_step")
+
+    def set_videos(self, videos):
+        """videos: list of CUDA uint8 tensors (T_i, H_i, W_i), resident for pf_batch_run."""
+        self._videos = list(videos)
+        _check(pf_batch_set_videos(self.h, [v.data_ptr() for v in videos], [v.stride(1) for v in videos],
+                                   [v.stride(0) for v in videos]), "pf_batch_set_videos")
+
+    def run(self, count):
+        _check(pf_batch_run(self.h, count), "pf_batch_run")
+
+    def reset(self):
+        _check(pf_batch_reset(self.h), "pf_batch_reset")
 
     def estimates(self, t):
         return pf_batch_estimates(self.h, self.n, t)

@@ -88,6 +88,10 @@ struct Engine {
     pf_status sticky = PF_OK;
     uint8_t *d_frame_buf = nullptr;    // single tracker: staging of host frames
     TrackerState *h_init_pinned = nullptr;  // initial state of every tracker (pf_reset)
+    cudaEvent_t frames_copied = nullptr;     // the pinned frame table may be rewritten after it
+    cudaStream_t capture_stream = nullptr;   // private stream used to capture step graphs
+    cudaGraphExec_t graph = nullptr;         // `graph_count` consecutive steps, replayed
+    int graph_count = 0;
     int64_t frame_buf_pitch = 0;
 
     pf_status fail(pf_status s) {
@@ -105,7 +109,11 @@ struct pf_batch {
 };
 
 static void engine_free(Engine &e) {
-    if (e.stream || true) cudaStreamSynchronize(e.stream);
+    cudaStreamSynchronize(e.stream);
+    if (e.graph) cudaGraphExecDestroy(e.graph);
+    if (e.capture_stream) cudaStreamDestroy(e.capture_stream);
+    if (e.frames_copied) cudaEventDestroy(e.frames_copied);
+    e.graph = nullptr; e.capture_stream = nullptr; e.frames_copied = nullptr; e.graph_count = 0;
     cudaFree(e.d_trk);
     cudaFree(e.d_frames);
     cudaFree(e.d_tile_trk);
@@ -209,6 +217,8 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
     if (err == cudaSuccess) err = cudaMalloc(reinterpret_cast<void **>(&e.d_ticket), sizeof(uint32_t));
     if (err == cudaSuccess) err = cudaMallocHost(reinterpret_cast<void **>(&e.h_frames_pinned), sizeof(FrameRef) * n);
     if (err == cudaSuccess) err = cudaMallocHost(reinterpret_cast<void **>(&e.h_init_pinned), sizeof(TrackerState) * n);
+    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&e.frames_copied, cudaEventDisableTiming);
+    if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&e.capture_stream, cudaStreamNonBlocking);
     if (err == cudaSuccess && stage_frames) {
         e.frame_buf_pitch = (cfgs[0].width + 15) & ~15;
         err = cudaMalloc(reinterpret_cast<void **>(&e.d_frame_buf), static_cast<size_t>(e.frame_buf_pitch) * cfgs[0].height);
@@ -288,6 +298,54 @@ static pf_status engine_launch(Engine &e, const uint8_t *override_frame, int64_t
     return PF_OK;
 }
 
+// Upload the frame table (pinned staging -> device) on the handle's stream.  The staging
+// copy is only rewritten once the previous upload has been consumed.
+static pf_status engine_upload_frames(Engine &e) {
+    cudaError_t err = cudaMemcpyAsync(e.d_frames, e.h_frames_pinned, sizeof(FrameRef) * e.n,
+                                      cudaMemcpyHostToDevice, e.stream);
+    if (err == cudaSuccess) err = cudaEventRecord(e.frames_copied, e.stream);
+    if (err != cudaSuccess) { cudaGetLastError(); return e.fail(PF_ERR_CUDA); }
+    return PF_OK;
+}
+
+static pf_status engine_wait_staging(Engine &e) {
+    if (cudaEventSynchronize(e.frames_copied) != cudaSuccess) { cudaGetLastError(); return e.fail(PF_ERR_CUDA); }
+    return PF_OK;
+}
+
+// `count` steps that read their frames through the frame table (base + t * stride), as
+// one CUDA graph of identical kernel nodes, captured once per count and replayed.
+static pf_status engine_run_resident(Engine &e, int32_t count) {
+    if (count <= 0) return PF_OK;
+    if (!e.graph || e.graph_count != count) {
+        if (e.graph) { cudaGraphExecDestroy(e.graph); e.graph = nullptr; e.graph_count = 0; }
+        StepLaunch L;
+        L.trk = e.d_trk;
+        L.states = e.h_trk[0].state;
+        L.frames = e.d_frames;
+        L.tile_trk = e.d_tile_trk;
+        L.ticket = e.d_ticket;
+        L.ntrk = e.n;
+        L.total_tiles = e.total_tiles;
+        L.frame_override = nullptr;
+        L.pitch_override = 0;
+        cudaGraph_t g = nullptr;
+        cudaError_t err = cudaStreamBeginCapture(e.capture_stream, cudaStreamCaptureModeThreadLocal);
+        int rc = 0;
+        for (int32_t i = 0; i < count && err == cudaSuccess && rc == 0; ++i)
+            rc = launch_step(e.prec, L, e.grid, e.capture_stream);
+        const cudaError_t end = cudaStreamEndCapture(e.capture_stream, &g);
+        if (err == cudaSuccess) err = end;
+        if (err == cudaSuccess && rc != 0) err = cudaErrorLaunchFailure;
+        if (err == cudaSuccess) err = cudaGraphInstantiate(&e.graph, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (err != cudaSuccess) { cudaGetLastError(); e.graph = nullptr; return e.fail(PF_ERR_CUDA); }
+        e.graph_count = count;
+    }
+    if (cudaGraphLaunch(e.graph, e.stream) != cudaSuccess) { cudaGetLastError(); return e.fail(PF_ERR_CUDA); }
+    return PF_OK;
+}
+
 static pf_status engine_sync_status(Engine &e) {
     if (e.sticky != PF_OK) return e.sticky;
     cudaError_t err = cudaStreamSynchronize(e.stream);
@@ -362,10 +420,31 @@ pf_status pf_step_frame(pf_filter *f, const uint8_t *frame, int64_t pitch_bytes,
 pf_status pf_run_frames(pf_filter *f, const uint8_t *frames, int64_t pitch_bytes, int64_t frame_stride,
                         int32_t count, int32_t frames_on_device) {
     if (!f || !frames || count < 0) return PF_ERR_ARG;
-    for (int32_t i = 0; i < count; ++i) {
-        pf_status s = pf_step_frame(f, frames + static_cast<int64_t>(i) * frame_stride, pitch_bytes, frames_on_device);
-        if (s != PF_OK) return s;
+    Engine &e = f->e;
+    if (e.sticky != PF_OK) return PF_ERR_STATE;
+    if (pitch_bytes < e.cfg[0].width) return PF_ERR_ARG;
+    if (!frames_on_device) {
+        for (int32_t i = 0; i < count; ++i) {
+            pf_status s = pf_step_frame(f, frames + static_cast<int64_t>(i) * frame_stride, pitch_bytes, 0);
+            if (s != PF_OK) return s;
+        }
+        return PF_OK;
     }
+    if (count == 0) return PF_OK;
+    // Device frames: the kernel finds frame t at base + t * stride, with base chosen so
+    // that the tracker's next frame (t = frames done) is `frames`; then `count` identical
+    // steps replay as one graph.
+    pf_status s = engine_wait_staging(e);
+    if (s != PF_OK) return s;
+    FrameRef &fr = e.h_frames_pinned[0];
+    fr.base = frames - e.done_frames[0] * frame_stride;
+    fr.pitch = pitch_bytes;
+    fr.stride = frame_stride;
+    fr.active = 1;
+    s = engine_upload_frames(e);
+    if (s == PF_OK) s = engine_run_resident(e, count);
+    if (s != PF_OK) return s;
+    e.done_frames[0] += count;
     return PF_OK;
 }
 
@@ -560,25 +639,79 @@ pf_status pf_batch_step(pf_batch *b, const uint8_t *const *frames, const int64_t
     if (!b || !frames || !pitches) return PF_ERR_ARG;
     Engine &e = b->e;
     if (e.sticky != PF_OK) return PF_ERR_STATE;
-    // the pinned staging copy of the frame table may still be read by the previous copy
-    cudaError_t err = cudaStreamSynchronize(e.stream);
-    if (err != cudaSuccess) { cudaGetLastError(); return e.fail(PF_ERR_CUDA); }
     for (int i = 0; i < e.n; ++i) {
         const int act = active_mask ? (active_mask[i] != 0) : 1;
         if (act && (!frames[i] || pitches[i] < e.cfg[i].width)) return PF_ERR_ARG;
+    }
+    pf_status s = engine_wait_staging(e);
+    if (s != PF_OK) return s;
+    for (int i = 0; i < e.n; ++i) {
+        const int act = active_mask ? (active_mask[i] != 0) : 1;
         FrameRef &fr = e.h_frames_pinned[i];
         fr.base = act ? frames[i] : nullptr;
         fr.pitch = act ? pitches[i] : 0;
         fr.stride = 0;
         fr.active = act;
     }
-    err = cudaMemcpyAsync(e.d_frames, e.h_frames_pinned, sizeof(FrameRef) * e.n, cudaMemcpyHostToDevice, e.stream);
-    if (err != cudaSuccess) { cudaGetLastError(); return e.fail(PF_ERR_CUDA); }
-    pf_status s = engine_launch(e, nullptr, 0);
+    s = engine_upload_frames(e);
+    if (s == PF_OK) s = engine_launch(e, nullptr, 0);
     if (s != PF_OK) return s;
     for (int i = 0; i < e.n; ++i)
         if (e.h_frames_pinned[i].active) e.done_frames[i] += 1;
     return PF_OK;
+}
+
+pf_status pf_batch_set_videos(pf_batch *b, const uint8_t *const *videos, const int64_t *pitches,
+                              const int64_t *frame_strides) {
+    if (!b || !videos || !pitches || !frame_strides) return PF_ERR_ARG;
+    Engine &e = b->e;
+    if (e.sticky != PF_OK) return PF_ERR_STATE;
+    for (int i = 0; i < e.n; ++i)
+        if (!videos[i] || pitches[i] < e.cfg[i].width || frame_strides[i] < pitches[i] * e.cfg[i].height)
+            return PF_ERR_ARG;
+    pf_status s = engine_wait_staging(e);
+    if (s != PF_OK) return s;
+    for (int i = 0; i < e.n; ++i) {
+        FrameRef &fr = e.h_frames_pinned[i];
+        fr.base = videos[i] - e.done_frames[i] * frame_strides[i];
+        fr.pitch = pitches[i];
+        fr.stride = frame_strides[i];
+        fr.active = 1;
+    }
+    return engine_upload_frames(e);
+}
+
+pf_status pf_batch_run(pf_batch *b, int32_t count) {
+    if (!b || count < 0) return PF_ERR_ARG;
+    Engine &e = b->e;
+    if (e.sticky != PF_OK) return PF_ERR_STATE;
+    for (int i = 0; i < e.n; ++i)
+        if (!e.h_frames_pinned[i].active || e.h_frames_pinned[i].stride == 0) return PF_ERR_STATE;
+    pf_status s = engine_run_resident(e, count);
+    if (s != PF_OK) return s;
+    for (int i = 0; i < e.n; ++i) e.done_frames[i] += count;
+    return PF_OK;
+}
+
+pf_status pf_batch_reset(pf_batch *b) {
+    if (!b) return PF_ERR_ARG;
+    Engine &e = b->e;
+    if (e.sticky != PF_OK) return PF_ERR_STATE;
+    const size_t tail = sizeof(TrackerState) - offsetof(TrackerState, M);
+    pf_status s = engine_wait_staging(e);
+    if (s != PF_OK) return s;
+    for (int i = 0; i < e.n; ++i) {
+        TrackerState *d = e.h_trk[i].state;
+        const TrackerState *h = &e.h_init_pinned[i];
+        cudaError_t err = cudaMemcpyAsync(&d->t, &h->t, sizeof(int64_t), cudaMemcpyHostToDevice, e.stream);
+        if (err == cudaSuccess) err = cudaMemcpyAsync(&d->M, &h->M, tail, cudaMemcpyHostToDevice, e.stream);
+        if (err != cudaSuccess) { cudaGetLastError(); return e.fail(PF_ERR_CUDA); }
+        // resident videos: frame 0 is again the video's first frame
+        FrameRef &fr = e.h_frames_pinned[i];
+        if (fr.stride) fr.base += e.done_frames[i] * fr.stride;
+        e.done_frames[i] = 0;
+    }
+    return engine_upload_frames(e);
 }
 
 pf_status pf_batch_estimates(pf_batch *b, int64_t frame_index, double *xy) {

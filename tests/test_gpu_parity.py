@@ -297,3 +297,48 @@ def test_full_size_config2_step_sampled(pf, prec):
     rng = np.random.default_rng(0)
     sample = np.unique(np.concatenate([rng.integers(0, 1 << 20, 4000), [0, (1 << 20) - 1]]))
     _check_step(pf, prec, 1 << 20, v, 2, seed=1, sample=sample)
+
+
+def test_run_in_chunks_equals_one_run(pf):
+    """Device-frame runs replay a captured graph; splitting a run (and mixing in single
+    steps) must give the same bits."""
+    torch = _torch()
+    v = synth.make_video(128, 128, 10, 5, noise=5.0, seed=16)
+    fr = torch.from_numpy(v.frames).cuda()
+    for prec in ("f32", "f16"):
+        a = pf.Filter(v.W, v.H, 5000, 5, prec, init=tuple(v.centres[0]), seed=8)
+        a.run(fr)
+        b = pf.Filter(v.W, v.H, 5000, 5, prec, init=tuple(v.centres[0]), seed=8)
+        b.run(fr[:3])
+        b.step(fr[3])
+        b.run(fr[4:7])
+        b.run(fr[7:])
+        assert np.array_equal(a.estimates(0, 10), b.estimates(0, 10)), prec
+        a.reset()
+        a.run(fr)
+        assert np.array_equal(a.estimates(0, 10), b.estimates(0, 10)), prec
+
+
+def test_batch_resident_videos_equal_single_trackers(pf):
+    torch = _torch()
+    vids = [synth.make_video(96, 80, 8, 3, noise=5.0, seed=40),
+            synth.make_video(200, 150, 8, 6, noise=5.0, seed=41, v=(-2, 1)),
+            synth.make_video(64, 64, 8, 2, noise=5.0, seed=42, v=(0.5, -0.5))]
+    Ns = [3000, 2 * TILE + 3, 1]
+    for prec in ("ref64", "f16"):
+        cfgs = [pf.make_config(v.W, v.H, n, v.radius, prec, init=tuple(v.centres[0]), seed=50 + i,
+                               tracker_id=i) for i, (v, n) in enumerate(zip(vids, Ns))]
+        b = pf.Batch(cfgs)
+        fr = [torch.from_numpy(v.frames).cuda() for v in vids]
+        b.set_videos(fr)
+        b.run(5)
+        b.run(3)
+        got = np.stack([b.estimates(t) for t in range(8)], axis=1)
+        for i, (v, n) in enumerate(zip(vids, Ns)):
+            s = pf.Filter(v.W, v.H, n, v.radius, prec, init=tuple(v.centres[0]), seed=50 + i, tracker_id=i)
+            s.run(fr[i])
+            assert np.array_equal(s.estimates(0, 8), got[i]), (prec, i)
+        b.reset()
+        b.run(8)
+        again = np.stack([b.estimates(t) for t in range(8)], axis=1)
+        assert np.array_equal(again, got), prec
