@@ -77,6 +77,7 @@ struct Engine {
     std::vector<TrackerDev> h_trk;     // host copy; device pointers inside
     std::vector<FrameRef> h_frames;
     std::vector<int64_t> done_frames;  // per tracker
+    std::vector<const uint8_t *> video_start;  // resident videos: first frame (pf_batch_reset)
     TrackerDev *d_trk = nullptr;
     FrameRef *d_frames = nullptr;
     FrameRef *h_frames_pinned = nullptr;
@@ -141,6 +142,7 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
     e.h_trk.assign(n, TrackerDev{});
     e.h_frames.assign(n, FrameRef{});
     e.done_frames.assign(n, 0);
+    e.video_start.assign(n, nullptr);
 
     // sizes
     const size_t pb = pos_bytes(e.prec);
@@ -652,6 +654,7 @@ pf_status pf_batch_step(pf_batch *b, const uint8_t *const *frames, const int64_t
         fr.pitch = act ? pitches[i] : 0;
         fr.stride = 0;
         fr.active = act;
+        e.video_start[i] = nullptr;
     }
     s = engine_upload_frames(e);
     if (s == PF_OK) s = engine_launch(e, nullptr, 0);
@@ -673,6 +676,7 @@ pf_status pf_batch_set_videos(pf_batch *b, const uint8_t *const *videos, const i
     if (s != PF_OK) return s;
     for (int i = 0; i < e.n; ++i) {
         FrameRef &fr = e.h_frames_pinned[i];
+        e.video_start[i] = videos[i];
         fr.base = videos[i] - e.done_frames[i] * frame_strides[i];
         fr.pitch = pitches[i];
         fr.stride = frame_strides[i];
@@ -708,7 +712,7 @@ pf_status pf_batch_reset(pf_batch *b) {
         if (err != cudaSuccess) { cudaGetLastError(); return e.fail(PF_ERR_CUDA); }
         // resident videos: frame 0 is again the video's first frame
         FrameRef &fr = e.h_frames_pinned[i];
-        if (fr.stride) fr.base += e.done_frames[i] * fr.stride;
+        if (fr.stride && e.video_start[i]) fr.base = e.video_start[i];
         e.done_frames[i] = 0;
     }
     return engine_upload_frames(e);
