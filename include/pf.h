@@ -167,6 +167,32 @@ pf_status pf_get_debug(pf_filter *f, int32_t which, void *host_buf, size_t bytes
  * out[4*i..] (host).  Synchronises the legacy default stream. */
 pf_status pf_debug_philox(const uint32_t *ctrs, int64_t n, uint64_t seed, uint32_t *out);
 
+/* One frame of the filter for callers that cannot allocate device memory: an engine or
+ * runtime that owns all CUDA memory and hands out buffers, a real-time loop that forbids
+ * allocation after start-up, or code that must not synchronise the device the way an
+ * allocation can.  The paper has no counterpart; this is a deployment form of
+ * pf_step_frame.  The caller owns every buffer (device pointers): the previous frame's
+ * particles x_in, y_in, l_in (ignored when state_in->t == 0) and the new frame's
+ * x_out, y_out, l_out (N elements each, in the precision's storage type, distinct from the
+ * inputs; F16/BF16 positions are offsets from the anchor in the header), and the frame
+ * (rows pitch_bytes apart).  state_in (host) carries the scalars of the previous frame in
+ * the pf_get_state header layout (t = 0: a fresh tracker); if state_out (host) is not NULL
+ * the call synchronises the stream and writes the new frame's scalars there (its t is
+ * state_in->t + 1, its est_x/est_y the estimate of this frame).
+ * Everything else the step needs (lookback descriptors, per-tile sums, counters, the
+ * tracker descriptor) lives in one 256 KiB array in the library's device memory, present
+ * on every GPU from the moment the library is loaded until the process exits; it limits
+ * num_particles to 2^22 (PF_ERR_ARG beyond).  The first call on each device looks up that
+ * array's address, so make it before any stream capture.  All calls share the array and
+ * clear what must start at zero themselves; calls whose GPU work overlaps (other streams,
+ * other threads) race on it and must be serialised by the caller.  No device or pinned
+ * memory is allocated.  Errors: PF_ERR_ARG, PF_ERR_CUDA, PF_ERR_TIMEOUT. */
+pf_status pf_step_frame_noalloc(const pf_config *cfg, const pf_state_header *state_in,
+                                const void *x_in, const void *y_in, const void *l_in,
+                                const uint8_t *frame, int64_t pitch_bytes,
+                                void *x_out, void *y_out, void *l_out,
+                                pf_state_header *state_out, void *cuda_stream);
+
 /* ---------------------------------------------------------------- batches
  * Many independent trackers (different N, frame sizes, radii, seeds), stepped together
  * by one persistent segmented launch per frame.  All trackers of a batch share one

@@ -22,7 +22,7 @@ __all__ = [
     "pf_status_string", "pf_create", "pf_step_frame", "pf_run_frames", "pf_estimate",
     "pf_estimates", "pf_frames_done", "pf_reset", "pf_destroy", "pf_get_state", "pf_set_state", "pf_get_debug",
     "pf_debug_philox", "pf_batch_create", "pf_batch_step", "pf_batch_estimates",
-    "pf_batch_set_videos", "pf_batch_run", "pf_batch_reset",
+    "pf_batch_set_videos", "pf_batch_run", "pf_batch_reset", "pf_step_frame_noalloc",
     "pf_batch_destroy", "Filter", "Batch", "PRECISIONS", "EXPORTED",
 ]
 
@@ -88,6 +88,8 @@ _SIG = {
     "pf_batch_set_videos": (ctypes.c_int, [_P, _P, _P, _P]),
     "pf_batch_run": (ctypes.c_int, [_P, _I32]),
     "pf_batch_reset": (ctypes.c_int, [_P]),
+    "pf_step_frame_noalloc": (ctypes.c_int, [ctypes.POINTER(PfConfig), _P, _P, _P, _P, _P, _I64,
+                                             _P, _P, _P, _P, _P]),
     "pf_batch_destroy": (ctypes.c_int, [_P]),
 }
 EXPORTED = tuple(_SIG)
@@ -240,6 +242,17 @@ def pf_batch_run(h, count: int):
 
 def pf_batch_reset(h):
     return lib().pf_batch_reset(h)
+
+
+def pf_step_frame_noalloc(cfg: PfConfig, state_in: "PfStateHeader", x_in: int, y_in: int, l_in: int,
+                          frame: int, pitch: int, x_out: int, y_out: int, l_out: int, stream=None):
+    """Allocation-free frame step on caller-owned device buffers (pointers as ints).
+    Returns the new frame's state header."""
+    out = PfStateHeader()
+    _check(lib().pf_step_frame_noalloc(ctypes.byref(cfg), ctypes.byref(state_in), _P(x_in), _P(y_in),
+                                       _P(l_in), _P(frame), pitch, _P(x_out), _P(y_out), _P(l_out),
+                                       ctypes.byref(out), _P(_stream_ptr(stream))), "pf_step_frame_noalloc")
+    return out
 
 
 def pf_batch_destroy(h):

@@ -1,0 +1,220 @@
+// pf_noalloc.cu -- pf_step_frame_noalloc: one frame of the filter for callers that
+// cannot allocate device memory.
+//
+// Some embedders cannot call cudaMalloc: a host program whose CUDA memory is owned and
+// budgeted by another runtime (a graphics or inference engine that hands out buffers), a
+// real-time loop that forbids allocation after start-up, or code running inside a
+// stream-ordered section where an allocation would synchronise the device.  They can still
+// provide their own input and output buffers; what the step needs beyond those (the
+// decoupled-lookback descriptors, per-tile partial sums, counters and the tracker's
+// descriptor) lives here, in a file-scope device array that exists in every GPU's memory
+// as soon as the library is loaded and stays there until the process exits.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stddef.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "pf.h"
+#include "pf_internal.h"
+
+using namespace pfk;
+
+namespace {
+
+constexpr size_t kScratchBytes = 256 * 1024;
+constexpr int kMaxTiles = 2048;                       // => at most 2^22 particles
+constexpr int kMaxDevices = 64;
+
+// The scratch array.  In host code its name is only a stand-in for the symbol; the
+// device address comes from cudaGetSymbolAddress (per device).
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+// Layout inside the scratch array.
+struct ScratchLayout {
+    size_t trk, state, frame, ticket, done, est, stat, look, part, end;
+};
+
+constexpr size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+constexpr ScratchLayout layout() {
+    ScratchLayout L{};
+    L.trk = 0;
+    L.state = align256(L.trk + sizeof(TrackerDev));
+    L.frame = align256(L.state + sizeof(TrackerState));
+    L.ticket = align256(L.frame + sizeof(FrameRef));
+    L.done = L.ticket + 16;
+    L.est = L.done + 16;
+    L.stat = L.est + 16;
+    L.look = align256(L.stat + 16);
+    L.part = align256(L.look + sizeof(LookbackDesc) * kMaxTiles);
+    L.end = L.part + sizeof(TilePartial) * kMaxTiles;
+    return L;
+}
+static_assert(layout().end <= kScratchBytes, "scratch layout exceeds the array");
+
+std::mutex g_lock;
+unsigned char *g_scratch_dev[kMaxDevices] = {};
+int g_grid[kMaxDevices][4] = {};
+
+double round_half_up(double v) { return floor(v) + ((v - floor(v)) >= 0.5 ? 1.0 : 0.0); }
+
+int disk_count(int r) {
+    int n = 0;
+    for (int dy = -r; dy <= r; ++dy)
+        for (int dx = -r; dx <= r; ++dx)
+            if (dx * dx + dy * dy <= r * r) ++n;
+    return n;
+}
+
+// Device address of the scratch array on the current device (looked up once per device).
+pf_status scratch_for_current_device(int *dev_out, unsigned char **ptr_out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return PF_ERR_CUDA; }
+    if (dev < 0 || dev >= kMaxDevices) return PF_ERR_ARG;
+    std::lock_guard<std::mutex> guard(g_lock);
+    if (!g_scratch_dev[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return PF_ERR_CUDA;
+        }
+        g_scratch_dev[dev] = static_cast<unsigned char *>(p);
+    }
+    *dev_out = dev;
+    *ptr_out = g_scratch_dev[dev];
+    return PF_OK;
+}
+
+}  // namespace
+
+extern "C" pf_status pf_step_frame_noalloc(const pf_config *cfg, const pf_state_header *state_in,
+                                           const void *x_in, const void *y_in, const void *l_in,
+                                           const uint8_t *frame, int64_t pitch_bytes,
+                                           void *x_out, void *y_out, void *l_out,
+                                           pf_state_header *state_out, void *cuda_stream) {
+    if (!cfg || !state_in || !frame || !x_out || !y_out || !l_out) return PF_ERR_ARG;
+    const pf_config &c = *cfg;
+    if (c.width < 1 || c.width > 65535 || c.height < 1 || c.height > 65535) return PF_ERR_ARG;
+    if (c.num_particles < 1 || c.num_particles > static_cast<int64_t>(kMaxTiles) * kTile) return PF_ERR_ARG;
+    if (c.disk_radius < 0 || c.disk_radius > kMaxRadius) return PF_ERR_ARG;
+    if (c.precision < PF_REF64 || c.precision > PF_BF16) return PF_ERR_ARG;
+    if (!(c.sigma_x >= 0) || !(c.sigma_y >= 0) || !isfinite(c.sigma_x) || !isfinite(c.sigma_y)) return PF_ERR_ARG;
+    if (!isfinite(c.init_x) || !isfinite(c.init_y) || fabs(c.init_x) > 1.0e6 || fabs(c.init_y) > 1.0e6) return PF_ERR_ARG;
+    if (!isfinite(c.drift_x) || !isfinite(c.drift_y) || !isfinite(c.bg_level) || !isfinite(c.fg_level)) return PF_ERR_ARG;
+    if (c.flags & ~PF_FLAG_ACCUM32) return PF_ERR_ARG;   // no debug arrays here
+    if (pitch_bytes < c.width) return PF_ERR_ARG;
+    const pf_state_header &h = *state_in;
+    if (h.magic != 0x31534650u || h.precision != c.precision || h.num_particles != c.num_particles || h.t < 0)
+        return PF_ERR_ARG;
+    if (h.t > 0 && (!x_in || !y_in || !l_in || !(h.sum_e > 0) || !isfinite(h.max_l))) return PF_ERR_ARG;
+
+    int dev = 0;
+    unsigned char *scr = nullptr;
+    pf_status s = scratch_for_current_device(&dev, &scr);
+    if (s != PF_OK) return s;
+    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    constexpr ScratchLayout LY = layout();
+
+    // descriptor of the tracker: the caller's buffers are the ping-pong slots of frame t
+    const int64_t N = c.num_particles;
+    const int nt = static_cast<int>((N + kTile - 1) / kTile);
+    const int in = static_cast<int>((h.t + 1) & 1), out = static_cast<int>(h.t & 1);
+    TrackerDev T;
+    memset(&T, 0, sizeof T);
+    T.N = N; T.W = c.width; T.H = c.height; T.r = c.disk_radius; T.D = disk_count(c.disk_radius);
+    T.tile_begin = 0; T.ntiles = nt;
+    T.key_lo = static_cast<uint32_t>(c.seed & 0xffffffffu); T.key_hi = static_cast<uint32_t>(c.seed >> 32);
+    T.tracker_id = c.tracker_id; T.flags = c.flags; T.est_cap = 1;
+    T.c1 = c.fg_level - c.bg_level; T.c2 = c.bg_level + c.fg_level; T.den = 50.0 * T.D;
+    T.kappa = static_cast<float>(1.0 / sqrt(50.0 * T.D));
+    T.bg_f = static_cast<float>(c.bg_level); T.fg_f = static_cast<float>(c.fg_level);
+    T.init_x = c.init_x; T.init_y = c.init_y; T.sigma_x = c.sigma_x; T.sigma_y = c.sigma_y;
+    T.drift_x = c.drift_x; T.drift_y = c.drift_y;
+    T.inv_n = 1.0 / static_cast<double>(N); T.inv_n_f = 1.0f / static_cast<float>(N);
+    T.init_xf = static_cast<float>(c.init_x); T.init_yf = static_cast<float>(c.init_y);
+    T.drift_xf = static_cast<float>(c.drift_x); T.drift_yf = static_cast<float>(c.drift_y);
+    T.sigma_xf = static_cast<float>(c.sigma_x); T.sigma_yf = static_cast<float>(c.sigma_y);
+    T.c1f = static_cast<float>(T.c1); T.c2Df = static_cast<float>(T.c2 * T.D); T.denf = static_cast<float>(T.den);
+    T.px[in] = const_cast<void *>(x_in); T.py[in] = const_cast<void *>(y_in); T.pl[in] = const_cast<void *>(l_in);
+    T.px[out] = x_out; T.py[out] = y_out; T.pl[out] = l_out;
+    T.look = reinterpret_cast<LookbackDesc *>(scr + LY.look);
+    T.part = reinterpret_cast<TilePartial *>(scr + LY.part);
+    T.done = reinterpret_cast<uint32_t *>(scr + LY.done);
+    T.state = reinterpret_cast<TrackerState *>(scr + LY.state);
+    T.est_ring = reinterpret_cast<double *>(scr + LY.est);
+    T.stat_ring = reinterpret_cast<double *>(scr + LY.stat);
+
+    // the scalars the step reads (frame 0: every particle at the initial position)
+    TrackerState st;
+    memset(&st, 0, sizeof st);
+    st.t = h.t;
+    st.epoch = 1;   // the lookback flags are cleared below, so any nonzero epoch works
+    if (h.t == 0) {
+        st.M = 0.0; st.S = 1.0;
+        st.ax = st.nx = round_half_up(c.init_x);
+        st.ay = st.ny = round_half_up(c.init_y);
+        st.est_x = c.init_x; st.est_y = c.init_y;
+    } else {
+        st.M = h.max_l; st.S = h.sum_e;
+        st.ax = h.anchor_x; st.ay = h.anchor_y; st.nx = h.next_anchor_x; st.ny = h.next_anchor_y;
+        st.est_x = h.est_x; st.est_y = h.est_y;
+    }
+    st.invS = c.precision == PF_REF64 ? 1.0 / st.S : static_cast<double>(1.0f / static_cast<float>(st.S));
+    st.M_f = static_cast<float>(st.M); st.invS_f = static_cast<float>(st.invS);
+    st.axi = static_cast<int32_t>(st.ax); st.ayi = static_cast<int32_t>(st.ay);
+    st.nxi = static_cast<int32_t>(st.nx); st.nyi = static_cast<int32_t>(st.ny);
+    FrameRef fr;
+    memset(&fr, 0, sizeof fr);
+    fr.base = frame; fr.pitch = pitch_bytes; fr.stride = 0; fr.active = 1;
+
+    // Every call shares the scratch array and finds the previous call's contents in it:
+    // the lookback flags, the tile counter and the ticket must start at zero.
+    cudaError_t err = cudaMemsetAsync(scr + LY.ticket, 0, LY.est - LY.ticket, stream);
+    if (err == cudaSuccess) err = cudaMemsetAsync(scr + LY.look, 0, sizeof(LookbackDesc) * nt, stream);
+    if (err == cudaSuccess) err = cudaMemcpyAsync(scr + LY.trk, &T, sizeof T, cudaMemcpyHostToDevice, stream);
+    if (err == cudaSuccess) err = cudaMemcpyAsync(scr + LY.state, &st, sizeof st, cudaMemcpyHostToDevice, stream);
+    if (err == cudaSuccess) err = cudaMemcpyAsync(scr + LY.frame, &fr, sizeof fr, cudaMemcpyHostToDevice, stream);
+    if (err != cudaSuccess) { cudaGetLastError(); return PF_ERR_CUDA; }
+    int grid;
+    {
+        std::lock_guard<std::mutex> guard(g_lock);
+        if (!g_grid[dev][c.precision]) g_grid[dev][c.precision] = step_grid_size(c.precision, kMaxTiles);
+        grid = g_grid[dev][c.precision];
+    }
+    if (grid < 1) return PF_ERR_CUDA;
+    if (grid > nt) grid = nt;
+    StepLaunch L;
+    L.trk = reinterpret_cast<const TrackerDev *>(scr + LY.trk);
+    L.states = T.state;
+    L.frames = reinterpret_cast<const FrameRef *>(scr + LY.frame);
+    L.tile_trk = nullptr;   // one tracker: every tile belongs to it
+    L.ticket = reinterpret_cast<uint32_t *>(scr + LY.ticket);
+    L.ntrk = 1;
+    L.total_tiles = nt;
+    L.frame_override = nullptr;
+    L.pitch_override = 0;
+    if (launch_step(c.precision, L, grid, stream) != 0) { cudaGetLastError(); return PF_ERR_CUDA; }
+
+    if (state_out) {
+        TrackerState res;
+        err = cudaMemcpyAsync(&res, scr + LY.state, sizeof res, cudaMemcpyDeviceToHost, stream);
+        if (err == cudaSuccess) err = cudaStreamSynchronize(stream);
+        if (err != cudaSuccess) { cudaGetLastError(); return PF_ERR_CUDA; }
+        if (res.status & kStatusTimeout) return PF_ERR_TIMEOUT;
+        pf_state_header o;
+        memset(&o, 0, sizeof o);
+        o.magic = 0x31534650u;
+        o.precision = c.precision;
+        o.num_particles = N;
+        o.t = res.t;
+        o.max_l = res.M;
+        o.sum_e = res.S;
+        o.anchor_x = res.ax; o.anchor_y = res.ay;
+        o.next_anchor_x = res.nx; o.next_anchor_y = res.ny;
+        o.est_x = res.est_x; o.est_y = res.est_y;
+        *state_out = o;
+    }
+    return PF_OK;
+}
