@@ -193,6 +193,12 @@ pf_status pf_step_frame_noalloc(const pf_config *cfg, const pf_state_header *sta
                                 void *x_out, void *y_out, void *l_out,
                                 pf_state_header *state_out, void *cuda_stream);
 
+/* Test hook for failure detection: runs the step kernel's bounded lookback wait on a
+ * descriptor that nobody publishes, giving up after spin_limit polls (1 .. 2^20); writes
+ * the resulting status bits to *status_out (host) and returns PF_ERR_TIMEOUT when the wait
+ * gave up, as it must.  The device stays usable afterwards.  Synchronises. */
+pf_status pf_debug_wait_timeout(uint32_t spin_limit, uint32_t *status_out);
+
 /* ---------------------------------------------------------------- batches
  * Many independent trackers (different N, frame sizes, radii, seeds), stepped together
  * by one persistent segmented launch per frame.  All trackers of a batch share one

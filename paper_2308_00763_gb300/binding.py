@@ -21,7 +21,7 @@ __all__ = [
     "PF_FLAG_ACCUM32", "PfConfig", "PfStateHeader", "PfError", "lib", "library_path",
     "pf_status_string", "pf_create", "pf_step_frame", "pf_run_frames", "pf_estimate",
     "pf_estimates", "pf_frames_done", "pf_reset", "pf_destroy", "pf_get_state", "pf_set_state", "pf_get_debug",
-    "pf_debug_philox", "pf_batch_create", "pf_batch_step", "pf_batch_estimates",
+    "pf_debug_philox", "pf_debug_wait_timeout", "pf_batch_create", "pf_batch_step", "pf_batch_estimates",
     "pf_batch_set_videos", "pf_batch_run", "pf_batch_reset", "pf_step_frame_noalloc",
     "pf_batch_destroy", "Filter", "Batch", "PRECISIONS", "EXPORTED",
 ]
@@ -82,6 +82,7 @@ _SIG = {
     "pf_set_state": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
     "pf_get_debug": (ctypes.c_int, [_P, _I32, _P, ctypes.c_size_t]),
     "pf_debug_philox": (ctypes.c_int, [_P, _I64, ctypes.c_uint64, _P]),
+    "pf_debug_wait_timeout": (ctypes.c_int, [ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)]),
     "pf_batch_create": (ctypes.c_int, [ctypes.POINTER(PfConfig), _I32, _P, ctypes.POINTER(_P)]),
     "pf_batch_step": (ctypes.c_int, [_P, _P, _P, _P]),
     "pf_batch_estimates": (ctypes.c_int, [_P, _I64, _P]),
@@ -205,6 +206,13 @@ def pf_debug_philox(ctrs, seed: int) -> np.ndarray:
     _check(lib().pf_debug_philox(c.ctypes.data_as(_P), c.shape[0], seed & 0xFFFFFFFFFFFFFFFF,
                                  out.ctypes.data_as(_P)), "pf_debug_philox")
     return out
+
+
+def pf_debug_wait_timeout(spin_limit: int):
+    """(status code, status bits) of a bounded wait on a flag nobody sets."""
+    bits = ctypes.c_uint32(0)
+    rc = lib().pf_debug_wait_timeout(spin_limit, ctypes.byref(bits))
+    return rc, bits.value
 
 
 def pf_batch_create(cfgs, stream=None):

@@ -105,5 +105,6 @@ int launch_step(int precision, const StepLaunch &L, int grid, void *stream);
 int step_grid_size(int precision, int total_tiles);
 int launch_debug_philox(const uint32_t *d_ctrs, int64_t n, uint64_t seed, uint32_t *d_out,
                         void *stream);
+int launch_wait_probe(void *d_desc, void *d_state, uint32_t limit, void *stream);
 
 }  // namespace pfk

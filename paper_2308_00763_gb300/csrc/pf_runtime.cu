@@ -624,6 +624,24 @@ pf_status pf_debug_philox(const uint32_t *ctrs, int64_t n, uint64_t seed, uint32
     return PF_OK;
 }
 
+pf_status pf_debug_wait_timeout(uint32_t spin_limit, uint32_t *status_out) {
+    if (!status_out || spin_limit == 0 || spin_limit > (1u << 20)) return PF_ERR_ARG;
+    void *d = nullptr;
+    const size_t bytes = sizeof(LookbackDesc) + sizeof(TrackerState);
+    cudaError_t err = cudaMalloc(&d, bytes);
+    if (err != cudaSuccess) { cudaGetLastError(); return PF_ERR_OOM; }
+    err = cudaMemset(d, 0, bytes);   // the descriptor's flag stays 0: nobody ever publishes it
+    char *base = static_cast<char *>(d);
+    if (err == cudaSuccess && launch_wait_probe(base, base + sizeof(LookbackDesc), spin_limit, nullptr) != 0)
+        err = cudaErrorLaunchFailure;
+    TrackerState st;
+    if (err == cudaSuccess) err = cudaMemcpy(&st, base + sizeof(LookbackDesc), sizeof st, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (err != cudaSuccess) { cudaGetLastError(); return PF_ERR_CUDA; }
+    *status_out = st.status;
+    return (st.status & kStatusTimeout) ? PF_ERR_TIMEOUT : PF_OK;
+}
+
 // ---------------------------------------------------------------------------- batches
 pf_status pf_batch_create(const pf_config *cfgs, int32_t n, void *cuda_stream, pf_batch **out) {
     if (!cfgs || !out || n < 1) return PF_ERR_ARG;

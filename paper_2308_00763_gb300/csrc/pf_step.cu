@@ -48,8 +48,11 @@ constexpr int kTableMax = 4096;            // pixels of the per-tile likelihood 
 constexpr int kRoiMax = 8192;              // staged frame pixels (window + template margin)
 constexpr int kMapMax = 8192;              // offspring of a tile served by the ancestor map
 constexpr uint32_t kSpinLimit = 1u << 22;  // bounded waits: ~1 s with backoff
-// Largest |N(0,1)| draw: sqrt(-2 ln 2^-24) = 5.7684 for the smallest 23-bit uniform.
-constexpr float kMaxNormal = 5.77f;
+// Half-width of the likelihood window in standard deviations of the transition noise.
+// Every draw is below sqrt(-2 ln 2^-24) = 5.77 in magnitude, but a tile's few offspring
+// beyond 3.5 sigma (probability 4.7e-4 per coordinate) are cheaper to evaluate directly
+// (same arithmetic, same bits) than a window twice as wide.
+constexpr float kWindowSigmas = 3.5f;
 
 __device__ __forceinline__ bool flag_ready(uint32_t f, uint32_t ep) {
     return (f >> 2) == (ep & 0x3fffffffu) && (f & 3u) != 0u;
@@ -73,9 +76,10 @@ __device__ __forceinline__ bool timed_out(const TrackerState *st) {
 
 // Wait (bounded) until the lookback descriptor of a tile carries this epoch.  Returns the
 // flag, or 0 on timeout (and raises the tracker's timeout bit).
-__device__ uint32_t wait_flag(const LookbackDesc *d, uint32_t ep, TrackerState *st) {
+__device__ uint32_t wait_flag(const LookbackDesc *d, uint32_t ep, TrackerState *st,
+                              uint32_t limit = kSpinLimit) {
     uint32_t ns = 8;
-    for (uint32_t it = 0; it < kSpinLimit; ++it) {
+    for (uint32_t it = 0; it < limit; ++it) {
         const uint32_t f = ld_acquire_u32(&d->flag);
         if (flag_ready(f, ep)) return f;
         if ((it & 1023u) == 1023u && timed_out(st)) return 0u;   // another wait already gave up
@@ -94,38 +98,44 @@ __device__ __forceinline__ double exp_le0(double d) {
 __device__ __forceinline__ float exp_le0(float d) {
     return d == 0.0f ? 1.0f : (d < -104.0f ? 0.0f : expf(d));
 }
+// The FP16/BF16 filters weigh with the hardware exp2 approximation (their likelihoods
+// carry ~11 bits); the scan and the statistics use the same function, so they agree.
+template <bool kFast, typename A> __device__ __forceinline__ A wexp(A d) { return exp_le0(d); }
+template <> __device__ __forceinline__ float wexp<true, float>(float d) {
+    return d == 0.0f ? 1.0f : (d < -104.0f ? 0.0f : __expf(d));
+}
 
 template <typename A>
 struct Stats {
     A m, s, sx, sy;
 };
 
-template <typename A>
+template <bool F, typename A>
 __device__ __forceinline__ void stats_merge(Stats<A> &a, const Stats<A> &b) {
     if (b.m == neg_inf<A>()) return;
     if (a.m == neg_inf<A>()) { a = b; return; }
     if (b.m > a.m) {
-        const A sc = exp_le0(a.m - b.m);
+        const A sc = wexp<F>(a.m - b.m);
         a.s = a.s * sc + b.s;
         a.sx = a.sx * sc + b.sx;
         a.sy = a.sy * sc + b.sy;
         a.m = b.m;
     } else {
-        const A sc = exp_le0(b.m - a.m);
+        const A sc = wexp<F>(b.m - a.m);
         a.s += b.s * sc;
         a.sx += b.sx * sc;
         a.sy += b.sy * sc;
     }
 }
 
-template <typename A>
+template <bool F, typename A>
 __device__ __forceinline__ void stats_add(Stats<A> &a, A L, A dx, A dy) {
     if (L > a.m) {
-        const A sc = (a.m == neg_inf<A>()) ? static_cast<A>(0) : exp_le0(a.m - L);
+        const A sc = (a.m == neg_inf<A>()) ? static_cast<A>(0) : wexp<F>(a.m - L);
         a.s *= sc; a.sx *= sc; a.sy *= sc;
         a.m = L;
     }
-    const A e = exp_le0(L - a.m);
+    const A e = wexp<F>(L - a.m);
     if (e != static_cast<A>(0)) {
         a.s += e;
         a.sx += e * dx;
@@ -315,14 +325,14 @@ __device__ Stats<A> block_stats(Stats<A> v, StepSmem<P> &sm) {
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         Stats<A> w = stats_shfl_xor(v, o);
-        if ((lane & o) == 0) stats_merge(v, w); else { stats_merge(w, v); v = w; }
+        if ((lane & o) == 0) stats_merge<Prec<P>::kHalf>(v, w); else { stats_merge<Prec<P>::kHalf>(w, v); v = w; }
     }
     if (lane == 0) sm.red[warp] = v;
     __syncthreads();
     Stats<A> r;
     if (threadIdx.x == 0) {
         r = sm.red[0];
-        for (int w = 1; w < kWarps; ++w) stats_merge(r, sm.red[w]);
+        for (int w = 1; w < kWarps; ++w) stats_merge<Prec<P>::kHalf>(r, sm.red[w]);
     }
     __syncthreads();
     return r;
@@ -392,7 +402,7 @@ __device__ void finalize_tracker(const TrackerDev &T, TrackerState *st, StepSmem
         w.s = static_cast<acc_t>(__ldcg(p + 1));
         w.sx = static_cast<acc_t>(__ldcg(p + 2));
         w.sy = static_cast<acc_t>(__ldcg(p + 3));
-        stats_merge(v, w);
+        stats_merge<Prec<P>::kHalf>(v, w);
     }
     const Stats<acc_t> r = block_stats<P>(v, sm);
     if (threadIdx.x == 0) {
@@ -521,7 +531,7 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
         for (int m = 0; m < kItems; ++m) {
             const int e = tid * kItems + m;
             acc_t v = static_cast<acc_t>(0);
-            if (e < cnt) v = exp_le0(to_acc(lv[m]) - M);
+            if (e < cnt) v = wexp<Tr::kHalf>(to_acc(lv[m]) - M);
             if (v > static_cast<acc_t>(9.3132257461547852e-10)) heavy |= 1u << m;   // 2^-30
             run = (m == 0) ? v : run + v;
             loc[m] = run;
@@ -621,8 +631,8 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
                 bx0 = fminf(bx0, sm.box[w][0]); bx1 = fmaxf(bx1, sm.box[w][1]);
                 by0 = fminf(by0, sm.box[w][2]); by1 = fmaxf(by1, sm.box[w][3]);
             }
-            const float mxr = fabsf(T.drift_xf) + kMaxNormal * T.sigma_xf + 1.0f;
-            const float myr = fabsf(T.drift_yf) + kMaxNormal * T.sigma_yf + 1.0f;
+            const float mxr = fabsf(T.drift_xf) + kWindowSigmas * T.sigma_xf + 1.0f;
+            const float myr = fabsf(T.drift_yf) + kWindowSigmas * T.sigma_yf + 1.0f;
             int ww = 0, wh = 0, x0 = 0, y0 = 0;
             if (bx0 <= bx1 && by0 <= by1 && bx1 - bx0 < 4096.0f && by1 - by0 < 4096.0f &&
                 fabsf(bx0) < 1.0e6f && fabsf(by0) < 1.0e6f && mxr < 4096.0f && myr < 4096.0f) {
@@ -658,11 +668,14 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
     if (cells > 0) {
         // stage the frame region the window's templates cover (clamped to the frame)
         const int rx0 = wx0 - r, ry0 = wy0 - r, rw = ww + 2 * r, rh = wh + 2 * r;
-        for (int i = tid; i < rw * rh; i += kThreads) {
-            const int yy = i / rw, xx = i - yy * rw;
-            const uint32_t I = fv.at(rx0 + xx, ry0 + yy);
-            if constexpr (Tr::kHalf) sm.u.term[i] = hk.term(I);
-            else sm.pix[i] = static_cast<uint8_t>(I);
+        // warp w stages rows w, w + kWarps, ...; its lanes walk the row
+        for (int yy = warp; yy < rh; yy += kWarps) {
+            const uint8_t *row = fv.p + static_cast<int64_t>(clampi(ry0 + yy, 0, fv.H - 1)) * fv.pitch;
+            for (int xx = lane; xx < rw; xx += 32) {
+                const uint32_t I = __ldg(row + clampi(rx0 + xx, 0, fv.W - 1));
+                if constexpr (Tr::kHalf) sm.u.term[yy * rw + xx] = hk.term(I);
+                else sm.pix[yy * rw + xx] = static_cast<uint8_t>(I);
+            }
         }
         __syncthreads();
         if constexpr (!Tr::kHalf) {
@@ -676,8 +689,7 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
             }
             __syncthreads();
         }
-        for (int c = tid; c < cells; c += kThreads) {
-            const int cy = c / ww, cx = c - cy * ww;
+        for (int c = tid, cy = tid / ww, cx = tid - (tid / ww) * ww; c < cells; c += kThreads) {
             if constexpr (Tr::kHalf) {
                 sm.table[c] = hk.from_terms(sm.u.term, rw, sm.w, r, cx, cy);
             } else {
@@ -689,6 +701,8 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
                 }
                 sm.table[c] = lik_from_sum<acc_t>(ssum, c1, c2D, den);
             }
+            cx += kThreads;               // next cell: kThreads further in row-major order
+            while (cx >= ww) { cx -= ww; ++cy; }
         }
         __syncthreads();
     }
@@ -877,8 +891,8 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
             } else if (v1) {
                 Xout[j1] = x1; Yout[j1] = y1; Lout[j1] = L1;
             }
-            if (v0) stats_add(stats, L0, x0 - nxa_a, y0 - nya_a);
-            if (v1) stats_add(stats, L1, x1 - nxa_a, y1 - nya_a);
+            if (v0) stats_add<false>(stats, L0, x0 - nxa_a, y0 - nya_a);
+            if (v1) stats_add<false>(stats, L1, x1 - nxa_a, y1 - nya_a);
         } else {
             // ---------------- F16 / BF16: half2 lanes = particles (j0, j1), offsets from the anchor
             using OPS = HalfOps<H>;
@@ -919,8 +933,8 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
             } else if (v1) {
                 Xout[j1] = OPS::hi_h(ox); Yout[j1] = OPS::hi_h(oy); Lout[j1] = l1;
             }
-            if (v0) stats_add(stats, OPS::to_f(l0), OPS::lo(ox), OPS::lo(oy));
-            if (v1) stats_add(stats, OPS::to_f(l1), OPS::hi(ox), OPS::hi(oy));
+            if (v0) stats_add<true>(stats, OPS::to_f(l0), OPS::lo(ox), OPS::lo(oy));
+            if (v1) stats_add<true>(stats, OPS::to_f(l1), OPS::hi(ox), OPS::hi(oy));
         }
     }
 
@@ -967,6 +981,12 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<P>::value) step_kernel(con
     }
 }
 
+// Test hook: the lookback wait on a descriptor that nobody publishes, with a short limit;
+// it must give up, raise the timeout bit and return.
+__global__ void wait_probe_kernel(const LookbackDesc *d, TrackerState *st, uint32_t limit) {
+    wait_flag(d, 1u, st, limit);
+}
+
 __global__ void philox_kernel(const uint4 *ctrs, int64_t n, uint32_t k0, uint32_t k1, uint4 *out) {
     const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i < n) out[i] = philox4x32_10(ctrs[i], k0, k1);
@@ -1008,6 +1028,12 @@ int launch_step(int precision, const StepLaunch &L, int grid, void *stream) {
         case 3: step_kernel<3><<<grid, kThreads, sizeof(StepSmem<3>), s>>>(L); break;
         default: return -1;
     }
+    return static_cast<int>(cudaGetLastError());
+}
+
+int launch_wait_probe(void *d_desc, void *d_state, uint32_t limit, void *stream) {
+    wait_probe_kernel<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(
+        static_cast<const LookbackDesc *>(d_desc), static_cast<TrackerState *>(d_state), limit);
     return static_cast<int>(cudaGetLastError());
 }
 

@@ -89,3 +89,43 @@ def make_video(W: int, H: int, T: int, r: int, *, v=(1.0, -2.0), c0=None,
             img = img + noise * rng.standard_normal((H, W))
         frames[t] = np.clip(np.floor(img + 0.5), 0, 255).astype(np.uint8)
     return Video(frames=frames, centres=centres, radius=int(r), noise=float(noise), seed=int(seed))
+
+
+def make_video_device(W: int, H: int, T: int, r: int, *, v=(1.0, -2.0), c0=None, noise: float = 5.0,
+                      bg: int = 100, fg: int = 228, seed: int = 1, bounce: bool = True, device="cuda"):
+    """The same recipe as :func:`make_video`, rendered on a torch device with torch's
+    generator (so its noise differs from the numpy stream).  For inputs too large to render
+    on the host, such as a batch of hundreds of videos.  Returns (frames (T, H, W) uint8
+    tensor, centres (T, 2) numpy)."""
+    import torch
+    centres = centre_track(W, H, T, r, v=v, c0=c0, bounce=bounce)
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    ys = torch.arange(H, dtype=torch.float32, device=device)[:, None]
+    xs = torch.arange(W, dtype=torch.float32, device=device)[None, :]
+    out = torch.empty((T, H, W), dtype=torch.uint8, device=device)
+    r2 = float(r) * float(r)
+    for t in range(T):
+        cx, cy = float(centres[t, 0]), float(centres[t, 1])
+        inside = (xs - cx) ** 2 + (ys - cy) ** 2 <= r2
+        img = torch.where(inside, torch.tensor(float(fg), device=device), torch.tensor(float(bg), device=device))
+        if noise > 0:
+            img = img + noise * torch.randn((H, W), generator=g, device=device)
+        out[t] = torch.clamp(torch.floor(img + 0.5), 0, 255).to(torch.uint8)
+    return out, centres
+
+
+def batch_workload(n: int = 256, T: int = 60, seed: int = 4):
+    """Parameters of the batched-trackers workload: frame sizes uniform from
+    {256^2, 512^2, 1024^2}, particle counts log-uniform in [1000, 262144], disk radius
+    uniform in 3..12, constant velocity of uniform angle and speed in [0, 4) px/frame,
+    noise 5, T frames; video i has seed 1000 + i."""
+    rng = np.random.default_rng(seed)
+    sizes = rng.choice([256, 512, 1024], size=n)
+    N = np.floor(np.exp(rng.uniform(np.log(1000.0), np.log(262144.0), size=n))).astype(np.int64)
+    r = rng.integers(3, 13, size=n)
+    ang = rng.uniform(0.0, 2.0 * np.pi, size=n)
+    spd = rng.uniform(0.0, 4.0, size=n)
+    return [dict(W=int(sizes[i]), H=int(sizes[i]), T=T, r=int(r[i]), N=int(N[i]),
+                 v=(float(spd[i] * np.cos(ang[i])), float(spd[i] * np.sin(ang[i]))),
+                 noise=5.0, seed=1000 + i) for i in range(n)]

@@ -342,3 +342,13 @@ def test_batch_resident_videos_equal_single_trackers(pf):
         b.run(8)
         again = np.stack([b.estimates(t) for t in range(8)], axis=1)
         assert np.array_equal(again, got), prec
+
+
+def test_bounded_wait_gives_up_and_context_survives(pf):
+    """Failure detection: the lookback wait on a flag that nothing sets gives up after its
+    limit, raises the timeout bit, and the device keeps working."""
+    rc, bits = pf.pf_debug_wait_timeout(2000)
+    assert rc == pf.PF_ERR_TIMEOUT and bits & 1
+    v = synth.make_video(64, 64, 3, 3, noise=5.0, seed=60)
+    _, est, _ = _run_gpu(pf, v, 1000, "f32")
+    assert np.isfinite(est).all()
