@@ -14,7 +14,7 @@
 
 namespace pfk {
 
-constexpr int kThreads = 256;             // threads per CTA of the step kernel
+constexpr int kThreads = 512;             // threads per CTA of the step kernel
 constexpr int kItems = 8;                 // CDF elements per thread
 constexpr int kTile = kThreads * kItems;  // particles of the resampled frame per tile
 constexpr int kMaxRadius = 64;

@@ -24,7 +24,7 @@ using namespace pfk;
 namespace {
 
 constexpr size_t kScratchBytes = 256 * 1024;
-constexpr int kMaxTiles = 2048;                       // => at most 2^22 particles
+constexpr int kMaxTiles = (1 << 22) / kTile;          // => at most 2^22 particles
 constexpr int kMaxDevices = 64;
 
 // The scratch array.  In host code its name is only a stand-in for the symbol; the

@@ -956,10 +956,10 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
 
 // CTAs per SM the register allocation must allow (measured best per precision on GB300:
 // the step is latency-bound, so the FP16/BF16 kernels trade a few spills for 4 CTAs/SM).
-template <int P> struct MinBlocks { static constexpr int value = 2; };
-template <> struct MinBlocks<1> { static constexpr int value = 3; };
-template <> struct MinBlocks<2> { static constexpr int value = 4; };
-template <> struct MinBlocks<3> { static constexpr int value = 4; };
+template <int P> struct MinBlocks { static constexpr int value = 1; };
+template <> struct MinBlocks<1> { static constexpr int value = 2; };
+template <> struct MinBlocks<2> { static constexpr int value = 2; };
+template <> struct MinBlocks<3> { static constexpr int value = 2; };
 
 template <int P>
 __global__ void __launch_bounds__(kThreads, MinBlocks<P>::value) step_kernel(const StepLaunch Lp) {

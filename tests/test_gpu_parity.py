@@ -15,7 +15,7 @@ from paper_2308_00763_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-TILE = 2048  # particles per tile of the step kernel (resampling side)
+TILE = 4096  # particles per tile of the step kernel (kTile: 512 threads x 8 elements)
 
 
 @pytest.fixture(scope="module")

@@ -36,7 +36,7 @@ _TORCH_DTYPE = {"ref64": "float64", "f32": "float32", "f16": "float16", "bf16": 
 @pytest.mark.parametrize("prec", ["ref64", "f32", "f16", "bf16"])
 def test_noalloc_two_frames_match_filter(pf, prec):
     import torch
-    N = 3 * 2048 + 11
+    N = 3 * 4096 + 11
     v = synth.make_video(160, 120, 2, 4, noise=5.0, seed=31, v=(1.0, -1.0))
     frames = torch.from_numpy(v.frames).cuda()
     kw = dict(init=tuple(v.centres[0]), seed=77, tracker_id=2)
