@@ -173,8 +173,8 @@ pf_status pf_debug_philox(const uint32_t *ctrs, int64_t n, uint64_t seed, uint32
  * allocation can.  The paper has no counterpart; this is a deployment form of
  * pf_step_frame.  The caller owns every buffer (device pointers): the previous frame's
  * particles x_in, y_in, l_in (ignored when state_in->t == 0) and the new frame's
- * x_out, y_out, l_out (N elements each, in the precision's storage type, distinct from the
- * inputs; F16/BF16 positions are offsets from the anchor in the header), and the frame
+ * x_out, y_out, l_out (N elements each, in the precision's storage type, 16-byte aligned,
+ * distinct from the inputs; F16/BF16 positions are offsets from the anchor in the header), and the frame
  * (rows pitch_bytes apart).  state_in (host) carries the scalars of the previous frame in
  * the pf_get_state header layout (t = 0: a fresh tracker); if state_out (host) is not NULL
  * the call synchronises the stream and writes the new frame's scalars there (its t is

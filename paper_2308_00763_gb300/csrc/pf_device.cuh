@@ -56,8 +56,13 @@ __device__ __forceinline__ void box_muller(float ua, float ub, float &nx, float 
 // units), for the FP16/BF16 filters whose positions keep ~11 bits anyway.  The angle
 // is taken in [-pi, pi), where the sin/cos approximations are most accurate:
 // (cos, sin)(2 pi u - pi) = -(cos, sin)(2 pi u).
+__device__ __forceinline__ float sqrt_approx(float v) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
 __device__ __forceinline__ void box_muller_fast(float ua, float ub, float &nx, float &ny) {
-    const float rad = __fsqrt_rn(-1.3862943611198906f * __log2f(ua));   // -2 ln u = -2 ln2 log2 u
+    const float rad = sqrt_approx(-1.3862943611198906f * __log2f(ua));   // -2 ln u = -2 ln2 log2 u
     const float ang = 6.2831853071795865f * (ub - 0.5f);
     float s, c;
     __sincosf(ang, &s, &c);
@@ -106,13 +111,23 @@ struct Strata {
         nf = static_cast<A>(n);
     }
     // number of strata j with u_j <= c
-    __device__ int count_le(A c) const {
+    __device__ __forceinline__ int count_le(A c) const {
         if (!(first <= c)) return 0;   // also NaN
         if (last <= c) return n;
-        // invariant wanted: u(lo) <= c < u(hi), 0 <= lo < hi <= n - 1
         const A est = c * nf - u0;
         int j = (est > static_cast<A>(0)) ? static_cast<int>(est) : 0;
         if (j > n - 2) j = n - 2;
+        // The estimate is almost always within one stratum of the answer: probe u_j and its
+        // neighbour on the far side (j = 0 has u_0 = first <= c, so j - 1 is never probed
+        // below 0), and search only when both probes fall on the same side.
+        const bool a = stratum_point32<A>(j, u0, inv_n) <= c;
+        const bool b = stratum_point32<A>(a ? j + 1 : j - 1, u0, inv_n) <= c;
+        if (a != b) return a ? j + 1 : j;
+        return search(c, j);
+    }
+    // the count for u_0 <= c < u_{n-1}, from the start point j (galloping, then bisection)
+    __device__ __noinline__ int search(A c, int j) const {
+        // invariant wanted: u(lo) <= c < u(hi), 0 <= lo < hi <= n - 1
         int lo, hi;
         if (stratum_point32<A>(j, u0, inv_n) <= c) {
             lo = j;
@@ -142,25 +157,8 @@ struct Strata {
 };
 
 // ----------------------------------------------------------------------------------
-// Memory-model helpers for the decoupled lookback and the last-block-done finalise.
-// ----------------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
-    uint32_t v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ double ld_relaxed_f64(const double *p) {
-    double v;
-    asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// ----------------------------------------------------------------------------------
 // 128-bit fixed point for the inter-tile prefix of the CDF scan: x -> round-down(x * 2^90).
-// Tile aggregates are at most 2^11 and a tracker's total at most 2^31, so 2^121 bounds
+// Tile aggregates are at most 2^12 and a tracker's total at most 2^31, so 2^121 bounds
 // every value; the sum of integers is exact and associative.
 // ----------------------------------------------------------------------------------
 constexpr int kFixShift = 90;
@@ -229,13 +227,6 @@ __device__ __forceinline__ double from_fixed(U128 x) {
     const int e2 = 64 - lz - kFixShift;                     // value = top * 2^e2
     const double scale = __longlong_as_double(static_cast<long long>(1023 + e2) << 52);
     return __ull2double_rn(top) * scale;
-}
-
-__device__ __forceinline__ U128 ld_relaxed_u128(const uint64_t *lo_hi) {
-    U128 r;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(r.lo) : "l"(lo_hi) : "memory");
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(r.hi) : "l"(lo_hi + 1) : "memory");
-    return r;
 }
 
 __device__ __forceinline__ U128 shfl_down128(U128 v, int o) {

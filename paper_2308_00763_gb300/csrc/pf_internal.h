@@ -22,18 +22,28 @@ constexpr int kMaxRadius = 64;
 // Device status bits (sticky, per tracker).
 constexpr uint32_t kStatusTimeout = 0x1u;
 
-// Tile status of the decoupled lookback.  The inter-tile prefix is an exact fixed-point
-// sum (value * 2^kFixShift in 128 bits), so its value does not depend on the order in
-// which a tile collects its predecessors' aggregates.
+// Lookback descriptor of one tile: its aggregate and its inclusive prefix, each an exact
+// 128-bit fixed-point value (value * 2^kFixShift; the inter-tile prefix then does not
+// depend on the order in which a tile collects its predecessors' aggregates).  Each value
+// is split into three 64-bit words (48 + 48 + 32 payload bits) whose top 16 bits carry a
+// tag of the launch (the tracker's epoch).  A word is written once per launch by a single
+// 64-bit store, so a reader that finds the current tag in all three words of a value holds
+// the whole value: neither side needs a fence.  Layout: w[0..1] aggregate words 0-1,
+// w[2..3] inclusive words 0-1 (16-byte aligned pairs), w[4] aggregate word 2, w[5]
+// inclusive word 2.
 struct alignas(16) LookbackDesc {
-    uint32_t flag;      // (epoch << 2) | state, state: 0 empty, 1 aggregate, 2 inclusive
-    uint32_t pad[3];
-    uint64_t agg_lo, agg_hi;    // tile aggregate of e, fixed point
-    uint64_t incl_lo, incl_hi;  // inclusive prefix through this tile, fixed point
+    uint64_t w[6];
 };
 
+// Per-tile (max L, sum exp(L - max), sum exp(L - max) * dx, * dy).  REF64 stores four
+// doubles (published by an acquire-release count); the FP32/FP16/BF16 kernels store four
+// 64-bit words (tag << 32 | float bits), the tag being the launch counter, so the tile
+// that completes the tracker can wait for each word without any fence.
 struct alignas(16) TilePartial {
-    double m, s, sx, sy;   // running max of L, sum exp(L-m), sum exp(L-m)*dx, *dy
+    union {
+        double d[4];
+        uint64_t w[4];
+    };
 };
 
 struct alignas(16) TrackerState {

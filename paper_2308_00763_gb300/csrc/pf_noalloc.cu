@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stddef.h>
+#include <stdint.h>
 #include <string.h>
 
 #include <mutex>
@@ -109,6 +110,10 @@ extern "C" pf_status pf_step_frame_noalloc(const pf_config *cfg, const pf_state_
     if (h.magic != 0x31534650u || h.precision != c.precision || h.num_particles != c.num_particles || h.t < 0)
         return PF_ERR_ARG;
     if (h.t > 0 && (!x_in || !y_in || !l_in || !(h.sum_e > 0) || !isfinite(h.max_l))) return PF_ERR_ARG;
+    // the step moves particles in 16-byte vectors
+    const auto misaligned = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) != 0u; };
+    if (misaligned(x_out) || misaligned(y_out) || misaligned(l_out)) return PF_ERR_ARG;
+    if (h.t > 0 && (misaligned(x_in) || misaligned(y_in) || misaligned(l_in))) return PF_ERR_ARG;
 
     int dev = 0;
     unsigned char *scr = nullptr;
@@ -150,7 +155,7 @@ extern "C" pf_status pf_step_frame_noalloc(const pf_config *cfg, const pf_state_
     TrackerState st;
     memset(&st, 0, sizeof st);
     st.t = h.t;
-    st.epoch = 1;   // the lookback flags are cleared below, so any nonzero epoch works
+    st.epoch = 1;   // the lookback descriptors and tile partials are cleared below
     if (h.t == 0) {
         st.M = 0.0; st.S = 1.0;
         st.ax = st.nx = round_half_up(c.init_x);
@@ -170,9 +175,11 @@ extern "C" pf_status pf_step_frame_noalloc(const pf_config *cfg, const pf_state_
     fr.base = frame; fr.pitch = pitch_bytes; fr.stride = 0; fr.active = 1;
 
     // Every call shares the scratch array and finds the previous call's contents in it:
-    // the lookback flags, the tile counter and the ticket must start at zero.
+    // the lookback descriptors, the tile partials (their words carry the launch counter,
+    // which is 1 on every call), the tile counter and the ticket must start at zero.
     cudaError_t err = cudaMemsetAsync(scr + LY.ticket, 0, LY.est - LY.ticket, stream);
     if (err == cudaSuccess) err = cudaMemsetAsync(scr + LY.look, 0, sizeof(LookbackDesc) * nt, stream);
+    if (err == cudaSuccess) err = cudaMemsetAsync(scr + LY.part, 0, sizeof(TilePartial) * nt, stream);
     if (err == cudaSuccess) err = cudaMemcpyAsync(scr + LY.trk, &T, sizeof T, cudaMemcpyHostToDevice, stream);
     if (err == cudaSuccess) err = cudaMemcpyAsync(scr + LY.state, &st, sizeof st, cudaMemcpyHostToDevice, stream);
     if (err == cudaSuccess) err = cudaMemcpyAsync(scr + LY.frame, &fr, sizeof fr, cudaMemcpyHostToDevice, stream);

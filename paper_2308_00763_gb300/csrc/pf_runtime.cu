@@ -493,17 +493,25 @@ pf_status pf_estimates(pf_filter *f, int64_t first, int32_t count, double *xy, d
 
 int64_t pf_frames_done(const pf_filter *f) { return f ? f->e.done_frames[0] : -1; }
 
+// Clear tracker i's lookback descriptors on the engine's stream.
+static cudaError_t clear_lookback(Engine &e, int i) {
+    const TrackerDev &T = e.h_trk[i];
+    return cudaMemsetAsync(T.look, 0, sizeof(LookbackDesc) * static_cast<size_t>(T.ntiles), e.stream);
+}
+
 pf_status pf_reset(pf_filter *f) {
     if (!f) return PF_ERR_ARG;
     Engine &e = f->e;
     if (e.sticky != PF_OK) return PF_ERR_STATE;
     // Rewrite every field of the state except the launch counter (epoch) and the status
-    // word: lookback flags written by earlier launches must stay stale.
+    // word, and clear the lookback descriptors (their tags are launch counters modulo
+    // 65535: cleared words can never look current).
     TrackerState *d = e.h_trk[0].state;
     const TrackerState *h = &e.h_init_pinned[0];
     const size_t tail = sizeof(TrackerState) - offsetof(TrackerState, M);
     cudaError_t err = cudaMemcpyAsync(&d->t, &h->t, sizeof(int64_t), cudaMemcpyHostToDevice, e.stream);
     if (err == cudaSuccess) err = cudaMemcpyAsync(&d->M, &h->M, tail, cudaMemcpyHostToDevice, e.stream);
+    if (err == cudaSuccess) err = clear_lookback(e, 0);
     if (err != cudaSuccess) { cudaGetLastError(); return e.fail(PF_ERR_CUDA); }
     e.done_frames[0] = 0;
     return PF_OK;
@@ -587,6 +595,7 @@ pf_status pf_set_state(pf_filter *f, const void *host_buf, size_t bytes) {
     const int slot = static_cast<int>((h.t + 1) & 1);
     const size_t nb = pb * static_cast<size_t>(T.N);
     err = cudaMemcpy(T.state, &st, sizeof st, cudaMemcpyHostToDevice);
+    if (err == cudaSuccess) err = cudaMemset(T.look, 0, sizeof(LookbackDesc) * static_cast<size_t>(T.ntiles));
     if (err == cudaSuccess) err = cudaMemcpy(T.px[slot], p, nb, cudaMemcpyHostToDevice);
     if (err == cudaSuccess) err = cudaMemcpy(T.py[slot], p + nb, nb, cudaMemcpyHostToDevice);
     if (err == cudaSuccess) err = cudaMemcpy(T.pl[slot], p + 2 * nb, nb, cudaMemcpyHostToDevice);
@@ -630,7 +639,7 @@ pf_status pf_debug_wait_timeout(uint32_t spin_limit, uint32_t *status_out) {
     const size_t bytes = sizeof(LookbackDesc) + sizeof(TrackerState);
     cudaError_t err = cudaMalloc(&d, bytes);
     if (err != cudaSuccess) { cudaGetLastError(); return PF_ERR_OOM; }
-    err = cudaMemset(d, 0, bytes);   // the descriptor's flag stays 0: nobody ever publishes it
+    err = cudaMemset(d, 0, bytes);   // the descriptor's words stay untagged: nobody publishes it
     char *base = static_cast<char *>(d);
     if (err == cudaSuccess && launch_wait_probe(base, base + sizeof(LookbackDesc), spin_limit, nullptr) != 0)
         err = cudaErrorLaunchFailure;
@@ -727,6 +736,7 @@ pf_status pf_batch_reset(pf_batch *b) {
         const TrackerState *h = &e.h_init_pinned[i];
         cudaError_t err = cudaMemcpyAsync(&d->t, &h->t, sizeof(int64_t), cudaMemcpyHostToDevice, e.stream);
         if (err == cudaSuccess) err = cudaMemcpyAsync(&d->M, &h->M, tail, cudaMemcpyHostToDevice, e.stream);
+        if (err == cudaSuccess) err = clear_lookback(e, i);
         if (err != cudaSuccess) { cudaGetLastError(); return e.fail(PF_ERR_CUDA); }
         // resident videos: frame 0 is again the video's first frame
         FrameRef &fr = e.h_frames_pinned[i];

@@ -32,6 +32,7 @@
 // every j is written by exactly one tile.
 #include <cuda_runtime.h>
 #include <float.h>
+#include <stddef.h>
 #include <math.h>
 
 #include <type_traits>
@@ -49,14 +50,12 @@ constexpr int kRoiMax = 8192;              // staged frame pixels (window + temp
 constexpr int kMapMax = 8192;              // offspring of a tile served by the ancestor map
 constexpr uint32_t kSpinLimit = 1u << 22;  // bounded waits: ~1 s with backoff
 // Half-width of the likelihood window in standard deviations of the transition noise.
-// Every draw is below sqrt(-2 ln 2^-24) = 5.77 in magnitude, but a tile's few offspring
-// beyond 3.5 sigma (probability 4.7e-4 per coordinate) are cheaper to evaluate directly
-// (same arithmetic, same bits) than a window twice as wide.
+// Every draw is below sqrt(-2 ln 2^-24) = 5.77 in magnitude (kDrawMax, rounded up).  When
+// that window has more cells than the block has threads, a window of 3.5 sigma is used:
+// a tile's few offspring beyond it (probability 4.7e-4 per coordinate) are cheaper to
+// evaluate directly (same arithmetic, same bits) than a window twice as wide.
+constexpr float kDrawMax = 5.7683f;
 constexpr float kWindowSigmas = 3.5f;
-
-__device__ __forceinline__ bool flag_ready(uint32_t f, uint32_t ep) {
-    return (f >> 2) == (ep & 0x3fffffffu) && (f & 3u) != 0u;
-}
 
 __device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t *p) {
     uint32_t v;
@@ -74,20 +73,87 @@ __device__ __forceinline__ bool timed_out(const TrackerState *st) {
     return (ld_relaxed_u32(&st->status) & kStatusTimeout) != 0u;
 }
 
-// Wait (bounded) until the lookback descriptor of a tile carries this epoch.  Returns the
-// flag, or 0 on timeout (and raises the tracker's timeout bit).
-__device__ uint32_t wait_flag(const LookbackDesc *d, uint32_t ep, TrackerState *st,
+// ---- lookback descriptor words (see LookbackDesc): 16-bit launch tag | 48-bit payload
+constexpr uint64_t kPayload48 = (1ull << 48) - 1ull;
+
+__device__ __forceinline__ uint64_t desc_tag(uint32_t ep) {   // never 0 (cleared memory)
+    return static_cast<uint64_t>(ep % 65535u + 1u) << 48;
+}
+
+__device__ __forceinline__ void st_relaxed_v2(uint64_t *p, uint64_t a, uint64_t b) {
+    asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b) : "memory");
+}
+__device__ __forceinline__ void st_relaxed_u64(uint64_t *p, uint64_t a) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(a) : "memory");
+}
+__device__ __forceinline__ void ld_relaxed_v2(const uint64_t *p, uint64_t &a, uint64_t &b) {
+    asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
+}
+
+// Publish a tile's aggregate (which = 0) or inclusive prefix (which = 1).
+__device__ __forceinline__ void desc_publish(LookbackDesc *d, int which, U128 v, uint64_t tag) {
+    const uint64_t w0 = (v.lo & kPayload48) | tag;
+    const uint64_t w1 = (((v.lo >> 48) | (v.hi << 16)) & kPayload48) | tag;
+    const uint64_t w2 = (v.hi >> 32) | tag;
+    st_relaxed_v2(&d->w[2 * which], w0, w1);
+    st_relaxed_u64(&d->w[4 + which], w2);
+}
+
+__device__ __forceinline__ U128 desc_value(uint64_t w0, uint64_t w1, uint64_t w2) {
+    U128 v;
+    v.lo = (w0 & kPayload48) | (w1 << 48);
+    v.hi = ((w1 & kPayload48) >> 16) | ((w2 & kPayload48) << 32);
+    return v;
+}
+
+// Wait (bounded) until a predecessor tile has published this launch's inclusive prefix
+// (returns 2) or aggregate (returns 1), with its value in v.  Returns 0 on timeout (and
+// raises the tracker's timeout bit).
+__device__ uint32_t wait_desc(const LookbackDesc *d, uint64_t tag, TrackerState *st, U128 &v,
                               uint32_t limit = kSpinLimit) {
     uint32_t ns = 8;
     for (uint32_t it = 0; it < limit; ++it) {
-        const uint32_t f = ld_acquire_u32(&d->flag);
-        if (flag_ready(f, ep)) return f;
+        uint64_t a0, a1, i0, i1, w4, w5;
+        ld_relaxed_v2(&d->w[2], i0, i1);
+        ld_relaxed_v2(&d->w[4], w4, w5);
+        const uint64_t hm = ~kPayload48;
+        if ((i0 & hm) == tag && (i1 & hm) == tag && (w5 & hm) == tag) { v = desc_value(i0, i1, w5); return 2u; }
+        ld_relaxed_v2(&d->w[0], a0, a1);
+        if ((a0 & hm) == tag && (a1 & hm) == tag && (w4 & hm) == tag) { v = desc_value(a0, a1, w4); return 1u; }
         if ((it & 1023u) == 1023u && timed_out(st)) return 0u;   // another wait already gave up
         __nanosleep(ns);
         if (ns < 256) ns <<= 1;
     }
     atomicOr(&st->status, kStatusTimeout);
     return 0u;
+}
+
+__device__ __forceinline__ uint32_t atom_add_relaxed(uint32_t *p, uint32_t v) {
+    uint32_t old;
+    asm volatile("atom.relaxed.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+// Tile partials of the FP32/FP16/BF16 kernels: 32-bit launch tag | float bits per word.
+__device__ __forceinline__ uint64_t partial_tag(uint32_t ep) {   // never 0 (cleared memory)
+    return static_cast<uint64_t>(ep % 0x7fffffffu + 1u) << 32;
+}
+
+// Wait (bounded) until the four words of a tile partial carry this launch's tag; on
+// timeout the tracker's timeout bit is raised and the words read last are returned.
+__device__ void wait_partial(const TilePartial *p, uint64_t tag, TrackerState *st, uint64_t (&q)[4],
+                             uint32_t limit = kSpinLimit) {
+    uint32_t ns = 8;
+    const uint64_t hm = 0xffffffff00000000ull;
+    for (uint32_t it = 0; it < limit; ++it) {
+        ld_relaxed_v2(&p->w[0], q[0], q[1]);
+        ld_relaxed_v2(&p->w[2], q[2], q[3]);
+        if ((q[0] & hm) == tag && (q[1] & hm) == tag && (q[2] & hm) == tag && (q[3] & hm) == tag) return;
+        if ((it & 1023u) == 1023u && timed_out(st)) return;
+        __nanosleep(ns);
+        if (ns < 256) ns <<= 1;
+    }
+    atomicOr(&st->status, kStatusTimeout);
 }
 
 // exp(d) for d <= 0 with the two exact shortcuts: exp(0) = 1, and 0 below the point
@@ -110,37 +176,37 @@ struct Stats {
     A m, s, sx, sy;
 };
 
+// Merge of two partial (max, sums) with rescaling to the larger max.  Symmetric:
+// stats_merge(a, b) and stats_merge(b, a) give the same bits (no fused multiply-add).
 template <bool F, typename A>
-__device__ __forceinline__ void stats_merge(Stats<A> &a, const Stats<A> &b) {
-    if (b.m == neg_inf<A>()) return;
-    if (a.m == neg_inf<A>()) { a = b; return; }
-    if (b.m > a.m) {
-        const A sc = wexp<F>(a.m - b.m);
-        a.s = a.s * sc + b.s;
-        a.sx = a.sx * sc + b.sx;
-        a.sy = a.sy * sc + b.sy;
-        a.m = b.m;
-    } else {
-        const A sc = wexp<F>(b.m - a.m);
-        a.s += b.s * sc;
-        a.sx += b.sx * sc;
-        a.sy += b.sy * sc;
-    }
+__device__ __forceinline__ Stats<A> stats_merge(const Stats<A> &a, const Stats<A> &b) {
+    const A m = a.m > b.m ? a.m : b.m;
+    if (m == neg_inf<A>()) return a;
+    const A sa = (a.m == neg_inf<A>()) ? static_cast<A>(0) : wexp<F>(a.m - m);
+    const A sb = (b.m == neg_inf<A>()) ? static_cast<A>(0) : wexp<F>(b.m - m);
+    Stats<A> r;
+    r.m = m;
+    r.s = add_rn(mul_rn(a.s, sa), mul_rn(b.s, sb));
+    r.sx = add_rn(mul_rn(a.sx, sa), mul_rn(b.sx, sb));
+    r.sy = add_rn(mul_rn(a.sy, sa), mul_rn(b.sy, sb));
+    return r;
 }
 
+// Two particles at once (a particle whose flag is false is skipped): one rescale check.
 template <bool F, typename A>
-__device__ __forceinline__ void stats_add(Stats<A> &a, A L, A dx, A dy) {
-    if (L > a.m) {
-        const A sc = (a.m == neg_inf<A>()) ? static_cast<A>(0) : wexp<F>(a.m - L);
+__device__ __forceinline__ void stats_add2(Stats<A> &a, bool v0, A L0, A dx0, A dy0, bool v1, A L1, A dx1, A dy1) {
+    const A l0 = v0 ? L0 : neg_inf<A>(), l1 = v1 ? L1 : neg_inf<A>();
+    const A mx = l0 > l1 ? l0 : l1;
+    if (mx > a.m) {
+        const A sc = (a.m == neg_inf<A>()) ? static_cast<A>(0) : wexp<F>(a.m - mx);
         a.s *= sc; a.sx *= sc; a.sy *= sc;
-        a.m = L;
+        a.m = mx;
     }
-    const A e = wexp<F>(L - a.m);
-    if (e != static_cast<A>(0)) {
-        a.s += e;
-        a.sx += e * dx;
-        a.sy += e * dy;
-    }
+    const A e0 = v0 ? wexp<F>(l0 - a.m) : static_cast<A>(0);
+    const A e1 = v1 ? wexp<F>(l1 - a.m) : static_cast<A>(0);
+    a.s += e0 + e1;
+    a.sx += e0 * dx0 + e1 * dx1;
+    a.sy += e0 * dy0 + e1 * dy1;
 }
 
 template <typename A>
@@ -163,6 +229,26 @@ __device__ __forceinline__ int pixel_of(float v) {
 }
 __device__ __forceinline__ int pixel_of(double v) {
     return __double2int_rd(fmin(fmax(v, -1048576.0), 1048576.0) + 0.5);
+}
+
+// kItems consecutive elements between memory and registers as 16-byte vectors (kItems *
+// sizeof(T) is a multiple of 16 for every element type here; the address is 16-byte aligned).
+template <typename T>
+__device__ __forceinline__ void load_items(T (&dst)[kItems], const T *src) {
+    constexpr int kVec = static_cast<int>(sizeof(T)) * kItems / 16;
+    static_assert(kVec * 16 == static_cast<int>(sizeof(T)) * kItems, "kItems elements must fill 16-byte vectors");
+    const uint4 *s = reinterpret_cast<const uint4 *>(src);
+    uint4 *d = reinterpret_cast<uint4 *>(dst);
+#pragma unroll
+    for (int v = 0; v < kVec; ++v) d[v] = s[v];
+}
+template <typename T>
+__device__ __forceinline__ void store_items(T *dst, const T (&src)[kItems]) {
+    constexpr int kVec = static_cast<int>(sizeof(T)) * kItems / 16;
+    const uint4 *s = reinterpret_cast<const uint4 *>(src);
+    uint4 *d = reinterpret_cast<uint4 *>(dst);
+#pragma unroll
+    for (int v = 0; v < kVec; ++v) d[v] = s[v];
 }
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
@@ -272,6 +358,7 @@ struct HalfLik {
         for (int i = 0; i <= 2 * r; ++i) {
             const int hw = w[i];
             const H *row = tm + (cy + i) * rw + cx + r;
+#pragma unroll 8
             for (int dx = -hw; dx <= hw; ++dx) {
                 if (half_acc) hacc = __hadd(hacc, row[dx]); else facc += HalfOps<H>::to_f(row[dx]);
             }
@@ -300,9 +387,10 @@ struct __align__(16) StepSmem {
     uint8_t pix[kPixBytes];   // integer form: staged frame region
     acc_t warp_sum[kWarps];
     acc_t warp_max[kWarps];
-    float box[kWarps][4];
+    alignas(16) float box[kWarps][4];
     int warp_imax[kWarps];
     U128 red128[kWarps];
+    int warp_incl[kWarps];
     Stats<acc_t> red[kWarps];
     acc_t agg;
     U128 excl_x, end_x;       // exact fixed-point prefix before / after the tile
@@ -318,65 +406,60 @@ struct __align__(16) StepSmem {
     FrameRef fr;
 };
 
-// Block-wide merge of per-thread stats in a fixed order; result valid in thread 0.
+// Block-wide merge of per-thread stats (a butterfly in each warp, then one over the
+// warps' results in warp 0; the merge is symmetric, so the result is deterministic);
+// result valid in thread 0.  The caller
+// synchronises before sm.red is written again.
 template <int P, typename A>
 __device__ Stats<A> block_stats(Stats<A> v, StepSmem<P> &sm) {
+    constexpr bool F = Prec<P>::kHalf;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        Stats<A> w = stats_shfl_xor(v, o);
-        if ((lane & o) == 0) stats_merge<Prec<P>::kHalf>(v, w); else { stats_merge<Prec<P>::kHalf>(w, v); v = w; }
-    }
+    for (int o = 1; o < 32; o <<= 1) v = stats_merge<F>(v, stats_shfl_xor(v, o));
     if (lane == 0) sm.red[warp] = v;
     __syncthreads();
-    Stats<A> r;
-    if (threadIdx.x == 0) {
-        r = sm.red[0];
-        for (int w = 1; w < kWarps; ++w) stats_merge<Prec<P>::kHalf>(r, sm.red[w]);
-    }
-    __syncthreads();
-    return r;
-}
-
-// Block-wide sum of a 128-bit value (exact, so the order is irrelevant); valid in thread 0.
-template <int P>
-__device__ U128 block_sum128(U128 v, StepSmem<P> &sm) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (warp == 0) {
+        v = (lane < kWarps) ? sm.red[lane] : Stats<A>{neg_inf<A>(), 0, 0, 0};
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = add128(v, shfl_down128(v, o));
-    if (lane == 0) sm.red128[warp] = v;
-    __syncthreads();
-    U128 r{0ull, 0ull};
-    if (threadIdx.x == 0)
-        for (int w = 0; w < kWarps; ++w) r = add128(r, sm.red128[w]);
-    __syncthreads();
-    return r;
+        for (int o = 1; o < kWarps; o <<= 1) v = stats_merge<F>(v, stats_shfl_xor(v, o));
+    }
+    return v;
 }
 
 // Decoupled lookback over the tracker's earlier tiles, kThreads tiles per round (thread
 // i inspects tile base - i).  Sums the fixed-point aggregates back to the nearest tile
-// that has published its inclusive prefix.  Whole block; result valid in thread 0.
+// that has published its inclusive prefix.  Whole block, one barrier per round; the
+// result is valid in every thread.
 template <int P>
-__device__ U128 lookback(const LookbackDesc *look, int lt, uint32_t ep, TrackerState *st, StepSmem<P> &sm) {
-    const int tid = threadIdx.x;
+__device__ U128 lookback(const LookbackDesc *look, int lt, uint64_t tag, TrackerState *st, StepSmem<P> &sm) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     U128 total{0ull, 0ull};
     for (int base = lt - 1; base >= 0; base -= kThreads) {
         const int idx = base - tid;
         uint32_t f = 0u;
         U128 v{0ull, 0ull};
         if (idx >= 0) {
-            f = wait_flag(&look[idx], ep, st);
-            if (f == 0u) f = 2u;   // timed out: an inclusive zero (the step is flagged invalid)
-            else v = ld_relaxed_u128((f & 3u) == 2u ? &look[idx].incl_lo : &look[idx].agg_lo);
+            f = wait_desc(&look[idx], tag, st, v);
+            if (f == 0u) { f = 2u; v = U128{0ull, 0ull}; }   // timed out: an inclusive zero (step flagged invalid)
         }
-        if (tid == 0) sm.qmin = kThreads;
+        // the warp's nearest inclusive predecessor (lowest lane); lanes past it contribute 0
+        const uint32_t incl = __ballot_sync(0xffffffffu, f == 2u);
+        const int first = incl ? __ffs(static_cast<int>(incl)) - 1 : 32;
+        if (lane > first) v = U128{0ull, 0ull};
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = add128(v, shfl_down128(v, o));
+        if (lane == 0) { sm.red128[warp] = v; sm.warp_incl[warp] = incl != 0u; }
         __syncthreads();
-        if (idx >= 0 && (f & 3u) == 2u) atomicMin(&sm.qmin, tid);
-        __syncthreads();
-        const int q = sm.qmin;      // nearest inclusive predecessor, kThreads if none here
-        if (idx < 0 || tid > q) v = U128{0ull, 0ull};
-        total = add128(total, block_sum128<P>(v, sm));
-        if (q < kThreads) break;
+        bool done = false;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+            const U128 x = sm.red128[w];
+            const int inc = sm.warp_incl[w];
+            if (!done) total = add128(total, x);
+            done = done || inc != 0;
+        }
+        if (done) break;
+        __syncthreads();           // red128 is rewritten by the next round
     }
     return total;
 }
@@ -395,46 +478,74 @@ template <int P>
 __device__ void finalize_tracker(const TrackerDev &T, TrackerState *st, StepSmem<P> &sm) {
     using acc_t = typename Prec<P>::acc_t;
     Stats<acc_t> v{neg_inf<acc_t>(), 0, 0, 0};
+    const uint64_t tg = partial_tag(sm.st.epoch);
     for (int i = threadIdx.x; i < T.ntiles; i += kThreads) {
-        const double *p = &T.part[i].m;
         Stats<acc_t> w;
-        w.m = static_cast<acc_t>(__ldcg(p + 0));
-        w.s = static_cast<acc_t>(__ldcg(p + 1));
-        w.sx = static_cast<acc_t>(__ldcg(p + 2));
-        w.sy = static_cast<acc_t>(__ldcg(p + 3));
-        stats_merge<Prec<P>::kHalf>(v, w);
+        if constexpr (sizeof(acc_t) == 8) {
+            const double *p = T.part[i].d;
+            w.m = __ldcg(p + 0);
+            w.s = __ldcg(p + 1);
+            w.sx = __ldcg(p + 2);
+            w.sy = __ldcg(p + 3);
+        } else {
+            uint64_t q[4];
+            wait_partial(&T.part[i], tg, st, q);
+            w.m = __uint_as_float(static_cast<uint32_t>(q[0]));
+            w.s = __uint_as_float(static_cast<uint32_t>(q[1]));
+            w.sx = __uint_as_float(static_cast<uint32_t>(q[2]));
+            w.sy = __uint_as_float(static_cast<uint32_t>(q[3]));
+        }
+        v = stats_merge<Prec<P>::kHalf>(v, w);
     }
     const Stats<acc_t> r = block_stats<P>(v, sm);
     if (threadIdx.x == 0) {
-        const int64_t t = st->t;
+        // The new state is built from the copy in shared memory (this launch's starting
+        // state, which no tile changes) and written with stores only: no load round trip.
+        const TrackerState &o = sm.st;
+        TrackerState n = o;
         const double M = static_cast<double>(r.m);
         const double S = static_cast<double>(r.s);
-        const double ex = st->nx + static_cast<double>(r.sx) / S;
-        const double ey = st->ny + static_cast<double>(r.sy) / S;
-        st->M = M;
-        st->S = S;
-        st->invS = static_cast<double>(static_cast<acc_t>(1) / r.s);
-        st->ax = st->nx;
-        st->ay = st->ny;
-        if (isfinite(ex) && fabs(ex) < 1.0e6) st->nx = floor(ex) + ((ex - floor(ex)) >= 0.5 ? 1.0 : 0.0);
-        if (isfinite(ey) && fabs(ey) < 1.0e6) st->ny = floor(ey) + ((ey - floor(ey)) >= 0.5 ? 1.0 : 0.0);
-        st->M_f = static_cast<float>(r.m);
-        st->invS_f = static_cast<float>(static_cast<acc_t>(1) / r.s);
-        st->axi = st->nxi;
-        st->ayi = st->nyi;
-        st->nxi = static_cast<int32_t>(st->nx);
-        st->nyi = static_cast<int32_t>(st->ny);
-        st->est_x = ex;
-        st->est_y = ey;
-        const int64_t slot = t % T.est_cap;
-        T.est_ring[2 * slot] = ex;
-        T.est_ring[2 * slot + 1] = ey;
-        T.stat_ring[2 * slot] = M;
-        T.stat_ring[2 * slot + 1] = S;
-        st->t = t + 1;
-        st->epoch = st->epoch + 1u;
-        __threadfence();
-        atomicExch(T.done, 0u);
+        double ex, ey;
+        if constexpr (sizeof(acc_t) == 8) {
+            ex = o.nx + static_cast<double>(r.sx) / S;
+            ey = o.ny + static_cast<double>(r.sy) / S;
+        } else {   // the FP32 quotient, then the exact integer anchor added in FP64
+            ex = o.nx + static_cast<double>(r.sx / r.s);
+            ey = o.ny + static_cast<double>(r.sy / r.s);
+        }
+        const acc_t inv = static_cast<acc_t>(1) / r.s;
+        n.M = M;
+        n.S = S;
+        n.invS = static_cast<double>(inv);
+        n.ax = o.nx;
+        n.ay = o.ny;
+        if (isfinite(ex) && fabs(ex) < 1.0e6) n.nx = floor(ex) + ((ex - floor(ex)) >= 0.5 ? 1.0 : 0.0);
+        if (isfinite(ey) && fabs(ey) < 1.0e6) n.ny = floor(ey) + ((ey - floor(ey)) >= 0.5 ? 1.0 : 0.0);
+        n.M_f = static_cast<float>(r.m);
+        n.invS_f = static_cast<float>(inv);
+        n.axi = o.nxi;
+        n.ayi = o.nyi;
+        n.nxi = static_cast<int32_t>(n.nx);
+        n.nyi = static_cast<int32_t>(n.ny);
+        n.est_x = ex;
+        n.est_y = ey;
+        n.t = o.t + 1;
+        n.epoch = o.epoch + 1u;
+        const int64_t slot = o.t % T.est_cap;
+        *reinterpret_cast<double2 *>(T.est_ring + 2 * slot) = make_double2(ex, ey);
+        *reinterpret_cast<double2 *>(T.stat_ring + 2 * slot) = make_double2(M, S);
+        // every field but the sticky status word (another tile may have raised it)
+        st->t = n.t;
+        st->epoch = n.epoch;
+        constexpr int kHead = static_cast<int>(offsetof(TrackerState, M));
+        static_assert(kHead == 16 && sizeof(TrackerState) % 16 == 0, "TrackerState layout");
+        const uint4 *src = reinterpret_cast<const uint4 *>(reinterpret_cast<const char *>(&n) + kHead);
+        uint4 *dst = reinterpret_cast<uint4 *>(reinterpret_cast<char *>(st) + kHead);
+#pragma unroll
+        for (int k = 0; k < static_cast<int>(sizeof(TrackerState) - kHead) / 16; ++k) dst[k] = src[k];
+        // every tile of this launch has counted; the next launch sees the reset after the
+        // kernel boundary
+        *T.done = 0u;
     }
 }
 
@@ -477,7 +588,7 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
     const int k0 = lt * kTile;
     const int cnt = (N - k0) < kTile ? (N - k0) : kTile;
     const int64_t t = sm.st.t;
-    const uint32_t ep = sm.st.epoch;
+    const uint64_t dtag = desc_tag(sm.st.epoch);    // this launch's lookback tag
     constexpr bool kF64 = sizeof(acc_t) == 8;    // REF64; the other kernels use no FP64
     const int nxi = sm.st.nxi, nyi = sm.st.nyi;     // anchor of the offspring
     const int axi_anc = sm.st.axi, ayi_anc = sm.st.ayi;   // anchor of the ancestors
@@ -499,40 +610,49 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
 
     // ------------------------------------------------------------ 1a. local scan of e
     acc_t loc[kItems];
-    uint32_t heavy = 0u;          // bit m: element tid*kItems+m carries a non-negligible weight
     U128 aggx{0ull, 0ull};
+    // bounding box of the ancestors with non-negligible weight (absolute pixel units)
+    float bx0 = FLT_MAX, bx1 = -FLT_MAX, by0 = FLT_MAX, by1 = -FLT_MAX;
+    const int eb = tid * kItems;  // blocked arrangement: thread tid owns elements eb .. eb+kItems-1
     if (t > 0) {
         const lik_t *__restrict__ Lin = static_cast<const lik_t *>(T.pl[in]);
         const pos_t *__restrict__ Xin = static_cast<const pos_t *>(T.px[in]);
         const pos_t *__restrict__ Yin = static_cast<const pos_t *>(T.py[in]);
         const acc_t M = kF64 ? static_cast<acc_t>(sm.st.M) : static_cast<acc_t>(sm.st.M_f);
-        for (int e = tid; e < cnt; e += kThreads) {
-            sm.ax[e] = Xin[k0 + e];
-            sm.ay[e] = Yin[k0 + e];
-        }
-        // blocked arrangement: thread tid owns elements tid*kItems .. +kItems-1
         lik_t lv[kItems];
-        if (tid * kItems + kItems <= cnt) {
-            // kItems consecutive values, 16-byte aligned (k0 and tid*kItems are multiples of 8)
-            constexpr int kVec = sizeof(lik_t) * kItems / 16;
-            const uint4 *src = reinterpret_cast<const uint4 *>(Lin + k0 + tid * kItems);
-            uint4 *dst = reinterpret_cast<uint4 *>(lv);
-#pragma unroll
-            for (int v = 0; v < kVec; ++v) dst[v] = src[v];
+        pos_t xv[kItems], yv[kItems];
+        if (eb + kItems <= cnt) {
+            // kItems consecutive values of each array, 16-byte aligned (k0 and eb are
+            // multiples of kItems = 8 and the buffers are 16-byte aligned)
+            load_items(lv, Lin + k0 + eb);
+            load_items(xv, Xin + k0 + eb);
+            load_items(yv, Yin + k0 + eb);
         } else {
 #pragma unroll
             for (int m = 0; m < kItems; ++m) {
-                const int e = tid * kItems + m;
+                const int e = eb + m;
                 lv[m] = (e < cnt) ? Lin[k0 + e] : lik_t{};
+                xv[m] = (e < cnt) ? Xin[k0 + e] : pos_t{};
+                yv[m] = (e < cnt) ? Yin[k0 + e] : pos_t{};
             }
         }
+        // the offspring loop reads its ancestors' positions from shared memory
+        store_items(sm.ax + eb, xv);
+        store_items(sm.ay + eb, yv);
+        const float sx = Tr::kHalf ? static_cast<float>(axi_anc) : 0.0f;
+        const float sy = Tr::kHalf ? static_cast<float>(ayi_anc) : 0.0f;
         acc_t run = static_cast<acc_t>(0);
 #pragma unroll
         for (int m = 0; m < kItems; ++m) {
-            const int e = tid * kItems + m;
+            const int e = eb + m;
             acc_t v = static_cast<acc_t>(0);
             if (e < cnt) v = wexp<Tr::kHalf>(to_acc(lv[m]) - M);
-            if (v > static_cast<acc_t>(9.3132257461547852e-10)) heavy |= 1u << m;   // 2^-30
+            if (v > static_cast<acc_t>(9.3132257461547852e-10)) {   // weight above 2^-30 of the max
+                const float xa = static_cast<float>(to_acc(xv[m])) + sx;
+                const float ya = static_cast<float>(to_acc(yv[m])) + sy;
+                bx0 = fminf(bx0, xa); bx1 = fmaxf(bx1, xa);
+                by0 = fminf(by0, ya); by1 = fmaxf(by1, ya);
+            }
             run = (m == 0) ? v : run + v;
             loc[m] = run;
         }
@@ -548,7 +668,11 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
         if (lane == 0) xex = static_cast<acc_t>(0);
         __syncthreads();
         acc_t wpre = static_cast<acc_t>(0);
-        for (int w = 0; w < warp; ++w) wpre += sm.warp_sum[w];
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+            const acc_t v = sm.warp_sum[w];
+            if (w < warp) wpre += v;
+        }
         const acc_t off = wpre + xex;
         if (tid != 0) {
 #pragma unroll
@@ -565,7 +689,11 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
         acc_t mex = __shfl_up_sync(0xffffffffu, mx, 1);
         __syncthreads();
         acc_t wmax = static_cast<acc_t>(0);
-        for (int w = 0; w < warp; ++w) wmax = fmax(wmax, sm.warp_max[w]);
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+            const acc_t v = sm.warp_max[w];
+            if (w < warp) wmax = fmax(wmax, v);
+        }
         if (lane == 0) mex = wmax; else mex = fmax(mex, wmax);
 #pragma unroll
         for (int m = 0; m < kItems; ++m) loc[m] = fmax(loc[m], mex);
@@ -580,43 +708,17 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
         }
         __syncthreads();
         aggx = to_fixed(sm.agg);
-        const uint32_t tag = (ep & 0x3fffffffu) << 2;
-        if (tid == 0) {
-            if (lt == 0) {
-                look[0].incl_lo = aggx.lo;
-                look[0].incl_hi = aggx.hi;
-                st_release_u32(&look[0].flag, tag | 2u);
-            } else {
-                look[lt].agg_lo = aggx.lo;
-                look[lt].agg_hi = aggx.hi;
-                st_release_u32(&look[lt].flag, tag | 1u);
-            }
-        }
+        if (tid == 0) desc_publish(&look[lt], lt == 0 ? 1 : 0, aggx, dtag);   // tile 0: inclusive
+    } else {
+        bx0 = bx1 = T.init_xf;
+        by0 = by1 = T.init_yf;
     }
 
     // ------------------------------------------------------------ 1b. likelihood window
-    // Bounding box of the ancestors with non-negligible weight (absolute pixel units),
-    // widened by the drift and the largest draw: their offspring's pixels fall inside it.
-    // Computed before the lookback, so that the predecessors publish meanwhile.
+    // The bounding box of the heavy ancestors, widened by the drift and 3.5 sigma of the
+    // draw: almost all of their offspring's pixels fall inside it.  Computed before the
+    // lookback, so that the predecessors publish meanwhile.
     {
-        float bx0 = FLT_MAX, bx1 = -FLT_MAX, by0 = FLT_MAX, by1 = -FLT_MAX;
-        if (t > 0) {
-            const float sx = Tr::kHalf ? static_cast<float>(axi_anc) : 0.0f;
-            const float sy = Tr::kHalf ? static_cast<float>(ayi_anc) : 0.0f;
-#pragma unroll
-            for (int m = 0; m < kItems; ++m) {
-                if (heavy & (1u << m)) {
-                    const int e = tid * kItems + m;
-                    const float xv = static_cast<float>(to_acc(sm.ax[e])) + sx;
-                    const float yv = static_cast<float>(to_acc(sm.ay[e])) + sy;
-                    bx0 = fminf(bx0, xv); bx1 = fmaxf(bx1, xv);
-                    by0 = fminf(by0, yv); by1 = fmaxf(by1, yv);
-                }
-            }
-        } else {
-            bx0 = bx1 = T.init_xf;
-            by0 = by1 = T.init_yf;
-        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             bx0 = fminf(bx0, __shfl_xor_sync(0xffffffffu, bx0, o));
@@ -627,12 +729,21 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
         if (lane == 0) { sm.box[warp][0] = bx0; sm.box[warp][1] = bx1; sm.box[warp][2] = by0; sm.box[warp][3] = by1; }
         __syncthreads();
         if (tid == 0) {
+#pragma unroll
             for (int w = 1; w < kWarps; ++w) {
-                bx0 = fminf(bx0, sm.box[w][0]); bx1 = fmaxf(bx1, sm.box[w][1]);
-                by0 = fminf(by0, sm.box[w][2]); by1 = fmaxf(by1, sm.box[w][3]);
+                const float4 v = *reinterpret_cast<const float4 *>(sm.box[w]);
+                bx0 = fminf(bx0, v.x); bx1 = fmaxf(bx1, v.y);
+                by0 = fminf(by0, v.z); by1 = fmaxf(by1, v.w);
             }
-            const float mxr = fabsf(T.drift_xf) + kWindowSigmas * T.sigma_xf + 1.0f;
-            const float myr = fabsf(T.drift_yf) + kWindowSigmas * T.sigma_yf + 1.0f;
+            // Every draw lies within kDrawMax sigma: if that window takes a single pass of
+            // the block, no offspring needs the direct route; otherwise kWindowSigmas.
+            float mxr = fabsf(T.drift_xf) + kDrawMax * T.sigma_xf + 1.0f;
+            float myr = fabsf(T.drift_yf) + kDrawMax * T.sigma_yf + 1.0f;
+            if ((ceilf(bx1 + mxr) - floorf(bx0 - mxr) + 1.0f) * (ceilf(by1 + myr) - floorf(by0 - myr) + 1.0f) >
+                static_cast<float>(kThreads)) {
+                mxr = fabsf(T.drift_xf) + kWindowSigmas * T.sigma_xf + 1.0f;
+                myr = fabsf(T.drift_yf) + kWindowSigmas * T.sigma_yf + 1.0f;
+            }
             int ww = 0, wh = 0, x0 = 0, y0 = 0;
             if (bx0 <= bx1 && by0 <= by1 && bx1 - bx0 < 4096.0f && by1 - by0 < 4096.0f &&
                 fabsf(bx0) < 1.0e6f && fabsf(by0) < 1.0e6f && mxr < 4096.0f && myr < 4096.0f) {
@@ -694,6 +805,7 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
                 sm.table[c] = hk.from_terms(sm.u.term, rw, sm.w, r, cx, cy);
             } else {
                 uint32_t ssum = 0;
+#pragma unroll 4
                 for (int i = 0; i <= 2 * r; ++i) {
                     const uint16_t *p = sm.u.pre + (cy + i) * (rw + 1) + cx + r;
                     const int hw = sm.w[i];
@@ -708,6 +820,8 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
     }
 
     // ------------------------------------------------------------ 1d. lookback, CDF, strata
+    int Jr[kItems];           // J of the thread's elements (frames t > 0)
+    int jb, je;               // the tile's offspring are j in [jb, je)
     if (t > 0) {
         const acc_t invS = kF64 ? static_cast<acc_t>(sm.st.invS) : static_cast<acc_t>(sm.st.invS_f);
         const uint32_t w0 =
@@ -716,14 +830,10 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
         Strata<acc_t> str;
         str.init(N, u0, sizeof(acc_t) == 8 ? static_cast<acc_t>(T.inv_n) : static_cast<acc_t>(T.inv_n_f));
         U128 exclx{0ull, 0ull};
-        if (lt > 0) exclx = lookback<P>(look, lt, ep, st, sm);
+        if (lt > 0) exclx = lookback<P>(look, lt, dtag, st, sm);
         if (tid == 0) {
             const U128 endx = add128(exclx, aggx);
-            if (lt > 0) {
-                look[lt].incl_lo = endx.lo;
-                look[lt].incl_hi = endx.hi;
-                st_release_u32(&look[lt].flag, ((ep & 0x3fffffffu) << 2) | 2u);
-            }
+            if (lt > 0) desc_publish(&look[lt], 1, endx, dtag);
             sm.excl_x = exclx;
             sm.end_x = endx;
         }
@@ -733,35 +843,35 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
         acc_t excl, pend;
         if constexpr (kF64) { excl = from_fixed(sm.excl_x); pend = from_fixed(sm.end_x); }
         else { excl = from_fixed_f(sm.excl_x); pend = from_fixed_f(sm.end_x); }
+        if (tid == 0) sm.jbeg = (lt == 0) ? 0 : str.count_le(fmin(mul_rn(excl, invS), static_cast<acc_t>(1)));
         acc_t cprev = static_cast<acc_t>(-1);
         int jprev = 0;
 #pragma unroll
         for (int m = 0; m < kItems; ++m) {
-            const int e = tid * kItems + m;
+            const int e = eb + m;
+            int J = N;                                   // (elements past the tile: unused)
             if (e < cnt) {
                 const int k = k0 + e;
                 const acc_t Pk = (e == cnt - 1) ? pend : fmin(add_rn(excl, loc[m]), pend);
                 // the normalised CDF cannot exceed 1; the FP32 scan can round above it
                 acc_t C = fmin(mul_rn(Pk, invS), static_cast<acc_t>(1));
-                int J;
                 if (k == N - 1) { C = static_cast<acc_t>(1); J = N; }
                 else if (C == cprev) J = jprev;          // same CDF value, same count
                 else J = str.count_le(C);
                 cprev = C;
                 jprev = J;
-                sm.J[e] = J;
                 if (dbg_cdf) dbg_cdf[k] = C;
             }
+            Jr[m] = J;
         }
-        if (tid == 0) sm.jbeg = (lt == 0) ? 0 : str.count_le(fmin(mul_rn(excl, invS), static_cast<acc_t>(1)));
+        store_items(sm.J + eb, Jr);
         __syncthreads();
-        if (tid == 0) sm.jend = sm.J[cnt - 1];
-        __syncthreads();
+        jb = sm.jbeg;
+        je = sm.J[cnt - 1];
     } else {
-        if (tid == 0) { sm.jbeg = k0; sm.jend = k0 + cnt; }
-        __syncthreads();
+        jb = k0;
+        je = k0 + cnt;
     }
-    const int jb = sm.jbeg, je = sm.jend;
     const int nout = je - jb;
 
     // ------------------------------------------------------------ 1e. ancestor map
@@ -769,36 +879,47 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
     // first offspring of every element with offspring, then a running max fills the gaps.
     const bool use_map = (t > 0) && nout <= kMapMax;
     if (use_map) {
-        for (int i = tid; i < nout; i += kThreads) sm.u.map[i] = 0;
+        for (int i = tid * 8; i < nout; i += kThreads * 8)
+            *reinterpret_cast<uint4 *>(sm.u.map + i) = make_uint4(0u, 0u, 0u, 0u);
+        int jpt = __shfl_up_sync(0xffffffffu, Jr[kItems - 1], 1);   // J of element eb - 1
+        if (lane == 0) jpt = (tid == 0) ? jb : sm.J[eb - 1];
         __syncthreads();
 #pragma unroll
         for (int m = 0; m < kItems; ++m) {
-            const int e = tid * kItems + m;
-            if (e < cnt) {
-                const int jp = e ? sm.J[e - 1] : jb;
-                if (sm.J[e] > jp) sm.u.map[jp - jb] = static_cast<uint16_t>(e + 1);
-            }
+            const int jp = m ? Jr[m - 1] : jpt;
+            if (eb + m < cnt && Jr[m] > jp) sm.u.map[jp - jb] = static_cast<uint16_t>(eb + m + 1);
         }
         __syncthreads();
-        const int ch = (nout + kThreads - 1) / kThreads;
-        const int i0 = tid * ch, i1 = min(nout, i0 + ch);
-        int run = 0;
-        for (int i = i0; i < i1; ++i) run = max(run, static_cast<int>(sm.u.map[i]));
-        int xm = run;
+        // thread tid fills entries [tid*ch, tid*ch + ch) (16-byte vectors); entries past
+        // nout are never read, and the max only carries forward, into entries past nout
+        const int nv = (nout > kThreads * 8) ? 2 : 1;
+        uint4 *mv = reinterpret_cast<uint4 *>(sm.u.map) + tid * nv;
+        uint4 c0 = mv[0], c1 = make_uint4(0u, 0u, 0u, 0u);
+        if (nv == 2) c1 = mv[1];
+        uint32_t m2 = __vmaxu2(__vmaxu2(__vmaxu2(c0.x, c0.y), __vmaxu2(c0.z, c0.w)),
+                               __vmaxu2(__vmaxu2(c1.x, c1.y), __vmaxu2(c1.z, c1.w)));
+        int xm = static_cast<int>(max(m2 & 0xffffu, m2 >> 16));
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int y = __shfl_up_sync(0xffffffffu, xm, o);
             if (lane >= o) xm = max(xm, y);
         }
         if (lane == 31) sm.warp_imax[warp] = xm;
-        int xex = __shfl_up_sync(0xffffffffu, xm, 1);
-        if (lane == 0) xex = 0;
+        int run = __shfl_up_sync(0xffffffffu, xm, 1);
+        if (lane == 0) run = 0;
         __syncthreads();
-        for (int w = 0; w < warp; ++w) xex = max(xex, sm.warp_imax[w]);
-        run = xex;
-        for (int i = i0; i < i1; ++i) {
-            run = max(run, static_cast<int>(sm.u.map[i]));
-            sm.u.map[i] = static_cast<uint16_t>(run);
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+            const int v = sm.warp_imax[w];
+            if (w < warp) run = max(run, v);
+        }
+        uint32_t *wv = reinterpret_cast<uint32_t *>(mv);
+        for (int i = 0; i < 4 * nv; ++i) {
+            const uint32_t wd = wv[i];
+            const int r1 = max(run, static_cast<int>(wd & 0xffffu));
+            const int r2 = max(r1, static_cast<int>(wd >> 16));
+            wv[i] = static_cast<uint32_t>(r1) | (static_cast<uint32_t>(r2) << 16);
+            run = r2;
         }
         __syncthreads();
     }
@@ -891,8 +1012,7 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
             } else if (v1) {
                 Xout[j1] = x1; Yout[j1] = y1; Lout[j1] = L1;
             }
-            if (v0) stats_add<false>(stats, L0, x0 - nxa_a, y0 - nya_a);
-            if (v1) stats_add<false>(stats, L1, x1 - nxa_a, y1 - nya_a);
+            stats_add2<false>(stats, v0, L0, x0 - nxa_a, y0 - nya_a, v1, L1, x1 - nxa_a, y1 - nya_a);
         } else {
             // ---------------- F16 / BF16: half2 lanes = particles (j0, j1), offsets from the anchor
             using OPS = HalfOps<H>;
@@ -933,8 +1053,7 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
             } else if (v1) {
                 Xout[j1] = OPS::hi_h(ox); Yout[j1] = OPS::hi_h(oy); Lout[j1] = l1;
             }
-            if (v0) stats_add<true>(stats, OPS::to_f(l0), OPS::lo(ox), OPS::lo(oy));
-            if (v1) stats_add<true>(stats, OPS::to_f(l1), OPS::hi(ox), OPS::hi(oy));
+            stats_add2<true>(stats, v0, OPS::to_f(l0), OPS::lo(ox), OPS::lo(oy), v1, OPS::to_f(l1), OPS::hi(ox), OPS::hi(oy));
         }
     }
 
@@ -942,12 +1061,20 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
     const Stats<acc_t> tot = block_stats<P>(stats, sm);
     if (tid == 0) {
         TilePartial *p = &T.part[lt];
-        p->m = static_cast<double>(tot.m);
-        p->s = static_cast<double>(tot.s);
-        p->sx = static_cast<double>(tot.sx);
-        p->sy = static_cast<double>(tot.sy);
-        // release: the partial is visible before the count; acquire: the last tile sees all
-        const uint32_t prev = atom_add_acq_rel(T.done, 1u);
+        uint32_t prev;
+        if constexpr (kF64) {
+            p->d[0] = tot.m;
+            p->d[1] = tot.s;
+            p->d[2] = tot.sx;
+            p->d[3] = tot.sy;
+            // release: the partial is visible before the count; acquire: the last tile sees all
+            prev = atom_add_acq_rel(T.done, 1u);
+        } else {
+            const uint64_t tg = partial_tag(sm.st.epoch);
+            st_relaxed_v2(&p->w[0], tg | __float_as_uint(tot.m), tg | __float_as_uint(tot.s));
+            st_relaxed_v2(&p->w[2], tg | __float_as_uint(tot.sx), tg | __float_as_uint(tot.sy));
+            prev = atom_add_relaxed(T.done, 1u);
+        }
         sm.last = (prev == static_cast<uint32_t>(T.ntiles - 1)) ? 1u : 0u;
     }
     __syncthreads();
@@ -984,7 +1111,8 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<P>::value) step_kernel(con
 // Test hook: the lookback wait on a descriptor that nobody publishes, with a short limit;
 // it must give up, raise the timeout bit and return.
 __global__ void wait_probe_kernel(const LookbackDesc *d, TrackerState *st, uint32_t limit) {
-    wait_flag(d, 1u, st, limit);
+    U128 v;
+    wait_desc(d, desc_tag(1u), st, v, limit);
 }
 
 __global__ void philox_kernel(const uint4 *ctrs, int64_t n, uint32_t k0, uint32_t k1, uint4 *out) {

@@ -84,3 +84,20 @@ def test_noalloc_rejects_too_many_particles(pf):
                                         ctypes.c_void_p(1), 64, ctypes.c_void_p(1), ctypes.c_void_p(1),
                                         ctypes.c_void_p(1), ctypes.byref(out), None)
     assert rc == pf.PF_ERR_ARG
+
+
+def test_noalloc_rejects_misaligned_buffers(pf):
+    import torch
+    N = 64
+    cfg = pf.make_config(64, 64, N, 3, "f32")
+    hdr = pf.PfStateHeader(magic=0x31534650, precision=cfg.precision, num_particles=N, t=0)
+    frame = torch.zeros((64, 64), dtype=torch.uint8, device="cuda")
+    buf = torch.zeros(4 * N + 4, dtype=torch.float32, device="cuda")
+    base = buf.data_ptr()
+    out = pf.PfStateHeader()
+    # x_out 4 bytes past a 16-byte boundary: rejected before any work is queued
+    rc = pf.lib().pf_step_frame_noalloc(ctypes.byref(cfg), ctypes.byref(hdr), None, None, None,
+                                        ctypes.c_void_p(frame.data_ptr()), 64,
+                                        ctypes.c_void_p(base + 4), ctypes.c_void_p(base + 16 * 32),
+                                        ctypes.c_void_p(base + 16 * 48), ctypes.byref(out), None)
+    assert rc == pf.PF_ERR_ARG
