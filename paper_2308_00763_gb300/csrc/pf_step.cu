@@ -353,17 +353,24 @@ struct HalfLik {
     // from per-pixel terms staged in shared memory (row pitch rw, template centred at
     // column cx + r, row cy + r)
     __device__ H from_terms(const H *tm, int rw, const int8_t *w, int r, int cx, int cy) const {
-        H hacc = HalfOps<H>::from_f(0.0f);
-        float facc = 0.0f;
+        if (half_acc) {
+            H acc = HalfOps<H>::from_f(0.0f);
+            for (int i = 0; i <= 2 * r; ++i) {
+                const int hw = w[i];
+                const H *row = tm + (cy + i) * rw + cx + r;
+#pragma unroll 8
+                for (int dx = -hw; dx <= hw; ++dx) acc = __hadd(acc, row[dx]);
+            }
+            return acc;
+        }
+        float acc = 0.0f;
         for (int i = 0; i <= 2 * r; ++i) {
             const int hw = w[i];
             const H *row = tm + (cy + i) * rw + cx + r;
 #pragma unroll 8
-            for (int dx = -hw; dx <= hw; ++dx) {
-                if (half_acc) hacc = __hadd(hacc, row[dx]); else facc += HalfOps<H>::to_f(row[dx]);
-            }
+            for (int dx = -hw; dx <= hw; ++dx) acc += HalfOps<H>::to_f(row[dx]);
         }
-        return half_acc ? hacc : HalfOps<H>::from_f(facc);
+        return HalfOps<H>::from_f(acc);
     }
 };
 
@@ -385,16 +392,18 @@ struct __align__(16) StepSmem {
         uint16_t map[kMapMax];      // ancestor (tile element + 1) of each offspring
     } u;
     uint8_t pix[kPixBytes];   // integer form: staged frame region
-    acc_t warp_sum[kWarps];
-    acc_t warp_max[kWarps];
+    alignas(16) acc_t warp_sum[kWarps];
+    alignas(16) acc_t warp_max[kWarps];
     alignas(16) float box[kWarps][4];
-    int warp_imax[kWarps];
+    alignas(16) int warp_imax[kWarps];
     U128 red128[kWarps];
-    int warp_incl[kWarps];
+    alignas(16) int warp_incl[kWarps];
     Stats<acc_t> red[kWarps];
     acc_t agg;
     U128 excl_x, end_x;       // exact fixed-point prefix before / after the tile
     int jbeg, jend;
+    double u0d;               // resampling offset u0 of the previous frame
+    float u0f;
     int win_x0, win_y0, win_w, win_h;   // likelihood table window (win_w = 0: none)
     int qmin;
     int8_t w[2 * kMaxRadius + 1];
@@ -429,7 +438,7 @@ __device__ Stats<A> block_stats(Stats<A> v, StepSmem<P> &sm) {
 // Decoupled lookback over the tracker's earlier tiles, kThreads tiles per round (thread
 // i inspects tile base - i).  Sums the fixed-point aggregates back to the nearest tile
 // that has published its inclusive prefix.  Whole block, one barrier per round; the
-// result is valid in every thread.
+// result is valid in thread 0.
 template <int P>
 __device__ U128 lookback(const LookbackDesc *look, int lt, uint64_t tag, TrackerState *st, StepSmem<P> &sm) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -446,19 +455,23 @@ __device__ U128 lookback(const LookbackDesc *look, int lt, uint64_t tag, Tracker
         const uint32_t incl = __ballot_sync(0xffffffffu, f == 2u);
         const int first = incl ? __ffs(static_cast<int>(incl)) - 1 : 32;
         if (lane > first) v = U128{0ull, 0ull};
+        if (base - warp * 32 >= 0) {          // the warp has predecessors in this round
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v = add128(v, shfl_down128(v, o));
-        if (lane == 0) { sm.red128[warp] = v; sm.warp_incl[warp] = incl != 0u; }
-        __syncthreads();
-        bool done = false;
-#pragma unroll
-        for (int w = 0; w < kWarps; ++w) {
-            const U128 x = sm.red128[w];
-            const int inc = sm.warp_incl[w];
-            if (!done) total = add128(total, x);
-            done = done || inc != 0;
+            for (int o = 16; o > 0; o >>= 1) v = add128(v, shfl_down128(v, o));
         }
-        if (done) break;
+        if (lane == 0) { sm.red128[warp] = v; sm.warp_incl[warp] = incl != 0u; }
+        const int found = __syncthreads_or(incl != 0u);
+        if (tid == 0) {
+            bool done = false;
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) {
+                const U128 x = sm.red128[w];
+                const int inc = sm.warp_incl[w];
+                if (!done) total = add128(total, x);
+                done = done || inc != 0;
+            }
+        }
+        if (found) break;
         __syncthreads();           // red128 is rewritten by the next round
     }
     return total;
@@ -727,6 +740,12 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
             by1 = fmaxf(by1, __shfl_xor_sync(0xffffffffu, by1, o));
         }
         if (lane == 0) { sm.box[warp][0] = bx0; sm.box[warp][1] = bx1; sm.box[warp][2] = by0; sm.box[warp][3] = by1; }
+        // the resampling offset u0 of frame t - 1 (Philox tag 1, index 0), once per tile
+        if (t > 0 && tid == 32) {
+            const uint32_t w0 =
+                philox4x32_10(make_uint4(0u, static_cast<uint32_t>(t - 1), 1u, T.tracker_id), T.key_lo, T.key_hi).x;
+            if constexpr (kF64) sm.u0d = uniform_f64(w0); else sm.u0f = uniform_f32(w0);
+        }
         __syncthreads();
         if (tid == 0) {
 #pragma unroll
@@ -824,9 +843,7 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
     int jb, je;               // the tile's offspring are j in [jb, je)
     if (t > 0) {
         const acc_t invS = kF64 ? static_cast<acc_t>(sm.st.invS) : static_cast<acc_t>(sm.st.invS_f);
-        const uint32_t w0 =
-            philox4x32_10(make_uint4(0u, static_cast<uint32_t>(t - 1), 1u, T.tracker_id), T.key_lo, T.key_hi).x;
-        const acc_t u0 = kF64 ? static_cast<acc_t>(uniform_f64(w0)) : static_cast<acc_t>(uniform_f32(w0));
+        const acc_t u0 = kF64 ? static_cast<acc_t>(sm.u0d) : static_cast<acc_t>(sm.u0f);
         Strata<acc_t> str;
         str.init(N, u0, sizeof(acc_t) == 8 ? static_cast<acc_t>(T.inv_n) : static_cast<acc_t>(T.inv_n_f));
         U128 exclx{0ull, 0ull};
@@ -942,12 +959,20 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
     const float shx = static_cast<float>(axi_anc - nxi), shy = static_cast<float>(ayi_anc - nyi);
     const float ix0 = T.init_xf - static_cast<float>(nxi), iy0 = T.init_yf - static_cast<float>(nyi);
 
-    for (int q = (jb >> 1) + tid; q < ((je + 1) >> 1); q += kThreads) {
+    // One pair of offspring (j0, j1) = (2q, 2q + 1).  Compile-time flags: V0 / V1, the
+    // particle lies in [jb, je); FAST, frame t > 0 with the ancestor map and no debug
+    // arrays (the interior pairs of a tile in production take the FAST copy).
+    auto pair = [&](const int q, auto V0c, auto V1c, auto FASTc) {
+        constexpr bool v0 = decltype(V0c)::value, v1 = decltype(V1c)::value;
+        constexpr bool kFast = decltype(FASTc)::value;
         const int j0 = 2 * q, j1 = j0 + 1;
-        const bool v0 = j0 >= jb && j0 < je;
-        const bool v1 = j1 >= jb && j1 < je;
         int e0 = 0, e1 = 0;
-        if (t > 0) {
+        if (kFast) {
+            if (v0) e0 = static_cast<int>(sm.u.map[j0 - jb]) - 1;
+            if (v1) e1 = static_cast<int>(sm.u.map[j1 - jb]) - 1;
+            if (!v0) e0 = e1;
+            if (!v1) e1 = e0;
+        } else if (t > 0) {
             if (use_map) {
                 e0 = v0 ? static_cast<int>(sm.u.map[j0 - jb]) - 1 : 0;
                 e1 = v1 ? static_cast<int>(sm.u.map[j1 - jb]) - 1 : 0;
@@ -1055,6 +1080,19 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
             }
             stats_add2<true>(stats, v0, OPS::to_f(l0), OPS::lo(ox), OPS::lo(oy), v1, OPS::to_f(l1), OPS::hi(ox), OPS::hi(oy));
         }
+    };
+    {
+        using TT = std::true_type;
+        using FF = std::false_type;
+        const int qi0 = (jb + 1) >> 1, qi1 = je >> 1;   // pairs with both particles in [jb, je)
+        if (t > 0 && use_map && !dbg_anc) {
+            for (int q = qi0 + tid; q < qi1; q += kThreads) pair(q, TT{}, TT{}, TT{});
+        } else {
+            for (int q = qi0 + tid; q < qi1; q += kThreads) pair(q, TT{}, TT{}, FF{});
+        }
+        // the pairs that straddle the ends of [jb, je)
+        if (tid == 0 && (jb & 1) && jb < je) pair(jb >> 1, FF{}, TT{}, FF{});
+        if (tid == kThreads - 1 && (je & 1) && je > jb) pair(je >> 1, TT{}, FF{}, FF{});
     }
 
     // ------------------------------------------------------------ 5. tile partial + finalise
