@@ -48,6 +48,7 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kTableMax = 4096;            // pixels of the per-tile likelihood table
 constexpr int kRoiMax = 8192;              // staged frame pixels (window + template margin)
 constexpr int kMapMax = 8192;              // offspring of a tile served by the ancestor map
+constexpr int kOffMax = 1024;              // template entries served by the offset list (r <= 17)
 constexpr uint32_t kSpinLimit = 1u << 22;  // bounded waits: ~1 s with backoff
 // Half-width of the likelihood window in standard deviations of the transition noise.
 // Every draw is below sqrt(-2 ln 2^-24) = 5.77 in magnitude (kDrawMax, rounded up).  When
@@ -350,6 +351,20 @@ struct HalfLik {
         }
         return half_acc ? hacc : HalfOps<H>::from_f(facc);
     }
+    // the same sum through a list of template offsets (row-major over D, so the same
+    // order as from_terms and at)
+    __device__ H from_offsets(const H *base, const uint16_t *off, int D) const {
+        if (half_acc) {
+            H acc = HalfOps<H>::from_f(0.0f);
+#pragma unroll 8
+            for (int k = 0; k < D; ++k) acc = __hadd(acc, base[off[k]]);
+            return acc;
+        }
+        float acc = 0.0f;
+#pragma unroll 8
+        for (int k = 0; k < D; ++k) acc += HalfOps<H>::to_f(base[off[k]]);
+        return HalfOps<H>::from_f(acc);
+    }
     // from per-pixel terms staged in shared memory (row pitch rw, template centred at
     // column cx + r, row cy + r)
     __device__ H from_terms(const H *tm, int rw, const int8_t *w, int r, int cx, int cy) const {
@@ -381,7 +396,6 @@ struct __align__(16) StepSmem {
     using pos_t = typename Tr::pos_t;
     using lik_t = typename Tr::lik_t;
     using acc_t = typename Tr::acc_t;
-    static constexpr int kPixBytes = Tr::kHalf ? 16 : kRoiMax;
     pos_t ax[kTile];          // ancestor positions of the tile (previous frame)
     pos_t ay[kTile];
     int32_t J[kTile];         // J[e] = strata assigned to particles k0..k0+e (cumulative)
@@ -391,7 +405,7 @@ struct __align__(16) StepSmem {
         lik_t term[kRoiMax];        // half form: per-pixel Eq. 4 terms of the staged region
         uint16_t map[kMapMax];      // ancestor (tile element + 1) of each offspring
     } u;
-    uint8_t pix[kPixBytes];   // integer form: staged frame region
+    alignas(16) uint16_t toff[kOffMax];   // half form: template offsets in the staged region
     alignas(16) acc_t warp_sum[kWarps];
     alignas(16) acc_t warp_max[kWarps];
     alignas(16) float box[kWarps][4];
@@ -487,66 +501,74 @@ __device__ __forceinline__ int upper_index(const int32_t *J, int n, int j) {
     return lo;
 }
 
+// Merge of the tracker's tile partials (one per thread, all loads in flight, then the
+// block merge: deterministic) and the new state, by the tile that completed the tracker.
 template <int P>
 __device__ void finalize_tracker(const TrackerDev &T, TrackerState *st, StepSmem<P> &sm) {
     using acc_t = typename Prec<P>::acc_t;
+    constexpr bool kF64 = sizeof(acc_t) == 8;
+    constexpr bool F = Prec<P>::kHalf;
     Stats<acc_t> v{neg_inf<acc_t>(), 0, 0, 0};
     const uint64_t tg = partial_tag(sm.st.epoch);
     for (int i = threadIdx.x; i < T.ntiles; i += kThreads) {
         Stats<acc_t> w;
-        if constexpr (sizeof(acc_t) == 8) {
+        if constexpr (kF64) {
             const double *p = T.part[i].d;
-            w.m = __ldcg(p + 0);
-            w.s = __ldcg(p + 1);
-            w.sx = __ldcg(p + 2);
-            w.sy = __ldcg(p + 3);
+            w = Stats<acc_t>{__ldcg(p + 0), __ldcg(p + 1), __ldcg(p + 2), __ldcg(p + 3)};
         } else {
             uint64_t q[4];
             wait_partial(&T.part[i], tg, st, q);
-            w.m = __uint_as_float(static_cast<uint32_t>(q[0]));
-            w.s = __uint_as_float(static_cast<uint32_t>(q[1]));
-            w.sx = __uint_as_float(static_cast<uint32_t>(q[2]));
-            w.sy = __uint_as_float(static_cast<uint32_t>(q[3]));
+            w = Stats<acc_t>{__uint_as_float(static_cast<uint32_t>(q[0])), __uint_as_float(static_cast<uint32_t>(q[1])),
+                             __uint_as_float(static_cast<uint32_t>(q[2])), __uint_as_float(static_cast<uint32_t>(q[3]))};
         }
-        v = stats_merge<Prec<P>::kHalf>(v, w);
+        v = stats_merge<F>(v, w);
     }
-    const Stats<acc_t> r = block_stats<P>(v, sm);
+    v = block_stats<P>(v, sm);
     if (threadIdx.x == 0) {
+        const Stats<acc_t> r = v;
         // The new state is built from the copy in shared memory (this launch's starting
         // state, which no tile changes) and written with stores only: no load round trip.
         const TrackerState &o = sm.st;
         TrackerState n = o;
-        const double M = static_cast<double>(r.m);
-        const double S = static_cast<double>(r.s);
-        double ex, ey;
-        if constexpr (sizeof(acc_t) == 8) {
-            ex = o.nx + static_cast<double>(r.sx) / S;
-            ey = o.ny + static_cast<double>(r.sy) / S;
-        } else {   // the FP32 quotient, then the exact integer anchor added in FP64
-            ex = o.nx + static_cast<double>(r.sx / r.s);
-            ey = o.ny + static_cast<double>(r.sy / r.s);
-        }
         const acc_t inv = static_cast<acc_t>(1) / r.s;
-        n.M = M;
-        n.S = S;
+        double ex, ey;
+        if constexpr (kF64) {
+            ex = o.nx + r.sx / r.s;
+            ey = o.ny + r.sy / r.s;
+            if (isfinite(ex) && fabs(ex) < 1.0e6) n.nx = floor(ex) + ((ex - floor(ex)) >= 0.5 ? 1.0 : 0.0);
+            if (isfinite(ey) && fabs(ey) < 1.0e6) n.ny = floor(ey) + ((ey - floor(ey)) >= 0.5 ? 1.0 : 0.0);
+            n.nxi = static_cast<int32_t>(n.nx);
+            n.nyi = static_cast<int32_t>(n.ny);
+        } else {
+            // FP32 quotient; the next anchor in FP32 / integers (FP64 only to widen the
+            // results the host reads)
+            const float qx = r.sx / r.s, qy = r.sy / r.s;
+            const float fx = static_cast<float>(o.nxi) + qx, fy = static_cast<float>(o.nyi) + qy;
+            if (isfinite(fx) && fabsf(fx) < 1.0e6f) n.nxi = __float2int_rd(fx + 0.5f);
+            if (isfinite(fy) && fabsf(fy) < 1.0e6f) n.nyi = __float2int_rd(fy + 0.5f);
+            n.nx = static_cast<double>(n.nxi);
+            n.ny = static_cast<double>(n.nyi);
+            ex = o.nx + static_cast<double>(qx);
+            ey = o.ny + static_cast<double>(qy);
+        }
+        n.M = static_cast<double>(r.m);
+        n.S = static_cast<double>(r.s);
         n.invS = static_cast<double>(inv);
         n.ax = o.nx;
         n.ay = o.ny;
-        if (isfinite(ex) && fabs(ex) < 1.0e6) n.nx = floor(ex) + ((ex - floor(ex)) >= 0.5 ? 1.0 : 0.0);
-        if (isfinite(ey) && fabs(ey) < 1.0e6) n.ny = floor(ey) + ((ey - floor(ey)) >= 0.5 ? 1.0 : 0.0);
         n.M_f = static_cast<float>(r.m);
         n.invS_f = static_cast<float>(inv);
         n.axi = o.nxi;
         n.ayi = o.nyi;
-        n.nxi = static_cast<int32_t>(n.nx);
-        n.nyi = static_cast<int32_t>(n.ny);
         n.est_x = ex;
         n.est_y = ey;
         n.t = o.t + 1;
         n.epoch = o.epoch + 1u;
-        const int64_t slot = o.t % T.est_cap;
+        const int64_t slot = (o.t >= 0 && o.t < 0x7fffffffll)
+                                 ? static_cast<int64_t>(static_cast<uint32_t>(o.t) % static_cast<uint32_t>(T.est_cap))
+                                 : o.t % T.est_cap;
         *reinterpret_cast<double2 *>(T.est_ring + 2 * slot) = make_double2(ex, ey);
-        *reinterpret_cast<double2 *>(T.stat_ring + 2 * slot) = make_double2(M, S);
+        *reinterpret_cast<double2 *>(T.stat_ring + 2 * slot) = make_double2(n.M, n.S);
         // every field but the sticky status word (another tile may have raised it)
         st->t = n.t;
         st->epoch = n.epoch;
@@ -796,32 +818,48 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
 
     // ------------------------------------------------------------ 1c. likelihood table
     if (cells > 0) {
-        // stage the frame region the window's templates cover (clamped to the frame)
+        // stage the frame region the window's templates cover (clamped to the frame);
+        // warp w takes rows w, w + kWarps, ...; its lanes walk the row
         const int rx0 = wx0 - r, ry0 = wy0 - r, rw = ww + 2 * r, rh = wh + 2 * r;
-        // warp w stages rows w, w + kWarps, ...; its lanes walk the row
+        const bool use_off = Tr::kHalf && T.D <= kOffMax;
         for (int yy = warp; yy < rh; yy += kWarps) {
             const uint8_t *row = fv.p + static_cast<int64_t>(clampi(ry0 + yy, 0, fv.H - 1)) * fv.pitch;
-            for (int xx = lane; xx < rw; xx += 32) {
-                const uint32_t I = __ldg(row + clampi(rx0 + xx, 0, fv.W - 1));
-                if constexpr (Tr::kHalf) sm.u.term[yy * rw + xx] = hk.term(I);
-                else sm.pix[yy * rw + xx] = static_cast<uint8_t>(I);
+            if constexpr (Tr::kHalf) {
+                for (int xx = lane; xx < rw; xx += 32)
+                    sm.u.term[yy * rw + xx] = hk.term(__ldg(row + clampi(rx0 + xx, 0, fv.W - 1)));
+            } else {
+                // integer form: exclusive row prefix sums pre[y * (rw + 1) + x] = sum of the
+                // row's pixels 0 .. x-1 (uint16, modular), by a warp scan per 32 columns
+                uint16_t *pre = sm.u.pre + yy * (rw + 1);
+                if (lane == 0) pre[0] = 0;
+                uint32_t carry = 0;
+                for (int x0 = 0; x0 < rw; x0 += 32) {
+                    const int xx = x0 + lane;
+                    uint32_t v = (xx < rw) ? static_cast<uint32_t>(__ldg(row + clampi(rx0 + xx, 0, fv.W - 1))) : 0u;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+                        if (lane >= o) v += y;
+                    }
+                    if (xx < rw) pre[xx + 1] = static_cast<uint16_t>(carry + v);
+                    carry += __shfl_sync(0xffffffffu, v, 31);
+                }
+            }
+        }
+        // template offsets of the half form: entry k (row-major over D) of the template of
+        // cell (cx, cy) is the term at cy * rw + cx + toff[k]
+        if (use_off) {
+            for (int k = tid; k < T.D; k += kThreads) {   // entry k: row i, column dx
+                int i = 0, c0 = 0, hw = sm.w[0];
+                while (c0 + 2 * hw + 1 <= k) { c0 += 2 * hw + 1; hw = sm.w[++i]; }
+                sm.toff[k] = static_cast<uint16_t>(i * rw + r + (k - c0 - hw));
             }
         }
         __syncthreads();
-        if constexpr (!Tr::kHalf) {
-            // exclusive row prefix sums: pre[y * (rw + 1) + x] = sum of pix[y][0..x-1]
-            for (int yy = tid; yy < rh; yy += kThreads) {
-                uint32_t acc = 0;
-                uint16_t *p = sm.u.pre + yy * (rw + 1);
-                const uint8_t *q = sm.pix + yy * rw;
-                p[0] = 0;
-                for (int xx = 0; xx < rw; ++xx) { acc += q[xx]; p[xx + 1] = static_cast<uint16_t>(acc); }
-            }
-            __syncthreads();
-        }
         for (int c = tid, cy = tid / ww, cx = tid - (tid / ww) * ww; c < cells; c += kThreads) {
             if constexpr (Tr::kHalf) {
-                sm.table[c] = hk.from_terms(sm.u.term, rw, sm.w, r, cx, cy);
+                if (use_off) sm.table[c] = hk.from_offsets(sm.u.term + cy * rw + cx, sm.toff, T.D);
+                else sm.table[c] = hk.from_terms(sm.u.term, rw, sm.w, r, cx, cy);
             } else {
                 uint32_t ssum = 0;
 #pragma unroll 4
