@@ -229,6 +229,12 @@ __device__ __forceinline__ double from_fixed(U128 x) {
     return __ull2double_rn(top) * scale;
 }
 
+__device__ __forceinline__ U128 shfl_xor128(U128 v, int o) {
+    U128 r;
+    r.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+    r.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+    return r;
+}
 __device__ __forceinline__ U128 shfl_down128(U128 v, int o) {
     U128 r;
     r.lo = __shfl_down_sync(0xffffffffu, v.lo, o);

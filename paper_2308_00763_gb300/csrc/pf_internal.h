@@ -16,7 +16,8 @@ namespace pfk {
 
 constexpr int kThreads = 512;             // threads per CTA of the step kernel
 constexpr int kItems = 8;                 // CDF elements per thread
-constexpr int kTile = kThreads * kItems;  // particles of the resampled frame per tile
+constexpr int kTile = kThreads * kItems;  // largest tile (particles of the resampled frame)
+constexpr int kMinTile = 1024;            // smallest tile chosen for a large tracker
 constexpr int kMaxRadius = 64;
 
 // Device status bits (sticky, per tracker).
@@ -75,7 +76,8 @@ struct TrackerDev {
     int32_t r, D;              // radius and |D|
     int32_t tile_begin, ntiles;
     uint32_t key_lo, key_hi, tracker_id, flags;
-    int32_t est_cap, pad0;
+    int32_t est_cap;
+    int32_t tile;              // particles per tile (multiple of 8, <= kTile)
     // likelihood constants: L = c1 * (2 s - c2 * D) / den  (exact-integer form of Eq. 3)
     double c1, c2, den;
     float kappa, bg_f, fg_f, pad1;   // Eq. 4 scaled form: kappa = 1 / sqrt(50 |D|)
@@ -113,6 +115,12 @@ struct StepLaunch {
 // Host entry points into the kernel translation unit.
 int launch_step(int precision, const StepLaunch &L, int grid, void *stream);
 int step_grid_size(int precision, int total_tiles);
+// Particles per tile for a tracker of n particles: the smallest multiple of 8 that
+// splits n into a whole number of waves of the device's resident CTAs (SMs x CTAs per
+// SM), between kMinTile and kTile.  Every tile then carries the same load.  A function
+// of (precision, n, device model) only, so a tracker tiles the same alone, in a batch
+// and through the allocation-free entry point.
+int step_tile_size(int precision, int64_t n);
 int launch_debug_philox(const uint32_t *d_ctrs, int64_t n, uint64_t seed, uint32_t *d_out,
                         void *stream);
 int launch_wait_probe(void *d_desc, void *d_state, uint32_t limit, void *stream);

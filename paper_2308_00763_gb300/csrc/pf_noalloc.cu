@@ -24,8 +24,9 @@ using namespace pfk;
 
 namespace {
 
-constexpr size_t kScratchBytes = 256 * 1024;
-constexpr int kMaxTiles = (1 << 22) / kTile;          // => at most 2^22 particles
+constexpr size_t kScratchBytes = 384 * 1024;
+constexpr int64_t kMaxParticles = int64_t(1) << 22;
+constexpr int kMaxTiles = static_cast<int>(kMaxParticles / kMinTile);   // tiles hold >= kMinTile
 constexpr int kMaxDevices = 64;
 
 // The scratch array.  In host code its name is only a stand-in for the symbol; the
@@ -98,7 +99,7 @@ extern "C" pf_status pf_step_frame_noalloc(const pf_config *cfg, const pf_state_
     if (!cfg || !state_in || !frame || !x_out || !y_out || !l_out) return PF_ERR_ARG;
     const pf_config &c = *cfg;
     if (c.width < 1 || c.width > 65535 || c.height < 1 || c.height > 65535) return PF_ERR_ARG;
-    if (c.num_particles < 1 || c.num_particles > static_cast<int64_t>(kMaxTiles) * kTile) return PF_ERR_ARG;
+    if (c.num_particles < 1 || c.num_particles > kMaxParticles) return PF_ERR_ARG;
     if (c.disk_radius < 0 || c.disk_radius > kMaxRadius) return PF_ERR_ARG;
     if (c.precision < PF_REF64 || c.precision > PF_BF16) return PF_ERR_ARG;
     if (!(c.sigma_x >= 0) || !(c.sigma_y >= 0) || !isfinite(c.sigma_x) || !isfinite(c.sigma_y)) return PF_ERR_ARG;
@@ -124,12 +125,14 @@ extern "C" pf_status pf_step_frame_noalloc(const pf_config *cfg, const pf_state_
 
     // descriptor of the tracker: the caller's buffers are the ping-pong slots of frame t
     const int64_t N = c.num_particles;
-    const int nt = static_cast<int>((N + kTile - 1) / kTile);
+    const int tile = step_tile_size(c.precision, N);
+    const int nt = static_cast<int>((N + tile - 1) / tile);
+    if (nt > kMaxTiles) return PF_ERR_ARG;
     const int in = static_cast<int>((h.t + 1) & 1), out = static_cast<int>(h.t & 1);
     TrackerDev T;
     memset(&T, 0, sizeof T);
     T.N = N; T.W = c.width; T.H = c.height; T.r = c.disk_radius; T.D = disk_count(c.disk_radius);
-    T.tile_begin = 0; T.ntiles = nt;
+    T.tile_begin = 0; T.ntiles = nt; T.tile = tile;
     T.key_lo = static_cast<uint32_t>(c.seed & 0xffffffffu); T.key_hi = static_cast<uint32_t>(c.seed >> 32);
     T.tracker_id = c.tracker_id; T.flags = c.flags; T.est_cap = 1;
     T.c1 = c.fg_level - c.bg_level; T.c2 = c.bg_level + c.fg_level; T.den = 50.0 * T.D;

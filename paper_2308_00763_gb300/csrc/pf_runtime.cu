@@ -156,7 +156,10 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
     for (int i = 0; i < n; ++i) {
         const pf_config &c = cfgs[i];
         const int64_t N = c.num_particles;
-        const int nt = static_cast<int>((N + kTile - 1) / kTile);
+        const int tile = step_tile_size(e.prec, N);
+        const int64_t nt64 = (N + tile - 1) / tile;
+        if (nt64 > 0x7fffffff) return PF_ERR_ARG;
+        const int nt = static_cast<int>(nt64);
         if (tiles + nt > 0x7fffffff) return PF_ERR_ARG;
         const int cap = c.est_capacity ? c.est_capacity : 4096;
         Off &o = off[i];
@@ -182,6 +185,7 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
         T.r = c.disk_radius;
         T.D = disk_count(c.disk_radius);
         T.tile_begin = static_cast<int32_t>(tiles);
+        T.tile = tile;
         T.ntiles = nt;
         T.key_lo = static_cast<uint32_t>(c.seed & 0xffffffffu);
         T.key_hi = static_cast<uint32_t>(c.seed >> 32);

@@ -35,6 +35,7 @@
 #include <stddef.h>
 #include <math.h>
 
+#include <atomic>
 #include <type_traits>
 
 #include "pf_device.cuh"
@@ -402,19 +403,18 @@ struct __align__(16) StepSmem {
     lik_t table[kTableMax];   // likelihood of each pixel of the tile's window
     union {
         uint16_t pre[kRoiMax];      // integer form: row prefix sums of the staged region
-        lik_t term[kRoiMax];        // half form: per-pixel Eq. 4 terms of the staged region
-        uint16_t map[kMapMax];      // ancestor (tile element + 1) of each offspring
+        lik_t term[Tr::kHalf ? kRoiMax : 1];   // half form: per-pixel Eq. 4 terms of the staged region
     } u;
-    alignas(16) uint16_t toff[kOffMax];   // half form: template offsets in the staged region
+    alignas(16) uint16_t toff[Tr::kHalf ? kOffMax : 8];   // half form: template offsets in the staged region
+    alignas(16) uint16_t map[kMapMax];   // ancestor (tile element + 1) of each offspring
+    alignas(16) int warp_imax[kWarps];
     alignas(16) acc_t warp_sum[kWarps];
     alignas(16) acc_t warp_max[kWarps];
     alignas(16) float box[kWarps][4];
-    alignas(16) int warp_imax[kWarps];
     U128 red128[kWarps];
     alignas(16) int warp_incl[kWarps];
     Stats<acc_t> red[kWarps];
-    acc_t agg;
-    U128 excl_x, end_x;       // exact fixed-point prefix before / after the tile
+    U128 agg_x;               // the tile aggregate (fixed point)
     int jbeg, jend;
     double u0d;               // resampling offset u0 of the previous frame
     float u0f;
@@ -452,7 +452,7 @@ __device__ Stats<A> block_stats(Stats<A> v, StepSmem<P> &sm) {
 // Decoupled lookback over the tracker's earlier tiles, kThreads tiles per round (thread
 // i inspects tile base - i).  Sums the fixed-point aggregates back to the nearest tile
 // that has published its inclusive prefix.  Whole block, one barrier per round; the
-// result is valid in thread 0.
+// result is valid in every thread.
 template <int P>
 __device__ U128 lookback(const LookbackDesc *look, int lt, uint64_t tag, TrackerState *st, StepSmem<P> &sm) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -475,15 +475,16 @@ __device__ U128 lookback(const LookbackDesc *look, int lt, uint64_t tag, Tracker
         }
         if (lane == 0) { sm.red128[warp] = v; sm.warp_incl[warp] = incl != 0u; }
         const int found = __syncthreads_or(incl != 0u);
-        if (tid == 0) {
-            bool done = false;
+        {   // every warp: the warp sums up to the first warp with an inclusive predecessor
+            U128 x{0ull, 0ull};
+            int inc = 0;
+            if (lane < kWarps) { x = sm.red128[lane]; inc = sm.warp_incl[lane]; }
+            const uint32_t im = __ballot_sync(0xffffffffu, inc != 0);
+            const int fw = im ? __ffs(static_cast<int>(im)) - 1 : 32;
+            if (lane > fw) x = U128{0ull, 0ull};
 #pragma unroll
-            for (int w = 0; w < kWarps; ++w) {
-                const U128 x = sm.red128[w];
-                const int inc = sm.warp_incl[w];
-                if (!done) total = add128(total, x);
-                done = done || inc != 0;
-            }
+            for (int o = 1; o < 32; o <<= 1) x = add128(x, shfl_xor128(x, o));
+            total = add128(total, x);
         }
         if (found) break;
         __syncthreads();           // red128 is rewritten by the next round
@@ -620,8 +621,8 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
 
     const int N = static_cast<int>(T.N);
     const int lt = g - T.tile_begin;
-    const int k0 = lt * kTile;
-    const int cnt = (N - k0) < kTile ? (N - k0) : kTile;
+    const int k0 = lt * T.tile;
+    const int cnt = (N - k0) < T.tile ? (N - k0) : T.tile;
     const int64_t t = sm.st.t;
     const uint64_t dtag = desc_tag(sm.st.epoch);    // this launch's lookback tag
     constexpr bool kF64 = sizeof(acc_t) == 8;    // REF64; the other kernels use no FP64
@@ -645,7 +646,6 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
 
     // ------------------------------------------------------------ 1a. local scan of e
     acc_t loc[kItems];
-    U128 aggx{0ull, 0ull};
     // bounding box of the ancestors with non-negligible weight (absolute pixel units)
     float bx0 = FLT_MAX, bx1 = -FLT_MAX, by0 = FLT_MAX, by1 = -FLT_MAX;
     const int eb = tid * kItems;  // blocked arrangement: thread tid owns elements eb .. eb+kItems-1
@@ -674,6 +674,10 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
         // the offspring loop reads its ancestors' positions from shared memory
         store_items(sm.ax + eb, xv);
         store_items(sm.ay + eb, yv);
+        // clear the ancestor map (its heads are written after the strata are counted)
+#pragma unroll
+        for (int i = 0; i < kMapMax / 8 / kThreads; ++i)
+            reinterpret_cast<uint4 *>(sm.map)[tid + i * kThreads] = make_uint4(0u, 0u, 0u, 0u);
         const float sx = Tr::kHalf ? static_cast<float>(axi_anc) : 0.0f;
         const float sy = Tr::kHalf ? static_cast<float>(ayi_anc) : 0.0f;
         acc_t run = static_cast<acc_t>(0);
@@ -732,18 +736,21 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
         if (lane == 0) mex = wmax; else mex = fmax(mex, wmax);
 #pragma unroll
         for (int m = 0; m < kItems; ++m) loc[m] = fmax(loc[m], mex);
-        // the tile aggregate is the clamped prefix at its last particle
+        // The tile aggregate is the clamped prefix at its last particle; the thread that
+        // holds it publishes it (tile 0: as the inclusive prefix) and leaves it for thread
+        // 0, which reads it after the next barrier.
         {
             const int el = cnt - 1;
             if (el / kItems == tid) {
+                acc_t a = loc[0];
 #pragma unroll
-                for (int m = 0; m < kItems; ++m)
-                    if (m == el % kItems) sm.agg = loc[m];
+                for (int m = 1; m < kItems; ++m)
+                    if (m == el % kItems) a = loc[m];
+                const U128 ax = to_fixed(a);
+                desc_publish(&look[lt], lt == 0 ? 1 : 0, ax, dtag);
+                sm.agg_x = ax;
             }
         }
-        __syncthreads();
-        aggx = to_fixed(sm.agg);
-        if (tid == 0) desc_publish(&look[lt], lt == 0 ? 1 : 0, aggx, dtag);   // tile 0: inclusive
     } else {
         bx0 = bx1 = T.init_xf;
         by0 = by1 = T.init_yf;
@@ -873,7 +880,7 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
             cx += kThreads;               // next cell: kThreads further in row-major order
             while (cx >= ww) { cx -= ww; ++cy; }
         }
-        __syncthreads();
+        // (no barrier: the next one, before the offspring, orders the table's writes)
     }
 
     // ------------------------------------------------------------ 1d. lookback, CDF, strata
@@ -884,20 +891,15 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
         const acc_t u0 = kF64 ? static_cast<acc_t>(sm.u0d) : static_cast<acc_t>(sm.u0f);
         Strata<acc_t> str;
         str.init(N, u0, sizeof(acc_t) == 8 ? static_cast<acc_t>(T.inv_n) : static_cast<acc_t>(T.inv_n_f));
-        U128 exclx{0ull, 0ull};
-        if (lt > 0) exclx = lookback<P>(look, lt, dtag, st, sm);
-        if (tid == 0) {
-            const U128 endx = add128(exclx, aggx);
-            if (lt > 0) desc_publish(&look[lt], 1, endx, dtag);
-            sm.excl_x = exclx;
-            sm.end_x = endx;
-        }
-        __syncthreads();
+        // exact prefix before the tile (every thread) and after it (published as inclusive)
+        const U128 exclx = (lt > 0) ? lookback<P>(look, lt, dtag, st, sm) : U128{0ull, 0ull};
+        const U128 endx = add128(exclx, sm.agg_x);
+        if (tid == 0 && lt > 0) desc_publish(&look[lt], 1, endx, dtag);
         // Prefix of the tile's elements: FP inside the tile, pinned to the exact fixed-point
         // values at both tile boundaries, so neighbouring tiles see the same boundary.
         acc_t excl, pend;
-        if constexpr (kF64) { excl = from_fixed(sm.excl_x); pend = from_fixed(sm.end_x); }
-        else { excl = from_fixed_f(sm.excl_x); pend = from_fixed_f(sm.end_x); }
+        if constexpr (kF64) { excl = from_fixed(exclx); pend = from_fixed(endx); }
+        else { excl = from_fixed_f(exclx); pend = from_fixed_f(endx); }
         if (tid == 0) sm.jbeg = (lt == 0) ? 0 : str.count_le(fmin(mul_rn(excl, invS), static_cast<acc_t>(1)));
         acc_t cprev = static_cast<acc_t>(-1);
         int jprev = 0;
@@ -920,35 +922,33 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
             Jr[m] = J;
         }
         store_items(sm.J + eb, Jr);
-        __syncthreads();
+        __syncthreads();          // J, jbeg and the likelihood table are complete
         jb = sm.jbeg;
         je = sm.J[cnt - 1];
     } else {
         jb = k0;
         je = k0 + cnt;
+        __syncthreads();          // the likelihood table is complete
     }
     const int nout = je - jb;
 
     // ------------------------------------------------------------ 1e. ancestor map
     // map[j - jb] = 1 + tile element that is the ancestor of offspring j: a head at the
-    // first offspring of every element with offspring, then a running max fills the gaps.
+    // first offspring of every element with offspring (the map was cleared at the start of
+    // the tile), then a block-wide running max fills the gaps.
     const bool use_map = (t > 0) && nout <= kMapMax;
     if (use_map) {
-        for (int i = tid * 8; i < nout; i += kThreads * 8)
-            *reinterpret_cast<uint4 *>(sm.u.map + i) = make_uint4(0u, 0u, 0u, 0u);
         int jpt = __shfl_up_sync(0xffffffffu, Jr[kItems - 1], 1);   // J of element eb - 1
         if (lane == 0) jpt = (tid == 0) ? jb : sm.J[eb - 1];
-        __syncthreads();
 #pragma unroll
         for (int m = 0; m < kItems; ++m) {
             const int jp = m ? Jr[m - 1] : jpt;
-            if (eb + m < cnt && Jr[m] > jp) sm.u.map[jp - jb] = static_cast<uint16_t>(eb + m + 1);
+            if (eb + m < cnt && Jr[m] > jp) sm.map[jp - jb] = static_cast<uint16_t>(eb + m + 1);
         }
         __syncthreads();
-        // thread tid fills entries [tid*ch, tid*ch + ch) (16-byte vectors); entries past
-        // nout are never read, and the max only carries forward, into entries past nout
+        // thread tid fills entries [tid*ch, tid*ch + ch), ch = 8 or 16 (16-byte vectors)
         const int nv = (nout > kThreads * 8) ? 2 : 1;
-        uint4 *mv = reinterpret_cast<uint4 *>(sm.u.map) + tid * nv;
+        uint4 *mv = reinterpret_cast<uint4 *>(sm.map) + tid * nv;
         uint4 c0 = mv[0], c1 = make_uint4(0u, 0u, 0u, 0u);
         if (nv == 2) c1 = mv[1];
         uint32_t m2 = __vmaxu2(__vmaxu2(__vmaxu2(c0.x, c0.y), __vmaxu2(c0.z, c0.w)),
@@ -968,14 +968,18 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
             const int v = sm.warp_imax[w];
             if (w < warp) run = max(run, v);
         }
-        uint32_t *wv = reinterpret_cast<uint32_t *>(mv);
-        for (int i = 0; i < 4 * nv; ++i) {
-            const uint32_t wd = wv[i];
-            const int r1 = max(run, static_cast<int>(wd & 0xffffu));
-            const int r2 = max(r1, static_cast<int>(wd >> 16));
-            wv[i] = static_cast<uint32_t>(r1) | (static_cast<uint32_t>(r2) << 16);
-            run = r2;
+        uint32_t w4[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            if (i < 4 * nv) {
+                const int r1 = max(run, static_cast<int>(w4[i] & 0xffffu));
+                const int r2 = max(r1, static_cast<int>(w4[i] >> 16));
+                w4[i] = static_cast<uint32_t>(r1) | (static_cast<uint32_t>(r2) << 16);
+                run = r2;
+            }
         }
+        mv[0] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+        if (nv == 2) mv[1] = make_uint4(w4[4], w4[5], w4[6], w4[7]);
         __syncthreads();
     }
 
@@ -1006,14 +1010,14 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
         const int j0 = 2 * q, j1 = j0 + 1;
         int e0 = 0, e1 = 0;
         if (kFast) {
-            if (v0) e0 = static_cast<int>(sm.u.map[j0 - jb]) - 1;
-            if (v1) e1 = static_cast<int>(sm.u.map[j1 - jb]) - 1;
+            if (v0) e0 = static_cast<int>(sm.map[j0 - jb]) - 1;
+            if (v1) e1 = static_cast<int>(sm.map[j1 - jb]) - 1;
             if (!v0) e0 = e1;
             if (!v1) e1 = e0;
         } else if (t > 0) {
             if (use_map) {
-                e0 = v0 ? static_cast<int>(sm.u.map[j0 - jb]) - 1 : 0;
-                e1 = v1 ? static_cast<int>(sm.u.map[j1 - jb]) - 1 : 0;
+                e0 = v0 ? static_cast<int>(sm.map[j0 - jb]) - 1 : 0;
+                e1 = v1 ? static_cast<int>(sm.map[j1 - jb]) - 1 : 0;
             } else {
                 if (v0) e0 = upper_index(sm.J, cnt, j0);
                 if (v1) e1 = (v0 && sm.J[e0] > j1) ? e0 : upper_index(sm.J, cnt, j1);
@@ -1198,6 +1202,9 @@ __global__ void philox_kernel(const uint4 *ctrs, int64_t n, uint32_t k0, uint32_
 
 template <int P>
 int configure_and_grid(int total_tiles) {
+    // MinBlocks CTAs must fit in an SM's 228 KB of shared memory (1 KB reserved per CTA)
+    static_assert((sizeof(StepSmem<P>) + 1024) * MinBlocks<P>::value <= 228 * 1024,
+                  "shared memory of the step kernel exceeds its CTAs per SM");
     const int bytes = static_cast<int>(sizeof(StepSmem<P>));
     if (cudaFuncSetAttribute(step_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess)
         return -1;
@@ -1211,6 +1218,40 @@ int configure_and_grid(int total_tiles) {
 }
 
 }  // namespace
+
+namespace {
+// resident CTAs of the step kernel on the current device (cached per device and precision)
+int slots_of(int precision) {
+    static std::atomic<int> cache[64][4];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return -1; }
+    if (precision < 0 || precision > 3) return -1;
+    if (dev >= 0 && dev < 64) {
+        const int c = cache[dev][precision].load(std::memory_order_relaxed);
+        if (c > 0) return c;
+    }
+    int g = -1;
+    switch (precision) {
+        case 0: g = configure_and_grid<0>(0x7fffffff); break;
+        case 1: g = configure_and_grid<1>(0x7fffffff); break;
+        case 2: g = configure_and_grid<2>(0x7fffffff); break;
+        case 3: g = configure_and_grid<3>(0x7fffffff); break;
+    }
+    if (g > 0 && dev >= 0 && dev < 64) cache[dev][precision].store(g, std::memory_order_relaxed);
+    return g;
+}
+}  // namespace
+
+int step_tile_size(int precision, int64_t n) {
+    const int64_t slots = slots_of(precision);
+    if (slots < 1 || n < 1) return kTile;
+    const int64_t waves = (n + slots * kTile - 1) / (slots * kTile);
+    int64_t tile = (n + slots * waves - 1) / (slots * waves);
+    tile = (tile + 7) & ~int64_t(7);
+    if (tile < kMinTile) tile = kMinTile;
+    if (tile > kTile) tile = kTile;
+    return static_cast<int>(tile);
+}
 
 int step_grid_size(int precision, int total_tiles) {
     switch (precision) {
