@@ -17,7 +17,6 @@ namespace pfk {
 constexpr int kThreads = 512;             // threads per CTA of the step kernel
 constexpr int kItems = 8;                 // CDF elements per thread
 constexpr int kTile = kThreads * kItems;  // largest tile (particles of the resampled frame)
-constexpr int kMinTile = 1024;            // smallest tile chosen for a large tracker
 constexpr int kMaxRadius = 64;
 
 // Device status bits (sticky, per tracker).
@@ -115,11 +114,12 @@ struct StepLaunch {
 // Host entry points into the kernel translation unit.
 int launch_step(int precision, const StepLaunch &L, int grid, void *stream);
 int step_grid_size(int precision, int total_tiles);
-// Particles per tile for a tracker of n particles: the smallest multiple of 8 that
-// splits n into a whole number of waves of the device's resident CTAs (SMs x CTAs per
-// SM), between kMinTile and kTile.  Every tile then carries the same load.  A function
-// of (precision, n, device model) only, so a tracker tiles the same alone, in a batch
-// and through the allocation-free entry point.
+// Particles per tile for a tracker of n particles.  A tracker of at least half a device
+// of full tiles (SMs x CTAs per SM x kTile / 2 particles) takes the smallest multiple of
+// 8 that splits it into a whole number of waves of the device's resident CTAs, so every
+// tile carries the same load (between kTile / 2 and kTile); a smaller tracker takes
+// kTile.  A function of (precision, n, device model) only, so a tracker tiles the same
+// alone, in a batch and through the allocation-free entry point.
 int step_tile_size(int precision, int64_t n);
 int launch_debug_philox(const uint32_t *d_ctrs, int64_t n, uint64_t seed, uint32_t *d_out,
                         void *stream);

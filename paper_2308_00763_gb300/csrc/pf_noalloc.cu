@@ -24,9 +24,9 @@ using namespace pfk;
 
 namespace {
 
-constexpr size_t kScratchBytes = 384 * 1024;
+constexpr size_t kScratchBytes = 256 * 1024;
 constexpr int64_t kMaxParticles = int64_t(1) << 22;
-constexpr int kMaxTiles = static_cast<int>(kMaxParticles / kMinTile);   // tiles hold >= kMinTile
+constexpr int kMaxTiles = static_cast<int>(kMaxParticles / (kTile / 2));   // a tile holds >= kTile / 2
 constexpr int kMaxDevices = 64;
 
 // The scratch array.  In host code its name is only a stand-in for the symbol; the

@@ -1244,11 +1244,12 @@ int slots_of(int precision) {
 
 int step_tile_size(int precision, int64_t n) {
     const int64_t slots = slots_of(precision);
-    if (slots < 1 || n < 1) return kTile;
+    // a tracker that cannot fill half the device with full tiles keeps full tiles (in a
+    // batch, other trackers fill the device)
+    if (slots < 1 || n < slots * (kTile / 2)) return kTile;
     const int64_t waves = (n + slots * kTile - 1) / (slots * kTile);
-    int64_t tile = (n + slots * waves - 1) / (slots * waves);
+    int64_t tile = (n + slots * waves - 1) / (slots * waves);   // >= kTile / 2 here
     tile = (tile + 7) & ~int64_t(7);
-    if (tile < kMinTile) tile = kMinTile;
     if (tile > kTile) tile = kTile;
     return static_cast<int>(tile);
 }
