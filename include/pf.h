@@ -224,6 +224,109 @@ pf_status pf_batch_reset(pf_batch *b);
 pf_status pf_batch_estimates(pf_batch *b, int64_t frame_index, double *xy);
 pf_status pf_batch_destroy(pf_batch *b);
 
+/* ---------------------------------------------------------------- serving
+ * Continuous batching over many camera streams whose frames arrive over time.  The
+ * paper tracks one video; this is the deployment form of the same per-frame step.
+ *
+ * A server owns one device arena of hbm_budget_bytes, carved per stream (particles of
+ * both ping-pong slots, lookback descriptors, tile partials, and a queue of
+ * queue_depth frames for streams fed from host memory).  pf_server_open admits a stream
+ * while its bytes fit the arena AND the admitted demand (sum of N * fps over open
+ * streams) stays within headroom * capacity particle-steps/s; otherwise it returns
+ * PF_ERR_ADMISSION and the caller may retry once streams close.  Every stream keeps its
+ * particles on the device from open to close.
+ *
+ * pf_server_tick launches, for each precision with queued frames, one step over every
+ * stream of that precision that has a frame queued (its oldest one), on that precision's
+ * own CUDA stream: streams join and leave the batch from one tick to the next, launches
+ * of FP16 and FP32 streams overlap on the device, and up to max_in_flight launches per
+ * precision are queued behind one another.  A stream's result does not depend on which
+ * other streams share its launches (every tracker's arithmetic reads only its own state).
+ * Completions are signalled by a host callback at the end of each launch;
+ * pf_server_poll harvests them: estimates, and per frame the latency from its arrival
+ * time to the callback (arrival times are on pf_server_now's clock).
+ *
+ * Threading: one host thread drives a server.  Errors: PF_ERR_ARG, PF_ERR_OOM,
+ * PF_ERR_CUDA, PF_ERR_ADMISSION (stream refused, or the stream's frame queue is full),
+ * PF_ERR_STATE (closed stream or failed server), PF_ERR_TIMEOUT (a step gave up; the
+ * server is failed afterwards). */
+typedef struct pf_server pf_server;
+
+typedef struct {
+    int64_t hbm_budget_bytes;   /* device memory for all streams (> 0) */
+    double  capacity;           /* particle-steps/s the device serves; 0 = no compute budget */
+    double  headroom;           /* admitted demand <= headroom * capacity (0 = 1.0) */
+    int32_t max_streams;        /* open streams at once (>= 1) */
+    int32_t queue_depth;        /* frames per stream queued or in flight (>= 1) */
+    int32_t max_in_flight;      /* launches per precision in flight (1..8; 0 = 2) */
+    int32_t reserved;           /* 0 */
+} pf_server_config;
+
+typedef struct {
+    int64_t streams_open, streams_admitted, streams_rejected;
+    int64_t frames_submitted, frames_rejected, frames_done;
+    int64_t launches;
+    double  particle_steps;     /* sum of N over completed frames */
+    double  latency_p50_ms, latency_p99_ms, latency_max_ms;   /* arrival -> estimate available */
+    double  first_launch_s, last_done_s;   /* pf_server_now times of the first launch / last completion */
+    int64_t hbm_in_use, hbm_peak;
+    double  demand;             /* admitted sum of N * fps */
+} pf_server_stats;
+
+/* seconds on a monotonic clock (the clock of arrival times and latencies) */
+double pf_server_now(void);
+pf_status pf_server_create(const pf_server_config *cfg, pf_server **out);
+/* Admit a stream (cfg->est_capacity = results kept on the host, 0 = 64; debug flags are
+ * not allowed).  host_frames: 1 if its frames will come from host memory (reserves the
+ * frame queue in the arena), 0 for device frames.  *stream_id >= 0 on success. */
+pf_status pf_server_open(pf_server *s, const pf_config *cfg, double fps, int32_t host_frames,
+                         int32_t *stream_id);
+/* Queue the stream's next frame (frame index = submission order).  Device frames
+ * (frame_on_device = 1) are read in place and must stay valid until the frame completes;
+ * host frames are copied into the stream's queue (asynchronously; the caller's buffer
+ * may be reused once this returns if it is pageable, after the frame completes if it is
+ * pinned).  arrival_time_s < 0 means now. */
+pf_status pf_server_submit(pf_server *s, int32_t stream_id, const uint8_t *frame, int64_t pitch_bytes,
+                           int32_t frame_on_device, double arrival_time_s);
+/* Launch every precision's ready streams; *frames_launched (may be NULL) counts them. */
+pf_status pf_server_tick(pf_server *s, int32_t *frames_launched);
+/* Harvest completed launches; *frames_completed (may be NULL) counts their frames. */
+pf_status pf_server_poll(pf_server *s, int32_t *frames_completed);
+/* Launch and complete everything queued (blocking). */
+pf_status pf_server_drain(pf_server *s);
+/* Estimate of frame `frame_index` of a stream (the last est_capacity completed frames are
+ * kept); PF_ERR_STATE if it has not completed or was dropped from the ring. */
+pf_status pf_server_result(pf_server *s, int32_t stream_id, int64_t frame_index, double *x, double *y);
+/* Frames of the stream completed so far. */
+int64_t pf_server_frames_done(const pf_server *s, int32_t stream_id);
+/* Close a stream: its in-flight frames complete first, queued ones are dropped; its
+ * memory and compute budget return to the server. */
+pf_status pf_server_close(pf_server *s, int32_t stream_id);
+pf_status pf_server_get_stats(pf_server *s, pf_server_stats *out);
+pf_status pf_server_destroy(pf_server *s);
+/* Bytes a stream of this configuration takes from the arena (no device needed). */
+pf_status pf_server_stream_bytes(const pf_config *cfg, int32_t host_frames, int32_t queue_depth,
+                                 int64_t *bytes);
+
+/* Trace replay: the server's request loop.  Events in time order: kind 0 opens trace
+ * stream `stream` (cfg, fps; its frames are device frames), kind 1 submits a device frame
+ * to it, kind 2 closes it.  A stream refused at open drops its frames (counted as
+ * rejected); a full queue drops the frame.  realtime = 1 processes every event at its
+ * time (seconds from the start of the replay) while ticking and polling continuously;
+ * realtime = 0 takes events as fast as the loop runs.  Returns after every event is
+ * processed and every launched frame has completed; streams left open stay open. */
+typedef struct {
+    double time_s;
+    int32_t kind;               /* 0 open, 1 frame, 2 close */
+    int32_t stream;             /* trace stream index, 0 <= stream < n_streams */
+    const uint8_t *frame;       /* kind 1 */
+    int64_t pitch_bytes;        /* kind 1 */
+    const pf_config *cfg;       /* kind 0 */
+    double fps;                 /* kind 0 */
+} pf_trace_event;
+pf_status pf_server_replay(pf_server *s, const pf_trace_event *events, int64_t n_events,
+                           int32_t n_streams, int32_t realtime);
+
 #ifdef __cplusplus
 }
 #endif

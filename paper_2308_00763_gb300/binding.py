@@ -24,6 +24,10 @@ __all__ = [
     "pf_debug_philox", "pf_debug_wait_timeout", "pf_batch_create", "pf_batch_step", "pf_batch_estimates",
     "pf_batch_set_videos", "pf_batch_run", "pf_batch_reset", "pf_step_frame_noalloc",
     "pf_batch_destroy", "Filter", "Batch", "PRECISIONS", "EXPORTED",
+    "PfServerConfig", "PfServerStats", "PfTraceEvent", "Server", "pf_server_now", "pf_server_create",
+    "pf_server_open", "pf_server_submit", "pf_server_tick", "pf_server_poll", "pf_server_drain",
+    "pf_server_result", "pf_server_frames_done", "pf_server_close", "pf_server_get_stats",
+    "pf_server_destroy", "pf_server_stream_bytes", "pf_server_replay",
 ]
 
 PF_OK, PF_ERR_ARG, PF_ERR_OOM, PF_ERR_CUDA, PF_ERR_TIMEOUT, PF_ERR_STATE, PF_ERR_ADMISSION = range(7)
@@ -56,6 +60,36 @@ class PfStateHeader(ctypes.Structure):
         ("anchor_x", ctypes.c_double), ("anchor_y", ctypes.c_double),
         ("next_anchor_x", ctypes.c_double), ("next_anchor_y", ctypes.c_double),
         ("est_x", ctypes.c_double), ("est_y", ctypes.c_double),
+    ]
+
+
+class PfServerConfig(ctypes.Structure):
+    _fields_ = [
+        ("hbm_budget_bytes", ctypes.c_int64), ("capacity", ctypes.c_double), ("headroom", ctypes.c_double),
+        ("max_streams", ctypes.c_int32), ("queue_depth", ctypes.c_int32),
+        ("max_in_flight", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    ]
+
+
+class PfServerStats(ctypes.Structure):
+    _fields_ = [
+        ("streams_open", ctypes.c_int64), ("streams_admitted", ctypes.c_int64), ("streams_rejected", ctypes.c_int64),
+        ("frames_submitted", ctypes.c_int64), ("frames_rejected", ctypes.c_int64), ("frames_done", ctypes.c_int64),
+        ("launches", ctypes.c_int64), ("particle_steps", ctypes.c_double),
+        ("latency_p50_ms", ctypes.c_double), ("latency_p99_ms", ctypes.c_double), ("latency_max_ms", ctypes.c_double),
+        ("first_launch_s", ctypes.c_double), ("last_done_s", ctypes.c_double),
+        ("hbm_in_use", ctypes.c_int64), ("hbm_peak", ctypes.c_int64), ("demand", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class PfTraceEvent(ctypes.Structure):
+    _fields_ = [
+        ("time_s", ctypes.c_double), ("kind", ctypes.c_int32), ("stream", ctypes.c_int32),
+        ("frame", ctypes.c_void_p), ("pitch_bytes", ctypes.c_int64),
+        ("cfg", ctypes.POINTER(PfConfig)), ("fps", ctypes.c_double),
     ]
 
 
@@ -92,6 +126,21 @@ _SIG = {
     "pf_step_frame_noalloc": (ctypes.c_int, [ctypes.POINTER(PfConfig), _P, _P, _P, _P, _P, _I64,
                                              _P, _P, _P, _P, _P]),
     "pf_batch_destroy": (ctypes.c_int, [_P]),
+    "pf_server_now": (ctypes.c_double, []),
+    "pf_server_create": (ctypes.c_int, [ctypes.POINTER(PfServerConfig), ctypes.POINTER(_P)]),
+    "pf_server_open": (ctypes.c_int, [_P, ctypes.POINTER(PfConfig), ctypes.c_double, _I32, ctypes.POINTER(_I32)]),
+    "pf_server_submit": (ctypes.c_int, [_P, _I32, _P, _I64, _I32, ctypes.c_double]),
+    "pf_server_tick": (ctypes.c_int, [_P, ctypes.POINTER(_I32)]),
+    "pf_server_poll": (ctypes.c_int, [_P, ctypes.POINTER(_I32)]),
+    "pf_server_drain": (ctypes.c_int, [_P]),
+    "pf_server_result": (ctypes.c_int, [_P, _I32, _I64, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_double)]),
+    "pf_server_frames_done": (_I64, [_P, _I32]),
+    "pf_server_close": (ctypes.c_int, [_P, _I32]),
+    "pf_server_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(PfServerStats)]),
+    "pf_server_destroy": (ctypes.c_int, [_P]),
+    "pf_server_stream_bytes": (ctypes.c_int, [ctypes.POINTER(PfConfig), _I32, _I32, ctypes.POINTER(_I64)]),
+    "pf_server_replay": (ctypes.c_int, [_P, ctypes.POINTER(PfTraceEvent), _I64, _I32, _I32]),
 }
 EXPORTED = tuple(_SIG)
 
@@ -268,6 +317,80 @@ def pf_batch_destroy(h):
 
 
 # ------------------------------------------------------------------ convenience wrappers
+def pf_server_now() -> float:
+    return float(lib().pf_server_now())
+
+
+def pf_server_create(cfg: PfServerConfig):
+    h = _P()
+    _check(lib().pf_server_create(ctypes.byref(cfg), ctypes.byref(h)), "pf_server_create")
+    return h
+
+
+def pf_server_open(h, cfg: PfConfig, fps: float, host_frames: int):
+    """(status, stream id)."""
+    sid = _I32(-1)
+    rc = lib().pf_server_open(h, ctypes.byref(cfg), float(fps), int(host_frames), ctypes.byref(sid))
+    return rc, sid.value
+
+
+def pf_server_submit(h, sid: int, frame_ptr: int, pitch: int, on_device: int, arrival: float = -1.0):
+    return lib().pf_server_submit(h, sid, _P(frame_ptr), pitch, on_device, float(arrival))
+
+
+def pf_server_tick(h) -> int:
+    n = _I32(0)
+    _check(lib().pf_server_tick(h, ctypes.byref(n)), "pf_server_tick")
+    return n.value
+
+
+def pf_server_poll(h) -> int:
+    n = _I32(0)
+    _check(lib().pf_server_poll(h, ctypes.byref(n)), "pf_server_poll")
+    return n.value
+
+
+def pf_server_drain(h):
+    _check(lib().pf_server_drain(h), "pf_server_drain")
+
+
+def pf_server_result(h, sid: int, index: int):
+    x = ctypes.c_double()
+    y = ctypes.c_double()
+    rc = lib().pf_server_result(h, sid, index, ctypes.byref(x), ctypes.byref(y))
+    return rc, (x.value, y.value)
+
+
+def pf_server_frames_done(h, sid: int) -> int:
+    return int(lib().pf_server_frames_done(h, sid))
+
+
+def pf_server_close(h, sid: int):
+    _check(lib().pf_server_close(h, sid), "pf_server_close")
+
+
+def pf_server_get_stats(h) -> dict:
+    st = PfServerStats()
+    _check(lib().pf_server_get_stats(h, ctypes.byref(st)), "pf_server_get_stats")
+    return st.as_dict()
+
+
+def pf_server_destroy(h):
+    return lib().pf_server_destroy(h)
+
+
+def pf_server_stream_bytes(cfg: PfConfig, host_frames: int, queue_depth: int) -> int:
+    b = _I64(0)
+    _check(lib().pf_server_stream_bytes(ctypes.byref(cfg), host_frames, queue_depth, ctypes.byref(b)),
+           "pf_server_stream_bytes")
+    return b.value
+
+
+def pf_server_replay(h, events, n_streams: int, realtime: bool):
+    arr = (PfTraceEvent * len(events))(*events)
+    _check(lib().pf_server_replay(h, arr, len(events), n_streams, 1 if realtime else 0), "pf_server_replay")
+
+
 def make_config(width, height, num_particles, disk_radius, precision="f32", *, init=(0.0, 0.0),
                 sigma=(1.0, 1.0), drift=(0.0, 0.0), seed=1, tracker_id=0, bg=100.0, fg=228.0,
                 flags=0, est_capacity=0) -> PfConfig:
@@ -429,6 +552,80 @@ class Batch:
     def close(self):
         if getattr(self, "h", None):
             pf_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous batching over camera streams (pf_server_*)."""
+
+    def __init__(self, hbm_budget_bytes, *, capacity=0.0, headroom=1.0, max_streams=64, queue_depth=4,
+                 max_in_flight=2):
+        self.cfg = PfServerConfig(hbm_budget_bytes=int(hbm_budget_bytes), capacity=float(capacity),
+                                  headroom=float(headroom), max_streams=int(max_streams),
+                                  queue_depth=int(queue_depth), max_in_flight=int(max_in_flight), reserved=0)
+        self.h = pf_server_create(self.cfg)
+        self._keep = {}
+
+    def open(self, cfg: PfConfig, fps=30.0, host_frames=False):
+        """Stream id, or None when admission refuses the stream."""
+        rc, sid = pf_server_open(self.h, cfg, fps, 1 if host_frames else 0)
+        if rc == PF_ERR_ADMISSION:
+            return None
+        _check(rc, "pf_server_open")
+        return sid
+
+    def submit(self, sid, frame, arrival=-1.0):
+        """Queue a frame (CUDA tensor read in place, or host array copied); False when the
+        stream's queue is full.  A CUDA frame is kept alive here until it completes."""
+        ptr, pitch, on_dev, keep = _frame_ptr(frame)
+        rc = pf_server_submit(self.h, sid, ptr, pitch, on_dev, arrival)
+        if rc == PF_ERR_ADMISSION:
+            return False
+        _check(rc, "pf_server_submit")
+        q = self._keep.setdefault(sid, [0, []])     # [frames submitted, [(index, tensor)]]
+        if on_dev:
+            q[1].append((q[0], keep))
+        q[0] += 1
+        done = pf_server_frames_done(self.h, sid)
+        q[1] = [(i, t) for i, t in q[1] if i >= done]
+        return True
+
+    def tick(self):
+        return pf_server_tick(self.h)
+
+    def poll(self):
+        return pf_server_poll(self.h)
+
+    def drain(self):
+        pf_server_drain(self.h)
+
+    def result(self, sid, index):
+        rc, xy = pf_server_result(self.h, sid, index)
+        _check(rc, "pf_server_result")
+        return xy
+
+    def frames_done(self, sid):
+        return pf_server_frames_done(self.h, sid)
+
+    def close_stream(self, sid):
+        pf_server_close(self.h, sid)
+        self._keep.pop(sid, None)
+
+    def stats(self):
+        return pf_server_get_stats(self.h)
+
+    def replay(self, events, n_streams, realtime=True):
+        pf_server_replay(self.h, events, n_streams, realtime)
+
+    def close(self):
+        if getattr(self, "h", None):
+            pf_server_destroy(self.h)
             self.h = None
 
     def __del__(self):

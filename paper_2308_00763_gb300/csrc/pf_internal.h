@@ -99,11 +99,17 @@ struct TrackerDev {
 };
 
 // Launch of one step over a batch of trackers of one precision.
+// The launch steps ntrk trackers; launch position p (0 <= p < ntrk) is the tracker in
+// slot slot_of[p] of the descriptor and state arrays (slot p if slot_of is null).
 struct StepLaunch {
-    const TrackerDev *trk;     // device array [ntrk]
-    TrackerState *states;      // device array [ntrk] (trk[i].state == states + i)
-    const FrameRef *frames;    // device array [ntrk]
-    const int32_t *tile_trk;   // device array [total_tiles]: tracker of each tile
+    const TrackerDev *trk;     // device array indexed by slot
+    TrackerState *states;      // device array indexed by slot (trk[s].state == states + s)
+    const FrameRef *frames;    // device array [ntrk], by launch position
+    const int32_t *tile_trk;   // device array [total_tiles]: launch position of each tile, or null
+    const int32_t *tile_prefix;  // device array [ntrk + 1]: first tile of each position (when
+                                 // tile_trk is null and ntrk > 1: positions found by bisection)
+    const int32_t *slot_of;    // device array [ntrk], or null
+    double *est_out;           // device array [2 * ntrk], or null: each position's new estimate
     uint32_t *ticket;          // device counter, 0 between launches
     int32_t ntrk;
     int32_t total_tiles;

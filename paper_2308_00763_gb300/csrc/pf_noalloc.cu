@@ -19,6 +19,7 @@
 
 #include "pf.h"
 #include "pf_internal.h"
+#include "pf_host.h"
 
 using namespace pfk;
 
@@ -59,16 +60,6 @@ static_assert(layout().end <= kScratchBytes, "scratch layout exceeds the array")
 std::mutex g_lock;
 unsigned char *g_scratch_dev[kMaxDevices] = {};
 int g_grid[kMaxDevices][4] = {};
-
-double round_half_up(double v) { return floor(v) + ((v - floor(v)) >= 0.5 ? 1.0 : 0.0); }
-
-int disk_count(int r) {
-    int n = 0;
-    for (int dy = -r; dy <= r; ++dy)
-        for (int dx = -r; dx <= r; ++dx)
-            if (dx * dx + dy * dy <= r * r) ++n;
-    return n;
-}
 
 // Device address of the scratch array on the current device (looked up once per device).
 pf_status scratch_for_current_device(int *dev_out, unsigned char **ptr_out) {
@@ -131,20 +122,8 @@ extern "C" pf_status pf_step_frame_noalloc(const pf_config *cfg, const pf_state_
     const int in = static_cast<int>((h.t + 1) & 1), out = static_cast<int>(h.t & 1);
     TrackerDev T;
     memset(&T, 0, sizeof T);
-    T.N = N; T.W = c.width; T.H = c.height; T.r = c.disk_radius; T.D = disk_count(c.disk_radius);
-    T.tile_begin = 0; T.ntiles = nt; T.tile = tile;
-    T.key_lo = static_cast<uint32_t>(c.seed & 0xffffffffu); T.key_hi = static_cast<uint32_t>(c.seed >> 32);
-    T.tracker_id = c.tracker_id; T.flags = c.flags; T.est_cap = 1;
-    T.c1 = c.fg_level - c.bg_level; T.c2 = c.bg_level + c.fg_level; T.den = 50.0 * T.D;
-    T.kappa = static_cast<float>(1.0 / sqrt(50.0 * T.D));
-    T.bg_f = static_cast<float>(c.bg_level); T.fg_f = static_cast<float>(c.fg_level);
-    T.init_x = c.init_x; T.init_y = c.init_y; T.sigma_x = c.sigma_x; T.sigma_y = c.sigma_y;
-    T.drift_x = c.drift_x; T.drift_y = c.drift_y;
-    T.inv_n = 1.0 / static_cast<double>(N); T.inv_n_f = 1.0f / static_cast<float>(N);
-    T.init_xf = static_cast<float>(c.init_x); T.init_yf = static_cast<float>(c.init_y);
-    T.drift_xf = static_cast<float>(c.drift_x); T.drift_yf = static_cast<float>(c.drift_y);
-    T.sigma_xf = static_cast<float>(c.sigma_x); T.sigma_yf = static_cast<float>(c.sigma_y);
-    T.c1f = static_cast<float>(T.c1); T.c2Df = static_cast<float>(T.c2 * T.D); T.denf = static_cast<float>(T.den);
+    fill_tracker_constants(c, T);
+    T.tile_begin = 0; T.ntiles = nt; T.tile = tile; T.est_cap = 1;
     T.px[in] = const_cast<void *>(x_in); T.py[in] = const_cast<void *>(y_in); T.pl[in] = const_cast<void *>(l_in);
     T.px[out] = x_out; T.py[out] = y_out; T.pl[out] = l_out;
     T.look = reinterpret_cast<LookbackDesc *>(scr + LY.look);
@@ -170,9 +149,7 @@ extern "C" pf_status pf_step_frame_noalloc(const pf_config *cfg, const pf_state_
         st.est_x = h.est_x; st.est_y = h.est_y;
     }
     st.invS = c.precision == PF_REF64 ? 1.0 / st.S : static_cast<double>(1.0f / static_cast<float>(st.S));
-    st.M_f = static_cast<float>(st.M); st.invS_f = static_cast<float>(st.invS);
-    st.axi = static_cast<int32_t>(st.ax); st.ayi = static_cast<int32_t>(st.ay);
-    st.nxi = static_cast<int32_t>(st.nx); st.nyi = static_cast<int32_t>(st.ny);
+    state_copies(st);
     FrameRef fr;
     memset(&fr, 0, sizeof fr);
     fr.base = frame; fr.pitch = pitch_bytes; fr.stride = 0; fr.active = 1;
@@ -200,6 +177,9 @@ extern "C" pf_status pf_step_frame_noalloc(const pf_config *cfg, const pf_state_
     L.states = T.state;
     L.frames = reinterpret_cast<const FrameRef *>(scr + LY.frame);
     L.tile_trk = nullptr;   // one tracker: every tile belongs to it
+    L.tile_prefix = nullptr;
+    L.slot_of = nullptr;
+    L.est_out = nullptr;
     L.ticket = reinterpret_cast<uint32_t *>(scr + LY.ticket);
     L.ntrk = 1;
     L.total_tiles = nt;

@@ -11,39 +11,11 @@
 
 #include "pf.h"
 #include "pf_internal.h"
+#include "pf_host.h"
 
 using namespace pfk;
 
 namespace {
-
-size_t pos_bytes(int prec) { return prec == PF_REF64 ? 8 : prec == PF_F32 ? 4 : 2; }
-
-double round_half_up(double v) { return floor(v) + ((v - floor(v)) >= 0.5 ? 1.0 : 0.0); }
-
-int disk_count(int r) {
-    int n = 0;
-    for (int dy = -r; dy <= r; ++dy)
-        for (int dx = -r; dx <= r; ++dx)
-            if (dx * dx + dy * dy <= r * r) ++n;
-    return n;
-}
-
-pf_status check_config(const pf_config *c) {
-    if (!c) return PF_ERR_ARG;
-    if (c->width < 1 || c->width > 65535 || c->height < 1 || c->height > 65535) return PF_ERR_ARG;
-    if (c->num_particles < 1 || c->num_particles > 2147483647ll) return PF_ERR_ARG;
-    if (c->disk_radius < 0 || c->disk_radius > kMaxRadius) return PF_ERR_ARG;
-    if (c->precision < PF_REF64 || c->precision > PF_BF16) return PF_ERR_ARG;
-    if (!(c->sigma_x >= 0) || !(c->sigma_y >= 0)) return PF_ERR_ARG;
-    if (!isfinite(c->init_x) || !isfinite(c->init_y) || !isfinite(c->drift_x) || !isfinite(c->drift_y))
-        return PF_ERR_ARG;
-    if (!isfinite(c->bg_level) || !isfinite(c->fg_level) || !isfinite(c->sigma_x) || !isfinite(c->sigma_y))
-        return PF_ERR_ARG;
-    if (fabs(c->init_x) > 1.0e6 || fabs(c->init_y) > 1.0e6) return PF_ERR_ARG;
-    if (c->est_capacity < 0 || c->reserved != 0) return PF_ERR_ARG;
-    if (c->flags & ~(PF_FLAG_DEBUG_ARRAYS | PF_FLAG_ACCUM32)) return PF_ERR_ARG;
-    return PF_OK;
-}
 
 // One allocation carved into aligned pieces.
 struct Arena {
@@ -55,16 +27,6 @@ struct Arena {
         return off;
     }
 };
-
-// Fill the FP32 / integer copies of the state scalars from the FP64 ones.
-void state_copies(TrackerState &s) {
-    s.M_f = static_cast<float>(s.M);
-    s.invS_f = static_cast<float>(s.invS);
-    s.axi = static_cast<int32_t>(s.ax);
-    s.ayi = static_cast<int32_t>(s.ay);
-    s.nxi = static_cast<int32_t>(s.nx);
-    s.nyi = static_cast<int32_t>(s.ny);
-}
 
 }  // namespace
 
@@ -179,36 +141,11 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
             o.dbgc = a.take(cdf_b * N);
         }
         TrackerDev &T = e.h_trk[i];
-        T.N = N;
-        T.W = c.width;
-        T.H = c.height;
-        T.r = c.disk_radius;
-        T.D = disk_count(c.disk_radius);
+        fill_tracker_constants(c, T);
         T.tile_begin = static_cast<int32_t>(tiles);
         T.tile = tile;
         T.ntiles = nt;
-        T.key_lo = static_cast<uint32_t>(c.seed & 0xffffffffu);
-        T.key_hi = static_cast<uint32_t>(c.seed >> 32);
-        T.tracker_id = c.tracker_id;
-        T.flags = c.flags;
         T.est_cap = cap;
-        T.c1 = c.fg_level - c.bg_level;
-        T.c2 = c.bg_level + c.fg_level;
-        T.den = 50.0 * T.D;
-        T.kappa = static_cast<float>(1.0 / sqrt(50.0 * T.D));
-        T.bg_f = static_cast<float>(c.bg_level);
-        T.fg_f = static_cast<float>(c.fg_level);
-        T.init_x = c.init_x; T.init_y = c.init_y;
-        T.sigma_x = c.sigma_x; T.sigma_y = c.sigma_y;
-        T.drift_x = c.drift_x; T.drift_y = c.drift_y;
-        T.inv_n = 1.0 / static_cast<double>(N);
-        T.inv_n_f = 1.0f / static_cast<float>(N);
-        T.init_xf = static_cast<float>(c.init_x); T.init_yf = static_cast<float>(c.init_y);
-        T.drift_xf = static_cast<float>(c.drift_x); T.drift_yf = static_cast<float>(c.drift_y);
-        T.sigma_xf = static_cast<float>(c.sigma_x); T.sigma_yf = static_cast<float>(c.sigma_y);
-        T.c1f = static_cast<float>(T.c1);
-        T.c2Df = static_cast<float>(T.c2 * T.D);
-        T.denf = static_cast<float>(T.den);
         tiles += nt;
     }
     e.total_tiles = static_cast<int>(tiles);
@@ -255,18 +192,7 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
             T.dbg_cdf = e.d_arena + o.dbgc;
         }
         for (int k = 0; k < T.ntiles; ++k) tile_trk[T.tile_begin + k] = i;
-        TrackerState &s = st[i];
-        memset(&s, 0, sizeof s);
-        s.t = 0;
-        s.epoch = 1;
-        s.M = 0.0;
-        s.S = 1.0;
-        s.invS = 1.0;
-        s.ax = s.nx = round_half_up(e.cfg[i].init_x);
-        s.ay = s.ny = round_half_up(e.cfg[i].init_y);
-        s.est_x = e.cfg[i].init_x;
-        s.est_y = e.cfg[i].init_y;
-        state_copies(s);
+        st[i] = initial_state(e.cfg[i]);
         e.h_frames[i].active = 1;
     }
     err = cudaMemcpyAsync(e.d_trk, e.h_trk.data(), sizeof(TrackerDev) * n, cudaMemcpyHostToDevice, e.stream);
@@ -294,6 +220,9 @@ static pf_status engine_launch(Engine &e, const uint8_t *override_frame, int64_t
     L.states = e.h_trk[0].state;
     L.frames = e.d_frames;
     L.tile_trk = e.d_tile_trk;
+    L.tile_prefix = nullptr;
+    L.slot_of = nullptr;
+    L.est_out = nullptr;
     L.ticket = e.d_ticket;
     L.ntrk = e.n;
     L.total_tiles = e.total_tiles;
@@ -330,6 +259,9 @@ static pf_status engine_run_resident(Engine &e, int32_t count) {
         L.states = e.h_trk[0].state;
         L.frames = e.d_frames;
         L.tile_trk = e.d_tile_trk;
+        L.tile_prefix = nullptr;
+        L.slot_of = nullptr;
+        L.est_out = nullptr;
         L.ticket = e.d_ticket;
         L.ntrk = e.n;
         L.total_tiles = e.total_tiles;

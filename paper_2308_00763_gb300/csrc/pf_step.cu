@@ -505,7 +505,7 @@ __device__ __forceinline__ int upper_index(const int32_t *J, int n, int j) {
 // Merge of the tracker's tile partials (one per thread, all loads in flight, then the
 // block merge: deterministic) and the new state, by the tile that completed the tracker.
 template <int P>
-__device__ void finalize_tracker(const TrackerDev &T, TrackerState *st, StepSmem<P> &sm) {
+__device__ void finalize_tracker(const TrackerDev &T, TrackerState *st, StepSmem<P> &sm, double *est_out) {
     using acc_t = typename Prec<P>::acc_t;
     constexpr bool kF64 = sizeof(acc_t) == 8;
     constexpr bool F = Prec<P>::kHalf;
@@ -570,6 +570,7 @@ __device__ void finalize_tracker(const TrackerDev &T, TrackerState *st, StepSmem
                                  : o.t % T.est_cap;
         *reinterpret_cast<double2 *>(T.est_ring + 2 * slot) = make_double2(ex, ey);
         *reinterpret_cast<double2 *>(T.stat_ring + 2 * slot) = make_double2(n.M, n.S);
+        if (est_out) *reinterpret_cast<double2 *>(est_out) = make_double2(ex, ey);
         // every field but the sticky status word (another tile may have raised it)
         st->t = n.t;
         st->epoch = n.epoch;
@@ -593,14 +594,28 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
     using acc_t = typename Tr::acc_t;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int ti = (Lp.ntrk == 1) ? 0 : __ldg(&Lp.tile_trk[g]);
-    TrackerState *const st = Lp.states + ti;
+    // launch position of the tile, its first tile and its slot
+    int ti = 0;
+    if (Lp.ntrk > 1) {
+        if (Lp.tile_trk) {
+            ti = __ldg(&Lp.tile_trk[g]);
+        } else {   // last position whose first tile is <= g
+            int lo = 0, hi = Lp.ntrk - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (__ldg(&Lp.tile_prefix[mid]) <= g) lo = mid; else hi = mid - 1;
+            }
+            ti = lo;
+        }
+    }
+    const int slot = Lp.slot_of ? __ldg(&Lp.slot_of[ti]) : ti;
+    TrackerState *const st = Lp.states + slot;
 
     // ---- the tracker's descriptor, state and frame reference, loaded in one round trip
     // and kept for the CTA's later tiles of the same tracker (none of them changes
     // before the tracker's last tile of this launch has finished)
     if (ti != sm.cached) {
-        const uint32_t *src_t = reinterpret_cast<const uint32_t *>(Lp.trk + ti);
+        const uint32_t *src_t = reinterpret_cast<const uint32_t *>(Lp.trk + slot);
         const uint32_t *src_s = reinterpret_cast<const uint32_t *>(st);
         const uint32_t *src_f = reinterpret_cast<const uint32_t *>(Lp.frames + ti);
         uint32_t *dt = reinterpret_cast<uint32_t *>(&sm.trk);
@@ -620,7 +635,7 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
     if (sm.st.status & kStatusTimeout) return;   // a failed step: results are invalid
 
     const int N = static_cast<int>(T.N);
-    const int lt = g - T.tile_begin;
+    const int lt = g - (Lp.tile_prefix ? __ldg(&Lp.tile_prefix[ti]) : T.tile_begin);
     const int k0 = lt * T.tile;
     const int cnt = (N - k0) < T.tile ? (N - k0) : T.tile;
     const int64_t t = sm.st.t;
@@ -1158,7 +1173,7 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
         sm.last = (prev == static_cast<uint32_t>(T.ntiles - 1)) ? 1u : 0u;
     }
     __syncthreads();
-    if (sm.last) finalize_tracker<P>(T, st, sm);
+    if (sm.last) finalize_tracker<P>(T, st, sm, Lp.est_out ? Lp.est_out + 2 * ti : nullptr);
 }
 
 // CTAs per SM the register allocation must allow (measured best per precision on GB300:

@@ -78,3 +78,19 @@ def test_invalid_configs_rejected_without_gpu(libpath):
         assert not h.value
     assert pf.lib().pf_create(None, None, None) == pf.PF_ERR_ARG
     assert pf.lib().pf_destroy(None) == pf.PF_OK
+
+
+def test_server_stream_bytes_without_gpu(libpath):
+    """The arena bytes a serving stream takes: both ping-pong slots of x, y, L at the
+    precision's width, plus the frame queue when it is fed from host memory."""
+    import paper_2308_00763_gb300 as pf
+    for prec, width in (("ref64", 8), ("f32", 4), ("f16", 2), ("bf16", 2)):
+        for N in (1000, 123457, 1 << 20):
+            c = pf.make_config(640, 480, N, 5, prec)
+            dev = pf.pf_server_stream_bytes(c, 0, 4)
+            host = pf.pf_server_stream_bytes(c, 1, 4)
+            assert dev >= 6 * N * width and dev < 6 * N * width + 64 * 1024 + N // 4
+            assert host - dev == ((640 + 15) // 16 * 16) * 480 * 4
+            assert pf.pf_server_stream_bytes(c, 0, 1) == dev
+    with pytest.raises(pf.PfError):
+        pf.pf_server_stream_bytes(pf.make_config(0, 480, 10, 5, "f16"), 0, 4)

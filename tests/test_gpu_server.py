@@ -1,0 +1,184 @@
+"""Serving (pf_server_*): continuous batching over camera streams.
+
+The checks: a stream's estimates are the same bits alone, in a mix of other streams
+(other sizes, particle counts and precisions, joining and leaving between its frames) and
+through a plain pf_filter; admission refuses streams beyond the memory or compute budget
+and admits them again once budget returns; host frames and device frames give the same
+track; a trace replay completes every admitted frame and reports its latencies.
+"""
+import ctypes
+import time
+
+import numpy as np
+import pytest
+
+from paper_2308_00763_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pf():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2308_00763_gb300 as m
+    m.lib(build_if_missing=True)
+    return m
+
+
+def _video(W, H, T, r, seed, v=(1.0, -2.0)):
+    import torch
+    vid = synth.make_video(W, H, T, r, noise=5.0, seed=seed, v=v)
+    return vid, torch.from_numpy(vid.frames).cuda()
+
+
+def _cfg(pf, vid, N, prec, seed, tid):
+    return pf.make_config(vid.W, vid.H, N, vid.radius, prec, init=tuple(vid.centres[0]), seed=seed,
+                          tracker_id=tid, est_capacity=64)
+
+
+def _put(s, sid, frame):
+    """Submit, ticking until the stream's queue has room (bounded)."""
+    for _ in range(10000):
+        if s.submit(sid, frame):
+            return
+        s.tick()
+        s.poll()
+        time.sleep(0.0002)
+    raise AssertionError("the stream's queue never drained")
+
+
+def _serve_alone(pf, cfg, frames):
+    s = pf.Server(1 << 30, max_streams=4, queue_depth=4)
+    sid = s.open(cfg, fps=30.0)
+    out = []
+    for t in range(frames.shape[0]):
+        assert s.submit(sid, frames[t])
+        s.drain()
+        out.append(s.result(sid, t))
+    s.close()
+    return np.array(out)
+
+
+@pytest.mark.parametrize("prec", ["ref64", "f32", "f16", "bf16"])
+def test_stream_alone_equals_stream_in_mix(pf, prec):
+    T = 8
+    vid, fr = _video(160, 120, T, 4, seed=61)
+    cfg = _cfg(pf, vid, 3 * 4096 + 5, prec, 7, 3)
+    alone = _serve_alone(pf, cfg, fr)
+
+    # the same stream among others that join, leave and run other precisions
+    others = [(_video(96, 96, T, 3, seed=62 + k, v=(0.5, 1.0)), n, p)
+              for k, (n, p) in enumerate([(1000, "f32"), (9000, "f16"), (20000, prec), (500, "ref64")])]
+    s = pf.Server(1 << 30, max_streams=16, queue_depth=4, max_in_flight=3)
+    sid = s.open(cfg, fps=30.0)
+    oid = [None] * len(others)
+    for t in range(T):
+        for k, ((ov, ofr), n, p) in enumerate(others):
+            if t == k and oid[k] is None:                    # joins at frame k
+                oid[k] = s.open(_cfg(pf, ov, n, p, 100 + k, 10 + k), fps=30.0)
+                oid[k] = (oid[k], 0)
+            if oid[k] is not None and t == k + 5:            # leaves five frames later
+                s.close_stream(oid[k][0])
+                oid[k] = None
+                continue
+            if oid[k] is not None:
+                _put(s, oid[k][0], ofr[oid[k][1]])
+                oid[k] = (oid[k][0], oid[k][1] + 1)
+        _put(s, sid, fr[t])
+        s.tick()                                             # launch without waiting
+        s.poll()
+    s.drain()
+    mixed = np.array([s.result(sid, t) for t in range(T)])
+    st = s.stats()
+    s.close()
+    assert np.array_equal(alone, mixed), prec
+    assert st["launches"] >= T and st["frames_done"] == st["frames_submitted"] - st["frames_rejected"]
+
+    # and through a plain single-tracker handle (same tiling, same arithmetic)
+    f = pf.Filter(vid.W, vid.H, cfg.num_particles, vid.radius, prec, init=tuple(vid.centres[0]), seed=7,
+                  tracker_id=3)
+    f.run(fr)
+    assert np.array_equal(f.estimates(0, T), alone), prec
+    f.close()
+
+
+def test_host_frames_equal_device_frames(pf):
+    T = 5
+    vid, fr = _video(128, 96, T, 5, seed=70)
+    cfg = _cfg(pf, vid, 5000, "f16", 3, 1)
+    s = pf.Server(1 << 28, max_streams=2, queue_depth=3)
+    a = s.open(cfg, fps=30.0, host_frames=True)
+    for t in range(T):
+        _put(s, a, vid.frames[t])              # numpy: copied into the stream's queue
+        s.tick()
+    s.drain()
+    host = np.array([s.result(a, t) for t in range(T)])
+    s.close()
+    assert np.array_equal(host, _serve_alone(pf, cfg, fr))
+
+
+def test_admission_by_memory_and_compute_budget(pf):
+    vid, fr = _video(128, 128, 2, 5, seed=71)
+    cfg = _cfg(pf, vid, 200000, "f32", 1, 0)
+    need = pf.pf_server_stream_bytes(cfg, 0, 2)
+    # memory: room for two such streams, not three
+    s = pf.Server(2 * need + 1024, max_streams=8, queue_depth=2)
+    a, b = s.open(cfg), s.open(cfg)
+    assert a is not None and b is not None
+    assert s.open(cfg) is None
+    s.close_stream(a)
+    c = s.open(cfg)
+    assert c is not None
+    st = s.stats()
+    assert st["streams_rejected"] == 1 and st["streams_open"] == 2 and st["hbm_in_use"] <= 2 * need + 1024
+    s.close()
+    # compute: capacity for 2.5 streams of N * fps
+    cap = 2.5 * cfg.num_particles * 30.0
+    s = pf.Server(1 << 30, capacity=cap, max_streams=8, queue_depth=2)
+    ids = [s.open(cfg, fps=30.0) for _ in range(3)]
+    assert ids[0] is not None and ids[1] is not None and ids[2] is None
+    assert s.open(cfg, fps=10.0) is not None          # a slower stream still fits
+    s.close()
+
+
+def test_queue_full_refuses_frames(pf):
+    vid, fr = _video(96, 96, 6, 3, seed=72)
+    s = pf.Server(1 << 28, max_streams=2, queue_depth=2)
+    a = s.open(_cfg(pf, vid, 2000, "f16", 1, 0))
+    assert s.submit(a, fr[0]) and s.submit(a, fr[1])
+    assert not s.submit(a, fr[2])               # two queued: the third is refused
+    s.drain()
+    assert s.submit(a, fr[2])
+    s.drain()
+    assert s.frames_done(a) == 3
+    s.close()
+
+
+def test_trace_replay_completes_admitted_frames(pf):
+    import torch
+    T = 6
+    vids = [_video(128, 128, T, 4, seed=80 + k) for k in range(3)]
+    cfgs = [_cfg(pf, v, n, p, 90 + k, k) for k, ((v, _), n, p) in
+            enumerate(zip(vids, [4000, 30000, 120000], ["f16", "f32", "f16"]))]
+    ev = []
+    for k, (cfg, (v, fr)) in enumerate(zip(cfgs, vids)):
+        t_open = 0.01 * k
+        ev.append(pf.PfTraceEvent(time_s=t_open, kind=0, stream=k, frame=None, pitch_bytes=0,
+                                  cfg=ctypes.pointer(cfg), fps=100.0))
+        for t in range(T):
+            ev.append(pf.PfTraceEvent(time_s=t_open + 0.01 * (t + 1), kind=1, stream=k, frame=fr[t].data_ptr(),
+                                      pitch_bytes=fr.stride(1), cfg=None, fps=0.0))
+        ev.append(pf.PfTraceEvent(time_s=t_open + 0.01 * (T + 6), kind=2, stream=k, frame=None, pitch_bytes=0,
+                                  cfg=None, fps=0.0))
+    ev.sort(key=lambda e: (e.time_s, e.kind != 0, e.kind == 2))
+    s = pf.Server(1 << 30, max_streams=8, queue_depth=4)
+    s.replay(ev, 3, realtime=True)
+    st = s.stats()
+    torch.cuda.synchronize()
+    assert st["streams_admitted"] == 3 and st["streams_open"] == 0
+    assert st["frames_done"] == 3 * T and st["frames_rejected"] == 0
+    assert 0 < st["latency_p50_ms"] <= st["latency_p99_ms"] <= st["latency_max_ms"]
+    assert st["particle_steps"] == T * sum(c.num_particles for c in cfgs)
+    s.close()
