@@ -50,6 +50,8 @@ def _args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--frames", type=int, default=T_)
     p.add_argument("--no-batch", action="store_true", help="skip the batched-trackers measurement")
+    p.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    p.add_argument("--serve-seconds", type=float, default=20.0, help="length of the served-streams run")
     return p.parse_args()
 
 
@@ -59,6 +61,27 @@ def _dist():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def _max_over_ranks(x, device=None):
+    """The largest x over the ranks of the default process group (x itself without one)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(units_per_rank, ms_local, device=None):
+    """Whole-job throughput of independent replicas (one per rank, no data-path
+    collective): the units all ranks processed over the slowest rank's time.  Returns
+    (units per second, slowest time in ms)."""
+    import torch.distributed as dist
+    ws = dist.get_world_size() if dist.is_available() and dist.is_initialized() else 1
+    ms = _max_over_ranks(ms_local, device)
+    return units_per_rank * ws / (ms * 1e-3), ms
 
 
 # ---------------------------------------------------------------------------- clocks
@@ -235,11 +258,7 @@ def run_ours(args):
         torch.cuda.synchronize(dev)
 
     def max_over_ranks(x):
-        if ws == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+        return _max_over_ranks(x, dev)
 
     clocks = ClockSampler(local)
     results = {}
@@ -268,8 +287,7 @@ def run_ours(args):
         if headline:
             clocks.stop()
         total_ms = sum(a.elapsed_time(b) for a, b in ev)
-        total_ms = max_over_ranks(total_ms)
-        value = N_ * T * args.steps * ws / (total_ms * 1e-3)
+        value, total_ms = replica_value(N_ * T * args.steps, total_ms, dev)
         tracks[prec] = f.estimates(0, T)
         # per-launch duration of the step kernel (events between launches on its stream)
         f.reset()
@@ -339,6 +357,10 @@ def run_ours(args):
     line["clocks"] = cs
     if not args.no_batch and ws == 1:
         line["systems"] = {"batched": _batched(dev, stream, max(3, min(args.steps, 10)), 2, hp)}
+    if not args.no_serve and ws == 1:
+        cap = min(results[p]["value"] for p in results if p in ("f16", "f32")) if any(
+            p in results for p in ("f16", "f32")) else head["value"]
+        line.setdefault("systems", {})["serving"] = _serving(dev, cap, args.serve_seconds)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = _cpu_baseline(v, tracks)
     if ws > 1:
@@ -405,6 +427,61 @@ def _batched(dev, stream, steps, warmup, precision):
             "ms_per_step": sum(ms) / steps, "us_per_frame": 1e3 * sum(ms) / steps / T, "steps": steps,
             "gpu_launches_per_step": T, "rmse_px_vs_truth_median": float(np.median(err)),
             "trackers_within_2px": int(sum(e < 2.0 for e in err))}
+
+
+def _serving(dev, capacity, seconds):
+    """Served multi-camera tracking: 1024 camera streams opening and closing over a run
+    of `seconds` (frames 256^2..1024^2, 4k..1M particles, FP16/FP32 half and half, Poisson
+    arrivals at 30 fps) replayed through the server's request loop, once in real time
+    (per-frame latency from arrival to estimate) and once as fast as the loop runs (the
+    served throughput when frames are always waiting).  Frames are device-resident
+    8-frame videos per (size, radius), cycled."""
+    import ctypes
+    import torch
+    import paper_2308_00763_gb300 as pf
+    from paper_2308_00763_gb300 import synth
+    specs = synth.serving_workload(1024, seconds)
+    vids = {}
+    for s in specs:
+        key = (s["W"], s["r"])
+        if key not in vids:
+            vids[key] = synth.make_video_device(s["W"], s["H"], 8, s["r"], v=(1.0, -2.0), seed=300 + len(vids),
+                                                device=dev)
+    cfgs = [pf.make_config(s["W"], s["H"], s["N"], s["r"], s["precision"], init=tuple(vids[(s["W"], s["r"])][1][0]),
+                           seed=s["seed"], tracker_id=i, est_capacity=16) for i, s in enumerate(specs)]
+    ev = []
+    for i, (s, c) in enumerate(zip(specs, cfgs)):
+        fr = vids[(s["W"], s["r"])][0]
+        ev.append((s["open"], 0, i, None, 0, ctypes.pointer(c), 30.0))
+        for k, t in enumerate(s["arrivals"]):
+            ev.append((t, 1, i, fr[k % 8].data_ptr(), fr.stride(1), None, 0.0))
+        ev.append((s["close"], 2, i, None, 0, None, 0.0))
+    ev.sort(key=lambda e: (e[0], e[1] != 0, e[1] == 2))
+    events = [pf.PfTraceEvent(time_s=e[0], kind=e[1], stream=e[2], frame=e[3], pitch_bytes=e[4], cfg=e[5], fps=e[6])
+              for e in ev]
+    torch.cuda.synchronize(dev)
+    out = {"workload": "1024 camera streams over %g s: open U(0, %g s), lifetime U(%g s, %g s) clipped, "
+                       "frames 256^2-1024^2, N log-uniform 4096-2^20, r 3-12, FP16/FP32 1:1, Poisson 30 fps"
+                       % (seconds, seconds * 5 / 6, seconds / 12, seconds),
+           "frames_offered": sum(len(s["arrivals"]) for s in specs),
+           "particle_steps_offered": float(sum(len(s["arrivals"]) * s["N"] for s in specs)),
+           "capacity_admitted": capacity, "headroom": 0.8}
+    for mode, realtime in (("realtime", True), ("saturated", False)):
+        srv = pf.Server(24 << 30, capacity=capacity, headroom=0.8, max_streams=1024, queue_depth=8, max_in_flight=2)
+        t0 = time.perf_counter()
+        srv.replay(events, len(specs), realtime=realtime)
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        busy = max(1e-9, st["last_done_s"] - st["first_launch_s"])
+        out[mode] = {"wall_s": wall, "value": st["particle_steps"] / busy, "unit": METRIC,
+                     "latency_p50_ms": st["latency_p50_ms"], "latency_p99_ms": st["latency_p99_ms"],
+                     "latency_max_ms": st["latency_max_ms"], "streams_admitted": st["streams_admitted"],
+                     "streams_rejected": st["streams_rejected"], "frames_done": st["frames_done"],
+                     "frames_rejected": st["frames_rejected"], "launches": st["launches"],
+                     "hbm_peak_bytes": st["hbm_peak"]}
+    del vids
+    return out
 
 
 def main():

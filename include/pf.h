@@ -310,8 +310,9 @@ pf_status pf_server_stream_bytes(const pf_config *cfg, int32_t host_frames, int3
 
 /* Trace replay: the server's request loop.  Events in time order: kind 0 opens trace
  * stream `stream` (cfg, fps; its frames are device frames), kind 1 submits a device frame
- * to it, kind 2 closes it.  A stream refused at open drops its frames (counted as
- * rejected); a full queue drops the frame.  realtime = 1 processes every event at its
+ * to it, kind 2 closes it (after its queued frames are served).  A stream refused at
+ * open drops its frames (counted as rejected); in real time a full queue drops the frame,
+ * otherwise the replay waits for room.  realtime = 1 processes every event at its
  * time (seconds from the start of the replay) while ticking and polling continuously;
  * realtime = 0 takes events as fast as the loop runs.  Returns after every event is
  * processed and every launched frame has completed; streams left open stay open. */

@@ -674,6 +674,18 @@ pf_status pf_server_replay(pf_server *S, const pf_trace_event *ev, int64_t n, in
                 if (ps != PF_OK && ps != PF_ERR_ADMISSION) return ps;
             } else if (e.kind == 2) {
                 if (id >= 0) {
+                    // the stream's frames that arrived before it closed are still served
+                    Stream &st = S->streams[id];
+                    while (!st.queued.empty()) {
+                        int32_t launched = 0;
+                        pf_status pt = pf_server_tick(S, &launched);
+                        if (pt != PF_OK) return pt;
+                        if (!st.queued.empty() &&
+                            cudaStreamSynchronize(S->eng[st.cfg.precision].stream) != cudaSuccess) {
+                            cudaGetLastError();
+                            return S->fail(PF_ERR_CUDA);
+                        }
+                    }
                     const pf_status ps = pf_server_close(S, id);
                     if (ps != PF_OK) return ps;
                 }

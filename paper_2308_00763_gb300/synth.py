@@ -19,7 +19,8 @@ from dataclasses import dataclass
 
 import numpy as np
 
-__all__ = ["Video", "reflect", "centre_track", "make_video"]
+__all__ = ["Video", "reflect", "centre_track", "make_video", "make_video_device", "batch_workload",
+           "serving_workload"]
 
 
 @dataclass
@@ -129,3 +130,27 @@ def batch_workload(n: int = 256, T: int = 60, seed: int = 4):
     return [dict(W=int(sizes[i]), H=int(sizes[i]), T=T, r=int(r[i]), N=int(N[i]),
                  v=(float(spd[i] * np.cos(ang[i])), float(spd[i] * np.sin(ang[i]))),
                  noise=5.0, seed=1000 + i) for i in range(n)]
+
+
+def serving_workload(n: int = 1024, seconds: float = 60.0, fps: float = 30.0, seed: int = 5):
+    """Streams of the served multi-camera workload: stream i opens at U(0, 5/6 s) and stays
+    open U(1/12 s, s) (clipped to the run of s seconds; s = 60 gives opens over the first
+    50 s and lifetimes of 5-60 s), frames of 256^2, 512^2 or 1024^2 pixels, N log-uniform in
+    [4096, 2^20], disk radius 3..12, FP16 or FP32 with probability 1/2 each, and frames
+    arriving as a Poisson process of rate `fps` (exponential gaps) while it is open."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        size = int(rng.choice([256, 512, 1024]))
+        N = int(np.floor(np.exp(rng.uniform(np.log(4096.0), np.log(float(1 << 20))))))
+        t_open = float(rng.uniform(0.0, seconds * 5.0 / 6.0))
+        t_close = min(seconds, t_open + float(rng.uniform(seconds / 12.0, seconds)))
+        arrivals = []
+        t = t_open + float(rng.exponential(1.0 / fps))
+        while t < t_close:
+            arrivals.append(t)
+            t += float(rng.exponential(1.0 / fps))
+        out.append(dict(W=size, H=size, N=N, r=int(rng.integers(3, 13)),
+                        precision="f16" if rng.random() < 0.5 else "f32",
+                        open=t_open, close=t_close, arrivals=arrivals, seed=2000 + i))
+    return out
