@@ -58,6 +58,7 @@ typedef enum {
 /* pf_config.flags */
 #define PF_FLAG_DEBUG_ARRAYS 0x1u  /* keep the last step's CDF and ancestor indices (pf_get_debug) */
 #define PF_FLAG_ACCUM32      0x2u  /* PF_F16: accumulate the likelihood in FP32 instead of half */
+#define PF_FLAG_TUNED        0x4u  /* take the launch shape pf_autotune cached for this shape bucket */
 
 typedef struct {
     int32_t width, height;     /* frame size in pixels, each in [1, 65535] */
@@ -223,6 +224,36 @@ pf_status pf_batch_reset(pf_batch *b);
  * have not stepped that frame get NaN.  Synchronises. */
 pf_status pf_batch_estimates(pf_batch *b, int64_t frame_index, double *xy);
 pf_status pf_batch_destroy(pf_batch *b);
+
+/* ---------------------------------------------------------------- autotuning
+ * Launch shapes of the step: the tile (particles of the previous frame per CTA task, a
+ * multiple of 8 from 1024 to 4096; 0 = the default rule), the likelihood window policy
+ * (0 adaptive, 1 always 3.5 sigma, 2 always the full draw range) and the CTAs per SM
+ * (0 = as many as fit, else at most this many).  They change no formula, but the tile
+ * partitions the FP scan and so the rounding of the CDF.
+ *
+ * pf_autotune times candidate shapes for one configuration on the caller's resident video
+ * (n_frames frames of rows pitch_bytes apart, frame_stride bytes apart, on the device)
+ * with `copies` trackers of that configuration in one batch (1 = the tracker alone; more
+ * = throughput with the device full, as in a batch), and caches the fastest for the
+ * configuration's shape bucket: (precision, floor(log2 N), disk radius, the larger sigma
+ * in quarter pixels).  Trackers created with PF_FLAG_TUNED take their bucket's cached
+ * shape (the default shape if none), so equal configurations tile alike alone and in a
+ * batch.  The cache lives in the process (pf_tuning_clear empties it).  Synchronises. */
+typedef struct {
+    int32_t tile;
+    int32_t window;
+    int32_t ctas_per_sm;
+    int32_t reserved;           /* 0 */
+} pf_tuning;
+
+pf_status pf_autotune(const pf_config *cfg, int32_t copies, const uint8_t *video, int64_t pitch_bytes,
+                      int64_t frame_stride, int32_t n_frames, pf_tuning *best, double *best_us_per_frame);
+/* The cached shape of cfg's bucket; PF_ERR_STATE if none. */
+pf_status pf_tuning_lookup(const pf_config *cfg, pf_tuning *out);
+/* Cache a shape for cfg's bucket (checked as pf_autotune's candidates are). */
+pf_status pf_tuning_store(const pf_config *cfg, const pf_tuning *t);
+pf_status pf_tuning_clear(void);
 
 /* ---------------------------------------------------------------- serving
  * Continuous batching over many camera streams whose frames arrive over time.  The

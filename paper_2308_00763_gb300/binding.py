@@ -18,7 +18,8 @@ from . import build as _build
 __all__ = [
     "PF_OK", "PF_ERR_ARG", "PF_ERR_OOM", "PF_ERR_CUDA", "PF_ERR_TIMEOUT", "PF_ERR_STATE",
     "PF_ERR_ADMISSION", "PF_REF64", "PF_F32", "PF_F16", "PF_BF16", "PF_FLAG_DEBUG_ARRAYS",
-    "PF_FLAG_ACCUM32", "PfConfig", "PfStateHeader", "PfError", "lib", "library_path",
+    "PF_FLAG_ACCUM32", "PF_FLAG_TUNED", "PfTuning", "pf_autotune", "pf_tuning_lookup", "pf_tuning_store",
+    "pf_tuning_clear", "autotune", "PfConfig", "PfStateHeader", "PfError", "lib", "library_path",
     "pf_status_string", "pf_create", "pf_step_frame", "pf_run_frames", "pf_estimate",
     "pf_estimates", "pf_frames_done", "pf_reset", "pf_destroy", "pf_get_state", "pf_set_state", "pf_get_debug",
     "pf_debug_philox", "pf_debug_wait_timeout", "pf_batch_create", "pf_batch_step", "pf_batch_estimates",
@@ -34,6 +35,7 @@ PF_OK, PF_ERR_ARG, PF_ERR_OOM, PF_ERR_CUDA, PF_ERR_TIMEOUT, PF_ERR_STATE, PF_ERR
 PF_REF64, PF_F32, PF_F16, PF_BF16 = range(4)
 PF_FLAG_DEBUG_ARRAYS = 0x1
 PF_FLAG_ACCUM32 = 0x2
+PF_FLAG_TUNED = 0x4
 PRECISIONS = {"ref64": PF_REF64, "f64": PF_REF64, "f32": PF_F32, "f16": PF_F16, "bf16": PF_BF16}
 _POS_DTYPE = {PF_REF64: np.float64, PF_F32: np.float32, PF_F16: np.float16, PF_BF16: None}
 
@@ -61,6 +63,14 @@ class PfStateHeader(ctypes.Structure):
         ("next_anchor_x", ctypes.c_double), ("next_anchor_y", ctypes.c_double),
         ("est_x", ctypes.c_double), ("est_y", ctypes.c_double),
     ]
+
+
+class PfTuning(ctypes.Structure):
+    _fields_ = [("tile", ctypes.c_int32), ("window", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {"tile": self.tile, "window": self.window, "ctas_per_sm": self.ctas_per_sm}
 
 
 class PfServerConfig(ctypes.Structure):
@@ -126,6 +136,11 @@ _SIG = {
     "pf_step_frame_noalloc": (ctypes.c_int, [ctypes.POINTER(PfConfig), _P, _P, _P, _P, _P, _I64,
                                              _P, _P, _P, _P, _P]),
     "pf_batch_destroy": (ctypes.c_int, [_P]),
+    "pf_autotune": (ctypes.c_int, [ctypes.POINTER(PfConfig), _I32, _P, _I64, _I64, _I32, ctypes.POINTER(PfTuning),
+                                   ctypes.POINTER(ctypes.c_double)]),
+    "pf_tuning_lookup": (ctypes.c_int, [ctypes.POINTER(PfConfig), ctypes.POINTER(PfTuning)]),
+    "pf_tuning_store": (ctypes.c_int, [ctypes.POINTER(PfConfig), ctypes.POINTER(PfTuning)]),
+    "pf_tuning_clear": (ctypes.c_int, []),
     "pf_server_now": (ctypes.c_double, []),
     "pf_server_create": (ctypes.c_int, [ctypes.POINTER(PfServerConfig), ctypes.POINTER(_P)]),
     "pf_server_open": (ctypes.c_int, [_P, ctypes.POINTER(PfConfig), ctypes.c_double, _I32, ctypes.POINTER(_I32)]),
@@ -317,6 +332,41 @@ def pf_batch_destroy(h):
 
 
 # ------------------------------------------------------------------ convenience wrappers
+def pf_autotune(cfg: PfConfig, copies: int, video_ptr: int, pitch: int, stride: int, n_frames: int):
+    """(tuning, us per frame of the fastest candidate)."""
+    t = PfTuning()
+    us = ctypes.c_double(0.0)
+    _check(lib().pf_autotune(ctypes.byref(cfg), copies, _P(video_ptr), pitch, stride, n_frames, ctypes.byref(t),
+                             ctypes.byref(us)), "pf_autotune")
+    return t, us.value
+
+
+def pf_tuning_lookup(cfg: PfConfig):
+    """The cached tuning of cfg's shape bucket, or None."""
+    t = PfTuning()
+    rc = lib().pf_tuning_lookup(ctypes.byref(cfg), ctypes.byref(t))
+    if rc == PF_ERR_STATE:
+        return None
+    _check(rc, "pf_tuning_lookup")
+    return t
+
+
+def pf_tuning_store(cfg: PfConfig, tile: int, window: int, ctas_per_sm: int):
+    t = PfTuning(tile=tile, window=window, ctas_per_sm=ctas_per_sm, reserved=0)
+    _check(lib().pf_tuning_store(ctypes.byref(cfg), ctypes.byref(t)), "pf_tuning_store")
+
+
+def pf_tuning_clear():
+    _check(lib().pf_tuning_clear(), "pf_tuning_clear")
+
+
+def autotune(cfg: PfConfig, video, copies: int = 1):
+    """Tune cfg's shape bucket on a resident video (CUDA uint8 tensor (T, H, W)); returns
+    (tuning dict, microseconds per frame of the fastest shape)."""
+    t, us = pf_autotune(cfg, copies, video.data_ptr(), video.stride(1), video.stride(0), video.shape[0])
+    return t.as_dict(), us
+
+
 def pf_server_now() -> float:
     return float(lib().pf_server_now())
 

@@ -38,7 +38,7 @@ inline pf_status check_config(const pf_config *c) {
         return PF_ERR_ARG;
     if (fabs(c->init_x) > 1.0e6 || fabs(c->init_y) > 1.0e6) return PF_ERR_ARG;
     if (c->est_capacity < 0 || c->reserved != 0) return PF_ERR_ARG;
-    if (c->flags & ~(PF_FLAG_DEBUG_ARRAYS | PF_FLAG_ACCUM32)) return PF_ERR_ARG;
+    if (c->flags & ~(PF_FLAG_DEBUG_ARRAYS | PF_FLAG_ACCUM32 | PF_FLAG_TUNED)) return PF_ERR_ARG;
     return PF_OK;
 }
 

@@ -86,7 +86,8 @@ struct TrackerDev {
     float pad2;
     // FP32 copies for the FP32 kernels
     float init_xf, init_yf, drift_xf, drift_yf, sigma_xf, sigma_yf;
-    float c1f, c2Df, denf, pad3;
+    float c1f, c2Df, denf;
+    int32_t window;            // likelihood window: 0 adaptive, 1 always 3.5 sigma, 2 always the full draw range
     void *px[2], *py[2], *pl[2];
     int32_t *dbg_anc;          // NULL unless PF_FLAG_DEBUG_ARRAYS
     void *dbg_cdf;

@@ -6,6 +6,9 @@
 #include <stddef.h>
 #include <string.h>
 
+#include <algorithm>
+#include <map>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -16,6 +19,46 @@
 using namespace pfk;
 
 namespace {
+
+// ---------------------------------------------------------------- launch-shape cache
+struct TuneKey {
+    int prec, lg, r, sq;
+    bool operator<(const TuneKey &o) const {
+        if (prec != o.prec) return prec < o.prec;
+        if (lg != o.lg) return lg < o.lg;
+        if (r != o.r) return r < o.r;
+        return sq < o.sq;
+    }
+};
+
+std::mutex g_tune_lock;
+std::map<TuneKey, pf_tuning> g_tune;
+
+// shape bucket: precision, floor(log2 N), radius, the larger sigma in quarter pixels
+TuneKey tune_key(const pf_config &c) {
+    int lg = 0;
+    while (lg < 62 && (int64_t(1) << (lg + 1)) <= c.num_particles) ++lg;
+    const double sg = std::max(c.sigma_x, c.sigma_y);
+    const int sq = static_cast<int>(std::min(4.0 * sg + 0.5, 1.0e6));
+    return TuneKey{c.precision, lg, c.disk_radius, sq};
+}
+
+bool valid_tuning(const pf_tuning &t) {
+    return (t.tile == 0 || (t.tile % 8 == 0 && t.tile >= 1024 && t.tile <= kTile)) && t.window >= 0 &&
+           t.window <= 2 && t.ctas_per_sm >= 0 && t.ctas_per_sm <= 32 && t.reserved == 0;
+}
+
+// the launch shape a tracker takes: forced, else its bucket's (PF_FLAG_TUNED), else default
+pf_tuning tuning_for(const pf_config &c, const pf_tuning *force) {
+    if (force) return *force;
+    pf_tuning t{0, 0, 0, 0};
+    if (c.flags & PF_FLAG_TUNED) {
+        std::lock_guard<std::mutex> g(g_tune_lock);
+        auto it = g_tune.find(tune_key(c));
+        if (it != g_tune.end()) t = it->second;
+    }
+    return t;
+}
 
 // One allocation carved into aligned pieces.
 struct Arena {
@@ -48,6 +91,7 @@ struct Engine {
     char *d_arena = nullptr;
     int total_tiles = 0;
     int grid = 0;
+    int ctas_cap = 0;                  // CTAs per SM (0: as many as fit)
     pf_status sticky = PF_OK;
     uint8_t *d_frame_buf = nullptr;    // single tracker: staging of host frames
     TrackerState *h_init_pinned = nullptr;  // initial state of every tracker (pf_reset)
@@ -90,7 +134,8 @@ static void engine_free(Engine &e) {
     e.d_arena = nullptr; e.d_frame_buf = nullptr; e.h_frames_pinned = nullptr;
 }
 
-static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stream, bool stage_frames) {
+static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stream, bool stage_frames,
+                             const pf_tuning *force = nullptr) {
     if (n < 1 || !cfgs) return PF_ERR_ARG;
     for (int i = 0; i < n; ++i) {
         pf_status s = check_config(&cfgs[i]);
@@ -118,7 +163,10 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
     for (int i = 0; i < n; ++i) {
         const pf_config &c = cfgs[i];
         const int64_t N = c.num_particles;
-        const int tile = step_tile_size(e.prec, N);
+        const pf_tuning tun = tuning_for(c, force);
+        if (!valid_tuning(tun)) return PF_ERR_ARG;
+        const int tile = tun.tile ? tun.tile : step_tile_size(e.prec, N);
+        e.ctas_cap = (i == 0 || (e.ctas_cap > 0 && tun.ctas_per_sm > 0)) ? std::max(e.ctas_cap, tun.ctas_per_sm) : 0;
         const int64_t nt64 = (N + tile - 1) / tile;
         if (nt64 > 0x7fffffff) return PF_ERR_ARG;
         const int nt = static_cast<int>(nt64);
@@ -146,6 +194,7 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
         T.tile = tile;
         T.ntiles = nt;
         T.est_cap = cap;
+        T.window = tun.window;
         tiles += nt;
     }
     e.total_tiles = static_cast<int>(tiles);
@@ -211,6 +260,12 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
     if (err == cudaSuccess) err = cudaStreamSynchronize(e.stream);   // host vectors go out of scope
     if (err != cudaSuccess) { cudaGetLastError(); engine_free(e); return PF_ERR_CUDA; }
     e.grid = step_grid_size(e.prec, e.total_tiles);
+    if (e.ctas_cap > 0) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms > 0) e.grid = std::min(e.grid, sms * e.ctas_cap);
+    }
     return PF_OK;
 }
 
@@ -627,11 +682,8 @@ pf_status pf_batch_step(pf_batch *b, const uint8_t *const *frames, const int64_t
     return PF_OK;
 }
 
-pf_status pf_batch_set_videos(pf_batch *b, const uint8_t *const *videos, const int64_t *pitches,
-                              const int64_t *frame_strides) {
-    if (!b || !videos || !pitches || !frame_strides) return PF_ERR_ARG;
-    Engine &e = b->e;
-    if (e.sticky != PF_OK) return PF_ERR_STATE;
+static pf_status engine_set_videos(Engine &e, const uint8_t *const *videos, const int64_t *pitches,
+                                   const int64_t *frame_strides) {
     for (int i = 0; i < e.n; ++i)
         if (!videos[i] || pitches[i] < e.cfg[i].width || frame_strides[i] < pitches[i] * e.cfg[i].height)
             return PF_ERR_ARG;
@@ -648,6 +700,13 @@ pf_status pf_batch_set_videos(pf_batch *b, const uint8_t *const *videos, const i
     return engine_upload_frames(e);
 }
 
+pf_status pf_batch_set_videos(pf_batch *b, const uint8_t *const *videos, const int64_t *pitches,
+                              const int64_t *frame_strides) {
+    if (!b || !videos || !pitches || !frame_strides) return PF_ERR_ARG;
+    if (b->e.sticky != PF_OK) return PF_ERR_STATE;
+    return engine_set_videos(b->e, videos, pitches, frame_strides);
+}
+
 pf_status pf_batch_run(pf_batch *b, int32_t count) {
     if (!b || count < 0) return PF_ERR_ARG;
     Engine &e = b->e;
@@ -660,10 +719,7 @@ pf_status pf_batch_run(pf_batch *b, int32_t count) {
     return PF_OK;
 }
 
-pf_status pf_batch_reset(pf_batch *b) {
-    if (!b) return PF_ERR_ARG;
-    Engine &e = b->e;
-    if (e.sticky != PF_OK) return PF_ERR_STATE;
+static pf_status engine_reset(Engine &e) {
     const size_t tail = sizeof(TrackerState) - offsetof(TrackerState, M);
     pf_status s = engine_wait_staging(e);
     if (s != PF_OK) return s;
@@ -680,6 +736,12 @@ pf_status pf_batch_reset(pf_batch *b) {
         e.done_frames[i] = 0;
     }
     return engine_upload_frames(e);
+}
+
+pf_status pf_batch_reset(pf_batch *b) {
+    if (!b) return PF_ERR_ARG;
+    if (b->e.sticky != PF_OK) return PF_ERR_STATE;
+    return engine_reset(b->e);
 }
 
 pf_status pf_batch_estimates(pf_batch *b, int64_t frame_index, double *xy) {
@@ -708,3 +770,93 @@ pf_status pf_batch_destroy(pf_batch *b) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------- autotuning
+pf_status pf_tuning_lookup(const pf_config *cfg, pf_tuning *out) {
+    if (!out || check_config(cfg) != PF_OK) return PF_ERR_ARG;
+    std::lock_guard<std::mutex> g(g_tune_lock);
+    auto it = g_tune.find(tune_key(*cfg));
+    if (it == g_tune.end()) return PF_ERR_STATE;
+    *out = it->second;
+    return PF_OK;
+}
+
+pf_status pf_tuning_store(const pf_config *cfg, const pf_tuning *t) {
+    if (!t || check_config(cfg) != PF_OK || !valid_tuning(*t)) return PF_ERR_ARG;
+    std::lock_guard<std::mutex> g(g_tune_lock);
+    g_tune[tune_key(*cfg)] = *t;
+    return PF_OK;
+}
+
+pf_status pf_tuning_clear(void) {
+    std::lock_guard<std::mutex> g(g_tune_lock);
+    g_tune.clear();
+    return PF_OK;
+}
+
+pf_status pf_autotune(const pf_config *cfg, int32_t copies, const uint8_t *video, int64_t pitch_bytes,
+                      int64_t frame_stride, int32_t n_frames, pf_tuning *best, double *best_us_per_frame) {
+    if (!best || check_config(cfg) != PF_OK || copies < 1 || copies > 4096 || !video || n_frames < 1) return PF_ERR_ARG;
+    if (pitch_bytes < cfg->width || frame_stride < pitch_bytes * cfg->height) return PF_ERR_ARG;
+    std::vector<pf_config> cfgs(copies, *cfg);
+    for (int i = 0; i < copies; ++i) {
+        cfgs[i].tracker_id = cfg->tracker_id + static_cast<uint32_t>(i);
+        cfgs[i].flags &= ~(PF_FLAG_DEBUG_ARRAYS | PF_FLAG_TUNED);
+        cfgs[i].est_capacity = n_frames + 1;
+    }
+    std::vector<const uint8_t *> vids(copies, video);
+    std::vector<int64_t> pitches(copies, pitch_bytes), strides(copies, frame_stride);
+    cudaStream_t stream = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t err = cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking);
+    if (err == cudaSuccess) err = cudaEventCreate(&e0);
+    if (err == cudaSuccess) err = cudaEventCreate(&e1);
+    if (err != cudaSuccess) {
+        cudaGetLastError();
+        if (e0) cudaEventDestroy(e0);
+        if (stream) cudaStreamDestroy(stream);
+        return PF_ERR_CUDA;
+    }
+    static const int32_t kTiles[] = {0, 1024, 2048, 3072, 4096};
+    pf_tuning win{0, 0, 0, 0};
+    double win_ms = -1.0;
+    pf_status result = PF_OK;
+    for (int32_t tile : kTiles) {
+        for (int32_t window = 0; window <= 2; ++window) {
+            for (int32_t ctas = 0; ctas <= 1; ++ctas) {
+                const pf_tuning cand{tile, window, ctas, 0};
+                pf_batch *b = new (std::nothrow) pf_batch();
+                if (!b) { result = PF_ERR_OOM; break; }
+                pf_status s = engine_init(b->e, cfgs.data(), copies, stream, false, &cand);
+                if (s != PF_OK) { delete b; if (s == PF_ERR_OOM) continue; result = s; break; }
+                Engine &e = b->e;
+                float ms = 0.0f;
+                s = engine_set_videos(e, vids.data(), pitches.data(), strides.data());
+                if (s == PF_OK) s = engine_run_resident(e, n_frames);       // warm-up (and graph capture)
+                if (s == PF_OK) s = engine_reset(e);
+                if (s == PF_OK && (cudaEventRecord(e0, stream) != cudaSuccess)) s = PF_ERR_CUDA;
+                if (s == PF_OK) s = engine_run_resident(e, n_frames);
+                if (s == PF_OK && (cudaEventRecord(e1, stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                                   cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                    s = PF_ERR_CUDA;
+                if (s == PF_OK) s = engine_sync_status(e);
+                engine_free(e);
+                delete b;
+                if (s != PF_OK) { cudaGetLastError(); result = s; break; }
+                if (win_ms < 0 || ms < win_ms) { win_ms = ms; win = cand; }
+            }
+            if (result != PF_OK) break;
+        }
+        if (result != PF_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(stream);
+    if (result != PF_OK) return result;
+    if (win_ms < 0) return PF_ERR_OOM;
+    *best = win;
+    if (best_us_per_frame) *best_us_per_frame = 1e3 * win_ms / n_frames;
+    std::lock_guard<std::mutex> g(g_tune_lock);
+    g_tune[tune_key(*cfg)] = win;
+    return PF_OK;
+}

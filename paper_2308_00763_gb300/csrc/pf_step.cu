@@ -799,11 +799,13 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
                 by0 = fminf(by0, v.z); by1 = fmaxf(by1, v.w);
             }
             // Every draw lies within kDrawMax sigma: if that window takes a single pass of
-            // the block, no offspring needs the direct route; otherwise kWindowSigmas.
+            // the block, no offspring needs the direct route; otherwise kWindowSigmas
+            // (the tracker's window policy may force either).
             float mxr = fabsf(T.drift_xf) + kDrawMax * T.sigma_xf + 1.0f;
             float myr = fabsf(T.drift_yf) + kDrawMax * T.sigma_yf + 1.0f;
-            if ((ceilf(bx1 + mxr) - floorf(bx0 - mxr) + 1.0f) * (ceilf(by1 + myr) - floorf(by0 - myr) + 1.0f) >
-                static_cast<float>(kThreads)) {
+            if (T.window == 1 ||
+                (T.window == 0 && (ceilf(bx1 + mxr) - floorf(bx0 - mxr) + 1.0f) * (ceilf(by1 + myr) - floorf(by0 - myr) + 1.0f) >
+                                      static_cast<float>(kThreads))) {
                 mxr = fabsf(T.drift_xf) + kWindowSigmas * T.sigma_xf + 1.0f;
                 myr = fabsf(T.drift_yf) + kWindowSigmas * T.sigma_yf + 1.0f;
             }

@@ -94,3 +94,23 @@ def test_server_stream_bytes_without_gpu(libpath):
             assert pf.pf_server_stream_bytes(c, 0, 1) == dev
     with pytest.raises(pf.PfError):
         pf.pf_server_stream_bytes(pf.make_config(0, 480, 10, 5, "f16"), 0, 4)
+
+
+def test_tuning_cache_without_gpu(libpath):
+    """The launch-shape cache is host state keyed by the shape bucket (precision,
+    floor(log2 N), radius, larger sigma in quarter pixels); invalid shapes are refused."""
+    import paper_2308_00763_gb300 as pf
+    pf.pf_tuning_clear()
+    a = pf.make_config(512, 512, 1 << 20, 5, "f16", sigma=(1.0, 1.0))
+    same_bucket = pf.make_config(256, 256, (1 << 21) - 1, 5, "f16", sigma=(1.1, 0.9))
+    other = pf.make_config(512, 512, 1 << 20, 5, "f32", sigma=(1.0, 1.0))
+    assert pf.pf_tuning_lookup(a) is None
+    pf.pf_tuning_store(a, 2048, 1, 1)
+    t = pf.pf_tuning_lookup(same_bucket)
+    assert t is not None and (t.tile, t.window, t.ctas_per_sm) == (2048, 1, 1)
+    assert pf.pf_tuning_lookup(other) is None
+    for bad in ((1000, 0, 0), (8192, 0, 0), (2048, 3, 0), (2048, 0, -1)):
+        with pytest.raises(pf.PfError):
+            pf.pf_tuning_store(a, *bad)
+    pf.pf_tuning_clear()
+    assert pf.pf_tuning_lookup(a) is None
