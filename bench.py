@@ -391,7 +391,9 @@ def _cpu_baseline(v, tracks):
 def _batched(dev, stream, steps, warmup, precision):
     """256 independent trackers of uneven size (frames 256^2..1024^2, 1k..262k particles,
     radius 3..12, speed < 4 px/frame, 60 frames, sigma 2 px) in one launch per frame, their
-    videos resident in HBM, the 60 launches of a step replayed from one CUDA graph."""
+    videos resident in HBM, the 60 launches of a step replayed from one CUDA graph; timed
+    with the default launch shapes and again with the shape the autotuner picks for this
+    batch (its sweep timed on the batch itself)."""
     import numpy as np
     import torch
     import paper_2308_00763_gb300 as pf
@@ -399,34 +401,55 @@ def _batched(dev, stream, steps, warmup, precision):
     specs = synth.batch_workload()
     vids = [synth.make_video_device(s["W"], s["H"], s["T"], s["r"], v=s["v"], noise=s["noise"], seed=s["seed"],
                                     device=dev) for s in specs]
-    cfgs = [pf.make_config(s["W"], s["H"], s["N"], s["r"], precision, init=tuple(c[0]), sigma=(2.0, 2.0),
-                           seed=s["seed"], tracker_id=i) for i, (s, (_, c)) in enumerate(zip(specs, vids))]
     T = specs[0]["T"]
-    b = pf.Batch(cfgs, stream=stream)
-    b.set_videos([f for f, _ in vids])
-    for _ in range(warmup):
-        b.reset()
-        b.run(T)
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-    for k in range(steps):
-        flush.zero_()
-        ev[k][0].record(stream)
-        b.reset()
-        b.run(T)
-        ev[k][1].record(stream)
-    torch.cuda.synchronize(dev)
-    ms = [a.elapsed_time(c) for a, c in ev]
     total_n = sum(s["N"] for s in specs)
-    est = np.stack([b.estimates(t) for t in range(T)], axis=1)        # (trackers, T, 2)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    def cfgs_for(flags):
+        return [pf.make_config(s["W"], s["H"], s["N"], s["r"], precision, init=tuple(c[0]), sigma=(2.0, 2.0),
+                               seed=s["seed"], tracker_id=i, flags=flags)
+                for i, (s, (_, c)) in enumerate(zip(specs, vids))]
+
+    def timed(cfgs):
+        b = pf.Batch(cfgs, stream=stream)
+        b.set_videos([f for f, _ in vids])
+        for _ in range(warmup):
+            b.reset()
+            b.run(T)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for k in range(steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            b.reset()
+            b.run(T)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+        ms = [a.elapsed_time(c) for a, c in ev]
+        est = np.stack([b.estimates(t) for t in range(T)], axis=1)        # (trackers, T, 2)
+        b.close()
+        return ms, est
+
+    ms, est = timed(cfgs_for(0))
     err = [float(np.sqrt(np.mean(np.sum((est[i] - vids[i][1]) ** 2, axis=1)))) for i in range(len(specs))]
-    b.close()
+    out = {"workload": "256 trackers, frames 256^2-1024^2, 1k-262k particles (sum %d), r 3-12, 60 frames" % total_n,
+           "precision": precision, "value": total_n * T * steps / (sum(ms) * 1e-3), "unit": METRIC,
+           "ms_per_step": sum(ms) / steps, "us_per_frame": 1e3 * sum(ms) / steps / T, "steps": steps,
+           "gpu_launches_per_step": T, "rmse_px_vs_truth_median": float(np.median(err)),
+           "trackers_within_2px": int(sum(e < 2.0 for e in err))}
+
+    # autotuned shape: the sweep run on this batch itself (8 frames of every video)
+    pf.pf_tuning_clear()
+    t0 = time.perf_counter()
+    shape, us = pf.autotune_batch(cfgs_for(0), [f[:8] for f, _ in vids])
+    tune_s = time.perf_counter() - t0
+    ms_t, est_t = timed(cfgs_for(pf.PF_FLAG_TUNED))
+    err_t = [float(np.sqrt(np.mean(np.sum((est_t[i] - vids[i][1]) ** 2, axis=1)))) for i in range(len(specs))]
+    pf.pf_tuning_clear()
+    out["autotuned"] = {"value": total_n * T * steps / (sum(ms_t) * 1e-3), "unit": METRIC,
+                        "us_per_frame": 1e3 * sum(ms_t) / steps / T, "tuning_seconds": tune_s, "shape": shape,
+                        "sweep_best_us_per_frame": us, "rmse_px_vs_truth_median": float(np.median(err_t))}
     del vids
-    return {"workload": "256 trackers, frames 256^2-1024^2, 1k-262k particles (sum %d), r 3-12, 60 frames" % total_n,
-            "precision": precision, "value": total_n * T * steps / (sum(ms) * 1e-3), "unit": METRIC,
-            "ms_per_step": sum(ms) / steps, "us_per_frame": 1e3 * sum(ms) / steps / T, "steps": steps,
-            "gpu_launches_per_step": T, "rmse_px_vs_truth_median": float(np.median(err)),
-            "trackers_within_2px": int(sum(e < 2.0 for e in err))}
+    return out
 
 
 def _serving(dev, capacity, seconds):

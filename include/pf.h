@@ -236,8 +236,8 @@ pf_status pf_batch_destroy(pf_batch *b);
  * (n_frames frames of rows pitch_bytes apart, frame_stride bytes apart, on the device)
  * with `copies` trackers of that configuration in one batch (1 = the tracker alone; more
  * = throughput with the device full, as in a batch), and caches the fastest for the
- * configuration's shape bucket: (precision, floor(log2 N), disk radius, the larger sigma
- * in quarter pixels).  Trackers created with PF_FLAG_TUNED take their bucket's cached
+ * configuration's shape bucket: (precision, floor(log2 N), the larger sigma in quarter
+ * pixels).  Trackers created with PF_FLAG_TUNED take their bucket's cached
  * shape (the default shape if none), so equal configurations tile alike alone and in a
  * batch.  The cache lives in the process (pf_tuning_clear empties it).  Synchronises. */
 typedef struct {
@@ -249,6 +249,12 @@ typedef struct {
 
 pf_status pf_autotune(const pf_config *cfg, int32_t copies, const uint8_t *video, int64_t pitch_bytes,
                       int64_t frame_stride, int32_t n_frames, pf_tuning *best, double *best_us_per_frame);
+/* The same sweep with every candidate applied to a whole batch (trackers cfgs[0..n) over
+ * their resident videos, as pf_batch_set_videos takes them): the fastest shape is cached
+ * for every bucket of the batch. */
+pf_status pf_autotune_batch(const pf_config *cfgs, int32_t n, const uint8_t *const *videos, const int64_t *pitches,
+                            const int64_t *frame_strides, int32_t n_frames, pf_tuning *best,
+                            double *best_us_per_frame);
 /* The cached shape of cfg's bucket; PF_ERR_STATE if none. */
 pf_status pf_tuning_lookup(const pf_config *cfg, pf_tuning *out);
 /* Cache a shape for cfg's bucket (checked as pf_autotune's candidates are). */

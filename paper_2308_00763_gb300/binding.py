@@ -18,8 +18,8 @@ from . import build as _build
 __all__ = [
     "PF_OK", "PF_ERR_ARG", "PF_ERR_OOM", "PF_ERR_CUDA", "PF_ERR_TIMEOUT", "PF_ERR_STATE",
     "PF_ERR_ADMISSION", "PF_REF64", "PF_F32", "PF_F16", "PF_BF16", "PF_FLAG_DEBUG_ARRAYS",
-    "PF_FLAG_ACCUM32", "PF_FLAG_TUNED", "PfTuning", "pf_autotune", "pf_tuning_lookup", "pf_tuning_store",
-    "pf_tuning_clear", "autotune", "PfConfig", "PfStateHeader", "PfError", "lib", "library_path",
+    "PF_FLAG_ACCUM32", "PF_FLAG_TUNED", "PfTuning", "pf_autotune", "pf_autotune_batch", "pf_tuning_lookup",
+    "pf_tuning_store", "pf_tuning_clear", "autotune", "autotune_batch", "PfConfig", "PfStateHeader", "PfError", "lib", "library_path",
     "pf_status_string", "pf_create", "pf_step_frame", "pf_run_frames", "pf_estimate",
     "pf_estimates", "pf_frames_done", "pf_reset", "pf_destroy", "pf_get_state", "pf_set_state", "pf_get_debug",
     "pf_debug_philox", "pf_debug_wait_timeout", "pf_batch_create", "pf_batch_step", "pf_batch_estimates",
@@ -138,6 +138,8 @@ _SIG = {
     "pf_batch_destroy": (ctypes.c_int, [_P]),
     "pf_autotune": (ctypes.c_int, [ctypes.POINTER(PfConfig), _I32, _P, _I64, _I64, _I32, ctypes.POINTER(PfTuning),
                                    ctypes.POINTER(ctypes.c_double)]),
+    "pf_autotune_batch": (ctypes.c_int, [ctypes.POINTER(PfConfig), _I32, _P, _P, _P, _I32, ctypes.POINTER(PfTuning),
+                                         ctypes.POINTER(ctypes.c_double)]),
     "pf_tuning_lookup": (ctypes.c_int, [ctypes.POINTER(PfConfig), ctypes.POINTER(PfTuning)]),
     "pf_tuning_store": (ctypes.c_int, [ctypes.POINTER(PfConfig), ctypes.POINTER(PfTuning)]),
     "pf_tuning_clear": (ctypes.c_int, []),
@@ -339,6 +341,29 @@ def pf_autotune(cfg: PfConfig, copies: int, video_ptr: int, pitch: int, stride: 
     _check(lib().pf_autotune(ctypes.byref(cfg), copies, _P(video_ptr), pitch, stride, n_frames, ctypes.byref(t),
                              ctypes.byref(us)), "pf_autotune")
     return t, us.value
+
+
+def pf_autotune_batch(cfgs, video_ptrs, pitches, strides, n_frames: int):
+    """(tuning, us per frame of the fastest shape) over a whole batch."""
+    n = len(cfgs)
+    arr = (PfConfig * n)(*cfgs)
+    vp = (ctypes.c_void_p * n)(*video_ptrs)
+    pp = (ctypes.c_int64 * n)(*pitches)
+    sp = (ctypes.c_int64 * n)(*strides)
+    t = PfTuning()
+    us = ctypes.c_double(0.0)
+    _check(lib().pf_autotune_batch(arr, n, vp, pp, sp, n_frames, ctypes.byref(t), ctypes.byref(us)),
+           "pf_autotune_batch")
+    return t, us.value
+
+
+def autotune_batch(cfgs, videos, n_frames=None):
+    """Tune a batch's shape on its resident videos (CUDA uint8 tensors (T_i, H_i, W_i));
+    returns (tuning dict, microseconds per frame of the fastest shape)."""
+    n_frames = n_frames or min(v.shape[0] for v in videos)
+    t, us = pf_autotune_batch(cfgs, [v.data_ptr() for v in videos], [v.stride(1) for v in videos],
+                              [v.stride(0) for v in videos], n_frames)
+    return t.as_dict(), us
 
 
 def pf_tuning_lookup(cfg: PfConfig):

@@ -22,11 +22,10 @@ namespace {
 
 // ---------------------------------------------------------------- launch-shape cache
 struct TuneKey {
-    int prec, lg, r, sq;
+    int prec, lg, sq;
     bool operator<(const TuneKey &o) const {
         if (prec != o.prec) return prec < o.prec;
         if (lg != o.lg) return lg < o.lg;
-        if (r != o.r) return r < o.r;
         return sq < o.sq;
     }
 };
@@ -34,13 +33,13 @@ struct TuneKey {
 std::mutex g_tune_lock;
 std::map<TuneKey, pf_tuning> g_tune;
 
-// shape bucket: precision, floor(log2 N), radius, the larger sigma in quarter pixels
+// shape bucket: precision, floor(log2 N), the larger sigma in quarter pixels
 TuneKey tune_key(const pf_config &c) {
     int lg = 0;
     while (lg < 62 && (int64_t(1) << (lg + 1)) <= c.num_particles) ++lg;
     const double sg = std::max(c.sigma_x, c.sigma_y);
     const int sq = static_cast<int>(std::min(4.0 * sg + 0.5, 1.0e6));
-    return TuneKey{c.precision, lg, c.disk_radius, sq};
+    return TuneKey{c.precision, lg, sq};
 }
 
 bool valid_tuning(const pf_tuning &t) {
@@ -794,18 +793,16 @@ pf_status pf_tuning_clear(void) {
     return PF_OK;
 }
 
-pf_status pf_autotune(const pf_config *cfg, int32_t copies, const uint8_t *video, int64_t pitch_bytes,
-                      int64_t frame_stride, int32_t n_frames, pf_tuning *best, double *best_us_per_frame) {
-    if (!best || check_config(cfg) != PF_OK || copies < 1 || copies > 4096 || !video || n_frames < 1) return PF_ERR_ARG;
-    if (pitch_bytes < cfg->width || frame_stride < pitch_bytes * cfg->height) return PF_ERR_ARG;
-    std::vector<pf_config> cfgs(copies, *cfg);
-    for (int i = 0; i < copies; ++i) {
-        cfgs[i].tracker_id = cfg->tracker_id + static_cast<uint32_t>(i);
-        cfgs[i].flags &= ~(PF_FLAG_DEBUG_ARRAYS | PF_FLAG_TUNED);
-        cfgs[i].est_capacity = n_frames + 1;
+// Time every candidate shape, applied to all trackers alike, on a batch of these trackers
+// over their resident videos; the fastest shape and its time per frame.
+static pf_status sweep_shapes(std::vector<pf_config> cfgs, const std::vector<const uint8_t *> &vids,
+                              const std::vector<int64_t> &pitches, const std::vector<int64_t> &strides,
+                              int32_t n_frames, pf_tuning *best, double *best_us) {
+    const int n = static_cast<int>(cfgs.size());
+    for (pf_config &c : cfgs) {
+        c.flags &= ~(PF_FLAG_DEBUG_ARRAYS | PF_FLAG_TUNED);
+        c.est_capacity = n_frames + 1;
     }
-    std::vector<const uint8_t *> vids(copies, video);
-    std::vector<int64_t> pitches(copies, pitch_bytes), strides(copies, frame_stride);
     cudaStream_t stream = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t err = cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking);
@@ -822,30 +819,29 @@ pf_status pf_autotune(const pf_config *cfg, int32_t copies, const uint8_t *video
     double win_ms = -1.0;
     pf_status result = PF_OK;
     for (int32_t tile : kTiles) {
-        for (int32_t window = 0; window <= 2; ++window) {
-            for (int32_t ctas = 0; ctas <= 1; ++ctas) {
+        for (int32_t window = 0; window <= 2 && result == PF_OK; ++window) {
+            for (int32_t ctas = 0; ctas <= 1 && result == PF_OK; ++ctas) {
                 const pf_tuning cand{tile, window, ctas, 0};
                 pf_batch *b = new (std::nothrow) pf_batch();
                 if (!b) { result = PF_ERR_OOM; break; }
-                pf_status s = engine_init(b->e, cfgs.data(), copies, stream, false, &cand);
-                if (s != PF_OK) { delete b; if (s == PF_ERR_OOM) continue; result = s; break; }
+                pf_status st = engine_init(b->e, cfgs.data(), n, stream, false, &cand);
+                if (st != PF_OK) { delete b; if (st != PF_ERR_OOM) result = st; continue; }
                 Engine &e = b->e;
                 float ms = 0.0f;
-                s = engine_set_videos(e, vids.data(), pitches.data(), strides.data());
-                if (s == PF_OK) s = engine_run_resident(e, n_frames);       // warm-up (and graph capture)
-                if (s == PF_OK) s = engine_reset(e);
-                if (s == PF_OK && (cudaEventRecord(e0, stream) != cudaSuccess)) s = PF_ERR_CUDA;
-                if (s == PF_OK) s = engine_run_resident(e, n_frames);
-                if (s == PF_OK && (cudaEventRecord(e1, stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-                                   cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
-                    s = PF_ERR_CUDA;
-                if (s == PF_OK) s = engine_sync_status(e);
+                st = engine_set_videos(e, vids.data(), pitches.data(), strides.data());
+                if (st == PF_OK) st = engine_run_resident(e, n_frames);       // warm-up (and graph capture)
+                if (st == PF_OK) st = engine_reset(e);
+                if (st == PF_OK && cudaEventRecord(e0, stream) != cudaSuccess) st = PF_ERR_CUDA;
+                if (st == PF_OK) st = engine_run_resident(e, n_frames);
+                if (st == PF_OK && (cudaEventRecord(e1, stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                                    cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                    st = PF_ERR_CUDA;
+                if (st == PF_OK) st = engine_sync_status(e);
                 engine_free(e);
                 delete b;
-                if (s != PF_OK) { cudaGetLastError(); result = s; break; }
+                if (st != PF_OK) { cudaGetLastError(); result = st; break; }
                 if (win_ms < 0 || ms < win_ms) { win_ms = ms; win = cand; }
             }
-            if (result != PF_OK) break;
         }
         if (result != PF_OK) break;
     }
@@ -855,8 +851,36 @@ pf_status pf_autotune(const pf_config *cfg, int32_t copies, const uint8_t *video
     if (result != PF_OK) return result;
     if (win_ms < 0) return PF_ERR_OOM;
     *best = win;
-    if (best_us_per_frame) *best_us_per_frame = 1e3 * win_ms / n_frames;
+    if (best_us) *best_us = 1e3 * win_ms / n_frames;
+    return PF_OK;
+}
+
+pf_status pf_autotune(const pf_config *cfg, int32_t copies, const uint8_t *video, int64_t pitch_bytes,
+                      int64_t frame_stride, int32_t n_frames, pf_tuning *best, double *best_us_per_frame) {
+    if (!best || check_config(cfg) != PF_OK || copies < 1 || copies > 4096 || !video || n_frames < 1) return PF_ERR_ARG;
+    if (pitch_bytes < cfg->width || frame_stride < pitch_bytes * cfg->height) return PF_ERR_ARG;
+    std::vector<pf_config> cfgs(copies, *cfg);
+    for (int i = 0; i < copies; ++i) cfgs[i].tracker_id = cfg->tracker_id + static_cast<uint32_t>(i);
+    pf_status s = sweep_shapes(cfgs, std::vector<const uint8_t *>(copies, video), std::vector<int64_t>(copies, pitch_bytes),
+                               std::vector<int64_t>(copies, frame_stride), n_frames, best, best_us_per_frame);
+    if (s != PF_OK) return s;
     std::lock_guard<std::mutex> g(g_tune_lock);
-    g_tune[tune_key(*cfg)] = win;
+    g_tune[tune_key(*cfg)] = *best;
+    return PF_OK;
+}
+
+pf_status pf_autotune_batch(const pf_config *cfgs, int32_t n, const uint8_t *const *videos, const int64_t *pitches,
+                            const int64_t *frame_strides, int32_t n_frames, pf_tuning *best, double *best_us_per_frame) {
+    if (!best || !cfgs || n < 1 || !videos || !pitches || !frame_strides || n_frames < 1) return PF_ERR_ARG;
+    for (int i = 0; i < n; ++i) {
+        if (check_config(&cfgs[i]) != PF_OK || cfgs[i].precision != cfgs[0].precision || !videos[i]) return PF_ERR_ARG;
+        if (pitches[i] < cfgs[i].width || frame_strides[i] < pitches[i] * cfgs[i].height) return PF_ERR_ARG;
+    }
+    pf_status s = sweep_shapes(std::vector<pf_config>(cfgs, cfgs + n), std::vector<const uint8_t *>(videos, videos + n),
+                               std::vector<int64_t>(pitches, pitches + n), std::vector<int64_t>(frame_strides, frame_strides + n),
+                               n_frames, best, best_us_per_frame);
+    if (s != PF_OK) return s;
+    std::lock_guard<std::mutex> g(g_tune_lock);
+    for (int i = 0; i < n; ++i) g_tune[tune_key(cfgs[i])] = *best;
     return PF_OK;
 }

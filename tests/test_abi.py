@@ -98,11 +98,11 @@ def test_server_stream_bytes_without_gpu(libpath):
 
 def test_tuning_cache_without_gpu(libpath):
     """The launch-shape cache is host state keyed by the shape bucket (precision,
-    floor(log2 N), radius, larger sigma in quarter pixels); invalid shapes are refused."""
+    floor(log2 N), larger sigma in quarter pixels); invalid shapes are refused."""
     import paper_2308_00763_gb300 as pf
     pf.pf_tuning_clear()
     a = pf.make_config(512, 512, 1 << 20, 5, "f16", sigma=(1.0, 1.0))
-    same_bucket = pf.make_config(256, 256, (1 << 21) - 1, 5, "f16", sigma=(1.1, 0.9))
+    same_bucket = pf.make_config(256, 256, (1 << 21) - 1, 9, "f16", sigma=(1.1, 0.9))
     other = pf.make_config(512, 512, 1 << 20, 5, "f32", sigma=(1.0, 1.0))
     assert pf.pf_tuning_lookup(a) is None
     pf.pf_tuning_store(a, 2048, 1, 1)

@@ -95,3 +95,17 @@ def test_tuned_batch_equals_tuned_singles(pf):
         assert np.array_equal(f.estimates(0, 5), got[i])
         f.close()
     pf.pf_tuning_clear()
+
+
+def test_autotune_batch_caches_every_bucket(pf):
+    pf.pf_tuning_clear()
+    vids = [_vid(T=4, seed=97), _vid(T=4, seed=98), _vid(T=4, seed=99)]
+    Ns = [3000, 40000, 300000]
+    cfgs = [pf.make_config(v.W, v.H, n, v.radius, "f32", init=tuple(v.centres[0]), seed=60 + i, tracker_id=i)
+            for i, ((v, _), n) in enumerate(zip(vids, Ns))]
+    t, us = pf.autotune_batch(cfgs, [fr for _, fr in vids])
+    assert us > 0 and t["tile"] in (0, 1024, 2048, 3072, 4096)
+    for c in cfgs:
+        got = pf.pf_tuning_lookup(c)
+        assert got is not None and got.as_dict() == t
+    pf.pf_tuning_clear()
