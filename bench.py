@@ -51,6 +51,7 @@ def _args():
     p.add_argument("--frames", type=int, default=T_)
     p.add_argument("--no-batch", action="store_true", help="skip the batched-trackers measurement")
     p.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    p.add_argument("--no-sweep", action="store_true", help="skip the precision/size sweep and the paper workload")
     p.add_argument("--serve-seconds", type=float, default=20.0, help="length of the served-streams run")
     return p.parse_args()
 
@@ -357,6 +358,9 @@ def run_ours(args):
     line["clocks"] = cs
     if not args.no_batch and ws == 1:
         line["systems"] = {"batched": _batched(dev, stream, max(3, min(args.steps, 10)), 2, hp)}
+    if not args.no_sweep and ws == 1:
+        line.setdefault("systems", {})["sweep"] = _sweep(dev, stream)
+        line["systems"]["paper_workload"] = _paper_workload(dev, stream)
     if not args.no_serve and ws == 1:
         cap = min(results[p]["value"] for p in results if p in ("f16", "f32")) if any(
             p in results for p in ("f16", "f32")) else head["value"]
@@ -505,6 +509,79 @@ def _serving(dev, capacity, seconds):
                      "hbm_peak_bytes": st["hbm_peak"]}
     del vids
     return out
+
+
+def _sweep(dev, stream):
+    """Precision / size sweep: 1024^2 frames, 50 frames, disk radius 10, noise sigma in
+    {2, 5, 15} (video seeds 1, 2, 3), N = 2^14 .. 2^24 by powers of 4, REF64 / F32 / F16 /
+    BF16 with FP32 accumulation of the likelihood; per run the particle-steps/s of the
+    whole track (resident frames, one replayed graph) and the track RMSE against the REF64
+    GPU track of the same video and N."""
+    import torch
+    import paper_2308_00763_gb300 as pf
+    from paper_2308_00763_gb300 import synth
+    T, W, r = 50, 1024, 10
+    runs = []
+    for k, noise in enumerate((2.0, 5.0, 15.0)):
+        v = synth.make_video(W, W, T, r, noise=noise, seed=k + 1)
+        fr = torch.from_numpy(v.frames).to(dev)
+        for lg in range(14, 25, 2):
+            N = 1 << lg
+            ref = None
+            for prec in ("ref64", "f32", "f16", "bf16"):
+                f = pf.Filter(W, W, N, r, prec, init=tuple(v.centres[0]), seed=k + 1, stream=stream,
+                              flags=pf.PF_FLAG_ACCUM32 if prec == "f16" else 0)
+                f.run(fr[:4])                                    # warm-up (graph capture)
+                f.reset()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                f.run(fr)
+                b.record(stream)
+                torch.cuda.synchronize(dev)
+                ms = a.elapsed_time(b)
+                est = f.estimates(0, T)
+                f.close()
+                if prec == "ref64":
+                    ref = est
+                runs.append({"noise": noise, "N": N, "precision": prec, "value": N * T / (ms * 1e-3),
+                             "us_per_frame": 1e3 * ms / T, "rmse_px_vs_ref64_gpu": _rmse(est, ref),
+                             "rmse_px_vs_truth": _rmse(est, v.centres)})
+        del fr
+    return {"workload": "1024^2 frames, 50 frames, r = 10, noise {2, 5, 15}, N 2^14..2^24 by 4x, "
+                        "FP32 accumulation of the likelihood", "unit": METRIC, "runs": runs}
+
+
+def _paper_workload(dev, stream):
+    """The paper's own motion model (drift (1, 2), sigma (5, 2); Eq. 1-2) on a 512^2
+    bouncing-disk video of 100 frames at its particle counts (128, 32k, 64k): us per frame
+    per precision and the FP16 speedups over FP32 and REF64 (the paper reports 1.5-2x and
+    2.5-4.6x on V100 / A100 / A40 / T4; quoted as context, other hardware)."""
+    import torch
+    import paper_2308_00763_gb300 as pf
+    from paper_2308_00763_gb300 import synth
+    v = synth.make_video(512, 512, 100, 5, noise=5.0, seed=1, v=(1.0, 2.0))
+    fr = torch.from_numpy(v.frames).to(dev)
+    out = {}
+    for N in (128, 32768, 65536):
+        row = {}
+        for prec in ("ref64", "f32", "f16"):
+            f = pf.Filter(512, 512, N, 5, prec, init=tuple(v.centres[0]), seed=1, stream=stream, sigma=(5.0, 2.0),
+                          drift=(1.0, 2.0))
+            f.run(fr[:4])
+            f.reset()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            f.run(fr)
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            row[prec] = {"us_per_frame": 10.0 * a.elapsed_time(b), "rmse_px_vs_truth": _rmse(f.estimates(0, 100), v.centres)}
+            f.close()
+        row["speedup_f16_over_f32"] = row["f32"]["us_per_frame"] / row["f16"]["us_per_frame"]
+        row["speedup_f16_over_ref64"] = row["ref64"]["us_per_frame"] / row["f16"]["us_per_frame"]
+        out[str(N)] = row
+    return {"workload": "512^2, 100 frames, disk r = 5 moving (+1, +2), drift (1, 2), sigma (5, 2)", "by_particles": out}
 
 
 def main():
