@@ -102,7 +102,11 @@ pf_status pf_step_frame(pf_filter *f, const uint8_t *frame, int64_t pitch_bytes,
 /* Run `count` frames in one call: frame i at frames + i * frame_stride (bytes), rows
  * pitch_bytes apart, all on the host (frames_on_device = 0) or all on the device (1).
  * Equivalent to `count` calls of pf_step_frame.  With device frames the `count` steps
- * are replayed from a CUDA graph captured on the first call with this count.
+ * are replayed from a CUDA graph captured on the first call with this count.  Host
+ * frames (frame_stride >= pitch_bytes * height) are copied chunk by chunk into a
+ * library ring of 16 frames on a copy stream while the previous chunk is stepped (each
+ * chunk of up to 8 frames replayed from a graph); pageable frames may be reused when
+ * the call returns, pinned frames once a synchronising call (pf_estimate) has returned.
  * Asynchronous. */
 pf_status pf_run_frames(pf_filter *f, const uint8_t *frames, int64_t pitch_bytes,
                         int64_t frame_stride, int32_t count, int32_t frames_on_device);

@@ -66,7 +66,7 @@ struct FrameRef {
     int64_t pitch;         // bytes between rows
     int64_t stride;        // if nonzero, frame of step t is base + t * stride
     int32_t active;        // 0: tracker not stepped this launch
-    int32_t pad;
+    int32_t ring;          // if nonzero (with stride): frame of step t is base + (t % ring) * stride
 };
 
 struct TrackerDev {

@@ -96,8 +96,13 @@ struct Engine {
     TrackerState *h_init_pinned = nullptr;  // initial state of every tracker (pf_reset)
     cudaEvent_t frames_copied = nullptr;     // the pinned frame table may be rewritten after it
     cudaStream_t capture_stream = nullptr;   // private stream used to capture step graphs
-    cudaGraphExec_t graph = nullptr;         // `graph_count` consecutive steps, replayed
-    int graph_count = 0;
+    std::vector<std::pair<int32_t, cudaGraphExec_t>> graphs;   // count consecutive steps, replayed
+    // host-frame runs: a ring of two chunks of staged frames, filled on a copy stream
+    uint8_t *d_ring = nullptr;
+    int64_t ring_pitch = 0;
+    int32_t ring_chunk = 0;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ring_copied[2] = {nullptr, nullptr}, ring_free[2] = {nullptr, nullptr};
     int64_t frame_buf_pitch = 0;
 
     pf_status fail(pf_status s) {
@@ -116,10 +121,19 @@ struct pf_batch {
 
 static void engine_free(Engine &e) {
     cudaStreamSynchronize(e.stream);
-    if (e.graph) cudaGraphExecDestroy(e.graph);
+    for (auto &g : e.graphs) cudaGraphExecDestroy(g.second);
+    e.graphs.clear();
     if (e.capture_stream) cudaStreamDestroy(e.capture_stream);
     if (e.frames_copied) cudaEventDestroy(e.frames_copied);
-    e.graph = nullptr; e.capture_stream = nullptr; e.frames_copied = nullptr; e.graph_count = 0;
+    e.capture_stream = nullptr; e.frames_copied = nullptr;
+    if (e.copy_stream) { cudaStreamSynchronize(e.copy_stream); cudaStreamDestroy(e.copy_stream); }
+    for (int k = 0; k < 2; ++k) {
+        if (e.ring_copied[k]) cudaEventDestroy(e.ring_copied[k]);
+        if (e.ring_free[k]) cudaEventDestroy(e.ring_free[k]);
+        e.ring_copied[k] = e.ring_free[k] = nullptr;
+    }
+    cudaFree(e.d_ring);
+    e.d_ring = nullptr; e.copy_stream = nullptr; e.ring_chunk = 0;
     cudaFree(e.d_trk);
     cudaFree(e.d_frames);
     cudaFree(e.d_tile_trk);
@@ -306,8 +320,14 @@ static pf_status engine_wait_staging(Engine &e) {
 // one CUDA graph of identical kernel nodes, captured once per count and replayed.
 static pf_status engine_run_resident(Engine &e, int32_t count) {
     if (count <= 0) return PF_OK;
-    if (!e.graph || e.graph_count != count) {
-        if (e.graph) { cudaGraphExecDestroy(e.graph); e.graph = nullptr; e.graph_count = 0; }
+    cudaGraphExec_t exec = nullptr;
+    for (auto &g : e.graphs)
+        if (g.first == count) exec = g.second;
+    if (!exec) {
+        if (e.graphs.size() >= 4) {   // keep a few counts (a run's chunk and its tail)
+            cudaGraphExecDestroy(e.graphs.front().second);
+            e.graphs.erase(e.graphs.begin());
+        }
         StepLaunch L;
         L.trk = e.d_trk;
         L.states = e.h_trk[0].state;
@@ -329,12 +349,82 @@ static pf_status engine_run_resident(Engine &e, int32_t count) {
         const cudaError_t end = cudaStreamEndCapture(e.capture_stream, &g);
         if (err == cudaSuccess) err = end;
         if (err == cudaSuccess && rc != 0) err = cudaErrorLaunchFailure;
-        if (err == cudaSuccess) err = cudaGraphInstantiate(&e.graph, g, 0);
+        if (err == cudaSuccess) err = cudaGraphInstantiate(&exec, g, 0);
         if (g) cudaGraphDestroy(g);
-        if (err != cudaSuccess) { cudaGetLastError(); e.graph = nullptr; return e.fail(PF_ERR_CUDA); }
-        e.graph_count = count;
+        if (err != cudaSuccess) { cudaGetLastError(); return e.fail(PF_ERR_CUDA); }
+        e.graphs.emplace_back(count, exec);
     }
-    if (cudaGraphLaunch(e.graph, e.stream) != cudaSuccess) { cudaGetLastError(); return e.fail(PF_ERR_CUDA); }
+    if (cudaGraphLaunch(exec, e.stream) != cudaSuccess) { cudaGetLastError(); return e.fail(PF_ERR_CUDA); }
+    return PF_OK;
+}
+
+// Host frames, `count` of them `frame_stride` bytes apart: copied chunk by chunk into a
+// ring of two chunks on the device by a copy stream, each chunk stepped by a replayed
+// graph on the handle's stream as soon as its copy lands, so copies overlap the steps
+// of the previous chunk.  The frame table points the kernel at the ring
+// (frame t at ring + (t % 2C) * frame bytes).
+static pf_status engine_run_host_frames(Engine &e, const uint8_t *frames, int64_t pitch_bytes,
+                                        int64_t frame_stride, int32_t count) {
+    const pf_config &c = e.cfg[0];
+    constexpr int32_t kChunk = 8;
+    cudaError_t err = cudaSuccess;
+    if (!e.d_ring) {
+        e.ring_pitch = (c.width + 15) & ~int64_t(15);
+        err = cudaMalloc(reinterpret_cast<void **>(&e.d_ring), static_cast<size_t>(e.ring_pitch) * c.height * 2 * kChunk);
+        if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&e.copy_stream, cudaStreamNonBlocking);
+        for (int k = 0; k < 2 && err == cudaSuccess; ++k) {
+            err = cudaEventCreateWithFlags(&e.ring_copied[k], cudaEventDisableTiming);
+            if (err == cudaSuccess) err = cudaEventCreateWithFlags(&e.ring_free[k], cudaEventDisableTiming);
+        }
+        if (err != cudaSuccess) {
+            cudaGetLastError();
+            return err == cudaErrorMemoryAllocation ? PF_ERR_OOM : e.fail(PF_ERR_CUDA);
+        }
+        e.ring_chunk = kChunk;
+    }
+    const int64_t fbytes = e.ring_pitch * c.height;
+    const int64_t t0 = e.done_frames[0];
+    pf_status s = engine_wait_staging(e);
+    if (s != PF_OK) return s;
+    FrameRef &fr = e.h_frames_pinned[0];
+    fr.base = e.d_ring;
+    fr.pitch = e.ring_pitch;
+    fr.stride = fbytes;
+    fr.active = 1;
+    fr.ring = 2 * kChunk;
+    s = engine_upload_frames(e);
+    if (s != PF_OK) return s;
+    // the copy stream must not overwrite frames earlier steps on the handle's stream still read
+    err = cudaEventRecord(e.ring_free[0], e.stream);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(e.copy_stream, e.ring_free[0], 0);
+    for (int32_t done = 0; done < count && err == cudaSuccess;) {
+        const int32_t n = std::min(kChunk, count - done);
+        // a chunk of up to kChunk frames may span both halves of the ring (its first frame
+        // in half kc, its last in half kl); before overwriting them the copies wait for the
+        // steps that last read those halves
+        const int kc = static_cast<int>(((t0 + done) / kChunk) % 2);
+        const int kl = static_cast<int>(((t0 + done + n - 1) / kChunk) % 2);
+        if (done > 0) {
+            err = cudaStreamWaitEvent(e.copy_stream, e.ring_free[kc], 0);
+            if (err == cudaSuccess && kl != kc) err = cudaStreamWaitEvent(e.copy_stream, e.ring_free[kl], 0);
+        }
+        for (int32_t i = 0; i < n && err == cudaSuccess; ++i) {
+            const int64_t t = t0 + done + i;
+            err = cudaMemcpy2DAsync(e.d_ring + (t % (2 * kChunk)) * fbytes, e.ring_pitch,
+                                    frames + static_cast<int64_t>(done + i) * frame_stride, pitch_bytes, c.width,
+                                    c.height, cudaMemcpyHostToDevice, e.copy_stream);
+        }
+        if (err == cudaSuccess) err = cudaEventRecord(e.ring_copied[kc], e.copy_stream);
+        if (err == cudaSuccess) err = cudaStreamWaitEvent(e.stream, e.ring_copied[kc], 0);
+        if (err != cudaSuccess) break;
+        s = engine_run_resident(e, n);
+        if (s != PF_OK) return s;
+        err = cudaEventRecord(e.ring_free[kl], e.stream);
+        if (err == cudaSuccess && kl != kc) err = cudaEventRecord(e.ring_free[kc], e.stream);
+        done += n;
+        e.done_frames[0] += n;
+    }
+    if (err != cudaSuccess) { cudaGetLastError(); return e.fail(PF_ERR_CUDA); }
     return PF_OK;
 }
 
@@ -416,11 +506,9 @@ pf_status pf_run_frames(pf_filter *f, const uint8_t *frames, int64_t pitch_bytes
     if (e.sticky != PF_OK) return PF_ERR_STATE;
     if (pitch_bytes < e.cfg[0].width) return PF_ERR_ARG;
     if (!frames_on_device) {
-        for (int32_t i = 0; i < count; ++i) {
-            pf_status s = pf_step_frame(f, frames + static_cast<int64_t>(i) * frame_stride, pitch_bytes, 0);
-            if (s != PF_OK) return s;
-        }
-        return PF_OK;
+        if (count == 0) return PF_OK;
+        if (frame_stride < pitch_bytes * e.cfg[0].height) return PF_ERR_ARG;
+        return engine_run_host_frames(e, frames, pitch_bytes, frame_stride, count);
     }
     if (count == 0) return PF_OK;
     // Device frames: the kernel finds frame t at base + t * stride, with base chosen so
@@ -433,6 +521,7 @@ pf_status pf_run_frames(pf_filter *f, const uint8_t *frames, int64_t pitch_bytes
     fr.pitch = pitch_bytes;
     fr.stride = frame_stride;
     fr.active = 1;
+    fr.ring = 0;
     s = engine_upload_frames(e);
     if (s == PF_OK) s = engine_run_resident(e, count);
     if (s != PF_OK) return s;
@@ -695,6 +784,7 @@ static pf_status engine_set_videos(Engine &e, const uint8_t *const *videos, cons
         fr.pitch = pitches[i];
         fr.stride = frame_strides[i];
         fr.active = 1;
+        fr.ring = 0;
     }
     return engine_upload_frames(e);
 }

@@ -650,7 +650,11 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
     FrameView fv;
     fv.W = T.W; fv.H = T.H; fv.r = T.r;
     if (Lp.frame_override) { fv.p = Lp.frame_override; fv.pitch = Lp.pitch_override; }
-    else { fv.p = sm.fr.base + (sm.fr.stride ? t * sm.fr.stride : 0); fv.pitch = sm.fr.pitch; }
+    else {
+        const int64_t ft = sm.fr.ring ? t % sm.fr.ring : t;   // a ring of staged frames, or a resident video
+        fv.p = sm.fr.base + (sm.fr.stride ? ft * sm.fr.stride : 0);
+        fv.pitch = sm.fr.pitch;
+    }
     const int r = fv.r;
     for (int i = tid; i <= 2 * r; i += kThreads) {
         const int dy = i - r;

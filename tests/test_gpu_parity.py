@@ -97,6 +97,29 @@ def test_host_and_device_frames_agree(pf):
     assert np.array_equal(e1, e2)
 
 
+def test_host_frame_runs_in_uneven_chunks_equal_device_runs(pf):
+    """Host-frame runs stage frames through a ring of 16 on a copy stream, in chunks of 8
+    that need not start on a ring boundary: runs of odd lengths, mixed with device runs
+    and single steps, give the device run's bits."""
+    torch = _torch()
+    v = synth.make_video(128, 96, 40, 4, noise=5.0, seed=17, v=(1.0, 1.5))
+    fr = torch.from_numpy(v.frames).cuda()
+    pin = torch.from_numpy(v.frames).pin_memory()
+    for prec in ("f32", "f16"):
+        a = pf.Filter(v.W, v.H, 6000, 4, prec, init=tuple(v.centres[0]), seed=21)
+        a.run(fr)
+        b = pf.Filter(v.W, v.H, 6000, 4, prec, init=tuple(v.centres[0]), seed=21)
+        b.run(v.frames[:5])            # pageable, 5 frames
+        b.run(pin[5:18])               # pinned, 13 frames (a chunk across the ring halves)
+        b.step(fr[18])
+        b.run(fr[19:22])
+        b.run(v.frames[22:31])
+        b.run(pin[31:40])
+        assert np.array_equal(a.estimates(0, 40), b.estimates(0, 40)), prec
+        a.close()
+        b.close()
+
+
 def test_deterministic_bits(pf):
     v = synth.make_video(128, 128, 8, 5, noise=5.0, seed=3)
     for prec in ("ref64", "f32", "f16"):
