@@ -257,6 +257,48 @@ def test_dominant_particle(pf):
     assert np.all(f.debug(0) == 3777)
 
 
+@pytest.mark.parametrize("N", [1 << 14, 3 * TILE + 5])
+def test_equal_weights_resample_to_identity(pf, N):
+    """Equal likelihoods (a constant frame after a constant one): in REF64 every particle
+    keeps exactly one offspring, itself (u_j = (j + u0)/N falls in ((j-1)/N, j/N]); a
+    non-power-of-two N still gives every particle one offspring up to rounding at j/N."""
+    f = pf.Filter(96, 96, N, 3, "ref64", init=(48.0, 48.0), seed=4, flags=pf.PF_FLAG_DEBUG_ARRAYS)
+    flat = np.full((96, 96), 100, np.uint8)
+    f.step(flat)
+    f.step(flat)
+    anc = f.debug(0).astype(np.int64)
+    C = f.debug(1)
+    assert np.all(np.diff(anc) >= 0) and anc[0] == 0 and anc[-1] == N - 1
+    if N & (N - 1) == 0:
+        assert np.array_equal(anc, np.arange(N))
+        assert np.array_equal(C, (np.arange(N) + 1.0) / N)
+    else:
+        cnt = np.bincount(anc, minlength=N)
+        assert cnt.max() <= 2 and np.abs(np.cumsum(cnt) - np.arange(1, N + 1)).max() <= 1
+    f.close()
+
+
+@pytest.mark.parametrize("prec", ["ref64", "f32", "f16"])
+def test_offspring_counts_are_floor_or_ceil_of_n_w(pf, prec):
+    """The systematic-resampling invariant on the GPU's own step: particle k receives
+    floor(N w_k) or ceil(N w_k) offspring, w_k = C_k - C_(k-1) of the CDF the step used."""
+    v = synth.make_video(160, 120, 4, 4, noise=15.0, seed=33)
+    N = 5 * TILE + 123
+    torch = _torch()
+    fr = torch.from_numpy(v.frames).cuda()
+    f = pf.Filter(v.W, v.H, N, 4, prec, init=tuple(v.centres[0]), seed=8, sigma=(3.0, 3.0),
+                  flags=pf.PF_FLAG_DEBUG_ARRAYS)
+    f.run(fr)
+    anc = f.debug(0).astype(np.int64)
+    C = f.debug(1).astype(np.float64)
+    w = np.diff(np.concatenate([[0.0], C]))
+    cnt = np.bincount(anc, minlength=N)
+    slack = 1e-9 if prec == "ref64" else N * 2.0 ** -21   # FP32 CDF and strata points carry ~2^-24
+    assert cnt.sum() == N
+    assert np.all(cnt >= np.floor(N * w - slack)) and np.all(cnt <= np.ceil(N * w + slack))
+    f.close()
+
+
 def test_checkpoint_resume_bit_identical(pf):
     v = synth.make_video(128, 128, 10, 5, noise=5.0, seed=15)
     torch = _torch()
