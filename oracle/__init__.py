@@ -67,9 +67,12 @@ def _load():
             "orc_cdf": (None, [_I64, _P, _D, _P]),
             "orc_resample_f64": (None, [_I64, _P, _D, _P]),
             "orc_resample_f32": (None, [_I64, _P, ctypes.c_float, _P]),
+            "orc_stratified_offsets": (None, [_U64, _U32, _U32, _I64, _P]),
+            "orc_resample_strat_f64": (None, [_I64, _P, _P, _P]),
+            "orc_resample_strat_f32": (None, [_I64, _P, _P, _P]),
             "orc_run": (ctypes.c_int, [_P, _I64, ctypes.c_int, ctypes.c_int, ctypes.c_int, _I64,
                                        _I64, ctypes.c_int, _D, _D, _D, _D, _D, _D, _D, _D,
-                                       _U64, _U32, ctypes.c_int, _P, _P, _P]),
+                                       _U64, _U32, ctypes.c_int, ctypes.c_int, _P, _P, _P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -216,6 +219,36 @@ def resample(C, u0, precision: str = "f64"):
     return a
 
 
+def stratified_offsets(seed: int, t: int, N: int, tracker: int = 0) -> np.ndarray:
+    """Offsets v_j (j < N) of frame t's strata for stratified resampling."""
+    v = np.empty(int(N), np.float64)
+    _load().orc_stratified_offsets(seed & 0xFFFFFFFFFFFFFFFF, t, tracker, int(N), _ptr(v))
+    return v
+
+
+def resample_stratified(C, v, precision: str = "f64"):
+    """Stratified-resampling ancestors of CDF ``C`` with offsets ``v`` (u_j = (j + v_j)/N),
+    the decision taken in FP64 or FP32 (C and v rounded to FP32)."""
+    if precision == "f64":
+        Cc = np.ascontiguousarray(C, np.float64)
+        vv = np.ascontiguousarray(v, np.float64)
+        fn = _load().orc_resample_strat_f64
+    elif precision == "f32":
+        Cc = np.ascontiguousarray(C, np.float32)
+        vv = np.ascontiguousarray(v, np.float32)
+        fn = _load().orc_resample_strat_f32
+    else:
+        raise ValueError(precision)
+    if vv.size != Cc.size:
+        raise ValueError("one offset per stratum")
+    a = np.empty(Cc.size, np.int64)
+    fn(Cc.size, _ptr(Cc), _ptr(vv), _ptr(a))
+    return a
+
+
+RESAMPLERS = {"systematic": 0, "stratified": 1}
+
+
 # --------------------------------------------------------------------------- whole tracker
 @dataclass
 class FrameRecord:
@@ -233,7 +266,7 @@ class FrameRecord:
 
 
 def track_steps(frames: np.ndarray, N: int, r: int, *, init, sigma=(1.0, 1.0), drift=(0.0, 0.0),
-                seed: int = 1, tracker: int = 0, bg=100.0, fg=228.0, nthreads=1):
+                seed: int = 1, tracker: int = 0, bg=100.0, fg=228.0, nthreads=1, resampler="systematic"):
     """Run the tracker phase by phase (Fig. 1), yielding a FrameRecord per frame.
     Same arithmetic as :func:`track`, with every intermediate array exposed."""
     anc = None
@@ -246,13 +279,18 @@ def track_steps(frames: np.ndarray, N: int, r: int, *, init, sigma=(1.0, 1.0), d
         S, xh, yh = normalise(e, x, y)
         C = cdf(e, S)
         u0 = resample_u0(seed, t, tracker)
-        a = resample(C, u0, "f64")
+        if resampler == "stratified":
+            a = resample_stratified(C, stratified_offsets(seed, t, N, tracker), "f64")
+        elif resampler == "systematic":
+            a = resample(C, u0, "f64")
+        else:
+            raise ValueError(resampler)
         yield FrameRecord(x=x, y=y, L=L, M=M, S=S, est=(xh, yh), C=C, u0=u0, anc=a, anc_in=anc)
         xa, ya, anc = x, y, a
 
 
 def track(frames: np.ndarray, N: int, r: int, *, init, sigma=(1.0, 1.0), drift=(0.0, 0.0),
-          seed: int = 1, tracker: int = 0, bg=100.0, fg=228.0, nthreads=1):
+          seed: int = 1, tracker: int = 0, bg=100.0, fg=228.0, nthreads=1, resampler="systematic"):
     """Whole FP64 track in C.  Returns (est (T,2), M (T,), S (T,))."""
     f = np.ascontiguousarray(frames, dtype=np.uint8)
     T, H, W = f.shape
@@ -261,7 +299,7 @@ def track(frames: np.ndarray, N: int, r: int, *, init, sigma=(1.0, 1.0), drift=(
     S = np.empty(T, np.float64)
     rc = _load().orc_run(_ptr(f), H * W, T, W, H, W, N, r, bg, fg, init[0], init[1],
                          sigma[0], sigma[1], drift[0], drift[1], seed & 0xFFFFFFFFFFFFFFFF,
-                         tracker, nthreads, _ptr(est), _ptr(M), _ptr(S))
+                         tracker, nthreads, RESAMPLERS[resampler], _ptr(est), _ptr(M), _ptr(S))
     if rc != 0:
         raise MemoryError("oracle could not allocate its arrays")
     return est, M, S

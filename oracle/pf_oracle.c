@@ -14,6 +14,7 @@
  *   normalising (sum + estimate)    orc_normalise
  *   normalising (CDF, inclusive prefix sum)  orc_cdf
  *   systematic resampling (Sec. 3)  orc_resample_f64 / orc_resample_f32
+ *   stratified resampling (Sec. 2)  orc_stratified_offsets, orc_resample_strat_f64 / _f32
  * Where the paper is silent the readings are (numbered as in the design notes):
  *   C1  Eq. 3 is summed over the template pixels and divided by 50*|D|.
  *   C2  template D = integer offsets with dx^2+dy^2 <= r^2 (centre included).
@@ -25,6 +26,7 @@
  *   C7  estimate = weighted mean of the propagated particles, before resampling.
  *   C8  systematic: one u0 per frame, u_j = (j + u0) * (1/N) in the CDF's precision,
  *       a_j = min{k : C_k >= u_j}, N-1 if there is none.
+ *       Stratified (alternative scheme): u_j = (j + v_j) * (1/N), v_j independent.
  *   C11 draws: Philox4x32-10 words -> 23-bit uniforms -> Box-Muller in FP64.
  *   C12 at t = 0 every ancestor sits at (init_x, init_y).
  * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), written here
@@ -385,6 +387,52 @@ void orc_resample_f32(int64_t N, const float *C, float u0, int64_t *a)
     }
 }
 
+/* Stratified resampling (Sec. 2 lists it with multinomial and systematic resampling as
+ * the standard schemes): the same N strata, each sampled at its own offset, u_j =
+ * (j + v_j) * (1/N).  Offset v_j of frame t is the uniform of word (j mod 4) of the
+ * Philox draw (j / 4, t, tag 1, tracker), so v_0 is the systematic u0 of that frame. */
+void orc_stratified_offsets(uint64_t seed, uint32_t t, uint32_t tracker, int64_t N, double *v)
+{
+    for (int64_t j = 0; j < N; ++j) {
+        uint32_t w[4];
+        orc_philox_draw(seed, (uint32_t)(j / 4), t, 1u, tracker, w);
+        v[j] = orc_uniform(w[j % 4]);
+    }
+}
+
+/* a_j = min{k : C_k >= u_j} (N - 1 if there is none), by bisection for every j, with
+ * u_j = (j + v_j) * (1/N) in FP64. */
+void orc_resample_strat_f64(int64_t N, const double *C, const double *v, int64_t *a)
+{
+    double inv_n = 1.0 / (double)N;
+    for (int64_t j = 0; j < N; ++j) {
+        double u = ((double)j + v[j]) * inv_n;
+        int64_t lo = 0, hi = N;          /* first index in [lo, hi] with C >= u; N: none */
+        while (lo < hi) {
+            int64_t mid = lo + (hi - lo) / 2;
+            if (C[mid] >= u) hi = mid; else lo = mid + 1;
+        }
+        a[j] = lo < N ? lo : N - 1;
+    }
+}
+
+/* The same decision taken in FP32, for a CDF held in FP32. */
+void orc_resample_strat_f32(int64_t N, const float *C, const float *v, int64_t *a)
+{
+    volatile float inv_n = 1.0f / (float)N;
+    for (int64_t j = 0; j < N; ++j) {
+        volatile float jf = (float)j;
+        volatile float s = jf + v[j];
+        volatile float u = s * inv_n;
+        int64_t lo = 0, hi = N;
+        while (lo < hi) {
+            int64_t mid = lo + (hi - lo) / 2;
+            if (C[mid] >= u) hi = mid; else lo = mid + 1;
+        }
+        a[j] = lo < N ? lo : N - 1;
+    }
+}
+
 /* ------------------------------------------------------------------------- */
 /* The whole tracker (Fig. 1): for t = 0..T-1 propagate, weigh, normalise,      */
 /* estimate, resample.  Outputs per frame: estimate (x, y), M and S.             */
@@ -394,7 +442,7 @@ void orc_resample_f32(int64_t N, const float *C, float u0, int64_t *a)
 int orc_run(const uint8_t *frames, int64_t frame_stride, int T, int W, int H, int64_t pitch,
             int64_t N, int r, double bg, double fg, double init_x, double init_y,
             double sigma_x, double sigma_y, double drift_x, double drift_y,
-            uint64_t seed, uint32_t tracker, int nthreads,
+            uint64_t seed, uint32_t tracker, int nthreads, int resampler,
             double *est, double *M_out, double *S_out)
 {
     double *xa = malloc((size_t)N * sizeof(double));
@@ -405,7 +453,8 @@ int orc_run(const uint8_t *frames, int64_t frame_stride, int T, int W, int H, in
     double *e = malloc((size_t)N * sizeof(double));
     double *C = malloc((size_t)N * sizeof(double));
     int64_t *a = malloc((size_t)N * sizeof(int64_t));
-    int ok = xa && ya && x && y && L && e && C && a;
+    double *v = resampler ? malloc((size_t)N * sizeof(double)) : NULL;
+    int ok = xa && ya && x && y && L && e && C && a && (v || !resampler);
     if (ok) {
         for (int t = 0; t < T; ++t) {
             const uint8_t *frame = frames + (int64_t)t * frame_stride;
@@ -419,12 +468,17 @@ int orc_run(const uint8_t *frames, int64_t frame_stride, int T, int W, int H, in
             if (M_out) M_out[t] = M;
             if (S_out) S_out[t] = S;
             orc_cdf(N, e, S, C);
-            orc_resample_f64(N, C, orc_resample_u0(seed, (uint32_t)t, tracker), a);
+            if (resampler) {
+                orc_stratified_offsets(seed, (uint32_t)t, tracker, N, v);
+                orc_resample_strat_f64(N, C, v, a);
+            } else {
+                orc_resample_f64(N, C, orc_resample_u0(seed, (uint32_t)t, tracker), a);
+            }
             double *sw;
             sw = xa; xa = x; x = sw;
             sw = ya; ya = y; y = sw;
         }
     }
-    free(xa); free(ya); free(x); free(y); free(L); free(e); free(C); free(a);
+    free(xa); free(ya); free(x); free(y); free(L); free(e); free(C); free(a); free(v);
     return ok ? 0 : -1;
 }

@@ -338,6 +338,89 @@ def test_resample_dominant_and_clamp():
         assert np.array_equal(oracle.resample(C3, 0.0, prec), [0, 0, 1, 2])
 
 
+# ----------------------------------------------------------------------------- stratified resampling
+def test_stratified_offsets_are_the_tag1_words():
+    """v_j = uniform word (j mod 4) of Philox(j / 4, t, 1, tracker); v_0 is the systematic u0."""
+    seed, t, trk, n = 0x5EED, 7, 3, 11
+    v = oracle.stratified_offsets(seed, t, n, trk)
+    ctrs = np.array([[j // 4, t, 1, trk] for j in range(n)], np.uint32)
+    words = oracle.philox(ctrs, seed)
+    want = oracle.uniform(np.array([words[j, j % 4] for j in range(n)], np.uint32))
+    assert np.array_equal(v, want)
+    assert v[0] == oracle.resample_u0(seed, t, trk)
+    assert len(set(v.tolist())) == n
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_stratified_with_equal_offsets_is_systematic(prec):
+    """With every v_j = u0 the stratified points are the systematic ones."""
+    rng = np.random.default_rng(12)
+    for n in (1, 2, 5, 100, 4097):
+        e = rng.exponential(size=n) ** 2
+        S, _, _ = oracle.normalise(e, np.zeros(n), np.zeros(n))
+        C = oracle.cdf(e, S)
+        for u0 in (0.125, 0.5, 0.875):
+            assert np.array_equal(oracle.resample_stratified(C, np.full(n, u0), prec),
+                                  oracle.resample(C, u0, prec))
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_stratified_uniform_weights_identity(prec):
+    """Equal weights (N a power of two, exact CDF): u_j lies in stratum j's own CDF step."""
+    rng = np.random.default_rng(13)
+    for n in (1, 2, 8, 1024, 1 << 16):
+        C = (np.arange(n, dtype=np.float64) + 1) / n
+        v = rng.uniform(0.25, 0.75, n)     # (float)j + v_j stays inside (j, j + 1) in FP32 too
+        assert np.array_equal(oracle.resample_stratified(C, v, prec), np.arange(n))
+
+
+def test_stratified_counts_within_two_strata():
+    """Each stratum holds one point, so particle k (CDF step of width w_k) receives between
+    N w_k - 2 and N w_k + 2 offspring (exclusive); the ancestors are ordered."""
+    rng = np.random.default_rng(14)
+    for n in (1, 3, 7, 100, 1000, 4097):
+        for trial in range(4):
+            e = rng.exponential(size=n) ** 3
+            S, _, _ = oracle.normalise(e, np.zeros(n), np.zeros(n))
+            C = oracle.cdf(e, S)
+            v = oracle.uniform(rng.integers(0, 2 ** 32, size=n, dtype=np.uint64).astype(np.uint32))
+            a = oracle.resample_stratified(C, v, "f64")
+            assert np.all(np.diff(a) >= 0) and a.min() >= 0 and a.max() < n
+            cnt = _counts(a, n)
+            w = np.diff(np.concatenate([[0.0], C]))
+            assert cnt.sum() == n
+            assert np.all(np.abs(cnt - n * w) < 2.0)
+
+
+def test_stratified_monte_carlo_expectation():
+    """N <= 8: over independent offsets the mean offspring count of particle k is N w_k
+    (stratified resampling is unbiased); 20000 draws, 6 standard errors."""
+    rng = np.random.default_rng(15)
+    trials = 20000
+    for n in (2, 3, 5, 8):
+        e = rng.uniform(0.01, 1.0, n)
+        S, _, _ = oracle.normalise(e, np.zeros(n), np.zeros(n))
+        C = oracle.cdf(e, S)
+        w = np.diff(np.concatenate([[0.0], C]))
+        tot = np.zeros(n)
+        sq = np.zeros(n)
+        for _ in range(trials):
+            c = _counts(oracle.resample_stratified(C, rng.uniform(0.0, 1.0, n), "f64"), n)
+            tot += c
+            sq += c * c
+        mean = tot / trials
+        se = np.sqrt(np.maximum(sq / trials - mean ** 2, 1e-12) / trials)
+        assert np.all(np.abs(mean - n * w) <= 6 * se + 1e-12)
+
+
+def test_stratified_dominant_and_clamp():
+    C = np.array([0.0, 0.0, 1.0, 1.0])
+    assert np.array_equal(oracle.resample_stratified(C, [0.1, 0.9, 0.5, 0.3], "f64"), [2, 2, 2, 2])
+    C2 = np.array([0.2, 0.5, 0.9])     # a point above every entry: clamp to N-1
+    assert np.array_equal(oracle.resample_stratified(C2, [0.1, 0.2, 0.95], "f64"), [0, 1, 2])
+    assert np.array_equal(oracle.resample_stratified(C2, [0.9, 0.6, 0.7], "f64"), [1, 2, 2])
+
+
 # ----------------------------------------------------------------------------- propagation, Eq. 1-2
 def test_propagation_moments_paper_motion():
     """Eq. 1-2: x ~ N(1 + x_anc, 5^2), y ~ N(2 + y_anc, 2^2)."""
@@ -372,6 +455,15 @@ def test_track_recovers_ground_truth_config1():
     err = np.sqrt(np.sum((est - v.centres) ** 2, axis=1))
     assert np.sqrt(np.mean(err ** 2)) < 1.0 and err.max() < 1.5
     assert np.all(S >= 1.0) and np.all(M <= 11648 / 25)
+
+
+def test_track_stratified_recovers_ground_truth_config1():
+    v = synth.make_video(128, 128, 10, 5, noise=5.0, seed=1)
+    est, _, _ = oracle.track(v.frames, 1000, 5, init=tuple(v.centres[0]), seed=1, resampler="stratified")
+    err = np.sqrt(np.sum((est - v.centres) ** 2, axis=1))
+    assert np.sqrt(np.mean(err ** 2)) < 1.0 and err.max() < 1.5
+    recs = list(oracle.track_steps(v.frames, 1000, 5, init=tuple(v.centres[0]), seed=1, resampler="stratified"))
+    assert np.array_equal(np.array([r.est for r in recs]), est)
 
 
 def test_track_noiseless_recovers_integer_centres():
