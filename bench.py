@@ -361,6 +361,7 @@ def run_ours(args):
     if not args.no_sweep and ws == 1:
         line.setdefault("systems", {})["sweep"] = _sweep(dev, stream)
         line["systems"]["paper_workload"] = _paper_workload(dev, stream)
+        line["systems"]["resamplers"] = _resamplers(dev, stream)
     if not args.no_serve and ws == 1:
         cap = min(results[p]["value"] for p in results if p in ("f16", "f32")) if any(
             p in results for p in ("f16", "f32")) else head["value"]
@@ -582,6 +583,42 @@ def _paper_workload(dev, stream):
         row["speedup_f16_over_ref64"] = row["ref64"]["us_per_frame"] / row["f16"]["us_per_frame"]
         out[str(N)] = row
     return {"workload": "512^2, 100 frames, disk r = 5 moving (+1, +2), drift (1, 2), sigma (5, 2)", "by_particles": out}
+
+
+def _resamplers(dev, stream):
+    """Systematic (the paper's scheme, Sec. 3) against stratified resampling (one offset per
+    stratum, Sec. 2) on the headline workload: us per frame and the track's RMSE against
+    the ground truth, per precision."""
+    import torch
+    import paper_2308_00763_gb300 as pf
+    from paper_2308_00763_gb300 import synth
+    v = synth.make_video(W_, H_, T_, R_, noise=NOISE_, seed=SEED_)
+    fr = torch.from_numpy(v.frames).to(dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    out = {}
+    for prec in ("ref64", "f32", "f16"):
+        row = {}
+        for rs in ("systematic", "stratified"):
+            f = pf.Filter(W_, H_, N_, R_, prec, init=tuple(v.centres[0]), seed=SEED_, stream=stream, resampler=rs)
+            f.run(fr[:4])
+            best = None
+            for _ in range(2):
+                flush.zero_()
+                f.reset()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                f.run(fr)
+                b.record(stream)
+                torch.cuda.synchronize(dev)
+                us = 1e3 * a.elapsed_time(b) / T_
+                best = us if best is None else min(best, us)
+            row[rs] = {"us_per_frame": best, "value": N_ / (best * 1e-6),
+                       "rmse_px_vs_truth": _rmse(f.estimates(0, T_), v.centres)}
+            f.close()
+        row["stratified_over_systematic_time"] = row["stratified"]["us_per_frame"] / row["systematic"]["us_per_frame"]
+        out[prec] = row
+    return {"workload": WORKLOAD, "unit": METRIC, "by_precision": out}
 
 
 def main():

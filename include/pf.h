@@ -55,6 +55,21 @@ typedef enum {
     PF_BF16 = 3    /* as PF_F16 in bfloat16, with the likelihood accumulated in FP32 */
 } pf_precision;
 
+/* Resampling scheme (pf_config.resampler).  Both cut the unit interval into N strata
+ * [j/N, (j+1)/N), draw one point u_j in each and give offspring j the first particle whose
+ * normalised CDF value reaches u_j (Sec. 3, "Resampling"; Sec. 2 names the standard
+ * multinomial, stratified and systematic schemes).  The points are evaluated in the CDF's
+ * precision exactly as ((A)j + v_j) * (A)(1/N), A = double (PF_REF64) or float.
+ *   SYSTEMATIC: v_j = u0 for every j, u0 = uniform word 0 of Philox(0, t, 1, tracker_id)
+ *               (the paper's scheme; the default).
+ *   STRATIFIED: v_j independent, v_j = uniform word (j mod 4) of Philox(j / 4, t, 1,
+ *               tracker_id), so v_0 = u0.  With a FP32 CDF it needs N <= 2^24 (beyond,
+ *               (float)j rounds and the points would no longer be ordered). */
+typedef enum {
+    PF_RESAMPLE_SYSTEMATIC = 0,
+    PF_RESAMPLE_STRATIFIED = 1
+} pf_resampler;
+
 /* pf_config.flags */
 #define PF_FLAG_DEBUG_ARRAYS 0x1u  /* keep the last step's CDF and ancestor indices (pf_get_debug) */
 #define PF_FLAG_ACCUM32      0x2u  /* PF_F16: accumulate the likelihood in FP32 instead of half */
@@ -73,7 +88,7 @@ typedef struct {
     uint32_t tracker_id;       /* Philox counter word 3: separates trackers sharing a seed */
     uint32_t flags;            /* PF_FLAG_* */
     int32_t est_capacity;      /* frames of estimates kept on the device; 0 = 4096 */
-    int32_t reserved;          /* must be 0 */
+    int32_t resampler;         /* pf_resampler (0 = systematic) */
 } pf_config;
 
 typedef struct pf_filter pf_filter;

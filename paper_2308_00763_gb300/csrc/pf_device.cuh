@@ -87,28 +87,44 @@ template <> __device__ __forceinline__ double neg_inf<double>() { return -__long
 template <> __device__ __forceinline__ float neg_inf<float>() { return -__int_as_float(0x7f800000); }
 
 // ----------------------------------------------------------------------------------
-// Systematic resampling (Sec. 3, "Resampling"): stratum j is sampled at
-// u_j = (j + u0) * (1/N), evaluated in the CDF's precision A.  count_le(c) is the number
-// of strata with u_j <= c; particle k receives strata [count_le(C_{k-1}), count_le(C_k)),
+// Resampling points (Sec. 3, "Resampling"): stratum j is sampled at u_j = (j + v_j) * (1/N),
+// evaluated in the CDF's precision A; systematic resampling takes v_j = u0 for every j,
+// stratified resampling an independent v_j per stratum.  count_le(c) is the number of
+// strata with u_j <= c; particle k receives strata [count_le(C_{k-1}), count_le(C_k)),
 // which is exactly a_j = min{k : C_k >= u_j} for a non-decreasing C.  u_j is
-// non-decreasing in j (both roundings are monotone), so the count is found from an
-// arithmetic estimate and a short galloping search.
+// non-decreasing in j (both roundings are monotone, and (A)j + v_j stays within
+// [j, j + 1] while (A)j is exact), so the count is found from an arithmetic estimate and a
+// short galloping search.
 // ----------------------------------------------------------------------------------
 template <typename A>
 __device__ __forceinline__ A stratum_point32(int j, A u0, A inv_n) {
     return mul_rn(add_rn(static_cast<A>(j), u0), inv_n);
 }
 
-// Strata of one tracker's frame: n = N, u0, 1/N, and the first / last stratum points.
-template <typename A>
+// Strata of one tracker's frame: n = N, 1/N, the offsets and the first / last points.
+// kStrat: stratified, v_j = uniform word j % 4 of Philox(j / 4, tf, 1, trk), with
+// (key_lo, key_hi, tf, trk) read from `keys` (shared memory); else systematic, v_j = u0.
+template <typename A, bool kStrat>
 struct Strata {
     A u0, inv_n, first, last, nf;
     int n;
-    __device__ __forceinline__ void init(int n_, A u0_, A inv_n_) {
-        n = n_; u0 = u0_; inv_n = inv_n_;
-        first = stratum_point32<A>(0, u0, inv_n);
-        last = stratum_point32<A>(n - 1, u0, inv_n);
+    const uint32_t *keys;
+    __device__ __forceinline__ void init(int n_, A u0_, A inv_n_, const uint32_t *keys_ = nullptr) {
+        n = n_; u0 = u0_; inv_n = inv_n_; keys = keys_;
+        first = point(0);
+        last = point(n - 1);
         nf = static_cast<A>(n);
+    }
+    __device__ __noinline__ A strat_point(int j) const {
+        const uint4 w = philox4x32_10(make_uint4(static_cast<uint32_t>(j) >> 2, keys[2], 1u, keys[3]), keys[0], keys[1]);
+        const int q = j & 3;
+        const uint32_t x = q == 0 ? w.x : (q == 1 ? w.y : (q == 2 ? w.z : w.w));
+        const A v = sizeof(A) == 8 ? static_cast<A>(uniform_f64(x)) : static_cast<A>(uniform_f32(x));
+        return stratum_point32<A>(j, v, inv_n);
+    }
+    __device__ __forceinline__ A point(int j) const {
+        if constexpr (kStrat) return strat_point(j);
+        else return stratum_point32<A>(j, u0, inv_n);
     }
     // number of strata j with u_j <= c
     __device__ __forceinline__ int count_le(A c) const {
@@ -120,8 +136,8 @@ struct Strata {
         // The estimate is almost always within one stratum of the answer: probe u_j and its
         // neighbour on the far side (j = 0 has u_0 = first <= c, so j - 1 is never probed
         // below 0), and search only when both probes fall on the same side.
-        const bool a = stratum_point32<A>(j, u0, inv_n) <= c;
-        const bool b = stratum_point32<A>(a ? j + 1 : j - 1, u0, inv_n) <= c;
+        const bool a = point(j) <= c;
+        const bool b = point(a ? j + 1 : j - 1) <= c;
         if (a != b) return a ? j + 1 : j;
         return search(c, j);
     }
@@ -129,11 +145,11 @@ struct Strata {
     __device__ __noinline__ int search(A c, int j) const {
         // invariant wanted: u(lo) <= c < u(hi), 0 <= lo < hi <= n - 1
         int lo, hi;
-        if (stratum_point32<A>(j, u0, inv_n) <= c) {
+        if (point(j) <= c) {
             lo = j;
             hi = j + 1;
             long long step = 1;
-            while (hi < n - 1 && stratum_point32<A>(hi, u0, inv_n) <= c) {
+            while (hi < n - 1 && point(hi) <= c) {
                 lo = hi;
                 step <<= 1;
                 hi = (hi + step < n - 1) ? static_cast<int>(hi + step) : n - 1;
@@ -142,7 +158,7 @@ struct Strata {
             hi = j;
             lo = j - 1;
             long long step = 1;
-            while (lo > 0 && !(stratum_point32<A>(lo, u0, inv_n) <= c)) {
+            while (lo > 0 && !(point(lo) <= c)) {
                 hi = lo;
                 step <<= 1;
                 lo = (lo > step) ? static_cast<int>(lo - step) : 0;
@@ -150,7 +166,7 @@ struct Strata {
         }
         while (hi - lo > 1) {
             const int mid = lo + ((hi - lo) >> 1);
-            if (stratum_point32<A>(mid, u0, inv_n) <= c) lo = mid; else hi = mid;
+            if (point(mid) <= c) lo = mid; else hi = mid;
         }
         return lo + 1;
     }

@@ -37,7 +37,11 @@ inline pf_status check_config(const pf_config *c) {
     if (!isfinite(c->bg_level) || !isfinite(c->fg_level) || !isfinite(c->sigma_x) || !isfinite(c->sigma_y))
         return PF_ERR_ARG;
     if (fabs(c->init_x) > 1.0e6 || fabs(c->init_y) > 1.0e6) return PF_ERR_ARG;
-    if (c->est_capacity < 0 || c->reserved != 0) return PF_ERR_ARG;
+    if (c->est_capacity < 0) return PF_ERR_ARG;
+    if (c->resampler != PF_RESAMPLE_SYSTEMATIC && c->resampler != PF_RESAMPLE_STRATIFIED) return PF_ERR_ARG;
+    // stratified points in FP32 are ordered only while (float)j is exact
+    if (c->resampler == PF_RESAMPLE_STRATIFIED && c->precision != PF_REF64 && c->num_particles > (1ll << 24))
+        return PF_ERR_ARG;
     if (c->flags & ~(PF_FLAG_DEBUG_ARRAYS | PF_FLAG_ACCUM32 | PF_FLAG_TUNED)) return PF_ERR_ARG;
     return PF_OK;
 }
@@ -74,6 +78,7 @@ inline void fill_tracker_constants(const pf_config &c, TrackerDev &T) {
     T.drift_x = c.drift_x; T.drift_y = c.drift_y;
     T.inv_n = 1.0 / static_cast<double>(c.num_particles);
     T.inv_n_f = 1.0f / static_cast<float>(c.num_particles);
+    T.resampler = c.resampler;
     T.init_xf = static_cast<float>(c.init_x); T.init_yf = static_cast<float>(c.init_y);
     T.drift_xf = static_cast<float>(c.drift_x); T.drift_yf = static_cast<float>(c.drift_y);
     T.sigma_xf = static_cast<float>(c.sigma_x); T.sigma_yf = static_cast<float>(c.sigma_y);

@@ -83,7 +83,7 @@ struct TrackerDev {
     double init_x, init_y, sigma_x, sigma_y, drift_x, drift_y;
     double inv_n;              // 1.0 / N
     float inv_n_f;             // 1.0f / (float)N
-    float pad2;
+    int32_t resampler;         // pf_resampler
     // FP32 copies for the FP32 kernels
     float init_xf, init_yf, drift_xf, drift_yf, sigma_xf, sigma_yf;
     float c1f, c2Df, denf;

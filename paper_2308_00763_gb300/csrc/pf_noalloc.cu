@@ -97,6 +97,7 @@ extern "C" pf_status pf_step_frame_noalloc(const pf_config *cfg, const pf_state_
     if (!isfinite(c.init_x) || !isfinite(c.init_y) || fabs(c.init_x) > 1.0e6 || fabs(c.init_y) > 1.0e6) return PF_ERR_ARG;
     if (!isfinite(c.drift_x) || !isfinite(c.drift_y) || !isfinite(c.bg_level) || !isfinite(c.fg_level)) return PF_ERR_ARG;
     if (c.flags & ~PF_FLAG_ACCUM32) return PF_ERR_ARG;   // no debug arrays here
+    if (c.resampler != PF_RESAMPLE_SYSTEMATIC && c.resampler != PF_RESAMPLE_STRATIFIED) return PF_ERR_ARG;
     if (pitch_bytes < c.width) return PF_ERR_ARG;
     const pf_state_header &h = *state_in;
     if (h.magic != 0x31534650u || h.precision != c.precision || h.num_particles != c.num_particles || h.t < 0)

@@ -418,6 +418,7 @@ struct __align__(16) StepSmem {
     int jbeg, jend;
     double u0d;               // resampling offset u0 of the previous frame
     float u0f;
+    uint32_t skeys[4];        // stratified resampling: key_lo, key_hi, frame t - 1, tracker id
     int win_x0, win_y0, win_w, win_h;   // likelihood table window (win_w = 0: none)
     int qmin;
     int8_t w[2 * kMaxRadius + 1];
@@ -793,6 +794,8 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
             const uint32_t w0 =
                 philox4x32_10(make_uint4(0u, static_cast<uint32_t>(t - 1), 1u, T.tracker_id), T.key_lo, T.key_hi).x;
             if constexpr (kF64) sm.u0d = uniform_f64(w0); else sm.u0f = uniform_f32(w0);
+            sm.skeys[0] = T.key_lo; sm.skeys[1] = T.key_hi;
+            sm.skeys[2] = static_cast<uint32_t>(t - 1); sm.skeys[3] = T.tracker_id;
         }
         __syncthreads();
         if (tid == 0) {
@@ -910,8 +913,7 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
     if (t > 0) {
         const acc_t invS = kF64 ? static_cast<acc_t>(sm.st.invS) : static_cast<acc_t>(sm.st.invS_f);
         const acc_t u0 = kF64 ? static_cast<acc_t>(sm.u0d) : static_cast<acc_t>(sm.u0f);
-        Strata<acc_t> str;
-        str.init(N, u0, sizeof(acc_t) == 8 ? static_cast<acc_t>(T.inv_n) : static_cast<acc_t>(T.inv_n_f));
+        const acc_t inv_n = sizeof(acc_t) == 8 ? static_cast<acc_t>(T.inv_n) : static_cast<acc_t>(T.inv_n_f);
         // exact prefix before the tile (every thread) and after it (published as inclusive)
         const U128 exclx = (lt > 0) ? lookback<P>(look, lt, dtag, st, sm) : U128{0ull, 0ull};
         const U128 endx = add128(exclx, sm.agg_x);
@@ -921,26 +923,39 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
         acc_t excl, pend;
         if constexpr (kF64) { excl = from_fixed(exclx); pend = from_fixed(endx); }
         else { excl = from_fixed_f(exclx); pend = from_fixed_f(endx); }
-        if (tid == 0) sm.jbeg = (lt == 0) ? 0 : str.count_le(fmin(mul_rn(excl, invS), static_cast<acc_t>(1)));
-        acc_t cprev = static_cast<acc_t>(-1);
-        int jprev = 0;
+        // J of the tile's first element and of each element, for either resampling scheme
+        const auto count_strata = [&](const auto &str) {
+            if (tid == 0) sm.jbeg = (lt == 0) ? 0 : str.count_le(fmin(mul_rn(excl, invS), static_cast<acc_t>(1)));
+            acc_t cprev = static_cast<acc_t>(-1);
+            int jprev = 0;
 #pragma unroll
-        for (int m = 0; m < kItems; ++m) {
-            const int e = eb + m;
-            int J = N;                                   // (elements past the tile: unused)
-            if (e < cnt) {
-                const int k = k0 + e;
-                const acc_t Pk = (e == cnt - 1) ? pend : fmin(add_rn(excl, loc[m]), pend);
-                // the normalised CDF cannot exceed 1; the FP32 scan can round above it
-                acc_t C = fmin(mul_rn(Pk, invS), static_cast<acc_t>(1));
-                if (k == N - 1) { C = static_cast<acc_t>(1); J = N; }
-                else if (C == cprev) J = jprev;          // same CDF value, same count
-                else J = str.count_le(C);
-                cprev = C;
-                jprev = J;
-                if (dbg_cdf) dbg_cdf[k] = C;
+            for (int m = 0; m < kItems; ++m) {
+                const int e = eb + m;
+                int J = N;                                   // (elements past the tile: unused)
+                if (e < cnt) {
+                    const int k = k0 + e;
+                    const acc_t Pk = (e == cnt - 1) ? pend : fmin(add_rn(excl, loc[m]), pend);
+                    // the normalised CDF cannot exceed 1; the FP32 scan can round above it
+                    acc_t C = fmin(mul_rn(Pk, invS), static_cast<acc_t>(1));
+                    if (k == N - 1) { C = static_cast<acc_t>(1); J = N; }
+                    else if (C == cprev) J = jprev;          // same CDF value, same count
+                    else J = str.count_le(C);
+                    cprev = C;
+                    jprev = J;
+                    if (dbg_cdf) dbg_cdf[k] = C;
+                }
+                Jr[m] = J;
             }
-            Jr[m] = J;
+        };
+        if (T.resampler == 1) {
+            // (key_lo, key_hi, frame t - 1, tracker id) of the stratum offsets
+            Strata<acc_t, true> str;
+            str.init(N, static_cast<acc_t>(0.5), inv_n, sm.skeys);   // u0 = 1/2 only centres the estimate
+            count_strata(str);
+        } else {
+            Strata<acc_t, false> str;
+            str.init(N, u0, inv_n);
+            count_strata(str);
         }
         store_items(sm.J + eb, Jr);
         __syncthreads();          // J, jbeg and the likelihood table are complete

@@ -65,7 +65,10 @@ def test_invalid_configs_rejected_without_gpu(libpath):
     """Argument validation happens on the host before any CUDA call."""
     import paper_2308_00763_gb300 as pf
     bad = [dict(num_particles=0), dict(disk_radius=-1), dict(disk_radius=65), dict(width=0),
-           dict(precision=7), dict(sigma=(-1.0, 1.0)), dict(init=(float("nan"), 0.0))]
+           dict(precision=7), dict(sigma=(-1.0, 1.0)), dict(init=(float("nan"), 0.0)),
+           dict(resampler=2), dict(resampler=-1),
+           # stratified points in FP32 are ordered only while (float)j is exact
+           dict(resampler="stratified", num_particles=(1 << 24) + 1)]
     for b in bad:
         kw = dict(width=64, height=64, num_particles=100, disk_radius=3, precision="f32")
         kw.update({k: v for k, v in b.items() if k in kw})

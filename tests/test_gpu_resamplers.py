@@ -1,0 +1,124 @@
+"""Stratified resampling (pf_config.resampler = PF_RESAMPLE_STRATIFIED) on the GPU.
+
+The fused step with one independent offset per stratum, u_j = (j + v_j) / N (Sec. 2 names
+stratified resampling beside the paper's systematic scheme of Sec. 3).  The checks: the
+ancestors are exactly the oracle's stratified resampling of the CDF the step computed, with
+the offsets drawn by the oracle's own Philox; the REF64 track equals the oracle's FP64
+stratified track within 1e-9 px; offspring counts stay within two strata of N w_k; the
+option takes effect; stratified and systematic trackers share a batch, each equal to its
+own single run; the bench's launch configuration (2^20 particles) resamples exactly.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2308_00763_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TILE = 4096  # particles per tile of the step kernel
+
+
+@pytest.fixture(scope="module")
+def pf():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2308_00763_gb300 as m
+    m.lib(build_if_missing=True)
+    oracle.build()
+    return m
+
+
+def _frames(v):
+    import torch
+    return torch.from_numpy(v.frames).cuda()
+
+
+def _last_step(pf, v, N, prec, seed, *, resampler="stratified", tracker=0, sigma=(1.0, 1.0), T=None):
+    """Run T frames with debug arrays; the ancestors and CDF of the last step."""
+    T = v.T if T is None else T
+    f = pf.Filter(v.W, v.H, N, v.radius, prec, init=tuple(v.centres[0]), seed=seed, tracker_id=tracker,
+                  sigma=sigma, flags=pf.PF_FLAG_DEBUG_ARRAYS, resampler=resampler)
+    fr = _frames(v)
+    f.run(fr[:T])
+    anc = f.debug(0).astype(np.int64)
+    C = f.debug(1).astype(np.float64)
+    f.close()
+    return anc, C
+
+
+@pytest.mark.parametrize("prec", ["ref64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("N", [1, 3, TILE + 1, 3 * TILE + 17])
+def test_stratified_ancestors_exact(pf, prec, N):
+    v = synth.make_video(128, 128, 4, 5, noise=5.0, seed=41)
+    anc, C = _last_step(pf, v, N, prec, 17, tracker=2)
+    assert np.all(np.diff(C) >= 0) and C[-1] == 1.0
+    offs = oracle.stratified_offsets(17, v.T - 2, N, 2)
+    a_o = oracle.resample_stratified(C, offs, "f64" if prec == "ref64" else "f32")
+    assert np.array_equal(anc, a_o)
+
+
+def test_stratified_ref64_track_within_1e9(pf):
+    v = synth.make_video(128, 128, 10, 5, noise=5.0, seed=1)
+    for N in (1000, 3 * TILE + 17):
+        est_o, M_o, _ = oracle.track(v.frames, N, 5, init=tuple(v.centres[0]), seed=1, resampler="stratified")
+        f = pf.Filter(v.W, v.H, N, 5, "ref64", init=tuple(v.centres[0]), seed=1, resampler="stratified")
+        f.run(_frames(v))
+        est, ms = f.estimates(0, v.T, with_stats=True)
+        f.close()
+        assert np.abs(est - est_o).max() <= 1e-9, N
+        assert np.array_equal(ms[:, 0], M_o)
+
+
+@pytest.mark.parametrize("prec", ["ref64", "f32", "f16"])
+def test_stratified_counts_within_two_strata(pf, prec):
+    v = synth.make_video(160, 120, 4, 4, noise=15.0, seed=33)
+    N = 5 * TILE + 123
+    anc, C = _last_step(pf, v, N, prec, 8, sigma=(3.0, 3.0))
+    w = np.diff(np.concatenate([[0.0], C]))
+    cnt = np.bincount(anc, minlength=N)
+    slack = 1e-9 if prec == "ref64" else N * 2.0 ** -21
+    assert cnt.sum() == N and np.all(np.diff(anc) >= 0)
+    assert np.all(np.abs(cnt - N * w) < 2.0 + slack)
+
+
+def test_stratified_differs_from_systematic(pf):
+    v = synth.make_video(128, 128, 4, 5, noise=15.0, seed=42)
+    N = 2 * TILE + 9
+    a_s, C_s = _last_step(pf, v, N, "f32", 5, resampler="stratified", sigma=(2.0, 2.0))
+    a_y, C_y = _last_step(pf, v, N, "f32", 5, resampler="systematic", sigma=(2.0, 2.0))
+    assert not np.array_equal(a_s, a_y)
+    # the systematic run is the oracle's systematic resampling of its own CDF
+    assert np.array_equal(a_y, oracle.resample(C_y, oracle.resample_u0(5, v.T - 2), "f32"))
+
+
+def test_mixed_resamplers_batch_equals_singles(pf):
+    vids = [synth.make_video(96, 96, 5, 3, noise=5.0, seed=50 + i, v=(1.0, -1.0)) for i in range(3)]
+    Ns = [3000, 2 * TILE + 5, 777]
+    rs = ["stratified", "systematic", "stratified"]
+    for prec in ("ref64", "f16"):
+        cfgs = [pf.make_config(v.W, v.H, n, v.radius, prec, init=tuple(v.centres[0]), seed=60 + i,
+                               tracker_id=i, resampler=r) for i, (v, n, r) in enumerate(zip(vids, Ns, rs))]
+        b = pf.Batch(cfgs)
+        fr = [_frames(v) for v in vids]
+        for t in range(5):
+            b.step([f[t] for f in fr])
+        got = np.stack([b.estimates(t) for t in range(5)], axis=1)
+        b.close()
+        for i, (v, n, r) in enumerate(zip(vids, Ns, rs)):
+            s = pf.Filter(v.W, v.H, n, v.radius, prec, init=tuple(v.centres[0]), seed=60 + i, tracker_id=i,
+                          resampler=r)
+            s.run(fr[i])
+            assert np.array_equal(s.estimates(0, 5), got[i]), (prec, i)
+            s.close()
+
+
+@pytest.mark.parametrize("prec", ["ref64", "f16"])
+def test_stratified_full_size_ancestors_exact(pf, prec):
+    """512x512, r = 5, N = 2^20 (the bench's launch configuration, balanced tiles)."""
+    v = synth.make_video(512, 512, 3, 5, noise=5.0, seed=1)
+    N = 1 << 20
+    anc, C = _last_step(pf, v, N, prec, 1)
+    offs = oracle.stratified_offsets(1, v.T - 2, N, 0)
+    assert np.array_equal(anc, oracle.resample_stratified(C, offs, "f64" if prec == "ref64" else "f32"))
