@@ -227,11 +227,20 @@ __device__ __forceinline__ U128 to_fixed(float v) {
 // Fixed point -> float: the top 64 significant bits rounded to nearest (monotone,
 // deterministic); no FP64 instruction.
 __device__ __forceinline__ float from_fixed_f(U128 x) {
-    if (x.hi == 0ull) return __ull2float_rn(x.lo) * 8.0779356694631609e-28f;   // 2^-90
-    const int lz = __clzll(static_cast<long long>(x.hi));
-    const uint64_t top = (x.hi << lz) | (lz ? (x.lo >> (64 - lz)) : 0ull);
-    const int e2 = 64 - lz - kFixShift;                     // value = top * 2^e2, e2 in [-26, 38]
-    return __ull2float_rn(top) * __int_as_float((127 + e2) << 23);
+    if (x.hi == 0ull && (x.lo >> 32) == 0ull)
+        return __uint2float_rn(static_cast<uint32_t>(x.lo)) * 8.0779356694631609e-28f;   // 2^-90
+    // normalise so the top set bit is bit 63 of `top`, value = top * 2^e2
+    const int lz = x.hi ? __clzll(static_cast<long long>(x.hi)) : 64 + __clzll(static_cast<long long>(x.lo));
+    uint64_t top;
+    if (lz == 0) top = x.hi;
+    else if (lz < 64) top = (x.hi << lz) | (x.lo >> (64 - lz));
+    else top = x.lo << (lz - 64);
+    const int e2 = 64 - lz - kFixShift;                     // in [-121, -26]
+    // round to nearest on the top 32 bits with the rest folded into a sticky bit: the
+    // same result as converting all 64 bits (24 + guard + round bits are inside the 32),
+    // without a 64-bit integer conversion
+    const uint32_t t32 = static_cast<uint32_t>(top >> 32) | (static_cast<uint32_t>(top) != 0u ? 1u : 0u);
+    return __uint2float_rn(t32) * __int_as_float((127 + 32 + e2) << 23);
 }
 
 // Fixed point -> double: the top 64 significant bits rounded to nearest; monotone
