@@ -53,6 +53,9 @@ def _args():
     p.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     p.add_argument("--no-sweep", action="store_true", help="skip the precision/size sweep and the paper workload")
     p.add_argument("--serve-seconds", type=float, default=20.0, help="length of the served-streams run")
+    p.add_argument("--tpb-sweep", action="store_true",
+                   help="thread-block study: build the step kernel at 128/256/512/1024 threads per CTA and time each")
+    p.add_argument("--tpb-child", action="store_true", help=argparse.SUPPRESS)
     return p.parse_args()
 
 
@@ -621,8 +624,89 @@ def _resamplers(dev, stream):
     return {"workload": WORKLOAD, "unit": METRIC, "by_precision": out}
 
 
+def _tpb_child():
+    """One study build (selected by PF_STEP_THREADS): us per frame of the headline workload
+    (2^20 particles) and of a small tracker (2^16) per precision; one JSON object."""
+    import torch
+    import paper_2308_00763_gb300 as pf
+    from paper_2308_00763_gb300 import synth
+    pf.lib(build_if_missing=True)
+    dev = torch.device("cuda")
+    stream = torch.cuda.Stream()
+    v = synth.make_video(W_, H_, T_, R_, noise=NOISE_, seed=SEED_)
+    fr = torch.from_numpy(v.frames).to(dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    def timed(n, prec, flags=0):
+        try:
+            f = pf.Filter(W_, H_, n, R_, prec, init=tuple(v.centres[0]), seed=SEED_, stream=stream, flags=flags)
+        except RuntimeError as e:           # the 1024-thread build has no REF64 kernel
+            return {"unavailable": str(e)}
+        f.run(fr[:4])
+        best = None
+        for _ in range(3):
+            flush.zero_()
+            f.reset()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            f.run(fr)
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            us = 1e3 * a.elapsed_time(b) / T_
+            best = us if best is None else min(best, us)
+        r = {"us_per_frame": best, "value": n / (best * 1e-6), "rmse_px_vs_truth": _rmse(f.estimates(0, T_), v.centres)}
+        f.close()
+        return r
+
+    out = {}
+    for n in (N_, 1 << 16):
+        out[str(n)] = {prec: timed(n, prec) for prec in ("ref64", "f32", "f16", "bf16")}
+    if os.environ.get("PF_STEP_THREADS") == "512":
+        # the library's kernel with the tile forced through the tuning cache (the default
+        # rule keeps 4096-particle tiles below half a device, which batches prefer)
+        tiles = {}
+        for n in (1 << 16, 1 << 18, N_):
+            for prec in ("ref64", "f32", "f16"):
+                for tile in (1024, 2048, 4096):
+                    pf.pf_tuning_clear()
+                    pf.pf_tuning_store(pf.make_config(W_, H_, n, R_, prec), tile, 0, 0)
+                    tiles["%s/%d/%d" % (prec, n, tile)] = timed(n, prec, pf.PF_FLAG_TUNED)["us_per_frame"]
+        pf.pf_tuning_clear()
+        out["forced_tiles_us_per_frame"] = tiles
+    print(json.dumps(out))
+    return 0
+
+
+def _tpb_sweep():
+    """Thread-block study (the paper varies threads per block from 32 to 1024): the step
+    kernel built at 128, 256, 512 (the library) and 1024 threads per CTA, 8 CDF elements a
+    thread, each timed in its own process; one JSON line."""
+    import subprocess
+    from concurrent.futures import ThreadPoolExecutor
+    from paper_2308_00763_gb300 import build as pbuild
+    with ThreadPoolExecutor(len(pbuild.STUDY_THREADS)) as ex:
+        list(ex.map(lambda t: pbuild.build(threads=t), pbuild.STUDY_THREADS))
+    res = {}
+    for t in pbuild.STUDY_THREADS:
+        env = dict(os.environ, PF_STEP_THREADS=str(t))
+        p = subprocess.run([sys.executable, os.path.abspath(__file__), "--tpb-child"], env=env,
+                           capture_output=True, text=True, timeout=900)
+        if p.returncode != 0:
+            res[str(t)] = {"error": (p.stderr or p.stdout).strip().splitlines()[-1:]}
+            continue
+        res[str(t)] = json.loads(p.stdout.strip().splitlines()[-1])
+    print(json.dumps({"study": "threads per CTA of the step kernel", "workload": WORKLOAD, "unit": "us per frame",
+                      "particles": [N_, 1 << 16], "by_threads": res}))
+    return 0
+
+
 def main():
     args = _args()
+    if args.tpb_child:
+        return _tpb_child()
+    if args.tpb_sweep:
+        return _tpb_sweep()
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -167,8 +167,15 @@ _lock = threading.Lock()
 _lib = None
 
 
+def _study_threads():
+    """Threads per CTA of a thread-block study build selected by the environment
+    (PF_STEP_THREADS, one of 128, 256, 512, 1024), or None for the library."""
+    v = os.environ.get("PF_STEP_THREADS")
+    return int(v) if v else None
+
+
 def library_path() -> str:
-    return _build.LIB
+    return _build.lib_path(_study_threads())
 
 
 def lib(build_if_missing: bool = False):
@@ -180,7 +187,7 @@ def lib(build_if_missing: bool = False):
         path = library_path()
         if not os.path.exists(path):
             if build_if_missing:
-                _build.build()
+                _build.build(threads=_study_threads())
             else:
                 raise RuntimeError("the CUDA library %s is not built; run "
                                    "`python -c 'import __graft_entry__ as g; g.build()'`" % path)

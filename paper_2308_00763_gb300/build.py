@@ -35,26 +35,45 @@ def deps():
         os.path.join(ROOT, "include", "pf.h"), os.path.abspath(__file__)]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+STUDY_THREADS = (128, 256, 512, 1024)   # threads per CTA of the step kernel's study builds
+
+
+def lib_path(threads: int | None = None) -> str:
+    """The library, or the thread-block study build with `threads` threads per CTA."""
+    if not threads or threads == 512:
+        return LIB
+    return os.path.join(BUILD, "t%d" % threads, "libpf_gb300.so")
+
+
+def up_to_date(threads: int | None = None) -> bool:
+    lib = lib_path(threads)
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(d) <= t for d in deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra=(), threads: int | None = None) -> str:
+    """Build the library (512 threads per CTA), or with `threads` in STUDY_THREADS a
+    separate study build under _build/t<threads>/ (-DPF_STEP_THREADS)."""
+    if threads and threads not in STUDY_THREADS:
+        raise ValueError("threads per CTA must be one of %s" % (STUDY_THREADS,))
+    lib = lib_path(threads)
+    if not force and up_to_date(threads):
+        return lib
+    bdir = os.path.dirname(lib)
+    os.makedirs(bdir, exist_ok=True)
     cc = nvcc()
     flags = [ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
              "--expt-relaxed-constexpr", *extra]
+    if lib != LIB:
+        flags.append("-DPF_STEP_THREADS=%d" % threads)
     if verbose:
         flags += ["-Xptxas", "-v"]
     procs = []
     objs = []
     for src in sources():
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(bdir, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         procs.append((src, subprocess.Popen([cc, *flags, "-c", src, "-o", obj],
                                             stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
@@ -67,10 +86,10 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
             failed.append(src)
     if failed:
         raise RuntimeError("nvcc failed on: " + ", ".join(os.path.basename(f) for f in failed))
-    tmp = LIB + ".tmp%d" % os.getpid()
+    tmp = lib + ".tmp%d" % os.getpid()
     subprocess.run([cc, ARCH, "-shared", "-o", tmp, *objs], check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

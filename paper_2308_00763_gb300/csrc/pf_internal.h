@@ -14,7 +14,14 @@
 
 namespace pfk {
 
-constexpr int kThreads = 512;             // threads per CTA of the step kernel
+// Threads per CTA of the step kernel: 512 (measured best on GB300 for large trackers).
+// Other builds (-DPF_STEP_THREADS=128/256/1024) exist for the thread-block study only.
+#ifndef PF_STEP_THREADS
+#define PF_STEP_THREADS 512
+#endif
+constexpr int kThreads = PF_STEP_THREADS;
+static_assert(kThreads == 128 || kThreads == 256 || kThreads == 512 || kThreads == 1024,
+              "the step kernel is built for 128, 256, 512 or 1024 threads per CTA");
 constexpr int kItems = 8;                 // CDF elements per thread
 constexpr int kTile = kThreads * kItems;  // largest tile (particles of the resampled frame)
 constexpr int kMaxRadius = 64;

@@ -25,10 +25,11 @@ using namespace pfk;
 
 namespace {
 
-constexpr size_t kScratchBytes = 256 * 1024;
 constexpr int64_t kMaxParticles = int64_t(1) << 22;
 constexpr int kMaxTiles = static_cast<int>(kMaxParticles / (kTile / 2));   // a tile holds >= kTile / 2
 constexpr int kMaxDevices = 64;
+// tracker descriptor, state, frame and counters, then the per-tile descriptors and partials
+constexpr size_t kScratchBytes = 8192 + (sizeof(LookbackDesc) + sizeof(TilePartial)) * size_t(kMaxTiles);
 
 // The scratch array.  In host code its name is only a stand-in for the symbol; the
 // device address comes from cudaGetSymbolAddress (per device).

@@ -273,6 +273,7 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
     if (err == cudaSuccess) err = cudaStreamSynchronize(e.stream);   // host vectors go out of scope
     if (err != cudaSuccess) { cudaGetLastError(); engine_free(e); return PF_ERR_CUDA; }
     e.grid = step_grid_size(e.prec, e.total_tiles);
+    if (e.grid < 1) { engine_free(e); return PF_ERR_CUDA; }   // no launchable kernel for this precision
     if (e.ctas_cap > 0) {
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
@@ -909,6 +910,7 @@ static pf_status sweep_shapes(std::vector<pf_config> cfgs, const std::vector<con
     double win_ms = -1.0;
     pf_status result = PF_OK;
     for (int32_t tile : kTiles) {
+        if (tile > kTile) continue;
         for (int32_t window = 0; window <= 2 && result == PF_OK; ++window) {
             for (int32_t ctas = 0; ctas <= 1 && result == PF_OK; ++ctas) {
                 const pf_tuning cand{tile, window, ctas, 0};

@@ -46,9 +46,9 @@ namespace pfk {
 namespace {
 
 constexpr int kWarps = kThreads / 32;
-constexpr int kTableMax = 4096;            // pixels of the per-tile likelihood table
-constexpr int kRoiMax = 8192;              // staged frame pixels (window + template margin)
-constexpr int kMapMax = 8192;              // offspring of a tile served by the ancestor map
+constexpr int kTableMax = kTile < 4096 ? kTile : 4096;   // pixels of the per-tile likelihood table
+constexpr int kRoiMax = 2 * kTableMax;     // staged frame pixels (window + template margin)
+constexpr int kMapMax = 2 * kTile;         // offspring of a tile served by the ancestor map
 constexpr int kOffMax = 1024;              // template entries served by the offset list (r <= 17)
 constexpr uint32_t kSpinLimit = 1u << 22;  // bounded waits: ~1 s with backoff
 // Half-width of the likelihood window in standard deviations of the transition noise.
@@ -1197,12 +1197,12 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
     if (sm.last) finalize_tracker<P>(T, st, sm, Lp.est_out ? Lp.est_out + 2 * ti : nullptr);
 }
 
-// CTAs per SM the register allocation must allow (measured best per precision on GB300:
-// the step is latency-bound, so the FP16/BF16 kernels trade a few spills for 4 CTAs/SM).
-template <int P> struct MinBlocks { static constexpr int value = 1; };
-template <> struct MinBlocks<1> { static constexpr int value = 2; };
-template <> struct MinBlocks<2> { static constexpr int value = 2; };
-template <> struct MinBlocks<3> { static constexpr int value = 2; };
+// CTAs per SM the register allocation must allow: 1024 threads per SM (64 registers a
+// thread) for the FP32/FP16/BF16 kernels, 512 for REF64 (its FP64 Box-Muller needs ~128);
+// measured best on GB300 for the latency-bound step.
+template <int P> struct MinBlocks {
+    static constexpr int value = (P == 0 ? 512 : 1024) / kThreads > 0 ? (P == 0 ? 512 : 1024) / kThreads : 1;
+};
 
 template <int P>
 __global__ void __launch_bounds__(kThreads, MinBlocks<P>::value) step_kernel(const StepLaunch Lp) {
@@ -1239,8 +1239,10 @@ __global__ void philox_kernel(const uint4 *ctrs, int64_t n, uint32_t k0, uint32_
 template <int P>
 int configure_and_grid(int total_tiles) {
     // MinBlocks CTAs must fit in an SM's 228 KB of shared memory (1 KB reserved per CTA)
-    static_assert((sizeof(StepSmem<P>) + 1024) * MinBlocks<P>::value <= 228 * 1024,
+    // (the 1024-thread study build has no REF64 kernel: its tile does not fit)
+    static_assert((sizeof(StepSmem<P>) + 1024) * MinBlocks<P>::value <= 228 * 1024 || kThreads > 512,
                   "shared memory of the step kernel exceeds its CTAs per SM");
+    if (sizeof(StepSmem<P>) + 1024 > 228 * 1024) return -1;
     const int bytes = static_cast<int>(sizeof(StepSmem<P>));
     if (cudaFuncSetAttribute(step_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess)
         return -1;

@@ -117,3 +117,18 @@ def test_tuning_cache_without_gpu(libpath):
             pf.pf_tuning_store(a, *bad)
     pf.pf_tuning_clear()
     assert pf.pf_tuning_lookup(a) is None
+
+
+def test_thread_block_study_builds_are_separate(monkeypatch):
+    """The thread-block study builds (-DPF_STEP_THREADS) live beside the library and are
+    selected only through PF_STEP_THREADS; 512 threads is the library itself."""
+    from paper_2308_00763_gb300 import binding, build
+    assert build.lib_path(None) == build.LIB == build.lib_path(512)
+    paths = {build.lib_path(t) for t in build.STUDY_THREADS}
+    assert len(paths) == len(build.STUDY_THREADS)
+    monkeypatch.setenv("PF_STEP_THREADS", "256")
+    assert binding.library_path() == build.lib_path(256) != build.LIB
+    monkeypatch.delenv("PF_STEP_THREADS")
+    assert binding.library_path() == build.LIB
+    with pytest.raises(ValueError):
+        build.build(threads=96)
