@@ -70,6 +70,8 @@ def _load():
             "orc_stratified_offsets": (None, [_U64, _U32, _U32, _I64, _P]),
             "orc_resample_strat_f64": (None, [_I64, _P, _P, _P]),
             "orc_resample_strat_f32": (None, [_I64, _P, _P, _P]),
+            "orc_resample_multi_f64": (None, [_I64, _P, _P, _P]),
+            "orc_resample_multi_f32": (None, [_I64, _P, _P, _P]),
             "orc_run": (ctypes.c_int, [_P, _I64, ctypes.c_int, ctypes.c_int, ctypes.c_int, _I64,
                                        _I64, ctypes.c_int, _D, _D, _D, _D, _D, _D, _D, _D,
                                        _U64, _U32, ctypes.c_int, ctypes.c_int, _P, _P, _P]),
@@ -246,7 +248,27 @@ def resample_stratified(C, v, precision: str = "f64"):
     return a
 
 
-RESAMPLERS = {"systematic": 0, "stratified": 1}
+def resample_multinomial(C, v, precision: str = "f64"):
+    """Multinomial-resampling ancestors of CDF ``C`` from independent uniforms ``v``
+    (a_j = min{k : C_k >= v_j}), decided in FP64 or FP32 (C and v rounded to FP32)."""
+    if precision == "f64":
+        Cc = np.ascontiguousarray(C, np.float64)
+        vv = np.ascontiguousarray(v, np.float64)
+        fn = _load().orc_resample_multi_f64
+    elif precision == "f32":
+        Cc = np.ascontiguousarray(C, np.float32)
+        vv = np.ascontiguousarray(v, np.float32)
+        fn = _load().orc_resample_multi_f32
+    else:
+        raise ValueError(precision)
+    if vv.size != Cc.size:
+        raise ValueError("one draw per offspring")
+    a = np.empty(Cc.size, np.int64)
+    fn(Cc.size, _ptr(Cc), _ptr(vv), _ptr(a))
+    return a
+
+
+RESAMPLERS = {"systematic": 0, "stratified": 1, "multinomial": 2}
 
 
 # --------------------------------------------------------------------------- whole tracker
@@ -281,6 +303,8 @@ def track_steps(frames: np.ndarray, N: int, r: int, *, init, sigma=(1.0, 1.0), d
         u0 = resample_u0(seed, t, tracker)
         if resampler == "stratified":
             a = resample_stratified(C, stratified_offsets(seed, t, N, tracker), "f64")
+        elif resampler == "multinomial":
+            a = resample_multinomial(C, stratified_offsets(seed, t, N, tracker), "f64")
         elif resampler == "systematic":
             a = resample(C, u0, "f64")
         else:

@@ -15,6 +15,7 @@
  *   normalising (CDF, inclusive prefix sum)  orc_cdf
  *   systematic resampling (Sec. 3)  orc_resample_f64 / orc_resample_f32
  *   stratified resampling (Sec. 2)  orc_stratified_offsets, orc_resample_strat_f64 / _f32
+ *   multinomial resampling (Sec. 3) orc_resample_multi_f64 / _f32 (draws: orc_stratified_offsets)
  * Where the paper is silent the readings are (numbered as in the design notes):
  *   C1  Eq. 3 is summed over the template pixels and divided by 50*|D|.
  *   C2  template D = integer offsets with dx^2+dy^2 <= r^2 (centre included).
@@ -27,6 +28,7 @@
  *   C8  systematic: one u0 per frame, u_j = (j + u0) * (1/N) in the CDF's precision,
  *       a_j = min{k : C_k >= u_j}, N-1 if there is none.
  *       Stratified (alternative scheme): u_j = (j + v_j) * (1/N), v_j independent.
+ *       Multinomial (alternative scheme): u_j = v_j, N independent draws.
  *   C11 draws: Philox4x32-10 words -> 23-bit uniforms -> Box-Muller in FP64.
  *   C12 at t = 0 every ancestor sits at (init_x, init_y).
  * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), written here
@@ -433,6 +435,35 @@ void orc_resample_strat_f32(int64_t N, const float *C, const float *v, int64_t *
     }
 }
 
+/* Multinomial resampling (Sec. 3 describes it as drawing each ancestor from the
+ * categorical distribution of the normalised weights): offspring j takes the first
+ * particle whose CDF value reaches an independent uniform v_j (the same Philox words as
+ * the stratified offsets), N - 1 if there is none. */
+void orc_resample_multi_f64(int64_t N, const double *C, const double *v, int64_t *a)
+{
+    for (int64_t j = 0; j < N; ++j) {
+        int64_t lo = 0, hi = N;
+        while (lo < hi) {
+            int64_t mid = lo + (hi - lo) / 2;
+            if (C[mid] >= v[j]) hi = mid; else lo = mid + 1;
+        }
+        a[j] = lo < N ? lo : N - 1;
+    }
+}
+
+/* The same decision taken in FP32, for a CDF held in FP32. */
+void orc_resample_multi_f32(int64_t N, const float *C, const float *v, int64_t *a)
+{
+    for (int64_t j = 0; j < N; ++j) {
+        int64_t lo = 0, hi = N;
+        while (lo < hi) {
+            int64_t mid = lo + (hi - lo) / 2;
+            if (C[mid] >= v[j]) hi = mid; else lo = mid + 1;
+        }
+        a[j] = lo < N ? lo : N - 1;
+    }
+}
+
 /* ------------------------------------------------------------------------- */
 /* The whole tracker (Fig. 1): for t = 0..T-1 propagate, weigh, normalise,      */
 /* estimate, resample.  Outputs per frame: estimate (x, y), M and S.             */
@@ -470,7 +501,8 @@ int orc_run(const uint8_t *frames, int64_t frame_stride, int T, int W, int H, in
             orc_cdf(N, e, S, C);
             if (resampler) {
                 orc_stratified_offsets(seed, (uint32_t)t, tracker, N, v);
-                orc_resample_strat_f64(N, C, v, a);
+                if (resampler == 2) orc_resample_multi_f64(N, C, v, a);
+                else orc_resample_strat_f64(N, C, v, a);
             } else {
                 orc_resample_f64(N, C, orc_resample_u0(seed, (uint32_t)t, tracker), a);
             }

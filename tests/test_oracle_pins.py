@@ -421,6 +421,48 @@ def test_stratified_dominant_and_clamp():
     assert np.array_equal(oracle.resample_stratified(C2, [0.9, 0.6, 0.7], "f64"), [1, 2, 2])
 
 
+# ----------------------------------------------------------------------------- multinomial resampling
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_multinomial_equal_weights_is_floor_of_n_u(prec):
+    """Equal weights, N a power of two (C_k = (k + 1)/N exact): the ancestor of draw v is
+    the first step reaching it, ceil(N v) - 1, which is floor(N v) here (a draw is an odd
+    multiple of 2^-24, so N v is never an integer)."""
+    rng = np.random.default_rng(16)
+    for n in (1, 2, 8, 1024, 1 << 16):
+        C = (np.arange(n, dtype=np.float64) + 1) / n
+        v = oracle.uniform(rng.integers(0, 2 ** 32, size=n, dtype=np.uint64).astype(np.uint32))
+        a = oracle.resample_multinomial(C, v, prec)
+        want = np.ceil(v * n).astype(np.int64) - 1       # first k with (k + 1)/N >= v
+        assert np.array_equal(a, want) and np.array_equal(want, np.floor(v * n).astype(np.int64))
+
+
+def test_multinomial_counts_mean_and_variance():
+    """Counts of particle k are Binomial(N, w_k): mean N w_k and variance N w_k (1 - w_k)
+    over 4000 independent sets of draws (6 standard errors; variance within 15 %)."""
+    rng = np.random.default_rng(17)
+    n, trials = 6, 4000
+    e = rng.uniform(0.05, 1.0, n)
+    S, _, _ = oracle.normalise(e, np.zeros(n), np.zeros(n))
+    C = oracle.cdf(e, S)
+    w = np.diff(np.concatenate([[0.0], C]))
+    cnts = np.array([_counts(oracle.resample_multinomial(C, rng.uniform(0.0, 1.0, n), "f64"), n)
+                     for _ in range(trials)], np.float64)
+    mean, var = cnts.mean(axis=0), cnts.var(axis=0)
+    want_var = n * w * (1 - w)
+    assert np.all(np.abs(mean - n * w) <= 6 * np.sqrt(want_var / trials))
+    assert np.all(np.abs(var / want_var - 1.0) < 0.15)
+
+
+def test_multinomial_dominant_clamp_and_order():
+    C = np.array([0.0, 0.0, 1.0, 1.0])
+    assert np.array_equal(oracle.resample_multinomial(C, [0.9, 0.1, 0.5, 1e-6], "f64"), [2, 2, 2, 2])
+    C2 = np.array([0.2, 0.5, 0.9])     # a draw above every entry: clamp to N-1
+    assert np.array_equal(oracle.resample_multinomial(C2, [0.95, 0.2, 0.21], "f64"), [2, 0, 1])
+    # ancestors follow the draws, not the offspring index (no ordering)
+    C3 = np.array([0.25, 0.5, 0.75, 1.0])
+    assert np.array_equal(oracle.resample_multinomial(C3, [0.9, 0.6, 0.3, 0.1], "f32"), [3, 2, 1, 0])
+
+
 # ----------------------------------------------------------------------------- propagation, Eq. 1-2
 def test_propagation_moments_paper_motion():
     """Eq. 1-2: x ~ N(1 + x_anc, 5^2), y ~ N(2 + y_anc, 2^2)."""
@@ -463,6 +505,15 @@ def test_track_stratified_recovers_ground_truth_config1():
     err = np.sqrt(np.sum((est - v.centres) ** 2, axis=1))
     assert np.sqrt(np.mean(err ** 2)) < 1.0 and err.max() < 1.5
     recs = list(oracle.track_steps(v.frames, 1000, 5, init=tuple(v.centres[0]), seed=1, resampler="stratified"))
+    assert np.array_equal(np.array([r.est for r in recs]), est)
+
+
+def test_track_multinomial_recovers_ground_truth_config1():
+    v = synth.make_video(128, 128, 10, 5, noise=5.0, seed=1)
+    est, _, _ = oracle.track(v.frames, 1000, 5, init=tuple(v.centres[0]), seed=1, resampler="multinomial")
+    err = np.sqrt(np.sum((est - v.centres) ** 2, axis=1))
+    assert np.sqrt(np.mean(err ** 2)) < 1.0 and err.max() < 1.5
+    recs = list(oracle.track_steps(v.frames, 1000, 5, init=tuple(v.centres[0]), seed=1, resampler="multinomial"))
     assert np.array_equal(np.array([r.est for r in recs]), est)
 
 
