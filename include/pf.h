@@ -64,10 +64,16 @@ typedef enum {
  *               (the paper's scheme; the default).
  *   STRATIFIED: v_j independent, v_j = uniform word (j mod 4) of Philox(j / 4, t, 1,
  *               tracker_id), so v_0 = u0.  With a FP32 CDF it needs N <= 2^24 (beyond,
- *               (float)j rounds and the points would no longer be ordered). */
+ *               (float)j rounds and the points would no longer be ordered).
+ *   MULTINOMIAL: no strata: offspring j takes the first particle whose CDF value reaches
+ *               u_j = v_j, the stratified offsets used as N independent uniforms (Sec. 3
+ *               describes this categorical draw).  Two kernels per frame (the CDF is
+ *               written to device memory, then every offspring searches it); trackers
+ *               and batches only (pf_server_open and pf_step_frame_noalloc reject it). */
 typedef enum {
     PF_RESAMPLE_SYSTEMATIC = 0,
-    PF_RESAMPLE_STRATIFIED = 1
+    PF_RESAMPLE_STRATIFIED = 1,
+    PF_RESAMPLE_MULTINOMIAL = 2
 } pf_resampler;
 
 /* pf_config.flags */

@@ -26,6 +26,11 @@ constexpr int kItems = 8;                 // CDF elements per thread
 constexpr int kTile = kThreads * kItems;  // largest tile (particles of the resampled frame)
 constexpr int kMaxRadius = 64;
 
+// Resampling schemes (pf_config.resampler).
+constexpr int kResampleSystematic = 0;
+constexpr int kResampleStratified = 1;
+constexpr int kResampleMultinomial = 2;   // CDF by the step kernel, offspring by the pull kernel
+
 // Device status bits (sticky, per tracker).
 constexpr uint32_t kStatusTimeout = 0x1u;
 
@@ -98,6 +103,7 @@ struct TrackerDev {
     void *px[2], *py[2], *pl[2];
     int32_t *dbg_anc;          // NULL unless PF_FLAG_DEBUG_ARRAYS
     void *dbg_cdf;
+    void *cdf;                 // multinomial: the normalised CDF of the previous frame [N] (FP64 / FP32)
     LookbackDesc *look;
     TilePartial *part;
     uint32_t *done;
@@ -127,6 +133,9 @@ struct StepLaunch {
 
 // Host entry points into the kernel translation unit.
 int launch_step(int precision, const StepLaunch &L, int grid, void *stream);
+// The multinomial trackers' CDF kernel and pull kernel (their offspring), after launch_step
+// on the same stream.
+int launch_pull(int precision, const StepLaunch &L, int grid, void *stream);
 int step_grid_size(int precision, int total_tiles);
 // Particles per tile for a tracker of n particles.  A tracker of at least half a device
 // of full tiles (SMs x CTAs per SM x kTile / 2 particles) takes the smallest multiple of

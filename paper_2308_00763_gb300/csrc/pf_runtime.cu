@@ -91,6 +91,7 @@ struct Engine {
     int total_tiles = 0;
     int grid = 0;
     int ctas_cap = 0;                  // CTAs per SM (0: as many as fit)
+    bool any_pull = false;             // a multinomial tracker: each frame also launches the pull kernel
     pf_status sticky = PF_OK;
     uint8_t *d_frame_buf = nullptr;    // single tracker: staging of host frames
     TrackerState *h_init_pinned = nullptr;  // initial state of every tracker (pf_reset)
@@ -168,7 +169,7 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
     const size_t pb = pos_bytes(e.prec);
     const size_t cdf_b = e.prec == PF_REF64 ? 8 : 4;
     Arena a;
-    struct Off { size_t px[2], py[2], pl[2], look, part, done, state, est, stat, dbga, dbgc; };
+    struct Off { size_t px[2], py[2], pl[2], look, part, done, state, est, stat, dbga, dbgc, cdf; };
     std::vector<Off> off(n);
     // the trackers' states form one array (the kernel indexes it by tracker)
     const size_t states_off = a.take(sizeof(TrackerState) * n);
@@ -197,9 +198,14 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
         o.state = states_off + sizeof(TrackerState) * i;
         o.est = a.take(sizeof(double) * 2 * cap);
         o.stat = a.take(sizeof(double) * 2 * cap);
+        const bool multi = c.resampler == PF_RESAMPLE_MULTINOMIAL;
         if (c.flags & PF_FLAG_DEBUG_ARRAYS) {
             o.dbga = a.take(sizeof(int32_t) * N);
-            o.dbgc = a.take(cdf_b * N);
+            if (!multi) o.dbgc = a.take(cdf_b * N);
+        }
+        if (multi) {
+            o.cdf = a.take(cdf_b * N + 16);
+            e.any_pull = true;
         }
         TrackerDev &T = e.h_trk[i];
         fill_tracker_constants(c, T);
@@ -253,6 +259,11 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
             T.dbg_anc = reinterpret_cast<int32_t *>(e.d_arena + o.dbga);
             T.dbg_cdf = e.d_arena + o.dbgc;
         }
+        if (e.cfg[i].resampler == PF_RESAMPLE_MULTINOMIAL) {
+            // written by the CDF kernel, read by the pull kernel and by pf_get_debug
+            T.cdf = e.d_arena + o.cdf;
+            T.dbg_cdf = T.cdf;
+        }
         for (int k = 0; k < T.ntiles; ++k) tile_trk[T.tile_begin + k] = i;
         st[i] = initial_state(e.cfg[i]);
         e.h_frames[i].active = 1;
@@ -297,7 +308,8 @@ static pf_status engine_launch(Engine &e, const uint8_t *override_frame, int64_t
     L.total_tiles = e.total_tiles;
     L.frame_override = override_frame;
     L.pitch_override = override_pitch;
-    const int rc = launch_step(e.prec, L, e.grid, e.stream);
+    int rc = launch_step(e.prec, L, e.grid, e.stream);
+    if (rc == 0 && e.any_pull) rc = launch_pull(e.prec, L, e.grid, e.stream);
     if (rc != 0) { cudaGetLastError(); return e.fail(PF_ERR_CUDA); }
     return PF_OK;
 }
@@ -345,8 +357,10 @@ static pf_status engine_run_resident(Engine &e, int32_t count) {
         cudaGraph_t g = nullptr;
         cudaError_t err = cudaStreamBeginCapture(e.capture_stream, cudaStreamCaptureModeThreadLocal);
         int rc = 0;
-        for (int32_t i = 0; i < count && err == cudaSuccess && rc == 0; ++i)
+        for (int32_t i = 0; i < count && err == cudaSuccess && rc == 0; ++i) {
             rc = launch_step(e.prec, L, e.grid, e.capture_stream);
+            if (rc == 0 && e.any_pull) rc = launch_pull(e.prec, L, e.grid, e.capture_stream);
+        }
         const cudaError_t end = cudaStreamEndCapture(e.capture_stream, &g);
         if (err == cudaSuccess) err = end;
         if (err == cudaSuccess && rc != 0) err = cudaErrorLaunchFailure;

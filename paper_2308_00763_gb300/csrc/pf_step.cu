@@ -24,6 +24,14 @@
 //      particles).
 // Frame t = 0 has no resampling: every particle starts at the initial position.
 //
+// Multinomial trackers (Sec. 3: each ancestor drawn from the categorical distribution of
+// the weights) are skipped by the step kernel and take two more launches per frame (the
+// same code in other modes): the CDF kernel runs phase 1 up to the CDF and writes it to
+// T.cdf; the pull kernel then gives each offspring j the first particle whose CDF value
+// reaches an independent uniform v_j (a binary search over T.cdf), gathers its position
+// from the previous frame and runs phases 2-5 for it (likelihood always evaluated from
+// the frame).
+//
 // Scan boundaries.  The prefix between tiles is an exact 128-bit fixed-point sum of
 // the tiles' aggregates, so every tile obtains the same boundary value whichever
 // predecessors its lookback visits.  Inside a tile the prefix is an FP scan made
@@ -40,6 +48,10 @@
 
 #include "pf_device.cuh"
 #include "pf_internal.h"
+
+// The pull kernel's offspring have no likelihood table (window width 0), so its bounds
+// tests against the window compare unsigned values with a constant 0.
+#pragma nv_diag_suppress 186
 
 namespace pfk {
 
@@ -493,6 +505,17 @@ __device__ U128 lookback(const LookbackDesc *look, int lt, uint64_t tag, Tracker
     return total;
 }
 
+// Multinomial ancestor: the first k with C[k] >= u (n - 1 if none), C non-decreasing.
+template <typename A>
+__device__ __forceinline__ int cdf_lower_bound(const A *C, int n, A u) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = lo + ((hi - lo) >> 1);
+        if (__ldg(C + mid) >= u) hi = mid; else lo = mid + 1;
+    }
+    return lo < n ? lo : n - 1;
+}
+
 // First index e in [0, n) with J[e] > j (J non-decreasing, J[n-1] > j).
 __device__ __forceinline__ int upper_index(const int32_t *J, int n, int j) {
     int lo = 0, hi = n - 1;
@@ -587,8 +610,15 @@ __device__ void finalize_tracker(const TrackerDev &T, TrackerState *st, StepSmem
     }
 }
 
-template <int P>
+// Kernel modes: the step kernel (systematic and stratified trackers, every phase), and for
+// multinomial trackers the CDF kernel (phase 1 up to the CDF, written to T.cdf) and the
+// pull kernel (resampling from T.cdf, phases 2-5), launched in that order.
+constexpr int kModeStep = 0, kModeCdf = 1, kModePull = 2;
+
+// One tile of a launch in mode kMode (trackers of the other modes are skipped).
+template <int P, int kMode>
 __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
+    constexpr bool kPull = kMode == kModePull;
     using Tr = Prec<P>;
     using pos_t = typename Tr::pos_t;
     using lik_t = typename Tr::lik_t;
@@ -634,12 +664,20 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
     const TrackerDev &T = sm.trk;
     if (!sm.fr.active) return;
     if (sm.st.status & kStatusTimeout) return;   // a failed step: results are invalid
+    if constexpr (kMode == kModeStep) {
+        if (T.resampler == kResampleMultinomial) return;
+    } else {
+        if (T.resampler != kResampleMultinomial) return;
+    }
 
     const int N = static_cast<int>(T.N);
     const int lt = g - (Lp.tile_prefix ? __ldg(&Lp.tile_prefix[ti]) : T.tile_begin);
     const int k0 = lt * T.tile;
     const int cnt = (N - k0) < T.tile ? (N - k0) : T.tile;
     const int64_t t = sm.st.t;
+    if constexpr (kMode == kModeCdf) {
+        if (t == 0) return;                        // frame 0 resamples nothing
+    }
     const uint64_t dtag = desc_tag(sm.st.epoch);    // this launch's lookback tag
     constexpr bool kF64 = sizeof(acc_t) == 8;    // REF64; the other kernels use no FP64
     const int nxi = sm.st.nxi, nyi = sm.st.nyi;     // anchor of the offspring
@@ -669,7 +707,7 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
     // bounding box of the ancestors with non-negligible weight (absolute pixel units)
     float bx0 = FLT_MAX, bx1 = -FLT_MAX, by0 = FLT_MAX, by1 = -FLT_MAX;
     const int eb = tid * kItems;  // blocked arrangement: thread tid owns elements eb .. eb+kItems-1
-    if (t > 0) {
+    if (!kPull && t > 0) {
         const lik_t *__restrict__ Lin = static_cast<const lik_t *>(T.pl[in]);
         const pos_t *__restrict__ Xin = static_cast<const pos_t *>(T.px[in]);
         const pos_t *__restrict__ Yin = static_cast<const pos_t *>(T.py[in]);
@@ -779,8 +817,9 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
     // ------------------------------------------------------------ 1b. likelihood window
     // The bounding box of the heavy ancestors, widened by the drift and 3.5 sigma of the
     // draw: almost all of their offspring's pixels fall inside it.  Computed before the
-    // lookback, so that the predecessors publish meanwhile.
-    {
+    // lookback, so that the predecessors publish meanwhile.  (Only the step kernel has a
+    // table: the pull kernel's offspring take the direct route.)
+    if constexpr (kMode == kModeStep) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             bx0 = fminf(bx0, __shfl_xor_sync(0xffffffffu, bx0, o));
@@ -831,7 +870,9 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
         }
         __syncthreads();
     }
-    const int wx0 = sm.win_x0, wy0 = sm.win_y0, ww = sm.win_w, wh = sm.win_h;
+    const bool no_table = kMode != kModeStep;
+    const int wx0 = no_table ? 0 : sm.win_x0, wy0 = no_table ? 0 : sm.win_y0;
+    const int ww = no_table ? 0 : sm.win_w, wh = no_table ? 0 : sm.win_h;
     const int cells = ww * wh;
 
     using H = typename std::conditional<Tr::kHalf, pos_t, __half>::type;
@@ -848,7 +889,7 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
     const acc_t den = kF64 ? static_cast<acc_t>(T.den) : static_cast<acc_t>(T.denf);
 
     // ------------------------------------------------------------ 1c. likelihood table
-    if (cells > 0) {
+    if (kMode == kModeStep && cells > 0) {
         // stage the frame region the window's templates cover (clamped to the frame);
         // warp w takes rows w, w + kWarps, ...; its lanes walk the row
         const int rx0 = wx0 - r, ry0 = wy0 - r, rw = ww + 2 * r, rh = wh + 2 * r;
@@ -887,7 +928,8 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
             }
         }
         __syncthreads();
-        for (int c = tid, cy = tid / ww, cx = tid - (tid / ww) * ww; c < cells; c += kThreads) {
+        const int wdiv = kMode == kModeStep ? ww : 1;   // (a table in the step kernel only)
+        for (int c = tid, cy = tid / wdiv, cx = tid - (tid / wdiv) * wdiv; c < cells; c += kThreads) {
             if constexpr (Tr::kHalf) {
                 if (use_off) sm.table[c] = hk.from_offsets(sm.u.term + cy * rw + cx, sm.toff, T.D);
                 else sm.table[c] = hk.from_terms(sm.u.term, rw, sm.w, r, cx, cy);
@@ -910,7 +952,10 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
     // ------------------------------------------------------------ 1d. lookback, CDF, strata
     int Jr[kItems];           // J of the thread's elements (frames t > 0)
     int jb, je;               // the tile's offspring are j in [jb, je)
-    if (t > 0) {
+    if (!kPull && t > 0) {
+        // the step kernel's window phase ordered the tile aggregate (sm.agg_x) before this
+        // point; the CDF kernel has no window phase
+        if constexpr (kMode == kModeCdf) __syncthreads();
         const acc_t invS = kF64 ? static_cast<acc_t>(sm.st.invS) : static_cast<acc_t>(sm.st.invS_f);
         const acc_t u0 = kF64 ? static_cast<acc_t>(sm.u0d) : static_cast<acc_t>(sm.u0f);
         const acc_t inv_n = sizeof(acc_t) == 8 ? static_cast<acc_t>(T.inv_n) : static_cast<acc_t>(T.inv_n_f);
@@ -923,6 +968,21 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
         acc_t excl, pend;
         if constexpr (kF64) { excl = from_fixed(exclx); pend = from_fixed(endx); }
         else { excl = from_fixed_f(exclx); pend = from_fixed_f(endx); }
+        if constexpr (kMode == kModeCdf) {
+            acc_t *const cdf = static_cast<acc_t *>(T.cdf);
+#pragma unroll
+            for (int m = 0; m < kItems; ++m) {
+                const int e = eb + m;
+                if (e < cnt) {
+                    const int k = k0 + e;
+                    const acc_t Pk = (e == cnt - 1) ? pend : fmin(add_rn(excl, loc[m]), pend);
+                    acc_t C = fmin(mul_rn(Pk, invS), static_cast<acc_t>(1));
+                    if (k == N - 1) C = static_cast<acc_t>(1);
+                    cdf[k] = C;
+                }
+            }
+            return;                       // the pull kernel takes the offspring
+        }
         // J of the tile's first element and of each element, for either resampling scheme
         const auto count_strata = [&](const auto &str) {
             if (tid == 0) sm.jbeg = (lt == 0) ? 0 : str.count_le(fmin(mul_rn(excl, invS), static_cast<acc_t>(1)));
@@ -947,7 +1007,7 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
                 Jr[m] = J;
             }
         };
-        if (T.resampler == 1) {
+        if (T.resampler == kResampleStratified) {
             // (key_lo, key_hi, frame t - 1, tracker id) of the stratum offsets
             Strata<acc_t, true> str;
             str.init(N, static_cast<acc_t>(0.5), inv_n, sm.skeys);   // u0 = 1/2 only centres the estimate
@@ -972,7 +1032,7 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
     // map[j - jb] = 1 + tile element that is the ancestor of offspring j: a head at the
     // first offspring of every element with offspring (the map was cleared at the start of
     // the tile), then a block-wide running max fills the gaps.
-    const bool use_map = (t > 0) && nout <= kMapMax;
+    const bool use_map = !kPull && (t > 0) && nout <= kMapMax;
     if (use_map) {
         int jpt = __shfl_up_sync(0xffffffffu, Jr[kItems - 1], 1);   // J of element eb - 1
         if (lane == 0) jpt = (tid == 0) ? jb : sm.J[eb - 1];
@@ -1037,6 +1097,10 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
     const float shx = static_cast<float>(axi_anc - nxi), shy = static_cast<float>(ayi_anc - nyi);
     const float ix0 = T.init_xf - static_cast<float>(nxi), iy0 = T.init_yf - static_cast<float>(nyi);
 
+    // the previous frame's positions (the pull kernel gathers its ancestors from them)
+    const pos_t *__restrict__ pXin = static_cast<const pos_t *>(T.px[in]);
+    const pos_t *__restrict__ pYin = static_cast<const pos_t *>(T.py[in]);
+
     // One pair of offspring (j0, j1) = (2q, 2q + 1).  Compile-time flags: V0 / V1, the
     // particle lies in [jb, je); FAST, frame t > 0 with the ancestor map and no debug
     // arrays (the interior pairs of a tile in production take the FAST copy).
@@ -1051,7 +1115,22 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
             if (!v0) e0 = e1;
             if (!v1) e1 = e0;
         } else if (t > 0) {
-            if (use_map) {
+            if constexpr (kPull) {
+                // multinomial: offspring j draws v_j (word j mod 4 of Philox(j / 4, t - 1, 1,
+                // tracker)) and takes the first particle whose CDF value reaches it (global
+                // indices into the previous frame)
+                const uint4 wv = philox4x32_10(make_uint4(static_cast<uint32_t>(q) >> 1, tctr - 1u, 1u, trk_id),
+                                               key_lo, key_hi);
+                const uint32_t w0 = (q & 1) ? wv.z : wv.x, w1 = (q & 1) ? wv.w : wv.y;
+                const acc_t *cdf = static_cast<const acc_t *>(T.cdf);
+                if constexpr (kF64) {
+                    if (v0) e0 = cdf_lower_bound(cdf, N, uniform_f64(w0));
+                    if (v1) e1 = cdf_lower_bound(cdf, N, uniform_f64(w1));
+                } else {
+                    if (v0) e0 = cdf_lower_bound(cdf, N, uniform_f32(w0));
+                    if (v1) e1 = cdf_lower_bound(cdf, N, uniform_f32(w1));
+                }
+            } else if (use_map) {
                 e0 = v0 ? static_cast<int>(sm.map[j0 - jb]) - 1 : 0;
                 e1 = v1 ? static_cast<int>(sm.map[j1 - jb]) - 1 : 0;
             } else {
@@ -1061,8 +1140,9 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
             if (!v0) e0 = e1;
             if (!v1) e1 = e0;
             if (dbg_anc) {
-                if (v0) dbg_anc[j0] = k0 + e0;
-                if (v1) dbg_anc[j1] = k0 + e1;
+                const int base = kPull ? 0 : k0;
+                if (v0) dbg_anc[j0] = base + e0;
+                if (v1) dbg_anc[j1] = base + e1;
             }
         }
         // one Philox block per particle pair: words (x, y) for j0, (z, w) for j1
@@ -1071,7 +1151,10 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
         if constexpr (!Tr::kHalf) {
             // ---------------- REF64 / F32: absolute positions, exact-integer likelihood
             acc_t xa0, ya0, xa1, ya1;
-            if (t > 0) { xa0 = sm.ax[e0]; ya0 = sm.ay[e0]; xa1 = sm.ax[e1]; ya1 = sm.ay[e1]; }
+            if (t > 0) {
+                if constexpr (kPull) { xa0 = pXin[e0]; ya0 = pYin[e0]; xa1 = pXin[e1]; ya1 = pYin[e1]; }
+                else { xa0 = sm.ax[e0]; ya0 = sm.ay[e0]; xa1 = sm.ax[e1]; ya1 = sm.ay[e1]; }
+            }
             else {
                 xa0 = xa1 = kF64 ? static_cast<acc_t>(T.init_x) : static_cast<acc_t>(T.init_xf);
                 ya0 = ya1 = kF64 ? static_cast<acc_t>(T.init_y) : static_cast<acc_t>(T.init_yf);
@@ -1122,8 +1205,13 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
             using h2 = typename OPS::h2;
             h2 ox, oy;
             if (t > 0) {
-                ox = OPS::pack(sm.ax[e0], sm.ax[e1]);
-                oy = OPS::pack(sm.ay[e0], sm.ay[e1]);
+                if constexpr (kPull) {
+                    ox = OPS::pack(pXin[e0], pXin[e1]);
+                    oy = OPS::pack(pYin[e0], pYin[e1]);
+                } else {
+                    ox = OPS::pack(sm.ax[e0], sm.ax[e1]);
+                    oy = OPS::pack(sm.ay[e0], sm.ay[e1]);
+                }
                 if (shx != 0.0f || shy != 0.0f) {
                     ox = __hadd2(ox, OPS::from_f2(shx, shx));
                     oy = __hadd2(oy, OPS::from_f2(shy, shy));
@@ -1204,7 +1292,7 @@ template <int P> struct MinBlocks {
     static constexpr int value = (P == 0 ? 512 : 1024) / kThreads > 0 ? (P == 0 ? 512 : 1024) / kThreads : 1;
 };
 
-template <int P>
+template <int P, int kMode>
 __global__ void __launch_bounds__(kThreads, MinBlocks<P>::value) step_kernel(const StepLaunch Lp) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StepSmem<P> &sm = *reinterpret_cast<StepSmem<P> *>(smem_raw);
@@ -1219,7 +1307,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<P>::value) step_kernel(con
                 atomicExch(Lp.ticket, 0u);
             return;
         }
-        run_tile<P>(Lp, static_cast<int>(g), sm);
+        run_tile<P, kMode>(Lp, static_cast<int>(g), sm);
         __syncthreads();
     }
 }
@@ -1244,12 +1332,14 @@ int configure_and_grid(int total_tiles) {
                   "shared memory of the step kernel exceeds its CTAs per SM");
     if (sizeof(StepSmem<P>) + 1024 > 228 * 1024) return -1;
     const int bytes = static_cast<int>(sizeof(StepSmem<P>));
-    if (cudaFuncSetAttribute(step_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess)
+    if (cudaFuncSetAttribute(step_kernel<P, kModeStep>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess ||
+        cudaFuncSetAttribute(step_kernel<P, kModeCdf>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess ||
+        cudaFuncSetAttribute(step_kernel<P, kModePull>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess)
         return -1;
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel<P>, kThreads, bytes);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel<P, kModeStep>, kThreads, bytes);
     if (per_sm < 1) per_sm = 1;
     const int g = sms * per_sm;
     return total_tiles < g ? total_tiles : g;
@@ -1302,17 +1392,27 @@ int step_grid_size(int precision, int total_tiles) {
     return -1;
 }
 
-int launch_step(int precision, const StepLaunch &L, int grid, void *stream) {
+template <int kMode>
+int launch_mode(int precision, const StepLaunch &L, int grid, void *stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (grid < 1) grid = 1;
     switch (precision) {
-        case 0: step_kernel<0><<<grid, kThreads, sizeof(StepSmem<0>), s>>>(L); break;
-        case 1: step_kernel<1><<<grid, kThreads, sizeof(StepSmem<1>), s>>>(L); break;
-        case 2: step_kernel<2><<<grid, kThreads, sizeof(StepSmem<2>), s>>>(L); break;
-        case 3: step_kernel<3><<<grid, kThreads, sizeof(StepSmem<3>), s>>>(L); break;
+        case 0: step_kernel<0, kMode><<<grid, kThreads, sizeof(StepSmem<0>), s>>>(L); break;
+        case 1: step_kernel<1, kMode><<<grid, kThreads, sizeof(StepSmem<1>), s>>>(L); break;
+        case 2: step_kernel<2, kMode><<<grid, kThreads, sizeof(StepSmem<2>), s>>>(L); break;
+        case 3: step_kernel<3, kMode><<<grid, kThreads, sizeof(StepSmem<3>), s>>>(L); break;
         default: return -1;
     }
     return static_cast<int>(cudaGetLastError());
+}
+
+int launch_step(int precision, const StepLaunch &L, int grid, void *stream) {
+    return launch_mode<kModeStep>(precision, L, grid, stream);
+}
+
+int launch_pull(int precision, const StepLaunch &L, int grid, void *stream) {
+    const int rc = launch_mode<kModeCdf>(precision, L, grid, stream);
+    return rc != 0 ? rc : launch_mode<kModePull>(precision, L, grid, stream);
 }
 
 int launch_wait_probe(void *d_desc, void *d_state, uint32_t limit, void *stream) {

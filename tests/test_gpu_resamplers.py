@@ -1,12 +1,14 @@
-"""Stratified resampling (pf_config.resampler = PF_RESAMPLE_STRATIFIED) on the GPU.
+"""Alternative resampling schemes on the GPU (pf_config.resampler).
 
-The fused step with one independent offset per stratum, u_j = (j + v_j) / N (Sec. 2 names
-stratified resampling beside the paper's systematic scheme of Sec. 3).  The checks: the
-ancestors are exactly the oracle's stratified resampling of the CDF the step computed, with
-the offsets drawn by the oracle's own Philox; the REF64 track equals the oracle's FP64
-stratified track within 1e-9 px; offspring counts stay within two strata of N w_k; the
-option takes effect; stratified and systematic trackers share a batch, each equal to its
-own single run; the bench's launch configuration (2^20 particles) resamples exactly.
+Stratified: the fused step with one independent offset per stratum, u_j = (j + v_j) / N
+(Sec. 2 names stratified resampling beside the paper's systematic scheme of Sec. 3).
+Multinomial: the step kernel writes the CDF, the pull kernel gives offspring j the first
+particle whose CDF value reaches an independent uniform v_j (Sec. 3's categorical draw).
+The checks: the ancestors are exactly the oracle's resampling of the CDF the step computed,
+with the draws from the oracle's own Philox; the REF64 track equals the oracle's FP64 track
+of the same scheme within 1e-9 px; stratified offspring counts stay within two strata of
+N w_k; the option takes effect; the schemes share a batch, each tracker equal to its own
+single run; the bench's launch configuration (2^20 particles) resamples exactly.
 """
 import numpy as np
 import pytest
@@ -122,3 +124,75 @@ def test_stratified_full_size_ancestors_exact(pf, prec):
     anc, C = _last_step(pf, v, N, prec, 1)
     offs = oracle.stratified_offsets(1, v.T - 2, N, 0)
     assert np.array_equal(anc, oracle.resample_stratified(C, offs, "f64" if prec == "ref64" else "f32"))
+
+
+# ----------------------------------------------------------------------------- multinomial
+@pytest.mark.parametrize("prec", ["ref64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("N", [1, 3, TILE + 1, 3 * TILE + 17])
+def test_multinomial_ancestors_exact(pf, prec, N):
+    v = synth.make_video(128, 128, 4, 5, noise=5.0, seed=43)
+    anc, C = _last_step(pf, v, N, prec, 19, tracker=5, resampler="multinomial")
+    assert np.all(np.diff(C) >= 0) and C[-1] == 1.0
+    draws = oracle.stratified_offsets(19, v.T - 2, N, 5)
+    assert np.array_equal(anc, oracle.resample_multinomial(C, draws, "f64" if prec == "ref64" else "f32"))
+
+
+def test_multinomial_ref64_track_within_1e9(pf):
+    v = synth.make_video(128, 128, 10, 5, noise=5.0, seed=1)
+    for N in (1000, 3 * TILE + 17):
+        est_o, M_o, _ = oracle.track(v.frames, N, 5, init=tuple(v.centres[0]), seed=1, resampler="multinomial")
+        f = pf.Filter(v.W, v.H, N, 5, "ref64", init=tuple(v.centres[0]), seed=1, resampler="multinomial")
+        f.run(_frames(v))
+        est, ms = f.estimates(0, v.T, with_stats=True)
+        f.close()
+        assert np.abs(est - est_o).max() <= 1e-9, N
+        assert np.array_equal(ms[:, 0], M_o)
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16"])
+def test_multinomial_tracks_the_truth_and_steps_equal_runs(pf, prec):
+    """Free-running multinomial tracks stay within half a pixel of the oracle's FP64
+    multinomial track (RMSE); single steps equal a graph-replayed run bit for bit."""
+    v = synth.make_video(128, 128, 10, 5, noise=5.0, seed=1)
+    est_o, _, _ = oracle.track(v.frames, 1000, 5, init=tuple(v.centres[0]), seed=1, resampler="multinomial")
+    fr = _frames(v)
+    a = pf.Filter(v.W, v.H, 1000, 5, prec, init=tuple(v.centres[0]), seed=1, resampler="multinomial")
+    a.run(fr)
+    b = pf.Filter(v.W, v.H, 1000, 5, prec, init=tuple(v.centres[0]), seed=1, resampler="multinomial")
+    for t in range(v.T):
+        b.step(fr[t])
+    ea, eb = a.estimates(0, v.T), b.estimates(0, v.T)
+    a.close()
+    b.close()
+    assert np.array_equal(ea, eb)
+    assert np.sqrt(np.mean(np.sum((ea - est_o) ** 2, axis=1))) <= 0.5
+
+
+def test_all_schemes_in_one_batch_equal_singles(pf):
+    vids = [synth.make_video(96, 96, 5, 3, noise=5.0, seed=70 + i, v=(1.0, -1.0)) for i in range(4)]
+    Ns = [3000, 2 * TILE + 5, 777, 5000]
+    rs = ["multinomial", "systematic", "stratified", "multinomial"]
+    for prec in ("ref64", "f32", "f16"):
+        cfgs = [pf.make_config(v.W, v.H, n, v.radius, prec, init=tuple(v.centres[0]), seed=80 + i,
+                               tracker_id=i, resampler=r) for i, (v, n, r) in enumerate(zip(vids, Ns, rs))]
+        b = pf.Batch(cfgs)
+        fr = [_frames(v) for v in vids]
+        for t in range(5):
+            b.step([f[t] for f in fr])
+        got = np.stack([b.estimates(t) for t in range(5)], axis=1)
+        b.close()
+        for i, (v, n, r) in enumerate(zip(vids, Ns, rs)):
+            s = pf.Filter(v.W, v.H, n, v.radius, prec, init=tuple(v.centres[0]), seed=80 + i, tracker_id=i,
+                          resampler=r)
+            s.run(fr[i])
+            assert np.array_equal(s.estimates(0, 5), got[i]), (prec, i, r)
+            s.close()
+
+
+@pytest.mark.parametrize("prec", ["ref64", "f16"])
+def test_multinomial_full_size_ancestors_exact(pf, prec):
+    v = synth.make_video(512, 512, 3, 5, noise=5.0, seed=1)
+    N = 1 << 20
+    anc, C = _last_step(pf, v, N, prec, 1, resampler="multinomial")
+    draws = oracle.stratified_offsets(1, v.T - 2, N, 0)
+    assert np.array_equal(anc, oracle.resample_multinomial(C, draws, "f64" if prec == "ref64" else "f32"))
