@@ -589,9 +589,10 @@ def _paper_workload(dev, stream):
 
 
 def _resamplers(dev, stream):
-    """Systematic (the paper's scheme, Sec. 3) against stratified resampling (one offset per
-    stratum, Sec. 2) on the headline workload: us per frame and the track's RMSE against
-    the ground truth, per precision."""
+    """Systematic (the paper's scheme, Sec. 3) against stratified (one offset per stratum,
+    Sec. 2) and multinomial resampling (independent draws searched in the CDF; CDF and pull
+    kernels) on the headline workload: us per frame and the track's RMSE against the
+    ground truth, per precision."""
     import torch
     import paper_2308_00763_gb300 as pf
     from paper_2308_00763_gb300 import synth
@@ -601,7 +602,7 @@ def _resamplers(dev, stream):
     out = {}
     for prec in ("ref64", "f32", "f16"):
         row = {}
-        for rs in ("systematic", "stratified"):
+        for rs in ("systematic", "stratified", "multinomial"):
             f = pf.Filter(W_, H_, N_, R_, prec, init=tuple(v.centres[0]), seed=SEED_, stream=stream, resampler=rs)
             f.run(fr[:4])
             best = None
@@ -619,7 +620,8 @@ def _resamplers(dev, stream):
             row[rs] = {"us_per_frame": best, "value": N_ / (best * 1e-6),
                        "rmse_px_vs_truth": _rmse(f.estimates(0, T_), v.centres)}
             f.close()
-        row["stratified_over_systematic_time"] = row["stratified"]["us_per_frame"] / row["systematic"]["us_per_frame"]
+        for rs in ("stratified", "multinomial"):
+            row[rs + "_over_systematic_time"] = row[rs]["us_per_frame"] / row["systematic"]["us_per_frame"]
         out[prec] = row
     return {"workload": WORKLOAD, "unit": METRIC, "by_precision": out}
 
