@@ -28,9 +28,9 @@
 // the weights) are skipped by the step kernel and take two more launches per frame (the
 // same code in other modes): the CDF kernel runs phase 1 up to the CDF and writes it to
 // T.cdf; the pull kernel then gives each offspring j the first particle whose CDF value
-// reaches an independent uniform v_j (a binary search over T.cdf), gathers its position
-// from the previous frame and runs phases 2-5 for it (likelihood always evaluated from
-// the frame).
+// reaches an independent uniform v_j (a binary search over T.cdf), gathers the ancestors'
+// positions of its tile's offspring into shared memory, sizes the likelihood window by
+// them and runs phases 2-5 as the step kernel does.
 //
 // Scan boundaries.  The prefix between tiles is an exact 128-bit fixed-point sum of
 // the tiles' aggregates, so every tile obtains the same boundary value whichever
@@ -505,17 +505,6 @@ __device__ U128 lookback(const LookbackDesc *look, int lt, uint64_t tag, Tracker
     return total;
 }
 
-// Multinomial ancestor: the first k with C[k] >= u (n - 1 if none), C non-decreasing.
-template <typename A>
-__device__ __forceinline__ int cdf_lower_bound(const A *C, int n, A u) {
-    int lo = 0, hi = n;
-    while (lo < hi) {
-        const int mid = lo + ((hi - lo) >> 1);
-        if (__ldg(C + mid) >= u) hi = mid; else lo = mid + 1;
-    }
-    return lo < n ? lo : n - 1;
-}
-
 // First index e in [0, n) with J[e] > j (J non-decreasing, J[n-1] > j).
 __device__ __forceinline__ int upper_index(const int32_t *J, int n, int j) {
     int lo = 0, hi = n - 1;
@@ -809,6 +798,57 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
                 sm.agg_x = ax;
             }
         }
+    } else if (kPull && t > 0) {
+        // The pull kernel's gather: offspring j = k0 + e takes the first particle a whose
+        // CDF value reaches v_j (word j mod 4 of Philox(j / 4, t - 1, 1, tracker)); the
+        // eight searches of a thread advance together.  a goes to J[e], the ancestor's
+        // position (previous frame) to ax/ay[e], and the box of the gathered positions
+        // sizes the likelihood window as in the step kernel.
+        const acc_t *cdf = static_cast<const acc_t *>(T.cdf);
+        const pos_t *__restrict__ Xin = static_cast<const pos_t *>(T.px[in]);
+        const pos_t *__restrict__ Yin = static_cast<const pos_t *>(T.py[in]);
+        acc_t uq[kItems];
+        int lo[kItems], hi[kItems];
+#pragma unroll
+        for (int h = 0; h < kItems; h += 4) {
+            const uint32_t blk = static_cast<uint32_t>(k0 + eb + h) >> 2;   // k0 + eb is a multiple of 8
+            const uint4 wv = philox4x32_10(make_uint4(blk, static_cast<uint32_t>(t - 1), 1u, T.tracker_id),
+                                           T.key_lo, T.key_hi);
+            const uint32_t ws[4] = {wv.x, wv.y, wv.z, wv.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                if constexpr (kF64) uq[h + i] = uniform_f64(ws[i]); else uq[h + i] = uniform_f32(ws[i]);
+                lo[h + i] = 0;
+                hi[h + i] = (eb + h + i < cnt) ? N : 0;
+            }
+        }
+        for (bool more = true; more;) {           // first k with C_k >= u, in [lo, hi]
+            more = false;
+#pragma unroll
+            for (int m = 0; m < kItems; ++m) {
+                if (lo[m] < hi[m]) {
+                    const int mid = lo[m] + ((hi[m] - lo[m]) >> 1);
+                    if (__ldg(cdf + mid) >= uq[m]) hi[m] = mid; else lo[m] = mid + 1;
+                    more = true;
+                }
+            }
+        }
+        const float sx = Tr::kHalf ? static_cast<float>(axi_anc) : 0.0f;
+        const float sy = Tr::kHalf ? static_cast<float>(ayi_anc) : 0.0f;
+#pragma unroll
+        for (int m = 0; m < kItems; ++m) {
+            const int e = eb + m;
+            if (e < cnt) {
+                const int a = lo[m] < N ? lo[m] : N - 1;
+                const pos_t xa = Xin[a], ya = Yin[a];
+                sm.J[e] = a;
+                sm.ax[e] = xa;
+                sm.ay[e] = ya;
+                const float xf = static_cast<float>(to_acc(xa)) + sx, yf = static_cast<float>(to_acc(ya)) + sy;
+                bx0 = fminf(bx0, xf); bx1 = fmaxf(bx1, xf);
+                by0 = fminf(by0, yf); by1 = fmaxf(by1, yf);
+            }
+        }
     } else {
         bx0 = bx1 = T.init_xf;
         by0 = by1 = T.init_yf;
@@ -817,9 +857,9 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
     // ------------------------------------------------------------ 1b. likelihood window
     // The bounding box of the heavy ancestors, widened by the drift and 3.5 sigma of the
     // draw: almost all of their offspring's pixels fall inside it.  Computed before the
-    // lookback, so that the predecessors publish meanwhile.  (Only the step kernel has a
-    // table: the pull kernel's offspring take the direct route.)
-    if constexpr (kMode == kModeStep) {
+    // lookback, so that the predecessors publish meanwhile.  (The pull kernel sizes it by
+    // the gathered ancestors; the CDF kernel has none.)
+    if constexpr (kMode != kModeCdf) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             bx0 = fminf(bx0, __shfl_xor_sync(0xffffffffu, bx0, o));
@@ -870,7 +910,7 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
         }
         __syncthreads();
     }
-    const bool no_table = kMode != kModeStep;
+    const bool no_table = kMode == kModeCdf;
     const int wx0 = no_table ? 0 : sm.win_x0, wy0 = no_table ? 0 : sm.win_y0;
     const int ww = no_table ? 0 : sm.win_w, wh = no_table ? 0 : sm.win_h;
     const int cells = ww * wh;
@@ -889,7 +929,7 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
     const acc_t den = kF64 ? static_cast<acc_t>(T.den) : static_cast<acc_t>(T.denf);
 
     // ------------------------------------------------------------ 1c. likelihood table
-    if (kMode == kModeStep && cells > 0) {
+    if (kMode != kModeCdf && cells > 0) {
         // stage the frame region the window's templates cover (clamped to the frame);
         // warp w takes rows w, w + kWarps, ...; its lanes walk the row
         const int rx0 = wx0 - r, ry0 = wy0 - r, rw = ww + 2 * r, rh = wh + 2 * r;
@@ -928,7 +968,7 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
             }
         }
         __syncthreads();
-        const int wdiv = kMode == kModeStep ? ww : 1;   // (a table in the step kernel only)
+        const int wdiv = kMode != kModeCdf ? ww : 1;    // (no table in the CDF kernel)
         for (int c = tid, cy = tid / wdiv, cx = tid - (tid / wdiv) * wdiv; c < cells; c += kThreads) {
             if constexpr (Tr::kHalf) {
                 if (use_off) sm.table[c] = hk.from_offsets(sm.u.term + cy * rw + cx, sm.toff, T.D);
@@ -1097,10 +1137,6 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
     const float shx = static_cast<float>(axi_anc - nxi), shy = static_cast<float>(ayi_anc - nyi);
     const float ix0 = T.init_xf - static_cast<float>(nxi), iy0 = T.init_yf - static_cast<float>(nyi);
 
-    // the previous frame's positions (the pull kernel gathers its ancestors from them)
-    const pos_t *__restrict__ pXin = static_cast<const pos_t *>(T.px[in]);
-    const pos_t *__restrict__ pYin = static_cast<const pos_t *>(T.py[in]);
-
     // One pair of offspring (j0, j1) = (2q, 2q + 1).  Compile-time flags: V0 / V1, the
     // particle lies in [jb, je); FAST, frame t > 0 with the ancestor map and no debug
     // arrays (the interior pairs of a tile in production take the FAST copy).
@@ -1116,20 +1152,10 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
             if (!v1) e1 = e0;
         } else if (t > 0) {
             if constexpr (kPull) {
-                // multinomial: offspring j draws v_j (word j mod 4 of Philox(j / 4, t - 1, 1,
-                // tracker)) and takes the first particle whose CDF value reaches it (global
-                // indices into the previous frame)
-                const uint4 wv = philox4x32_10(make_uint4(static_cast<uint32_t>(q) >> 1, tctr - 1u, 1u, trk_id),
-                                               key_lo, key_hi);
-                const uint32_t w0 = (q & 1) ? wv.z : wv.x, w1 = (q & 1) ? wv.w : wv.y;
-                const acc_t *cdf = static_cast<const acc_t *>(T.cdf);
-                if constexpr (kF64) {
-                    if (v0) e0 = cdf_lower_bound(cdf, N, uniform_f64(w0));
-                    if (v1) e1 = cdf_lower_bound(cdf, N, uniform_f64(w1));
-                } else {
-                    if (v0) e0 = cdf_lower_bound(cdf, N, uniform_f32(w0));
-                    if (v1) e1 = cdf_lower_bound(cdf, N, uniform_f32(w1));
-                }
+                // multinomial: the ancestors were gathered into ax/ay at the tile's own
+                // output positions (J holds their indices)
+                e0 = j0 - k0;
+                e1 = j1 - k0;
             } else if (use_map) {
                 e0 = v0 ? static_cast<int>(sm.map[j0 - jb]) - 1 : 0;
                 e1 = v1 ? static_cast<int>(sm.map[j1 - jb]) - 1 : 0;
@@ -1140,9 +1166,13 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
             if (!v0) e0 = e1;
             if (!v1) e1 = e0;
             if (dbg_anc) {
-                const int base = kPull ? 0 : k0;
-                if (v0) dbg_anc[j0] = base + e0;
-                if (v1) dbg_anc[j1] = base + e1;
+                if constexpr (kPull) {
+                    if (v0) dbg_anc[j0] = sm.J[e0];
+                    if (v1) dbg_anc[j1] = sm.J[e1];
+                } else {
+                    if (v0) dbg_anc[j0] = k0 + e0;
+                    if (v1) dbg_anc[j1] = k0 + e1;
+                }
             }
         }
         // one Philox block per particle pair: words (x, y) for j0, (z, w) for j1
@@ -1151,10 +1181,7 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
         if constexpr (!Tr::kHalf) {
             // ---------------- REF64 / F32: absolute positions, exact-integer likelihood
             acc_t xa0, ya0, xa1, ya1;
-            if (t > 0) {
-                if constexpr (kPull) { xa0 = pXin[e0]; ya0 = pYin[e0]; xa1 = pXin[e1]; ya1 = pYin[e1]; }
-                else { xa0 = sm.ax[e0]; ya0 = sm.ay[e0]; xa1 = sm.ax[e1]; ya1 = sm.ay[e1]; }
-            }
+            if (t > 0) { xa0 = sm.ax[e0]; ya0 = sm.ay[e0]; xa1 = sm.ax[e1]; ya1 = sm.ay[e1]; }
             else {
                 xa0 = xa1 = kF64 ? static_cast<acc_t>(T.init_x) : static_cast<acc_t>(T.init_xf);
                 ya0 = ya1 = kF64 ? static_cast<acc_t>(T.init_y) : static_cast<acc_t>(T.init_yf);
@@ -1205,13 +1232,8 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
             using h2 = typename OPS::h2;
             h2 ox, oy;
             if (t > 0) {
-                if constexpr (kPull) {
-                    ox = OPS::pack(pXin[e0], pXin[e1]);
-                    oy = OPS::pack(pYin[e0], pYin[e1]);
-                } else {
-                    ox = OPS::pack(sm.ax[e0], sm.ax[e1]);
-                    oy = OPS::pack(sm.ay[e0], sm.ay[e1]);
-                }
+                ox = OPS::pack(sm.ax[e0], sm.ax[e1]);
+                oy = OPS::pack(sm.ay[e0], sm.ay[e1]);
                 if (shx != 0.0f || shy != 0.0f) {
                     ox = __hadd2(ox, OPS::from_f2(shx, shx));
                     oy = __hadd2(oy, OPS::from_f2(shy, shy));
