@@ -90,6 +90,25 @@ def test_config1_half_track_rmse(pf, prec, flags):
     assert rmse <= 0.5, rmse
 
 
+@pytest.mark.parametrize("N", [128, 32768])
+def test_paper_motion_workload_tracks(pf, N):
+    """The paper's own workload (Sec. 4): 512x512 video of a disk moving (+1, +2) px per
+    frame, motion model x ~ N(x + 1, 5^2), y ~ N(y + 2, 2^2) (Eq. 1-2), at the paper's
+    particle counts: the REF64 track equals the oracle's within 1e-9 px, the F32 track
+    within 1e-3 px at 128 particles, and the F16 track's RMSE is within 0.5 px."""
+    v = synth.make_video(512, 512, 30, 5, noise=5.0, seed=1, v=(1.0, 2.0))
+    kw = dict(sigma=(5.0, 2.0), drift=(1.0, 2.0))
+    est_o, M_o, _ = oracle.track(v.frames, N, 5, init=tuple(v.centres[0]), seed=1, **kw)
+    _, est, ms = _run_gpu(pf, v, N, "ref64", seed=1, **kw)
+    assert np.abs(est - est_o).max() <= 1e-9
+    assert np.array_equal(ms[:, 0], M_o)
+    if N == 128:
+        _, est32, _ = _run_gpu(pf, v, N, "f32", seed=1, **kw)
+        assert np.abs(est32 - est_o).max() <= 1e-3
+    _, est16, _ = _run_gpu(pf, v, N, "f16", seed=1, **kw)
+    assert math.sqrt(np.mean(np.sum((est16 - est_o) ** 2, axis=1))) <= 0.5
+
+
 def test_host_and_device_frames_agree(pf):
     v = synth.make_video(96, 80, 6, 4, noise=5.0, seed=7, v=(1.5, 1.0))
     _, e1, _ = _run_gpu(pf, v, 3000, "f32", on_device=True)
