@@ -88,10 +88,11 @@ struct Engine {
     int32_t *d_tile_trk = nullptr;
     uint32_t *d_ticket = nullptr;
     char *d_arena = nullptr;
-    int total_tiles = 0;
+    int total_tiles = 0;               // tiles of the step kernel's trackers (systematic, stratified)
+    int pull_tiles = 0;                // tiles of the multinomial trackers (CDF and pull kernels)
     int grid = 0;
+    int grid_pull = 0;
     int ctas_cap = 0;                  // CTAs per SM (0: as many as fit)
-    bool any_pull = false;             // a multinomial tracker: each frame also launches the pull kernel
     pf_status sticky = PF_OK;
     uint8_t *d_frame_buf = nullptr;    // single tracker: staging of host frames
     TrackerState *h_init_pinned = nullptr;  // initial state of every tracker (pf_reset)
@@ -173,7 +174,9 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
     std::vector<Off> off(n);
     // the trackers' states form one array (the kernel indexes it by tracker)
     const size_t states_off = a.take(sizeof(TrackerState) * n);
-    int64_t tiles = 0;
+    // Tiles are numbered per kernel family: the step kernel's trackers first, then the
+    // multinomial trackers (CDF and pull kernels), so no launch carries tiles it skips.
+    int64_t tiles = 0, mtiles = 0;
     for (int i = 0; i < n; ++i) {
         const pf_config &c = cfgs[i];
         const int64_t N = c.num_particles;
@@ -184,7 +187,7 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
         const int64_t nt64 = (N + tile - 1) / tile;
         if (nt64 > 0x7fffffff) return PF_ERR_ARG;
         const int nt = static_cast<int>(nt64);
-        if (tiles + nt > 0x7fffffff) return PF_ERR_ARG;
+        if (tiles + mtiles + nt > 0x7fffffff) return PF_ERR_ARG;
         const int cap = c.est_capacity ? c.est_capacity : 4096;
         Off &o = off[i];
         for (int s = 0; s < 2; ++s) {
@@ -203,20 +206,18 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
             o.dbga = a.take(sizeof(int32_t) * N);
             if (!multi) o.dbgc = a.take(cdf_b * N);
         }
-        if (multi) {
-            o.cdf = a.take(cdf_b * N + 16);
-            e.any_pull = true;
-        }
+        if (multi) o.cdf = a.take(cdf_b * N + 16);
         TrackerDev &T = e.h_trk[i];
         fill_tracker_constants(c, T);
-        T.tile_begin = static_cast<int32_t>(tiles);
+        T.tile_begin = static_cast<int32_t>(multi ? mtiles : tiles);
         T.tile = tile;
         T.ntiles = nt;
         T.est_cap = cap;
         T.window = tun.window;
-        tiles += nt;
+        (multi ? mtiles : tiles) += nt;
     }
     e.total_tiles = static_cast<int>(tiles);
+    e.pull_tiles = static_cast<int>(mtiles);
     a.size = a.used + 256;
 
     cudaError_t err = cudaMalloc(reinterpret_cast<void **>(&e.d_arena), a.size);
@@ -224,7 +225,8 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
     err = cudaMemsetAsync(e.d_arena, 0, a.size, e.stream);
     if (err == cudaSuccess) err = cudaMalloc(reinterpret_cast<void **>(&e.d_trk), sizeof(TrackerDev) * n);
     if (err == cudaSuccess) err = cudaMalloc(reinterpret_cast<void **>(&e.d_frames), sizeof(FrameRef) * n);
-    if (err == cudaSuccess) err = cudaMalloc(reinterpret_cast<void **>(&e.d_tile_trk), sizeof(int32_t) * e.total_tiles);
+    if (err == cudaSuccess)
+        err = cudaMalloc(reinterpret_cast<void **>(&e.d_tile_trk), sizeof(int32_t) * (e.total_tiles + e.pull_tiles + 1));
     if (err == cudaSuccess) err = cudaMalloc(reinterpret_cast<void **>(&e.d_ticket), sizeof(uint32_t));
     if (err == cudaSuccess) err = cudaMallocHost(reinterpret_cast<void **>(&e.h_frames_pinned), sizeof(FrameRef) * n);
     if (err == cudaSuccess) err = cudaMallocHost(reinterpret_cast<void **>(&e.h_init_pinned), sizeof(TrackerState) * n);
@@ -239,7 +241,7 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
         engine_free(e);
         return err == cudaErrorMemoryAllocation ? PF_ERR_OOM : PF_ERR_CUDA;
     }
-    std::vector<int32_t> tile_trk(e.total_tiles);
+    std::vector<int32_t> tile_trk(e.total_tiles + e.pull_tiles + 1);   // step family, then pull family
     std::vector<TrackerState> st(n);
     for (int i = 0; i < n; ++i) {
         TrackerDev &T = e.h_trk[i];
@@ -264,13 +266,14 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
             T.cdf = e.d_arena + o.cdf;
             T.dbg_cdf = T.cdf;
         }
-        for (int k = 0; k < T.ntiles; ++k) tile_trk[T.tile_begin + k] = i;
+        const int base = (e.cfg[i].resampler == PF_RESAMPLE_MULTINOMIAL) ? e.total_tiles : 0;
+        for (int k = 0; k < T.ntiles; ++k) tile_trk[base + T.tile_begin + k] = i;
         st[i] = initial_state(e.cfg[i]);
         e.h_frames[i].active = 1;
     }
     err = cudaMemcpyAsync(e.d_trk, e.h_trk.data(), sizeof(TrackerDev) * n, cudaMemcpyHostToDevice, e.stream);
     if (err == cudaSuccess)
-        err = cudaMemcpyAsync(e.d_tile_trk, tile_trk.data(), sizeof(int32_t) * e.total_tiles,
+        err = cudaMemcpyAsync(e.d_tile_trk, tile_trk.data(), sizeof(int32_t) * tile_trk.size(),
                               cudaMemcpyHostToDevice, e.stream);
     if (err == cudaSuccess) err = cudaMemsetAsync(e.d_ticket, 0, sizeof(uint32_t), e.stream);
     memcpy(e.h_init_pinned, st.data(), sizeof(TrackerState) * n);
@@ -283,15 +286,36 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
     }
     if (err == cudaSuccess) err = cudaStreamSynchronize(e.stream);   // host vectors go out of scope
     if (err != cudaSuccess) { cudaGetLastError(); engine_free(e); return PF_ERR_CUDA; }
-    e.grid = step_grid_size(e.prec, e.total_tiles);
-    if (e.grid < 1) { engine_free(e); return PF_ERR_CUDA; }   // no launchable kernel for this precision
+    e.grid = e.total_tiles ? step_grid_size(e.prec, e.total_tiles) : 0;
+    e.grid_pull = e.pull_tiles ? step_grid_size(e.prec, e.pull_tiles) : 0;
+    if ((e.total_tiles && e.grid < 1) || (e.pull_tiles && e.grid_pull < 1)) {
+        engine_free(e);
+        return PF_ERR_CUDA;                  // no launchable kernel for this precision
+    }
     if (e.ctas_cap > 0) {
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms > 0) e.grid = std::min(e.grid, sms * e.ctas_cap);
+        if (sms > 0) {
+            e.grid = std::min(e.grid, sms * e.ctas_cap);
+            e.grid_pull = std::min(e.grid_pull, sms * e.ctas_cap);
+        }
     }
     return PF_OK;
+}
+
+// One frame's launches: the step kernel over its family's tiles, then, for multinomial
+// trackers, the CDF and pull kernels over theirs (tile table entries after the step
+// family's).  L carries the step family's table and count.
+static int engine_enqueue(const Engine &e, StepLaunch L, cudaStream_t stream) {
+    int rc = 0;
+    if (e.total_tiles > 0) rc = launch_step(e.prec, L, e.grid, stream);
+    if (rc == 0 && e.pull_tiles > 0) {
+        L.tile_trk = e.d_tile_trk + e.total_tiles;
+        L.total_tiles = e.pull_tiles;
+        rc = launch_pull(e.prec, L, e.grid_pull, stream);
+    }
+    return rc;
 }
 
 static pf_status engine_launch(Engine &e, const uint8_t *override_frame, int64_t override_pitch) {
@@ -308,9 +332,7 @@ static pf_status engine_launch(Engine &e, const uint8_t *override_frame, int64_t
     L.total_tiles = e.total_tiles;
     L.frame_override = override_frame;
     L.pitch_override = override_pitch;
-    int rc = launch_step(e.prec, L, e.grid, e.stream);
-    if (rc == 0 && e.any_pull) rc = launch_pull(e.prec, L, e.grid, e.stream);
-    if (rc != 0) { cudaGetLastError(); return e.fail(PF_ERR_CUDA); }
+    if (engine_enqueue(e, L, e.stream) != 0) { cudaGetLastError(); return e.fail(PF_ERR_CUDA); }
     return PF_OK;
 }
 
@@ -357,10 +379,8 @@ static pf_status engine_run_resident(Engine &e, int32_t count) {
         cudaGraph_t g = nullptr;
         cudaError_t err = cudaStreamBeginCapture(e.capture_stream, cudaStreamCaptureModeThreadLocal);
         int rc = 0;
-        for (int32_t i = 0; i < count && err == cudaSuccess && rc == 0; ++i) {
-            rc = launch_step(e.prec, L, e.grid, e.capture_stream);
-            if (rc == 0 && e.any_pull) rc = launch_pull(e.prec, L, e.grid, e.capture_stream);
-        }
+        for (int32_t i = 0; i < count && err == cudaSuccess && rc == 0; ++i)
+            rc = engine_enqueue(e, L, e.capture_stream);
         const cudaError_t end = cudaStreamEndCapture(e.capture_stream, &g);
         if (err == cudaSuccess) err = end;
         if (err == cudaSuccess && rc != 0) err = cudaErrorLaunchFailure;

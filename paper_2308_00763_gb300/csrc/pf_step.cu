@@ -25,8 +25,8 @@
 // Frame t = 0 has no resampling: every particle starts at the initial position.
 //
 // Multinomial trackers (Sec. 3: each ancestor drawn from the categorical distribution of
-// the weights) are skipped by the step kernel and take two more launches per frame (the
-// same code in other modes): the CDF kernel runs phase 1 up to the CDF and writes it to
+// the weights) are not in the step kernel's launch; they take two other launches per
+// frame (the same code in other modes): the CDF kernel runs phase 1 up to the CDF and writes it to
 // T.cdf; the pull kernel then gives each offspring j the first particle whose CDF value
 // reaches an independent uniform v_j (a binary search over T.cdf), gathers the ancestors'
 // positions of its tile's offspring into shared memory, sizes the likelihood window by
@@ -653,9 +653,9 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
     const TrackerDev &T = sm.trk;
     if (!sm.fr.active) return;
     if (sm.st.status & kStatusTimeout) return;   // a failed step: results are invalid
-    if constexpr (kMode == kModeStep) {
-        if (T.resampler == kResampleMultinomial) return;
-    } else {
+    // (the host gives each launch only its own family's tiles; the CDF and pull kernels
+    // check as well)
+    if constexpr (kMode != kModeStep) {
         if (T.resampler != kResampleMultinomial) return;
     }
 
