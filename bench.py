@@ -53,6 +53,8 @@ def _args():
     p.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     p.add_argument("--no-sweep", action="store_true", help="skip the precision/size sweep and the paper workload")
     p.add_argument("--serve-seconds", type=float, default=20.0, help="length of the served-streams run")
+    p.add_argument("--resampler", default="systematic", choices=["systematic", "stratified", "multinomial"],
+                   help="resampling scheme of the timed filters (the paper's is systematic)")
     p.add_argument("--tpb-sweep", action="store_true",
                    help="thread-block study: build the step kernel at 128/256/512/1024 threads per CTA and time each")
     p.add_argument("--tpb-child", action="store_true", help=argparse.SUPPRESS)
@@ -268,7 +270,8 @@ def run_ours(args):
     results = {}
     tracks = {}
     for prec in precs:
-        f = pf.Filter(W_, H_, N_, R_, prec, init=init, seed=SEED_ + rank, tracker_id=rank, stream=stream)
+        f = pf.Filter(W_, H_, N_, R_, prec, init=init, seed=SEED_ + rank, tracker_id=rank, stream=stream,
+                      resampler=args.resampler)
         for _ in range(args.warmup):
             f.reset()
             f.run(frames_dev)
@@ -341,6 +344,7 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": DTYPE_NAME[hp], "data": "synthetic",
         "config": {"workload": WORKLOAD, "frames_per_step": T, "particles": N_, "precision": hp,
+                   "resampler": args.resampler,
                    "l2": "flushed between timed steps (512 MiB write); state stays L2-resident across the frames of a step",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
@@ -350,7 +354,7 @@ def run_ours(args):
                      "launch_us_median": head["launch_us_median"]},
         "e2e": {"value": head["e2e_value"], "unit": METRIC, "h2d_bytes_per_step": int(W_ * H_ * T),
                 "d2h_bytes_per_step": int(16 * T)},
-        "gpu_launches": args.steps * T,
+        "gpu_launches": args.steps * T * (3 if args.resampler == "multinomial" else 1),
         "accuracy": {"rmse_px_vs_ref64_gpu": head["rmse_px_vs_ref64_gpu"],
                      "rmse_px_vs_ground_truth": results_truth.get(hp)},
         "per_precision": {p: {k: r[k] for k in ("value", "ms_per_step", "launch_us_median", "e2e_value",
