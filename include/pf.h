@@ -206,7 +206,7 @@ pf_status pf_debug_philox(const uint32_t *ctrs, int64_t n, uint64_t seed, uint32
  * the call synchronises the stream and writes the new frame's scalars there (its t is
  * state_in->t + 1, its est_x/est_y the estimate of this frame).
  * Everything else the step needs (lookback descriptors, per-tile sums, counters, the
- * tracker descriptor) lives in one 256 KiB array in the library's device memory, present
+ * tracker descriptor) lives in one array (about 170 KiB) in the library's device memory, present
  * on every GPU from the moment the library is loaded until the process exits; it limits
  * num_particles to 2^22 (PF_ERR_ARG beyond).  The first call on each device looks up that
  * array's address, so make it before any stream capture.  All calls share the array and
