@@ -223,16 +223,6 @@ __device__ __forceinline__ void stats_add2(Stats<A> &a, bool v0, A L0, A dx0, A 
     a.sy += e0 * dy0 + e1 * dy1;
 }
 
-template <typename A>
-__device__ __forceinline__ Stats<A> stats_shfl_xor(const Stats<A> &a, int o) {
-    Stats<A> b;
-    b.m = __shfl_xor_sync(0xffffffffu, a.m, o);
-    b.s = __shfl_xor_sync(0xffffffffu, a.s, o);
-    b.sx = __shfl_xor_sync(0xffffffffu, a.sx, o);
-    b.sy = __shfl_xor_sync(0xffffffffu, a.sy, o);
-    return b;
-}
-
 // Pixel of a position (reading C3): floor(v) + (v - floor(v) >= 0.5).  For |v| below
 // 2^22 (float) or 2^51 (double) this equals floor(v + 0.5): adding 1/2 is exact unless
 // it crosses into the next binade, which happens only when the fraction is >= 1/2 and
@@ -442,22 +432,41 @@ struct __align__(16) StepSmem {
     FrameRef fr;
 };
 
-// Block-wide merge of per-thread stats (a butterfly in each warp, then one over the
-// warps' results in warp 0; the merge is symmetric, so the result is deterministic);
-// result valid in thread 0.  The caller
-// synchronises before sm.red is written again.
+// Block-wide merge of per-thread stats, result valid in thread 0.  Each warp takes its
+// max of m (butterfly), rescales every lane's sums to it (one exp a lane) and adds them
+// (butterfly); warp 0 does the same over the warps' results.  Max, rescale and sums run
+// in a fixed order, so the result is deterministic.  The caller synchronises before
+// sm.red is written again.
+template <int P, typename A>
+__device__ __forceinline__ Stats<A> warp_stats(Stats<A> v) {
+    constexpr bool F = Prec<P>::kHalf;
+    A m = v.m;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const A y = __shfl_xor_sync(0xffffffffu, m, o);
+        m = y > m ? y : m;
+    }
+    if (m == neg_inf<A>()) return Stats<A>{m, 0, 0, 0};
+    const A sc = (v.m == neg_inf<A>()) ? static_cast<A>(0) : wexp<F>(v.m - m);
+    A s = mul_rn(v.s, sc), sx = mul_rn(v.sx, sc), sy = mul_rn(v.sy, sc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s = add_rn(s, __shfl_xor_sync(0xffffffffu, s, o));
+        sx = add_rn(sx, __shfl_xor_sync(0xffffffffu, sx, o));
+        sy = add_rn(sy, __shfl_xor_sync(0xffffffffu, sy, o));
+    }
+    return Stats<A>{m, s, sx, sy};
+}
+
 template <int P, typename A>
 __device__ Stats<A> block_stats(Stats<A> v, StepSmem<P> &sm) {
-    constexpr bool F = Prec<P>::kHalf;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) v = stats_merge<F>(v, stats_shfl_xor(v, o));
+    v = warp_stats<P>(v);
     if (lane == 0) sm.red[warp] = v;
     __syncthreads();
     if (warp == 0) {
         v = (lane < kWarps) ? sm.red[lane] : Stats<A>{neg_inf<A>(), 0, 0, 0};
-#pragma unroll
-        for (int o = 1; o < kWarps; o <<= 1) v = stats_merge<F>(v, stats_shfl_xor(v, o));
+        v = warp_stats<P>(v);
     }
     return v;
 }
