@@ -104,6 +104,24 @@ def test_stream_alone_equals_stream_in_mix(pf, prec):
     f.close()
 
 
+def test_stratified_stream_equals_filter_and_multinomial_is_refused(pf):
+    T = 6
+    vid, fr = _video(128, 96, T, 4, seed=73)
+    cfg = pf.make_config(vid.W, vid.H, 2 * 4096 + 3, vid.radius, "f16", init=tuple(vid.centres[0]), seed=9,
+                         tracker_id=4, est_capacity=64, resampler="stratified")
+    served = _serve_alone(pf, cfg, fr)
+    f = pf.Filter(vid.W, vid.H, cfg.num_particles, vid.radius, "f16", init=tuple(vid.centres[0]), seed=9,
+                  tracker_id=4, resampler="stratified")
+    f.run(fr)
+    assert np.array_equal(f.estimates(0, T), served)
+    f.close()
+    multi = pf.make_config(vid.W, vid.H, 1000, vid.radius, "f16", init=tuple(vid.centres[0]), resampler="multinomial")
+    s = pf.Server(1 << 28, max_streams=2, queue_depth=2)
+    with pytest.raises(pf.PfError):             # one kernel per tick: no multinomial streams
+        s.open(multi)
+    s.close()
+
+
 def test_host_frames_equal_device_frames(pf):
     T = 5
     vid, fr = _video(128, 96, T, 5, seed=70)

@@ -33,13 +33,14 @@ def pf():
 _TORCH_DTYPE = {"ref64": "float64", "f32": "float32", "f16": "float16", "bf16": "bfloat16"}
 
 
+@pytest.mark.parametrize("resampler", ["systematic", "stratified"])
 @pytest.mark.parametrize("prec", ["ref64", "f32", "f16", "bf16"])
-def test_noalloc_two_frames_match_filter(pf, prec):
+def test_noalloc_two_frames_match_filter(pf, prec, resampler):
     import torch
     N = 3 * 4096 + 11
     v = synth.make_video(160, 120, 2, 4, noise=5.0, seed=31, v=(1.0, -1.0))
     frames = torch.from_numpy(v.frames).cuda()
-    kw = dict(init=tuple(v.centres[0]), seed=77, tracker_id=2)
+    kw = dict(init=tuple(v.centres[0]), seed=77, tracker_id=2, resampler=resampler)
 
     # reference: a pf_filter handle
     f = pf.Filter(v.W, v.H, N, 4, prec, **kw)
@@ -74,6 +75,15 @@ def test_noalloc_two_frames_match_filter(pf, prec):
     for got, name in zip(bufs[1], ("x", "y", "L")):
         g = got.float().cpu().numpy().astype(np.float64) if prec == "bf16" else got.cpu().numpy().astype(np.float64)
         np.testing.assert_allclose(g, st1[name], rtol=0, atol=tol if name != "L" else 1e-6)
+
+
+def test_noalloc_rejects_multinomial(pf):
+    """Multinomial resampling needs its CDF in device memory and two more kernels; the
+    allocation-free entry point takes systematic and stratified trackers only."""
+    cfg = pf.make_config(64, 64, 1000, 3, "f32", resampler="multinomial")
+    hdr = pf.PfStateHeader(magic=0x31534650, precision=cfg.precision, num_particles=1000, t=0)
+    with pytest.raises(pf.PfError):
+        pf.pf_step_frame_noalloc(cfg, hdr, 0, 0, 0, 1 << 20, 64, 1 << 20, 1 << 20, 1 << 20, stream=0)
 
 
 def test_noalloc_rejects_too_many_particles(pf):
