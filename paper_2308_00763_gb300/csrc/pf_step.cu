@@ -913,7 +913,9 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
                 wh = static_cast<int>(ceilf(by1 + myr)) - y0 + 1;
                 const int64_t cells = static_cast<int64_t>(ww) * wh;
                 const int64_t roi = static_cast<int64_t>(ww + 2 * r + 1) * (wh + 2 * r);
-                if (cells > kTableMax || cells > cnt || roi > kRoiMax) { ww = 0; wh = 0; }
+                // (a table is built even for fewer particles than cells: 81-odd global loads
+                // in a dependent chain per particle cost more than the table's shared loads)
+                if (cells > kTableMax || roi > kRoiMax) { ww = 0; wh = 0; }
             }
             sm.win_x0 = x0; sm.win_y0 = y0; sm.win_w = ww; sm.win_h = wh;
         }
