@@ -196,3 +196,15 @@ def test_multinomial_full_size_ancestors_exact(pf, prec):
     anc, C = _last_step(pf, v, N, prec, 1, resampler="multinomial")
     draws = oracle.stratified_offsets(1, v.T - 2, N, 0)
     assert np.array_equal(anc, oracle.resample_multinomial(C, draws, "f64" if prec == "ref64" else "f32"))
+
+
+@pytest.mark.parametrize("scheme,N", [("stratified", 1 << 24), ("multinomial", 1 << 22)])
+def test_alternative_schemes_at_large_sizes(pf, scheme, N):
+    """1024x1024, r = 10: stratified at N = 2^24 (the sweep's largest configuration, and in
+    FP32 the largest N whose points stay ordered), multinomial at 2^22 (the oracle's N
+    binary searches stay within seconds): every ancestor exact."""
+    v = synth.make_video(1024, 1024, 3, 10, noise=15.0, seed=3)
+    anc, C = _last_step(pf, v, N, "f16", 3, resampler=scheme)
+    draws = oracle.stratified_offsets(3, v.T - 2, N, 0)
+    fn = oracle.resample_stratified if scheme == "stratified" else oracle.resample_multinomial
+    assert np.array_equal(anc, fn(C, draws, "f32"))
