@@ -5,10 +5,20 @@
 #include <stddef.h>
 #include <string.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "pf.h"
 #include "pf_internal.h"
 
 namespace pfk {
+
+// NVTX range over an entry point (visible to Nsight tools; a no-op without one attached).
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
 
 // bytes of one stored position / likelihood value
 inline size_t pos_bytes(int prec) { return prec == PF_REF64 ? 8 : prec == PF_F32 ? 4 : 2; }

@@ -514,6 +514,7 @@ pf_status pf_create(const pf_config *cfg, void *cuda_stream, pf_filter **out) {
 }
 
 pf_status pf_step_frame(pf_filter *f, const uint8_t *frame, int64_t pitch_bytes, int32_t frame_on_device) {
+    TraceRange trace("pf_step_frame");
     if (!f || !frame) return PF_ERR_ARG;
     Engine &e = f->e;
     if (e.sticky != PF_OK) return PF_ERR_STATE;
@@ -536,6 +537,7 @@ pf_status pf_step_frame(pf_filter *f, const uint8_t *frame, int64_t pitch_bytes,
 
 pf_status pf_run_frames(pf_filter *f, const uint8_t *frames, int64_t pitch_bytes, int64_t frame_stride,
                         int32_t count, int32_t frames_on_device) {
+    TraceRange trace("pf_run_frames");
     if (!f || !frames || count < 0) return PF_ERR_ARG;
     Engine &e = f->e;
     if (e.sticky != PF_OK) return PF_ERR_STATE;
@@ -779,6 +781,7 @@ pf_status pf_batch_create(const pf_config *cfgs, int32_t n, void *cuda_stream, p
 
 pf_status pf_batch_step(pf_batch *b, const uint8_t *const *frames, const int64_t *pitches,
                         const uint8_t *active_mask) {
+    TraceRange trace("pf_batch_step");
     if (!b || !frames || !pitches) return PF_ERR_ARG;
     Engine &e = b->e;
     if (e.sticky != PF_OK) return PF_ERR_STATE;
@@ -832,6 +835,7 @@ pf_status pf_batch_set_videos(pf_batch *b, const uint8_t *const *videos, const i
 }
 
 pf_status pf_batch_run(pf_batch *b, int32_t count) {
+    TraceRange trace("pf_batch_run");
     if (!b || count < 0) return PF_ERR_ARG;
     Engine &e = b->e;
     if (e.sticky != PF_OK) return PF_ERR_STATE;
@@ -983,6 +987,7 @@ static pf_status sweep_shapes(std::vector<pf_config> cfgs, const std::vector<con
 
 pf_status pf_autotune(const pf_config *cfg, int32_t copies, const uint8_t *video, int64_t pitch_bytes,
                       int64_t frame_stride, int32_t n_frames, pf_tuning *best, double *best_us_per_frame) {
+    TraceRange trace("pf_autotune");
     if (!best || check_config(cfg) != PF_OK || copies < 1 || copies > 4096 || !video || n_frames < 1) return PF_ERR_ARG;
     if (pitch_bytes < cfg->width || frame_stride < pitch_bytes * cfg->height) return PF_ERR_ARG;
     std::vector<pf_config> cfgs(copies, *cfg);
@@ -997,6 +1002,7 @@ pf_status pf_autotune(const pf_config *cfg, int32_t copies, const uint8_t *video
 
 pf_status pf_autotune_batch(const pf_config *cfgs, int32_t n, const uint8_t *const *videos, const int64_t *pitches,
                             const int64_t *frame_strides, int32_t n_frames, pf_tuning *best, double *best_us_per_frame) {
+    TraceRange trace("pf_autotune_batch");
     if (!best || !cfgs || n < 1 || !videos || !pitches || !frame_strides || n_frames < 1) return PF_ERR_ARG;
     for (int i = 0; i < n; ++i) {
         if (check_config(&cfgs[i]) != PF_OK || cfgs[i].precision != cfgs[0].precision || !videos[i]) return PF_ERR_ARG;

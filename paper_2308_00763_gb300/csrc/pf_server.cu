@@ -511,6 +511,7 @@ pf_status pf_server_poll(pf_server *S, int32_t *completed) {
 }
 
 pf_status pf_server_tick(pf_server *S, int32_t *launched) {
+    TraceRange trace("pf_server_tick");
     if (!S) return PF_ERR_ARG;
     if (launched) *launched = 0;
     if (S->sticky != PF_OK) return PF_ERR_STATE;
@@ -631,6 +632,7 @@ pf_status pf_server_destroy(pf_server *S) {
 }
 
 pf_status pf_server_replay(pf_server *S, const pf_trace_event *ev, int64_t n, int32_t n_streams, int32_t realtime) {
+    TraceRange trace("pf_server_replay");
     if (!S || (n > 0 && !ev) || n < 0 || n_streams < 0) return PF_ERR_ARG;
     if (S->sticky != PF_OK) return PF_ERR_STATE;
     std::vector<int32_t> sid(n_streams, -2);   // -2 never opened, -1 refused / closed
