@@ -42,7 +42,8 @@ typedef enum {
     PF_ERR_OOM = 2,        /* device or pinned memory could not be allocated */
     PF_ERR_CUDA = 3,       /* a CUDA runtime call or kernel launch failed */
     PF_ERR_TIMEOUT = 4,    /* a bounded device-side wait gave up (results of that step are invalid) */
-    PF_ERR_STATE = 5,      /* the handle failed earlier, or the call does not fit its state */
+    PF_ERR_STATE = 5,      /* the handle failed earlier, or the call does not fit its state
+                              (also: a checked build, -DPF_CHECKED, found an index out of range) */
     PF_ERR_ADMISSION = 6   /* serving: a stream was refused by the memory or compute budget */
 } pf_status;
 

@@ -175,8 +175,13 @@ def _study_threads():
     return int(v) if v else None
 
 
+def _checked() -> bool:
+    """The checked build (PF_CHECKED=1 in the environment)."""
+    return os.environ.get("PF_CHECKED", "") not in ("", "0")
+
+
 def library_path() -> str:
-    return _build.lib_path(_study_threads())
+    return _build.lib_path(_study_threads(), _checked())
 
 
 def lib(build_if_missing: bool = False):
@@ -188,7 +193,7 @@ def lib(build_if_missing: bool = False):
         path = library_path()
         if not os.path.exists(path):
             if build_if_missing:
-                _build.build(threads=_study_threads())
+                _build.build(threads=_study_threads(), checked=_checked())
             else:
                 raise RuntimeError("the CUDA library %s is not built; run "
                                    "`python -c 'import __graft_entry__ as g; g.build()'`" % path)

@@ -38,35 +38,45 @@ def deps():
 STUDY_THREADS = (128, 256, 512, 1024)   # threads per CTA of the step kernel's study builds
 
 
-def lib_path(threads: int | None = None) -> str:
-    """The library, or the thread-block study build with `threads` threads per CTA."""
+def lib_path(threads: int | None = None, checked: bool = False) -> str:
+    """The library, the thread-block study build with `threads` threads per CTA, or the
+    checked build (index tests in the kernels, -DPF_CHECKED)."""
+    if checked:
+        return os.path.join(BUILD, "checked", "libpf_gb300.so")
     if not threads or threads == 512:
         return LIB
     return os.path.join(BUILD, "t%d" % threads, "libpf_gb300.so")
 
 
-def up_to_date(threads: int | None = None) -> bool:
-    lib = lib_path(threads)
+def up_to_date(threads: int | None = None, checked: bool = False) -> bool:
+    lib = lib_path(threads, checked)
     if not os.path.exists(lib):
         return False
     t = os.path.getmtime(lib)
     return all(os.path.getmtime(d) <= t for d in deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra=(), threads: int | None = None) -> str:
-    """Build the library (512 threads per CTA), or with `threads` in STUDY_THREADS a
-    separate study build under _build/t<threads>/ (-DPF_STEP_THREADS)."""
+def build(force: bool = False, verbose: bool = False, extra=(), threads: int | None = None,
+          checked: bool = False) -> str:
+    """Build the library (512 threads per CTA); with `threads` in STUDY_THREADS a separate
+    study build under _build/t<threads>/ (-DPF_STEP_THREADS); with `checked` the checked
+    build under _build/checked/ (-DPF_CHECKED: every kernel index that is in range by
+    construction is tested, a miss fails the step with PF_ERR_STATE instead of faulting)."""
     if threads and threads not in STUDY_THREADS:
         raise ValueError("threads per CTA must be one of %s" % (STUDY_THREADS,))
-    lib = lib_path(threads)
-    if not force and up_to_date(threads):
+    if threads and checked:
+        raise ValueError("the checked build has the library's 512 threads per CTA")
+    lib = lib_path(threads, checked)
+    if not force and up_to_date(threads, checked):
         return lib
     bdir = os.path.dirname(lib)
     os.makedirs(bdir, exist_ok=True)
     cc = nvcc()
     flags = [ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
              "--expt-relaxed-constexpr", *extra]
-    if lib != LIB:
+    if checked:
+        flags.append("-DPF_CHECKED")
+    elif lib != LIB:
         flags.append("-DPF_STEP_THREADS=%d" % threads)
     if verbose:
         flags += ["-Xptxas", "-v"]

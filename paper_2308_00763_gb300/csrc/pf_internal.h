@@ -33,6 +33,7 @@ constexpr int kResampleMultinomial = 2;   // CDF by the step kernel, offspring b
 
 // Device status bits (sticky, per tracker).
 constexpr uint32_t kStatusTimeout = 0x1u;
+constexpr uint32_t kStatusBounds = 0x2u;    // checked builds: an index left its array (the access was redirected)
 
 // Lookback descriptor of one tile: its aggregate and its inclusive prefix, each an exact
 // 128-bit fixed-point value (value * 2^kFixShift; the inter-tile prefix then does not

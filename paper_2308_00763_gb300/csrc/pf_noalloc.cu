@@ -195,6 +195,7 @@ extern "C" pf_status pf_step_frame_noalloc(const pf_config *cfg, const pf_state_
         if (err == cudaSuccess) err = cudaStreamSynchronize(stream);
         if (err != cudaSuccess) { cudaGetLastError(); return PF_ERR_CUDA; }
         if (res.status & kStatusTimeout) return PF_ERR_TIMEOUT;
+        if (res.status & kStatusBounds) return PF_ERR_STATE;   // checked builds
         pf_state_header o;
         memset(&o, 0, sizeof o);
         o.magic = 0x31534650u;

@@ -472,6 +472,7 @@ static pf_status engine_sync_status(Engine &e) {
         err = cudaMemcpy(&status, &e.h_trk[i].state->status, sizeof status, cudaMemcpyDeviceToHost);
         if (err != cudaSuccess) { cudaGetLastError(); return e.fail(PF_ERR_CUDA); }
         if (status & kStatusTimeout) return e.fail(PF_ERR_TIMEOUT);
+        if (status & kStatusBounds) return e.fail(PF_ERR_STATE);   // checked builds
     }
     return PF_OK;
 }
@@ -764,6 +765,7 @@ pf_status pf_debug_wait_timeout(uint32_t spin_limit, uint32_t *status_out) {
     cudaFree(d);
     if (err != cudaSuccess) { cudaGetLastError(); return PF_ERR_CUDA; }
     *status_out = st.status;
+    if (st.status & kStatusBounds) return PF_ERR_STATE;   // checked builds
     return (st.status & kStatusTimeout) ? PF_ERR_TIMEOUT : PF_OK;
 }
 

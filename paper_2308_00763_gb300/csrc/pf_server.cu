@@ -343,6 +343,7 @@ pf_status check_status(pf_server *S) {
                 return S->fail(PF_ERR_CUDA);
             }
             if (status & kStatusTimeout) return S->fail(PF_ERR_TIMEOUT);
+            if (status & kStatusBounds) return S->fail(PF_ERR_STATE);   // checked builds
         }
     }
     return PF_OK;

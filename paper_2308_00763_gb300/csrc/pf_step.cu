@@ -87,6 +87,22 @@ __device__ __forceinline__ bool timed_out(const TrackerState *st) {
     return (ld_relaxed_u32(&st->status) & kStatusTimeout) != 0u;
 }
 
+// Checked builds (-DPF_CHECKED): every index below that is in range by construction is
+// tested; one out of range raises the tracker's bounds bit and is redirected to element 0
+// (the host then reports the step as failed).  Other builds use the index as it is.
+#ifdef PF_CHECKED
+__device__ __forceinline__ int checked_index(int i, int n, TrackerState *st) {
+    if (static_cast<unsigned>(i) >= static_cast<unsigned>(n)) {
+        atomicOr(&st->status, kStatusBounds);
+        return 0;
+    }
+    return i;
+}
+#define PF_IDX(i, n) checked_index((i), (n), st)
+#else
+#define PF_IDX(i, n) (i)
+#endif
+
 // ---- lookback descriptor words (see LookbackDesc): 16-bit launch tag | 48-bit payload
 constexpr uint64_t kPayload48 = (1ull << 48) - 1ull;
 
@@ -849,10 +865,10 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
             const int e = eb + m;
             if (e < cnt) {
                 const int a = lo[m] < N ? lo[m] : N - 1;
-                const pos_t xa = Xin[a], ya = Yin[a];
-                sm.J[e] = a;
-                sm.ax[e] = xa;
-                sm.ay[e] = ya;
+                const pos_t xa = Xin[PF_IDX(a, N)], ya = Yin[PF_IDX(a, N)];
+                sm.J[PF_IDX(e, kTile)] = a;
+                sm.ax[PF_IDX(e, kTile)] = xa;
+                sm.ay[PF_IDX(e, kTile)] = ya;
                 const float xf = static_cast<float>(to_acc(xa)) + sx, yf = static_cast<float>(to_acc(ya)) + sy;
                 bx0 = fminf(bx0, xf); bx1 = fmaxf(bx1, xf);
                 by0 = fminf(by0, yf); by1 = fmaxf(by1, yf);
@@ -949,11 +965,12 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
             const uint8_t *row = fv.p + static_cast<int64_t>(clampi(ry0 + yy, 0, fv.H - 1)) * fv.pitch;
             if constexpr (Tr::kHalf) {
                 for (int xx = lane; xx < rw; xx += 32)
-                    sm.u.term[yy * rw + xx] = hk.term(__ldg(row + clampi(rx0 + xx, 0, fv.W - 1)));
+                    sm.u.term[PF_IDX(yy * rw + xx, kRoiMax)] = hk.term(__ldg(row + clampi(rx0 + xx, 0, fv.W - 1)));
             } else {
                 // integer form: exclusive row prefix sums pre[y * (rw + 1) + x] = sum of the
                 // row's pixels 0 .. x-1 (uint16, modular), by a warp scan per 32 columns
-                uint16_t *pre = sm.u.pre + yy * (rw + 1);
+                const int last = yy * (rw + 1) + rw;      // the row's last prefix entry
+                uint16_t *pre = sm.u.pre + (PF_IDX(last, kRoiMax) == last ? last - rw : 0);
                 if (lane == 0) pre[0] = 0;
                 uint32_t carry = 0;
                 for (int x0 = 0; x0 < rw; x0 += 32) {
@@ -975,15 +992,15 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
             for (int k = tid; k < T.D; k += kThreads) {   // entry k: row i, column dx
                 int i = 0, c0 = 0, hw = sm.w[0];
                 while (c0 + 2 * hw + 1 <= k) { c0 += 2 * hw + 1; hw = sm.w[++i]; }
-                sm.toff[k] = static_cast<uint16_t>(i * rw + r + (k - c0 - hw));
+                sm.toff[PF_IDX(k, kOffMax)] = static_cast<uint16_t>(i * rw + r + (k - c0 - hw));
             }
         }
         __syncthreads();
         const int wdiv = kMode != kModeCdf ? ww : 1;    // (no table in the CDF kernel)
         for (int c = tid, cy = tid / wdiv, cx = tid - (tid / wdiv) * wdiv; c < cells; c += kThreads) {
             if constexpr (Tr::kHalf) {
-                if (use_off) sm.table[c] = hk.from_offsets(sm.u.term + cy * rw + cx, sm.toff, T.D);
-                else sm.table[c] = hk.from_terms(sm.u.term, rw, sm.w, r, cx, cy);
+                if (use_off) sm.table[PF_IDX(c, kTableMax)] = hk.from_offsets(sm.u.term + cy * rw + cx, sm.toff, T.D);
+                else sm.table[PF_IDX(c, kTableMax)] = hk.from_terms(sm.u.term, rw, sm.w, r, cx, cy);
             } else {
                 uint32_t ssum = 0;
 #pragma unroll 4
@@ -992,7 +1009,7 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
                     const int hw = sm.w[i];
                     ssum += static_cast<uint32_t>(static_cast<uint16_t>(p[hw + 1] - p[-hw]));
                 }
-                sm.table[c] = lik_from_sum<acc_t>(ssum, c1, c2D, den);
+                sm.table[PF_IDX(c, kTableMax)] = lik_from_sum<acc_t>(ssum, c1, c2D, den);
             }
             cx += kThreads;               // next cell: kThreads further in row-major order
             while (cx >= ww) { cx -= ww; ++cy; }
@@ -1029,7 +1046,7 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
                     const acc_t Pk = (e == cnt - 1) ? pend : fmin(add_rn(excl, loc[m]), pend);
                     acc_t C = fmin(mul_rn(Pk, invS), static_cast<acc_t>(1));
                     if (k == N - 1) C = static_cast<acc_t>(1);
-                    cdf[k] = C;
+                    cdf[PF_IDX(k, N)] = C;
                 }
             }
             return;                       // the pull kernel takes the offspring
@@ -1053,7 +1070,7 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
                     else J = str.count_le(C);
                     cprev = C;
                     jprev = J;
-                    if (dbg_cdf) dbg_cdf[k] = C;
+                    if (dbg_cdf) dbg_cdf[PF_IDX(k, N)] = C;
                 }
                 Jr[m] = J;
             }
@@ -1090,7 +1107,7 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
 #pragma unroll
         for (int m = 0; m < kItems; ++m) {
             const int jp = m ? Jr[m - 1] : jpt;
-            if (eb + m < cnt && Jr[m] > jp) sm.map[jp - jb] = static_cast<uint16_t>(eb + m + 1);
+            if (eb + m < cnt && Jr[m] > jp) sm.map[PF_IDX(jp - jb, kMapMax)] = static_cast<uint16_t>(eb + m + 1);
         }
         __syncthreads();
         // thread tid fills entries [tid*ch, tid*ch + ch), ch = 8 or 16 (16-byte vectors)
@@ -1157,8 +1174,8 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
         const int j0 = 2 * q, j1 = j0 + 1;
         int e0 = 0, e1 = 0;
         if (kFast) {
-            if (v0) e0 = static_cast<int>(sm.map[j0 - jb]) - 1;
-            if (v1) e1 = static_cast<int>(sm.map[j1 - jb]) - 1;
+            if (v0) e0 = static_cast<int>(sm.map[PF_IDX(j0 - jb, kMapMax)]) - 1;
+            if (v1) e1 = static_cast<int>(sm.map[PF_IDX(j1 - jb, kMapMax)]) - 1;
             if (!v0) e0 = e1;
             if (!v1) e1 = e0;
         } else if (t > 0) {
@@ -1168,8 +1185,8 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
                 e0 = j0 - k0;
                 e1 = j1 - k0;
             } else if (use_map) {
-                e0 = v0 ? static_cast<int>(sm.map[j0 - jb]) - 1 : 0;
-                e1 = v1 ? static_cast<int>(sm.map[j1 - jb]) - 1 : 0;
+                e0 = v0 ? static_cast<int>(sm.map[PF_IDX(j0 - jb, kMapMax)]) - 1 : 0;
+                e1 = v1 ? static_cast<int>(sm.map[PF_IDX(j1 - jb, kMapMax)]) - 1 : 0;
             } else {
                 if (v0) e0 = upper_index(sm.J, cnt, j0);
                 if (v1) e1 = (v0 && sm.J[e0] > j1) ? e0 : upper_index(sm.J, cnt, j1);
@@ -1178,11 +1195,11 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
             if (!v1) e1 = e0;
             if (dbg_anc) {
                 if constexpr (kPull) {
-                    if (v0) dbg_anc[j0] = sm.J[e0];
-                    if (v1) dbg_anc[j1] = sm.J[e1];
+                    if (v0) dbg_anc[PF_IDX(j0, N)] = sm.J[e0];
+                    if (v1) dbg_anc[PF_IDX(j1, N)] = sm.J[e1];
                 } else {
-                    if (v0) dbg_anc[j0] = k0 + e0;
-                    if (v1) dbg_anc[j1] = k0 + e1;
+                    if (v0) dbg_anc[PF_IDX(j0, N)] = k0 + e0;
+                    if (v1) dbg_anc[PF_IDX(j1, N)] = k0 + e1;
                 }
             }
         }
@@ -1192,7 +1209,10 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
         if constexpr (!Tr::kHalf) {
             // ---------------- REF64 / F32: absolute positions, exact-integer likelihood
             acc_t xa0, ya0, xa1, ya1;
-            if (t > 0) { xa0 = sm.ax[e0]; ya0 = sm.ay[e0]; xa1 = sm.ax[e1]; ya1 = sm.ay[e1]; }
+            if (t > 0) {
+                xa0 = sm.ax[PF_IDX(e0, kTile)]; ya0 = sm.ay[PF_IDX(e0, kTile)];
+                xa1 = sm.ax[PF_IDX(e1, kTile)]; ya1 = sm.ay[PF_IDX(e1, kTile)];
+            }
             else {
                 xa0 = xa1 = kF64 ? static_cast<acc_t>(T.init_x) : static_cast<acc_t>(T.init_xf);
                 ya0 = ya1 = kF64 ? static_cast<acc_t>(T.init_y) : static_cast<acc_t>(T.init_yf);
@@ -1223,18 +1243,18 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
             }
             if (v0 && v1) {
                 if constexpr (sizeof(acc_t) == 8) {
-                    reinterpret_cast<double2 *>(Xout)[q] = make_double2(x0, x1);
+                    reinterpret_cast<double2 *>(Xout)[PF_IDX(q, N / 2)] = make_double2(x0, x1);
                     reinterpret_cast<double2 *>(Yout)[q] = make_double2(y0, y1);
                     reinterpret_cast<double2 *>(Lout)[q] = make_double2(L0, L1);
                 } else {
-                    reinterpret_cast<float2 *>(Xout)[q] = make_float2(x0, x1);
+                    reinterpret_cast<float2 *>(Xout)[PF_IDX(q, N / 2)] = make_float2(x0, x1);
                     reinterpret_cast<float2 *>(Yout)[q] = make_float2(y0, y1);
                     reinterpret_cast<float2 *>(Lout)[q] = make_float2(L0, L1);
                 }
             } else if (v0) {
-                Xout[j0] = x0; Yout[j0] = y0; Lout[j0] = L0;
+                Xout[PF_IDX(j0, N)] = x0; Yout[j0] = y0; Lout[j0] = L0;
             } else if (v1) {
-                Xout[j1] = x1; Yout[j1] = y1; Lout[j1] = L1;
+                Xout[PF_IDX(j1, N)] = x1; Yout[j1] = y1; Lout[j1] = L1;
             }
             stats_add2<false>(stats, v0, L0, x0 - nxa_a, y0 - nya_a, v1, L1, x1 - nxa_a, y1 - nya_a);
         } else {
@@ -1243,8 +1263,8 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
             using h2 = typename OPS::h2;
             h2 ox, oy;
             if (t > 0) {
-                ox = OPS::pack(sm.ax[e0], sm.ax[e1]);
-                oy = OPS::pack(sm.ay[e0], sm.ay[e1]);
+                ox = OPS::pack(sm.ax[PF_IDX(e0, kTile)], sm.ax[PF_IDX(e1, kTile)]);
+                oy = OPS::pack(sm.ay[PF_IDX(e0, kTile)], sm.ay[PF_IDX(e1, kTile)]);
                 if (shx != 0.0f || shy != 0.0f) {
                     ox = __hadd2(ox, OPS::from_f2(shx, shx));
                     oy = __hadd2(oy, OPS::from_f2(shy, shy));
@@ -1269,13 +1289,13 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
             if (v0 && !in0) l0 = hk.at(fv, sm.w, px0, py0);
             if (v1 && !in1) l1 = hk.at(fv, sm.w, px1, py1);
             if (v0 && v1) {
-                reinterpret_cast<h2 *>(Xout)[q] = ox;
+                reinterpret_cast<h2 *>(Xout)[PF_IDX(q, N / 2)] = ox;
                 reinterpret_cast<h2 *>(Yout)[q] = oy;
                 reinterpret_cast<h2 *>(Lout)[q] = OPS::pack(l0, l1);
             } else if (v0) {
-                Xout[j0] = OPS::lo_h(ox); Yout[j0] = OPS::lo_h(oy); Lout[j0] = l0;
+                Xout[PF_IDX(j0, N)] = OPS::lo_h(ox); Yout[j0] = OPS::lo_h(oy); Lout[j0] = l0;
             } else if (v1) {
-                Xout[j1] = OPS::hi_h(ox); Yout[j1] = OPS::hi_h(oy); Lout[j1] = l1;
+                Xout[PF_IDX(j1, N)] = OPS::hi_h(ox); Yout[j1] = OPS::hi_h(oy); Lout[j1] = l1;
             }
             stats_add2<true>(stats, v0, OPS::to_f(l0), OPS::lo(ox), OPS::lo(oy), v1, OPS::to_f(l1), OPS::hi(ox), OPS::hi(oy));
         }
@@ -1297,7 +1317,7 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
     // ------------------------------------------------------------ 5. tile partial + finalise
     const Stats<acc_t> tot = block_stats<P>(stats, sm);
     if (tid == 0) {
-        TilePartial *p = &T.part[lt];
+        TilePartial *p = &T.part[PF_IDX(lt, T.ntiles)];
         uint32_t prev;
         if constexpr (kF64) {
             p->d[0] = tot.m;

@@ -134,3 +134,15 @@ def test_thread_block_study_builds_are_separate(monkeypatch):
     assert binding.library_path() == build.LIB
     with pytest.raises(ValueError):
         build.build(threads=96)
+
+
+def test_checked_build_is_separate(monkeypatch):
+    """The checked build (-DPF_CHECKED) lives beside the library, selected by PF_CHECKED."""
+    from paper_2308_00763_gb300 import binding, build
+    assert build.lib_path(checked=True) not in (build.LIB,) + tuple(build.lib_path(t) for t in build.STUDY_THREADS)
+    monkeypatch.setenv("PF_CHECKED", "1")
+    assert binding.library_path() == build.lib_path(checked=True)
+    monkeypatch.setenv("PF_CHECKED", "0")
+    assert binding.library_path() == build.LIB
+    with pytest.raises(ValueError):
+        build.build(threads=256, checked=True)
