@@ -154,6 +154,20 @@ pf_status pf_reset(pf_filter *f);
 /* Number of frames stepped so far (host-side count; no synchronisation). */
 int64_t pf_frames_done(const pf_filter *f);
 
+/* Host-side counters of a handle or batch (no synchronisation): what was enqueued, not
+ * what has completed. */
+typedef struct {
+    int64_t frames;            /* tracker-frames stepped (a batch: summed over its trackers) */
+    int64_t step_launches;     /* frame steps enqueued (one per frame of the handle) */
+    int64_t kernel_launches;   /* kernels enqueued, graph nodes included (1 per step; 2 more
+                                  for multinomial trackers: CDF and pull) */
+    int64_t graph_launches;    /* CUDA graph replays (pf_run_frames, pf_batch_run) */
+    int64_t host_frame_bytes;  /* frame bytes copied from host memory to the device */
+    int32_t status;            /* the handle's sticky pf_status */
+    int32_t reserved;
+} pf_counters;
+pf_status pf_get_counters(const pf_filter *f, pf_counters *out);
+
 /* Release the handle and every device buffer it owns (synchronises its stream first).
  * NULL is accepted. */
 pf_status pf_destroy(pf_filter *f);
@@ -246,6 +260,9 @@ pf_status pf_batch_run(pf_batch *b, int32_t count);
 /* Restart every tracker at frame 0 (as after pf_batch_create); resident videos restart
  * at their first frame.  Asynchronous. */
 pf_status pf_batch_reset(pf_batch *b);
+/* Counters of a batch (see pf_counters). */
+pf_status pf_batch_get_counters(const pf_batch *b, pf_counters *out);
+
 /* Estimates of frame `frame_index` of every tracker into xy[2*n] (host); trackers that
  * have not stepped that frame get NaN.  Synchronises. */
 pf_status pf_batch_estimates(pf_batch *b, int64_t frame_index, double *xy);

@@ -21,7 +21,7 @@ __all__ = [
     "PF_FLAG_ACCUM32", "PF_FLAG_TUNED", "PF_RESAMPLE_SYSTEMATIC", "PF_RESAMPLE_STRATIFIED", "PF_RESAMPLE_MULTINOMIAL", "RESAMPLERS", "PfTuning", "pf_autotune", "pf_autotune_batch", "pf_tuning_lookup",
     "pf_tuning_store", "pf_tuning_clear", "autotune", "autotune_batch", "PfConfig", "PfStateHeader", "PfError", "lib", "library_path",
     "pf_status_string", "pf_create", "pf_step_frame", "pf_run_frames", "pf_estimate",
-    "pf_estimates", "pf_frames_done", "pf_reset", "pf_destroy", "pf_get_state", "pf_set_state", "pf_get_debug",
+    "pf_estimates", "pf_frames_done", "pf_get_counters", "pf_batch_get_counters", "PfCounters", "pf_reset", "pf_destroy", "pf_get_state", "pf_set_state", "pf_get_debug",
     "pf_debug_philox", "pf_debug_wait_timeout", "pf_batch_create", "pf_batch_step", "pf_batch_estimates",
     "pf_batch_set_videos", "pf_batch_run", "pf_batch_reset", "pf_step_frame_noalloc",
     "pf_batch_destroy", "Filter", "Batch", "PRECISIONS", "EXPORTED",
@@ -55,6 +55,15 @@ class PfConfig(ctypes.Structure):
         ("seed", ctypes.c_uint64), ("tracker_id", ctypes.c_uint32), ("flags", ctypes.c_uint32),
         ("est_capacity", ctypes.c_int32), ("resampler", ctypes.c_int32),
     ]
+
+
+class PfCounters(ctypes.Structure):
+    _fields_ = [("frames", ctypes.c_int64), ("step_launches", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
+                ("graph_launches", ctypes.c_int64), ("host_frame_bytes", ctypes.c_int64),
+                ("status", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
 class PfStateHeader(ctypes.Structure):
@@ -123,6 +132,8 @@ _SIG = {
     "pf_estimate": (ctypes.c_int, [_P, _I64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "pf_estimates": (ctypes.c_int, [_P, _I64, _I32, _P, _P]),
     "pf_frames_done": (_I64, [_P]),
+    "pf_get_counters": (ctypes.c_int, [_P, ctypes.POINTER(PfCounters)]),
+    "pf_batch_get_counters": (ctypes.c_int, [_P, ctypes.POINTER(PfCounters)]),
     "pf_reset": (ctypes.c_int, [_P]),
     "pf_destroy": (ctypes.c_int, [_P]),
     "pf_get_state": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_size_t)]),
@@ -257,6 +268,18 @@ def pf_reset(h):
 
 def pf_frames_done(h) -> int:
     return int(lib().pf_frames_done(h))
+
+
+def pf_get_counters(h) -> dict:
+    c = PfCounters()
+    _check(lib().pf_get_counters(h, ctypes.byref(c)), "pf_get_counters")
+    return c.as_dict()
+
+
+def pf_batch_get_counters(h) -> dict:
+    c = PfCounters()
+    _check(lib().pf_batch_get_counters(h, ctypes.byref(c)), "pf_batch_get_counters")
+    return c.as_dict()
 
 
 def pf_destroy(h):
@@ -565,6 +588,9 @@ class Filter:
     def frames_done(self):
         return pf_frames_done(self.h)
 
+    def counters(self) -> dict:
+        return pf_get_counters(self.h)
+
     # -- checkpoint
     def _pos_dtype(self):
         return _POS_DTYPE[self.precision]
@@ -639,6 +665,9 @@ class Batch:
 
     def estimates(self, t):
         return pf_batch_estimates(self.h, self.n, t)
+
+    def counters(self) -> dict:
+        return pf_batch_get_counters(self.h)
 
     def close(self):
         if getattr(self, "h", None):

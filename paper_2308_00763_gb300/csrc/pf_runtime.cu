@@ -106,6 +106,9 @@ struct Engine {
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t ring_copied[2] = {nullptr, nullptr}, ring_free[2] = {nullptr, nullptr};
     int64_t frame_buf_pitch = 0;
+    // counters (pf_get_counters): launches enqueued, graph replays, host frame bytes copied
+    int64_t n_step_launches = 0, n_kernels = 0, n_graphs = 0, n_host_bytes = 0;
+    int kernels_per_step() const { return (total_tiles > 0 ? 1 : 0) + (pull_tiles > 0 ? 2 : 0); }
 
     pf_status fail(pf_status s) {
         if (sticky == PF_OK) sticky = s;
@@ -333,6 +336,8 @@ static pf_status engine_launch(Engine &e, const uint8_t *override_frame, int64_t
     L.frame_override = override_frame;
     L.pitch_override = override_pitch;
     if (engine_enqueue(e, L, e.stream) != 0) { cudaGetLastError(); return e.fail(PF_ERR_CUDA); }
+    e.n_step_launches += 1;
+    e.n_kernels += e.kernels_per_step();
     return PF_OK;
 }
 
@@ -390,6 +395,9 @@ static pf_status engine_run_resident(Engine &e, int32_t count) {
         e.graphs.emplace_back(count, exec);
     }
     if (cudaGraphLaunch(exec, e.stream) != cudaSuccess) { cudaGetLastError(); return e.fail(PF_ERR_CUDA); }
+    e.n_graphs += 1;
+    e.n_step_launches += count;
+    e.n_kernels += static_cast<int64_t>(count) * e.kernels_per_step();
     return PF_OK;
 }
 
@@ -449,6 +457,7 @@ static pf_status engine_run_host_frames(Engine &e, const uint8_t *frames, int64_
                                     frames + static_cast<int64_t>(done + i) * frame_stride, pitch_bytes, c.width,
                                     c.height, cudaMemcpyHostToDevice, e.copy_stream);
         }
+        if (err == cudaSuccess) e.n_host_bytes += static_cast<int64_t>(n) * c.width * c.height;
         if (err == cudaSuccess) err = cudaEventRecord(e.ring_copied[kc], e.copy_stream);
         if (err == cudaSuccess) err = cudaStreamWaitEvent(e.stream, e.ring_copied[kc], 0);
         if (err != cudaSuccess) break;
@@ -529,6 +538,7 @@ pf_status pf_step_frame(pf_filter *f, const uint8_t *frame, int64_t pitch_bytes,
         if (err != cudaSuccess) { cudaGetLastError(); return e.fail(PF_ERR_CUDA); }
         dev = e.d_frame_buf;
         pitch = e.frame_buf_pitch;
+        e.n_host_bytes += static_cast<int64_t>(c.width) * c.height;
     }
     pf_status s = engine_launch(e, dev, pitch);
     if (s != PF_OK) return s;
@@ -609,6 +619,24 @@ pf_status pf_estimates(pf_filter *f, int64_t first, int32_t count, double *xy, d
 }
 
 int64_t pf_frames_done(const pf_filter *f) { return f ? f->e.done_frames[0] : -1; }
+
+static void fill_counters(const Engine &e, pf_counters *out) {
+    memset(out, 0, sizeof *out);
+    int64_t frames = 0;
+    for (int i = 0; i < e.n; ++i) frames += e.done_frames[i];
+    out->frames = frames;
+    out->step_launches = e.n_step_launches;
+    out->kernel_launches = e.n_kernels;
+    out->graph_launches = e.n_graphs;
+    out->host_frame_bytes = e.n_host_bytes;
+    out->status = e.sticky;
+}
+
+pf_status pf_get_counters(const pf_filter *f, pf_counters *out) {
+    if (!f || !out) return PF_ERR_ARG;
+    fill_counters(f->e, out);
+    return PF_OK;
+}
 
 // Clear tracker i's lookback descriptors on the engine's stream.
 static cudaError_t clear_lookback(Engine &e, int i) {
@@ -846,6 +874,12 @@ pf_status pf_batch_run(pf_batch *b, int32_t count) {
     pf_status s = engine_run_resident(e, count);
     if (s != PF_OK) return s;
     for (int i = 0; i < e.n; ++i) e.done_frames[i] += count;
+    return PF_OK;
+}
+
+pf_status pf_batch_get_counters(const pf_batch *b, pf_counters *out) {
+    if (!b || !out) return PF_ERR_ARG;
+    fill_counters(b->e, out);
     return PF_OK;
 }
 

@@ -208,3 +208,27 @@ def test_alternative_schemes_at_large_sizes(pf, scheme, N):
     draws = oracle.stratified_offsets(3, v.T - 2, N, 0)
     fn = oracle.resample_stratified if scheme == "stratified" else oracle.resample_multinomial
     assert np.array_equal(anc, fn(C, draws, "f32"))
+
+
+def test_counters_count_launches_graphs_and_host_bytes(pf):
+    """pf_get_counters: one kernel per frame for systematic trackers, three for multinomial
+    (step kernel skipped: CDF and pull), one graph replay per resident run, host bytes."""
+    v = synth.make_video(96, 80, 7, 3, noise=5.0, seed=44)
+    fr = _frames(v)
+    for rs, per in (("systematic", 1), ("multinomial", 2)):
+        f = pf.Filter(v.W, v.H, 3000, 3, "f32", init=tuple(v.centres[0]), seed=2, resampler=rs)
+        f.step(v.frames[0])                      # host frame
+        f.step(fr[1])
+        f.run(fr[2:7])                            # one graph replay of 5 steps
+        c = f.counters()
+        f.close()
+        assert c == {"frames": 7, "step_launches": 7, "kernel_launches": 7 * per, "graph_launches": 1,
+                     "host_frame_bytes": v.W * v.H, "status": 0}, (rs, c)
+    cfgs = [pf.make_config(v.W, v.H, n, 3, "f16", init=tuple(v.centres[0]), seed=5 + i, tracker_id=i, resampler=rs)
+            for i, (n, rs) in enumerate(((2000, "systematic"), (900, "multinomial")))]
+    b = pf.Batch(cfgs)
+    for t in range(3):
+        b.step([fr[t], fr[t]])
+    c = b.counters()
+    b.close()
+    assert c["frames"] == 6 and c["step_launches"] == 3 and c["kernel_launches"] == 9 and c["graph_launches"] == 0
