@@ -280,7 +280,8 @@ pf_status pf_batch_destroy(pf_batch *b);
  * with `copies` trackers of that configuration in one batch (1 = the tracker alone; more
  * = throughput with the device full, as in a batch), and caches the fastest for the
  * configuration's shape bucket: (precision, floor(log2 N), the larger sigma in quarter
- * pixels).  Trackers created with PF_FLAG_TUNED take their bucket's cached
+ * pixels, disk radius, floor(log2 (width x height)), the device's SM count).  Trackers
+ * created with PF_FLAG_TUNED take their bucket's cached
  * shape (the default shape if none), so equal configurations tile alike alone and in a
  * batch.  The cache lives in the process (pf_tuning_clear empties it).  Synchronises. */
 typedef struct {

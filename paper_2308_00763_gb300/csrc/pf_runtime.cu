@@ -22,24 +22,36 @@ namespace {
 
 // ---------------------------------------------------------------- launch-shape cache
 struct TuneKey {
-    int prec, lg, sq;
+    int prec, lg, sq, r, fb, sms;
     bool operator<(const TuneKey &o) const {
         if (prec != o.prec) return prec < o.prec;
         if (lg != o.lg) return lg < o.lg;
-        return sq < o.sq;
+        if (sq != o.sq) return sq < o.sq;
+        if (r != o.r) return r < o.r;
+        if (fb != o.fb) return fb < o.fb;
+        return sms < o.sms;
     }
 };
 
 std::mutex g_tune_lock;
 std::map<TuneKey, pf_tuning> g_tune;
 
-// shape bucket: precision, floor(log2 N), the larger sigma in quarter pixels
+// shape bucket: precision, floor(log2 N), the larger sigma in quarter pixels, the disk
+// radius, floor(log2 (W H)) and the current device's SM count
 TuneKey tune_key(const pf_config &c) {
     int lg = 0;
     while (lg < 62 && (int64_t(1) << (lg + 1)) <= c.num_particles) ++lg;
     const double sg = std::max(c.sigma_x, c.sigma_y);
     const int sq = static_cast<int>(std::min(4.0 * sg + 0.5, 1.0e6));
-    return TuneKey{c.precision, lg, sq};
+    const int64_t px = static_cast<int64_t>(c.width) * c.height;
+    int fb = 0;
+    while (fb < 62 && (int64_t(1) << (fb + 1)) <= px) ++fb;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        sms = 0;                           // no device (host-only use of the cache)
+    }
+    return TuneKey{c.precision, lg, sq, c.disk_radius, fb, sms};
 }
 
 bool valid_tuning(const pf_tuning &t) {

@@ -103,17 +103,23 @@ def test_server_stream_bytes_without_gpu(libpath):
 
 def test_tuning_cache_without_gpu(libpath):
     """The launch-shape cache is host state keyed by the shape bucket (precision,
-    floor(log2 N), larger sigma in quarter pixels); invalid shapes are refused."""
+    floor(log2 N), larger sigma in quarter pixels, radius, floor(log2 W*H), SM count);
+    invalid shapes are refused."""
     import paper_2308_00763_gb300 as pf
     pf.pf_tuning_clear()
     a = pf.make_config(512, 512, 1 << 20, 5, "f16", sigma=(1.0, 1.0))
-    same_bucket = pf.make_config(256, 256, (1 << 21) - 1, 9, "f16", sigma=(1.1, 0.9))
-    other = pf.make_config(512, 512, 1 << 20, 5, "f32", sigma=(1.0, 1.0))
+    same_bucket = pf.make_config(512, 600, (1 << 21) - 1, 5, "f16", sigma=(1.1, 0.9))
+    others = [pf.make_config(512, 512, 1 << 20, 5, "f32", sigma=(1.0, 1.0)),     # precision
+              pf.make_config(512, 512, 1 << 21, 5, "f16", sigma=(1.0, 1.0)),     # N bucket
+              pf.make_config(512, 512, 1 << 20, 5, "f16", sigma=(2.0, 1.0)),     # sigma
+              pf.make_config(512, 512, 1 << 20, 9, "f16", sigma=(1.0, 1.0)),     # radius
+              pf.make_config(1024, 1024, 1 << 20, 5, "f16", sigma=(1.0, 1.0))]   # frame size
     assert pf.pf_tuning_lookup(a) is None
     pf.pf_tuning_store(a, 2048, 1, 1)
     t = pf.pf_tuning_lookup(same_bucket)
     assert t is not None and (t.tile, t.window, t.ctas_per_sm) == (2048, 1, 1)
-    assert pf.pf_tuning_lookup(other) is None
+    for o in others:
+        assert pf.pf_tuning_lookup(o) is None
     for bad in ((1000, 0, 0), (8192, 0, 0), (2048, 3, 0), (2048, 0, -1)):
         with pytest.raises(pf.PfError):
             pf.pf_tuning_store(a, *bad)
