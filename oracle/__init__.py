@@ -67,6 +67,8 @@ def _load():
             "orc_cdf": (None, [_I64, _P, _D, _P]),
             "orc_resample_f64": (None, [_I64, _P, _D, _P]),
             "orc_resample_f32": (None, [_I64, _P, ctypes.c_float, _P]),
+            "orc_resample_div_f64": (None, [_I64, _P, _D, _P]),
+            "orc_resample_div_f32": (None, [_I64, _P, ctypes.c_float, _P]),
             "orc_stratified_offsets": (None, [_U64, _U32, _U32, _I64, _P]),
             "orc_resample_strat_f64": (None, [_I64, _P, _P, _P]),
             "orc_resample_strat_f32": (None, [_I64, _P, _P, _P]),
@@ -205,17 +207,19 @@ def cdf(e, S):
     return C
 
 
-def resample(C, u0, precision: str = "f64"):
+def resample(C, u0, precision: str = "f64", divide: bool = False):
     """Systematic-resampling ancestors of CDF ``C`` with offset ``u0``, the decision taken
-    in FP64 (``precision='f64'``) or FP32 (``'f32'``; C and u0 are rounded to FP32)."""
+    in FP64 (``precision='f64'``) or FP32 (``'f32'``; C and u0 are rounded to FP32).  The
+    stratum points are ``(j + u0) * (1/N)``, or ``(j + u0) / N`` with ``divide``."""
+    L = _load()
     if precision == "f64":
         Cc = np.ascontiguousarray(C, np.float64)
         a = np.empty(Cc.size, np.int64)
-        _load().orc_resample_f64(Cc.size, _ptr(Cc), float(u0), _ptr(a))
+        (L.orc_resample_div_f64 if divide else L.orc_resample_f64)(Cc.size, _ptr(Cc), float(u0), _ptr(a))
     elif precision == "f32":
         Cc = np.ascontiguousarray(C, np.float32)
         a = np.empty(Cc.size, np.int64)
-        _load().orc_resample_f32(Cc.size, _ptr(Cc), float(np.float32(u0)), _ptr(a))
+        (L.orc_resample_div_f32 if divide else L.orc_resample_f32)(Cc.size, _ptr(Cc), float(np.float32(u0)), _ptr(a))
     else:
         raise ValueError(precision)
     return a

@@ -14,6 +14,7 @@
  *   normalising (sum + estimate)    orc_normalise
  *   normalising (CDF, inclusive prefix sum)  orc_cdf
  *   systematic resampling (Sec. 3)  orc_resample_f64 / orc_resample_f32
+ *     (naive form, points by division)  orc_resample_div_f64 / orc_resample_div_f32
  *   stratified resampling (Sec. 2)  orc_stratified_offsets, orc_resample_strat_f64 / _f32
  *   multinomial resampling (Sec. 3) orc_resample_multi_f64 / _f32 (draws: orc_stratified_offsets)
  * Where the paper is silent the readings are (numbered as in the design notes):
@@ -461,6 +462,32 @@ void orc_resample_multi_f32(int64_t N, const float *C, const float *v, int64_t *
             if (C[mid] >= v[j]) hi = mid; else lo = mid + 1;
         }
         a[j] = lo < N ? lo : N - 1;
+    }
+}
+
+/* The same systematic decisions with the stratum points formed by a division,
+ * u_j = (j + u0) / N, and no saved reciprocal: the naive form of Sec. 3's performance
+ * optimisation (the GPU's naive study build takes these decisions). */
+void orc_resample_div_f64(int64_t N, const double *C, double u0, int64_t *a)
+{
+    int64_t k = 0;
+    for (int64_t j = 0; j < N; ++j) {
+        double u = ((double)j + u0) / (double)N;
+        while (k < N && C[k] < u) ++k;
+        a[j] = k < N ? k : N - 1;
+    }
+}
+
+void orc_resample_div_f32(int64_t N, const float *C, float u0, int64_t *a)
+{
+    int64_t k = 0;
+    for (int64_t j = 0; j < N; ++j) {
+        volatile float jf = (float)j;
+        volatile float s = jf + u0;
+        volatile float nf = (float)N;
+        volatile float u = s / nf;
+        while (k < N && C[k] < u) ++k;
+        a[j] = k < N ? k : N - 1;
     }
 }
 

@@ -338,6 +338,33 @@ def test_resample_dominant_and_clamp():
         assert np.array_equal(oracle.resample(C3, 0.0, prec), [0, 0, 1, 2])
 
 
+# ----------------------------------------------------------------------------- naive form (division)
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_resample_by_division_pins(prec):
+    """Points formed as (j + u0) / N: for N a power of two the division and the product
+    with 1/N are the same exact operation, so the decisions equal the saved-constant form;
+    for any N the offspring counts keep the floor/ceil property (FP64) and the ancestors
+    are ordered."""
+    rng = np.random.default_rng(18)
+    for n in (1, 2, 8, 1024, 1 << 14):
+        e = rng.exponential(size=n) ** 2
+        S, _, _ = oracle.normalise(e, np.zeros(n), np.zeros(n))
+        C = oracle.cdf(e, S)
+        for u0 in (0.125, 0.5, 0.875):
+            assert np.array_equal(oracle.resample(C, u0, prec, divide=True), oracle.resample(C, u0, prec))
+    for n in (3, 7, 100, 4097):
+        e = rng.exponential(size=n) ** 3
+        S, _, _ = oracle.normalise(e, np.zeros(n), np.zeros(n))
+        C = oracle.cdf(e, S)
+        a = oracle.resample(C, 0.37, prec, divide=True)
+        assert np.all(np.diff(a) >= 0) and a.min() >= 0 and a.max() < n
+        cnt = _counts(a, n)
+        assert cnt.sum() == n
+        if prec == "f64":
+            w = np.diff(np.concatenate([[0.0], C]))
+            assert np.all(cnt >= np.floor(n * w - 1e-9)) and np.all(cnt <= np.ceil(n * w + 1e-9))
+
+
 # ----------------------------------------------------------------------------- stratified resampling
 def test_stratified_offsets_are_the_tag1_words():
     """v_j = uniform word (j mod 4) of Philox(j / 4, t, 1, tracker); v_0 is the systematic u0."""
