@@ -191,8 +191,13 @@ def _checked() -> bool:
     return os.environ.get("PF_CHECKED", "") not in ("", "0")
 
 
+def _naive() -> bool:
+    """The naive-resampling study build (PF_NAIVE=1 in the environment)."""
+    return os.environ.get("PF_NAIVE", "") not in ("", "0")
+
+
 def library_path() -> str:
-    return _build.lib_path(_study_threads(), _checked())
+    return _build.lib_path(_study_threads(), _checked(), _naive())
 
 
 def lib(build_if_missing: bool = False):
@@ -204,7 +209,7 @@ def lib(build_if_missing: bool = False):
         path = library_path()
         if not os.path.exists(path):
             if build_if_missing:
-                _build.build(threads=_study_threads(), checked=_checked())
+                _build.build(threads=_study_threads(), checked=_checked(), naive=_naive())
             else:
                 raise RuntimeError("the CUDA library %s is not built; run "
                                    "`python -c 'import __graft_entry__ as g; g.build()'`" % path)

@@ -38,18 +38,21 @@ def deps():
 STUDY_THREADS = (128, 256, 512, 1024)   # threads per CTA of the step kernel's study builds
 
 
-def lib_path(threads: int | None = None, checked: bool = False) -> str:
-    """The library, the thread-block study build with `threads` threads per CTA, or the
-    checked build (index tests in the kernels, -DPF_CHECKED)."""
+def lib_path(threads: int | None = None, checked: bool = False, naive: bool = False) -> str:
+    """The library, the thread-block study build with `threads` threads per CTA, the
+    checked build (index tests in the kernels, -DPF_CHECKED) or the naive-resampling study
+    build (a reciprocal per element instead of saved constants, -DPF_NAIVE_RESAMPLE)."""
     if checked:
         return os.path.join(BUILD, "checked", "libpf_gb300.so")
+    if naive:
+        return os.path.join(BUILD, "naive", "libpf_gb300.so")
     if not threads or threads == 512:
         return LIB
     return os.path.join(BUILD, "t%d" % threads, "libpf_gb300.so")
 
 
-def up_to_date(threads: int | None = None, checked: bool = False) -> bool:
-    lib = lib_path(threads, checked)
+def up_to_date(threads: int | None = None, checked: bool = False, naive: bool = False) -> bool:
+    lib = lib_path(threads, checked, naive)
     if not os.path.exists(lib):
         return False
     t = os.path.getmtime(lib)
@@ -57,17 +60,20 @@ def up_to_date(threads: int | None = None, checked: bool = False) -> bool:
 
 
 def build(force: bool = False, verbose: bool = False, extra=(), threads: int | None = None,
-          checked: bool = False) -> str:
+          checked: bool = False, naive: bool = False) -> str:
     """Build the library (512 threads per CTA); with `threads` in STUDY_THREADS a separate
     study build under _build/t<threads>/ (-DPF_STEP_THREADS); with `checked` the checked
     build under _build/checked/ (-DPF_CHECKED: every kernel index that is in range by
-    construction is tested, a miss fails the step with PF_ERR_STATE instead of faulting)."""
+    construction is tested, a miss fails the step with PF_ERR_STATE instead of faulting);
+    with `naive` the study build under _build/naive/ (-DPF_NAIVE_RESAMPLE: divisions by S
+    and N per element and an integer-to-half conversion per pixel, the form the paper's
+    saved-constant optimisation removes)."""
     if threads and threads not in STUDY_THREADS:
         raise ValueError("threads per CTA must be one of %s" % (STUDY_THREADS,))
-    if threads and checked:
-        raise ValueError("the checked build has the library's 512 threads per CTA")
-    lib = lib_path(threads, checked)
-    if not force and up_to_date(threads, checked):
+    if sum(bool(x) for x in (threads and threads != 512, checked, naive)) > 1:
+        raise ValueError("one study or checked variant at a time")
+    lib = lib_path(threads, checked, naive)
+    if not force and up_to_date(threads, checked, naive):
         return lib
     bdir = os.path.dirname(lib)
     os.makedirs(bdir, exist_ok=True)
@@ -76,6 +82,8 @@ def build(force: bool = False, verbose: bool = False, extra=(), threads: int | N
              "--expt-relaxed-constexpr", *extra]
     if checked:
         flags.append("-DPF_CHECKED")
+    elif naive:
+        flags.append("-DPF_NAIVE_RESAMPLE")
     elif lib != LIB:
         flags.append("-DPF_STEP_THREADS=%d" % threads)
     if verbose:

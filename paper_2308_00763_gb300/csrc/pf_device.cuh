@@ -78,6 +78,8 @@ __device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double div_rn(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ float div_rn(float a, float b) { return __fdiv_rn(a, b); }
 
 __device__ __forceinline__ double exp_acc(double x) { return exp(x); }
 __device__ __forceinline__ float exp_acc(float x) { return expf(x); }
@@ -98,7 +100,12 @@ template <> __device__ __forceinline__ float neg_inf<float>() { return -__int_as
 // ----------------------------------------------------------------------------------
 template <typename A>
 __device__ __forceinline__ A stratum_point32(int j, A u0, A inv_n) {
+#ifdef PF_NAIVE_RESAMPLE
+    // study build: a reciprocal per point, (j + u0) / N (inv_n carries N here)
+    return div_rn(add_rn(static_cast<A>(j), u0), inv_n);
+#else
     return mul_rn(add_rn(static_cast<A>(j), u0), inv_n);
+#endif
 }
 
 // Strata of one tracker's frame: n = N, 1/N, the offsets and the first / last points.

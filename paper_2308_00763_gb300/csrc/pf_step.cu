@@ -103,6 +103,15 @@ __device__ __forceinline__ int checked_index(int i, int n, TrackerState *st) {
 #define PF_IDX(i, n) (i)
 #endif
 
+// The normalised CDF value of a prefix P: P * (1/S) with the reciprocal saved by the
+// previous step (the paper's saved constant); the naive study build (-DPF_NAIVE_RESAMPLE)
+// divides by S for every element instead.
+#ifdef PF_NAIVE_RESAMPLE
+#define PF_NORM(P) div_rn((P), Sdiv)
+#else
+#define PF_NORM(P) mul_rn((P), invS)
+#endif
+
 // ---- lookback descriptor words (see LookbackDesc): 16-bit launch tag | 48-bit payload
 constexpr uint64_t kPayload48 = (1ull << 48) - 1ull;
 
@@ -318,10 +327,16 @@ template <typename H> struct HalfOps;
 template <>
 struct HalfOps<__half> {
     using h2 = __half2;
+#ifndef PF_NAIVE_RESAMPLE
     // (1024 + I) has the bit pattern 0x6400 | I in binary16, so the pixel enters the
     // half arithmetic without a conversion instruction: h - (1024 + level) is exact.
     static constexpr float kLevelOffset = 1024.0f;
     __device__ static __forceinline__ __half pix(uint32_t i) { return __ushort_as_half(static_cast<unsigned short>(0x6400u | i)); }
+#else
+    // study build: an integer-to-half conversion per pixel (the same exact value of I - level)
+    static constexpr float kLevelOffset = 0.0f;
+    __device__ static __forceinline__ __half pix(uint32_t i) { return __uint2half_rn(i); }
+#endif
     __device__ static __forceinline__ __half from_f(float v) { return __float2half_rn(v); }
     __device__ static __forceinline__ float to_f(__half v) { return __half2float(v); }
     __device__ static __forceinline__ h2 pack(__half a, __half b) { return __halves2half2(a, b); }
@@ -1025,8 +1040,15 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
         // point; the CDF kernel has no window phase
         if constexpr (kMode == kModeCdf) __syncthreads();
         const acc_t invS = kF64 ? static_cast<acc_t>(sm.st.invS) : static_cast<acc_t>(sm.st.invS_f);
+#ifdef PF_NAIVE_RESAMPLE
+        const acc_t Sdiv = static_cast<acc_t>(sm.st.S);   // study build: a division per element
+#endif
         const acc_t u0 = kF64 ? static_cast<acc_t>(sm.u0d) : static_cast<acc_t>(sm.u0f);
+#ifdef PF_NAIVE_RESAMPLE
+        const acc_t inv_n = static_cast<acc_t>(N);     // the study build divides by N per point
+#else
         const acc_t inv_n = sizeof(acc_t) == 8 ? static_cast<acc_t>(T.inv_n) : static_cast<acc_t>(T.inv_n_f);
+#endif
         // exact prefix before the tile (every thread) and after it (published as inclusive)
         const U128 exclx = (lt > 0) ? lookback<P>(look, lt, dtag, st, sm) : U128{0ull, 0ull};
         const U128 endx = add128(exclx, sm.agg_x);
@@ -1044,7 +1066,7 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
                 if (e < cnt) {
                     const int k = k0 + e;
                     const acc_t Pk = (e == cnt - 1) ? pend : fmin(add_rn(excl, loc[m]), pend);
-                    acc_t C = fmin(mul_rn(Pk, invS), static_cast<acc_t>(1));
+                    acc_t C = fmin(PF_NORM(Pk), static_cast<acc_t>(1));
                     if (k == N - 1) C = static_cast<acc_t>(1);
                     cdf[PF_IDX(k, N)] = C;
                 }
@@ -1053,7 +1075,7 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
         }
         // J of the tile's first element and of each element, for either resampling scheme
         const auto count_strata = [&](const auto &str) {
-            if (tid == 0) sm.jbeg = (lt == 0) ? 0 : str.count_le(fmin(mul_rn(excl, invS), static_cast<acc_t>(1)));
+            if (tid == 0) sm.jbeg = (lt == 0) ? 0 : str.count_le(fmin(PF_NORM(excl), static_cast<acc_t>(1)));
             acc_t cprev = static_cast<acc_t>(-1);
             int jprev = 0;
 #pragma unroll
@@ -1064,7 +1086,7 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
                     const int k = k0 + e;
                     const acc_t Pk = (e == cnt - 1) ? pend : fmin(add_rn(excl, loc[m]), pend);
                     // the normalised CDF cannot exceed 1; the FP32 scan can round above it
-                    acc_t C = fmin(mul_rn(Pk, invS), static_cast<acc_t>(1));
+                    acc_t C = fmin(PF_NORM(Pk), static_cast<acc_t>(1));
                     if (k == N - 1) { C = static_cast<acc_t>(1); J = N; }
                     else if (C == cprev) J = jprev;          // same CDF value, same count
                     else J = str.count_le(C);

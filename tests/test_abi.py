@@ -152,3 +152,12 @@ def test_checked_build_is_separate(monkeypatch):
     assert binding.library_path() == build.LIB
     with pytest.raises(ValueError):
         build.build(threads=256, checked=True)
+
+
+def test_naive_study_build_is_separate(monkeypatch):
+    from paper_2308_00763_gb300 import binding, build
+    assert build.lib_path(naive=True) not in (build.LIB, build.lib_path(checked=True))
+    monkeypatch.setenv("PF_NAIVE", "1")
+    assert binding.library_path() == build.lib_path(naive=True)
+    with pytest.raises(ValueError):
+        build.build(naive=True, checked=True)

@@ -1,4 +1,7 @@
-"""The checked build (-DPF_CHECKED): every kernel index that is in range by construction
+"""Variant builds run in child processes: the checked build and the naive-resampling study
+build.
+
+The checked build (-DPF_CHECKED): every kernel index that is in range by construction
 is tested on the device; a miss would raise the tracker's bounds bit, redirect the access
 to element 0 and fail the step with PF_ERR_STATE.  compute-sanitizer is not part of this
 project's runs, so this build is how the index arithmetic is exercised on the GPU.
@@ -105,6 +108,7 @@ print(json.dumps(out))
 def _run(checked):
     env = dict(os.environ)
     env.pop("PF_STEP_THREADS", None)
+    env.pop("PF_NAIVE", None)
     if checked:
         env["PF_CHECKED"] = "1"
     else:
@@ -124,3 +128,61 @@ def test_checked_build_runs_every_workload_clean():
     plain = _run(False)
     assert "/checked/" not in plain["lib"]
     assert checked["tracks"] == plain["tracks"]
+
+
+NAIVE_CHILD = r'''
+import json, sys
+sys.path.insert(0, sys.argv[1])
+import numpy as np, torch
+import oracle
+import paper_2308_00763_gb300 as pf
+from paper_2308_00763_gb300 import synth
+pf.lib(build_if_missing=True)
+v = synth.make_video(160, 120, 5, 4, noise=8.0, seed=9, v=(1.0, -1.0))
+fr = torch.from_numpy(v.frames).cuda()
+res = {"lib": pf.library_path(), "cases": []}
+for prec in ("ref64", "f32", "f16", "bf16"):
+    for N in (3, 4097, 3 * 4096 + 17):
+        f = pf.Filter(v.W, v.H, N, 4, prec, init=tuple(v.centres[0]), seed=6, sigma=(2.0, 2.0),
+                      flags=pf.PF_FLAG_DEBUG_ARRAYS)
+        f.run(fr)
+        anc = f.debug(0).astype(np.int64)
+        C = f.debug(1).astype(np.float64)
+        a_o = oracle.resample(C, oracle.resample_u0(6, v.T - 2), "f64" if prec == "ref64" else "f32", divide=True)
+        res["cases"].append([prec, N, bool(np.array_equal(anc, a_o)), bool(np.all(np.diff(C) >= 0) and C[-1] == 1.0)])
+        f.close()
+# the first frame's likelihoods (no resampling yet) must not depend on how pixels enter half
+f = pf.Filter(v.W, v.H, 5000, 4, "f16", init=tuple(v.centres[0]), seed=6)
+f.step(fr[0])
+res["L0"] = f.get_state()["L"].astype(np.float64).tolist()
+f.close()
+print(json.dumps(res))
+'''
+
+
+def test_naive_resampling_study_build_is_exact_for_its_own_arithmetic():
+    """The naive study build (-DPF_NAIVE_RESAMPLE, PF_NAIVE=1) divides by S and N per
+    element: its ancestors equal the oracle's systematic resampling with points (j + u0)/N
+    on the CDF the step computed, in every precision; and its per-pixel integer-to-half
+    conversion leaves the likelihoods unchanged."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import json
+    env = dict(os.environ)
+    env.pop("PF_STEP_THREADS", None)
+    env.pop("PF_CHECKED", None)
+    out = {}
+    for naive in (True, False):
+        if naive:
+            env["PF_NAIVE"] = "1"
+        else:
+            env.pop("PF_NAIVE", None)
+        p = subprocess.run([sys.executable, "-c", NAIVE_CHILD, ROOT], env=env, capture_output=True, text=True,
+                           timeout=900)
+        assert p.returncode == 0, (p.stdout[-2000:], p.stderr[-4000:])
+        out[naive] = json.loads(p.stdout.strip().splitlines()[-1])
+    assert "/naive/" in out[True]["lib"] and "/naive/" not in out[False]["lib"]
+    for prec, N, exact, monotone in out[True]["cases"]:
+        assert exact and monotone, (prec, N)
+    assert out[True]["L0"] == out[False]["L0"]
