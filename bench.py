@@ -322,6 +322,9 @@ def run_ours(args):
             "value": value, "ms_per_step": total_ms / args.steps,
             "launch_us_mean": 1e3 * statistics.mean(launch_ms),
             "launch_us_median": 1e3 * statistics.median(launch_ms),
+            # per-frame step latency (one pf_step_frame per frame, device frames)
+            "frame_latency_us_p50": 1e3 * statistics.median(launch_ms),
+            "frame_latency_us_p99": 1e3 * sorted(launch_ms)[min(len(launch_ms) - 1, int(0.99 * len(launch_ms)))],
             "e2e_value": N_ * T * ws / e2e_s, "wall": (wall0, wall1),
         }
         f.close()
@@ -354,10 +357,11 @@ def run_ours(args):
                      "launch_us_median": head["launch_us_median"]},
         "e2e": {"value": head["e2e_value"], "unit": METRIC, "h2d_bytes_per_step": int(W_ * H_ * T),
                 "d2h_bytes_per_step": int(16 * T)},
-        "gpu_launches": args.steps * T * (3 if args.resampler == "multinomial" else 1),
+        "gpu_launches": args.steps * T * (2 if args.resampler == "multinomial" else 1),   # CDF + pull
         "accuracy": {"rmse_px_vs_ref64_gpu": head["rmse_px_vs_ref64_gpu"],
                      "rmse_px_vs_ground_truth": results_truth.get(hp)},
-        "per_precision": {p: {k: r[k] for k in ("value", "ms_per_step", "launch_us_median", "e2e_value",
+        "per_precision": {p: {k: r[k] for k in ("value", "ms_per_step", "launch_us_median", "frame_latency_us_p50",
+                                                "frame_latency_us_p99", "e2e_value",
                                                 "rmse_px_vs_ref64_gpu")}
                           for p, r in results.items()},
     }
