@@ -178,8 +178,8 @@ def _kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def _traffic(prec):
-    """DRAM bytes per launch of the step kernel from the committed ncu summary, if it was
+def _ncu_figure(key, prec):
+    """A per-launch figure of the step kernel from the committed ncu summary, if it was
     taken on the current kernel source; else None."""
     try:
         with open(os.path.join(ROOT, "profiles", "step_kernel_traffic.json")) as f:
@@ -188,8 +188,35 @@ def _traffic(prec):
         return None
     if d.get("source_sha") != _kernel_source_hash():
         return None
-    v = d.get("dram_bytes_per_launch", {}).get(prec)
+    v = d.get(key, {}).get(prec)
     return float(v) if v is not None else None
+
+
+def _traffic(prec):
+    """DRAM bytes per launch of the step kernel (ncu), or None."""
+    return _ncu_figure("dram_bytes_per_launch", prec)
+
+
+def _issue_view(prec, launch_us, dev):
+    """Instruction-issue view of the step kernel: achieved thread instructions per second
+    (warp instructions per launch from the committed ncu capture x 32 / launch time)
+    against SMs x 4 schedulers x 32 lanes x the maximum SM clock (nvidia-smi)."""
+    import torch
+    warp_instr = _ncu_figure("warp_instructions_per_launch", prec)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = None
+    try:
+        out = subprocess.run(["nvidia-smi", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits",
+                              "-i", str(dev.index or 0)], capture_output=True, text=True, timeout=20)
+        mhz = float(out.stdout.strip().splitlines()[0])
+    except (OSError, ValueError, IndexError, subprocess.SubprocessError):
+        mhz = None
+    peak = sms * 4 * 32 * mhz * 1e6 if mhz else None
+    achieved = warp_instr * 32 / (launch_us * 1e-6) if warp_instr else None
+    return {"bound": "issue", "achieved": achieved, "peak": peak, "unit": "thread instructions/s",
+            "frac": achieved / peak if (achieved and peak) else None,
+            "instructions_per_particle_step": warp_instr * 32 / N_ if warp_instr else None,
+            "peak_source": "SMs x 4 schedulers x 32 lanes x max SM clock (%s MHz)" % mhz}
 
 
 def _rmse(a, b):
@@ -355,6 +382,9 @@ def run_ours(args):
                      "kernel": "step_kernel<%s>" % hp, "peak_source": peak_kind,
                      "bytes_per_particle_step": BYTES_PER_PSTEP[hp],
                      "launch_us_median": head["launch_us_median"]},
+        # the same kernel against instruction issue: thread instructions per launch (ncu) over
+        # the launch time, against every SM sub-partition issuing one warp instruction a cycle
+        "roofline_issue": _issue_view(hp, head["launch_us_median"], dev),
         "e2e": {"value": head["e2e_value"], "unit": METRIC, "h2d_bytes_per_step": int(W_ * H_ * T),
                 "d2h_bytes_per_step": int(16 * T)},
         "gpu_launches": args.steps * T * (2 if args.resampler == "multinomial" else 1),   # CDF + pull
