@@ -122,12 +122,25 @@ struct Strata {
         last = point(n - 1);
         nf = static_cast<A>(n);
     }
-    __device__ __noinline__ A strat_point(int j) const {
-        const uint4 w = philox4x32_10(make_uint4(static_cast<uint32_t>(j) >> 2, keys[2], 1u, keys[3]), keys[0], keys[1]);
+    __device__ __forceinline__ uint4 strat_block(int j) const {
+        return philox4x32_10(make_uint4(static_cast<uint32_t>(j) >> 2, keys[2], 1u, keys[3]), keys[0], keys[1]);
+    }
+    __device__ __forceinline__ A strat_point_from(const uint4 &w, int j) const {
         const int q = j & 3;
         const uint32_t x = q == 0 ? w.x : (q == 1 ? w.y : (q == 2 ? w.z : w.w));
         const A v = sizeof(A) == 8 ? static_cast<A>(uniform_f64(x)) : static_cast<A>(uniform_f32(x));
         return stratum_point32<A>(j, v, inv_n);
+    }
+    __device__ __noinline__ A strat_point(int j) const { return strat_point_from(strat_block(j), j); }
+    // The two probes of count_le for stratified points: one Philox block serves both when
+    // the neighbour shares it (three times in four).
+    __device__ __noinline__ int strat_probes(A c, int j) const {
+        const uint4 w = strat_block(j);
+        const bool a = strat_point_from(w, j) <= c;
+        const int nb = a ? j + 1 : j - 1;
+        const bool b = ((nb >> 2) == (j >> 2) ? strat_point_from(w, nb) : strat_point(nb)) <= c;
+        if (a != b) return a ? j + 1 : j;
+        return -1;
     }
     __device__ __forceinline__ A point(int j) const {
         if constexpr (kStrat) return strat_point(j);
@@ -143,10 +156,15 @@ struct Strata {
         // The estimate is almost always within one stratum of the answer: probe u_j and its
         // neighbour on the far side (j = 0 has u_0 = first <= c, so j - 1 is never probed
         // below 0), and search only when both probes fall on the same side.
-        const bool a = point(j) <= c;
-        const bool b = point(a ? j + 1 : j - 1) <= c;
-        if (a != b) return a ? j + 1 : j;
-        return search(c, j);
+        if constexpr (kStrat) {
+            const int r = strat_probes(c, j);
+            return r >= 0 ? r : search(c, j);
+        } else {
+            const bool a = point(j) <= c;
+            const bool b = point(a ? j + 1 : j - 1) <= c;
+            if (a != b) return a ? j + 1 : j;
+            return search(c, j);
+        }
     }
     // the count for u_0 <= c < u_{n-1}, from the start point j (galloping, then bisection)
     __device__ __noinline__ int search(A c, int j) const {
