@@ -74,6 +74,8 @@ def _load():
             "orc_resample_strat_f32": (None, [_I64, _P, _P, _P]),
             "orc_resample_multi_f64": (None, [_I64, _P, _P, _P]),
             "orc_resample_multi_f32": (None, [_I64, _P, _P, _P]),
+            "orc_gumbel_f64": (None, [_U64, _U32, _U32, _I64, _P, _P]),
+            "orc_gumbel_f32": (None, [_U64, _U32, _U32, _I64, _P, _P]),
             "orc_run": (ctypes.c_int, [_P, _I64, ctypes.c_int, ctypes.c_int, ctypes.c_int, _I64,
                                        _I64, ctypes.c_int, _D, _D, _D, _D, _D, _D, _D, _D,
                                        _U64, _U32, ctypes.c_int, ctypes.c_int, _P, _P, _P]),
@@ -272,7 +274,32 @@ def resample_multinomial(C, v, precision: str = "f64"):
     return a
 
 
-RESAMPLERS = {"systematic": 0, "stratified": 1, "multinomial": 2}
+def resample_gumbel(L, seed: int, t: int, tracker: int = 0, precision: str = "f64"):
+    """Gumbel-max ancestors of frame t's unnormalised log weights ``L``:
+    a_j = argmax_k (L_k - ln(-ln u_jk)), ties to the smallest k, decided in FP64 or FP32
+    (L rounded to FP32, the variates from logf).  N^2 draws."""
+    if precision == "f64":
+        Lc = np.ascontiguousarray(L, np.float64)
+        fn = _load().orc_gumbel_f64
+    elif precision == "f32":
+        Lc = np.ascontiguousarray(L, np.float32)
+        fn = _load().orc_gumbel_f32
+    else:
+        raise ValueError(precision)
+    a = np.empty(Lc.size, np.int64)
+    fn(seed & 0xFFFFFFFFFFFFFFFF, t, tracker, Lc.size, _ptr(Lc), _ptr(a))
+    return a
+
+
+def gumbel_variates(seed: int, t: int, j: int, N: int, tracker: int = 0) -> np.ndarray:
+    """The variates g_jk = -ln(-ln u_jk), k < N, of offspring j at frame t (FP64)."""
+    k = np.arange(N)
+    ctr = np.stack([k // 4, np.full(N, t), np.full(N, 4 + 256 * j), np.full(N, tracker)], axis=1)
+    w = philox(ctr, seed)[k, k % 4]
+    return -np.log(-np.log(uniform(w)))
+
+
+RESAMPLERS = {"systematic": 0, "stratified": 1, "multinomial": 2, "gumbel": 3}
 
 
 # --------------------------------------------------------------------------- whole tracker
@@ -309,6 +336,8 @@ def track_steps(frames: np.ndarray, N: int, r: int, *, init, sigma=(1.0, 1.0), d
             a = resample_stratified(C, stratified_offsets(seed, t, N, tracker), "f64")
         elif resampler == "multinomial":
             a = resample_multinomial(C, stratified_offsets(seed, t, N, tracker), "f64")
+        elif resampler == "gumbel":
+            a = resample_gumbel(L, seed, t, tracker, "f64")
         elif resampler == "systematic":
             a = resample(C, u0, "f64")
         else:

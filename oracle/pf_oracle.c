@@ -17,6 +17,7 @@
  *     (naive form, points by division)  orc_resample_div_f64 / orc_resample_div_f32
  *   stratified resampling (Sec. 2)  orc_stratified_offsets, orc_resample_strat_f64 / _f32
  *   multinomial resampling (Sec. 3) orc_resample_multi_f64 / _f32 (draws: orc_stratified_offsets)
+ *   Gumbel-max resampling (Sec. 3)  orc_gumbel_f64 / _f32 (argmax of L + Gumbel variates)
  * Where the paper is silent the readings are (numbered as in the design notes):
  *   C1  Eq. 3 is summed over the template pixels and divided by 50*|D|.
  *   C2  template D = integer offsets with dx^2+dy^2 <= r^2 (centre included).
@@ -30,6 +31,8 @@
  *       a_j = min{k : C_k >= u_j}, N-1 if there is none.
  *       Stratified (alternative scheme): u_j = (j + v_j) * (1/N), v_j independent.
  *       Multinomial (alternative scheme): u_j = v_j, N independent draws.
+ *       Gumbel-max (alternative scheme): a_j = argmax_k L_k - ln(-ln u_jk), ties to the
+ *       smallest k, N draws per offspring (tag 4 + 256 j).
  *   C11 draws: Philox4x32-10 words -> 23-bit uniforms -> Box-Muller in FP64.
  *   C12 at t = 0 every ancestor sits at (init_x, init_y).
  * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), written here
@@ -465,6 +468,48 @@ void orc_resample_multi_f32(int64_t N, const float *C, const float *v, int64_t *
     }
 }
 
+/* Gumbel-max resampling, the log-domain alternative Sec. 3 weighs against log-sum-exp:
+ * with g_jk = -ln(-ln u_jk) independent standard Gumbel variates, offspring j takes
+ * a_j = argmax_k (L_k + g_jk) over the unnormalised log weights L (the smallest k among
+ * equal values).  The Gumbel-max property makes a_j a draw from the categorical law
+ * exp(L_k) / sum_i exp(L_i) -- the multinomial draw, with no maximum, sum or CDF.
+ * u_jk is the uniform of word (k mod 4) of the Philox draw (k / 4, t, 4 + 256 j,
+ * tracker); j < 2^24.  N^2 draws, so for small trackers only. */
+void orc_gumbel_f64(uint64_t seed, uint32_t t, uint32_t tracker, int64_t N, const double *L, int64_t *a)
+{
+    for (int64_t j = 0; j < N; ++j) {
+        double best = 0.0;
+        int64_t arg = -1;
+        for (int64_t k = 0; k < N; ++k) {
+            uint32_t w[4];
+            orc_philox_draw(seed, (uint32_t)(k / 4), t, 4u + 256u * (uint32_t)j, tracker, w);
+            double g = -log(-log(orc_uniform(w[k % 4])));
+            double v = L[k] + g;
+            if (arg < 0 || v > best) { best = v; arg = k; }
+        }
+        a[j] = arg;
+    }
+}
+
+/* The same decisions taken in FP32 (L held in FP32, the variates from logf). */
+void orc_gumbel_f32(uint64_t seed, uint32_t t, uint32_t tracker, int64_t N, const float *L, int64_t *a)
+{
+    for (int64_t j = 0; j < N; ++j) {
+        float best = 0.0f;
+        int64_t arg = -1;
+        for (int64_t k = 0; k < N; ++k) {
+            uint32_t w[4];
+            orc_philox_draw(seed, (uint32_t)(k / 4), t, 4u + 256u * (uint32_t)j, tracker, w);
+            volatile float u = (float)orc_uniform(w[k % 4]);
+            volatile float e = -logf(u);
+            volatile float g = -logf(e);
+            volatile float v = L[k] + g;
+            if (arg < 0 || v > best) { best = v; arg = k; }
+        }
+        a[j] = arg;
+    }
+}
+
 /* The same systematic decisions with the stratum points formed by a division,
  * u_j = (j + u0) / N, and no saved reciprocal: the naive form of Sec. 3's performance
  * optimisation (the GPU's naive study build takes these decisions). */
@@ -526,7 +571,9 @@ int orc_run(const uint8_t *frames, int64_t frame_stride, int T, int W, int H, in
             if (M_out) M_out[t] = M;
             if (S_out) S_out[t] = S;
             orc_cdf(N, e, S, C);
-            if (resampler) {
+            if (resampler == 3) {
+                orc_gumbel_f64(seed, (uint32_t)t, tracker, N, L, a);
+            } else if (resampler) {
                 orc_stratified_offsets(seed, (uint32_t)t, tracker, N, v);
                 if (resampler == 2) orc_resample_multi_f64(N, C, v, a);
                 else orc_resample_strat_f64(N, C, v, a);

@@ -490,6 +490,86 @@ def test_multinomial_dominant_clamp_and_order():
     assert np.array_equal(oracle.resample_multinomial(C3, [0.9, 0.6, 0.3, 0.1], "f32"), [3, 2, 1, 0])
 
 
+# ----------------------------------------------------------------------------- Gumbel-max resampling
+# The variates are bounded: u lies in [2^-24, 1 - 2^-24], so g = -ln(-ln u) lies in
+# [-ln(24 ln 2), -ln(-ln(1 - 2^-24))] = [-2.81, 16.64].
+G_LO = -math.log(24 * math.log(2.0))
+G_HI = -math.log(-math.log1p(-2.0 ** -24))
+
+
+def _softmax(L):
+    z = np.exp(np.asarray(L, np.float64) - np.max(L))
+    return z / z.sum()
+
+
+def test_gumbel_counts_follow_the_categorical_law():
+    """Gumbel-max property: argmax_k (L_k + g_k) is distributed as exp(L_k) / sum exp(L).
+    Over 4000 frames of 6 offspring each, the counts of particle k have mean N p_k and
+    variance N p_k (1 - p_k) (6 standard errors; variance within 15 %), with p the
+    softmax of L computed here by numpy."""
+    rng = np.random.default_rng(21)
+    n, trials = 6, 4000
+    L = rng.uniform(-2.0, 2.0, n)
+    p = _softmax(L)
+    cnts = np.array([_counts(oracle.resample_gumbel(L, 5, t, 2), n) for t in range(trials)], np.float64)
+    mean, var = cnts.mean(axis=0), cnts.var(axis=0)
+    want_var = n * p * (1 - p)
+    assert np.all(np.abs(mean - n * p) <= 6 * np.sqrt(want_var / trials))
+    assert np.all(np.abs(var / want_var - 1.0) < 0.15)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_gumbel_two_particles_closed_form(prec):
+    """L = (0, ln 3): particle 1 is drawn with probability 3/4 (binomial, 5 standard
+    errors over 2 x 10000 draws); swapping the weights swaps the law."""
+    n_frames = 10000
+    a = np.concatenate([oracle.resample_gumbel([0.0, math.log(3.0)], 9, t, 0, prec) for t in range(n_frames)])
+    se = math.sqrt(0.75 * 0.25 / a.size)
+    assert abs(np.mean(a == 1) - 0.75) <= 5 * se
+    b = np.concatenate([oracle.resample_gumbel([math.log(3.0), 0.0], 9, t, 0, prec) for t in range(n_frames)])
+    assert abs(np.mean(b == 0) - 0.75) <= 5 * se
+
+
+def test_gumbel_equal_weights_are_uniform():
+    """Equal log weights: every particle equally likely (chi-square over 64 particles,
+    64 x 200 draws, below the 0.9999 quantile with 63 degrees of freedom)."""
+    n, frames = 64, 200
+    L = np.full(n, -3.5)
+    c = sum(_counts(oracle.resample_gumbel(L, 11, t, 1), n) for t in range(frames)).astype(np.float64)
+    expect = frames * np.ones(n)
+    chi2 = float(np.sum((c - expect) ** 2 / expect))
+    assert chi2 < 116.0                     # chi2_{63}(0.9999) = 115.3
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_gumbel_gap_beyond_the_variate_range_is_deterministic(prec):
+    """A particle whose L exceeds every other by more than G_HI - G_LO always wins; one
+    below the best by more than that is never drawn."""
+    gap = G_HI - G_LO
+    L = np.array([0.0, 0.0, gap + 0.05, 0.0, -1.0])
+    for t in range(20):
+        assert np.all(oracle.resample_gumbel(L, 3, t, 0, prec) == 2)
+    L2 = np.array([1.0, 1.0 - gap - 0.05, 0.5, 1.0 - gap - 0.05])
+    seen = np.concatenate([oracle.resample_gumbel(L2, 3, t, 0, prec) for t in range(300)])
+    assert not np.any((seen == 1) | (seen == 3))
+    assert set(np.unique(seen)) == {0, 2}
+
+
+def test_gumbel_fp32_decisions_agree_with_fp64_outside_near_ties():
+    """FP32 decisions equal the FP64 ones except where the two best values of an offspring
+    lie within FP32 rounding of each other."""
+    rng = np.random.default_rng(22)
+    L = np.round(rng.normal(0.0, 3.0, 700), 3)
+    for t in range(3):
+        a64 = oracle.resample_gumbel(L, 7, t, 0, "f64")
+        a32 = oracle.resample_gumbel(L, 7, t, 0, "f32")
+        for j in np.nonzero(a64 != a32)[0]:
+            g = oracle.gumbel_variates(7, t, int(j), L.size)
+            v = L + g
+            assert abs(v[a64[j]] - v[a32[j]]) <= 1e-5 * max(1.0, abs(v[a64[j]])), (t, j)
+        assert np.mean(a64 == a32) >= 0.999
+
+
 # ----------------------------------------------------------------------------- propagation, Eq. 1-2
 def test_propagation_moments_paper_motion():
     """Eq. 1-2: x ~ N(1 + x_anc, 5^2), y ~ N(2 + y_anc, 2^2)."""
@@ -541,6 +621,15 @@ def test_track_multinomial_recovers_ground_truth_config1():
     err = np.sqrt(np.sum((est - v.centres) ** 2, axis=1))
     assert np.sqrt(np.mean(err ** 2)) < 1.0 and err.max() < 1.5
     recs = list(oracle.track_steps(v.frames, 1000, 5, init=tuple(v.centres[0]), seed=1, resampler="multinomial"))
+    assert np.array_equal(np.array([r.est for r in recs]), est)
+
+
+def test_track_gumbel_recovers_ground_truth_config1():
+    v = synth.make_video(128, 128, 10, 5, noise=5.0, seed=1)
+    est, _, _ = oracle.track(v.frames, 1000, 5, init=tuple(v.centres[0]), seed=1, resampler="gumbel")
+    err = np.sqrt(np.sum((est - v.centres) ** 2, axis=1))
+    assert np.sqrt(np.mean(err ** 2)) < 1.0 and err.max() < 1.5
+    recs = list(oracle.track_steps(v.frames, 1000, 5, init=tuple(v.centres[0]), seed=1, resampler="gumbel"))
     assert np.array_equal(np.array([r.est for r in recs]), est)
 
 
