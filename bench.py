@@ -403,6 +403,7 @@ def run_ours(args):
         line.setdefault("systems", {})["sweep"] = _sweep(dev, stream)
         line["systems"]["paper_workload"] = _paper_workload(dev, stream)
         line["systems"]["resamplers"] = _resamplers(dev, stream)
+        line["systems"]["gumbel_max"] = _gumbel_max(dev, stream)
     if not args.no_serve and ws == 1:
         cap = min(results[p]["value"] for p in results if p in ("f16", "f32")) if any(
             p in results for p in ("f16", "f32")) else head["value"]
@@ -662,6 +663,53 @@ def _resamplers(dev, stream):
             row[rs + "_over_systematic_time"] = row[rs]["us_per_frame"] / row["systematic"]["us_per_frame"]
         out[prec] = row
     return {"workload": WORKLOAD, "unit": METRIC, "by_precision": out}
+
+
+def _gumbel_max(dev, stream):
+    """Gumbel-max resampling (argmax of L + Gumbel variates, Sec. 3's log-domain
+    alternative) against systematic and multinomial resampling on the headline video at
+    the tracker sizes it allows (N^2 variates a frame): us per frame over 20 frames, and
+    the argmax kernel's variate rate (N^2 per frame over the frame time)."""
+    import torch
+    import paper_2308_00763_gb300 as pf
+    from paper_2308_00763_gb300 import synth
+    T = 20
+    v = synth.make_video(W_, H_, T, R_, noise=NOISE_, seed=SEED_)
+    fr = torch.from_numpy(v.frames).to(dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    def timed(n, prec, rs):
+        f = pf.Filter(W_, H_, n, R_, prec, init=tuple(v.centres[0]), seed=SEED_, stream=stream, resampler=rs)
+        f.run(fr[:4])
+        best = None
+        for _ in range(2):
+            flush.zero_()
+            f.reset()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            f.run(fr)
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            us = 1e3 * a.elapsed_time(b) / T
+            best = us if best is None else min(best, us)
+        rmse = _rmse(f.estimates(0, T), v.centres[:T])
+        f.close()
+        return best, rmse
+
+    out = {}
+    for prec, sizes in (("ref64", (1000, 4096, 16384)), ("f32", (1000, 4096, 16384, 65536)),
+                        ("f16", (1000, 4096, 16384, 65536))):
+        rows = []
+        for n in sizes:
+            g_us, g_rmse = timed(n, prec, "gumbel")
+            s_us, _ = timed(n, prec, "systematic")
+            m_us, _ = timed(n, prec, "multinomial")
+            rows.append({"N": n, "gumbel_us_per_frame": g_us, "systematic_us_per_frame": s_us,
+                         "multinomial_us_per_frame": m_us, "gumbel_variates_per_s": n * n / (g_us * 1e-6),
+                         "gumbel_rmse_px_vs_truth": g_rmse})
+        out[prec] = rows
+    return {"video": "%dx%d, r = %d, %d frames" % (W_, H_, R_, T), "by_precision": out}
 
 
 def _tpb_child():

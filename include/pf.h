@@ -56,8 +56,9 @@ typedef enum {
     PF_BF16 = 3    /* as PF_F16 in bfloat16, with the likelihood accumulated in FP32 */
 } pf_precision;
 
-/* Resampling scheme (pf_config.resampler).  Both cut the unit interval into N strata
- * [j/N, (j+1)/N), draw one point u_j in each and give offspring j the first particle whose
+/* Resampling scheme (pf_config.resampler).  SYSTEMATIC and STRATIFIED cut the unit
+ * interval into N strata [j/N, (j+1)/N), draw one point u_j in each and give offspring j
+ * the first particle whose
  * normalised CDF value reaches u_j (Sec. 3, "Resampling"; Sec. 2 names the standard
  * multinomial, stratified and systematic schemes).  The points are evaluated in the CDF's
  * precision exactly as ((A)j + v_j) * (A)(1/N), A = double (PF_REF64) or float.
@@ -70,11 +71,22 @@ typedef enum {
  *               u_j = v_j, the stratified offsets used as N independent uniforms (Sec. 3
  *               describes this categorical draw).  Two kernels per frame (the CDF is
  *               written to device memory, then every offspring searches it); trackers
- *               and batches only (pf_server_open and pf_step_frame_noalloc reject it). */
+ *               and batches only (pf_server_open and pf_step_frame_noalloc reject it).
+ *   GUMBEL:     the same categorical draw in the log domain (the Gumbel-max alternative to
+ *               log-sum-exp that Sec. 3 weighs): offspring j takes the particle
+ *               a_j = argmax_k (L_k + g_jk), ties to the smallest k, where L_k is the
+ *               unnormalised log weight, g_jk = -ln(-ln u_jk) and u_jk = uniform word
+ *               (k mod 4) of Philox(k / 4, t, 4 + 256 j, tracker_id); evaluated in FP64
+ *               (PF_REF64) or FP32 (the others, L widened from its stored type).  No
+ *               maximum, sum or CDF of the weights is needed for the draw, but it costs N^2
+ *               variates a frame, so N <= 2^16 (PF_ERR_ARG beyond).  Two kernels per frame
+ *               (the argmax, then the pull kernel); trackers and batches only, as
+ *               MULTINOMIAL.  pf_get_debug(which = 1) answers PF_ERR_ARG (no CDF). */
 typedef enum {
     PF_RESAMPLE_SYSTEMATIC = 0,
     PF_RESAMPLE_STRATIFIED = 1,
-    PF_RESAMPLE_MULTINOMIAL = 2
+    PF_RESAMPLE_MULTINOMIAL = 2,
+    PF_RESAMPLE_GUMBEL = 3
 } pf_resampler;
 
 /* pf_config.flags */

@@ -48,7 +48,9 @@ inline pf_status check_config(const pf_config *c) {
         return PF_ERR_ARG;
     if (fabs(c->init_x) > 1.0e6 || fabs(c->init_y) > 1.0e6) return PF_ERR_ARG;
     if (c->est_capacity < 0) return PF_ERR_ARG;
-    if (c->resampler < PF_RESAMPLE_SYSTEMATIC || c->resampler > PF_RESAMPLE_MULTINOMIAL) return PF_ERR_ARG;
+    if (c->resampler < PF_RESAMPLE_SYSTEMATIC || c->resampler > PF_RESAMPLE_GUMBEL) return PF_ERR_ARG;
+    // Gumbel-max draws N^2 variates a frame
+    if (c->resampler == PF_RESAMPLE_GUMBEL && c->num_particles > kGumbelMaxN) return PF_ERR_ARG;
     // stratified points in FP32 are ordered only while (float)j is exact
     if (c->resampler == PF_RESAMPLE_STRATIFIED && c->precision != PF_REF64 && c->num_particles > (1ll << 24))
         return PF_ERR_ARG;

@@ -30,6 +30,8 @@ constexpr int kMaxRadius = 64;
 constexpr int kResampleSystematic = 0;
 constexpr int kResampleStratified = 1;
 constexpr int kResampleMultinomial = 2;   // CDF by the step kernel, offspring by the pull kernel
+constexpr int kResampleGumbel = 3;        // ancestors by the Gumbel-max kernel, offspring by the pull kernel
+constexpr int64_t kGumbelMaxN = 1ll << 16; // N^2 draws a frame
 
 // Device status bits (sticky, per tracker).
 constexpr uint32_t kStatusTimeout = 0x1u;
@@ -105,6 +107,7 @@ struct TrackerDev {
     int32_t *dbg_anc;          // NULL unless PF_FLAG_DEBUG_ARRAYS
     void *dbg_cdf;
     void *cdf;                 // multinomial: the normalised CDF of the previous frame [N] (FP64 / FP32)
+    int32_t *anc;              // Gumbel-max: the ancestor of every offspring [N]
     LookbackDesc *look;
     TilePartial *part;
     uint32_t *done;
@@ -134,9 +137,26 @@ struct StepLaunch {
 
 // Host entry points into the kernel translation unit.
 int launch_step(int precision, const StepLaunch &L, int grid, void *stream);
-// The multinomial trackers' CDF kernel and pull kernel (their offspring), after launch_step
-// on the same stream.
-int launch_pull(int precision, const StepLaunch &L, int grid, void *stream);
+// The pull family's kernels after launch_step on the same stream: the multinomial
+// trackers' CDF kernel (when with_cdf), then the pull kernel (the offspring of the
+// multinomial and Gumbel-max trackers; the Gumbel-max ancestors come from launch_gumbel,
+// enqueued before it).
+int launch_pull(int precision, const StepLaunch &L, int grid, bool with_cdf, void *stream);
+
+// Gumbel-max ancestors of the trackers in slots[0 .. ntrk-1]: CTA b works on tracker g with
+// cta_prefix[g] <= b < cta_prefix[g + 1], offspring (b - cta_prefix[g]) * kGumbelOffspring
+// onwards.  A tracker at frame 0, with a failed step, or inactive in frames[] is skipped.
+constexpr int kGumbelOffspring = 8;       // offspring per CTA
+constexpr int kGumbelThreads = 256;
+struct GumbelLaunch {
+    const TrackerDev *trk;     // device array indexed by slot
+    const FrameRef *frames;    // device array indexed by slot
+    const int32_t *slots;      // device array [ntrk]
+    const int32_t *cta_prefix; // device array [ntrk + 1]
+    int32_t ntrk;
+    int32_t total_ctas;
+};
+int launch_gumbel(int precision, const GumbelLaunch &G, void *stream);
 int step_grid_size(int precision, int total_tiles);
 // Particles per tile for a tracker of n particles.  A tracker of at least half a device
 // of full tiles (SMs x CTAs per SM x kTile / 2 particles) takes the smallest multiple of

@@ -98,10 +98,14 @@ struct Engine {
     FrameRef *d_frames = nullptr;
     FrameRef *h_frames_pinned = nullptr;
     int32_t *d_tile_trk = nullptr;
+    int32_t *d_gumbel = nullptr;       // Gumbel-max trackers: [n_gumbel] slots, then [n_gumbel + 1] CTA prefix
     uint32_t *d_ticket = nullptr;
     char *d_arena = nullptr;
     int total_tiles = 0;               // tiles of the step kernel's trackers (systematic, stratified)
-    int pull_tiles = 0;                // tiles of the multinomial trackers (CDF and pull kernels)
+    int pull_tiles = 0;                // tiles of the pull kernel's trackers (multinomial, Gumbel-max)
+    int n_multi = 0;                   // multinomial trackers (the CDF kernel runs when > 0)
+    int n_gumbel = 0;                  // Gumbel-max trackers (the argmax kernel runs when > 0)
+    int gumbel_ctas = 0;
     int grid = 0;
     int grid_pull = 0;
     int ctas_cap = 0;                  // CTAs per SM (0: as many as fit)
@@ -120,7 +124,9 @@ struct Engine {
     int64_t frame_buf_pitch = 0;
     // counters (pf_get_counters): launches enqueued, graph replays, host frame bytes copied
     int64_t n_step_launches = 0, n_kernels = 0, n_graphs = 0, n_host_bytes = 0;
-    int kernels_per_step() const { return (total_tiles > 0 ? 1 : 0) + (pull_tiles > 0 ? 2 : 0); }
+    int kernels_per_step() const {
+        return (total_tiles > 0 ? 1 : 0) + (pull_tiles > 0 ? 1 : 0) + (n_multi > 0 ? 1 : 0) + (n_gumbel > 0 ? 1 : 0);
+    }
 
     pf_status fail(pf_status s) {
         if (sticky == PF_OK) sticky = s;
@@ -154,13 +160,14 @@ static void engine_free(Engine &e) {
     cudaFree(e.d_trk);
     cudaFree(e.d_frames);
     cudaFree(e.d_tile_trk);
+    cudaFree(e.d_gumbel);
     cudaFree(e.d_ticket);
     cudaFree(e.d_arena);
     cudaFree(e.d_frame_buf);
     if (e.h_frames_pinned) cudaFreeHost(e.h_frames_pinned);
     if (e.h_init_pinned) cudaFreeHost(e.h_init_pinned);
     e.h_init_pinned = nullptr;
-    e.d_trk = nullptr; e.d_frames = nullptr; e.d_tile_trk = nullptr; e.d_ticket = nullptr;
+    e.d_trk = nullptr; e.d_frames = nullptr; e.d_tile_trk = nullptr; e.d_gumbel = nullptr; e.d_ticket = nullptr;
     e.d_arena = nullptr; e.d_frame_buf = nullptr; e.h_frames_pinned = nullptr;
 }
 
@@ -190,8 +197,9 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
     // the trackers' states form one array (the kernel indexes it by tracker)
     const size_t states_off = a.take(sizeof(TrackerState) * n);
     // Tiles are numbered per kernel family: the step kernel's trackers first, then the
-    // multinomial trackers (CDF and pull kernels), so no launch carries tiles it skips.
-    int64_t tiles = 0, mtiles = 0;
+    // pull kernel's (multinomial and Gumbel-max), so no launch carries tiles it skips.
+    int64_t tiles = 0, mtiles = 0, gctas = 0;
+    std::vector<int32_t> gumbel_slots, gumbel_prefix(1, 0);
     for (int i = 0; i < n; ++i) {
         const pf_config &c = cfgs[i];
         const int64_t N = c.num_particles;
@@ -216,12 +224,20 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
         o.state = states_off + sizeof(TrackerState) * i;
         o.est = a.take(sizeof(double) * 2 * cap);
         o.stat = a.take(sizeof(double) * 2 * cap);
-        const bool multi = c.resampler == PF_RESAMPLE_MULTINOMIAL;
+        const bool gumbel = c.resampler == PF_RESAMPLE_GUMBEL;
+        const bool multi = c.resampler == PF_RESAMPLE_MULTINOMIAL || gumbel;   // the pull family
         if (c.flags & PF_FLAG_DEBUG_ARRAYS) {
             o.dbga = a.take(sizeof(int32_t) * N);
             if (!multi) o.dbgc = a.take(cdf_b * N);
         }
-        if (multi) o.cdf = a.take(cdf_b * N + 16);
+        if (multi) o.cdf = a.take((gumbel ? sizeof(int32_t) : cdf_b) * N + 16);
+        if (gumbel) {
+            gctas += (N + kGumbelOffspring - 1) / kGumbelOffspring;
+            if (gctas > 0x7fffffff) return PF_ERR_ARG;
+            gumbel_slots.push_back(i);
+            gumbel_prefix.push_back(static_cast<int32_t>(gctas));
+        }
+        e.n_multi += (c.resampler == PF_RESAMPLE_MULTINOMIAL) ? 1 : 0;
         TrackerDev &T = e.h_trk[i];
         fill_tracker_constants(c, T);
         T.tile_begin = static_cast<int32_t>(multi ? mtiles : tiles);
@@ -233,6 +249,8 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
     }
     e.total_tiles = static_cast<int>(tiles);
     e.pull_tiles = static_cast<int>(mtiles);
+    e.n_gumbel = static_cast<int>(gumbel_slots.size());
+    e.gumbel_ctas = static_cast<int>(gctas);
     a.size = a.used + 256;
 
     cudaError_t err = cudaMalloc(reinterpret_cast<void **>(&e.d_arena), a.size);
@@ -242,6 +260,8 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
     if (err == cudaSuccess) err = cudaMalloc(reinterpret_cast<void **>(&e.d_frames), sizeof(FrameRef) * n);
     if (err == cudaSuccess)
         err = cudaMalloc(reinterpret_cast<void **>(&e.d_tile_trk), sizeof(int32_t) * (e.total_tiles + e.pull_tiles + 1));
+    if (err == cudaSuccess && e.n_gumbel > 0)
+        err = cudaMalloc(reinterpret_cast<void **>(&e.d_gumbel), sizeof(int32_t) * (2 * e.n_gumbel + 1));
     if (err == cudaSuccess) err = cudaMalloc(reinterpret_cast<void **>(&e.d_ticket), sizeof(uint32_t));
     if (err == cudaSuccess) err = cudaMallocHost(reinterpret_cast<void **>(&e.h_frames_pinned), sizeof(FrameRef) * n);
     if (err == cudaSuccess) err = cudaMallocHost(reinterpret_cast<void **>(&e.h_init_pinned), sizeof(TrackerState) * n);
@@ -281,7 +301,13 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
             T.cdf = e.d_arena + o.cdf;
             T.dbg_cdf = T.cdf;
         }
-        const int base = (e.cfg[i].resampler == PF_RESAMPLE_MULTINOMIAL) ? e.total_tiles : 0;
+        if (e.cfg[i].resampler == PF_RESAMPLE_GUMBEL) {
+            // written by the argmax kernel, read by the pull kernel; no CDF exists
+            T.anc = reinterpret_cast<int32_t *>(e.d_arena + o.cdf);
+            T.dbg_cdf = nullptr;
+        }
+        const int base = (e.cfg[i].resampler == PF_RESAMPLE_MULTINOMIAL ||
+                          e.cfg[i].resampler == PF_RESAMPLE_GUMBEL) ? e.total_tiles : 0;
         for (int k = 0; k < T.ntiles; ++k) tile_trk[base + T.tile_begin + k] = i;
         st[i] = initial_state(e.cfg[i]);
         e.h_frames[i].active = 1;
@@ -290,6 +316,10 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
     if (err == cudaSuccess)
         err = cudaMemcpyAsync(e.d_tile_trk, tile_trk.data(), sizeof(int32_t) * tile_trk.size(),
                               cudaMemcpyHostToDevice, e.stream);
+    std::vector<int32_t> gtab(gumbel_slots);
+    gtab.insert(gtab.end(), gumbel_prefix.begin(), gumbel_prefix.end());
+    if (err == cudaSuccess && e.n_gumbel > 0)
+        err = cudaMemcpyAsync(e.d_gumbel, gtab.data(), sizeof(int32_t) * gtab.size(), cudaMemcpyHostToDevice, e.stream);
     if (err == cudaSuccess) err = cudaMemsetAsync(e.d_ticket, 0, sizeof(uint32_t), e.stream);
     memcpy(e.h_init_pinned, st.data(), sizeof(TrackerState) * n);
     for (int i = 0; i < n && err == cudaSuccess; ++i)
@@ -320,15 +350,26 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
 }
 
 // One frame's launches: the step kernel over its family's tiles, then, for multinomial
-// trackers, the CDF and pull kernels over theirs (tile table entries after the step
+// and Gumbel-max trackers, the CDF kernel (multinomial), the argmax kernel (Gumbel-max)
+// and the pull kernel over the pull family's tiles (tile table entries after the step
 // family's).  L carries the step family's table and count.
 static int engine_enqueue(const Engine &e, StepLaunch L, cudaStream_t stream) {
     int rc = 0;
     if (e.total_tiles > 0) rc = launch_step(e.prec, L, e.grid, stream);
+    if (rc == 0 && e.n_gumbel > 0) {
+        GumbelLaunch G;
+        G.trk = e.d_trk;
+        G.frames = e.d_frames;
+        G.slots = e.d_gumbel;
+        G.cta_prefix = e.d_gumbel + e.n_gumbel;
+        G.ntrk = e.n_gumbel;
+        G.total_ctas = e.gumbel_ctas;
+        rc = launch_gumbel(e.prec, G, stream);
+    }
     if (rc == 0 && e.pull_tiles > 0) {
         L.tile_trk = e.d_tile_trk + e.total_tiles;
         L.total_tiles = e.pull_tiles;
-        rc = launch_pull(e.prec, L, e.grid_pull, stream);
+        rc = launch_pull(e.prec, L, e.grid_pull, e.n_multi > 0, stream);
     }
     return rc;
 }
@@ -766,6 +807,7 @@ pf_status pf_get_debug(pf_filter *f, int32_t which, void *host_buf, size_t bytes
     Engine &e = f->e;
     const TrackerDev &T = e.h_trk[0];
     if (!T.dbg_anc) return PF_ERR_STATE;
+    if (which == 1 && !T.dbg_cdf) return PF_ERR_ARG;   // a Gumbel-max tracker has no CDF
     const size_t elem = which == 0 ? 4 : (e.prec == PF_REF64 ? 8 : 4);
     if (which < 0 || which > 1 || bytes < elem * static_cast<size_t>(T.N)) return PF_ERR_ARG;
     cudaError_t err = cudaStreamSynchronize(e.stream);

@@ -30,7 +30,9 @@
 // T.cdf; the pull kernel then gives each offspring j the first particle whose CDF value
 // reaches an independent uniform v_j (a binary search over T.cdf), gathers the ancestors'
 // positions of its tile's offspring into shared memory, sizes the likelihood window by
-// them and runs phases 2-5 as the step kernel does.
+// them and runs phases 2-5 as the step kernel does.  Gumbel-max trackers (the log-domain
+// form of the same draw, Sec. 3) skip the CDF kernel: the pull kernel reads the ancestors
+// the argmax kernel (pf_gumbel.cu) wrote to T.anc instead of searching.
 //
 // Scan boundaries.  The prefix between tiles is an exact 128-bit fixed-point sum of
 // the tiles' aggregates, so every tile obtains the same boundary value whichever
@@ -641,7 +643,8 @@ __device__ void finalize_tracker(const TrackerDev &T, TrackerState *st, StepSmem
 
 // Kernel modes: the step kernel (systematic and stratified trackers, every phase), and for
 // multinomial trackers the CDF kernel (phase 1 up to the CDF, written to T.cdf) and the
-// pull kernel (resampling from T.cdf, phases 2-5), launched in that order.
+// pull kernel (resampling from T.cdf, phases 2-5), launched in that order; the pull kernel
+// also takes the Gumbel-max trackers (ancestors from T.anc).
 constexpr int kModeStep = 0, kModeCdf = 1, kModePull = 2;
 
 // One tile of a launch in mode kMode (trackers of the other modes are skipped).
@@ -695,8 +698,10 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
     if (sm.st.status & kStatusTimeout) return;   // a failed step: results are invalid
     // (the host gives each launch only its own family's tiles; the CDF and pull kernels
     // check as well)
-    if constexpr (kMode != kModeStep) {
+    if constexpr (kMode == kModeCdf) {
         if (T.resampler != kResampleMultinomial) return;
+    } else if constexpr (kMode == kModePull) {
+        if (T.resampler != kResampleMultinomial && T.resampler != kResampleGumbel) return;
     }
 
     const int N = static_cast<int>(T.N);
@@ -849,17 +854,26 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
         const pos_t *__restrict__ Yin = static_cast<const pos_t *>(T.py[in]);
         acc_t uq[kItems];
         int lo[kItems], hi[kItems];
+        if (T.resampler == kResampleGumbel) {
+            // Gumbel-max: the argmax kernel wrote every offspring's ancestor
 #pragma unroll
-        for (int h = 0; h < kItems; h += 4) {
-            const uint32_t blk = static_cast<uint32_t>(k0 + eb + h) >> 2;   // k0 + eb is a multiple of 8
-            const uint4 wv = philox4x32_10(make_uint4(blk, static_cast<uint32_t>(t - 1), 1u, T.tracker_id),
-                                           T.key_lo, T.key_hi);
-            const uint32_t ws[4] = {wv.x, wv.y, wv.z, wv.w};
+            for (int m = 0; m < kItems; ++m) {
+                const int a = (eb + m < cnt) ? __ldg(T.anc + PF_IDX(k0 + eb + m, N)) : 0;
+                lo[m] = hi[m] = a > 0 ? a : 0;
+            }
+        } else {
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                if constexpr (kF64) uq[h + i] = uniform_f64(ws[i]); else uq[h + i] = uniform_f32(ws[i]);
-                lo[h + i] = 0;
-                hi[h + i] = (eb + h + i < cnt) ? N : 0;
+            for (int h = 0; h < kItems; h += 4) {
+                const uint32_t blk = static_cast<uint32_t>(k0 + eb + h) >> 2;   // k0 + eb is a multiple of 8
+                const uint4 wv = philox4x32_10(make_uint4(blk, static_cast<uint32_t>(t - 1), 1u, T.tracker_id),
+                                               T.key_lo, T.key_hi);
+                const uint32_t ws[4] = {wv.x, wv.y, wv.z, wv.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    if constexpr (kF64) uq[h + i] = uniform_f64(ws[i]); else uq[h + i] = uniform_f32(ws[i]);
+                    lo[h + i] = 0;
+                    hi[h + i] = (eb + h + i < cnt) ? N : 0;
+                }
             }
         }
         for (bool more = true; more;) {           // first k with C_k >= u, in [lo, hi]
@@ -1485,8 +1499,8 @@ int launch_step(int precision, const StepLaunch &L, int grid, void *stream) {
     return launch_mode<kModeStep>(precision, L, grid, stream);
 }
 
-int launch_pull(int precision, const StepLaunch &L, int grid, void *stream) {
-    const int rc = launch_mode<kModeCdf>(precision, L, grid, stream);
+int launch_pull(int precision, const StepLaunch &L, int grid, bool with_cdf, void *stream) {
+    const int rc = with_cdf ? launch_mode<kModeCdf>(precision, L, grid, stream) : 0;
     return rc != 0 ? rc : launch_mode<kModePull>(precision, L, grid, stream);
 }
 

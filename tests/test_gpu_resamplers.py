@@ -4,11 +4,15 @@ Stratified: the fused step with one independent offset per stratum, u_j = (j + v
 (Sec. 2 names stratified resampling beside the paper's systematic scheme of Sec. 3).
 Multinomial: the step kernel writes the CDF, the pull kernel gives offspring j the first
 particle whose CDF value reaches an independent uniform v_j (Sec. 3's categorical draw).
+Gumbel-max: the argmax kernel gives offspring j the particle maximising L_k + g_jk (the
+log-domain form of the same draw that Sec. 3 weighs), the pull kernel gathers them.
 The checks: the ancestors are exactly the oracle's resampling of the CDF the step computed,
 with the draws from the oracle's own Philox; the REF64 track equals the oracle's FP64 track
 of the same scheme within 1e-9 px; stratified offspring counts stay within two strata of
 N w_k; the option takes effect; the schemes share a batch, each tracker equal to its own
-single run; the bench's launch configuration (2^20 particles) resamples exactly.
+single run; the bench's launch configuration (2^20 particles) resamples exactly.  Gumbel-max
+ancestors equal the oracle's decisions in the kernel's precision up to near ties (FP32
+logs may differ in the last bit between the two sides).
 """
 import numpy as np
 import pytest
@@ -210,12 +214,144 @@ def test_alternative_schemes_at_large_sizes(pf, scheme, N):
     assert np.array_equal(anc, fn(C, draws, "f32"))
 
 
+# ----------------------------------------------------------------------------- Gumbel-max
+def _gumbel_step(pf, v, N, prec, seed, *, tracker=0, T=None):
+    """Run T - 1 frames, read the state's log weights, run frame T - 1 with debug arrays:
+    (ancestors of that step, the log weights they were drawn from, the draws' frame)."""
+    T = v.T if T is None else T
+    f = pf.Filter(v.W, v.H, N, v.radius, prec, init=tuple(v.centres[0]), seed=seed, tracker_id=tracker,
+                  flags=pf.PF_FLAG_DEBUG_ARRAYS, resampler="gumbel")
+    fr = _frames(v)
+    f.run(fr[:T - 1])
+    st = f.get_state()
+    f.step(fr[T - 1])
+    anc = f.debug(0).astype(np.int64)
+    f.close()
+    return anc, st["L"].astype(np.float64), int(st["t"]) - 1
+
+
+def _near_tie(L, seed, t, tracker, j, k_want, k_got, prec):
+    """Offspring j's values at the two indices are within the decision precision's
+    rounding (FP64 variates, the kernel's FP32 or FP64 sum)."""
+    g = oracle.gumbel_variates(seed, t, int(j), L.size, tracker)
+    v = L + g
+    tol = (1e-12 if prec == "ref64" else 1e-5) * max(1.0, abs(v[k_want]))
+    return abs(v[k_want] - v[k_got]) <= tol
+
+
+def _check_gumbel(L, seed, t, tracker, anc, prec):
+    """Ancestors equal the oracle's Gumbel-max decisions in the kernel's precision; where
+    they differ (FP32 logs of the two sides may differ in the last bit) the two values
+    are a near tie, and such offspring are rare."""
+    want = oracle.resample_gumbel(L, seed, t, tracker, "f64" if prec == "ref64" else "f32")
+    bad = np.nonzero(anc != want)[0]
+    assert np.all((anc >= 0) & (anc < L.size))
+    assert bad.size <= max(1, L.size // 1000), bad[:10]
+    for j in bad:
+        assert _near_tie(L, seed, t, tracker, j, want[j], anc[j], prec), (j, want[j], anc[j])
+
+
+@pytest.mark.parametrize("prec", ["ref64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("N", [1, 3, 1000, TILE + 1])
+def test_gumbel_ancestors_exact(pf, prec, N):
+    v = synth.make_video(128, 128, 4, 5, noise=5.0, seed=47)
+    anc, L, t = _gumbel_step(pf, v, N, prec, 23, tracker=6)
+    _check_gumbel(L, 23, t, 6, anc, prec)
+
+
+def test_gumbel_ragged_tiles_f16(pf):
+    """Three tiles and a ragged tail (argmax CTAs of 8 offspring, the last one partial)."""
+    v = synth.make_video(160, 120, 4, 4, noise=5.0, seed=48, v=(1.0, -1.0))
+    anc, L, t = _gumbel_step(pf, v, 3 * TILE + 17, "f16", 24, tracker=1)
+    _check_gumbel(L, 24, t, 1, anc, "f16")
+
+
+@pytest.mark.parametrize("prec", ["ref64", "f16"])
+def test_gumbel_largest_tracker_sampled(pf, prec):
+    """N = 2^16, the largest Gumbel-max tracker: 96 sampled offspring are the argmax of
+    L + g computed one by one from the oracle's variates (up to a near tie)."""
+    v = synth.make_video(512, 512, 3, 5, noise=5.0, seed=1)
+    N = 1 << 16
+    anc, L, t = _gumbel_step(pf, v, N, prec, 1)
+    assert np.all((anc >= 0) & (anc < N))
+    rng = np.random.default_rng(3)
+    for j in np.concatenate([[0, N - 1], rng.choice(N, 94, replace=False)]):
+        best = int(np.argmax(L + oracle.gumbel_variates(1, t, int(j), N, 0)))
+        assert anc[j] == best or _near_tie(L, 1, t, 0, j, best, anc[j], prec), (j, best, anc[j])
+
+
+def test_gumbel_ref64_track_within_1e9(pf):
+    v = synth.make_video(128, 128, 10, 5, noise=5.0, seed=1)
+    est_o, M_o, _ = oracle.track(v.frames, 1000, 5, init=tuple(v.centres[0]), seed=1, resampler="gumbel")
+    f = pf.Filter(v.W, v.H, 1000, 5, "ref64", init=tuple(v.centres[0]), seed=1, resampler="gumbel")
+    f.run(_frames(v))
+    est, ms = f.estimates(0, v.T, with_stats=True)
+    f.close()
+    assert np.abs(est - est_o).max() <= 1e-9
+    assert np.array_equal(ms[:, 0], M_o)
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16", "bf16"])
+def test_gumbel_tracks_the_truth_and_steps_equal_runs(pf, prec):
+    v = synth.make_video(128, 128, 10, 5, noise=5.0, seed=1)
+    est_o, _, _ = oracle.track(v.frames, 1000, 5, init=tuple(v.centres[0]), seed=1, resampler="gumbel")
+    fr = _frames(v)
+    a = pf.Filter(v.W, v.H, 1000, 5, prec, init=tuple(v.centres[0]), seed=1, resampler="gumbel")
+    a.run(fr)
+    b = pf.Filter(v.W, v.H, 1000, 5, prec, init=tuple(v.centres[0]), seed=1, resampler="gumbel")
+    for t in range(v.T):
+        b.step(fr[t])
+    ea, eb = a.estimates(0, v.T), b.estimates(0, v.T)
+    a.close()
+    b.close()
+    assert np.array_equal(ea, eb)
+    assert np.sqrt(np.mean(np.sum((ea - est_o) ** 2, axis=1))) <= 0.5
+
+
+def test_four_schemes_in_one_batch_equal_singles(pf):
+    vids = [synth.make_video(96, 96, 5, 3, noise=5.0, seed=90 + i, v=(1.0, -1.0)) for i in range(5)]
+    Ns = [3000, 2 * TILE + 5, 777, 5000, 1500]
+    rs = ["gumbel", "systematic", "stratified", "multinomial", "gumbel"]
+    for prec in ("ref64", "f32", "f16"):
+        cfgs = [pf.make_config(v.W, v.H, n, v.radius, prec, init=tuple(v.centres[0]), seed=60 + i,
+                               tracker_id=i, resampler=r) for i, (v, n, r) in enumerate(zip(vids, Ns, rs))]
+        b = pf.Batch(cfgs)
+        fr = [_frames(v) for v in vids]
+        for t in range(5):
+            b.step([f[t] for f in fr])
+        got = np.stack([b.estimates(t) for t in range(5)], axis=1)
+        c = b.counters()
+        b.close()
+        assert c["kernel_launches"] == 5 * 4, c      # step, CDF, argmax, pull
+        for i, (v, n, r) in enumerate(zip(vids, Ns, rs)):
+            s = pf.Filter(v.W, v.H, n, v.radius, prec, init=tuple(v.centres[0]), seed=60 + i, tracker_id=i,
+                          resampler=r)
+            s.run(fr[i])
+            assert np.array_equal(s.estimates(0, 5), got[i]), (prec, i, r)
+            s.close()
+
+
+def test_gumbel_limits_and_debug(pf):
+    """N <= 2^16; no CDF to read back; the server refuses Gumbel-max streams."""
+    with pytest.raises(pf.PfError):
+        pf.Filter(64, 64, (1 << 16) + 1, 3, "f16", resampler="gumbel")
+    f = pf.Filter(64, 64, 100, 3, "f32", init=(32.0, 32.0), resampler="gumbel", flags=pf.PF_FLAG_DEBUG_ARRAYS)
+    f.step(np.full((64, 64), 100, np.uint8))
+    with pytest.raises(pf.PfError):
+        f.debug(1)
+    f.close()
+    s = pf.Server(1 << 26, max_streams=2, queue_depth=2)
+    with pytest.raises(pf.PfError):
+        s.open(pf.make_config(64, 64, 100, 3, "f16", resampler="gumbel"))
+    s.close()
+
+
 def test_counters_count_launches_graphs_and_host_bytes(pf):
     """pf_get_counters: one kernel per frame for systematic trackers, three for multinomial
     (step kernel skipped: CDF and pull), one graph replay per resident run, host bytes."""
     v = synth.make_video(96, 80, 7, 3, noise=5.0, seed=44)
     fr = _frames(v)
-    for rs, per in (("systematic", 1), ("multinomial", 2)):
+    for rs, per in (("systematic", 1), ("multinomial", 2), ("gumbel", 2)):
         f = pf.Filter(v.W, v.H, 3000, 3, "f32", init=tuple(v.centres[0]), seed=2, resampler=rs)
         f.step(v.frames[0])                      # host frame
         f.step(fr[1])
