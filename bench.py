@@ -58,6 +58,9 @@ def _args():
     p.add_argument("--tpb-sweep", action="store_true",
                    help="thread-block study: build the step kernel at 128/256/512/1024 threads per CTA and time each")
     p.add_argument("--tpb-child", action="store_true", help=argparse.SUPPRESS)
+    p.add_argument("--gumbel", type=int, default=0, metavar="N",
+                   help="Gumbel-max study only: time Gumbel-max, systematic and multinomial resampling of "
+                        "an N-particle tracker (N <= 2^16) in --precision on the headline video; one JSON object")
     return p.parse_args()
 
 
@@ -665,7 +668,7 @@ def _resamplers(dev, stream):
     return {"workload": WORKLOAD, "unit": METRIC, "by_precision": out}
 
 
-def _gumbel_max(dev, stream):
+def _gumbel_max(dev, stream, sizes=None):
     """Gumbel-max resampling (argmax of L + Gumbel variates, Sec. 3's log-domain
     alternative) against systematic and multinomial resampling on the headline video at
     the tracker sizes it allows (N^2 variates a frame): us per frame over 20 frames, and
@@ -698,10 +701,11 @@ def _gumbel_max(dev, stream):
         return best, rmse
 
     out = {}
-    for prec, sizes in (("ref64", (1000, 4096, 16384)), ("f32", (1000, 4096, 16384, 65536)),
-                        ("f16", (1000, 4096, 16384, 65536))):
+    if sizes is None:
+        sizes = {"ref64": (1000, 4096, 16384), "f32": (1000, 4096, 16384, 65536), "f16": (1000, 4096, 16384, 65536)}
+    for prec, ns in sizes.items():
         rows = []
-        for n in sizes:
+        for n in ns:
             g_us, g_rmse = timed(n, prec, "gumbel")
             s_us, _ = timed(n, prec, "systematic")
             m_us, _ = timed(n, prec, "multinomial")
@@ -795,6 +799,10 @@ def main():
         return _tpb_child()
     if args.tpb_sweep:
         return _tpb_sweep()
+    if args.gumbel:
+        import torch
+        print(json.dumps(_gumbel_max(torch.device("cuda"), torch.cuda.Stream(), {args.precision: (args.gumbel,)})))
+        return 0
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
