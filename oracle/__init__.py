@@ -76,9 +76,11 @@ def _load():
             "orc_resample_multi_f32": (None, [_I64, _P, _P, _P]),
             "orc_gumbel_f64": (None, [_U64, _U32, _U32, _I64, _P, _P]),
             "orc_gumbel_f32": (None, [_U64, _U32, _U32, _I64, _P, _P]),
+            "orc_metropolis_f64": (None, [_U64, _U32, _U32, _I64, _P, ctypes.c_int, _P]),
+            "orc_metropolis_f32": (None, [_U64, _U32, _U32, _I64, _P, ctypes.c_int, _P]),
             "orc_run": (ctypes.c_int, [_P, _I64, ctypes.c_int, ctypes.c_int, ctypes.c_int, _I64,
                                        _I64, ctypes.c_int, _D, _D, _D, _D, _D, _D, _D, _D,
-                                       _U64, _U32, ctypes.c_int, ctypes.c_int, _P, _P, _P]),
+                                       _U64, _U32, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -299,7 +301,45 @@ def gumbel_variates(seed: int, t: int, j: int, N: int, tracker: int = 0) -> np.n
     return -np.log(-np.log(uniform(w)))
 
 
-RESAMPLERS = {"systematic": 0, "stratified": 1, "multinomial": 2, "gumbel": 3}
+METROPOLIS_STEPS = 64     # default chain length B
+
+
+def resample_metropolis(L, B: int, seed: int, t: int, tracker: int = 0, precision: str = "f64"):
+    """Metropolis ancestors of frame t's log weights ``L``: offspring j runs a B-step chain
+    from k = j, proposals k' = floor(w N / 2^32) accepted when ln u <= L_k' - L_k, decided
+    in FP64 or FP32 (L rounded to FP32, ln u from logf)."""
+    if precision == "f64":
+        Lc = np.ascontiguousarray(L, np.float64)
+        fn = _load().orc_metropolis_f64
+    elif precision == "f32":
+        Lc = np.ascontiguousarray(L, np.float32)
+        fn = _load().orc_metropolis_f32
+    else:
+        raise ValueError(precision)
+    a = np.empty(Lc.size, np.int64)
+    fn(seed & 0xFFFFFFFFFFFFFFFF, t, tracker, Lc.size, _ptr(Lc), int(B), _ptr(a))
+    return a
+
+
+def metropolis_chain(L, B: int, seed: int, t: int, j: int, tracker: int = 0):
+    """Offspring j's chain in FP64, step by step: (states after each step, the margin
+    |ln u - (L_k' - L_k)| of each acceptance test)."""
+    L = np.asarray(L, np.float64)
+    N = L.size
+    k, states, margins = j, [], []
+    for b in range(B):
+        w = philox([[b // 2, t, 5 + 256 * j, tracker]], seed)[0]
+        kp = (int(w[2 * (b % 2)]) * N) >> 32
+        lu = float(np.log(uniform([w[2 * (b % 2) + 1]])[0]))
+        d = L[kp] - L[k]
+        margins.append(abs(lu - d))
+        if lu <= d:
+            k = kp
+        states.append(k)
+    return states, margins
+
+
+RESAMPLERS = {"systematic": 0, "stratified": 1, "multinomial": 2, "gumbel": 3, "metropolis": 4}
 
 
 # --------------------------------------------------------------------------- whole tracker
@@ -319,7 +359,8 @@ class FrameRecord:
 
 
 def track_steps(frames: np.ndarray, N: int, r: int, *, init, sigma=(1.0, 1.0), drift=(0.0, 0.0),
-                seed: int = 1, tracker: int = 0, bg=100.0, fg=228.0, nthreads=1, resampler="systematic"):
+                seed: int = 1, tracker: int = 0, bg=100.0, fg=228.0, nthreads=1, resampler="systematic",
+                iters=METROPOLIS_STEPS):
     """Run the tracker phase by phase (Fig. 1), yielding a FrameRecord per frame.
     Same arithmetic as :func:`track`, with every intermediate array exposed."""
     anc = None
@@ -338,6 +379,8 @@ def track_steps(frames: np.ndarray, N: int, r: int, *, init, sigma=(1.0, 1.0), d
             a = resample_multinomial(C, stratified_offsets(seed, t, N, tracker), "f64")
         elif resampler == "gumbel":
             a = resample_gumbel(L, seed, t, tracker, "f64")
+        elif resampler == "metropolis":
+            a = resample_metropolis(L, iters, seed, t, tracker, "f64")
         elif resampler == "systematic":
             a = resample(C, u0, "f64")
         else:
@@ -347,7 +390,8 @@ def track_steps(frames: np.ndarray, N: int, r: int, *, init, sigma=(1.0, 1.0), d
 
 
 def track(frames: np.ndarray, N: int, r: int, *, init, sigma=(1.0, 1.0), drift=(0.0, 0.0),
-          seed: int = 1, tracker: int = 0, bg=100.0, fg=228.0, nthreads=1, resampler="systematic"):
+          seed: int = 1, tracker: int = 0, bg=100.0, fg=228.0, nthreads=1, resampler="systematic",
+          iters=METROPOLIS_STEPS):
     """Whole FP64 track in C.  Returns (est (T,2), M (T,), S (T,))."""
     f = np.ascontiguousarray(frames, dtype=np.uint8)
     T, H, W = f.shape
@@ -356,7 +400,7 @@ def track(frames: np.ndarray, N: int, r: int, *, init, sigma=(1.0, 1.0), drift=(
     S = np.empty(T, np.float64)
     rc = _load().orc_run(_ptr(f), H * W, T, W, H, W, N, r, bg, fg, init[0], init[1],
                          sigma[0], sigma[1], drift[0], drift[1], seed & 0xFFFFFFFFFFFFFFFF,
-                         tracker, nthreads, RESAMPLERS[resampler], _ptr(est), _ptr(M), _ptr(S))
+                         tracker, nthreads, RESAMPLERS[resampler], int(iters), _ptr(est), _ptr(M), _ptr(S))
     if rc != 0:
         raise MemoryError("oracle could not allocate its arrays")
     return est, M, S

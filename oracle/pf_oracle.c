@@ -18,6 +18,7 @@
  *   stratified resampling (Sec. 2)  orc_stratified_offsets, orc_resample_strat_f64 / _f32
  *   multinomial resampling (Sec. 3) orc_resample_multi_f64 / _f32 (draws: orc_stratified_offsets)
  *   Gumbel-max resampling (Sec. 3)  orc_gumbel_f64 / _f32 (argmax of L + Gumbel variates)
+ *   Metropolis resampling (Sec. 2)  orc_metropolis_f64 / _f32 (B-step chains on exp(L))
  * Where the paper is silent the readings are (numbered as in the design notes):
  *   C1  Eq. 3 is summed over the template pixels and divided by 50*|D|.
  *   C2  template D = integer offsets with dx^2+dy^2 <= r^2 (centre included).
@@ -33,6 +34,8 @@
  *       Multinomial (alternative scheme): u_j = v_j, N independent draws.
  *       Gumbel-max (alternative scheme): a_j = argmax_k L_k - ln(-ln u_jk), ties to the
  *       smallest k, N draws per offspring (tag 4 + 256 j).
+ *       Metropolis (alternative scheme): a B-step chain from k = j, proposals uniform,
+ *       accepted when ln u <= L_k' - L_k (tag 5 + 256 j, two steps per draw).
  *   C11 draws: Philox4x32-10 words -> 23-bit uniforms -> Box-Muller in FP64.
  *   C12 at t = 0 every ancestor sits at (init_x, init_y).
  * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), written here
@@ -510,6 +513,46 @@ void orc_gumbel_f32(uint64_t seed, uint32_t t, uint32_t tracker, int64_t N, cons
     }
 }
 
+/* Metropolis resampling (Sec. 2 cites it, with rejection resampling, as a scheme that
+ * needs no global sum; Murray, Lee and Jacob, 2016): offspring j runs a Metropolis chain
+ * of B steps over the particle indices with target exp(L_k), started at k = j.  Step b
+ * proposes k' uniform on {0, ..., N-1} and moves there when u <= exp(L_k' - L_k), taken in
+ * the log form ln u <= L_k' - L_k; a_j is the state after B steps.  Step b of offspring j
+ * reads the Philox draw (b / 2, t, 5 + 256 j, tracker): word 2 (b mod 2) gives the
+ * proposal k' = floor(w N / 2^32), word 2 (b mod 2) + 1 the uniform u; j < 2^24. */
+void orc_metropolis_f64(uint64_t seed, uint32_t t, uint32_t tracker, int64_t N, const double *L, int B, int64_t *a)
+{
+    for (int64_t j = 0; j < N; ++j) {
+        int64_t k = j;
+        for (int b = 0; b < B; ++b) {
+            uint32_t w[4];
+            orc_philox_draw(seed, (uint32_t)(b / 2), t, 5u + 256u * (uint32_t)j, tracker, w);
+            int64_t kp = (int64_t)(((uint64_t)w[2 * (b % 2)] * (uint64_t)N) >> 32);
+            double u = orc_uniform(w[2 * (b % 2) + 1]);
+            if (log(u) <= L[kp] - L[k]) k = kp;
+        }
+        a[j] = k;
+    }
+}
+
+/* The same chains with the acceptance test in FP32 (L held in FP32, ln u from logf). */
+void orc_metropolis_f32(uint64_t seed, uint32_t t, uint32_t tracker, int64_t N, const float *L, int B, int64_t *a)
+{
+    for (int64_t j = 0; j < N; ++j) {
+        int64_t k = j;
+        for (int b = 0; b < B; ++b) {
+            uint32_t w[4];
+            orc_philox_draw(seed, (uint32_t)(b / 2), t, 5u + 256u * (uint32_t)j, tracker, w);
+            int64_t kp = (int64_t)(((uint64_t)w[2 * (b % 2)] * (uint64_t)N) >> 32);
+            volatile float u = (float)orc_uniform(w[2 * (b % 2) + 1]);
+            volatile float lu = logf(u);
+            volatile float d = L[kp] - L[k];
+            if (lu <= d) k = kp;
+        }
+        a[j] = k;
+    }
+}
+
 /* The same systematic decisions with the stratum points formed by a division,
  * u_j = (j + u0) / N, and no saved reciprocal: the naive form of Sec. 3's performance
  * optimisation (the GPU's naive study build takes these decisions). */
@@ -545,7 +588,7 @@ void orc_resample_div_f32(int64_t N, const float *C, float u0, int64_t *a)
 int orc_run(const uint8_t *frames, int64_t frame_stride, int T, int W, int H, int64_t pitch,
             int64_t N, int r, double bg, double fg, double init_x, double init_y,
             double sigma_x, double sigma_y, double drift_x, double drift_y,
-            uint64_t seed, uint32_t tracker, int nthreads, int resampler,
+            uint64_t seed, uint32_t tracker, int nthreads, int resampler, int iters,
             double *est, double *M_out, double *S_out)
 {
     double *xa = malloc((size_t)N * sizeof(double));
@@ -573,6 +616,8 @@ int orc_run(const uint8_t *frames, int64_t frame_stride, int T, int W, int H, in
             orc_cdf(N, e, S, C);
             if (resampler == 3) {
                 orc_gumbel_f64(seed, (uint32_t)t, tracker, N, L, a);
+            } else if (resampler == 4) {
+                orc_metropolis_f64(seed, (uint32_t)t, tracker, N, L, iters, a);
             } else if (resampler) {
                 orc_stratified_offsets(seed, (uint32_t)t, tracker, N, v);
                 if (resampler == 2) orc_resample_multi_f64(N, C, v, a);

@@ -570,6 +570,92 @@ def test_gumbel_fp32_decisions_agree_with_fp64_outside_near_ties():
         assert np.mean(a64 == a32) >= 0.999
 
 
+# ----------------------------------------------------------------------------- Metropolis resampling
+def _chain_matrix(L):
+    """Transition matrix of one Metropolis step on exp(L): propose k' uniformly (itself
+    included), move with probability min(1, exp(L_k' - L_k))."""
+    L = np.asarray(L, np.float64)
+    n = L.size
+    P = np.zeros((n, n))
+    for k in range(n):
+        for kp in range(n):
+            if kp != k:
+                P[k, kp] = min(1.0, math.exp(L[kp] - L[k])) / n
+        P[k, k] = 1.0 - P[k].sum()
+    return P
+
+
+def test_metropolis_zero_steps_is_identity():
+    L = np.array([0.0, 5.0, -3.0, 2.0, 1.0])
+    assert np.array_equal(oracle.resample_metropolis(L, 0, 1, 0), np.arange(5))
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("B", [1, 2, 5])
+def test_metropolis_small_chains_follow_the_transition_matrix(prec, B):
+    """N = 3: offspring j's ancestor after B steps is distributed as row j of P^B, P the
+    Metropolis transition matrix (built here from its definition); 6000 frames, every
+    entry within 5 binomial standard errors."""
+    L = np.array([0.0, math.log(3.0), -0.7])
+    PB = np.linalg.matrix_power(_chain_matrix(L), B)
+    frames = 6000
+    a = np.array([oracle.resample_metropolis(L, B, 13, t, 3, prec) for t in range(frames)])
+    for j in range(3):
+        freq = np.bincount(a[:, j], minlength=3) / frames
+        se = np.sqrt(PB[j] * (1 - PB[j]) / frames)
+        assert np.all(np.abs(freq - PB[j]) <= 5 * se + 1e-12), (j, freq, PB[j])
+
+
+def test_metropolis_long_chains_reach_the_categorical_law():
+    """The chain's stationary law is exp(L_k) / sum exp(L): after 200 steps the counts
+    over 3000 frames of 5 offspring match the softmax (6 standard errors)."""
+    L = np.array([0.0, 1.0, -0.5, 0.7, 0.2])
+    p = _softmax(L)
+    frames, n = 3000, L.size
+    c = sum(_counts(oracle.resample_metropolis(L, 200, 17, t, 0), n) for t in range(frames)).astype(np.float64)
+    tot = frames * n
+    assert np.all(np.abs(c / tot - p) <= 6 * np.sqrt(p * (1 - p) / tot))
+
+
+def test_metropolis_equal_weights_take_the_last_proposal():
+    """Equal log weights: ln u < 0 accepts every proposal, so the ancestor is uniform over
+    the particles whatever the start (chi-square, 0.9999 quantile, 63 dof)."""
+    n, frames = 64, 200
+    c = sum(_counts(oracle.resample_metropolis(np.full(n, 2.5), 3, 19, t, 0), n) for t in range(frames))
+    expect = frames * np.ones(n)
+    assert float(np.sum((c - expect) ** 2 / expect)) < 116.0
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_metropolis_dominant_particle_absorbs(prec):
+    """One particle far above the rest (which share one log weight): a chain that proposes
+    it moves there and never leaves, so a_j is the dominant particle exactly when one of
+    the B proposals hits it (or j is it), which happens with probability
+    1 - (1 - 1/N)^B."""
+    n, B, d = 16, 12, 5
+    L = np.full(n, -500.0)
+    L[d] = 0.0
+    frames = 3000
+    a = np.concatenate([oracle.resample_metropolis(L, B, 23, t, 0, prec) for t in range(frames)])
+    starts = np.tile(np.arange(n), frames)
+    others = starts != d
+    p = 1.0 - (1.0 - 1.0 / n) ** B
+    se = math.sqrt(p * (1 - p) / others.sum())
+    assert abs(np.mean(a[others] == d) - p) <= 5 * se
+    assert np.all(a[~others] == d)
+
+
+def test_metropolis_fp32_decisions_agree_with_fp64():
+    rng = np.random.default_rng(25)
+    L = np.round(rng.normal(0.0, 2.0, 3000), 3)
+    a64 = oracle.resample_metropolis(L, 32, 29, 4, 1, "f64")
+    a32 = oracle.resample_metropolis(L, 32, 29, 4, 1, "f32")
+    for j in np.nonzero(a64 != a32)[0]:
+        _, margins = oracle.metropolis_chain(L, 32, 29, 4, int(j), 1)
+        assert min(margins) <= 1e-5, j                 # a near tie in some acceptance test
+    assert np.mean(a64 == a32) >= 0.999
+
+
 # ----------------------------------------------------------------------------- propagation, Eq. 1-2
 def test_propagation_moments_paper_motion():
     """Eq. 1-2: x ~ N(1 + x_anc, 5^2), y ~ N(2 + y_anc, 2^2)."""
@@ -631,6 +717,21 @@ def test_track_gumbel_recovers_ground_truth_config1():
     assert np.sqrt(np.mean(err ** 2)) < 1.0 and err.max() < 1.5
     recs = list(oracle.track_steps(v.frames, 1000, 5, init=tuple(v.centres[0]), seed=1, resampler="gumbel"))
     assert np.array_equal(np.array([r.est for r in recs]), est)
+
+
+def test_track_metropolis_recovers_ground_truth_config1():
+    v = synth.make_video(128, 128, 10, 5, noise=5.0, seed=1)
+    est, _, _ = oracle.track(v.frames, 1000, 5, init=tuple(v.centres[0]), seed=1, resampler="metropolis")
+    err = np.sqrt(np.sum((est - v.centres) ** 2, axis=1))
+    assert np.sqrt(np.mean(err ** 2)) < 1.0 and err.max() < 1.5
+    recs = list(oracle.track_steps(v.frames, 1000, 5, init=tuple(v.centres[0]), seed=1, resampler="metropolis"))
+    assert np.array_equal(np.array([r.est for r in recs]), est)
+    # the chain is the oracle's own: its states, replayed step by step, end at a_j
+    L = recs[4].L
+    a = oracle.resample_metropolis(L, 64, 1, 4, 0)
+    for j in (0, 17, 999):
+        states, _ = oracle.metropolis_chain(L, 64, 1, 4, j, 0)
+        assert states[-1] == a[j]
 
 
 def test_track_noiseless_recovers_integer_centres():
