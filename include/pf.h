@@ -81,12 +81,26 @@ typedef enum {
  *               maximum, sum or CDF of the weights is needed for the draw, but it costs N^2
  *               variates a frame, so N <= 2^16 (PF_ERR_ARG beyond).  Two kernels per frame
  *               (the argmax, then the pull kernel); trackers and batches only, as
- *               MULTINOMIAL.  pf_get_debug(which = 1) answers PF_ERR_ARG (no CDF). */
+ *               MULTINOMIAL.  pf_get_debug(which = 1) answers PF_ERR_ARG (no CDF).
+ *   METROPOLIS: Metropolis resampling (Sec. 2 cites it, after Murray, Lee and Jacob, as a
+ *               scheme with no global sum): offspring j runs a chain of B =
+ *               pf_config.resampler_steps steps over the particle indices with target
+ *               exp(L_k), started at k = j; step b proposes k' = floor(w N / 2^32) and
+ *               moves there when ln u <= L_k' - L_k, with w and u the words 2 (b mod 2)
+ *               and 2 (b mod 2) + 1 of Philox(b / 2, t, 5 + 256 j, tracker_id) (u uniform
+ *               as above); a_j is the state after B steps.  The test runs in FP64
+ *               (PF_REF64) or FP32 (the others), as for GUMBEL.  Biased for small B (the
+ *               chain has not mixed); no maximum, sum or CDF is needed for the draw and
+ *               the cost is B steps per offspring at any N (N <= 2^24, PF_ERR_ARG beyond).
+ *               Two kernels per frame (the chains, then the
+ *               pull kernel); trackers and batches only; pf_get_debug(which = 1) answers
+ *               PF_ERR_ARG. */
 typedef enum {
     PF_RESAMPLE_SYSTEMATIC = 0,
     PF_RESAMPLE_STRATIFIED = 1,
     PF_RESAMPLE_MULTINOMIAL = 2,
-    PF_RESAMPLE_GUMBEL = 3
+    PF_RESAMPLE_GUMBEL = 3,
+    PF_RESAMPLE_METROPOLIS = 4
 } pf_resampler;
 
 /* pf_config.flags */
@@ -108,6 +122,8 @@ typedef struct {
     uint32_t flags;            /* PF_FLAG_* */
     int32_t est_capacity;      /* frames of estimates kept on the device; 0 = 4096 */
     int32_t resampler;         /* pf_resampler (0 = systematic) */
+    int32_t resampler_steps;   /* METROPOLIS: chain length B in [1, 4096]; 0 = 64.  Others: 0 */
+    int32_t reserved;          /* must be 0 */
 } pf_config;
 
 typedef struct pf_filter pf_filter;

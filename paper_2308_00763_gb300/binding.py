@@ -19,7 +19,7 @@ __all__ = [
     "PF_OK", "PF_ERR_ARG", "PF_ERR_OOM", "PF_ERR_CUDA", "PF_ERR_TIMEOUT", "PF_ERR_STATE",
     "PF_ERR_ADMISSION", "PF_REF64", "PF_F32", "PF_F16", "PF_BF16", "PF_FLAG_DEBUG_ARRAYS",
     "PF_FLAG_ACCUM32", "PF_FLAG_TUNED", "PF_RESAMPLE_SYSTEMATIC", "PF_RESAMPLE_STRATIFIED", "PF_RESAMPLE_MULTINOMIAL",
-    "PF_RESAMPLE_GUMBEL", "RESAMPLERS", "PfTuning", "pf_autotune", "pf_autotune_batch", "pf_tuning_lookup",
+    "PF_RESAMPLE_GUMBEL", "PF_RESAMPLE_METROPOLIS", "RESAMPLERS", "PfTuning", "pf_autotune", "pf_autotune_batch", "pf_tuning_lookup",
     "pf_tuning_store", "pf_tuning_clear", "autotune", "autotune_batch", "PfConfig", "PfStateHeader", "PfError", "lib", "library_path",
     "pf_status_string", "pf_create", "pf_step_frame", "pf_run_frames", "pf_estimate",
     "pf_estimates", "pf_frames_done", "pf_get_counters", "pf_batch_get_counters", "PfCounters", "pf_reset", "pf_destroy", "pf_get_state", "pf_set_state", "pf_get_debug",
@@ -38,9 +38,11 @@ PF_FLAG_DEBUG_ARRAYS = 0x1
 PF_FLAG_ACCUM32 = 0x2
 PF_FLAG_TUNED = 0x4
 PRECISIONS = {"ref64": PF_REF64, "f64": PF_REF64, "f32": PF_F32, "f16": PF_F16, "bf16": PF_BF16}
-PF_RESAMPLE_SYSTEMATIC, PF_RESAMPLE_STRATIFIED, PF_RESAMPLE_MULTINOMIAL, PF_RESAMPLE_GUMBEL = range(4)
+PF_RESAMPLE_SYSTEMATIC, PF_RESAMPLE_STRATIFIED, PF_RESAMPLE_MULTINOMIAL, PF_RESAMPLE_GUMBEL, \
+    PF_RESAMPLE_METROPOLIS = range(5)
 RESAMPLERS = {"systematic": PF_RESAMPLE_SYSTEMATIC, "stratified": PF_RESAMPLE_STRATIFIED,
-              "multinomial": PF_RESAMPLE_MULTINOMIAL, "gumbel": PF_RESAMPLE_GUMBEL}
+              "multinomial": PF_RESAMPLE_MULTINOMIAL, "gumbel": PF_RESAMPLE_GUMBEL,
+              "metropolis": PF_RESAMPLE_METROPOLIS}
 _POS_DTYPE = {PF_REF64: np.float64, PF_F32: np.float32, PF_F16: np.float16, PF_BF16: None}
 
 
@@ -55,6 +57,7 @@ class PfConfig(ctypes.Structure):
         ("drift_x", ctypes.c_double), ("drift_y", ctypes.c_double),
         ("seed", ctypes.c_uint64), ("tracker_id", ctypes.c_uint32), ("flags", ctypes.c_uint32),
         ("est_capacity", ctypes.c_int32), ("resampler", ctypes.c_int32),
+        ("resampler_steps", ctypes.c_int32), ("reserved", ctypes.c_int32),
     ]
 
 
@@ -512,14 +515,14 @@ def pf_server_replay(h, events, n_streams: int, realtime: bool):
 
 def make_config(width, height, num_particles, disk_radius, precision="f32", *, init=(0.0, 0.0),
                 sigma=(1.0, 1.0), drift=(0.0, 0.0), seed=1, tracker_id=0, bg=100.0, fg=228.0,
-                flags=0, est_capacity=0, resampler="systematic") -> PfConfig:
+                flags=0, est_capacity=0, resampler="systematic", resampler_steps=0) -> PfConfig:
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     rs = RESAMPLERS[resampler] if isinstance(resampler, str) else int(resampler)
     return PfConfig(width=width, height=height, num_particles=num_particles, disk_radius=disk_radius,
                     precision=prec, bg_level=bg, fg_level=fg, init_x=init[0], init_y=init[1],
                     sigma_x=sigma[0], sigma_y=sigma[1], drift_x=drift[0], drift_y=drift[1],
                     seed=seed & 0xFFFFFFFFFFFFFFFF, tracker_id=tracker_id, flags=flags,
-                    est_capacity=est_capacity, resampler=rs)
+                    est_capacity=est_capacity, resampler=rs, resampler_steps=int(resampler_steps), reserved=0)
 
 
 def _torch():

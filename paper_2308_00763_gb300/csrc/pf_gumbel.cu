@@ -20,6 +20,7 @@
 // offspring over the warps' results.  The pull kernel gathers the ancestors written here.
 #include <math.h>
 
+#include "pf_ancestor.cuh"
 #include "pf_device.cuh"
 #include "pf_internal.h"
 
@@ -39,7 +40,7 @@ __device__ __forceinline__ void take_best(A &v, int &k, A v2, int k2) {
 }
 
 template <int P>
-__global__ void __launch_bounds__(kGumbelThreads) gumbel_kernel(const GumbelLaunch G) {
+__global__ void __launch_bounds__(kGumbelThreads) gumbel_kernel(const AncestorLaunch G) {
     using lik_t = typename Prec<P>::lik_t;
     using acc_t = typename Prec<P>::acc_t;
     constexpr int kJ = kGumbelOffspring;
@@ -47,20 +48,15 @@ __global__ void __launch_bounds__(kGumbelThreads) gumbel_kernel(const GumbelLaun
     __shared__ acc_t s_v[kWarps][kJ];
     __shared__ int s_k[kWarps][kJ];
 
-    // the tracker g with cta_prefix[g] <= b < cta_prefix[g + 1]
     const int b = static_cast<int>(blockIdx.x);
-    int lo = 0, hi = G.ntrk - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(G.cta_prefix + mid) <= b) lo = mid; else hi = mid - 1;
-    }
-    const int slot = __ldg(G.slots + lo);
+    const int g = ancestor_tracker(G, b);
+    const int slot = __ldg(G.slots + g);
     const TrackerDev &T = G.trk[slot];
     const TrackerState *st = T.state;
     const int64_t t = st->t;
     if (t <= 0 || (st->status & kStatusTimeout) || !G.frames[slot].active) return;
     const int N = static_cast<int>(T.N);
-    const int j0 = (b - __ldg(G.cta_prefix + lo)) * kJ;
+    const int j0 = (b - __ldg(G.cta_prefix + g)) * kJ;
     const lik_t *__restrict__ L = static_cast<const lik_t *>(T.pl[static_cast<int>((t + 1) & 1)]);
     const uint32_t tctr = static_cast<uint32_t>(t - 1);
     const uint32_t key_lo = T.key_lo, key_hi = T.key_hi, trk_id = T.tracker_id;
@@ -127,14 +123,14 @@ __global__ void __launch_bounds__(kGumbelThreads) gumbel_kernel(const GumbelLaun
 }
 
 template <int P>
-int launch_p(const GumbelLaunch &G, cudaStream_t s) {
+int launch_p(const AncestorLaunch &G, cudaStream_t s) {
     gumbel_kernel<P><<<G.total_ctas, kGumbelThreads, 0, s>>>(G);
     return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
 
 }  // namespace
 
-int launch_gumbel(int precision, const GumbelLaunch &G, void *stream) {
+int launch_gumbel(int precision, const AncestorLaunch &G, void *stream) {
     if (G.total_ctas <= 0 || G.ntrk <= 0) return 0;
     const cudaStream_t s = static_cast<cudaStream_t>(stream);
     switch (precision) {

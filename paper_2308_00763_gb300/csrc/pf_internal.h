@@ -31,7 +31,16 @@ constexpr int kResampleSystematic = 0;
 constexpr int kResampleStratified = 1;
 constexpr int kResampleMultinomial = 2;   // CDF by the step kernel, offspring by the pull kernel
 constexpr int kResampleGumbel = 3;        // ancestors by the Gumbel-max kernel, offspring by the pull kernel
+constexpr int kResampleMetropolis = 4;    // ancestors by the Metropolis kernel, offspring by the pull kernel
 constexpr int64_t kGumbelMaxN = 1ll << 16; // N^2 draws a frame
+constexpr int64_t kMetropolisMaxN = 1ll << 24;   // offspring index in the Philox tag
+constexpr int kMetropolisMaxSteps = 4096;
+constexpr int kMetropolisDefaultSteps = 64;
+
+// Schemes whose ancestors an ancestor kernel writes to T.anc before the pull kernel runs.
+__host__ __device__ constexpr bool ancestors_given(int resampler) {
+    return resampler == kResampleGumbel || resampler == kResampleMetropolis;
+}
 
 // Device status bits (sticky, per tracker).
 constexpr uint32_t kStatusTimeout = 0x1u;
@@ -99,6 +108,7 @@ struct TrackerDev {
     double inv_n;              // 1.0 / N
     float inv_n_f;             // 1.0f / (float)N
     int32_t resampler;         // pf_resampler
+    int32_t steps;             // Metropolis: chain length B
     // FP32 copies for the FP32 kernels
     float init_xf, init_yf, drift_xf, drift_yf, sigma_xf, sigma_yf;
     float c1f, c2Df, denf;
@@ -107,7 +117,7 @@ struct TrackerDev {
     int32_t *dbg_anc;          // NULL unless PF_FLAG_DEBUG_ARRAYS
     void *dbg_cdf;
     void *cdf;                 // multinomial: the normalised CDF of the previous frame [N] (FP64 / FP32)
-    int32_t *anc;              // Gumbel-max: the ancestor of every offspring [N]
+    int32_t *anc;              // Gumbel-max, Metropolis: the ancestor of every offspring [N]
     LookbackDesc *look;
     TilePartial *part;
     uint32_t *done;
@@ -139,16 +149,18 @@ struct StepLaunch {
 int launch_step(int precision, const StepLaunch &L, int grid, void *stream);
 // The pull family's kernels after launch_step on the same stream: the multinomial
 // trackers' CDF kernel (when with_cdf), then the pull kernel (the offspring of the
-// multinomial and Gumbel-max trackers; the Gumbel-max ancestors come from launch_gumbel,
-// enqueued before it).
+// multinomial, Gumbel-max and Metropolis trackers; the last two read the ancestors that
+// launch_gumbel / launch_metropolis wrote, enqueued before it).
 int launch_pull(int precision, const StepLaunch &L, int grid, bool with_cdf, void *stream);
 
-// Gumbel-max ancestors of the trackers in slots[0 .. ntrk-1]: CTA b works on tracker g with
-// cta_prefix[g] <= b < cta_prefix[g + 1], offspring (b - cta_prefix[g]) * kGumbelOffspring
-// onwards.  A tracker at frame 0, with a failed step, or inactive in frames[] is skipped.
-constexpr int kGumbelOffspring = 8;       // offspring per CTA
+// An ancestor kernel over the trackers in slots[0 .. ntrk-1]: CTA b works on tracker g with
+// cta_prefix[g] <= b < cta_prefix[g + 1], offspring (b - cta_prefix[g]) * (offspring per
+// CTA) onwards.  A tracker at frame 0, with a failed step, or inactive in frames[] is
+// skipped.
+constexpr int kGumbelOffspring = 8;       // Gumbel-max: offspring per CTA
 constexpr int kGumbelThreads = 256;
-struct GumbelLaunch {
+constexpr int kMetropolisThreads = 256;   // Metropolis: one offspring per thread
+struct AncestorLaunch {
     const TrackerDev *trk;     // device array indexed by slot
     const FrameRef *frames;    // device array indexed by slot
     const int32_t *slots;      // device array [ntrk]
@@ -156,7 +168,8 @@ struct GumbelLaunch {
     int32_t ntrk;
     int32_t total_ctas;
 };
-int launch_gumbel(int precision, const GumbelLaunch &G, void *stream);
+int launch_gumbel(int precision, const AncestorLaunch &G, void *stream);
+int launch_metropolis(int precision, const AncestorLaunch &G, void *stream);
 int step_grid_size(int precision, int total_tiles);
 // Particles per tile for a tracker of n particles.  A tracker of at least half a device
 // of full tiles (SMs x CTAs per SM x kTile / 2 particles) takes the smallest multiple of

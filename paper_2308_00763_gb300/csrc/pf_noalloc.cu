@@ -99,6 +99,7 @@ extern "C" pf_status pf_step_frame_noalloc(const pf_config *cfg, const pf_state_
     if (!isfinite(c.drift_x) || !isfinite(c.drift_y) || !isfinite(c.bg_level) || !isfinite(c.fg_level)) return PF_ERR_ARG;
     if (c.flags & ~PF_FLAG_ACCUM32) return PF_ERR_ARG;   // no debug arrays here
     if (c.resampler != PF_RESAMPLE_SYSTEMATIC && c.resampler != PF_RESAMPLE_STRATIFIED) return PF_ERR_ARG;
+    if (c.resampler_steps != 0 || c.reserved != 0) return PF_ERR_ARG;
     if (pitch_bytes < c.width) return PF_ERR_ARG;
     const pf_state_header &h = *state_in;
     if (h.magic != 0x31534650u || h.precision != c.precision || h.num_particles != c.num_particles || h.t < 0)

@@ -98,14 +98,18 @@ struct Engine {
     FrameRef *d_frames = nullptr;
     FrameRef *h_frames_pinned = nullptr;
     int32_t *d_tile_trk = nullptr;
-    int32_t *d_gumbel = nullptr;       // Gumbel-max trackers: [n_gumbel] slots, then [n_gumbel + 1] CTA prefix
+    // an ancestor kernel's trackers: device table of [n] slots, then [n + 1] CTA prefix
+    struct AncestorTable {
+        int32_t *d = nullptr;
+        int n = 0;
+        int ctas = 0;
+    };
+    AncestorTable gumbel, metro;       // Gumbel-max, Metropolis
     uint32_t *d_ticket = nullptr;
     char *d_arena = nullptr;
     int total_tiles = 0;               // tiles of the step kernel's trackers (systematic, stratified)
     int pull_tiles = 0;                // tiles of the pull kernel's trackers (multinomial, Gumbel-max)
     int n_multi = 0;                   // multinomial trackers (the CDF kernel runs when > 0)
-    int n_gumbel = 0;                  // Gumbel-max trackers (the argmax kernel runs when > 0)
-    int gumbel_ctas = 0;
     int grid = 0;
     int grid_pull = 0;
     int ctas_cap = 0;                  // CTAs per SM (0: as many as fit)
@@ -125,7 +129,8 @@ struct Engine {
     // counters (pf_get_counters): launches enqueued, graph replays, host frame bytes copied
     int64_t n_step_launches = 0, n_kernels = 0, n_graphs = 0, n_host_bytes = 0;
     int kernels_per_step() const {
-        return (total_tiles > 0 ? 1 : 0) + (pull_tiles > 0 ? 1 : 0) + (n_multi > 0 ? 1 : 0) + (n_gumbel > 0 ? 1 : 0);
+        return (total_tiles > 0 ? 1 : 0) + (pull_tiles > 0 ? 1 : 0) + (n_multi > 0 ? 1 : 0) + (gumbel.n > 0 ? 1 : 0) +
+               (metro.n > 0 ? 1 : 0);
     }
 
     pf_status fail(pf_status s) {
@@ -160,14 +165,16 @@ static void engine_free(Engine &e) {
     cudaFree(e.d_trk);
     cudaFree(e.d_frames);
     cudaFree(e.d_tile_trk);
-    cudaFree(e.d_gumbel);
+    cudaFree(e.gumbel.d);
+    cudaFree(e.metro.d);
     cudaFree(e.d_ticket);
     cudaFree(e.d_arena);
     cudaFree(e.d_frame_buf);
     if (e.h_frames_pinned) cudaFreeHost(e.h_frames_pinned);
     if (e.h_init_pinned) cudaFreeHost(e.h_init_pinned);
     e.h_init_pinned = nullptr;
-    e.d_trk = nullptr; e.d_frames = nullptr; e.d_tile_trk = nullptr; e.d_gumbel = nullptr; e.d_ticket = nullptr;
+    e.d_trk = nullptr; e.d_frames = nullptr; e.d_tile_trk = nullptr; e.gumbel.d = nullptr; e.metro.d = nullptr;
+    e.d_ticket = nullptr;
     e.d_arena = nullptr; e.d_frame_buf = nullptr; e.h_frames_pinned = nullptr;
 }
 
@@ -197,9 +204,10 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
     // the trackers' states form one array (the kernel indexes it by tracker)
     const size_t states_off = a.take(sizeof(TrackerState) * n);
     // Tiles are numbered per kernel family: the step kernel's trackers first, then the
-    // pull kernel's (multinomial and Gumbel-max), so no launch carries tiles it skips.
-    int64_t tiles = 0, mtiles = 0, gctas = 0;
-    std::vector<int32_t> gumbel_slots, gumbel_prefix(1, 0);
+    // pull kernel's (multinomial, Gumbel-max, Metropolis), so no launch carries tiles it
+    // skips.  The ancestor kernels number their CTAs per scheme.
+    int64_t tiles = 0, mtiles = 0;
+    std::vector<int32_t> atab[2], aprefix[2] = {{0}, {0}};   // Gumbel-max, Metropolis
     for (int i = 0; i < n; ++i) {
         const pf_config &c = cfgs[i];
         const int64_t N = c.num_particles;
@@ -224,18 +232,20 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
         o.state = states_off + sizeof(TrackerState) * i;
         o.est = a.take(sizeof(double) * 2 * cap);
         o.stat = a.take(sizeof(double) * 2 * cap);
-        const bool gumbel = c.resampler == PF_RESAMPLE_GUMBEL;
-        const bool multi = c.resampler == PF_RESAMPLE_MULTINOMIAL || gumbel;   // the pull family
+        const bool given = ancestors_given(c.resampler);          // Gumbel-max, Metropolis
+        const bool multi = c.resampler == PF_RESAMPLE_MULTINOMIAL || given;   // the pull family
         if (c.flags & PF_FLAG_DEBUG_ARRAYS) {
             o.dbga = a.take(sizeof(int32_t) * N);
             if (!multi) o.dbgc = a.take(cdf_b * N);
         }
-        if (multi) o.cdf = a.take((gumbel ? sizeof(int32_t) : cdf_b) * N + 16);
-        if (gumbel) {
-            gctas += (N + kGumbelOffspring - 1) / kGumbelOffspring;
-            if (gctas > 0x7fffffff) return PF_ERR_ARG;
-            gumbel_slots.push_back(i);
-            gumbel_prefix.push_back(static_cast<int32_t>(gctas));
+        if (multi) o.cdf = a.take((given ? sizeof(int32_t) : cdf_b) * N + 16);
+        if (given) {
+            const int s = c.resampler == PF_RESAMPLE_GUMBEL ? 0 : 1;
+            const int per = s == 0 ? kGumbelOffspring : kMetropolisThreads;
+            const int64_t ctas = aprefix[s].back() + (N + per - 1) / per;
+            if (ctas > 0x7fffffff) return PF_ERR_ARG;
+            atab[s].push_back(i);
+            aprefix[s].push_back(static_cast<int32_t>(ctas));
         }
         e.n_multi += (c.resampler == PF_RESAMPLE_MULTINOMIAL) ? 1 : 0;
         TrackerDev &T = e.h_trk[i];
@@ -249,8 +259,12 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
     }
     e.total_tiles = static_cast<int>(tiles);
     e.pull_tiles = static_cast<int>(mtiles);
-    e.n_gumbel = static_cast<int>(gumbel_slots.size());
-    e.gumbel_ctas = static_cast<int>(gctas);
+    Engine::AncestorTable *tabs[2] = {&e.gumbel, &e.metro};
+    for (int s = 0; s < 2; ++s) {
+        tabs[s]->n = static_cast<int>(atab[s].size());
+        tabs[s]->ctas = aprefix[s].back();
+        atab[s].insert(atab[s].end(), aprefix[s].begin(), aprefix[s].end());   // slots, then prefix
+    }
     a.size = a.used + 256;
 
     cudaError_t err = cudaMalloc(reinterpret_cast<void **>(&e.d_arena), a.size);
@@ -260,8 +274,8 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
     if (err == cudaSuccess) err = cudaMalloc(reinterpret_cast<void **>(&e.d_frames), sizeof(FrameRef) * n);
     if (err == cudaSuccess)
         err = cudaMalloc(reinterpret_cast<void **>(&e.d_tile_trk), sizeof(int32_t) * (e.total_tiles + e.pull_tiles + 1));
-    if (err == cudaSuccess && e.n_gumbel > 0)
-        err = cudaMalloc(reinterpret_cast<void **>(&e.d_gumbel), sizeof(int32_t) * (2 * e.n_gumbel + 1));
+    for (int s = 0; s < 2 && err == cudaSuccess; ++s)
+        if (tabs[s]->n > 0) err = cudaMalloc(reinterpret_cast<void **>(&tabs[s]->d), sizeof(int32_t) * atab[s].size());
     if (err == cudaSuccess) err = cudaMalloc(reinterpret_cast<void **>(&e.d_ticket), sizeof(uint32_t));
     if (err == cudaSuccess) err = cudaMallocHost(reinterpret_cast<void **>(&e.h_frames_pinned), sizeof(FrameRef) * n);
     if (err == cudaSuccess) err = cudaMallocHost(reinterpret_cast<void **>(&e.h_init_pinned), sizeof(TrackerState) * n);
@@ -301,13 +315,13 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
             T.cdf = e.d_arena + o.cdf;
             T.dbg_cdf = T.cdf;
         }
-        if (e.cfg[i].resampler == PF_RESAMPLE_GUMBEL) {
-            // written by the argmax kernel, read by the pull kernel; no CDF exists
+        if (ancestors_given(e.cfg[i].resampler)) {
+            // written by the ancestor kernel, read by the pull kernel; no CDF exists
             T.anc = reinterpret_cast<int32_t *>(e.d_arena + o.cdf);
             T.dbg_cdf = nullptr;
         }
-        const int base = (e.cfg[i].resampler == PF_RESAMPLE_MULTINOMIAL ||
-                          e.cfg[i].resampler == PF_RESAMPLE_GUMBEL) ? e.total_tiles : 0;
+        const int base = (e.cfg[i].resampler == PF_RESAMPLE_MULTINOMIAL || ancestors_given(e.cfg[i].resampler))
+                             ? e.total_tiles : 0;
         for (int k = 0; k < T.ntiles; ++k) tile_trk[base + T.tile_begin + k] = i;
         st[i] = initial_state(e.cfg[i]);
         e.h_frames[i].active = 1;
@@ -316,10 +330,10 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
     if (err == cudaSuccess)
         err = cudaMemcpyAsync(e.d_tile_trk, tile_trk.data(), sizeof(int32_t) * tile_trk.size(),
                               cudaMemcpyHostToDevice, e.stream);
-    std::vector<int32_t> gtab(gumbel_slots);
-    gtab.insert(gtab.end(), gumbel_prefix.begin(), gumbel_prefix.end());
-    if (err == cudaSuccess && e.n_gumbel > 0)
-        err = cudaMemcpyAsync(e.d_gumbel, gtab.data(), sizeof(int32_t) * gtab.size(), cudaMemcpyHostToDevice, e.stream);
+    for (int s = 0; s < 2 && err == cudaSuccess; ++s)
+        if (tabs[s]->n > 0)
+            err = cudaMemcpyAsync(tabs[s]->d, atab[s].data(), sizeof(int32_t) * atab[s].size(), cudaMemcpyHostToDevice,
+                                  e.stream);
     if (err == cudaSuccess) err = cudaMemsetAsync(e.d_ticket, 0, sizeof(uint32_t), e.stream);
     memcpy(e.h_init_pinned, st.data(), sizeof(TrackerState) * n);
     for (int i = 0; i < n && err == cudaSuccess; ++i)
@@ -349,23 +363,26 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
     return PF_OK;
 }
 
-// One frame's launches: the step kernel over its family's tiles, then, for multinomial
-// and Gumbel-max trackers, the CDF kernel (multinomial), the argmax kernel (Gumbel-max)
-// and the pull kernel over the pull family's tiles (tile table entries after the step
-// family's).  L carries the step family's table and count.
+static AncestorLaunch ancestor_launch(const Engine &e, const Engine::AncestorTable &tab) {
+    AncestorLaunch G;
+    G.trk = e.d_trk;
+    G.frames = e.d_frames;
+    G.slots = tab.d;
+    G.cta_prefix = tab.d + tab.n;
+    G.ntrk = tab.n;
+    G.total_ctas = tab.ctas;
+    return G;
+}
+
+// One frame's launches: the step kernel over its family's tiles, then, for the pull
+// family, the CDF kernel (multinomial trackers), the ancestor kernels (Gumbel-max,
+// Metropolis) and the pull kernel over the pull family's tiles (tile table entries after
+// the step family's).  L carries the step family's table and count.
 static int engine_enqueue(const Engine &e, StepLaunch L, cudaStream_t stream) {
     int rc = 0;
     if (e.total_tiles > 0) rc = launch_step(e.prec, L, e.grid, stream);
-    if (rc == 0 && e.n_gumbel > 0) {
-        GumbelLaunch G;
-        G.trk = e.d_trk;
-        G.frames = e.d_frames;
-        G.slots = e.d_gumbel;
-        G.cta_prefix = e.d_gumbel + e.n_gumbel;
-        G.ntrk = e.n_gumbel;
-        G.total_ctas = e.gumbel_ctas;
-        rc = launch_gumbel(e.prec, G, stream);
-    }
+    if (rc == 0 && e.gumbel.n > 0) rc = launch_gumbel(e.prec, ancestor_launch(e, e.gumbel), stream);
+    if (rc == 0 && e.metro.n > 0) rc = launch_metropolis(e.prec, ancestor_launch(e, e.metro), stream);
     if (rc == 0 && e.pull_tiles > 0) {
         L.tile_trk = e.d_tile_trk + e.total_tiles;
         L.total_tiles = e.pull_tiles;
@@ -807,7 +824,7 @@ pf_status pf_get_debug(pf_filter *f, int32_t which, void *host_buf, size_t bytes
     Engine &e = f->e;
     const TrackerDev &T = e.h_trk[0];
     if (!T.dbg_anc) return PF_ERR_STATE;
-    if (which == 1 && !T.dbg_cdf) return PF_ERR_ARG;   // a Gumbel-max tracker has no CDF
+    if (which == 1 && !T.dbg_cdf) return PF_ERR_ARG;   // a Gumbel-max or Metropolis tracker has no CDF
     const size_t elem = which == 0 ? 4 : (e.prec == PF_REF64 ? 8 : 4);
     if (which < 0 || which > 1 || bytes < elem * static_cast<size_t>(T.N)) return PF_ERR_ARG;
     cudaError_t err = cudaStreamSynchronize(e.stream);

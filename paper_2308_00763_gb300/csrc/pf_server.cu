@@ -357,7 +357,7 @@ double pf_server_now(void) { return now_s(); }
 
 pf_status pf_server_stream_bytes(const pf_config *cfg, int32_t host_frames, int32_t queue_depth, int64_t *bytes) {
     if (!bytes || check_config(cfg) != PF_OK || queue_depth < 1 ||
-        cfg->resampler == PF_RESAMPLE_MULTINOMIAL || cfg->resampler == PF_RESAMPLE_GUMBEL) return PF_ERR_ARG;
+        cfg->resampler == PF_RESAMPLE_MULTINOMIAL || ancestors_given(cfg->resampler)) return PF_ERR_ARG;
     *bytes = static_cast<int64_t>(align_up(stream_layout(*cfg, host_frames != 0, queue_depth).total));
     return PF_OK;
 }
@@ -391,8 +391,8 @@ pf_status pf_server_create(const pf_server_config *cfg, pf_server **out) {
 pf_status pf_server_open(pf_server *S, const pf_config *cfg, double fps, int32_t host_frames, int32_t *stream_id) {
     if (!S || !stream_id || check_config(cfg) != PF_OK || !(fps >= 0) || !isfinite(fps)) return PF_ERR_ARG;
     if (cfg->flags & PF_FLAG_DEBUG_ARRAYS) return PF_ERR_ARG;
-    // one launch per tick: no pull kernel (multinomial, Gumbel-max)
-    if (cfg->resampler == PF_RESAMPLE_MULTINOMIAL || cfg->resampler == PF_RESAMPLE_GUMBEL) return PF_ERR_ARG;
+    // one launch per tick: no pull kernel (multinomial, Gumbel-max, Metropolis)
+    if (cfg->resampler == PF_RESAMPLE_MULTINOMIAL || ancestors_given(cfg->resampler)) return PF_ERR_ARG;
     if (S->sticky != PF_OK) return PF_ERR_STATE;
     *stream_id = -1;
     const pf_config &c = *cfg;

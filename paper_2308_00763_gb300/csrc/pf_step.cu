@@ -31,8 +31,9 @@
 // reaches an independent uniform v_j (a binary search over T.cdf), gathers the ancestors'
 // positions of its tile's offspring into shared memory, sizes the likelihood window by
 // them and runs phases 2-5 as the step kernel does.  Gumbel-max trackers (the log-domain
-// form of the same draw, Sec. 3) skip the CDF kernel: the pull kernel reads the ancestors
-// the argmax kernel (pf_gumbel.cu) wrote to T.anc instead of searching.
+// form of the same draw, Sec. 3) and Metropolis trackers (Sec. 2) skip the CDF kernel: the
+// pull kernel reads the ancestors their kernel (pf_gumbel.cu, pf_metropolis.cu) wrote to
+// T.anc instead of searching.
 //
 // Scan boundaries.  The prefix between tiles is an exact 128-bit fixed-point sum of
 // the tiles' aggregates, so every tile obtains the same boundary value whichever
@@ -644,7 +645,7 @@ __device__ void finalize_tracker(const TrackerDev &T, TrackerState *st, StepSmem
 // Kernel modes: the step kernel (systematic and stratified trackers, every phase), and for
 // multinomial trackers the CDF kernel (phase 1 up to the CDF, written to T.cdf) and the
 // pull kernel (resampling from T.cdf, phases 2-5), launched in that order; the pull kernel
-// also takes the Gumbel-max trackers (ancestors from T.anc).
+// also takes the Gumbel-max and Metropolis trackers (ancestors from T.anc).
 constexpr int kModeStep = 0, kModeCdf = 1, kModePull = 2;
 
 // One tile of a launch in mode kMode (trackers of the other modes are skipped).
@@ -701,7 +702,7 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
     if constexpr (kMode == kModeCdf) {
         if (T.resampler != kResampleMultinomial) return;
     } else if constexpr (kMode == kModePull) {
-        if (T.resampler != kResampleMultinomial && T.resampler != kResampleGumbel) return;
+        if (T.resampler != kResampleMultinomial && !ancestors_given(T.resampler)) return;
     }
 
     const int N = static_cast<int>(T.N);
@@ -854,8 +855,8 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
         const pos_t *__restrict__ Yin = static_cast<const pos_t *>(T.py[in]);
         acc_t uq[kItems];
         int lo[kItems], hi[kItems];
-        if (T.resampler == kResampleGumbel) {
-            // Gumbel-max: the argmax kernel wrote every offspring's ancestor
+        if (ancestors_given(T.resampler)) {
+            // Gumbel-max, Metropolis: the ancestor kernel wrote every offspring's ancestor
 #pragma unroll
             for (int m = 0; m < kItems; ++m) {
                 const int a = (eb + m < cnt) ? __ldg(T.anc + PF_IDX(k0 + eb + m, N)) : 0;

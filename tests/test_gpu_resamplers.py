@@ -6,13 +6,14 @@ Multinomial: the step kernel writes the CDF, the pull kernel gives offspring j t
 particle whose CDF value reaches an independent uniform v_j (Sec. 3's categorical draw).
 Gumbel-max: the argmax kernel gives offspring j the particle maximising L_k + g_jk (the
 log-domain form of the same draw that Sec. 3 weighs), the pull kernel gathers them.
+Metropolis: offspring j's B-step chain on exp(L) (the reduction-free scheme Sec. 2 cites).
 The checks: the ancestors are exactly the oracle's resampling of the CDF the step computed,
 with the draws from the oracle's own Philox; the REF64 track equals the oracle's FP64 track
 of the same scheme within 1e-9 px; stratified offspring counts stay within two strata of
 N w_k; the option takes effect; the schemes share a batch, each tracker equal to its own
 single run; the bench's launch configuration (2^20 particles) resamples exactly.  Gumbel-max
-ancestors equal the oracle's decisions in the kernel's precision up to near ties (FP32
-logs may differ in the last bit between the two sides).
+and Metropolis ancestors equal the oracle's decisions in the kernel's precision up to near
+ties (FP32 logs may differ in the last bit between the two sides).
 """
 import numpy as np
 import pytest
@@ -346,12 +347,139 @@ def test_gumbel_limits_and_debug(pf):
     s.close()
 
 
+# ----------------------------------------------------------------------------- Metropolis
+def _metropolis_step(pf, v, N, prec, seed, *, tracker=0, steps=0):
+    """As _gumbel_step, for a Metropolis tracker of chain length `steps` (0 = 64)."""
+    f = pf.Filter(v.W, v.H, N, v.radius, prec, init=tuple(v.centres[0]), seed=seed, tracker_id=tracker,
+                  flags=pf.PF_FLAG_DEBUG_ARRAYS, resampler="metropolis", resampler_steps=steps)
+    fr = _frames(v)
+    f.run(fr[:v.T - 1])
+    st = f.get_state()
+    f.step(fr[v.T - 1])
+    anc = f.debug(0).astype(np.int64)
+    f.close()
+    return anc, st["L"].astype(np.float64), int(st["t"]) - 1
+
+
+def _check_metropolis(L, B, seed, t, tracker, anc, prec):
+    """Ancestors equal the oracle's chains in the kernel's precision; a chain that ends
+    elsewhere must pass an acceptance test within rounding of its threshold (FP32 logs of
+    the two sides may differ in the last bit), and such chains are rare."""
+    want = oracle.resample_metropolis(L, B, seed, t, tracker, "f64" if prec == "ref64" else "f32")
+    bad = np.nonzero(anc != want)[0]
+    assert np.all((anc >= 0) & (anc < L.size))
+    assert bad.size <= max(1, L.size // 1000), bad[:10]
+    tol = 1e-12 if prec == "ref64" else 1e-4
+    for j in bad:
+        _, margins = oracle.metropolis_chain(L, B, seed, t, int(j), tracker)
+        assert min(margins) <= tol, (j, want[j], anc[j], min(margins))
+
+
+@pytest.mark.parametrize("prec", ["ref64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("N", [1, 3, 1000, TILE + 1, 3 * TILE + 17])
+def test_metropolis_ancestors_exact(pf, prec, N):
+    v = synth.make_video(128, 128, 4, 5, noise=5.0, seed=49)
+    anc, L, t = _metropolis_step(pf, v, N, prec, 27, tracker=7)
+    _check_metropolis(L, 64, 27, t, 7, anc, prec)
+
+
+@pytest.mark.parametrize("steps", [1, 2, 7, 300])
+def test_metropolis_chain_lengths(pf, steps):
+    v = synth.make_video(128, 128, 4, 5, noise=5.0, seed=50)
+    anc, L, t = _metropolis_step(pf, v, 5000, "f32", 28, tracker=2, steps=steps)
+    _check_metropolis(L, steps, 28, t, 2, anc, "f32")
+
+
+@pytest.mark.parametrize("prec", ["ref64", "f16"])
+def test_metropolis_full_size_ancestors_exact(pf, prec):
+    """The bench's configuration, 2^20 particles: every chain checked."""
+    v = synth.make_video(512, 512, 3, 5, noise=5.0, seed=1)
+    anc, L, t = _metropolis_step(pf, v, 1 << 20, prec, 1)
+    _check_metropolis(L, 64, 1, t, 0, anc, prec)
+
+
+def test_metropolis_ref64_track_within_1e9(pf):
+    v = synth.make_video(128, 128, 10, 5, noise=5.0, seed=1)
+    for N in (1000, 3 * TILE + 17):
+        est_o, M_o, _ = oracle.track(v.frames, N, 5, init=tuple(v.centres[0]), seed=1, resampler="metropolis")
+        f = pf.Filter(v.W, v.H, N, 5, "ref64", init=tuple(v.centres[0]), seed=1, resampler="metropolis")
+        f.run(_frames(v))
+        est, ms = f.estimates(0, v.T, with_stats=True)
+        f.close()
+        assert np.abs(est - est_o).max() <= 1e-9, N
+        assert np.array_equal(ms[:, 0], M_o)
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16", "bf16"])
+def test_metropolis_tracks_the_truth_and_steps_equal_runs(pf, prec):
+    v = synth.make_video(128, 128, 10, 5, noise=5.0, seed=1)
+    est_o, _, _ = oracle.track(v.frames, 1000, 5, init=tuple(v.centres[0]), seed=1, resampler="metropolis")
+    fr = _frames(v)
+    a = pf.Filter(v.W, v.H, 1000, 5, prec, init=tuple(v.centres[0]), seed=1, resampler="metropolis")
+    a.run(fr)
+    b = pf.Filter(v.W, v.H, 1000, 5, prec, init=tuple(v.centres[0]), seed=1, resampler="metropolis")
+    for t in range(v.T):
+        b.step(fr[t])
+    ea, eb = a.estimates(0, v.T), b.estimates(0, v.T)
+    a.close()
+    b.close()
+    assert np.array_equal(ea, eb)
+    assert np.sqrt(np.mean(np.sum((ea - est_o) ** 2, axis=1))) <= 0.5
+
+
+def test_five_schemes_in_one_batch_equal_singles(pf):
+    vids = [synth.make_video(96, 96, 5, 3, noise=5.0, seed=100 + i, v=(1.0, -1.0)) for i in range(6)]
+    Ns = [3000, 2 * TILE + 5, 777, 5000, 1500, 2 * TILE + 300]
+    rs = ["metropolis", "systematic", "stratified", "multinomial", "gumbel", "metropolis"]
+    steps = [0, 0, 0, 0, 0, 9]
+    for prec in ("ref64", "f32", "f16"):
+        cfgs = [pf.make_config(v.W, v.H, n, v.radius, prec, init=tuple(v.centres[0]), seed=40 + i,
+                               tracker_id=i, resampler=r, resampler_steps=b)
+                for i, (v, n, r, b) in enumerate(zip(vids, Ns, rs, steps))]
+        bt = pf.Batch(cfgs)
+        fr = [_frames(v) for v in vids]
+        for t in range(5):
+            bt.step([f[t] for f in fr])
+        got = np.stack([bt.estimates(t) for t in range(5)], axis=1)
+        c = bt.counters()
+        bt.close()
+        assert c["kernel_launches"] == 5 * 5, c      # step, CDF, argmax, chains, pull
+        for i, (v, n, r, b) in enumerate(zip(vids, Ns, rs, steps)):
+            s1 = pf.Filter(v.W, v.H, n, v.radius, prec, init=tuple(v.centres[0]), seed=40 + i, tracker_id=i,
+                           resampler=r, resampler_steps=b)
+            s1.run(fr[i])
+            assert np.array_equal(s1.estimates(0, 5), got[i]), (prec, i, r)
+            s1.close()
+
+
+def test_metropolis_limits_and_debug(pf):
+    """N <= 2^24 and chain length <= 4096; other schemes take no chain length; no CDF to
+    read back; the server refuses Metropolis streams."""
+    for kw in (dict(num_particles=(1 << 24) + 1), dict(resampler_steps=4097), dict(resampler_steps=-2)):
+        args = dict(num_particles=100, resampler_steps=0)
+        args.update(kw)
+        with pytest.raises(pf.PfError):
+            pf.Filter(64, 64, args["num_particles"], 3, "f16", resampler="metropolis",
+                      resampler_steps=args["resampler_steps"])
+    with pytest.raises(pf.PfError):
+        pf.Filter(64, 64, 100, 3, "f16", resampler="stratified", resampler_steps=5)
+    f = pf.Filter(64, 64, 100, 3, "f32", init=(32.0, 32.0), resampler="metropolis", flags=pf.PF_FLAG_DEBUG_ARRAYS)
+    f.step(np.full((64, 64), 100, np.uint8))
+    with pytest.raises(pf.PfError):
+        f.debug(1)
+    f.close()
+    s = pf.Server(1 << 26, max_streams=2, queue_depth=2)
+    with pytest.raises(pf.PfError):
+        s.open(pf.make_config(64, 64, 100, 3, "f16", resampler="metropolis"))
+    s.close()
+
+
 def test_counters_count_launches_graphs_and_host_bytes(pf):
     """pf_get_counters: one kernel per frame for systematic trackers, three for multinomial
     (step kernel skipped: CDF and pull), one graph replay per resident run, host bytes."""
     v = synth.make_video(96, 80, 7, 3, noise=5.0, seed=44)
     fr = _frames(v)
-    for rs, per in (("systematic", 1), ("multinomial", 2), ("gumbel", 2)):
+    for rs, per in (("systematic", 1), ("multinomial", 2), ("gumbel", 2), ("metropolis", 2)):
         f = pf.Filter(v.W, v.H, 3000, 3, "f32", init=tuple(v.centres[0]), seed=2, resampler=rs)
         f.step(v.frames[0])                      # host frame
         f.step(fr[1])
