@@ -78,6 +78,8 @@ def _load():
             "orc_gumbel_f32": (None, [_U64, _U32, _U32, _I64, _P, _P]),
             "orc_metropolis_f64": (None, [_U64, _U32, _U32, _I64, _P, ctypes.c_int, _P]),
             "orc_metropolis_f32": (None, [_U64, _U32, _U32, _I64, _P, ctypes.c_int, _P]),
+            "orc_rejection_f64": (None, [_U64, _U32, _U32, _I64, _P, _D, ctypes.c_int, _P]),
+            "orc_rejection_f32": (None, [_U64, _U32, _U32, _I64, _P, ctypes.c_float, ctypes.c_int, _P]),
             "orc_run": (ctypes.c_int, [_P, _I64, ctypes.c_int, ctypes.c_int, ctypes.c_int, _I64,
                                        _I64, ctypes.c_int, _D, _D, _D, _D, _D, _D, _D, _D,
                                        _U64, _U32, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P]),
@@ -339,7 +341,53 @@ def metropolis_chain(L, B: int, seed: int, t: int, j: int, tracker: int = 0):
     return states, margins
 
 
-RESAMPLERS = {"systematic": 0, "stratified": 1, "multinomial": 2, "gumbel": 3, "metropolis": 4}
+REJECTION_TRIES = 4096    # tries per offspring before the last candidate is kept
+
+
+def resample_rejection(L, M, seed: int, t: int, tracker: int = 0, precision: str = "f64",
+                       tries: int = REJECTION_TRIES):
+    """Rejection-resampling ancestors of frame t's log weights ``L`` with bound ``M``
+    (max L): candidates j, then proposals k' = floor(w N / 2^32), the first passing
+    ln u <= L_k - M kept (the last after ``tries``), decided in FP64 or FP32."""
+    if precision == "f64":
+        Lc = np.ascontiguousarray(L, np.float64)
+        fn, Mc = _load().orc_rejection_f64, float(M)
+    elif precision == "f32":
+        Lc = np.ascontiguousarray(L, np.float32)
+        fn, Mc = _load().orc_rejection_f32, float(np.float32(M))
+    else:
+        raise ValueError(precision)
+    a = np.empty(Lc.size, np.int64)
+    fn(seed & 0xFFFFFFFFFFFFFFFF, t, tracker, Lc.size, _ptr(Lc), Mc, int(tries), _ptr(a))
+    return a
+
+
+def rejection_trace(L, M, seed: int, t: int, j: int, tracker: int = 0, tries: int = REJECTION_TRIES):
+    """Offspring j's tries in FP64 until acceptance: (candidates, margins |ln u - (L_k - M)|)."""
+    L = np.asarray(L, np.float64)
+    N = L.size
+    k, cands, margins = j, [], []
+    for i in range(tries):
+        w = philox([[i // 2, t, 6 + 256 * j, tracker]], seed)[0]
+        if i > 0:
+            k = (int(w[2 * (i % 2)]) * N) >> 32
+        lu = float(np.log(uniform([w[2 * (i % 2) + 1]])[0]))
+        d = L[k] - M
+        cands.append(k)
+        margins.append(abs(lu - d))
+        if lu <= d:
+            break
+    return cands, margins
+
+
+RESAMPLERS = {"systematic": 0, "stratified": 1, "multinomial": 2, "gumbel": 3, "metropolis": 4, "rejection": 5}
+
+
+def _iters(resampler, iters):
+    """Chain length (Metropolis) or tries (rejection); None takes the library's default."""
+    if iters is not None:
+        return int(iters)
+    return {"metropolis": METROPOLIS_STEPS, "rejection": REJECTION_TRIES}.get(resampler, 0)
 
 
 # --------------------------------------------------------------------------- whole tracker
@@ -360,7 +408,7 @@ class FrameRecord:
 
 def track_steps(frames: np.ndarray, N: int, r: int, *, init, sigma=(1.0, 1.0), drift=(0.0, 0.0),
                 seed: int = 1, tracker: int = 0, bg=100.0, fg=228.0, nthreads=1, resampler="systematic",
-                iters=METROPOLIS_STEPS):
+                iters=None):
     """Run the tracker phase by phase (Fig. 1), yielding a FrameRecord per frame.
     Same arithmetic as :func:`track`, with every intermediate array exposed."""
     anc = None
@@ -380,7 +428,9 @@ def track_steps(frames: np.ndarray, N: int, r: int, *, init, sigma=(1.0, 1.0), d
         elif resampler == "gumbel":
             a = resample_gumbel(L, seed, t, tracker, "f64")
         elif resampler == "metropolis":
-            a = resample_metropolis(L, iters, seed, t, tracker, "f64")
+            a = resample_metropolis(L, _iters(resampler, iters), seed, t, tracker, "f64")
+        elif resampler == "rejection":
+            a = resample_rejection(L, M, seed, t, tracker, "f64", _iters(resampler, iters))
         elif resampler == "systematic":
             a = resample(C, u0, "f64")
         else:
@@ -391,7 +441,7 @@ def track_steps(frames: np.ndarray, N: int, r: int, *, init, sigma=(1.0, 1.0), d
 
 def track(frames: np.ndarray, N: int, r: int, *, init, sigma=(1.0, 1.0), drift=(0.0, 0.0),
           seed: int = 1, tracker: int = 0, bg=100.0, fg=228.0, nthreads=1, resampler="systematic",
-          iters=METROPOLIS_STEPS):
+          iters=None):
     """Whole FP64 track in C.  Returns (est (T,2), M (T,), S (T,))."""
     f = np.ascontiguousarray(frames, dtype=np.uint8)
     T, H, W = f.shape
@@ -400,7 +450,7 @@ def track(frames: np.ndarray, N: int, r: int, *, init, sigma=(1.0, 1.0), drift=(
     S = np.empty(T, np.float64)
     rc = _load().orc_run(_ptr(f), H * W, T, W, H, W, N, r, bg, fg, init[0], init[1],
                          sigma[0], sigma[1], drift[0], drift[1], seed & 0xFFFFFFFFFFFFFFFF,
-                         tracker, nthreads, RESAMPLERS[resampler], int(iters), _ptr(est), _ptr(M), _ptr(S))
+                         tracker, nthreads, RESAMPLERS[resampler], _iters(resampler, iters), _ptr(est), _ptr(M), _ptr(S))
     if rc != 0:
         raise MemoryError("oracle could not allocate its arrays")
     return est, M, S

@@ -19,6 +19,7 @@
  *   multinomial resampling (Sec. 3) orc_resample_multi_f64 / _f32 (draws: orc_stratified_offsets)
  *   Gumbel-max resampling (Sec. 3)  orc_gumbel_f64 / _f32 (argmax of L + Gumbel variates)
  *   Metropolis resampling (Sec. 2)  orc_metropolis_f64 / _f32 (B-step chains on exp(L))
+ *   rejection resampling (Sec. 2)   orc_rejection_f64 / _f32 (first candidate with u <= w/w_max)
  * Where the paper is silent the readings are (numbered as in the design notes):
  *   C1  Eq. 3 is summed over the template pixels and divided by 50*|D|.
  *   C2  template D = integer offsets with dx^2+dy^2 <= r^2 (centre included).
@@ -36,6 +37,8 @@
  *       smallest k, N draws per offspring (tag 4 + 256 j).
  *       Metropolis (alternative scheme): a B-step chain from k = j, proposals uniform,
  *       accepted when ln u <= L_k' - L_k (tag 5 + 256 j, two steps per draw).
+ *       Rejection (alternative scheme): candidates j, then uniform proposals, the first
+ *       with ln u <= L_k - max L kept; R tries at most (tag 6 + 256 j, two tries per draw).
  *   C11 draws: Philox4x32-10 words -> 23-bit uniforms -> Box-Muller in FP64.
  *   C12 at t = 0 every ancestor sits at (init_x, init_y).
  * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), written here
@@ -553,6 +556,52 @@ void orc_metropolis_f32(uint64_t seed, uint32_t t, uint32_t tracker, int64_t N, 
     }
 }
 
+/* Rejection resampling (Sec. 2 cites it beside Metropolis resampling; Murray, Lee and
+ * Jacob, 2016): offspring j tests k = j first, then proposals k' uniform on
+ * {0, ..., N-1}, and takes the first candidate k that passes u <= w_k / w_max, in the log
+ * form ln u <= L_k - M with M = max L (so w_k / w_max = exp(L_k - M)).  Offspring j thus
+ * keeps j with probability w_j / w_max at the first try and otherwise draws from the
+ * categorical law p_k = exp(L_k) / sum exp(L) (the later tries are plain rejection
+ * sampling): P(a_j = k) = (w_j / w_max) [k = j] + (1 - w_j / w_max) p_k, so particle k's
+ * expected offspring count is N p_k, with less spread than multinomial.  Try i of
+ * offspring j reads the Philox draw (i / 2, t, 6 + 256 j, tracker): word 2 (i mod 2) gives
+ * the proposal (not used by try 0, which tests j itself), word 2 (i mod 2) + 1 the uniform
+ * u.  After R tries without acceptance the offspring keeps the last candidate (R = 4096 in
+ * the library: a truncation of probability (1 - S/N)^R, S = sum exp(L - M)); j < 2^24. */
+void orc_rejection_f64(uint64_t seed, uint32_t t, uint32_t tracker, int64_t N, const double *L, double M, int R,
+                       int64_t *a)
+{
+    for (int64_t j = 0; j < N; ++j) {
+        int64_t k = j;
+        for (int i = 0; i < R; ++i) {
+            uint32_t w[4];
+            orc_philox_draw(seed, (uint32_t)(i / 2), t, 6u + 256u * (uint32_t)j, tracker, w);
+            if (i > 0) k = (int64_t)(((uint64_t)w[2 * (i % 2)] * (uint64_t)N) >> 32);
+            if (log(orc_uniform(w[2 * (i % 2) + 1])) <= L[k] - M) break;
+        }
+        a[j] = k;
+    }
+}
+
+/* The same tries with the test in FP32 (L and M held in FP32, ln u from logf). */
+void orc_rejection_f32(uint64_t seed, uint32_t t, uint32_t tracker, int64_t N, const float *L, float M, int R,
+                       int64_t *a)
+{
+    for (int64_t j = 0; j < N; ++j) {
+        int64_t k = j;
+        for (int i = 0; i < R; ++i) {
+            uint32_t w[4];
+            orc_philox_draw(seed, (uint32_t)(i / 2), t, 6u + 256u * (uint32_t)j, tracker, w);
+            if (i > 0) k = (int64_t)(((uint64_t)w[2 * (i % 2)] * (uint64_t)N) >> 32);
+            volatile float u = (float)orc_uniform(w[2 * (i % 2) + 1]);
+            volatile float lu = logf(u);
+            volatile float d = L[k] - M;
+            if (lu <= d) break;
+        }
+        a[j] = k;
+    }
+}
+
 /* The same systematic decisions with the stratum points formed by a division,
  * u_j = (j + u0) / N, and no saved reciprocal: the naive form of Sec. 3's performance
  * optimisation (the GPU's naive study build takes these decisions). */
@@ -618,6 +667,8 @@ int orc_run(const uint8_t *frames, int64_t frame_stride, int T, int W, int H, in
                 orc_gumbel_f64(seed, (uint32_t)t, tracker, N, L, a);
             } else if (resampler == 4) {
                 orc_metropolis_f64(seed, (uint32_t)t, tracker, N, L, iters, a);
+            } else if (resampler == 5) {
+                orc_rejection_f64(seed, (uint32_t)t, tracker, N, L, M, iters, a);
             } else if (resampler) {
                 orc_stratified_offsets(seed, (uint32_t)t, tracker, N, v);
                 if (resampler == 2) orc_resample_multi_f64(N, C, v, a);

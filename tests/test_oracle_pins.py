@@ -656,6 +656,79 @@ def test_metropolis_fp32_decisions_agree_with_fp64():
     assert np.mean(a64 == a32) >= 0.999
 
 
+# ----------------------------------------------------------------------------- rejection resampling
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_rejection_equal_weights_keep_every_particle(prec):
+    """Equal log weights: w_k / w_max = 1 and ln u < 0, so the first candidate (j itself)
+    is accepted: the identity."""
+    L = np.full(333, -7.25)
+    assert np.array_equal(oracle.resample_rejection(L, -7.25, 3, 0, 0, prec), np.arange(333))
+
+
+def test_rejection_per_offspring_law_and_unbiased_counts():
+    """Offspring j keeps j with probability r_j = w_j / w_max at the first try, otherwise
+    rejection sampling draws from p = softmax(L): P(a_j = k) = r_j [k = j] + (1 - r_j) p_k
+    (checked entry by entry over 4000 frames, 5 binomial standard errors), so the expected
+    count of particle k is N p_k (6 standard errors)."""
+    rng = np.random.default_rng(31)
+    n, trials = 6, 4000
+    L = rng.uniform(-2.0, 2.0, n)
+    p = _softmax(L)
+    r = np.exp(L - L.max())
+    a = np.array([oracle.resample_rejection(L, L.max(), 7, t, 1) for t in range(trials)])
+    for j in range(n):
+        want = (1 - r[j]) * p
+        want[j] += r[j]
+        freq = np.bincount(a[:, j], minlength=n) / trials
+        assert np.all(np.abs(freq - want) <= 5 * np.sqrt(want * (1 - want) / trials) + 1e-12), (j, freq, want)
+    cnts = np.array([_counts(row, n) for row in a], np.float64)
+    se = np.sqrt(cnts.var(axis=0) / trials)
+    assert np.all(np.abs(cnts.mean(axis=0) - n * p) <= 6 * se)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_rejection_two_particles_closed_form(prec):
+    """w = (1, 3): offspring 1 passes its first try (w_1 = w_max); offspring 0 keeps itself
+    with probability 1/3, else draws particle 1 with probability 3/4, so P(a_0 = 1) = 1/2
+    (5 standard errors over 10000 frames)."""
+    L = [0.0, math.log(3.0)]
+    a = np.array([oracle.resample_rejection(L, max(L), 9, t, 0, prec) for t in range(10000)])
+    assert np.all(a[:, 1] == 1)
+    assert abs(np.mean(a[:, 0] == 1) - 0.5) <= 5 * math.sqrt(0.25 / a.shape[0])
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_rejection_dominant_particle_takes_everything(prec):
+    """One particle at the maximum, the rest 1000 below: every other candidate is refused,
+    so every offspring ends on the dominant particle (the first proposal hitting it)."""
+    n, d = 16, 11
+    L = np.full(n, -1000.0)
+    L[d] = 0.0
+    for t in range(50):
+        assert np.all(oracle.resample_rejection(L, 0.0, 5, t, 0, prec) == d)
+
+
+def test_rejection_truncation_keeps_the_last_candidate():
+    """With R tries and no acceptance possible the offspring keeps the last candidate
+    (bound M above every weight by far: nothing passes)."""
+    L = np.zeros(50)
+    a = oracle.resample_rejection(L, 1000.0, 2, 3, 0, "f64", tries=5)
+    for j in (0, 13, 49):
+        cands, _ = oracle.rejection_trace(L, 1000.0, 2, 3, j, 0, tries=5)
+        assert len(cands) == 5 and a[j] == cands[-1]
+
+
+def test_rejection_fp32_decisions_agree_with_fp64():
+    rng = np.random.default_rng(33)
+    L = np.round(rng.normal(0.0, 1.5, 3000), 3)
+    a64 = oracle.resample_rejection(L, L.max(), 37, 2, 1, "f64")
+    a32 = oracle.resample_rejection(L, L.max(), 37, 2, 1, "f32")
+    for j in np.nonzero(a64 != a32)[0]:
+        _, margins = oracle.rejection_trace(L, L.max(), 37, 2, int(j), 1)
+        assert min(margins) <= 1e-5, j
+    assert np.mean(a64 == a32) >= 0.999
+
+
 # ----------------------------------------------------------------------------- propagation, Eq. 1-2
 def test_propagation_moments_paper_motion():
     """Eq. 1-2: x ~ N(1 + x_anc, 5^2), y ~ N(2 + y_anc, 2^2)."""
@@ -732,6 +805,15 @@ def test_track_metropolis_recovers_ground_truth_config1():
     for j in (0, 17, 999):
         states, _ = oracle.metropolis_chain(L, 64, 1, 4, j, 0)
         assert states[-1] == a[j]
+
+
+def test_track_rejection_recovers_ground_truth_config1():
+    v = synth.make_video(128, 128, 10, 5, noise=5.0, seed=1)
+    est, _, _ = oracle.track(v.frames, 1000, 5, init=tuple(v.centres[0]), seed=1, resampler="rejection")
+    err = np.sqrt(np.sum((est - v.centres) ** 2, axis=1))
+    assert np.sqrt(np.mean(err ** 2)) < 1.0 and err.max() < 1.5
+    recs = list(oracle.track_steps(v.frames, 1000, 5, init=tuple(v.centres[0]), seed=1, resampler="rejection"))
+    assert np.array_equal(np.array([r.est for r in recs]), est)
 
 
 def test_track_noiseless_recovers_integer_centres():
