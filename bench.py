@@ -53,7 +53,8 @@ def _args():
     p.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     p.add_argument("--no-sweep", action="store_true", help="skip the precision/size sweep and the paper workload")
     p.add_argument("--serve-seconds", type=float, default=20.0, help="length of the served-streams run")
-    p.add_argument("--resampler", default="systematic", choices=["systematic", "stratified", "multinomial", "metropolis"],
+    p.add_argument("--resampler", default="systematic",
+                   choices=["systematic", "stratified", "multinomial", "metropolis", "rejection"],
                    help="resampling scheme of the timed filters (the paper's is systematic)")
     p.add_argument("--tpb-sweep", action="store_true",
                    help="thread-block study: build the step kernel at 128/256/512/1024 threads per CTA and time each")
@@ -390,8 +391,8 @@ def run_ours(args):
         "roofline_issue": _issue_view(hp, head["launch_us_median"], dev),
         "e2e": {"value": head["e2e_value"], "unit": METRIC, "h2d_bytes_per_step": int(W_ * H_ * T),
                 "d2h_bytes_per_step": int(16 * T)},
-        # multinomial: CDF + pull; Metropolis: chains + pull
-        "gpu_launches": args.steps * T * (2 if args.resampler in ("multinomial", "metropolis") else 1),
+        # multinomial: CDF + pull; Metropolis, rejection: ancestors + pull
+        "gpu_launches": args.steps * T * (2 if args.resampler in ("multinomial", "metropolis", "rejection") else 1),
         "accuracy": {"rmse_px_vs_ref64_gpu": head["rmse_px_vs_ref64_gpu"],
                      "rmse_px_vs_ground_truth": results_truth.get(hp)},
         "per_precision": {p: {k: r[k] for k in ("value", "ms_per_step", "launch_us_median", "frame_latency_us_p50",
@@ -633,8 +634,9 @@ def _paper_workload(dev, stream):
 
 def _resamplers(dev, stream):
     """Systematic (the paper's scheme, Sec. 3) against stratified (one offset per stratum,
-    Sec. 2), multinomial (independent draws searched in the CDF; CDF and pull kernels) and
-    Metropolis resampling (64-step chains, Sec. 2; chain and pull kernels) on the headline
+    Sec. 2), multinomial (independent draws searched in the CDF; CDF and pull kernels),
+    Metropolis (64-step chains, Sec. 2; chain and pull kernels) and rejection resampling
+    (first candidate passing u <= w / w_max, Sec. 2; try and pull kernels) on the headline
     workload: us per frame and the track's RMSE against the ground truth, per precision."""
     import torch
     import paper_2308_00763_gb300 as pf
@@ -645,7 +647,7 @@ def _resamplers(dev, stream):
     out = {}
     for prec in ("ref64", "f32", "f16"):
         row = {}
-        for rs in ("systematic", "stratified", "multinomial", "metropolis"):
+        for rs in ("systematic", "stratified", "multinomial", "metropolis", "rejection"):
             f = pf.Filter(W_, H_, N_, R_, prec, init=tuple(v.centres[0]), seed=SEED_, stream=stream, resampler=rs)
             f.run(fr[:4])
             best = None
@@ -663,7 +665,7 @@ def _resamplers(dev, stream):
             row[rs] = {"us_per_frame": best, "value": N_ / (best * 1e-6),
                        "rmse_px_vs_truth": _rmse(f.estimates(0, T_), v.centres)}
             f.close()
-        for rs in ("stratified", "multinomial", "metropolis"):
+        for rs in ("stratified", "multinomial", "metropolis", "rejection"):
             row[rs + "_over_systematic_time"] = row[rs]["us_per_frame"] / row["systematic"]["us_per_frame"]
         out[prec] = row
     return {"workload": WORKLOAD, "unit": METRIC, "by_precision": out}

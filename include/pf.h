@@ -94,13 +94,25 @@ typedef enum {
  *               the cost is B steps per offspring at any N (N <= 2^24, PF_ERR_ARG beyond).
  *               Two kernels per frame (the chains, then the
  *               pull kernel); trackers and batches only; pf_get_debug(which = 1) answers
- *               PF_ERR_ARG. */
+ *               PF_ERR_ARG.
+ *   REJECTION:  rejection resampling (Sec. 2 cites it beside METROPOLIS): offspring j
+ *               tests candidate j, then proposals k' = floor(w N / 2^32), and keeps the
+ *               first candidate k with ln u <= L_k - M, M the maximum of L the previous
+ *               step computed (w_k / w_max = exp(L_k - M)); try i reads words 2 (i mod 2)
+ *               (proposal; unused by try 0) and 2 (i mod 2) + 1 (u) of Philox(i / 2, t,
+ *               6 + 256 j, tracker_id).  Offspring j keeps j with probability w_j / w_max,
+ *               else draws from the normalised weights, so expected offspring counts are
+ *               N w_k / sum w.  At most R = pf_config.resampler_steps tries (0 = 4096,
+ *               at most 65536); after R refusals the last candidate is kept.  Expected
+ *               tries per offspring: N w_max / sum w.  Same precision, limits (N <= 2^24)
+ *               and launches as METROPOLIS. */
 typedef enum {
     PF_RESAMPLE_SYSTEMATIC = 0,
     PF_RESAMPLE_STRATIFIED = 1,
     PF_RESAMPLE_MULTINOMIAL = 2,
     PF_RESAMPLE_GUMBEL = 3,
-    PF_RESAMPLE_METROPOLIS = 4
+    PF_RESAMPLE_METROPOLIS = 4,
+    PF_RESAMPLE_REJECTION = 5
 } pf_resampler;
 
 /* pf_config.flags */
@@ -122,7 +134,8 @@ typedef struct {
     uint32_t flags;            /* PF_FLAG_* */
     int32_t est_capacity;      /* frames of estimates kept on the device; 0 = 4096 */
     int32_t resampler;         /* pf_resampler (0 = systematic) */
-    int32_t resampler_steps;   /* METROPOLIS: chain length B in [1, 4096]; 0 = 64.  Others: 0 */
+    int32_t resampler_steps;   /* METROPOLIS: chain length B in [1, 4096], 0 = 64; REJECTION: tries
+                                  R in [1, 65536], 0 = 4096.  Others: 0 */
     int32_t reserved;          /* must be 0 */
 } pf_config;
 

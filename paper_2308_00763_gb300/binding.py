@@ -19,7 +19,8 @@ __all__ = [
     "PF_OK", "PF_ERR_ARG", "PF_ERR_OOM", "PF_ERR_CUDA", "PF_ERR_TIMEOUT", "PF_ERR_STATE",
     "PF_ERR_ADMISSION", "PF_REF64", "PF_F32", "PF_F16", "PF_BF16", "PF_FLAG_DEBUG_ARRAYS",
     "PF_FLAG_ACCUM32", "PF_FLAG_TUNED", "PF_RESAMPLE_SYSTEMATIC", "PF_RESAMPLE_STRATIFIED", "PF_RESAMPLE_MULTINOMIAL",
-    "PF_RESAMPLE_GUMBEL", "PF_RESAMPLE_METROPOLIS", "RESAMPLERS", "PfTuning", "pf_autotune", "pf_autotune_batch", "pf_tuning_lookup",
+    "PF_RESAMPLE_GUMBEL", "PF_RESAMPLE_METROPOLIS", "PF_RESAMPLE_REJECTION",
+    "RESAMPLERS", "PfTuning", "pf_autotune", "pf_autotune_batch", "pf_tuning_lookup",
     "pf_tuning_store", "pf_tuning_clear", "autotune", "autotune_batch", "PfConfig", "PfStateHeader", "PfError", "lib", "library_path",
     "pf_status_string", "pf_create", "pf_step_frame", "pf_run_frames", "pf_estimate",
     "pf_estimates", "pf_frames_done", "pf_get_counters", "pf_batch_get_counters", "PfCounters", "pf_reset", "pf_destroy", "pf_get_state", "pf_set_state", "pf_get_debug",
@@ -39,10 +40,10 @@ PF_FLAG_ACCUM32 = 0x2
 PF_FLAG_TUNED = 0x4
 PRECISIONS = {"ref64": PF_REF64, "f64": PF_REF64, "f32": PF_F32, "f16": PF_F16, "bf16": PF_BF16}
 PF_RESAMPLE_SYSTEMATIC, PF_RESAMPLE_STRATIFIED, PF_RESAMPLE_MULTINOMIAL, PF_RESAMPLE_GUMBEL, \
-    PF_RESAMPLE_METROPOLIS = range(5)
+    PF_RESAMPLE_METROPOLIS, PF_RESAMPLE_REJECTION = range(6)
 RESAMPLERS = {"systematic": PF_RESAMPLE_SYSTEMATIC, "stratified": PF_RESAMPLE_STRATIFIED,
               "multinomial": PF_RESAMPLE_MULTINOMIAL, "gumbel": PF_RESAMPLE_GUMBEL,
-              "metropolis": PF_RESAMPLE_METROPOLIS}
+              "metropolis": PF_RESAMPLE_METROPOLIS, "rejection": PF_RESAMPLE_REJECTION}
 _POS_DTYPE = {PF_REF64: np.float64, PF_F32: np.float32, PF_F16: np.float16, PF_BF16: None}
 
 

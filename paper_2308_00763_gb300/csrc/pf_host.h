@@ -48,12 +48,13 @@ inline pf_status check_config(const pf_config *c) {
         return PF_ERR_ARG;
     if (fabs(c->init_x) > 1.0e6 || fabs(c->init_y) > 1.0e6) return PF_ERR_ARG;
     if (c->est_capacity < 0) return PF_ERR_ARG;
-    if (c->resampler < PF_RESAMPLE_SYSTEMATIC || c->resampler > PF_RESAMPLE_METROPOLIS) return PF_ERR_ARG;
+    if (c->resampler < PF_RESAMPLE_SYSTEMATIC || c->resampler > PF_RESAMPLE_REJECTION) return PF_ERR_ARG;
     // Gumbel-max draws N^2 variates a frame
     if (c->resampler == PF_RESAMPLE_GUMBEL && c->num_particles > kGumbelMaxN) return PF_ERR_ARG;
-    if (c->resampler == PF_RESAMPLE_METROPOLIS) {
+    if (c->resampler == PF_RESAMPLE_METROPOLIS || c->resampler == PF_RESAMPLE_REJECTION) {
         if (c->num_particles > kMetropolisMaxN) return PF_ERR_ARG;   // offspring index in the draw tag
-        if (c->resampler_steps < 0 || c->resampler_steps > kMetropolisMaxSteps) return PF_ERR_ARG;
+        const int cap = c->resampler == PF_RESAMPLE_METROPOLIS ? kMetropolisMaxSteps : kRejectionMaxTries;
+        if (c->resampler_steps < 0 || c->resampler_steps > cap) return PF_ERR_ARG;
     } else if (c->resampler_steps != 0) {
         return PF_ERR_ARG;
     }
@@ -98,8 +99,9 @@ inline void fill_tracker_constants(const pf_config &c, TrackerDev &T) {
     T.inv_n = 1.0 / static_cast<double>(c.num_particles);
     T.inv_n_f = 1.0f / static_cast<float>(c.num_particles);
     T.resampler = c.resampler;
-    T.steps = c.resampler == PF_RESAMPLE_METROPOLIS
-                  ? (c.resampler_steps ? c.resampler_steps : kMetropolisDefaultSteps) : 0;
+    T.steps = c.resampler == PF_RESAMPLE_METROPOLIS   ? (c.resampler_steps ? c.resampler_steps : kMetropolisDefaultSteps)
+              : c.resampler == PF_RESAMPLE_REJECTION ? (c.resampler_steps ? c.resampler_steps : kRejectionDefaultTries)
+                                                     : 0;
     T.init_xf = static_cast<float>(c.init_x); T.init_yf = static_cast<float>(c.init_y);
     T.drift_xf = static_cast<float>(c.drift_x); T.drift_yf = static_cast<float>(c.drift_y);
     T.sigma_xf = static_cast<float>(c.sigma_x); T.sigma_yf = static_cast<float>(c.sigma_y);

@@ -32,14 +32,17 @@ constexpr int kResampleStratified = 1;
 constexpr int kResampleMultinomial = 2;   // CDF by the step kernel, offspring by the pull kernel
 constexpr int kResampleGumbel = 3;        // ancestors by the Gumbel-max kernel, offspring by the pull kernel
 constexpr int kResampleMetropolis = 4;    // ancestors by the Metropolis kernel, offspring by the pull kernel
+constexpr int kResampleRejection = 5;     // ancestors by the rejection kernel, offspring by the pull kernel
 constexpr int64_t kGumbelMaxN = 1ll << 16; // N^2 draws a frame
 constexpr int64_t kMetropolisMaxN = 1ll << 24;   // offspring index in the Philox tag
 constexpr int kMetropolisMaxSteps = 4096;
 constexpr int kMetropolisDefaultSteps = 64;
+constexpr int kRejectionMaxTries = 65536;
+constexpr int kRejectionDefaultTries = 4096;
 
 // Schemes whose ancestors an ancestor kernel writes to T.anc before the pull kernel runs.
 __host__ __device__ constexpr bool ancestors_given(int resampler) {
-    return resampler == kResampleGumbel || resampler == kResampleMetropolis;
+    return resampler == kResampleGumbel || resampler == kResampleMetropolis || resampler == kResampleRejection;
 }
 
 // Device status bits (sticky, per tracker).
@@ -108,7 +111,7 @@ struct TrackerDev {
     double inv_n;              // 1.0 / N
     float inv_n_f;             // 1.0f / (float)N
     int32_t resampler;         // pf_resampler
-    int32_t steps;             // Metropolis: chain length B
+    int32_t steps;             // Metropolis: chain length B; rejection: tries R
     // FP32 copies for the FP32 kernels
     float init_xf, init_yf, drift_xf, drift_yf, sigma_xf, sigma_yf;
     float c1f, c2Df, denf;
@@ -117,7 +120,7 @@ struct TrackerDev {
     int32_t *dbg_anc;          // NULL unless PF_FLAG_DEBUG_ARRAYS
     void *dbg_cdf;
     void *cdf;                 // multinomial: the normalised CDF of the previous frame [N] (FP64 / FP32)
-    int32_t *anc;              // Gumbel-max, Metropolis: the ancestor of every offspring [N]
+    int32_t *anc;              // Gumbel-max, Metropolis, rejection: the ancestor of every offspring [N]
     LookbackDesc *look;
     TilePartial *part;
     uint32_t *done;
@@ -149,8 +152,9 @@ struct StepLaunch {
 int launch_step(int precision, const StepLaunch &L, int grid, void *stream);
 // The pull family's kernels after launch_step on the same stream: the multinomial
 // trackers' CDF kernel (when with_cdf), then the pull kernel (the offspring of the
-// multinomial, Gumbel-max and Metropolis trackers; the last two read the ancestors that
-// launch_gumbel / launch_metropolis wrote, enqueued before it).
+// multinomial, Gumbel-max, Metropolis and rejection trackers; the last three read the
+// ancestors that launch_gumbel / launch_metropolis / launch_rejection wrote, enqueued
+// before it).
 int launch_pull(int precision, const StepLaunch &L, int grid, bool with_cdf, void *stream);
 
 // An ancestor kernel over the trackers in slots[0 .. ntrk-1]: CTA b works on tracker g with
@@ -160,6 +164,7 @@ int launch_pull(int precision, const StepLaunch &L, int grid, bool with_cdf, voi
 constexpr int kGumbelOffspring = 8;       // Gumbel-max: offspring per CTA
 constexpr int kGumbelThreads = 256;
 constexpr int kMetropolisThreads = 256;   // Metropolis: one offspring per thread
+constexpr int kRejectionThreads = 256;    // rejection: one offspring per thread
 struct AncestorLaunch {
     const TrackerDev *trk;     // device array indexed by slot
     const FrameRef *frames;    // device array indexed by slot
@@ -170,6 +175,7 @@ struct AncestorLaunch {
 };
 int launch_gumbel(int precision, const AncestorLaunch &G, void *stream);
 int launch_metropolis(int precision, const AncestorLaunch &G, void *stream);
+int launch_rejection(int precision, const AncestorLaunch &G, void *stream);
 int step_grid_size(int precision, int total_tiles);
 // Particles per tile for a tracker of n particles.  A tracker of at least half a device
 // of full tiles (SMs x CTAs per SM x kTile / 2 particles) takes the smallest multiple of

@@ -1,0 +1,86 @@
+// pf_rejection.cu -- rejection resampling (sm_103a, CUDA cores only).
+//
+// Sec. 2 cites rejection resampling (Murray, Lee and Jacob, 2016) beside Metropolis
+// resampling as avoiding the prefix sum of the standard schemes.  Offspring j tests the
+// candidate k = j, then proposals k' uniform on {0, ..., N-1}, and keeps the first
+// candidate with u <= w_k / w_max, in the log form ln u <= L_k - M where M is the maximum
+// of L the previous step already computed (the state's M).  Offspring j keeps j with
+// probability w_j / w_max and otherwise draws from the normalised weights, so particle k's
+// expected offspring count is N w_k / sum w.  Expected tries: N w_max / sum w.
+//
+// Draws: try i of offspring j reads Philox(i / 2, t - 1, 6 + 256 j, tracker); word
+// 2 (i mod 2) gives the proposal k' = floor(w N / 2^32) (unused by try 0), word
+// 2 (i mod 2) + 1 the uniform u.  At most R = T.steps tries: after R refusals the last
+// candidate is kept (the loop is bounded whatever the weights).  The test runs in FP64 for
+// REF64 and FP32 for the others (L widened exactly from its stored type).
+//
+// Layout: one thread per offspring, 256 offspring per CTA; a warp runs until its last
+// lane accepts, so its cost follows the largest of 32 geometric try counts.
+#include <math.h>
+
+#include "pf_ancestor.cuh"
+#include "pf_device.cuh"
+#include "pf_internal.h"
+
+namespace pfk {
+namespace {
+
+__device__ __forceinline__ double log_uniform(uint32_t w, double) { return log(uniform_f64(w)); }
+__device__ __forceinline__ float log_uniform(uint32_t w, float) { return logf(uniform_f32(w)); }
+
+template <int P>
+__global__ void __launch_bounds__(kRejectionThreads) rejection_kernel(const AncestorLaunch G) {
+    using lik_t = typename Prec<P>::lik_t;
+    using acc_t = typename Prec<P>::acc_t;
+    constexpr bool kF64 = sizeof(acc_t) == 8;
+    const int b = static_cast<int>(blockIdx.x);
+    const int g = ancestor_tracker(G, b);
+    const int slot = __ldg(G.slots + g);
+    const TrackerDev &T = G.trk[slot];
+    const TrackerState *st = T.state;
+    const int64_t t = st->t;
+    if (t <= 0 || (st->status & kStatusTimeout) || !G.frames[slot].active) return;
+    const int N = static_cast<int>(T.N);
+    const int j = (b - __ldg(G.cta_prefix + g)) * kRejectionThreads + static_cast<int>(threadIdx.x);
+    if (j >= N) return;
+    const lik_t *__restrict__ L = static_cast<const lik_t *>(T.pl[static_cast<int>((t + 1) & 1)]);
+    const acc_t M = kF64 ? static_cast<acc_t>(st->M) : static_cast<acc_t>(st->M_f);
+    const uint32_t tctr = static_cast<uint32_t>(t - 1);
+    const uint32_t tag = 6u + (static_cast<uint32_t>(j) << 8);
+    const uint32_t key_lo = T.key_lo, key_hi = T.key_hi, trk_id = T.tracker_id;
+    const uint32_t n = static_cast<uint32_t>(N);
+    const int R = T.steps;
+
+    int k = j;
+    for (int i = 0; i < R; i += 2) {
+        const uint4 w = philox4x32_10(make_uint4(static_cast<uint32_t>(i >> 1), tctr, tag, trk_id), key_lo, key_hi);
+        if (i > 0) k = static_cast<int>(__umulhi(w.x, n));
+        if (log_uniform(w.y, acc_t{}) <= to_acc(L[k]) - M) break;
+        if (i + 1 >= R) break;
+        k = static_cast<int>(__umulhi(w.z, n));
+        if (log_uniform(w.w, acc_t{}) <= to_acc(L[k]) - M) break;
+    }
+    T.anc[j] = k;
+}
+
+template <int P>
+int launch_p(const AncestorLaunch &G, cudaStream_t s) {
+    rejection_kernel<P><<<G.total_ctas, kRejectionThreads, 0, s>>>(G);
+    return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+
+}  // namespace
+
+int launch_rejection(int precision, const AncestorLaunch &G, void *stream) {
+    if (G.total_ctas <= 0 || G.ntrk <= 0) return 0;
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    switch (precision) {
+        case 0: return launch_p<0>(G, s);
+        case 1: return launch_p<1>(G, s);
+        case 2: return launch_p<2>(G, s);
+        case 3: return launch_p<3>(G, s);
+        default: return 1;
+    }
+}
+
+}  // namespace pfk

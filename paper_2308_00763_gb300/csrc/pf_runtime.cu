@@ -104,7 +104,7 @@ struct Engine {
         int n = 0;
         int ctas = 0;
     };
-    AncestorTable gumbel, metro;       // Gumbel-max, Metropolis
+    AncestorTable gumbel, metro, rej;  // Gumbel-max, Metropolis, rejection
     uint32_t *d_ticket = nullptr;
     char *d_arena = nullptr;
     int total_tiles = 0;               // tiles of the step kernel's trackers (systematic, stratified)
@@ -130,7 +130,7 @@ struct Engine {
     int64_t n_step_launches = 0, n_kernels = 0, n_graphs = 0, n_host_bytes = 0;
     int kernels_per_step() const {
         return (total_tiles > 0 ? 1 : 0) + (pull_tiles > 0 ? 1 : 0) + (n_multi > 0 ? 1 : 0) + (gumbel.n > 0 ? 1 : 0) +
-               (metro.n > 0 ? 1 : 0);
+               (metro.n > 0 ? 1 : 0) + (rej.n > 0 ? 1 : 0);
     }
 
     pf_status fail(pf_status s) {
@@ -167,13 +167,14 @@ static void engine_free(Engine &e) {
     cudaFree(e.d_tile_trk);
     cudaFree(e.gumbel.d);
     cudaFree(e.metro.d);
+    cudaFree(e.rej.d);
     cudaFree(e.d_ticket);
     cudaFree(e.d_arena);
     cudaFree(e.d_frame_buf);
     if (e.h_frames_pinned) cudaFreeHost(e.h_frames_pinned);
     if (e.h_init_pinned) cudaFreeHost(e.h_init_pinned);
     e.h_init_pinned = nullptr;
-    e.d_trk = nullptr; e.d_frames = nullptr; e.d_tile_trk = nullptr; e.gumbel.d = nullptr; e.metro.d = nullptr;
+    e.d_trk = nullptr; e.d_frames = nullptr; e.d_tile_trk = nullptr; e.gumbel.d = nullptr; e.metro.d = nullptr; e.rej.d = nullptr;
     e.d_ticket = nullptr;
     e.d_arena = nullptr; e.d_frame_buf = nullptr; e.h_frames_pinned = nullptr;
 }
@@ -207,7 +208,7 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
     // pull kernel's (multinomial, Gumbel-max, Metropolis), so no launch carries tiles it
     // skips.  The ancestor kernels number their CTAs per scheme.
     int64_t tiles = 0, mtiles = 0;
-    std::vector<int32_t> atab[2], aprefix[2] = {{0}, {0}};   // Gumbel-max, Metropolis
+    std::vector<int32_t> atab[3], aprefix[3] = {{0}, {0}, {0}};   // Gumbel-max, Metropolis, rejection
     for (int i = 0; i < n; ++i) {
         const pf_config &c = cfgs[i];
         const int64_t N = c.num_particles;
@@ -232,7 +233,7 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
         o.state = states_off + sizeof(TrackerState) * i;
         o.est = a.take(sizeof(double) * 2 * cap);
         o.stat = a.take(sizeof(double) * 2 * cap);
-        const bool given = ancestors_given(c.resampler);          // Gumbel-max, Metropolis
+        const bool given = ancestors_given(c.resampler);          // Gumbel-max, Metropolis, rejection
         const bool multi = c.resampler == PF_RESAMPLE_MULTINOMIAL || given;   // the pull family
         if (c.flags & PF_FLAG_DEBUG_ARRAYS) {
             o.dbga = a.take(sizeof(int32_t) * N);
@@ -240,8 +241,8 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
         }
         if (multi) o.cdf = a.take((given ? sizeof(int32_t) : cdf_b) * N + 16);
         if (given) {
-            const int s = c.resampler == PF_RESAMPLE_GUMBEL ? 0 : 1;
-            const int per = s == 0 ? kGumbelOffspring : kMetropolisThreads;
+            const int s = c.resampler == PF_RESAMPLE_GUMBEL ? 0 : c.resampler == PF_RESAMPLE_METROPOLIS ? 1 : 2;
+            const int per = s == 0 ? kGumbelOffspring : s == 1 ? kMetropolisThreads : kRejectionThreads;
             const int64_t ctas = aprefix[s].back() + (N + per - 1) / per;
             if (ctas > 0x7fffffff) return PF_ERR_ARG;
             atab[s].push_back(i);
@@ -259,8 +260,8 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
     }
     e.total_tiles = static_cast<int>(tiles);
     e.pull_tiles = static_cast<int>(mtiles);
-    Engine::AncestorTable *tabs[2] = {&e.gumbel, &e.metro};
-    for (int s = 0; s < 2; ++s) {
+    Engine::AncestorTable *tabs[3] = {&e.gumbel, &e.metro, &e.rej};
+    for (int s = 0; s < 3; ++s) {
         tabs[s]->n = static_cast<int>(atab[s].size());
         tabs[s]->ctas = aprefix[s].back();
         atab[s].insert(atab[s].end(), aprefix[s].begin(), aprefix[s].end());   // slots, then prefix
@@ -274,7 +275,7 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
     if (err == cudaSuccess) err = cudaMalloc(reinterpret_cast<void **>(&e.d_frames), sizeof(FrameRef) * n);
     if (err == cudaSuccess)
         err = cudaMalloc(reinterpret_cast<void **>(&e.d_tile_trk), sizeof(int32_t) * (e.total_tiles + e.pull_tiles + 1));
-    for (int s = 0; s < 2 && err == cudaSuccess; ++s)
+    for (int s = 0; s < 3 && err == cudaSuccess; ++s)
         if (tabs[s]->n > 0) err = cudaMalloc(reinterpret_cast<void **>(&tabs[s]->d), sizeof(int32_t) * atab[s].size());
     if (err == cudaSuccess) err = cudaMalloc(reinterpret_cast<void **>(&e.d_ticket), sizeof(uint32_t));
     if (err == cudaSuccess) err = cudaMallocHost(reinterpret_cast<void **>(&e.h_frames_pinned), sizeof(FrameRef) * n);
@@ -330,7 +331,7 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
     if (err == cudaSuccess)
         err = cudaMemcpyAsync(e.d_tile_trk, tile_trk.data(), sizeof(int32_t) * tile_trk.size(),
                               cudaMemcpyHostToDevice, e.stream);
-    for (int s = 0; s < 2 && err == cudaSuccess; ++s)
+    for (int s = 0; s < 3 && err == cudaSuccess; ++s)
         if (tabs[s]->n > 0)
             err = cudaMemcpyAsync(tabs[s]->d, atab[s].data(), sizeof(int32_t) * atab[s].size(), cudaMemcpyHostToDevice,
                                   e.stream);
@@ -376,13 +377,14 @@ static AncestorLaunch ancestor_launch(const Engine &e, const Engine::AncestorTab
 
 // One frame's launches: the step kernel over its family's tiles, then, for the pull
 // family, the CDF kernel (multinomial trackers), the ancestor kernels (Gumbel-max,
-// Metropolis) and the pull kernel over the pull family's tiles (tile table entries after
+// Metropolis, rejection) and the pull kernel over the pull family's tiles (tile table entries after
 // the step family's).  L carries the step family's table and count.
 static int engine_enqueue(const Engine &e, StepLaunch L, cudaStream_t stream) {
     int rc = 0;
     if (e.total_tiles > 0) rc = launch_step(e.prec, L, e.grid, stream);
     if (rc == 0 && e.gumbel.n > 0) rc = launch_gumbel(e.prec, ancestor_launch(e, e.gumbel), stream);
     if (rc == 0 && e.metro.n > 0) rc = launch_metropolis(e.prec, ancestor_launch(e, e.metro), stream);
+    if (rc == 0 && e.rej.n > 0) rc = launch_rejection(e.prec, ancestor_launch(e, e.rej), stream);
     if (rc == 0 && e.pull_tiles > 0) {
         L.tile_trk = e.d_tile_trk + e.total_tiles;
         L.total_tiles = e.pull_tiles;
@@ -824,7 +826,7 @@ pf_status pf_get_debug(pf_filter *f, int32_t which, void *host_buf, size_t bytes
     Engine &e = f->e;
     const TrackerDev &T = e.h_trk[0];
     if (!T.dbg_anc) return PF_ERR_STATE;
-    if (which == 1 && !T.dbg_cdf) return PF_ERR_ARG;   // a Gumbel-max or Metropolis tracker has no CDF
+    if (which == 1 && !T.dbg_cdf) return PF_ERR_ARG;   // Gumbel-max, Metropolis, rejection: no CDF
     const size_t elem = which == 0 ? 4 : (e.prec == PF_REF64 ? 8 : 4);
     if (which < 0 || which > 1 || bytes < elem * static_cast<size_t>(T.N)) return PF_ERR_ARG;
     cudaError_t err = cudaStreamSynchronize(e.stream);

@@ -391,7 +391,7 @@ pf_status pf_server_create(const pf_server_config *cfg, pf_server **out) {
 pf_status pf_server_open(pf_server *S, const pf_config *cfg, double fps, int32_t host_frames, int32_t *stream_id) {
     if (!S || !stream_id || check_config(cfg) != PF_OK || !(fps >= 0) || !isfinite(fps)) return PF_ERR_ARG;
     if (cfg->flags & PF_FLAG_DEBUG_ARRAYS) return PF_ERR_ARG;
-    // one launch per tick: no pull kernel (multinomial, Gumbel-max, Metropolis)
+    // one launch per tick: no pull kernel (multinomial, Gumbel-max, Metropolis, rejection)
     if (cfg->resampler == PF_RESAMPLE_MULTINOMIAL || ancestors_given(cfg->resampler)) return PF_ERR_ARG;
     if (S->sticky != PF_OK) return PF_ERR_STATE;
     *stream_id = -1;

@@ -31,9 +31,9 @@
 // reaches an independent uniform v_j (a binary search over T.cdf), gathers the ancestors'
 // positions of its tile's offspring into shared memory, sizes the likelihood window by
 // them and runs phases 2-5 as the step kernel does.  Gumbel-max trackers (the log-domain
-// form of the same draw, Sec. 3) and Metropolis trackers (Sec. 2) skip the CDF kernel: the
-// pull kernel reads the ancestors their kernel (pf_gumbel.cu, pf_metropolis.cu) wrote to
-// T.anc instead of searching.
+// form of the same draw, Sec. 3), Metropolis and rejection trackers (Sec. 2) skip the CDF
+// kernel: the pull kernel reads the ancestors their kernel (pf_gumbel.cu, pf_metropolis.cu,
+// pf_rejection.cu) wrote to T.anc instead of searching.
 //
 // Scan boundaries.  The prefix between tiles is an exact 128-bit fixed-point sum of
 // the tiles' aggregates, so every tile obtains the same boundary value whichever
@@ -645,7 +645,7 @@ __device__ void finalize_tracker(const TrackerDev &T, TrackerState *st, StepSmem
 // Kernel modes: the step kernel (systematic and stratified trackers, every phase), and for
 // multinomial trackers the CDF kernel (phase 1 up to the CDF, written to T.cdf) and the
 // pull kernel (resampling from T.cdf, phases 2-5), launched in that order; the pull kernel
-// also takes the Gumbel-max and Metropolis trackers (ancestors from T.anc).
+// also takes the Gumbel-max, Metropolis and rejection trackers (ancestors from T.anc).
 constexpr int kModeStep = 0, kModeCdf = 1, kModePull = 2;
 
 // One tile of a launch in mode kMode (trackers of the other modes are skipped).
@@ -856,7 +856,7 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
         acc_t uq[kItems];
         int lo[kItems], hi[kItems];
         if (ancestors_given(T.resampler)) {
-            // Gumbel-max, Metropolis: the ancestor kernel wrote every offspring's ancestor
+            // Gumbel-max, Metropolis, rejection: the ancestor kernel wrote every offspring's ancestor
 #pragma unroll
             for (int m = 0; m < kItems; ++m) {
                 const int a = (eb + m < cnt) ? __ldg(T.anc + PF_IDX(k0 + eb + m, N)) : 0;

@@ -66,7 +66,7 @@ def test_invalid_configs_rejected_without_gpu(libpath):
     import paper_2308_00763_gb300 as pf
     bad = [dict(num_particles=0), dict(disk_radius=-1), dict(disk_radius=65), dict(width=0),
            dict(precision=7), dict(sigma=(-1.0, 1.0)), dict(init=(float("nan"), 0.0)),
-           dict(resampler=5), dict(resampler=-1),
+           dict(resampler=6), dict(resampler=-1),
            # stratified points in FP32 are ordered only while (float)j is exact
            dict(resampler="stratified", num_particles=(1 << 24) + 1),
            # Gumbel-max draws N^2 variates a frame
@@ -76,7 +76,10 @@ def test_invalid_configs_rejected_without_gpu(libpath):
            dict(resampler="metropolis", num_particles=(1 << 24) + 1),
            dict(resampler="metropolis", resampler_steps=-1),
            dict(resampler="metropolis", resampler_steps=4097),
-           dict(resampler="systematic", resampler_steps=8)]
+           dict(resampler="systematic", resampler_steps=8),
+           # rejection: at most 65536 tries per offspring
+           dict(resampler="rejection", resampler_steps=65537),
+           dict(resampler="rejection", num_particles=(1 << 24) + 1)]
     for b in bad:
         kw = dict(width=64, height=64, num_particles=100, disk_radius=3, precision="f32")
         kw.update({k: v for k, v in b.items() if k in kw})
@@ -109,8 +112,9 @@ def test_server_stream_bytes_without_gpu(libpath):
         pf.pf_server_stream_bytes(pf.make_config(640, 480, 10, 5, "f16", resampler="multinomial"), 0, 4)
     with pytest.raises(pf.PfError):    # nor Gumbel-max or Metropolis streams (ancestor and pull kernels)
         pf.pf_server_stream_bytes(pf.make_config(640, 480, 10, 5, "f16", resampler="gumbel"), 0, 4)
-    with pytest.raises(pf.PfError):
-        pf.pf_server_stream_bytes(pf.make_config(640, 480, 10, 5, "f16", resampler="metropolis"), 0, 4)
+    for scheme in ("metropolis", "rejection"):
+        with pytest.raises(pf.PfError):
+            pf.pf_server_stream_bytes(pf.make_config(640, 480, 10, 5, "f16", resampler=scheme), 0, 4)
 
 
 def test_tuning_cache_without_gpu(libpath):

@@ -7,7 +7,7 @@ to element 0 and fail the step with PF_ERR_STATE.  compute-sanitizer is not part
 project's runs, so this build is how the index arithmetic is exercised on the GPU.
 
 A child process loads the checked library (PF_CHECKED=1) and runs a spread of workloads:
-every precision at ragged sizes, the five resampling schemes, a batch, radii 0 and 12 with
+every precision at ragged sizes, the six resampling schemes, a batch, radii 0 and 12 with
 template pixels off the frame, one dominant particle (a tile's offspring all from one
 ancestor), the bench's 2^20-particle configuration, a served trace and the
 allocation-free entry point.  Each must finish without a status error, and its tracks
@@ -39,7 +39,7 @@ v = synth.make_video(160, 120, 6, 4, noise=5.0, seed=5, v=(1.0, -1.0))
 fr = frames(v)
 for prec in ("ref64", "f32", "f16", "bf16"):
     for N in (1, 4097, 3 * 4096 + 17):
-        for rs in ("systematic", "stratified", "multinomial", "gumbel", "metropolis"):
+        for rs in ("systematic", "stratified", "multinomial", "gumbel", "metropolis", "rejection"):
             f = pf.Filter(v.W, v.H, N, 4, prec, init=tuple(v.centres[0]), seed=3, resampler=rs,
                           flags=pf.PF_FLAG_DEBUG_ARRAYS)
             f.run(fr)

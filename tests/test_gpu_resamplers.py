@@ -7,12 +7,13 @@ particle whose CDF value reaches an independent uniform v_j (Sec. 3's categorica
 Gumbel-max: the argmax kernel gives offspring j the particle maximising L_k + g_jk (the
 log-domain form of the same draw that Sec. 3 weighs), the pull kernel gathers them.
 Metropolis: offspring j's B-step chain on exp(L) (the reduction-free scheme Sec. 2 cites).
+Rejection: offspring j's first candidate (j, then uniform proposals) passing u <= w/w_max.
 The checks: the ancestors are exactly the oracle's resampling of the CDF the step computed,
 with the draws from the oracle's own Philox; the REF64 track equals the oracle's FP64 track
 of the same scheme within 1e-9 px; stratified offspring counts stay within two strata of
 N w_k; the option takes effect; the schemes share a batch, each tracker equal to its own
 single run; the bench's launch configuration (2^20 particles) resamples exactly.  Gumbel-max
-and Metropolis ancestors equal the oracle's decisions in the kernel's precision up to near
+Metropolis and rejection ancestors equal the oracle's decisions in the kernel's precision up to near
 ties (FP32 logs may differ in the last bit between the two sides).
 """
 import numpy as np
@@ -427,11 +428,90 @@ def test_metropolis_tracks_the_truth_and_steps_equal_runs(pf, prec):
     assert np.sqrt(np.mean(np.sum((ea - est_o) ** 2, axis=1))) <= 0.5
 
 
-def test_five_schemes_in_one_batch_equal_singles(pf):
-    vids = [synth.make_video(96, 96, 5, 3, noise=5.0, seed=100 + i, v=(1.0, -1.0)) for i in range(6)]
-    Ns = [3000, 2 * TILE + 5, 777, 5000, 1500, 2 * TILE + 300]
-    rs = ["metropolis", "systematic", "stratified", "multinomial", "gumbel", "metropolis"]
-    steps = [0, 0, 0, 0, 0, 9]
+# ----------------------------------------------------------------------------- rejection
+def _check_rejection(L, M, seed, t, tracker, anc, prec, tries=4096):
+    """Ancestors equal the oracle's tries in the kernel's precision (bound M from the
+    state); an offspring that ends elsewhere must have met a test within rounding of its
+    threshold, and such offspring are rare."""
+    want = oracle.resample_rejection(L, M, seed, t, tracker, "f64" if prec == "ref64" else "f32", tries)
+    bad = np.nonzero(anc != want)[0]
+    assert np.all((anc >= 0) & (anc < L.size))
+    assert bad.size <= max(1, L.size // 1000), bad[:10]
+    tol = 1e-12 if prec == "ref64" else 1e-4
+    for j in bad:
+        _, margins = oracle.rejection_trace(L, M, seed, t, int(j), tracker, tries)
+        assert min(margins) <= tol, (j, want[j], anc[j], min(margins))
+
+
+def _rejection_step(pf, v, N, prec, seed, *, tracker=0, tries=0):
+    f = pf.Filter(v.W, v.H, N, v.radius, prec, init=tuple(v.centres[0]), seed=seed, tracker_id=tracker,
+                  flags=pf.PF_FLAG_DEBUG_ARRAYS, resampler="rejection", resampler_steps=tries)
+    fr = _frames(v)
+    f.run(fr[:v.T - 1])
+    st = f.get_state()
+    f.step(fr[v.T - 1])
+    anc = f.debug(0).astype(np.int64)
+    f.close()
+    return anc, st["L"].astype(np.float64), float(st["max_l"]), int(st["t"]) - 1
+
+
+@pytest.mark.parametrize("prec", ["ref64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("N", [1, 3, 1000, TILE + 1, 3 * TILE + 17])
+def test_rejection_ancestors_exact(pf, prec, N):
+    v = synth.make_video(128, 128, 4, 5, noise=5.0, seed=51)
+    anc, L, M, t = _rejection_step(pf, v, N, prec, 29, tracker=8)
+    assert M == L.max() or prec != "ref64"
+    _check_rejection(L, M, 29, t, 8, anc, prec)
+
+
+@pytest.mark.parametrize("tries", [1, 2, 5])
+def test_rejection_truncated_tries(pf, tries):
+    """Few tries: many offspring keep their last candidate, exactly as the oracle does."""
+    v = synth.make_video(128, 128, 4, 5, noise=5.0, seed=52)
+    anc, L, M, t = _rejection_step(pf, v, 5000, "f32", 30, tracker=3, tries=tries)
+    _check_rejection(L, M, 30, t, 3, anc, "f32", tries)
+
+
+def test_rejection_full_size_ancestors_exact(pf):
+    v = synth.make_video(512, 512, 3, 5, noise=5.0, seed=1)
+    anc, L, M, t = _rejection_step(pf, v, 1 << 20, "f16", 1)
+    _check_rejection(L, M, 1, t, 0, anc, "f16")
+
+
+def test_rejection_ref64_track_within_1e9(pf):
+    v = synth.make_video(128, 128, 10, 5, noise=5.0, seed=1)
+    for N in (1000, 3 * TILE + 17):
+        est_o, M_o, _ = oracle.track(v.frames, N, 5, init=tuple(v.centres[0]), seed=1, resampler="rejection")
+        f = pf.Filter(v.W, v.H, N, 5, "ref64", init=tuple(v.centres[0]), seed=1, resampler="rejection")
+        f.run(_frames(v))
+        est, ms = f.estimates(0, v.T, with_stats=True)
+        f.close()
+        assert np.abs(est - est_o).max() <= 1e-9, N
+        assert np.array_equal(ms[:, 0], M_o)
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16", "bf16"])
+def test_rejection_tracks_the_truth_and_steps_equal_runs(pf, prec):
+    v = synth.make_video(128, 128, 10, 5, noise=5.0, seed=1)
+    est_o, _, _ = oracle.track(v.frames, 1000, 5, init=tuple(v.centres[0]), seed=1, resampler="rejection")
+    fr = _frames(v)
+    a = pf.Filter(v.W, v.H, 1000, 5, prec, init=tuple(v.centres[0]), seed=1, resampler="rejection")
+    a.run(fr)
+    b = pf.Filter(v.W, v.H, 1000, 5, prec, init=tuple(v.centres[0]), seed=1, resampler="rejection")
+    for t in range(v.T):
+        b.step(fr[t])
+    ea, eb = a.estimates(0, v.T), b.estimates(0, v.T)
+    a.close()
+    b.close()
+    assert np.array_equal(ea, eb)
+    assert np.sqrt(np.mean(np.sum((ea - est_o) ** 2, axis=1))) <= 0.5
+
+
+def test_six_schemes_in_one_batch_equal_singles(pf):
+    vids = [synth.make_video(96, 96, 5, 3, noise=5.0, seed=100 + i, v=(1.0, -1.0)) for i in range(7)]
+    Ns = [3000, 2 * TILE + 5, 777, 5000, 1500, 2 * TILE + 300, 2500]
+    rs = ["metropolis", "systematic", "stratified", "multinomial", "gumbel", "metropolis", "rejection"]
+    steps = [0, 0, 0, 0, 0, 9, 0]
     for prec in ("ref64", "f32", "f16"):
         cfgs = [pf.make_config(v.W, v.H, n, v.radius, prec, init=tuple(v.centres[0]), seed=40 + i,
                                tracker_id=i, resampler=r, resampler_steps=b)
@@ -443,7 +523,7 @@ def test_five_schemes_in_one_batch_equal_singles(pf):
         got = np.stack([bt.estimates(t) for t in range(5)], axis=1)
         c = bt.counters()
         bt.close()
-        assert c["kernel_launches"] == 5 * 5, c      # step, CDF, argmax, chains, pull
+        assert c["kernel_launches"] == 5 * 6, c      # step, CDF, argmax, chains, tries, pull
         for i, (v, n, r, b) in enumerate(zip(vids, Ns, rs, steps)):
             s1 = pf.Filter(v.W, v.H, n, v.radius, prec, init=tuple(v.centres[0]), seed=40 + i, tracker_id=i,
                            resampler=r, resampler_steps=b)
@@ -469,9 +549,12 @@ def test_metropolis_limits_and_debug(pf):
         f.debug(1)
     f.close()
     s = pf.Server(1 << 26, max_streams=2, queue_depth=2)
-    with pytest.raises(pf.PfError):
-        s.open(pf.make_config(64, 64, 100, 3, "f16", resampler="metropolis"))
+    for scheme in ("metropolis", "rejection"):
+        with pytest.raises(pf.PfError):
+            s.open(pf.make_config(64, 64, 100, 3, "f16", resampler=scheme))
     s.close()
+    with pytest.raises(pf.PfError):
+        pf.Filter(64, 64, 100, 3, "f16", resampler="rejection", resampler_steps=65537)
 
 
 def test_counters_count_launches_graphs_and_host_bytes(pf):
@@ -479,7 +562,7 @@ def test_counters_count_launches_graphs_and_host_bytes(pf):
     (step kernel skipped: CDF and pull), one graph replay per resident run, host bytes."""
     v = synth.make_video(96, 80, 7, 3, noise=5.0, seed=44)
     fr = _frames(v)
-    for rs, per in (("systematic", 1), ("multinomial", 2), ("gumbel", 2), ("metropolis", 2)):
+    for rs, per in (("systematic", 1), ("multinomial", 2), ("gumbel", 2), ("metropolis", 2), ("rejection", 2)):
         f = pf.Filter(v.W, v.H, 3000, 3, "f32", init=tuple(v.centres[0]), seed=2, resampler=rs)
         f.step(v.frames[0])                      # host frame
         f.step(fr[1])

@@ -77,9 +77,9 @@ def test_noalloc_two_frames_match_filter(pf, prec, resampler):
         np.testing.assert_allclose(g, st1[name], rtol=0, atol=tol if name != "L" else 1e-6)
 
 
-@pytest.mark.parametrize("scheme", ["multinomial", "gumbel", "metropolis"])
+@pytest.mark.parametrize("scheme", ["multinomial", "gumbel", "metropolis", "rejection"])
 def test_noalloc_rejects_pull_schemes(pf, scheme):
-    """Multinomial, Gumbel-max and Metropolis resampling keep a CDF or the ancestors in
+    """Multinomial, Gumbel-max, Metropolis and rejection resampling keep a CDF or the ancestors in
     device memory and run two more kernels; the allocation-free entry point takes
     systematic and stratified trackers only."""
     cfg = pf.make_config(64, 64, 1000, 3, "f32", resampler=scheme)
