@@ -200,8 +200,11 @@ int64_t pf_frames_done(const pf_filter *f);
 typedef struct {
     int64_t frames;            /* tracker-frames stepped (a batch: summed over its trackers) */
     int64_t step_launches;     /* frame steps enqueued (one per frame of the handle) */
-    int64_t kernel_launches;   /* kernels enqueued, graph nodes included (1 per step; 2 more
-                                  for multinomial trackers: CDF and pull) */
+    int64_t kernel_launches;   /* kernels enqueued, graph nodes included: per step 1 for the
+                                  systematic and stratified trackers, 1 pull kernel for the
+                                  others, plus 1 CDF kernel (multinomial) and 1 ancestor
+                                  kernel per scheme present (Gumbel-max, Metropolis,
+                                  rejection) */
     int64_t graph_launches;    /* CUDA graph replays (pf_run_frames, pf_batch_run) */
     int64_t host_frame_bytes;  /* frame bytes copied from host memory to the device */
     int32_t status;            /* the handle's sticky pf_status */
@@ -241,7 +244,9 @@ pf_status pf_set_state(pf_filter *f, const void *host_buf, size_t bytes);
 /* Test hooks (flags & PF_FLAG_DEBUG_ARRAYS): after a step, `which` = 0 copies the
  * ancestor index a_j of every particle j of that step (int32[N]; undefined at frame
  * 0), `which` = 1 the CDF C_k of the previous frame as the step computed it (double[N]
- * for REF64, float[N] otherwise).  Synchronises.  host_buf: host pointer of `bytes`. */
+ * for REF64, float[N] otherwise; PF_ERR_ARG for the schemes that build no CDF: Gumbel-max,
+ * Metropolis, rejection).  Synchronises.  host_buf: host pointer of `bytes`.
+ * Errors: PF_ERR_STATE (no debug arrays), PF_ERR_ARG, PF_ERR_CUDA. */
 pf_status pf_get_debug(pf_filter *f, int32_t which, void *host_buf, size_t bytes);
 
 /* Test hook: Philox4x32-10 on the device, the same generator the step uses: for each
