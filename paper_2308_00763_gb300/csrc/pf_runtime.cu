@@ -108,7 +108,8 @@ struct Engine {
     uint32_t *d_ticket = nullptr;
     char *d_arena = nullptr;
     int total_tiles = 0;               // tiles of the step kernel's trackers (systematic, stratified)
-    int pull_tiles = 0;                // tiles of the pull kernel's trackers (multinomial, Gumbel-max)
+    int pull_tiles = 0;                // tiles of the pull kernel's trackers (multinomial, Gumbel-max,
+                                       // Metropolis, rejection)
     int n_multi = 0;                   // multinomial trackers (the CDF kernel runs when > 0)
     int grid = 0;
     int grid_pull = 0;
@@ -174,8 +175,8 @@ static void engine_free(Engine &e) {
     if (e.h_frames_pinned) cudaFreeHost(e.h_frames_pinned);
     if (e.h_init_pinned) cudaFreeHost(e.h_init_pinned);
     e.h_init_pinned = nullptr;
-    e.d_trk = nullptr; e.d_frames = nullptr; e.d_tile_trk = nullptr; e.gumbel.d = nullptr; e.metro.d = nullptr; e.rej.d = nullptr;
-    e.d_ticket = nullptr;
+    e.d_trk = nullptr; e.d_frames = nullptr; e.d_tile_trk = nullptr; e.d_ticket = nullptr;
+    e.gumbel.d = nullptr; e.metro.d = nullptr; e.rej.d = nullptr;
     e.d_arena = nullptr; e.d_frame_buf = nullptr; e.h_frames_pinned = nullptr;
 }
 
@@ -205,8 +206,8 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
     // the trackers' states form one array (the kernel indexes it by tracker)
     const size_t states_off = a.take(sizeof(TrackerState) * n);
     // Tiles are numbered per kernel family: the step kernel's trackers first, then the
-    // pull kernel's (multinomial, Gumbel-max, Metropolis), so no launch carries tiles it
-    // skips.  The ancestor kernels number their CTAs per scheme.
+    // pull kernel's (multinomial, Gumbel-max, Metropolis, rejection), so no launch carries
+    // tiles it skips.  The ancestor kernels number their CTAs per scheme.
     int64_t tiles = 0, mtiles = 0;
     std::vector<int32_t> atab[3], aprefix[3] = {{0}, {0}, {0}};   // Gumbel-max, Metropolis, rejection
     for (int i = 0; i < n; ++i) {
