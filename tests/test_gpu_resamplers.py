@@ -12,9 +12,10 @@ The checks: the ancestors are exactly the oracle's resampling of the CDF the ste
 with the draws from the oracle's own Philox; the REF64 track equals the oracle's FP64 track
 of the same scheme within 1e-9 px; stratified offspring counts stay within two strata of
 N w_k; the option takes effect; the schemes share a batch, each tracker equal to its own
-single run; the bench's launch configuration (2^20 particles) resamples exactly.  Gumbel-max
-Metropolis and rejection ancestors equal the oracle's decisions in the kernel's precision up to near
-ties (FP32 logs may differ in the last bit between the two sides).
+single run; the bench's launch configuration (2^20 particles) resamples exactly.
+Gumbel-max, Metropolis and rejection ancestors equal the oracle's decisions in the
+kernel's precision up to near ties (FP32 logs may differ in the last bit between the two
+sides).
 """
 import numpy as np
 import pytest
