@@ -32,10 +32,14 @@ sys.path.insert(0, ROOT)
 W_, H_, T_, R_, N_, NOISE_, SEED_ = 512, 512, 100, 5, 1 << 20, 5.0, 1
 WORKLOAD = ("single tracker at scale: 512x512 uint8 synthetic video, 100 frames, disk r=5 "
             "moving (+1,-2) px/frame, noise sigma 5, 2^20 particles, random walk sigma 1 px, Philox seed 1")
+WORKLOAD_SHORT = "512x512 video, 100 frames, disk r=5 moving (+1,-2), noise 5, 2^20 particles, sigma 1 px, seed 1"
 METRIC = "particle-steps/s"
-# algorithmic HBM bytes per particle-step of the fused step kernel: read L + x,y of the
-# previous frame, write x,y + L of the new frame (the frame's template pixels are L2/L1 hits)
-BYTES_PER_PSTEP = {"ref64": 48, "f32": 24, "f16": 12, "bf16": 12}
+# Algorithmic HBM bytes per particle-step of a separate scan-and-search step (the roofline
+# unit): read parent x, y; write x, y; write L; scan (read L, write C); search (read C).
+BYTES_PER_PSTEP = {"ref64": 64, "f32": 32, "f16": 20, "bf16": 20}
+# The fused step kernel moves less: read L + x, y of the previous frame, write x, y + L of
+# the new frame (no CDF or ancestor array goes through memory).
+FUSED_BYTES_PER_PSTEP = {"ref64": 48, "f32": 24, "f16": 12, "bf16": 12}
 DTYPE_NAME = {"ref64": "f64", "f32": "f32", "f16": "f16", "bf16": "bf16"}
 
 
@@ -51,14 +55,24 @@ def _args():
     p.add_argument("--frames", type=int, default=T_)
     p.add_argument("--no-batch", action="store_true", help="skip the batched-trackers measurement")
     p.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
-    p.add_argument("--no-sweep", action="store_true", help="skip the precision/size sweep and the paper workload")
-    p.add_argument("--serve-seconds", type=float, default=20.0, help="length of the served-streams run")
+    p.add_argument("--serve-seconds", type=float, default=20.0,
+                   help="length of the served-streams run (the served workload is stated for 60 s; "
+                        "20 s by default to keep the bench within a few minutes)")
+    p.add_argument("--serve-overload", type=float, default=20.0,
+                   help="also replay the served workload with every stream's particle count scaled by this "
+                        "factor (capped at 2^24) so that admission refuses streams; 0 = skip")
+    p.add_argument("--systems", action="store_true",
+                   help="also run the precision/size sweep, the paper's workload, the resampler and Gumbel-max "
+                        "studies (printed in the detail line on stderr)")
     p.add_argument("--resampler", default="systematic",
                    choices=["systematic", "stratified", "multinomial", "metropolis", "rejection"],
                    help="resampling scheme of the timed filters (the paper's is systematic)")
     p.add_argument("--tpb-sweep", action="store_true",
                    help="thread-block study: build the step kernel at 128/256/512/1024 threads per CTA and time each")
     p.add_argument("--tpb-child", action="store_true", help=argparse.SUPPRESS)
+    p.add_argument("--core-peaks", action="store_true",
+                   help="measure the CUDA-core throughputs (FP32/FP16x2/BF16x2/FP64 FMA, ex2, IMAD, logic, "
+                        "shared loads) with the microbenchmark; one JSON object")
     p.add_argument("--gumbel", type=int, default=0, metavar="N",
                    help="Gumbel-max study only: time Gumbel-max, systematic and multinomial resampling of "
                         "an N-particle tracker (N <= 2^16) in --precision on the headline video; one JSON object")
@@ -201,10 +215,21 @@ def _traffic(prec):
     return _ncu_figure("dram_bytes_per_launch", prec)
 
 
+def _core_peaks():
+    """The committed CUDA-core microbenchmark result (profiles/cuda_core_peaks.json), or None."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "cuda_core_peaks.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return None
+
+
 def _issue_view(prec, launch_us, dev):
     """Instruction-issue view of the step kernel: achieved thread instructions per second
     (warp instructions per launch from the committed ncu capture x 32 / launch time)
-    against SMs x 4 schedulers x 32 lanes x the maximum SM clock (nvidia-smi)."""
+    against the issue rate of the SMs: 4 schedulers x 32 lanes x SMs x the maximum SM
+    clock (nvidia-smi); the measured rate of the integer-logic microbenchmark
+    (profiles/cuda_core_peaks.json) is reported beside it."""
     import torch
     warp_instr = _ncu_figure("warp_instructions_per_launch", prec)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -217,10 +242,27 @@ def _issue_view(prec, launch_us, dev):
         mhz = None
     peak = sms * 4 * 32 * mhz * 1e6 if mhz else None
     achieved = warp_instr * 32 / (launch_us * 1e-6) if warp_instr else None
-    return {"bound": "issue", "achieved": achieved, "peak": peak, "unit": "thread instructions/s",
+    cp = _core_peaks()
+    measured = None
+    if cp:
+        measured = cp.get("rates", {}).get("xor_add", {}).get("thread_instructions_per_s")
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "thread instructions/s",
             "frac": achieved / peak if (achieved and peak) else None,
+            "measured_alu_peak": measured,
             "instructions_per_particle_step": warp_instr * 32 / N_ if warp_instr else None,
-            "peak_source": "SMs x 4 schedulers x 32 lanes x max SM clock (%s MHz)" % mhz}
+            "peak_source": "issue: SMs x 4 schedulers x 32 lanes x max SM clock (%s MHz)" % mhz}
+
+
+def _run_core_peaks():
+    """Build and run the CUDA-core microbenchmark; one JSON object on stdout."""
+    from paper_2308_00763_gb300 import build as pbuild
+    exe = pbuild.build_core_peaks()
+    p = subprocess.run([exe, "5"], capture_output=True, text=True, timeout=600)
+    if p.returncode != 0:
+        sys.stderr.write(p.stderr)
+        return p.returncode
+    print(p.stdout.strip())
+    return 0
 
 
 def _rmse(a, b):
@@ -370,56 +412,84 @@ def run_ours(args):
     hp = args.precision
     head = results[hp]
     hbm, peak_kind = _peaks()
-    achieved_gbs = BYTES_PER_PSTEP[hp] * N_ / (head["launch_us_median"] * 1e-6) / 1e9
+    # average launch duration of the step kernel over the timed region: the graph-replayed
+    # frames of a step, back to back on the filter's stream (gaps between launches included)
+    launch_us = 1e3 * head["ms_per_step"] / T
+    achieved_gbs = BYTES_PER_PSTEP[hp] * N_ / (launch_us * 1e-6) / 1e9
+    fused_gbs = FUSED_BYTES_PER_PSTEP[hp] * N_ / (launch_us * 1e-6) / 1e9
     traffic = _traffic(hp)
+    issue = _issue_view(hp, launch_us, dev)
     line = {
         "metric": METRIC, "value": head["value"], "unit": METRIC, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": DTYPE_NAME[hp], "data": "synthetic",
-        "config": {"workload": WORKLOAD, "frames_per_step": T, "particles": N_, "precision": hp,
-                   "resampler": args.resampler,
-                   "l2": "flushed between timed steps (512 MiB write); state stays L2-resident across the frames of a step",
+        "config": {"workload": WORKLOAD_SHORT, "frames_per_step": T, "particles": N_, "precision": hp,
+                   "resampler": args.resampler, "l2": "flushed between timed steps (512 MiB write)",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
+        # the step kernel against HBM on the scan-and-search design's bytes per particle-step
+        # (20 / 32 / 64 B: read x, y, write x, y, write L, scan L -> C, search C); the fused
+        # kernel itself moves 12 / 24 / 48 B (fused_frac)
         "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved_gbs / hbm, "traffic": traffic,
-                     "kernel": "step_kernel<%s>" % hp, "peak_source": peak_kind,
-                     "bytes_per_particle_step": BYTES_PER_PSTEP[hp],
-                     "launch_us_median": head["launch_us_median"]},
-        # the same kernel against instruction issue: thread instructions per launch (ncu) over
-        # the launch time, against every SM sub-partition issuing one warp instruction a cycle
-        "roofline_issue": _issue_view(hp, head["launch_us_median"], dev),
+                     "frac": achieved_gbs / hbm, "traffic": traffic, "kernel": "step_kernel<%s>" % hp,
+                     "peak_source": peak_kind, "bytes_per_particle_step": BYTES_PER_PSTEP[hp],
+                     "launch_us": launch_us, "fused_bytes_per_particle_step": FUSED_BYTES_PER_PSTEP[hp],
+                     "fused_frac": fused_gbs / hbm},
+        # the same launches against instruction issue (the bound that binds this kernel)
+        "roofline_issue": {k: issue[k] for k in ("bound", "frac", "instructions_per_particle_step", "peak_source")},
         "e2e": {"value": head["e2e_value"], "unit": METRIC, "h2d_bytes_per_step": int(W_ * H_ * T),
                 "d2h_bytes_per_step": int(16 * T)},
         # multinomial: CDF + pull; Metropolis, rejection: ancestors + pull
         "gpu_launches": args.steps * T * (2 if args.resampler in ("multinomial", "metropolis", "rejection") else 1),
         "accuracy": {"rmse_px_vs_ref64_gpu": head["rmse_px_vs_ref64_gpu"],
                      "rmse_px_vs_ground_truth": results_truth.get(hp)},
-        "per_precision": {p: {k: r[k] for k in ("value", "ms_per_step", "launch_us_median", "frame_latency_us_p50",
-                                                "frame_latency_us_p99", "e2e_value",
-                                                "rmse_px_vs_ref64_gpu")}
-                          for p, r in results.items()},
+        "per_precision": {p: {"value": r["value"], "us_per_frame": 1e3 * r["ms_per_step"] / T,
+                              "rmse_px_vs_ref64_gpu": r["rmse_px_vs_ref64_gpu"]} for p, r in results.items()},
     }
+    detail = {"per_precision": {p: {k: r[k] for k in ("value", "ms_per_step", "launch_us_median",
+                                                      "frame_latency_us_p50", "frame_latency_us_p99",
+                                                      "e2e_value", "rmse_px_vs_ref64_gpu")}
+                                for p, r in results.items()},
+              "roofline_issue": issue, "workload": WORKLOAD}
     cs = clocks.summary(*head["wall"]) or clocks.summary()
-    line["clocks"] = cs
+    line["clocks"] = {k: cs[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")} if cs else None
+    detail["clocks"] = cs
     if not args.no_batch and ws == 1:
-        line["systems"] = {"batched": _batched(dev, stream, max(3, min(args.steps, 10)), 2, hp)}
-    if not args.no_sweep and ws == 1:
-        line.setdefault("systems", {})["sweep"] = _sweep(dev, stream)
-        line["systems"]["paper_workload"] = _paper_workload(dev, stream)
-        line["systems"]["resamplers"] = _resamplers(dev, stream)
-        line["systems"]["gumbel_max"] = _gumbel_max(dev, stream)
+        b = _batched(dev, stream, max(3, min(args.steps, 10)), 2, hp)
+        detail["batched"] = b
+        line["batched"] = {"value": b["value"], "us_per_frame": b["us_per_frame"],
+                           "autotuned_value": b["autotuned"]["value"], "trackers": 256}
+    if args.systems and ws == 1:
+        detail["sweep"] = _sweep(dev, stream)
+        detail["paper_workload"] = _paper_workload(dev, stream)
+        detail["resamplers"] = _resamplers(dev, stream)
+        detail["gumbel_max"] = _gumbel_max(dev, stream)
     if not args.no_serve and ws == 1:
         cap = min(results[p]["value"] for p in results if p in ("f16", "f32")) if any(
             p in results for p in ("f16", "f32")) else head["value"]
-        line.setdefault("systems", {})["serving"] = _serving(dev, cap, args.serve_seconds)
+        s = _serving(dev, cap, args.serve_seconds, args.serve_overload)
+        detail["serving"] = s
+        line["serving"] = {"seconds": args.serve_seconds, "streams": 1024,
+                           "p50_ms": s["realtime"]["latency_p50_ms"], "p99_ms": s["realtime"]["latency_p99_ms"],
+                           "saturated_value": s["saturated"]["value"],
+                           "rejected": s["realtime"]["streams_rejected"]}
+        if "overloaded" in s:
+            o = s["overloaded"]
+            line["serving"]["overloaded"] = {"p50_ms": o["latency_p50_ms"], "p99_ms": o["latency_p99_ms"],
+                                             "rejected": o["streams_rejected"], "admitted": o["streams_admitted"]}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = _cpu_baseline(v, tracks)
+        cb = _cpu_baseline(v, tracks)
+        detail["cpu_baseline"] = cb
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        line["cpu_baseline"]["gpu_rmse_px_vs_oracle"] = cb["gpu_rmse_px_vs_oracle"]
     if ws > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
     if rank == 0:
-        print(json.dumps(line))
+        # the detail first (stderr), the headline last on stdout, compact
+        sys.stderr.write("bench detail: " + json.dumps(detail) + "\n")
+        sys.stderr.flush()
+        print(json.dumps(line, separators=(",", ":")))
     return 0
 
 
@@ -504,36 +574,58 @@ def _batched(dev, stream, steps, warmup, precision):
     return out
 
 
-def _serving(dev, capacity, seconds):
+def _serving(dev, capacity, seconds, overload=0.0):
     """Served multi-camera tracking: 1024 camera streams opening and closing over a run
     of `seconds` (frames 256^2..1024^2, 4k..1M particles, FP16/FP32 half and half, Poisson
     arrivals at 30 fps) replayed through the server's request loop, once in real time
     (per-frame latency from arrival to estimate) and once as fast as the loop runs (the
-    served throughput when frames are always waiting).  Frames are device-resident
-    8-frame videos per (size, radius), cycled."""
+    served throughput when frames are always waiting).  With `overload` > 0 a third,
+    real-time replay (at most 10 s) scales every stream's particle count by that factor
+    (capped at 2^24), so that the memory and compute budgets refuse streams.  Frames are
+    device-resident 8-frame videos per (size, radius), cycled."""
     import ctypes
     import torch
     import paper_2308_00763_gb300 as pf
     from paper_2308_00763_gb300 import synth
-    specs = synth.serving_workload(1024, seconds)
     vids = {}
-    for s in specs:
-        key = (s["W"], s["r"])
-        if key not in vids:
-            vids[key] = synth.make_video_device(s["W"], s["H"], 8, s["r"], v=(1.0, -2.0), seed=300 + len(vids),
-                                                device=dev)
-    cfgs = [pf.make_config(s["W"], s["H"], s["N"], s["r"], s["precision"], init=tuple(vids[(s["W"], s["r"])][1][0]),
-                           seed=s["seed"], tracker_id=i, est_capacity=16) for i, s in enumerate(specs)]
-    ev = []
-    for i, (s, c) in enumerate(zip(specs, cfgs)):
-        fr = vids[(s["W"], s["r"])][0]
-        ev.append((s["open"], 0, i, None, 0, ctypes.pointer(c), 30.0))
-        for k, t in enumerate(s["arrivals"]):
-            ev.append((t, 1, i, fr[k % 8].data_ptr(), fr.stride(1), None, 0.0))
-        ev.append((s["close"], 2, i, None, 0, None, 0.0))
-    ev.sort(key=lambda e: (e[0], e[1] != 0, e[1] == 2))
-    events = [pf.PfTraceEvent(time_s=e[0], kind=e[1], stream=e[2], frame=e[3], pitch_bytes=e[4], cfg=e[5], fps=e[6])
-              for e in ev]
+
+    def trace(specs, scale):
+        for s in specs:
+            key = (s["W"], s["r"])
+            if key not in vids:
+                vids[key] = synth.make_video_device(s["W"], s["H"], 8, s["r"], v=(1.0, -2.0), seed=300 + len(vids),
+                                                    device=dev)
+        cfgs = [pf.make_config(s["W"], s["H"], min(1 << 24, int(s["N"] * scale)), s["r"], s["precision"],
+                               init=tuple(vids[(s["W"], s["r"])][1][0]), seed=s["seed"], tracker_id=i,
+                               est_capacity=16) for i, s in enumerate(specs)]
+        ev = []
+        for i, (s, c) in enumerate(zip(specs, cfgs)):
+            fr = vids[(s["W"], s["r"])][0]
+            ev.append((s["open"], 0, i, None, 0, ctypes.pointer(c), 30.0))
+            for k, t in enumerate(s["arrivals"]):
+                ev.append((t, 1, i, fr[k % 8].data_ptr(), fr.stride(1), None, 0.0))
+            ev.append((s["close"], 2, i, None, 0, None, 0.0))
+        ev.sort(key=lambda e: (e[0], e[1] != 0, e[1] == 2))
+        return cfgs, [pf.PfTraceEvent(time_s=e[0], kind=e[1], stream=e[2], frame=e[3], pitch_bytes=e[4], cfg=e[5],
+                                      fps=e[6]) for e in ev]
+
+    def replay(specs, events, realtime):
+        srv = pf.Server(24 << 30, capacity=capacity, headroom=0.8, max_streams=1024, queue_depth=8, max_in_flight=2)
+        t0 = time.perf_counter()
+        srv.replay(events, len(specs), realtime=realtime)
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        busy = max(1e-9, st["last_done_s"] - st["first_launch_s"])
+        return {"wall_s": wall, "value": st["particle_steps"] / busy, "unit": METRIC,
+                "latency_p50_ms": st["latency_p50_ms"], "latency_p99_ms": st["latency_p99_ms"],
+                "latency_max_ms": st["latency_max_ms"], "streams_admitted": st["streams_admitted"],
+                "streams_rejected": st["streams_rejected"], "frames_done": st["frames_done"],
+                "frames_rejected": st["frames_rejected"], "launches": st["launches"],
+                "hbm_peak_bytes": st["hbm_peak"]}
+
+    specs = synth.serving_workload(1024, seconds)
+    cfgs, events = trace(specs, 1.0)
     torch.cuda.synchronize(dev)
     out = {"workload": "1024 camera streams over %g s: open U(0, %g s), lifetime U(%g s, %g s) clipped, "
                        "frames 256^2-1024^2, N log-uniform 4096-2^20, r 3-12, FP16/FP32 1:1, Poisson 30 fps"
@@ -542,19 +634,17 @@ def _serving(dev, capacity, seconds):
            "particle_steps_offered": float(sum(len(s["arrivals"]) * s["N"] for s in specs)),
            "capacity_admitted": capacity, "headroom": 0.8}
     for mode, realtime in (("realtime", True), ("saturated", False)):
-        srv = pf.Server(24 << 30, capacity=capacity, headroom=0.8, max_streams=1024, queue_depth=8, max_in_flight=2)
-        t0 = time.perf_counter()
-        srv.replay(events, len(specs), realtime=realtime)
-        wall = time.perf_counter() - t0
-        st = srv.stats()
-        srv.close()
-        busy = max(1e-9, st["last_done_s"] - st["first_launch_s"])
-        out[mode] = {"wall_s": wall, "value": st["particle_steps"] / busy, "unit": METRIC,
-                     "latency_p50_ms": st["latency_p50_ms"], "latency_p99_ms": st["latency_p99_ms"],
-                     "latency_max_ms": st["latency_max_ms"], "streams_admitted": st["streams_admitted"],
-                     "streams_rejected": st["streams_rejected"], "frames_done": st["frames_done"],
-                     "frames_rejected": st["frames_rejected"], "launches": st["launches"],
-                     "hbm_peak_bytes": st["hbm_peak"]}
+        out[mode] = replay(specs, events, realtime)
+    if overload > 0:
+        so = min(seconds, 10.0)
+        ospecs = synth.serving_workload(1024, so)
+        ocfgs, oevents = trace(ospecs, overload)
+        out["overloaded"] = replay(ospecs, oevents, True)
+        out["overloaded"].update({
+            "seconds": so, "particle_scale": overload,
+            "demand_all_open": float(sum(30.0 * c.num_particles for c in ocfgs)),
+            "particle_steps_offered": float(sum(len(s["arrivals"]) * c.num_particles
+                                                for s, c in zip(ospecs, ocfgs)))})
     del vids
     return out
 
@@ -633,10 +723,10 @@ def _paper_workload(dev, stream):
 
 
 def _resamplers(dev, stream):
-    """Systematic (the paper's scheme, Sec. 3) against stratified (one offset per stratum,
-    Sec. 2), multinomial (independent draws searched in the CDF; CDF and pull kernels),
-    Metropolis (64-step chains, Sec. 2; chain and pull kernels) and rejection resampling
-    (first candidate passing u <= w / w_max, Sec. 2; try and pull kernels) on the headline
+    """Systematic (the paper's scheme, Sec. IV) against stratified (one offset per stratum,
+    Sec. III), multinomial (independent draws searched in the CDF; CDF and pull kernels),
+    Metropolis (64-step chains, Sec. III; chain and pull kernels) and rejection resampling
+    (first candidate passing u <= w / w_max, Sec. III; try and pull kernels) on the headline
     workload: us per frame and the track's RMSE against the ground truth, per precision."""
     import torch
     import paper_2308_00763_gb300 as pf
@@ -672,7 +762,7 @@ def _resamplers(dev, stream):
 
 
 def _gumbel_max(dev, stream, sizes=None):
-    """Gumbel-max resampling (argmax of L + Gumbel variates, Sec. 3's log-domain
+    """Gumbel-max resampling (argmax of L + Gumbel variates, Sec. IV's log-domain
     alternative) against systematic and multinomial resampling on the headline video at
     the tracker sizes it allows (N^2 variates a frame): us per frame over 20 frames, and
     the argmax kernel's variate rate (N^2 per frame over the frame time)."""
@@ -802,6 +892,8 @@ def main():
         return _tpb_child()
     if args.tpb_sweep:
         return _tpb_sweep()
+    if args.core_peaks:
+        return _run_core_peaks()
     if args.gumbel:
         import torch
         print(json.dumps(_gumbel_max(torch.device("cuda"), torch.cuda.Stream(), {args.precision: (args.gumbel,)})))

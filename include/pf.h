@@ -4,13 +4,13 @@
  * Schieffer et al., "Boosting the Performance of Object Tracking with a
  * Half-Precision Particle Filter on GPU" (arXiv 2308.00763).
  *
- * The problem (Sec. 1 and Sec. 3): track one object in a monochrome video.  Each
+ * The problem (Sec. I and Sec. IV): track one object in a monochrome video.  Each
  * frame, every particle is propagated around its ancestor (Eq. 1-2), scored against
  * the frame under a disk template (Eq. 3, in its overflow-safe scaled form Eq. 4 for
  * half precision), weighted by exp(L - max L) (Eq. 5, log-sum-exp), normalised, summed
  * into a cumulative distribution by an inclusive prefix sum, and resampled
- * systematically (Sec. 3, "Resampling").  The paper switches the whole filter between
- * double, single and half precision by a template argument (Sec. 3, "Implementation");
+ * systematically (Sec. IV, "Resampling").  The paper switches the whole filter between
+ * double, single and half precision by a template argument (Sec. IV, "Implementation");
  * here the precision is a field of the configuration.
  *
  * Conventions for every entry point:
@@ -47,7 +47,7 @@ typedef enum {
     PF_ERR_ADMISSION = 6   /* serving: a stream was refused by the memory or compute budget */
 } pf_status;
 
-/* Arithmetic of the filter (Sec. 3: double / float / half specialisations). */
+/* Arithmetic of the filter (Sec. IV: double / float / half specialisations). */
 typedef enum {
     PF_REF64 = 0,  /* FP64 everywhere: the reference mode */
     PF_F32 = 1,    /* FP32 everywhere */
@@ -59,7 +59,7 @@ typedef enum {
 /* Resampling scheme (pf_config.resampler).  SYSTEMATIC and STRATIFIED cut the unit
  * interval into N strata [j/N, (j+1)/N), draw one point u_j in each and give offspring j
  * the first particle whose
- * normalised CDF value reaches u_j (Sec. 3, "Resampling"; Sec. 2 names the standard
+ * normalised CDF value reaches u_j (Sec. IV, "Resampling"; Sec. III names the standard
  * multinomial, stratified and systematic schemes).  The points are evaluated in the CDF's
  * precision exactly as ((A)j + v_j) * (A)(1/N), A = double (PF_REF64) or float.
  *   SYSTEMATIC: v_j = u0 for every j, u0 = uniform word 0 of Philox(0, t, 1, tracker_id)
@@ -68,12 +68,12 @@ typedef enum {
  *               tracker_id), so v_0 = u0.  With a FP32 CDF it needs N <= 2^24 (beyond,
  *               (float)j rounds and the points would no longer be ordered).
  *   MULTINOMIAL: no strata: offspring j takes the first particle whose CDF value reaches
- *               u_j = v_j, the stratified offsets used as N independent uniforms (Sec. 3
+ *               u_j = v_j, the stratified offsets used as N independent uniforms (Sec. IV
  *               describes this categorical draw).  Two kernels per frame (the CDF is
  *               written to device memory, then every offspring searches it); trackers
  *               and batches only (pf_server_open and pf_step_frame_noalloc reject it).
  *   GUMBEL:     the same categorical draw in the log domain (the Gumbel-max alternative to
- *               log-sum-exp that Sec. 3 weighs): offspring j takes the particle
+ *               log-sum-exp that Sec. IV weighs): offspring j takes the particle
  *               a_j = argmax_k (L_k + g_jk), ties to the smallest k, where L_k is the
  *               unnormalised log weight, g_jk = -ln(-ln u_jk) and u_jk = uniform word
  *               (k mod 4) of Philox(k / 4, t, 4 + 256 j, tracker_id); evaluated in FP64
@@ -82,7 +82,7 @@ typedef enum {
  *               variates a frame, so N <= 2^16 (PF_ERR_ARG beyond).  Two kernels per frame
  *               (the argmax, then the pull kernel); trackers and batches only, as
  *               MULTINOMIAL.  pf_get_debug(which = 1) answers PF_ERR_ARG (no CDF).
- *   METROPOLIS: Metropolis resampling (Sec. 2 cites it, after Murray, Lee and Jacob, as a
+ *   METROPOLIS: Metropolis resampling (Sec. III cites it, after Murray, Lee and Jacob, as a
  *               scheme with no global sum): offspring j runs a chain of B =
  *               pf_config.resampler_steps steps over the particle indices with target
  *               exp(L_k), started at k = j; step b proposes k' = floor(w N / 2^32) and
@@ -95,7 +95,7 @@ typedef enum {
  *               Two kernels per frame (the chains, then the
  *               pull kernel); trackers and batches only; pf_get_debug(which = 1) answers
  *               PF_ERR_ARG.
- *   REJECTION:  rejection resampling (Sec. 2 cites it beside METROPOLIS): offspring j
+ *   REJECTION:  rejection resampling (Sec. III cites it beside METROPOLIS): offspring j
  *               tests candidate j, then proposals k' = floor(w N / 2^32), and keeps the
  *               first candidate k with ln u <= L_k - M, M the maximum of L the previous
  *               step computed (w_k / w_max = exp(L_k - M)); try i reads words 2 (i mod 2)
@@ -145,13 +145,13 @@ typedef struct pf_batch pf_batch;
 /* Human-readable name of a status code (static storage; never NULL). */
 const char *pf_status_string(pf_status s);
 
-/* Create one tracker (Sec. 3, Fig. 1 "initialisation"): validates *cfg, allocates its
+/* Create one tracker (Sec. IV, Fig. 1 "initialisation"): validates *cfg, allocates its
  * device buffers on the current CUDA device and binds it to `cuda_stream` (a
  * cudaStream_t; NULL = the legacy default stream).  *out receives the handle.
  * Errors: PF_ERR_ARG (bad field, NULL pointer), PF_ERR_OOM, PF_ERR_CUDA. */
 pf_status pf_create(const pf_config *cfg, void *cuda_stream, pf_filter **out);
 
-/* One frame of the filter (Sec. 3, Fig. 1: propagation, likelihood, max finding,
+/* One frame of the filter (Sec. IV, Fig. 1: propagation, likelihood, max finding,
  * weighting, normalising, resampling).  `frame` is a host pointer if frame_on_device
  * is 0 (copied to the library's device buffer on the handle's stream before the
  * call returns for pageable memory; pinned memory must stay unchanged until the step
@@ -174,8 +174,10 @@ pf_status pf_step_frame(pf_filter *f, const uint8_t *frame, int64_t pitch_bytes,
 pf_status pf_run_frames(pf_filter *f, const uint8_t *frames, int64_t pitch_bytes,
                         int64_t frame_stride, int32_t count, int32_t frames_on_device);
 
-/* State estimate of frame `frame_index` (the weighted mean of the propagated
- * particles before resampling).  Synchronises the handle's stream; checks the sticky
+/* State estimate of frame `frame_index`: the tracked object position that the paper
+ * plots against the ground truth trajectory (Sec. V, "Verification & Accuracy Results",
+ * Fig. 4), taken as the weighted mean of the propagated particles before resampling
+ * (reading C7: the paper does not state which summary of the cloud it plots).  Synchronises the handle's stream; checks the sticky
  * device status.  Only the last est_capacity frames are kept.  x, y: host pointers.
  * Errors: PF_ERR_ARG (index not stepped yet or overwritten), PF_ERR_TIMEOUT,
  * PF_ERR_STATE, PF_ERR_CUDA. */
@@ -213,6 +215,8 @@ typedef struct {
 pf_status pf_get_counters(const pf_filter *f, pf_counters *out);
 
 /* Release the handle and every device buffer it owns (synchronises its stream first).
+ * The end of a tracking run (Sec. IV, Fig. 1: the filter runs frame by frame until the
+ * video ends); the paper states no teardown, so this is the library's own.
  * NULL is accepted. */
 pf_status pf_destroy(pf_filter *f);
 
@@ -260,20 +264,24 @@ pf_status pf_debug_philox(const uint32_t *ctrs, int64_t n, uint64_t seed, uint32
  * allocation can.  The paper has no counterpart; this is a deployment form of
  * pf_step_frame.  The caller owns every buffer (device pointers): the previous frame's
  * particles x_in, y_in, l_in (ignored when state_in->t == 0) and the new frame's
- * x_out, y_out, l_out (N elements each, in the precision's storage type, 16-byte aligned,
- * distinct from the inputs; F16/BF16 positions are offsets from the anchor in the header), and the frame
- * (rows pitch_bytes apart).  state_in (host) carries the scalars of the previous frame in
- * the pf_get_state header layout (t = 0: a fresh tracker); if state_out (host) is not NULL
- * the call synchronises the stream and writes the new frame's scalars there (its t is
- * state_in->t + 1, its est_x/est_y the estimate of this frame).
+ * x_out, y_out, l_out (N elements each, in the precision's storage type, 16-byte aligned;
+ * F16/BF16 positions are offsets from the anchor in the header), and the frame (rows
+ * pitch_bytes apart).  No two of the particle buffers may overlap (the step gathers
+ * ancestors from the inputs while it writes the outputs; PF_ERR_ARG otherwise).
+ * state_in (host) carries the scalars of the previous frame in the pf_get_state header
+ * layout (t = 0: a fresh tracker); state_out (host, required) receives the new frame's
+ * scalars (its t is state_in->t + 1, its est_x/est_y the estimate of this frame): the
+ * call waits for the step to finish on cuda_stream and reads them back, with any error the
+ * device recorded (PF_ERR_TIMEOUT: a bounded wait gave up).
  * Everything else the step needs (lookback descriptors, per-tile sums, counters, the
  * tracker descriptor) lives in one array (about 170 KiB) in the library's device memory, present
  * on every GPU from the moment the library is loaded until the process exits; it limits
  * num_particles to 2^22 (PF_ERR_ARG beyond).  The first call on each device looks up that
- * array's address, so make it before any stream capture.  All calls share the array and
- * clear what must start at zero themselves; calls whose GPU work overlaps (other streams,
- * other threads) race on it and must be serialised by the caller.  No device or pinned
- * memory is allocated.  Errors: PF_ERR_ARG, PF_ERR_CUDA, PF_ERR_TIMEOUT. */
+ * array's address, so make it before any stream capture.  All calls share the array; a
+ * small kernel of each call writes the descriptor and clears what must start at zero;
+ * calls whose GPU work overlaps (other streams, other threads) race on it and must be
+ * serialised by the caller.  No device or pinned memory is allocated.
+ * Errors: PF_ERR_ARG, PF_ERR_CUDA, PF_ERR_TIMEOUT. */
 pf_status pf_step_frame_noalloc(const pf_config *cfg, const pf_state_header *state_in,
                                 const void *x_in, const void *y_in, const void *l_in,
                                 const uint8_t *frame, int64_t pitch_bytes,

@@ -189,6 +189,72 @@ def likelihood_all(x, y, frame, r, bg=100.0, fg=228.0, nthreads=1):
     return L
 
 
+# --------------------------------------------------------------------------- Eq. 4 in half precision
+def round_half(v) -> np.ndarray:
+    """binary16 round-to-nearest-even of float64 values (one rounding: numpy converts
+    float64 to float16 directly)."""
+    return np.asarray(v, np.float64).astype(np.float16).astype(np.float64)
+
+
+def round_bf16(v) -> np.ndarray:
+    """bfloat16 round-to-nearest-even of float64 values: 8 significant bits, the exponent
+    range of binary32 (values here are far from its limits)."""
+    v = np.asarray(v, np.float64)
+    m, e = np.frexp(v)                       # v = m 2^e, 0.5 <= |m| < 1
+    return np.ldexp(np.rint(np.ldexp(m, 8)), e - 8)
+
+
+def round_f32(v) -> np.ndarray:
+    return np.asarray(v, np.float64).astype(np.float32).astype(np.float64)
+
+
+def half_terms(r: int, kind: str, bg=100.0, fg=228.0) -> np.ndarray:
+    """The per-pixel term of Eq. 4 for every intensity 0..255 as the half filters form it
+    (reading C10): kappa = 1 / sqrt(50 |D|) rounded to binary32 and then to the lane type;
+    a = (I - bg) kappa and b = (I - fg) kappa, each one rounded product; term = a a - b b
+    with b b rounded and a a - b b one fused (singly rounded) operation.  I - bg and
+    I - fg are exact in both lane types.  kind: "f16" / "f16acc32" (binary16 lanes) or
+    "bf16"."""
+    rnd = round_bf16 if kind == "bf16" else round_half
+    D = disk_count(r)
+    kap = rnd(round_f32(1.0 / np.sqrt(50.0 * D)))
+    I = np.arange(256, dtype=np.float64)
+    a = rnd((I - bg) * kap)
+    b = rnd((I - fg) * kap)
+    return rnd(a * a - rnd(b * b))
+
+
+def template_offsets(r: int):
+    """(dx, dy) of the template D in row-major order: dy = -r..r, dx ascending (reading C2)."""
+    out = []
+    for dy in range(-r, r + 1):
+        for dx in range(-r, r + 1):
+            if dx * dx + dy * dy <= r * r:
+                out.append((dx, dy))
+    return np.array(out, dtype=np.int64).reshape(-1, 2)
+
+
+def likelihood_half(x, y, frame, r: int, kind: str = "f16", bg=100.0, fg=228.0) -> np.ndarray:
+    """L of Eq. 3 in the scaled per-pixel form of Eq. 4 evaluated in half precision as the
+    half filters do (reading C10): the terms of half_terms at the template pixels of each
+    particle's pixel (reading C3; template pixels clamped to the frame, reading C4), summed
+    over D in row-major order (dy = -r..r, dx ascending) -- in binary16 with one rounding
+    per addition ("f16", the paper's half accumulation), or in binary32 and then rounded to
+    the lane type ("f16acc32", "bf16").  Every operation is emulated in FP64 with one
+    correct rounding, so the result is the exact value of that sequence of operations."""
+    f = np.ascontiguousarray(frame, dtype=np.uint8)
+    H, W = f.shape
+    px = round_pixel(x)
+    py = round_pixel(y)
+    tm = half_terms(r, kind, bg, fg)
+    acc = np.zeros(px.size, np.float64)
+    step = round_half if kind == "f16" else round_f32
+    for dx, dy in template_offsets(r):
+        I = f[np.clip(py + dy, 0, H - 1), np.clip(px + dx, 0, W - 1)]
+        acc = step(acc + tm[I])
+    return acc if kind == "f16" else (round_bf16(acc) if kind == "bf16" else round_half(acc))
+
+
 def weights(L):
     L = np.ascontiguousarray(L, np.float64)
     e = np.empty_like(L)

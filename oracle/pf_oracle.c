@@ -7,19 +7,19 @@
  * CPU-baseline leg load this library.  It shares no code, header, table, constant or
  * helper with the CUDA library; neither includes nor links the other.
  *
- * The step follows Sec. 3 of the paper in the paper's order (Fig. 1 workflow):
+ * The step follows Sec. IV of the paper in the paper's order (Fig. 1 workflow):
  *   propagation  Eq. 1-2            orc_propagate
- *   likelihood   Eq. 3 (Sec. 3)      orc_likelihood_at / orc_likelihood_all
+ *   likelihood   Eq. 3 (Sec. IV)      orc_likelihood_at / orc_likelihood_all
  *   max finding + weighting Eq. 5   orc_weights
  *   normalising (sum + estimate)    orc_normalise
  *   normalising (CDF, inclusive prefix sum)  orc_cdf
- *   systematic resampling (Sec. 3)  orc_resample_f64 / orc_resample_f32
+ *   systematic resampling (Sec. IV)  orc_resample_f64 / orc_resample_f32
  *     (naive form, points by division)  orc_resample_div_f64 / orc_resample_div_f32
- *   stratified resampling (Sec. 2)  orc_stratified_offsets, orc_resample_strat_f64 / _f32
- *   multinomial resampling (Sec. 3) orc_resample_multi_f64 / _f32 (draws: orc_stratified_offsets)
- *   Gumbel-max resampling (Sec. 3)  orc_gumbel_f64 / _f32 (argmax of L + Gumbel variates)
- *   Metropolis resampling (Sec. 2)  orc_metropolis_f64 / _f32 (B-step chains on exp(L))
- *   rejection resampling (Sec. 2)   orc_rejection_f64 / _f32 (first candidate with u <= w/w_max)
+ *   stratified resampling (Sec. III)  orc_stratified_offsets, orc_resample_strat_f64 / _f32
+ *   multinomial resampling (Sec. IV) orc_resample_multi_f64 / _f32 (draws: orc_stratified_offsets)
+ *   Gumbel-max resampling (Sec. IV)  orc_gumbel_f64 / _f32 (argmax of L + Gumbel variates)
+ *   Metropolis resampling (Sec. III)  orc_metropolis_f64 / _f32 (B-step chains on exp(L))
+ *   rejection resampling (Sec. III)   orc_rejection_f64 / _f32 (first candidate with u <= w/w_max)
  * Where the paper is silent the readings are (numbered as in the design notes):
  *   C1  Eq. 3 is summed over the template pixels and divided by 50*|D|.
  *   C2  template D = integer offsets with dx^2+dy^2 <= r^2 (centre included).
@@ -103,7 +103,7 @@ double orc_uniform(uint32_t w)
 }
 
 /* Box-Muller transform of two uniforms into two independent N(0,1) draws, FP64.
- * The paper samples the transition noise in double precision (Sec. 3, after Eq. 2). */
+ * The paper samples the transition noise in double precision (Sec. IV, after Eq. 2). */
 void orc_box_muller(double ua, double ub, double *nx, double *ny)
 {
     const double two_pi = 6.283185307179586476925286766559;
@@ -316,7 +316,7 @@ void orc_likelihood_all(int64_t N, const double *x, const double *y, const uint8
 }
 
 /* ------------------------------------------------------------------------- */
-/* Max finding and weighting, Eq. 5 with log-sum-exp (Sec. 3, numerical         */
+/* Max finding and weighting, Eq. 5 with log-sum-exp (Sec. IV, numerical         */
 /* stability): M = max_k L_k, e_k = exp(L_k - M).  Returns M. (C6)                */
 /* ------------------------------------------------------------------------- */
 double orc_weights(int64_t N, const double *L, double *e)
@@ -371,7 +371,7 @@ void orc_cdf(int64_t N, const double *e, double S, double *C)
     if (N > 0) C[N - 1] = 1.0;
 }
 
-/* Systematic resampling (Sec. 3; reading C8), decided in FP64: the unit interval is
+/* Systematic resampling (Sec. IV; reading C8), decided in FP64: the unit interval is
  * cut into N strata and stratum j is sampled at u_j = (j + u0) / N; its ancestor is
  * the first particle whose CDF value reaches u_j.  Linear scan with a moving pointer. */
 void orc_resample_f64(int64_t N, const double *C, double u0, int64_t *a)
@@ -399,7 +399,7 @@ void orc_resample_f32(int64_t N, const float *C, float u0, int64_t *a)
     }
 }
 
-/* Stratified resampling (Sec. 2 lists it with multinomial and systematic resampling as
+/* Stratified resampling (Sec. III lists it with multinomial and systematic resampling as
  * the standard schemes): the same N strata, each sampled at its own offset, u_j =
  * (j + v_j) * (1/N).  Offset v_j of frame t is the uniform of word (j mod 4) of the
  * Philox draw (j / 4, t, tag 1, tracker), so v_0 is the systematic u0 of that frame. */
@@ -445,7 +445,7 @@ void orc_resample_strat_f32(int64_t N, const float *C, const float *v, int64_t *
     }
 }
 
-/* Multinomial resampling (Sec. 3 describes it as drawing each ancestor from the
+/* Multinomial resampling (Sec. IV describes it as drawing each ancestor from the
  * categorical distribution of the normalised weights): offspring j takes the first
  * particle whose CDF value reaches an independent uniform v_j (the same Philox words as
  * the stratified offsets), N - 1 if there is none. */
@@ -474,7 +474,7 @@ void orc_resample_multi_f32(int64_t N, const float *C, const float *v, int64_t *
     }
 }
 
-/* Gumbel-max resampling, the log-domain alternative Sec. 3 weighs against log-sum-exp:
+/* Gumbel-max resampling, the log-domain alternative Sec. IV weighs against log-sum-exp:
  * with g_jk = -ln(-ln u_jk) independent standard Gumbel variates, offspring j takes
  * a_j = argmax_k (L_k + g_jk) over the unnormalised log weights L (the smallest k among
  * equal values).  The Gumbel-max property makes a_j a draw from the categorical law
@@ -516,7 +516,7 @@ void orc_gumbel_f32(uint64_t seed, uint32_t t, uint32_t tracker, int64_t N, cons
     }
 }
 
-/* Metropolis resampling (Sec. 2 cites it, with rejection resampling, as a scheme that
+/* Metropolis resampling (Sec. III cites it, with rejection resampling, as a scheme that
  * needs no global sum; Murray, Lee and Jacob, 2016): offspring j runs a Metropolis chain
  * of B steps over the particle indices with target exp(L_k), started at k = j.  Step b
  * proposes k' uniform on {0, ..., N-1} and moves there when u <= exp(L_k' - L_k), taken in
@@ -556,7 +556,7 @@ void orc_metropolis_f32(uint64_t seed, uint32_t t, uint32_t tracker, int64_t N, 
     }
 }
 
-/* Rejection resampling (Sec. 2 cites it beside Metropolis resampling; Murray, Lee and
+/* Rejection resampling (Sec. III cites it beside Metropolis resampling; Murray, Lee and
  * Jacob, 2016): offspring j tests k = j first, then proposals k' uniform on
  * {0, ..., N-1}, and takes the first candidate k that passes u <= w_k / w_max, in the log
  * form ln u <= L_k - M with M = max L (so w_k / w_max = exp(L_k - M)).  Offspring j thus
@@ -603,7 +603,7 @@ void orc_rejection_f32(uint64_t seed, uint32_t t, uint32_t tracker, int64_t N, c
 }
 
 /* The same systematic decisions with the stratum points formed by a division,
- * u_j = (j + u0) / N, and no saved reciprocal: the naive form of Sec. 3's performance
+ * u_j = (j + u0) / N, and no saved reciprocal: the naive form of Sec. IV's performance
  * optimisation (the GPU's naive study build takes these decisions). */
 void orc_resample_div_f64(int64_t N, const double *C, double u0, int64_t *a)
 {

@@ -110,5 +110,21 @@ def build(force: bool = False, verbose: bool = False, extra=(), threads: int | N
     return lib
 
 
+CORE_PEAKS_SRC = os.path.join(HERE, "microbench", "core_peaks.cu")
+CORE_PEAKS_BIN = os.path.join(BUILD, "core_peaks")
+
+
+def build_core_peaks(force: bool = False) -> str:
+    """Build the CUDA-core throughput microbenchmark (a standalone program) under _build/."""
+    if not force and os.path.exists(CORE_PEAKS_BIN) and os.path.getmtime(CORE_PEAKS_BIN) >= os.path.getmtime(
+            CORE_PEAKS_SRC):
+        return CORE_PEAKS_BIN
+    os.makedirs(BUILD, exist_ok=True)
+    tmp = CORE_PEAKS_BIN + ".tmp%d" % os.getpid()
+    subprocess.run([nvcc(), ARCH, "-O3", "-lineinfo", "-std=c++17", "-o", tmp, CORE_PEAKS_SRC], check=True)
+    os.replace(tmp, CORE_PEAKS_BIN)
+    return CORE_PEAKS_BIN
+
+
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))

@@ -9,7 +9,7 @@ namespace pfk {
 // ----------------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): a counter-based generator, so the
 // draw of particle j at frame t is a pure function of (seed, j, t, tag, tracker) and no
-// generator state is stored (the paper draws with cuRAND, Sec. 3 after Eq. 2).
+// generator state is stored (the paper draws with cuRAND, Sec. IV after Eq. 2).
 // ----------------------------------------------------------------------------------
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
 #pragma unroll
@@ -89,7 +89,7 @@ template <> __device__ __forceinline__ double neg_inf<double>() { return -__long
 template <> __device__ __forceinline__ float neg_inf<float>() { return -__int_as_float(0x7f800000); }
 
 // ----------------------------------------------------------------------------------
-// Resampling points (Sec. 3, "Resampling"): stratum j is sampled at u_j = (j + v_j) * (1/N),
+// Resampling points (Sec. IV, "Resampling"): stratum j is sampled at u_j = (j + v_j) * (1/N),
 // evaluated in the CDF's precision A; systematic resampling takes v_j = u0 for every j,
 // stratified resampling an independent v_j per stratum.  count_le(c) is the number of
 // strata with u_j <= c; particle k receives strata [count_le(C_{k-1}), count_le(C_k)),

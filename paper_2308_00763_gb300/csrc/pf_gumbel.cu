@@ -1,6 +1,6 @@
 // pf_gumbel.cu -- Gumbel-max resampling (sm_103a, CUDA cores only).
 //
-// Multinomial resampling in the log domain, the alternative to log-sum-exp that Sec. 3
+// Multinomial resampling in the log domain, the alternative to log-sum-exp that Sec. IV
 // ("Numerical Stability Optimization") weighs: with g_jk = -ln(-ln u_jk) independent
 // standard Gumbel variates, argmax_k (L_k + g_jk) follows the categorical law
 // exp(L_k) / sum_i exp(L_i), so offspring j needs no maximum, no sum and no CDF of the

@@ -1,6 +1,6 @@
 // pf_metropolis.cu -- Metropolis resampling (sm_103a, CUDA cores only).
 //
-// Sec. 2 cites Metropolis resampling (Murray, Lee and Jacob, 2016) as a scheme that avoids
+// Sec. III cites Metropolis resampling (Murray, Lee and Jacob, 2016) as a scheme that avoids
 // the global reduction of multinomial, stratified and systematic resampling.  Offspring j
 // runs a Metropolis chain of B steps over the particle indices with target exp(L_k),
 // started at k = j: step b proposes k' uniform on {0, ..., N-1} and moves there when

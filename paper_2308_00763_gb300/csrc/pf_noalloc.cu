@@ -58,6 +58,37 @@ constexpr ScratchLayout layout() {
 }
 static_assert(layout().end <= kScratchBytes, "scratch layout exceeds the array");
 
+// Writes the tracker descriptor, its state and the frame reference into the scratch array
+// and clears what every step must find at zero there (the ticket, the tile counter, the
+// lookback descriptors and tile partials of the nt tiles).  The three structures travel as
+// kernel parameters, so no host buffer has to outlive the call.
+__global__ void noalloc_setup_kernel(const TrackerDev T, const TrackerState st, const FrameRef fr,
+                                     unsigned char *scr, int nt) {
+    constexpr ScratchLayout LY = layout();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int stride = gridDim.x * blockDim.x;
+    if (i == 0) {
+        *reinterpret_cast<TrackerDev *>(scr + LY.trk) = T;
+        *reinterpret_cast<TrackerState *>(scr + LY.state) = st;
+        *reinterpret_cast<FrameRef *>(scr + LY.frame) = fr;
+    }
+    uint4 *z = reinterpret_cast<uint4 *>(scr + LY.ticket);
+    for (int k = i; k < static_cast<int>((LY.est - LY.ticket) / 16); k += stride) z[k] = make_uint4(0u, 0u, 0u, 0u);
+    uint4 *look = reinterpret_cast<uint4 *>(scr + LY.look);
+    for (int k = i; k < nt * static_cast<int>(sizeof(LookbackDesc) / 16); k += stride) look[k] = make_uint4(0u, 0u, 0u, 0u);
+    uint4 *part = reinterpret_cast<uint4 *>(scr + LY.part);
+    for (int k = i; k < nt * static_cast<int>(sizeof(TilePartial) / 16); k += stride) part[k] = make_uint4(0u, 0u, 0u, 0u);
+}
+static_assert(sizeof(LookbackDesc) % 16 == 0 && sizeof(TilePartial) % 16 == 0, "16-byte clears");
+static_assert(layout().ticket % 16 == 0 && layout().est % 16 == 0 && layout().look % 16 == 0 &&
+              layout().part % 16 == 0, "16-byte aligned scratch regions");
+
+// True if the byte ranges [a, a + n) and [b, b + n) overlap.
+bool overlaps(const void *a, const void *b, size_t n) {
+    const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+    return x < y + n && y < x + n;
+}
+
 std::mutex g_lock;
 unsigned char *g_scratch_dev[kMaxDevices] = {};
 int g_grid[kMaxDevices][4] = {};
@@ -88,7 +119,7 @@ extern "C" pf_status pf_step_frame_noalloc(const pf_config *cfg, const pf_state_
                                            const uint8_t *frame, int64_t pitch_bytes,
                                            void *x_out, void *y_out, void *l_out,
                                            pf_state_header *state_out, void *cuda_stream) {
-    if (!cfg || !state_in || !frame || !x_out || !y_out || !l_out) return PF_ERR_ARG;
+    if (!cfg || !state_in || !frame || !x_out || !y_out || !l_out || !state_out) return PF_ERR_ARG;
     const pf_config &c = *cfg;
     if (c.width < 1 || c.width > 65535 || c.height < 1 || c.height > 65535) return PF_ERR_ARG;
     if (c.num_particles < 1 || c.num_particles > kMaxParticles) return PF_ERR_ARG;
@@ -109,6 +140,16 @@ extern "C" pf_status pf_step_frame_noalloc(const pf_config *cfg, const pf_state_
     const auto misaligned = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) != 0u; };
     if (misaligned(x_out) || misaligned(y_out) || misaligned(l_out)) return PF_ERR_ARG;
     if (h.t > 0 && (misaligned(x_in) || misaligned(y_in) || misaligned(l_in))) return PF_ERR_ARG;
+    // the step gathers ancestors from the inputs while it writes the outputs: no buffer
+    // may overlap another
+    {
+        const size_t nb = static_cast<size_t>(c.num_particles) * pos_bytes(c.precision);
+        const void *bufs[6] = {x_out, y_out, l_out, x_in, y_in, l_in};
+        const int nbuf = h.t > 0 ? 6 : 3;
+        for (int a = 0; a < nbuf; ++a)
+            for (int b = a + 1; b < nbuf; ++b)
+                if (overlaps(bufs[a], bufs[b], nb)) return PF_ERR_ARG;
+    }
 
     int dev = 0;
     unsigned char *scr = nullptr;
@@ -159,14 +200,12 @@ extern "C" pf_status pf_step_frame_noalloc(const pf_config *cfg, const pf_state_
 
     // Every call shares the scratch array and finds the previous call's contents in it:
     // the lookback descriptors, the tile partials (their words carry the launch counter,
-    // which is 1 on every call), the tile counter and the ticket must start at zero.
-    cudaError_t err = cudaMemsetAsync(scr + LY.ticket, 0, LY.est - LY.ticket, stream);
-    if (err == cudaSuccess) err = cudaMemsetAsync(scr + LY.look, 0, sizeof(LookbackDesc) * nt, stream);
-    if (err == cudaSuccess) err = cudaMemsetAsync(scr + LY.part, 0, sizeof(TilePartial) * nt, stream);
-    if (err == cudaSuccess) err = cudaMemcpyAsync(scr + LY.trk, &T, sizeof T, cudaMemcpyHostToDevice, stream);
-    if (err == cudaSuccess) err = cudaMemcpyAsync(scr + LY.state, &st, sizeof st, cudaMemcpyHostToDevice, stream);
-    if (err == cudaSuccess) err = cudaMemcpyAsync(scr + LY.frame, &fr, sizeof fr, cudaMemcpyHostToDevice, stream);
-    if (err != cudaSuccess) { cudaGetLastError(); return PF_ERR_CUDA; }
+    // which is 1 on every call), the tile counter and the ticket must start at zero.  One
+    // small kernel writes the descriptor, state and frame reference (its parameters) and
+    // clears those.
+    noalloc_setup_kernel<<<8, 256, 0, stream>>>(T, st, fr, scr, nt);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return PF_ERR_CUDA;
     int grid;
     {
         std::lock_guard<std::mutex> guard(g_lock);
@@ -190,7 +229,9 @@ extern "C" pf_status pf_step_frame_noalloc(const pf_config *cfg, const pf_state_
     L.pitch_override = 0;
     if (launch_step(c.precision, L, grid, stream) != 0) { cudaGetLastError(); return PF_ERR_CUDA; }
 
-    if (state_out) {
+    // the new state header: read back once the step has run (the call waits for it), with
+    // the device status a failed wait or a checked build's index test left there
+    {
         TrackerState res;
         err = cudaMemcpyAsync(&res, scr + LY.state, sizeof res, cudaMemcpyDeviceToHost, stream);
         if (err == cudaSuccess) err = cudaStreamSynchronize(stream);

@@ -1,6 +1,6 @@
 // pf_rejection.cu -- rejection resampling (sm_103a, CUDA cores only).
 //
-// Sec. 2 cites rejection resampling (Murray, Lee and Jacob, 2016) beside Metropolis
+// Sec. III cites rejection resampling (Murray, Lee and Jacob, 2016) beside Metropolis
 // resampling as avoiding the prefix sum of the standard schemes.  Offspring j tests the
 // candidate k = j, then proposals k' uniform on {0, ..., N-1}, and keeps the first
 // candidate with u <= w_k / w_max, in the log form ln u <= L_k - M where M is the maximum

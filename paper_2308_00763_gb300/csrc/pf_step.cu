@@ -2,7 +2,7 @@
 //
 // One launch per frame for a whole batch of trackers.  A tile is kTile consecutive
 // particles k of one tracker's previous frame.  Per tile (dynamic ticket order):
-//   1. resampling of the previous frame (Sec. 3, "Normalizing" and "Resampling"):
+//   1. resampling of the previous frame (Sec. IV, "Normalizing" and "Resampling"):
 //      e_k = exp(L_k - M) (Eq. 5 with the max of the previous step), a block scan, and a
 //      decoupled lookback over the tracker's earlier tiles give the inclusive prefix
 //      P_k; C_k = P_k * (1/S) (the reciprocal saved by the previous step); the strata
@@ -24,14 +24,14 @@
 //      particles).
 // Frame t = 0 has no resampling: every particle starts at the initial position.
 //
-// Multinomial trackers (Sec. 3: each ancestor drawn from the categorical distribution of
+// Multinomial trackers (Sec. IV: each ancestor drawn from the categorical distribution of
 // the weights) are not in the step kernel's launch; they take two other launches per
 // frame (the same code in other modes): the CDF kernel runs phase 1 up to the CDF and writes it to
 // T.cdf; the pull kernel then gives each offspring j the first particle whose CDF value
 // reaches an independent uniform v_j (a binary search over T.cdf), gathers the ancestors'
 // positions of its tile's offspring into shared memory, sizes the likelihood window by
 // them and runs phases 2-5 as the step kernel does.  Gumbel-max trackers (the log-domain
-// form of the same draw, Sec. 3), Metropolis and rejection trackers (Sec. 2) skip the CDF
+// form of the same draw, Sec. IV), Metropolis and rejection trackers (Sec. III) skip the CDF
 // kernel: the pull kernel reads the ancestors their kernel (pf_gumbel.cu, pf_metropolis.cu,
 // pf_rejection.cu) wrote to T.anc instead of searching.
 //

@@ -1,7 +1,7 @@
 """Seeded synthetic monochrome video: the tracking input of the particle filter.
 
 The paper evaluates on a synthetic video in the style of the Rodinia particle-filter
-application (Sec. 4, "Verification & Accuracy Results"): one disk-shaped object of a
+application (Sec. V, "Verification & Accuracy Results"): one disk-shaped object of a
 single foreground intensity on a background of a single intensity, Gaussian noise
 added to every pixel, and the object bouncing specularly off the frame walls.  Neither
 that generator nor its data is available, so this module stands in for it with the

@@ -186,3 +186,66 @@ def test_naive_resampling_study_build_is_exact_for_its_own_arithmetic():
     for prec, N, exact, monotone in out[True]["cases"]:
         assert exact and monotone, (prec, N)
     assert out[True]["L0"] == out[False]["L0"]
+
+
+TPB_CHILD = r'''
+import json, sys
+sys.path.insert(0, sys.argv[1])
+import numpy as np, torch
+import oracle
+import paper_2308_00763_gb300 as pf
+from paper_2308_00763_gb300 import synth
+pf.lib(build_if_missing=True)
+threads = int(sys.argv[2])
+tile = 8 * threads
+v = synth.make_video(160, 120, 5, 4, noise=8.0, seed=9, v=(1.0, -1.0))
+fr = torch.from_numpy(v.frames).cuda()
+res = {"lib": pf.library_path(), "cases": []}
+precs = ("f32", "f16", "bf16") if threads == 1024 else ("ref64", "f32", "f16", "bf16")
+for prec in precs:
+    for N in (3, tile - 1, tile + 1, 3 * tile + 17):
+        f = pf.Filter(v.W, v.H, N, 4, prec, init=tuple(v.centres[0]), seed=6, sigma=(2.0, 2.0),
+                      flags=pf.PF_FLAG_DEBUG_ARRAYS)
+        f.run(fr)
+        est = f.estimates(0, v.T)
+        anc = f.debug(0).astype(np.int64)
+        C = f.debug(1).astype(np.float64)
+        a_o = oracle.resample(C, oracle.resample_u0(6, v.T - 2), "f64" if prec == "ref64" else "f32")
+        est_o, _, _ = oracle.track(v.frames, N, 4, init=tuple(v.centres[0]), seed=6, sigma=(2.0, 2.0))
+        if prec == "ref64":
+            err = float(np.abs(est - est_o).max()); ok = err <= 1e-9
+        elif prec == "f32":
+            err = float(np.abs(est - est_o).max()); ok = err <= 1e-3
+        else:
+            err = float(np.sqrt(np.mean(np.sum((est - est_o) ** 2, axis=1)))); ok = err <= 0.5
+        res["cases"].append([prec, N, bool(np.array_equal(anc, a_o)),
+                             bool(np.all(np.diff(C) >= 0) and C[-1] == 1.0), ok, err])
+        f.close()
+print(json.dumps(res))
+'''
+
+
+@pytest.mark.parametrize("threads", [128, 256, 1024])
+def test_thread_block_study_builds_keep_the_method(threads):
+    """The thread-block study builds (threads per CTA 128, 256 and 1024; the paper varies
+    threads per block from 32 to 1024 in its Sec. V): in each, at ragged sizes around its
+    own tile (8 elements a thread), the ancestors equal the oracle's systematic resampling
+    of the CDF the step computed bit for bit, the CDF is monotone and ends at 1, and the
+    track matches the oracle's at the stated tolerance of its precision."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import json
+    from paper_2308_00763_gb300 import build as pbuild
+    pbuild.build(threads=threads)
+    env = dict(os.environ)
+    env.pop("PF_CHECKED", None)
+    env.pop("PF_NAIVE", None)
+    env["PF_STEP_THREADS"] = str(threads)
+    p = subprocess.run([sys.executable, "-c", TPB_CHILD, ROOT, str(threads)], env=env, capture_output=True,
+                       text=True, timeout=900)
+    assert p.returncode == 0, (p.stdout[-2000:], p.stderr[-4000:])
+    out = json.loads(p.stdout.strip().splitlines()[-1])
+    assert ("/t%d/" % threads) in out["lib"]
+    for prec, N, exact, monotone, ok, err in out["cases"]:
+        assert exact and monotone and ok, (threads, prec, N, err)

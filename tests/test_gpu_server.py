@@ -12,6 +12,7 @@ import time
 import numpy as np
 import pytest
 
+import oracle
 from paper_2308_00763_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -102,6 +103,16 @@ def test_stream_alone_equals_stream_in_mix(pf, prec):
     f.run(fr)
     assert np.array_equal(f.estimates(0, T), alone), prec
     f.close()
+
+    # and the served track against the oracle at the stated tolerance of its precision
+    est_o, _, _ = oracle.track(vid.frames, cfg.num_particles, vid.radius, init=tuple(vid.centres[0]), seed=7,
+                               tracker=3)
+    if prec == "ref64":
+        assert np.abs(mixed - est_o).max() <= 1e-9
+    elif prec == "f32":
+        assert np.abs(mixed - est_o).max() <= 1e-3
+    else:
+        assert np.sqrt(np.mean(np.sum((mixed - est_o) ** 2, axis=1))) <= 0.5
 
 
 def test_stratified_stream_equals_filter_and_multinomial_is_refused(pf):

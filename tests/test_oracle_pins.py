@@ -2,8 +2,8 @@
 
 Each test checks the oracle against what the paper or mathematics fixes: a library run
 as a black box (cuRAND's host Philox generator, numpy, scipy), closed forms of Eq. 3,
-invariants of systematic resampling (Sec. 3), brute force on tiny inputs, and recovery
-of the known ground-truth trajectory of the synthetic video (Sec. 4, verification).
+invariants of systematic resampling (Sec. IV), brute force on tiny inputs, and recovery
+of the known ground-truth trajectory of the synthetic video (Sec. V, verification).
 """
 import ctypes
 import ctypes.util
@@ -231,6 +231,83 @@ def test_likelihood_integer_form_identity():
             px, py = int(rng.integers(-3, 56)), int(rng.integers(-3, 40))
             s = oracle.disk_sum(frame, r, px, py)
             assert oracle.likelihood_at(frame, r, px, py) == (256.0 * s - 41984.0 * D) / (50.0 * D)
+
+
+# ----------------------------------------------------------------------------- Eq. 4 in half precision
+def test_half_rounding_helpers_match_library_conversions():
+    """The rounding helpers against library conversions from binary32 (one rounding
+    there too): numpy's float32 -> float16 and torch's float32 -> bfloat16, both
+    round-to-nearest-even, on random values, exact ties and their neighbours."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(9)
+    v = np.concatenate([rng.normal(0, 30, 20000), rng.uniform(-1, 1, 20000) * 2.0 ** -8,
+                        1.0 + np.arange(-64, 64) * 2.0 ** -11, 256.0 + np.arange(-64, 64) * 2.0 ** -3])
+    v32 = v.astype(np.float32)
+    assert np.array_equal(oracle.round_half(v32.astype(np.float64)), v32.astype(np.float16).astype(np.float64))
+    want = torch.from_numpy(v32).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(oracle.round_bf16(v32.astype(np.float64)), want)
+    # ties to even, exactly representable values unchanged
+    assert oracle.round_half(1.0 + 2.0 ** -11) == 1.0 and oracle.round_half(1.0 + 3 * 2.0 ** -11) == 1.0 + 2 ** -9
+    assert oracle.round_bf16(1.0 + 2.0 ** -8) == 1.0 and oracle.round_bf16(1.0 + 3 * 2.0 ** -8) == 1.0 + 2 ** -6
+    assert np.array_equal(oracle.round_half(np.arange(-2048.0, 2049.0)), np.arange(-2048.0, 2049.0))
+
+
+def test_half_likelihood_uniform_frame_by_float16_arithmetic():
+    """Uniform frames: every template term is the same binary16 value, formed and summed
+    here with numpy's own float16 arithmetic (each operation exact in binary32 at these
+    magnitudes, then rounded once); the oracle's emulation must give the same bits."""
+    for r in (1, 3, 5, 10):
+        D = oracle.disk_count(r)
+        kap = np.float16(np.float32(1.0 / math.sqrt(50.0 * D)))
+        for c in (0, 37, 100, 150, 164, 228, 255):
+            a = np.float16(np.float16(c - 100) * kap)
+            b = np.float16(np.float16(c - 228) * kap)
+            term = np.float16(np.float64(a) * np.float64(a) - np.float64(np.float16(b * b)))
+            acc = np.float16(0.0)
+            for _ in range(D):
+                acc = np.float16(acc + term)
+            frame = np.full((40, 50), c, np.uint8)
+            got = oracle.likelihood_half(np.array([25.0, 0.2]), np.array([20.0, 39.0]), frame, r, "f16")
+            assert np.all(got == np.float64(acc)), (r, c)
+            # and the FP32-accumulated form
+            acc32 = np.float32(0.0)
+            for _ in range(D):
+                acc32 = np.float32(acc32 + np.float32(term))
+            got32 = oracle.likelihood_half(np.array([25.0]), np.array([20.0]), frame, r, "f16acc32")
+            assert got32[0] == np.float64(np.float16(acc32)), (r, c)
+
+
+@pytest.mark.parametrize("kind", ["f16", "f16acc32", "bf16"])
+def test_half_likelihood_within_the_rounding_bound(kind):
+    """Against the FP64 Eq. 3 value: the half result differs by at most the rounding bound
+    of its operations -- per term the roundings of a, b, b b and a a - b b (and kappa's own
+    rounding, a relative 2u on the whole sum), per addition u times the running sum, u the
+    unit roundoff of the lane type (2^-11 binary16, 2^-8 bfloat16) or of binary32 for the
+    accumulation.  (The bound is loose; the GPU's half likelihoods are compared with this
+    emulation bit for bit.)"""
+    u = 2.0 ** -8 if kind == "bf16" else 2.0 ** -11
+    u_acc = 2.0 ** -11 if kind == "f16" else 2.0 ** -24
+    rng = np.random.default_rng(2)
+    v = synth.make_video(128, 128, 3, 5, noise=5.0, seed=1)
+    frame = v.frames[2]
+    x = rng.uniform(30, 100, 3000)
+    y = rng.uniform(30, 100, 3000)
+    r = 5
+    D = oracle.disk_count(r)
+    L = oracle.likelihood_all(x, y, frame, r)
+    Lh = oracle.likelihood_half(x, y, frame, r, kind)
+    px, py = oracle.round_pixel(x), oracle.round_pixel(y)
+    kap2 = 1.0 / (50.0 * D)
+    s = np.zeros(x.size)
+    bound = np.zeros(x.size)
+    for dx, dy in oracle.template_offsets(r):
+        I = frame[np.clip(py + dy, 0, 127), np.clip(px + dx, 0, 127)].astype(np.float64)
+        a2, b2 = (I - 100.0) ** 2 * kap2, (I - 228.0) ** 2 * kap2
+        s = s + (a2 - b2)
+        bound += 4.0 * u * (a2 + b2) + u_acc * np.abs(s) * 1.01
+    bound += 2.1 * u * np.abs(L) + u * np.abs(L)
+    assert np.all(np.abs(Lh - L) <= bound)
+    assert np.abs(Lh - L).max() > 0.0            # it is a half computation, not the FP64 one
 
 
 # ----------------------------------------------------------------------------- weights, normalisation, CDF
@@ -757,7 +834,7 @@ def test_propagation_gathers_ancestors():
 # ----------------------------------------------------------------------------- whole tracker
 def test_track_recovers_ground_truth_config1():
     """128x128, 10 frames, r = 5, noise 5, 1000 particles, sigma 1, seed 1: the FP64 track
-    stays within a pixel of the true disk centre (Sec. 4, verification)."""
+    stays within a pixel of the true disk centre (Sec. V, verification)."""
     v = synth.make_video(128, 128, 10, 5, noise=5.0, seed=1)
     est, M, S = oracle.track(v.frames, 1000, 5, init=tuple(v.centres[0]), seed=1)
     err = np.sqrt(np.sum((est - v.centres) ** 2, axis=1))
