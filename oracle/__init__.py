@@ -237,11 +237,12 @@ def template_offsets(r: int):
 def likelihood_half(x, y, frame, r: int, kind: str = "f16", bg=100.0, fg=228.0) -> np.ndarray:
     """L of Eq. 3 in the scaled per-pixel form of Eq. 4 evaluated in half precision as the
     half filters do (reading C10): the terms of half_terms at the template pixels of each
-    particle's pixel (reading C3; template pixels clamped to the frame, reading C4), summed
-    over D in row-major order (dy = -r..r, dx ascending) -- in binary16 with one rounding
-    per addition ("f16", the paper's half accumulation), or in binary32 and then rounded to
-    the lane type ("f16acc32", "bf16").  Every operation is emulated in FP64 with one
-    correct rounding, so the result is the exact value of that sequence of operations."""
+    particle's pixel (reading C3; template pixels clamped to the frame, reading C4); each
+    template row (dy = -r..r) summed left to right (dx ascending), then the row sums added
+    top to bottom -- in binary16 with one rounding per addition ("f16", the paper's half
+    accumulation), or in binary32 and then rounded to the lane type ("f16acc32", "bf16").
+    Every operation is emulated in FP64 with one correct rounding, so the result is the
+    exact value of that sequence of operations."""
     f = np.ascontiguousarray(frame, dtype=np.uint8)
     H, W = f.shape
     px = round_pixel(x)
@@ -249,9 +250,13 @@ def likelihood_half(x, y, frame, r: int, kind: str = "f16", bg=100.0, fg=228.0) 
     tm = half_terms(r, kind, bg, fg)
     acc = np.zeros(px.size, np.float64)
     step = round_half if kind == "f16" else round_f32
-    for dx, dy in template_offsets(r):
-        I = f[np.clip(py + dy, 0, H - 1), np.clip(px + dx, 0, W - 1)]
-        acc = step(acc + tm[I])
+    offs = template_offsets(r)
+    for dy in range(-r, r + 1):
+        row = np.zeros(px.size, np.float64)
+        for dx in offs[offs[:, 1] == dy, 0]:
+            I = f[np.clip(py + dy, 0, H - 1), np.clip(px + dx, 0, W - 1)]
+            row = step(row + tm[I])
+        acc = step(acc + row)
     return acc if kind == "f16" else (round_bf16(acc) if kind == "bf16" else round_half(acc))
 
 

@@ -123,8 +123,17 @@ inline TrackerState initial_state(const pf_config &c) {
     s.ay = s.ny = round_half_up(c.init_y);
     s.est_x = c.init_x;
     s.est_y = c.init_y;
+    // every particle starts at the initial position
+    s.bb_x0 = s.bb_x1 = static_cast<float>(c.init_x);
+    s.bb_y0 = s.bb_y1 = static_cast<float>(c.init_y);
     state_copies(s);
     return s;
+}
+
+// Mark the bounding box of the stored positions unknown (the next step builds its
+// likelihood tables per tile).
+inline void bbox_unknown(TrackerState &s) {
+    s.bb_x0 = s.bb_x1 = s.bb_y0 = s.bb_y1 = nanf("");
 }
 
 }  // namespace pfk

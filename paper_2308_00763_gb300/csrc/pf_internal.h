@@ -25,6 +25,9 @@ static_assert(kThreads == 128 || kThreads == 256 || kThreads == 512 || kThreads 
 constexpr int kItems = 8;                 // CDF elements per thread
 constexpr int kTile = kThreads * kItems;  // largest tile (particles of the resampled frame)
 constexpr int kMaxRadius = 64;
+// Pixels of a likelihood table (a tile's table in shared memory, and a tracker's table in
+// device memory, which tiles copy into theirs).
+constexpr int kTableMax = kTile < 4096 ? kTile : 4096;
 
 // Resampling schemes (pf_config.resampler).
 constexpr int kResampleSystematic = 0;
@@ -71,6 +74,9 @@ struct alignas(16) TilePartial {
         double d[4];
         uint64_t w[4];
     };
+    // bounding box of the tile's new positions (x0, x1, y0, y1, absolute pixel units): four
+    // tagged words (tag << 32 | float bits), as the FP32 statistics
+    uint64_t b[4];
 };
 
 struct alignas(16) TrackerState {
@@ -86,6 +92,9 @@ struct alignas(16) TrackerState {
     // the same scalars for the FP32 kernels (no FP64 instruction on their path)
     float M_f, invS_f;
     int32_t axi, ayi, nxi, nyi;
+    // bounding box of the stored positions (frame t-1; absolute pixel units), which sizes
+    // the tracker's likelihood table of the next step; NaN when unknown
+    float bb_x0, bb_x1, bb_y0, bb_y1;
 };
 
 struct FrameRef {
@@ -123,6 +132,10 @@ struct TrackerDev {
     int32_t *anc;              // Gumbel-max, Metropolis, rejection: the ancestor of every offspring [N]
     LookbackDesc *look;
     TilePartial *part;
+    // The tracker's likelihood table of the current step, kTableMax cells of one 64-bit word
+    // (launch tag << 32 | payload: the integer disk sum of Eq. 3, or the bits of the half
+    // form of Eq. 4); null = every tile builds its own table.
+    uint64_t *gtab;
     uint32_t *done;
     TrackerState *state;
     double *est_ring;          // [est_cap][2]

@@ -193,6 +193,7 @@ extern "C" pf_status pf_step_frame_noalloc(const pf_config *cfg, const pf_state_
         st.est_x = h.est_x; st.est_y = h.est_y;
     }
     st.invS = c.precision == PF_REF64 ? 1.0 / st.S : static_cast<double>(1.0f / static_cast<float>(st.S));
+    bbox_unknown(st);   // (no tracker table here: every tile tabulates its own window)
     state_copies(st);
     FrameRef fr;
     memset(&fr, 0, sizeof fr);

@@ -1,6 +1,7 @@
 // pf_runtime.cu -- host runtime behind the C ABI of include/pf.h: handles, device
 // buffers, frame staging, launches, estimates, checkpoints.
 #include <cuda_runtime.h>
+#include <stdint.h>
 #include <math.h>
 #include <stdlib.h>
 #include <stddef.h>
@@ -201,7 +202,7 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
     const size_t pb = pos_bytes(e.prec);
     const size_t cdf_b = e.prec == PF_REF64 ? 8 : 4;
     Arena a;
-    struct Off { size_t px[2], py[2], pl[2], look, part, done, state, est, stat, dbga, dbgc, cdf; };
+    struct Off { size_t px[2], py[2], pl[2], look, part, done, state, est, stat, dbga, dbgc, cdf, gtab; };
     std::vector<Off> off(n);
     // the trackers' states form one array (the kernel indexes it by tracker)
     const size_t states_off = a.take(sizeof(TrackerState) * n);
@@ -231,6 +232,10 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
         o.look = a.take(sizeof(LookbackDesc) * nt);
         o.part = a.take(sizeof(TilePartial) * nt);
         o.done = a.take(sizeof(uint32_t));
+        // the tracker's likelihood table (step-family trackers of two or more tiles)
+        o.gtab = SIZE_MAX;
+        if (nt >= 2 && !(c.resampler == PF_RESAMPLE_MULTINOMIAL || ancestors_given(c.resampler)))
+            o.gtab = a.take(sizeof(uint64_t) * kTableMax);
         o.state = states_off + sizeof(TrackerState) * i;
         o.est = a.take(sizeof(double) * 2 * cap);
         o.stat = a.take(sizeof(double) * 2 * cap);
@@ -305,6 +310,7 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
         T.look = reinterpret_cast<LookbackDesc *>(e.d_arena + o.look);
         T.part = reinterpret_cast<TilePartial *>(e.d_arena + o.part);
         T.done = reinterpret_cast<uint32_t *>(e.d_arena + o.done);
+        T.gtab = o.gtab == SIZE_MAX ? nullptr : reinterpret_cast<uint64_t *>(e.d_arena + o.gtab);
         T.state = reinterpret_cast<TrackerState *>(e.d_arena + o.state);
         T.est_ring = reinterpret_cast<double *>(e.d_arena + o.est);
         T.stat_ring = reinterpret_cast<double *>(e.d_arena + o.stat);
@@ -808,6 +814,7 @@ pf_status pf_set_state(pf_filter *f, const void *host_buf, size_t bytes) {
     st.ny = h.next_anchor_y;
     st.est_x = h.est_x;
     st.est_y = h.est_y;
+    bbox_unknown(st);   // the next step tabulates the likelihood per tile
     state_copies(st);
     const char *p = static_cast<const char *>(host_buf) + sizeof h;
     const int slot = static_cast<int>((h.t + 1) & 1);

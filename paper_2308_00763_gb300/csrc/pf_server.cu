@@ -80,7 +80,7 @@ private:
 
 // Pieces of a stream's arena block (offsets from the block start).
 struct StreamLayout {
-    size_t px[2], py[2], pl[2], look, part, done, est, stat, ring, total;
+    size_t px[2], py[2], pl[2], look, part, gtab, done, est, stat, ring, total;
     int64_t ring_pitch;
     int ntiles, tile;
 };
@@ -100,6 +100,9 @@ StreamLayout stream_layout(const pf_config &c, bool host_frames, int queue_depth
     }
     L.look = take(sizeof(LookbackDesc) * L.ntiles);
     L.part = take(sizeof(TilePartial) * L.ntiles);
+    // the stream's likelihood table (streams of two or more tiles; cleared with the
+    // descriptors when a stream opens, so no tag of an earlier stream in the slot survives)
+    L.gtab = L.ntiles >= 2 ? take(sizeof(uint64_t) * kTableMax) : SIZE_MAX;
     L.done = take(sizeof(uint32_t));
     L.est = take(sizeof(double) * 2 * 2);
     L.stat = take(sizeof(double) * 2 * 2);
@@ -446,6 +449,7 @@ pf_status pf_server_open(pf_server *S, const pf_config *cfg, double fps, int32_t
     T.look = reinterpret_cast<LookbackDesc *>(base + lay.look);
     T.part = reinterpret_cast<TilePartial *>(base + lay.part);
     T.done = reinterpret_cast<uint32_t *>(base + lay.done);
+    T.gtab = lay.gtab == SIZE_MAX ? nullptr : reinterpret_cast<uint64_t *>(base + lay.gtab);
     T.state = e.d_states + slot;
     T.est_ring = reinterpret_cast<double *>(base + lay.est);
     T.stat_ring = reinterpret_cast<double *>(base + lay.stat);

@@ -61,10 +61,8 @@ namespace pfk {
 namespace {
 
 constexpr int kWarps = kThreads / 32;
-constexpr int kTableMax = kTile < 4096 ? kTile : 4096;   // pixels of the per-tile likelihood table
 constexpr int kRoiMax = 2 * kTableMax;     // staged frame pixels (window + template margin)
 constexpr int kMapMax = 2 * kTile;         // offspring of a tile served by the ancestor map
-constexpr int kOffMax = 1024;              // template entries served by the offset list (r <= 17)
 constexpr uint32_t kSpinLimit = 1u << 22;  // bounded waits: ~1 s with backoff
 // Half-width of the likelihood window in standard deviations of the transition noise.
 // Every draw is below sqrt(-2 ln 2^-24) = 5.77 in magnitude (kDrawMax, rounded up).  When
@@ -181,16 +179,21 @@ __device__ __forceinline__ uint64_t partial_tag(uint32_t ep) {   // never 0 (cle
     return static_cast<uint64_t>(ep % 0x7fffffffu + 1u) << 32;
 }
 
-// Wait (bounded) until the four words of a tile partial carry this launch's tag; on
-// timeout the tracker's timeout bit is raised and the words read last are returned.
-__device__ void wait_partial(const TilePartial *p, uint64_t tag, TrackerState *st, uint64_t (&q)[4],
+// Wait (bounded) until the eight words of a tile partial (statistics, then bounding box)
+// carry this launch's tag; on timeout the tracker's timeout bit is raised and the words read
+// last are returned.
+__device__ void wait_partial(const TilePartial *p, uint64_t tag, TrackerState *st, uint64_t (&q)[8],
                              uint32_t limit = kSpinLimit) {
     uint32_t ns = 8;
     const uint64_t hm = 0xffffffff00000000ull;
     for (uint32_t it = 0; it < limit; ++it) {
         ld_relaxed_v2(&p->w[0], q[0], q[1]);
         ld_relaxed_v2(&p->w[2], q[2], q[3]);
-        if ((q[0] & hm) == tag && (q[1] & hm) == tag && (q[2] & hm) == tag && (q[3] & hm) == tag) return;
+        ld_relaxed_v2(&p->b[0], q[4], q[5]);
+        ld_relaxed_v2(&p->b[2], q[6], q[7]);
+        if ((q[0] & hm) == tag && (q[1] & hm) == tag && (q[2] & hm) == tag && (q[3] & hm) == tag &&
+            (q[4] & hm) == tag && (q[5] & hm) == tag && (q[6] & hm) == tag && (q[7] & hm) == tag)
+            return;
         if ((it & 1023u) == 1023u && timed_out(st)) return;
         __nanosleep(ns);
         if (ns < 256) ns <<= 1;
@@ -264,26 +267,95 @@ __device__ __forceinline__ int pixel_of(double v) {
 }
 
 // kItems consecutive elements between memory and registers as 16-byte vectors (kItems *
-// sizeof(T) is a multiple of 16 for every element type here; the address is 16-byte aligned).
+// sizeof(T) is a multiple of 16 for every element type here; the address is 16-byte
+// aligned).  The elements are unpacked from (packed into) the vector words with bit
+// operations on constant indices, so the register arrays never need an address (an
+// array whose address is taken lives in local memory).
+__device__ __forceinline__ uint32_t vword(const uint4 &v, int k) {
+    return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
+}
+__device__ __forceinline__ void set_vword(uint4 &v, int k, uint32_t w) {
+    if (k == 0) v.x = w; else if (k == 1) v.y = w; else if (k == 2) v.z = w; else v.w = w;
+}
+template <typename T> struct Bits;
+template <> struct Bits<double> {
+    __device__ static __forceinline__ double get(const uint4 *v, int m) {
+        return __hiloint2double(static_cast<int>(vword(v[m >> 1], 2 * (m & 1) + 1)),
+                                static_cast<int>(vword(v[m >> 1], 2 * (m & 1))));
+    }
+    __device__ static __forceinline__ void put(uint4 *v, int m, double x) {
+        set_vword(v[m >> 1], 2 * (m & 1), static_cast<uint32_t>(__double2loint(x)));
+        set_vword(v[m >> 1], 2 * (m & 1) + 1, static_cast<uint32_t>(__double2hiint(x)));
+    }
+};
+template <> struct Bits<float> {
+    __device__ static __forceinline__ float get(const uint4 *v, int m) { return __uint_as_float(vword(v[m >> 2], m & 3)); }
+    __device__ static __forceinline__ void put(uint4 *v, int m, float x) { set_vword(v[m >> 2], m & 3, __float_as_uint(x)); }
+};
+template <> struct Bits<int32_t> {
+    __device__ static __forceinline__ int32_t get(const uint4 *v, int m) { return static_cast<int32_t>(vword(v[m >> 2], m & 3)); }
+    __device__ static __forceinline__ void put(uint4 *v, int m, int32_t x) { set_vword(v[m >> 2], m & 3, static_cast<uint32_t>(x)); }
+};
+template <> struct Bits<__half> {
+    __device__ static __forceinline__ __half get(const uint4 *v, int m) {
+        const uint32_t w = vword(v[m >> 3], (m >> 1) & 3);
+        return __ushort_as_half(static_cast<unsigned short>((m & 1) ? (w >> 16) : (w & 0xffffu)));
+    }
+    __device__ static __forceinline__ void put(uint4 *v, int m, __half x) {
+        const uint32_t h = __half_as_ushort(x);
+        uint32_t w = vword(v[m >> 3], (m >> 1) & 3);
+        w = (m & 1) ? ((w & 0xffffu) | (h << 16)) : ((w & 0xffff0000u) | h);
+        set_vword(v[m >> 3], (m >> 1) & 3, w);
+    }
+};
+template <> struct Bits<__nv_bfloat16> {
+    __device__ static __forceinline__ __nv_bfloat16 get(const uint4 *v, int m) {
+        const uint32_t w = vword(v[m >> 3], (m >> 1) & 3);
+        return __ushort_as_bfloat16(static_cast<unsigned short>((m & 1) ? (w >> 16) : (w & 0xffffu)));
+    }
+    __device__ static __forceinline__ void put(uint4 *v, int m, __nv_bfloat16 x) {
+        const uint32_t h = __bfloat16_as_ushort(x);
+        uint32_t w = vword(v[m >> 3], (m >> 1) & 3);
+        w = (m & 1) ? ((w & 0xffffu) | (h << 16)) : ((w & 0xffff0000u) | h);
+        set_vword(v[m >> 3], (m >> 1) & 3, w);
+    }
+};
+
 template <typename T>
 __device__ __forceinline__ void load_items(T (&dst)[kItems], const T *src) {
     constexpr int kVec = static_cast<int>(sizeof(T)) * kItems / 16;
     static_assert(kVec * 16 == static_cast<int>(sizeof(T)) * kItems, "kItems elements must fill 16-byte vectors");
     const uint4 *s = reinterpret_cast<const uint4 *>(src);
-    uint4 *d = reinterpret_cast<uint4 *>(dst);
+    uint4 v[kVec];
 #pragma unroll
-    for (int v = 0; v < kVec; ++v) d[v] = s[v];
+    for (int k = 0; k < kVec; ++k) v[k] = s[k];
+#pragma unroll
+    for (int m = 0; m < kItems; ++m) dst[m] = Bits<T>::get(v, m);
 }
 template <typename T>
 __device__ __forceinline__ void store_items(T *dst, const T (&src)[kItems]) {
     constexpr int kVec = static_cast<int>(sizeof(T)) * kItems / 16;
-    const uint4 *s = reinterpret_cast<const uint4 *>(src);
+    uint4 v[kVec];
+#pragma unroll
+    for (int k = 0; k < kVec; ++k) v[k] = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+    for (int m = 0; m < kItems; ++m) Bits<T>::put(v, m, src[m]);
     uint4 *d = reinterpret_cast<uint4 *>(dst);
 #pragma unroll
-    for (int v = 0; v < kVec; ++v) d[v] = s[v];
+    for (int k = 0; k < kVec; ++k) d[k] = v[k];
 }
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+// Half-width of template row dy (reading C2): the largest w with w^2 + dy^2 <= r^2
+// (|dy| <= r <= 64; the float square root is corrected to the exact integer).
+__device__ __forceinline__ int row_half_width(int r, int dy) {
+    const int q = r * r - dy * dy;
+    int w = static_cast<int>(sqrtf(static_cast<float>(q)));
+    if ((w + 1) * (w + 1) <= q) ++w;
+    if (w * w > q) --w;
+    return w;
+}
 
 struct FrameView {
     const uint8_t *p;
@@ -365,6 +437,11 @@ struct HalfOps<__nv_bfloat16> {
     __device__ static __forceinline__ __nv_bfloat16 hi_h(h2 v) { return __high2bfloat16(v); }
 };
 
+// The half-form sum (reading C10): each template row summed left to right, then the row
+// sums added top to bottom, every addition in the lane type (F16, the paper's half
+// accumulation) or in FP32 (BF16 and PF_FLAG_ACCUM32) and the result rounded to the lane
+// type.  Every route below (a thread over the frame, a thread over staged terms, a warp
+// over the frame) performs exactly these operations in this order.
 template <typename H>
 struct HalfLik {
     H kap, bgo, fgo;
@@ -375,32 +452,21 @@ struct HalfLik {
         const H b = __hmul(__hsub(h, fgo), kap);
         return __hfma(a, a, __hneg(__hmul(b, b)));
     }
-    // direct evaluation from the frame (same terms, same order as the tabulated route)
+    // direct evaluation from the frame by one thread
     __device__ H at(const FrameView &f, const int8_t *w, int px, int py) const {
         H hacc = HalfOps<H>::from_f(0.0f);
         float facc = 0.0f;
         for (int dy = -f.r; dy <= f.r; ++dy) {
             const int hw = w[dy + f.r];
+            H hrow = HalfOps<H>::from_f(0.0f);
+            float frow = 0.0f;
             for (int dx = -hw; dx <= hw; ++dx) {
                 const H tm = term(f.at(px + dx, py + dy));
-                if (half_acc) hacc = __hadd(hacc, tm); else facc += HalfOps<H>::to_f(tm);
+                if (half_acc) hrow = __hadd(hrow, tm); else frow += HalfOps<H>::to_f(tm);
             }
+            if (half_acc) hacc = __hadd(hacc, hrow); else facc += frow;
         }
         return half_acc ? hacc : HalfOps<H>::from_f(facc);
-    }
-    // the same sum through a list of template offsets (row-major over D, so the same
-    // order as from_terms and at)
-    __device__ H from_offsets(const H *base, const uint16_t *off, int D) const {
-        if (half_acc) {
-            H acc = HalfOps<H>::from_f(0.0f);
-#pragma unroll 8
-            for (int k = 0; k < D; ++k) acc = __hadd(acc, base[off[k]]);
-            return acc;
-        }
-        float acc = 0.0f;
-#pragma unroll 8
-        for (int k = 0; k < D; ++k) acc += HalfOps<H>::to_f(base[off[k]]);
-        return HalfOps<H>::from_f(acc);
     }
     // from per-pixel terms staged in shared memory (row pitch rw, template centred at
     // column cx + r, row cy + r)
@@ -410,8 +476,10 @@ struct HalfLik {
             for (int i = 0; i <= 2 * r; ++i) {
                 const int hw = w[i];
                 const H *row = tm + (cy + i) * rw + cx + r;
-#pragma unroll 8
-                for (int dx = -hw; dx <= hw; ++dx) acc = __hadd(acc, row[dx]);
+                H rs = HalfOps<H>::from_f(0.0f);
+#pragma unroll 4
+                for (int dx = -hw; dx <= hw; ++dx) rs = __hadd(rs, row[dx]);
+                acc = __hadd(acc, rs);
             }
             return acc;
         }
@@ -419,12 +487,68 @@ struct HalfLik {
         for (int i = 0; i <= 2 * r; ++i) {
             const int hw = w[i];
             const H *row = tm + (cy + i) * rw + cx + r;
-#pragma unroll 8
-            for (int dx = -hw; dx <= hw; ++dx) acc += HalfOps<H>::to_f(row[dx]);
+            float rs = 0.0f;
+#pragma unroll 4
+            for (int dx = -hw; dx <= hw; ++dx) rs += HalfOps<H>::to_f(row[dx]);
+            acc += rs;
         }
         return HalfOps<H>::from_f(acc);
     }
+    // by one warp from the frame: lane l sums rows l, l + 32, ... (each left to right);
+    // lane 0 adds the row sums top to bottom.  Valid in lane 0.
+    __device__ H warp_at(const FrameView &f, int px, int py) const {
+        const int lane = threadIdx.x & 31, nrow = 2 * f.r + 1;
+        H hacc = HalfOps<H>::from_f(0.0f);
+        float facc = 0.0f;
+        for (int base = 0; base < nrow; base += 32) {
+            const int i = base + lane;
+            H hrow = HalfOps<H>::from_f(0.0f);
+            float frow = 0.0f;
+            if (i < nrow) {
+                const int dy = i - f.r;
+                const int hw = row_half_width(f.r, dy);
+                for (int dx = -hw; dx <= hw; ++dx) {
+                    const H tm = term(f.at(px + dx, py + dy));
+                    if (half_acc) hrow = __hadd(hrow, tm); else frow += HalfOps<H>::to_f(tm);
+                }
+            }
+            const int n = nrow - base < 32 ? nrow - base : 32;
+            for (int k = 0; k < n; ++k) {
+                if (half_acc) {
+                    const H v = __shfl_sync(0xffffffffu, hrow, k);
+                    hacc = __hadd(hacc, v);
+                } else {
+                    facc += __shfl_sync(0xffffffffu, frow, k);
+                }
+            }
+        }
+        return half_acc ? hacc : HalfOps<H>::from_f(facc);
+    }
 };
+
+// The half-form constants of a tracker: kappa, and the two levels offset so that a pixel
+// enters half arithmetic without a conversion (HalfOps<H>::pix).
+template <typename H>
+__device__ __forceinline__ HalfLik<H> half_lik(const TrackerDev &T) {
+    HalfLik<H> hk;
+    const float lo = HalfOps<H>::kLevelOffset;
+    hk.kap = HalfOps<H>::from_f(T.kappa);
+    hk.bgo = HalfOps<H>::from_f(lo + T.bg_f);
+    hk.fgo = HalfOps<H>::from_f(lo + T.fg_f);
+    hk.half_acc = std::is_same<H, __half>::value && !(T.flags & 0x2u);
+    return hk;
+}
+
+// Integer disk sum by one warp (lanes take template rows; exact, so the order is free).
+__device__ __forceinline__ uint32_t warp_disk_sum(const FrameView &f, int px, int py) {
+    const int lane = threadIdx.x & 31, nrow = 2 * f.r + 1;
+    uint32_t s = 0;
+    for (int i = lane; i < nrow; i += 32) {
+        const int hw = row_half_width(f.r, i - f.r);
+        for (int dx = -hw; dx <= hw; ++dx) s += f.at(px + dx, py + i - f.r);
+    }
+    return __reduce_add_sync(0xffffffffu, s);
+}
 
 // Shared memory of the step kernel (dynamic: sizeof(StepSmem<P>) bytes).
 template <int P>
@@ -441,7 +565,6 @@ struct __align__(16) StepSmem {
         uint16_t pre[kRoiMax];      // integer form: row prefix sums of the staged region
         lik_t term[Tr::kHalf ? kRoiMax : 1];   // half form: per-pixel Eq. 4 terms of the staged region
     } u;
-    alignas(16) uint16_t toff[Tr::kHalf ? kOffMax : 8];   // half form: template offsets in the staged region
     alignas(16) uint16_t map[kMapMax];   // ancestor (tile element + 1) of each offspring
     alignas(16) int warp_imax[kWarps];
     alignas(16) acc_t warp_sum[kWarps];
@@ -490,6 +613,30 @@ __device__ __forceinline__ Stats<A> warp_stats(Stats<A> v) {
         sy = add_rn(sy, __shfl_xor_sync(0xffffffffu, sy, o));
     }
     return Stats<A>{m, s, sx, sy};
+}
+
+// Warp-level min / max of a bounding box (x0, x1, y0, y1); lane 0 leaves it in sm.box for
+// merge_warp_boxes after the next barrier.
+template <int P>
+__device__ __forceinline__ void warp_box(float4 b, StepSmem<P> &sm) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        b.x = fminf(b.x, __shfl_xor_sync(0xffffffffu, b.x, o));
+        b.y = fmaxf(b.y, __shfl_xor_sync(0xffffffffu, b.y, o));
+        b.z = fminf(b.z, __shfl_xor_sync(0xffffffffu, b.z, o));
+        b.w = fmaxf(b.w, __shfl_xor_sync(0xffffffffu, b.w, o));
+    }
+    if ((threadIdx.x & 31) == 0) *reinterpret_cast<float4 *>(sm.box[threadIdx.x >> 5]) = b;
+}
+template <int P>
+__device__ __forceinline__ float4 merge_warp_boxes(const StepSmem<P> &sm) {
+    float4 b = *reinterpret_cast<const float4 *>(sm.box[0]);
+#pragma unroll
+    for (int w = 1; w < kWarps; ++w) {
+        const float4 v = *reinterpret_cast<const float4 *>(sm.box[w]);
+        b.x = fminf(b.x, v.x); b.y = fmaxf(b.y, v.y); b.z = fminf(b.z, v.z); b.w = fmaxf(b.w, v.w);
+    }
+    return b;
 }
 
 template <int P, typename A>
@@ -566,22 +713,32 @@ __device__ void finalize_tracker(const TrackerDev &T, TrackerState *st, StepSmem
     constexpr bool kF64 = sizeof(acc_t) == 8;
     constexpr bool F = Prec<P>::kHalf;
     Stats<acc_t> v{neg_inf<acc_t>(), 0, 0, 0};
+    float4 bb = make_float4(FLT_MAX, -FLT_MAX, FLT_MAX, -FLT_MAX);
     const uint64_t tg = partial_tag(sm.st.epoch);
     for (int i = threadIdx.x; i < T.ntiles; i += kThreads) {
         Stats<acc_t> w;
+        uint64_t q[8];
         if constexpr (kF64) {
             const double *p = T.part[i].d;
             w = Stats<acc_t>{__ldcg(p + 0), __ldcg(p + 1), __ldcg(p + 2), __ldcg(p + 3)};
+            const unsigned long long *pb = reinterpret_cast<const unsigned long long *>(T.part[i].b);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) q[4 + k] = __ldcg(pb + k);
         } else {
-            uint64_t q[4];
             wait_partial(&T.part[i], tg, st, q);
             w = Stats<acc_t>{__uint_as_float(static_cast<uint32_t>(q[0])), __uint_as_float(static_cast<uint32_t>(q[1])),
                              __uint_as_float(static_cast<uint32_t>(q[2])), __uint_as_float(static_cast<uint32_t>(q[3]))};
         }
         v = stats_merge<F>(v, w);
+        bb.x = fminf(bb.x, __uint_as_float(static_cast<uint32_t>(q[4])));
+        bb.y = fmaxf(bb.y, __uint_as_float(static_cast<uint32_t>(q[5])));
+        bb.z = fminf(bb.z, __uint_as_float(static_cast<uint32_t>(q[6])));
+        bb.w = fmaxf(bb.w, __uint_as_float(static_cast<uint32_t>(q[7])));
     }
+    warp_box(bb, sm);
     v = block_stats<P>(v, sm);
     if (threadIdx.x == 0) {
+        bb = merge_warp_boxes(sm);
         const Stats<acc_t> r = v;
         // The new state is built from the copy in shared memory (this launch's starting
         // state, which no tile changes) and written with stores only: no load round trip.
@@ -619,6 +776,12 @@ __device__ void finalize_tracker(const TrackerDev &T, TrackerState *st, StepSmem
         n.ayi = o.nyi;
         n.est_x = ex;
         n.est_y = ey;
+        // the box of the new positions sizes the next step's tracker table (none if empty)
+        const bool box_ok = bb.x <= bb.y && bb.z <= bb.w;
+        n.bb_x0 = box_ok ? bb.x : __int_as_float(0x7fc00000);
+        n.bb_x1 = box_ok ? bb.y : __int_as_float(0x7fc00000);
+        n.bb_y0 = box_ok ? bb.z : __int_as_float(0x7fc00000);
+        n.bb_y1 = box_ok ? bb.w : __int_as_float(0x7fc00000);
         n.t = o.t + 1;
         n.epoch = o.epoch + 1u;
         const int64_t slot = (o.t >= 0 && o.t < 0x7fffffffll)
@@ -639,6 +802,73 @@ __device__ void finalize_tracker(const TrackerDev &T, TrackerState *st, StepSmem
         // every tile of this launch has counted; the next launch sees the reset after the
         // kernel boundary
         *T.done = 0u;
+    }
+}
+
+// The tracker's likelihood table of this launch into the tile's shared-memory table: each
+// cell's word if it carries this launch's tag, else the cell computed here (the builder
+// has not reached it yet; the same operations give the same bits).
+template <int P, typename A>
+__device__ __forceinline__ void fetch_table(const TrackerDev &T, StepSmem<P> &sm, int gx0, int gy0, int gw, int cells,
+                                            const FrameView &fv, A c1, A c2D, A den, TrackerState *st) {
+    (void)st;
+    using H = typename std::conditional<Prec<P>::kHalf, typename Prec<P>::pos_t, __half>::type;
+    const uint64_t gtag = static_cast<uint64_t>(sm.st.epoch % 0x7fffffffu + 1u) << 32;
+    for (int c = threadIdx.x; c < cells; c += kThreads) {
+        const uint64_t v = __ldcg(reinterpret_cast<const unsigned long long *>(T.gtab) + PF_IDX(c, kTableMax));
+        uint32_t payload;
+        const bool built = (v & 0xffffffff00000000ull) == gtag;
+        if constexpr (Prec<P>::kHalf) {
+            if (built) {
+                payload = static_cast<uint32_t>(v);
+            } else {
+                const H h = half_lik<H>(T).at(fv, sm.w, gx0 + c % gw, gy0 + c / gw);
+                payload = static_cast<uint32_t>(*reinterpret_cast<const unsigned short *>(&h));
+            }
+            const unsigned short bits = static_cast<unsigned short>(payload);
+            sm.table[PF_IDX(c, kTableMax)] = *reinterpret_cast<const H *>(&bits);
+        } else {
+            payload = built ? static_cast<uint32_t>(v) : disk_sum(fv, sm.w, gx0 + c % gw, gy0 + c / gw);
+            sm.table[PF_IDX(c, kTableMax)] = lik_from_sum<A>(payload, c1, c2D, den);
+        }
+    }
+}
+
+// The strata counts of a thread's elements (phase 1d): C_k of each element from the tile's
+// local prefix loc[m] pinned to the exact boundaries excl / pend, and J = the number of
+// strata points at or below C_k (repeated C values reuse the count); the tile's first count
+// goes to jbeg (thread 0).  nrm is the saved 1/S (the naive study build: S itself).
+// Force-inlined so that loc and Jr stay in registers.
+template <typename A, typename Str>
+__device__ __forceinline__ void strata_counts(const Str &str, const A (&loc)[kItems], int (&Jr)[kItems], A excl,
+                                              A pend, A nrm, int tid, int lt, int eb, int cnt, int k0, int N,
+                                              A *dbg_cdf, int &jbeg, TrackerState *st) {
+    (void)st;
+#ifdef PF_NAIVE_RESAMPLE
+    const A Sdiv = nrm;
+#else
+    const A invS = nrm;
+#endif
+    if (tid == 0) jbeg = (lt == 0) ? 0 : str.count_le(fmin(PF_NORM(excl), static_cast<A>(1)));
+    A cprev = static_cast<A>(-1);
+    int jprev = 0;
+#pragma unroll
+    for (int m = 0; m < kItems; ++m) {
+        const int e = eb + m;
+        int J = N;                                   // (elements past the tile: unused)
+        if (e < cnt) {
+            const int k = k0 + e;
+            const A Pk = (e == cnt - 1) ? pend : fmin(add_rn(excl, loc[m]), pend);
+            // the normalised CDF cannot exceed 1; the FP32 scan can round above it
+            A C = fmin(PF_NORM(Pk), static_cast<A>(1));
+            if (k == N - 1) { C = static_cast<A>(1); J = N; }
+            else if (C == cprev) J = jprev;          // same CDF value, same count
+            else J = str.count_le(C);
+            cprev = C;
+            jprev = J;
+            if (dbg_cdf) dbg_cdf[PF_IDX(k, N)] = C;
+        }
+        Jr[m] = J;
     }
 }
 
@@ -730,11 +960,52 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
         fv.pitch = sm.fr.pitch;
     }
     const int r = fv.r;
-    for (int i = tid; i <= 2 * r; i += kThreads) {
-        const int dy = i - r;
-        int w = 0;
-        while ((w + 1) * (w + 1) + dy * dy <= r * r) ++w;
-        sm.w[i] = static_cast<int8_t>(w);
+    for (int i = tid; i <= 2 * r; i += kThreads) sm.w[i] = static_cast<int8_t>(row_half_width(r, i - r));
+
+    using H = typename std::conditional<Tr::kHalf, pos_t, __half>::type;
+
+    // ------------------------------------------------------------ 0. the tracker's table
+    // A step launch of a tracker of two or more tiles whose previous positions' bounding box
+    // is known shares one likelihood table per frame: the window every offspring can reach
+    // (the box widened by the drift and the largest draw, kDrawMax sigma, plus one pixel
+    // of rounding), tabulated once in device memory instead of once per tile.  The tiles
+    // that start first (the tracker's first min(ntiles, grid) tiles) build it, one cell per
+    // warp; every cell carries this launch's tag, and a tile that finds a cell not yet
+    // built computes it itself (same operations, same bits), so no tile waits for another.
+    bool gt = false;
+    if constexpr (kMode == kModeStep) {
+        int gx0 = 0, gy0 = 0, gw = 0, gh = 0;
+        const float b0 = sm.st.bb_x0, b1 = sm.st.bb_x1, c0 = sm.st.bb_y0, c1b = sm.st.bb_y1;
+        if (T.gtab != nullptr && T.ntiles >= 2 && b0 <= b1 && c0 <= c1b && fabsf(b0) < 1.0e6f && fabsf(b1) < 1.0e6f &&
+            fabsf(c0) < 1.0e6f && fabsf(c1b) < 1.0e6f) {
+            const float mxr = fabsf(T.drift_xf) + kDrawMax * T.sigma_xf + 1.0f;
+            const float myr = fabsf(T.drift_yf) + kDrawMax * T.sigma_yf + 1.0f;
+            if (mxr < 4096.0f && myr < 4096.0f && b1 - b0 < 4096.0f && c1b - c0 < 4096.0f) {
+                gx0 = static_cast<int>(floorf(b0 - mxr));
+                gy0 = static_cast<int>(floorf(c0 - myr));
+                gw = static_cast<int>(ceilf(b1 + mxr)) - gx0 + 1;
+                gh = static_cast<int>(ceilf(c1b + myr)) - gy0 + 1;
+                gt = static_cast<int64_t>(gw) * gh <= kTableMax;
+            }
+        }
+        if (gt) {
+            // the window for the rest of the tile (ordered by the barrier of phase 1b)
+            if (tid == 0) { sm.win_x0 = gx0; sm.win_y0 = gy0; sm.win_w = gw; sm.win_h = gh; }
+            const uint64_t gtag = static_cast<uint64_t>(sm.st.epoch % 0x7fffffffu + 1u) << 32;
+            const int K = T.ntiles < static_cast<int>(gridDim.x) ? T.ntiles : static_cast<int>(gridDim.x);
+            const int gcells = gw * gh;
+            for (int c = lt + K * warp; lt < K && c < gcells; c += K * kWarps) {
+                const int px = gx0 + c % gw, py = gy0 + c / gw;
+                uint32_t payload;
+                if constexpr (Tr::kHalf) {
+                    const H v = half_lik<H>(T).warp_at(fv, px, py);
+                    payload = static_cast<uint32_t>(*reinterpret_cast<const unsigned short *>(&v));
+                } else {
+                    payload = warp_disk_sum(fv, px, py);
+                }
+                if (lane == 0) st_relaxed_u64(&T.gtab[PF_IDX(c, kTableMax)], gtag | payload);
+            }
+        }
     }
 
     // ------------------------------------------------------------ 1a. local scan of e
@@ -779,7 +1050,7 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
             const int e = eb + m;
             acc_t v = static_cast<acc_t>(0);
             if (e < cnt) v = wexp<Tr::kHalf>(to_acc(lv[m]) - M);
-            if (v > static_cast<acc_t>(9.3132257461547852e-10)) {   // weight above 2^-30 of the max
+            if (!gt && v > static_cast<acc_t>(9.3132257461547852e-10)) {   // weight above 2^-30 of the max
                 const float xa = static_cast<float>(to_acc(xv[m])) + sx;
                 const float ya = static_cast<float>(to_acc(yv[m])) + sy;
                 bx0 = fminf(bx0, xa); bx1 = fmaxf(bx1, xa);
@@ -915,14 +1186,16 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
     // lookback, so that the predecessors publish meanwhile.  (The pull kernel sizes it by
     // the gathered ancestors; the CDF kernel has none.)
     if constexpr (kMode != kModeCdf) {
+        if (!gt) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            bx0 = fminf(bx0, __shfl_xor_sync(0xffffffffu, bx0, o));
-            bx1 = fmaxf(bx1, __shfl_xor_sync(0xffffffffu, bx1, o));
-            by0 = fminf(by0, __shfl_xor_sync(0xffffffffu, by0, o));
-            by1 = fmaxf(by1, __shfl_xor_sync(0xffffffffu, by1, o));
+            for (int o = 16; o > 0; o >>= 1) {
+                bx0 = fminf(bx0, __shfl_xor_sync(0xffffffffu, bx0, o));
+                bx1 = fmaxf(bx1, __shfl_xor_sync(0xffffffffu, bx1, o));
+                by0 = fminf(by0, __shfl_xor_sync(0xffffffffu, by0, o));
+                by1 = fmaxf(by1, __shfl_xor_sync(0xffffffffu, by1, o));
+            }
+            if (lane == 0) { sm.box[warp][0] = bx0; sm.box[warp][1] = bx1; sm.box[warp][2] = by0; sm.box[warp][3] = by1; }
         }
-        if (lane == 0) { sm.box[warp][0] = bx0; sm.box[warp][1] = bx1; sm.box[warp][2] = by0; sm.box[warp][3] = by1; }
         // the resampling offset u0 of frame t - 1 (Philox tag 1, index 0), once per tile
         if (t > 0 && tid == 32) {
             const uint32_t w0 =
@@ -932,7 +1205,7 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
             sm.skeys[2] = static_cast<uint32_t>(t - 1); sm.skeys[3] = T.tracker_id;
         }
         __syncthreads();
-        if (tid == 0) {
+        if (!gt && tid == 0) {
 #pragma unroll
             for (int w = 1; w < kWarps; ++w) {
                 const float4 v = *reinterpret_cast<const float4 *>(sm.box[w]);
@@ -965,32 +1238,24 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
             }
             sm.win_x0 = x0; sm.win_y0 = y0; sm.win_w = ww; sm.win_h = wh;
         }
-        __syncthreads();
+        if (!gt) __syncthreads();
     }
     const bool no_table = kMode == kModeCdf;
     const int wx0 = no_table ? 0 : sm.win_x0, wy0 = no_table ? 0 : sm.win_y0;
     const int ww = no_table ? 0 : sm.win_w, wh = no_table ? 0 : sm.win_h;
     const int cells = ww * wh;
-
-    using H = typename std::conditional<Tr::kHalf, pos_t, __half>::type;
     HalfLik<H> hk;
-    if constexpr (Tr::kHalf) {
-        const float lo = HalfOps<H>::kLevelOffset;
-        hk.kap = HalfOps<H>::from_f(T.kappa);
-        hk.bgo = HalfOps<H>::from_f(lo + T.bg_f);
-        hk.fgo = HalfOps<H>::from_f(lo + T.fg_f);
-        hk.half_acc = std::is_same<pos_t, __half>::value && !(T.flags & 0x2u);
-    }
+    if constexpr (Tr::kHalf) hk = half_lik<H>(T);
+
     const acc_t c1 = kF64 ? static_cast<acc_t>(T.c1) : static_cast<acc_t>(T.c1f);
     const acc_t c2D = kF64 ? static_cast<acc_t>(T.c2 * T.D) : static_cast<acc_t>(T.c2Df);
     const acc_t den = kF64 ? static_cast<acc_t>(T.den) : static_cast<acc_t>(T.denf);
 
     // ------------------------------------------------------------ 1c. likelihood table
-    if (kMode != kModeCdf && cells > 0) {
+    if (kMode != kModeCdf && cells > 0 && !gt) {
         // stage the frame region the window's templates cover (clamped to the frame);
         // warp w takes rows w, w + kWarps, ...; its lanes walk the row
         const int rx0 = wx0 - r, ry0 = wy0 - r, rw = ww + 2 * r, rh = wh + 2 * r;
-        const bool use_off = Tr::kHalf && T.D <= kOffMax;
         for (int yy = warp; yy < rh; yy += kWarps) {
             const uint8_t *row = fv.p + static_cast<int64_t>(clampi(ry0 + yy, 0, fv.H - 1)) * fv.pitch;
             if constexpr (Tr::kHalf) {
@@ -1016,21 +1281,11 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
                 }
             }
         }
-        // template offsets of the half form: entry k (row-major over D) of the template of
-        // cell (cx, cy) is the term at cy * rw + cx + toff[k]
-        if (use_off) {
-            for (int k = tid; k < T.D; k += kThreads) {   // entry k: row i, column dx
-                int i = 0, c0 = 0, hw = sm.w[0];
-                while (c0 + 2 * hw + 1 <= k) { c0 += 2 * hw + 1; hw = sm.w[++i]; }
-                sm.toff[PF_IDX(k, kOffMax)] = static_cast<uint16_t>(i * rw + r + (k - c0 - hw));
-            }
-        }
         __syncthreads();
         const int wdiv = kMode != kModeCdf ? ww : 1;    // (no table in the CDF kernel)
         for (int c = tid, cy = tid / wdiv, cx = tid - (tid / wdiv) * wdiv; c < cells; c += kThreads) {
             if constexpr (Tr::kHalf) {
-                if (use_off) sm.table[PF_IDX(c, kTableMax)] = hk.from_offsets(sm.u.term + cy * rw + cx, sm.toff, T.D);
-                else sm.table[PF_IDX(c, kTableMax)] = hk.from_terms(sm.u.term, rw, sm.w, r, cx, cy);
+                sm.table[PF_IDX(c, kTableMax)] = hk.from_terms(sm.u.term, rw, sm.w, r, cx, cy);
             } else {
                 uint32_t ssum = 0;
 #pragma unroll 4
@@ -1089,46 +1344,30 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
             return;                       // the pull kernel takes the offspring
         }
         // J of the tile's first element and of each element, for either resampling scheme
-        const auto count_strata = [&](const auto &str) {
-            if (tid == 0) sm.jbeg = (lt == 0) ? 0 : str.count_le(fmin(PF_NORM(excl), static_cast<acc_t>(1)));
-            acc_t cprev = static_cast<acc_t>(-1);
-            int jprev = 0;
-#pragma unroll
-            for (int m = 0; m < kItems; ++m) {
-                const int e = eb + m;
-                int J = N;                                   // (elements past the tile: unused)
-                if (e < cnt) {
-                    const int k = k0 + e;
-                    const acc_t Pk = (e == cnt - 1) ? pend : fmin(add_rn(excl, loc[m]), pend);
-                    // the normalised CDF cannot exceed 1; the FP32 scan can round above it
-                    acc_t C = fmin(PF_NORM(Pk), static_cast<acc_t>(1));
-                    if (k == N - 1) { C = static_cast<acc_t>(1); J = N; }
-                    else if (C == cprev) J = jprev;          // same CDF value, same count
-                    else J = str.count_le(C);
-                    cprev = C;
-                    jprev = J;
-                    if (dbg_cdf) dbg_cdf[PF_IDX(k, N)] = C;
-                }
-                Jr[m] = J;
-            }
-        };
+#ifdef PF_NAIVE_RESAMPLE
+        const acc_t nrm = Sdiv;
+#else
+        const acc_t nrm = invS;
+#endif
         if (T.resampler == kResampleStratified) {
             // (key_lo, key_hi, frame t - 1, tracker id) of the stratum offsets
             Strata<acc_t, true> str;
             str.init(N, static_cast<acc_t>(0.5), inv_n, sm.skeys);   // u0 = 1/2 only centres the estimate
-            count_strata(str);
+            strata_counts(str, loc, Jr, excl, pend, nrm, tid, lt, eb, cnt, k0, N, dbg_cdf, sm.jbeg, st);
         } else {
             Strata<acc_t, false> str;
             str.init(N, u0, inv_n);
-            count_strata(str);
+            strata_counts(str, loc, Jr, excl, pend, nrm, tid, lt, eb, cnt, k0, N, dbg_cdf, sm.jbeg, st);
         }
         store_items(sm.J + eb, Jr);
+        if (gt) fetch_table<P>(T, sm, wx0, wy0, ww, cells, fv, c1, c2D, den, st);
         __syncthreads();          // J, jbeg and the likelihood table are complete
         jb = sm.jbeg;
         je = sm.J[cnt - 1];
     } else {
         jb = k0;
         je = k0 + cnt;
+        if (gt) fetch_table<P>(T, sm, wx0, wy0, ww, cells, fv, c1, c2D, den, st);
         __syncthreads();          // the likelihood table is complete
     }
     const int nout = je - jb;
@@ -1201,6 +1440,14 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
     // offsets: the ancestors' anchor minus the offspring's anchor (integers)
     const float shx = static_cast<float>(axi_anc - nxi), shy = static_cast<float>(ayi_anc - nyi);
     const float ix0 = T.init_xf - static_cast<float>(nxi), iy0 = T.init_yf - static_cast<float>(nyi);
+
+    // bounding box of the thread's new positions (for the next step's tracker table):
+    // absolute in REF64 / F32, anchor offsets in half2 lanes in F16 / BF16
+    acc_t pbx0 = static_cast<acc_t>(FLT_MAX), pbx1 = static_cast<acc_t>(-FLT_MAX);
+    acc_t pby0 = static_cast<acc_t>(FLT_MAX), pby1 = static_cast<acc_t>(-FLT_MAX);
+    using HB2 = typename HalfOps<H>::h2;
+    HB2 hbx0 = HalfOps<H>::from_f2(65504.0f, 65504.0f), hbx1 = HalfOps<H>::from_f2(-65504.0f, -65504.0f);
+    HB2 hby0 = hbx0, hby1 = hbx1;
 
     // One pair of offspring (j0, j1) = (2q, 2q + 1).  Compile-time flags: V0 / V1, the
     // particle lies in [jb, je); FAST, frame t > 0 with the ancestor map and no debug
@@ -1294,6 +1541,8 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
                 Xout[PF_IDX(j1, N)] = x1; Yout[j1] = y1; Lout[j1] = L1;
             }
             stats_add2<false>(stats, v0, L0, x0 - nxa_a, y0 - nya_a, v1, L1, x1 - nxa_a, y1 - nya_a);
+            if (v0) { pbx0 = fmin(pbx0, x0); pbx1 = fmax(pbx1, x0); pby0 = fmin(pby0, y0); pby1 = fmax(pby1, y0); }
+            if (v1) { pbx0 = fmin(pbx0, x1); pbx1 = fmax(pbx1, x1); pby0 = fmin(pby0, y1); pby1 = fmax(pby1, y1); }
         } else {
             // ---------------- F16 / BF16: half2 lanes = particles (j0, j1), offsets from the anchor
             using OPS = HalfOps<H>;
@@ -1335,6 +1584,10 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
                 Xout[PF_IDX(j1, N)] = OPS::hi_h(ox); Yout[j1] = OPS::hi_h(oy); Lout[j1] = l1;
             }
             stats_add2<true>(stats, v0, OPS::to_f(l0), OPS::lo(ox), OPS::lo(oy), v1, OPS::to_f(l1), OPS::hi(ox), OPS::hi(oy));
+            // (a lane outside [jb, je) holds a draw around a valid ancestor: inside the reach
+            // of the next step's table all the same)
+            hbx0 = __hmin2(hbx0, ox); hbx1 = __hmax2(hbx1, ox);
+            hby0 = __hmin2(hby0, oy); hby1 = __hmax2(hby1, oy);
         }
     };
     {
@@ -1352,9 +1605,26 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
     }
 
     // ------------------------------------------------------------ 5. tile partial + finalise
+    float4 bb;
+    if constexpr (Tr::kHalf) {
+        const float ax = static_cast<float>(nxi), ay = static_cast<float>(nyi);
+        bb = make_float4(fminf(HalfOps<H>::lo(hbx0), HalfOps<H>::hi(hbx0)) + ax,
+                         fmaxf(HalfOps<H>::lo(hbx1), HalfOps<H>::hi(hbx1)) + ax,
+                         fminf(HalfOps<H>::lo(hby0), HalfOps<H>::hi(hby0)) + ay,
+                         fmaxf(HalfOps<H>::lo(hby1), HalfOps<H>::hi(hby1)) + ay);
+    } else {
+        // widened to whole pixels outwards, so the float box still contains every position
+        bb = make_float4(static_cast<float>(floor(pbx0)), static_cast<float>(ceil(pbx1)),
+                         static_cast<float>(floor(pby0)), static_cast<float>(ceil(pby1)));
+    }
+    warp_box(bb, sm);
     const Stats<acc_t> tot = block_stats<P>(stats, sm);
     if (tid == 0) {
+        bb = merge_warp_boxes(sm);
         TilePartial *p = &T.part[PF_IDX(lt, T.ntiles)];
+        const uint64_t btg = partial_tag(sm.st.epoch);
+        st_relaxed_v2(&p->b[0], btg | __float_as_uint(bb.x), btg | __float_as_uint(bb.y));
+        st_relaxed_v2(&p->b[2], btg | __float_as_uint(bb.z), btg | __float_as_uint(bb.w));
         uint32_t prev;
         if constexpr (kF64) {
             p->d[0] = tot.m;
@@ -1386,6 +1656,13 @@ template <int P, int kMode>
 __global__ void __launch_bounds__(kThreads, MinBlocks<P>::value) step_kernel(const StepLaunch Lp) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StepSmem<P> &sm = *reinterpret_cast<StepSmem<P> *>(smem_raw);
+    // Programmatic dependent launch: a launch that follows another step on the same stream
+    // may be scheduled while that one drains; everything it reads (ticket, descriptors,
+    // state, particles) is written by its predecessor, so it first waits for the
+    // predecessor grid to complete, then lets its own successor be scheduled.  (Both are
+    // no-ops for a launch without the programmatic-serialization attribute.)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (threadIdx.x == 0) sm.cached = -1;
     for (;;) {
         if (threadIdx.x == 0) sm.ticket = atomicAdd(Lp.ticket, 1u);
@@ -1482,17 +1759,38 @@ int step_grid_size(int precision, int total_tiles) {
     return -1;
 }
 
+// A step-family launch with programmatic stream serialization: when the previous work on
+// the stream is a step kernel (the previous frame), this launch is scheduled while that one
+// drains and waits for it on the device (griddepcontrol.wait) instead of the stream
+// serialising the two; captured into a CUDA graph as a programmatic dependency.
+template <int P, int kMode>
+int launch_one(int grid, const StepLaunch &L, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(grid));
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = sizeof(StepSmem<P>);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return static_cast<int>(cudaLaunchKernelEx(&cfg, step_kernel<P, kMode>, L));
+}
+
 template <int kMode>
 int launch_mode(int precision, const StepLaunch &L, int grid, void *stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (grid < 1) grid = 1;
+    int rc = -1;
     switch (precision) {
-        case 0: step_kernel<0, kMode><<<grid, kThreads, sizeof(StepSmem<0>), s>>>(L); break;
-        case 1: step_kernel<1, kMode><<<grid, kThreads, sizeof(StepSmem<1>), s>>>(L); break;
-        case 2: step_kernel<2, kMode><<<grid, kThreads, sizeof(StepSmem<2>), s>>>(L); break;
-        case 3: step_kernel<3, kMode><<<grid, kThreads, sizeof(StepSmem<3>), s>>>(L); break;
+        case 0: rc = launch_one<0, kMode>(grid, L, s); break;
+        case 1: rc = launch_one<1, kMode>(grid, L, s); break;
+        case 2: rc = launch_one<2, kMode>(grid, L, s); break;
+        case 3: rc = launch_one<3, kMode>(grid, L, s); break;
         default: return -1;
     }
+    if (rc != 0) return rc;
     return static_cast<int>(cudaGetLastError());
 }
 

@@ -255,7 +255,8 @@ def test_half_rounding_helpers_match_library_conversions():
 def test_half_likelihood_uniform_frame_by_float16_arithmetic():
     """Uniform frames: every template term is the same binary16 value, formed and summed
     here with numpy's own float16 arithmetic (each operation exact in binary32 at these
-    magnitudes, then rounded once); the oracle's emulation must give the same bits."""
+    magnitudes, then rounded once) row by row, the row sums then added top to bottom; the
+    oracle's emulation must give the same bits."""
     for r in (1, 3, 5, 10):
         D = oracle.disk_count(r)
         kap = np.float16(np.float32(1.0 / math.sqrt(50.0 * D)))
@@ -263,16 +264,23 @@ def test_half_likelihood_uniform_frame_by_float16_arithmetic():
             a = np.float16(np.float16(c - 100) * kap)
             b = np.float16(np.float16(c - 228) * kap)
             term = np.float16(np.float64(a) * np.float64(a) - np.float64(np.float16(b * b)))
+            # row widths of the disk: 2 floor(sqrt(r^2 - dy^2)) + 1
+            widths = [2 * math.isqrt(r * r - dy * dy) + 1 for dy in range(-r, r + 1)]
+            assert sum(widths) == D
             acc = np.float16(0.0)
-            for _ in range(D):
-                acc = np.float16(acc + term)
+            acc32 = np.float32(0.0)
+            for n in widths:
+                row = np.float16(0.0)
+                row32 = np.float32(0.0)
+                for _ in range(n):
+                    row = np.float16(row + term)
+                    row32 = np.float32(row32 + np.float32(term))
+                acc = np.float16(acc + row)
+                acc32 = np.float32(acc32 + row32)
             frame = np.full((40, 50), c, np.uint8)
             got = oracle.likelihood_half(np.array([25.0, 0.2]), np.array([20.0, 39.0]), frame, r, "f16")
             assert np.all(got == np.float64(acc)), (r, c)
             # and the FP32-accumulated form
-            acc32 = np.float32(0.0)
-            for _ in range(D):
-                acc32 = np.float32(acc32 + np.float32(term))
             got32 = oracle.likelihood_half(np.array([25.0]), np.array([20.0]), frame, r, "f16acc32")
             assert got32[0] == np.float64(np.float16(acc32)), (r, c)
 
