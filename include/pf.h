@@ -294,6 +294,60 @@ pf_status pf_step_frame_noalloc(const pf_config *cfg, const pf_state_header *sta
  * gave up, as it must.  The device stays usable afterwards.  Synchronises. */
 pf_status pf_debug_wait_timeout(uint32_t spin_limit, uint32_t *status_out);
 
+/* ---------------------------------------------------------------- one tracker on several GPUs
+ * A tracker of N particles sharded by particles across R ranks, one GPU per rank: rank q
+ * holds the contiguous particles [first_q, first_q + count_q) (pf_shard_partition).  The
+ * per-frame step (Sec. IV, Fig. 1) couples particles only through the previous frame's
+ * maximum log-likelihood M and weight sum S (Eq. 5 and the normalising kernel), the
+ * inclusive prefix of the weights that resampling searches (Sec. IV, "Resampling") and the
+ * ancestors themselves, so a frame of the sharded filter is, on every rank:
+ *   1. pf_shard_stats: the shard's (M_q, S_q, est_x_q, est_y_q) of its last frame; the
+ *      caller all-gathers them and forms, in rank order and identically on every rank,
+ *      the global M = max M_q, the rescaled totals s_q = S_q exp(M_q - M), S = sum s_q,
+ *      P_q = sum of s_r for r < q, and the frame's estimate sum s_q est_q / S;
+ *   2. pf_shard_resample: the shard's particles are the ancestors of the contiguous
+ *      offspring run [j0, j1) of the global systematic strata u_j = (j + u0) / N (reading
+ *      C8); their positions are written in offspring order;
+ *   3. the caller's all-to-all delivers to every rank the ancestor positions of its own
+ *      slots [first_q, first_q + count_q), in order; pf_shard_step propagates them (draws
+ *      keyed by the global particle index, Eq. 1-2), scores them on the frame (Eq. 3) and
+ *      forms the shard's statistics.
+ * Frame 0 has no steps 1-3: every particle starts at init_x, init_y.  The result is the
+ * unsharded filter's method (the CDF is summed in a different order, so its last bits
+ * differ).  REF64 and F32 shards, systematic resampling; positions travel as absolute
+ * coordinates in the precision's type (double / float).  All calls on one handle run on its
+ * stream; pf_shard_stats and pf_shard_resample synchronise it.  The paper tracks on one GPU;
+ * this splitting is the library's.  Errors: PF_ERR_ARG, PF_ERR_OOM, PF_ERR_CUDA,
+ * PF_ERR_STATE (failed handle, or a call out of order), PF_ERR_TIMEOUT. */
+typedef struct pf_shard pf_shard;
+/* Rank `rank`'s particles of an n_global-particle tracker over nranks ranks: first (even)
+ * and count; the last rank takes the remainder.  n_global >= 2 nranks.  No device needed. */
+pf_status pf_shard_partition(int64_t n_global, int32_t nranks, int32_t rank, int64_t *first, int64_t *count);
+/* Create rank `rank`'s shard of the tracker *cfg (cfg->num_particles = N, the whole
+ * tracker; precision PF_REF64 or PF_F32; resampler SYSTEMATIC; flags 0) on the current
+ * device, bound to cuda_stream. */
+pf_status pf_shard_create(const pf_config *cfg, int32_t rank, int32_t nranks, void *cuda_stream, pf_shard **out);
+/* out4[0..3] = (M_q, S_q, est_x_q, est_y_q) of the shard's last stepped frame (host).
+ * Synchronises.  PF_ERR_STATE before the first step. */
+pf_status pf_shard_stats(pf_shard *h, double *out4);
+/* Resample the shard's previous frame against the global weights: global4 = (M, S, P_q,
+ * P_(q+1)) of that frame (host; P_(q+1) = S on the last rank, which passes last = 1).  The
+ * ancestor position of every offspring j of the shard's run [run_out[0], run_out[1]) is
+ * written to send_x / send_y[j - run_out[0]] (device, the precision's type, capacity
+ * send_capacity elements; PF_ERR_ARG if short).  Consecutive ranks' runs meet; the first
+ * starts at 0 and the last ends at N.  Synchronises.  PF_ERR_STATE at frame 0. */
+pf_status pf_shard_resample(pf_shard *h, const double *global4, int32_t last, void *send_x, void *send_y,
+                            int64_t send_capacity, int64_t *run_out);
+/* Step the shard's slots on `frame` (a device pointer, rows pitch_bytes apart;
+ * frame_on_device must be 1): from frame 1 on, recv_x / recv_y (device, count_q elements)
+ * are the ancestor positions of slots first_q .. first_q + count_q - 1.  Asynchronous. */
+pf_status pf_shard_step(pf_shard *h, const void *recv_x, const void *recv_y, const uint8_t *frame,
+                        int64_t pitch_bytes, int32_t frame_on_device);
+/* Frames stepped so far (host-side count). */
+int64_t pf_shard_frames_done(const pf_shard *h);
+/* Release the shard (synchronises its stream).  NULL is accepted. */
+pf_status pf_shard_destroy(pf_shard *h);
+
 /* ---------------------------------------------------------------- batches
  * Many independent trackers (different N, frame sizes, radii, seeds), stepped together
  * by one persistent segmented launch per frame.  All trackers of a batch share one

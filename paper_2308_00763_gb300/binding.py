@@ -31,6 +31,8 @@ __all__ = [
     "pf_server_open", "pf_server_submit", "pf_server_tick", "pf_server_poll", "pf_server_drain",
     "pf_server_result", "pf_server_frames_done", "pf_server_close", "pf_server_get_stats",
     "pf_server_destroy", "pf_server_stream_bytes", "pf_server_replay",
+    "pf_shard_partition", "pf_shard_create", "pf_shard_stats", "pf_shard_resample", "pf_shard_step",
+    "pf_shard_frames_done", "pf_shard_destroy", "Shard",
 ]
 
 PF_OK, PF_ERR_ARG, PF_ERR_OOM, PF_ERR_CUDA, PF_ERR_TIMEOUT, PF_ERR_STATE, PF_ERR_ADMISSION = range(7)
@@ -177,6 +179,14 @@ _SIG = {
     "pf_server_destroy": (ctypes.c_int, [_P]),
     "pf_server_stream_bytes": (ctypes.c_int, [ctypes.POINTER(PfConfig), _I32, _I32, ctypes.POINTER(_I64)]),
     "pf_server_replay": (ctypes.c_int, [_P, ctypes.POINTER(PfTraceEvent), _I64, _I32, _I32]),
+    "pf_shard_partition": (ctypes.c_int, [_I64, _I32, _I32, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
+    "pf_shard_create": (ctypes.c_int, [ctypes.POINTER(PfConfig), _I32, _I32, _P, ctypes.POINTER(_P)]),
+    "pf_shard_stats": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
+    "pf_shard_resample": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), _I32, _P, _P, _I64,
+                                         ctypes.POINTER(_I64)]),
+    "pf_shard_step": (ctypes.c_int, [_P, _P, _P, _P, _I64, _I32]),
+    "pf_shard_frames_done": (_I64, [_P]),
+    "pf_shard_destroy": (ctypes.c_int, [_P]),
 }
 EXPORTED = tuple(_SIG)
 
@@ -379,6 +389,88 @@ def pf_step_frame_noalloc(cfg: PfConfig, state_in: "PfStateHeader", x_in: int, y
 
 def pf_batch_destroy(h):
     return lib().pf_batch_destroy(h)
+
+
+# ------------------------------------------------------------------ one tracker on several GPUs
+def pf_shard_partition(n_global: int, nranks: int, rank: int):
+    """(first, count) of rank `rank`'s particles."""
+    first, count = _I64(0), _I64(0)
+    _check(lib().pf_shard_partition(n_global, nranks, rank, ctypes.byref(first), ctypes.byref(count)),
+           "pf_shard_partition")
+    return first.value, count.value
+
+
+def pf_shard_create(cfg: "PfConfig", rank: int, nranks: int, stream=None):
+    h = _P()
+    _check(lib().pf_shard_create(ctypes.byref(cfg), rank, nranks, _P(_stream_ptr(stream)), ctypes.byref(h)),
+           "pf_shard_create")
+    return h
+
+
+def pf_shard_stats(h):
+    out = (ctypes.c_double * 4)()
+    _check(lib().pf_shard_stats(h, out), "pf_shard_stats")
+    return tuple(out)
+
+
+def pf_shard_resample(h, global4, last: bool, send_x: int, send_y: int, capacity: int):
+    g = (ctypes.c_double * 4)(*global4)
+    run = (_I64 * 2)()
+    _check(lib().pf_shard_resample(h, g, 1 if last else 0, _P(send_x), _P(send_y), capacity, run),
+           "pf_shard_resample")
+    return run[0], run[1]
+
+
+def pf_shard_step(h, recv_x: int, recv_y: int, frame: int, pitch: int):
+    _check(lib().pf_shard_step(h, _P(recv_x), _P(recv_y), _P(frame), pitch, 1), "pf_shard_step")
+
+
+def pf_shard_frames_done(h) -> int:
+    return lib().pf_shard_frames_done(h)
+
+
+def pf_shard_destroy(h):
+    return lib().pf_shard_destroy(h)
+
+
+class Shard:
+    """Rank `rank`'s shard of one tracker sharded by particles (pf_shard_*).  Positions
+    travel between ranks as torch tensors on the shard's device (float64 for REF64, float32
+    for F32); `paper_2308_00763_gb300.sharded.ShardedTracker` drives the exchanges."""
+
+    def __init__(self, width, height, num_particles, disk_radius, precision="ref64", *, rank=0, nranks=1,
+                 stream=None, **kw):
+        import torch
+        self.cfg = make_config(width, height, num_particles, disk_radius, precision, **kw)
+        self.rank, self.nranks = rank, nranks
+        self.first, self.count = pf_shard_partition(num_particles, nranks, rank)
+        self.stream = stream
+        self.dtype = torch.float64 if self.cfg.precision == PF_REF64 else torch.float32
+        self.h = pf_shard_create(self.cfg, rank, nranks, stream)
+
+    def stats(self):
+        return pf_shard_stats(self.h)
+
+    def resample(self, global4, last, send_x, send_y):
+        return pf_shard_resample(self.h, global4, last, send_x.data_ptr(), send_y.data_ptr(), send_x.numel())
+
+    def step(self, frame, recv_x=None, recv_y=None):
+        pf_shard_step(self.h, recv_x.data_ptr() if recv_x is not None else 0,
+                      recv_y.data_ptr() if recv_y is not None else 0, frame.data_ptr(), frame.stride(0))
+
+    def frames_done(self):
+        return pf_shard_frames_done(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            pf_shard_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ------------------------------------------------------------------ convenience wrappers

@@ -36,6 +36,10 @@ constexpr int kResampleMultinomial = 2;   // CDF by the step kernel, offspring b
 constexpr int kResampleGumbel = 3;        // ancestors by the Gumbel-max kernel, offspring by the pull kernel
 constexpr int kResampleMetropolis = 4;    // ancestors by the Metropolis kernel, offspring by the pull kernel
 constexpr int kResampleRejection = 5;     // ancestors by the rejection kernel, offspring by the pull kernel
+// One shard of a tracker sharded by particles (pf_shard_*; not a pf_config value): the
+// ancestors' positions arrive from the other ranks into the previous-frame slots, so the
+// ancestors are the identity (T.anc[k] = k) and the pull kernel takes the offspring.
+constexpr int kResampleShard = 6;
 constexpr int64_t kGumbelMaxN = 1ll << 16; // N^2 draws a frame
 constexpr int64_t kMetropolisMaxN = 1ll << 24;   // offspring index in the Philox tag
 constexpr int kMetropolisMaxSteps = 4096;
@@ -45,7 +49,8 @@ constexpr int kRejectionDefaultTries = 4096;
 
 // Schemes whose ancestors an ancestor kernel writes to T.anc before the pull kernel runs.
 __host__ __device__ constexpr bool ancestors_given(int resampler) {
-    return resampler == kResampleGumbel || resampler == kResampleMetropolis || resampler == kResampleRejection;
+    return resampler == kResampleGumbel || resampler == kResampleMetropolis || resampler == kResampleRejection ||
+           resampler == kResampleShard;
 }
 
 // Device status bits (sticky, per tracker).
@@ -125,6 +130,7 @@ struct TrackerDev {
     float init_xf, init_yf, drift_xf, drift_yf, sigma_xf, sigma_yf;
     float c1f, c2Df, denf;
     int32_t window;            // likelihood window: 0 adaptive, 1 always 3.5 sigma, 2 always the full draw range
+    int64_t j_base;            // global index of particle 0 (a shard of a sharded tracker; even), else 0
     void *px[2], *py[2], *pl[2];
     int32_t *dbg_anc;          // NULL unless PF_FLAG_DEBUG_ARRAYS
     void *dbg_cdf;
@@ -159,6 +165,11 @@ struct StepLaunch {
     int32_t total_tiles;
     const uint8_t *frame_override;  // single tracker: frame pointer passed by the call
     int64_t pitch_override;
+    // A shard's CDF launch (pf_shard_resample): the global M and 1/S replace the tracker's
+    // own, the shard's prefix starts at shard_lo and its last element is pinned to shard_hi
+    // (to 1 on the last shard).  shard = 0 for every other launch.
+    int32_t shard = 0, shard_last = 0;
+    double shard_lo = 0.0, shard_hi = 0.0, g_M = 0.0, g_invS = 0.0;
 };
 
 // Host entry points into the kernel translation unit.
@@ -169,6 +180,15 @@ int launch_step(int precision, const StepLaunch &L, int grid, void *stream);
 // ancestors that launch_gumbel / launch_metropolis / launch_rejection wrote, enqueued
 // before it).
 int launch_pull(int precision, const StepLaunch &L, int grid, bool with_cdf, void *stream);
+// The CDF kernel alone (a shard's resampling).
+int launch_cdf(int precision, const StepLaunch &L, int grid, void *stream);
+// A shard's offspring run: the counts J_k = #{j : u_j <= C_k} over the global strata
+// u_j = (j + u0) / N_global (u0 of frame t - 1) for the shard's CDF C[0..n), and the
+// ancestor position of every offspring j of its run [J(c_lo), J(C[n-1])) written to
+// sx / sy[j - J(c_lo)] (at most cap); run[0..1] = the run; status |= 1 if cap is short.
+int launch_shard_expand(int precision, const void *cdf, const void *x, const void *y, int64_t n, int64_t n_global,
+                        int64_t t, uint32_t key_lo, uint32_t key_hi, uint32_t tracker, double c_lo, void *sx,
+                        void *sy, int64_t cap, int64_t *run, uint32_t *status, void *stream);
 
 // An ancestor kernel over the trackers in slots[0 .. ntrk-1]: CTA b works on tracker g with
 // cta_prefix[g] <= b < cta_prefix[g + 1], offspring (b - cta_prefix[g]) * (offspring per

@@ -46,6 +46,7 @@
 #include <stddef.h>
 #include <math.h>
 
+#include <algorithm>
 #include <atomic>
 #include <type_traits>
 
@@ -179,18 +180,21 @@ __device__ __forceinline__ uint64_t partial_tag(uint32_t ep) {   // never 0 (cle
     return static_cast<uint64_t>(ep % 0x7fffffffu + 1u) << 32;
 }
 
-// Wait (bounded) until the eight words of a tile partial (statistics, then bounding box)
-// carry this launch's tag; on timeout the tracker's timeout bit is raised and the words read
-// last are returned.
-__device__ void wait_partial(const TilePartial *p, uint64_t tag, TrackerState *st, uint64_t (&q)[8],
+// Wait (bounded) until the words of a tile partial (statistics, and the bounding box when
+// the launch tracks it) carry this launch's tag; on timeout the tracker's timeout bit is
+// raised and the words read last are returned.
+__device__ void wait_partial(const TilePartial *p, uint64_t tag, TrackerState *st, uint64_t (&q)[8], bool with_box,
                              uint32_t limit = kSpinLimit) {
     uint32_t ns = 8;
     const uint64_t hm = 0xffffffff00000000ull;
+    q[4] = q[5] = q[6] = q[7] = tag;
     for (uint32_t it = 0; it < limit; ++it) {
         ld_relaxed_v2(&p->w[0], q[0], q[1]);
         ld_relaxed_v2(&p->w[2], q[2], q[3]);
-        ld_relaxed_v2(&p->b[0], q[4], q[5]);
-        ld_relaxed_v2(&p->b[2], q[6], q[7]);
+        if (with_box) {
+            ld_relaxed_v2(&p->b[0], q[4], q[5]);
+            ld_relaxed_v2(&p->b[2], q[6], q[7]);
+        }
         if ((q[0] & hm) == tag && (q[1] & hm) == tag && (q[2] & hm) == tag && (q[3] & hm) == tag &&
             (q[4] & hm) == tag && (q[5] & hm) == tag && (q[6] & hm) == tag && (q[7] & hm) == tag)
             return;
@@ -708,7 +712,8 @@ __device__ __forceinline__ int upper_index(const int32_t *J, int n, int j) {
 // Merge of the tracker's tile partials (one per thread, all loads in flight, then the
 // block merge: deterministic) and the new state, by the tile that completed the tracker.
 template <int P>
-__device__ void finalize_tracker(const TrackerDev &T, TrackerState *st, StepSmem<P> &sm, double *est_out) {
+__device__ void finalize_tracker(const TrackerDev &T, TrackerState *st, StepSmem<P> &sm, double *est_out,
+                                 bool track_box) {
     using acc_t = typename Prec<P>::acc_t;
     constexpr bool kF64 = sizeof(acc_t) == 8;
     constexpr bool F = Prec<P>::kHalf;
@@ -723,9 +728,9 @@ __device__ void finalize_tracker(const TrackerDev &T, TrackerState *st, StepSmem
             w = Stats<acc_t>{__ldcg(p + 0), __ldcg(p + 1), __ldcg(p + 2), __ldcg(p + 3)};
             const unsigned long long *pb = reinterpret_cast<const unsigned long long *>(T.part[i].b);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) q[4 + k] = __ldcg(pb + k);
+            for (int k = 0; k < 4; ++k) q[4 + k] = track_box ? __ldcg(pb + k) : 0ull;
         } else {
-            wait_partial(&T.part[i], tg, st, q);
+            wait_partial(&T.part[i], tg, st, q, track_box);
             w = Stats<acc_t>{__uint_as_float(static_cast<uint32_t>(q[0])), __uint_as_float(static_cast<uint32_t>(q[1])),
                              __uint_as_float(static_cast<uint32_t>(q[2])), __uint_as_float(static_cast<uint32_t>(q[3]))};
         }
@@ -735,10 +740,10 @@ __device__ void finalize_tracker(const TrackerDev &T, TrackerState *st, StepSmem
         bb.z = fminf(bb.z, __uint_as_float(static_cast<uint32_t>(q[6])));
         bb.w = fmaxf(bb.w, __uint_as_float(static_cast<uint32_t>(q[7])));
     }
-    warp_box(bb, sm);
+    if (track_box) warp_box(bb, sm);
     v = block_stats<P>(v, sm);
     if (threadIdx.x == 0) {
-        bb = merge_warp_boxes(sm);
+        if (track_box) bb = merge_warp_boxes(sm);
         const Stats<acc_t> r = v;
         // The new state is built from the copy in shared memory (this launch's starting
         // state, which no tile changes) and written with stores only: no load round trip.
@@ -776,8 +781,9 @@ __device__ void finalize_tracker(const TrackerDev &T, TrackerState *st, StepSmem
         n.ayi = o.nyi;
         n.est_x = ex;
         n.est_y = ey;
-        // the box of the new positions sizes the next step's tracker table (none if empty)
-        const bool box_ok = bb.x <= bb.y && bb.z <= bb.w;
+        // the box of the new positions sizes the next step's tracker table (unknown if the
+        // launch did not track it, or empty)
+        const bool box_ok = track_box && bb.x <= bb.y && bb.z <= bb.w;
         n.bb_x0 = box_ok ? bb.x : __int_as_float(0x7fc00000);
         n.bb_x1 = box_ok ? bb.y : __int_as_float(0x7fc00000);
         n.bb_y0 = box_ok ? bb.z : __int_as_float(0x7fc00000);
@@ -836,20 +842,19 @@ __device__ __forceinline__ void fetch_table(const TrackerDev &T, StepSmem<P> &sm
 
 // The strata counts of a thread's elements (phase 1d): C_k of each element from the tile's
 // local prefix loc[m] pinned to the exact boundaries excl / pend, and J = the number of
-// strata points at or below C_k (repeated C values reuse the count); the tile's first count
-// goes to jbeg (thread 0).  nrm is the saved 1/S (the naive study build: S itself).
-// Force-inlined so that loc and Jr stay in registers.
+// strata points at or below C_k (repeated C values reuse the count: on a peaked posterior
+// most elements repeat the previous C).  nrm is the saved 1/S (the naive study build: S
+// itself).  Force-inlined so that loc and Jr stay in registers.
 template <typename A, typename Str>
 __device__ __forceinline__ void strata_counts(const Str &str, const A (&loc)[kItems], int (&Jr)[kItems], A excl,
-                                              A pend, A nrm, int tid, int lt, int eb, int cnt, int k0, int N,
-                                              A *dbg_cdf, int &jbeg, TrackerState *st) {
+                                              A pend, A nrm, int eb, int cnt, int k0, int N, A *dbg_cdf,
+                                              TrackerState *st) {
     (void)st;
 #ifdef PF_NAIVE_RESAMPLE
     const A Sdiv = nrm;
 #else
     const A invS = nrm;
 #endif
-    if (tid == 0) jbeg = (lt == 0) ? 0 : str.count_le(fmin(PF_NORM(excl), static_cast<A>(1)));
     A cprev = static_cast<A>(-1);
     int jprev = 0;
 #pragma unroll
@@ -930,7 +935,7 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
     // (the host gives each launch only its own family's tiles; the CDF and pull kernels
     // check as well)
     if constexpr (kMode == kModeCdf) {
-        if (T.resampler != kResampleMultinomial) return;
+        if (T.resampler != kResampleMultinomial && T.resampler != kResampleShard) return;
     } else if constexpr (kMode == kModePull) {
         if (T.resampler != kResampleMultinomial && !ancestors_given(T.resampler)) return;
     }
@@ -965,18 +970,23 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
     using H = typename std::conditional<Tr::kHalf, pos_t, __half>::type;
 
     // ------------------------------------------------------------ 0. the tracker's table
-    // A step launch of a tracker of two or more tiles whose previous positions' bounding box
-    // is known shares one likelihood table per frame: the window every offspring can reach
-    // (the box widened by the drift and the largest draw, kDrawMax sigma, plus one pixel
-    // of rounding), tabulated once in device memory instead of once per tile.  The tiles
-    // that start first (the tracker's first min(ntiles, grid) tiles) build it, one cell per
-    // warp; every cell carries this launch's tag, and a tile that finds a cell not yet
-    // built computes it itself (same operations, same bits), so no tile waits for another.
+    // A step launch of a tracker of at least two waves of tiles (twice as many tiles as the
+    // launch has CTAs) whose previous positions' bounding box is known shares one likelihood
+    // table per frame: the window every offspring can reach (the box widened by the drift
+    // and the largest draw, kDrawMax sigma, plus one pixel of rounding), tabulated once in
+    // device memory instead of once per tile.  (With a single wave the per-tile tables are
+    // built while the tiles wait for their predecessors' aggregates, at no cost; so are the
+    // builders' cells here, after the aggregate is published.)  The tracker's first
+    // min(ntiles, grid) tiles build it, one cell per warp; every cell carries this launch's
+    // tag, and a tile that finds a cell not yet built computes it itself (same operations,
+    // same bits), so no tile waits for another.
+    const bool track_box = kMode == kModeStep && T.gtab != nullptr &&
+                           T.ntiles >= 2 * static_cast<int>(gridDim.x);
     bool gt = false;
+    int gx0 = 0, gy0 = 0, gw = 0, gh = 0;
     if constexpr (kMode == kModeStep) {
-        int gx0 = 0, gy0 = 0, gw = 0, gh = 0;
         const float b0 = sm.st.bb_x0, b1 = sm.st.bb_x1, c0 = sm.st.bb_y0, c1b = sm.st.bb_y1;
-        if (T.gtab != nullptr && T.ntiles >= 2 && b0 <= b1 && c0 <= c1b && fabsf(b0) < 1.0e6f && fabsf(b1) < 1.0e6f &&
+        if (track_box && b0 <= b1 && c0 <= c1b && fabsf(b0) < 1.0e6f && fabsf(b1) < 1.0e6f &&
             fabsf(c0) < 1.0e6f && fabsf(c1b) < 1.0e6f) {
             const float mxr = fabsf(T.drift_xf) + kDrawMax * T.sigma_xf + 1.0f;
             const float myr = fabsf(T.drift_yf) + kDrawMax * T.sigma_yf + 1.0f;
@@ -988,28 +998,13 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
                 gt = static_cast<int64_t>(gw) * gh <= kTableMax;
             }
         }
-        if (gt) {
-            // the window for the rest of the tile (ordered by the barrier of phase 1b)
-            if (tid == 0) { sm.win_x0 = gx0; sm.win_y0 = gy0; sm.win_w = gw; sm.win_h = gh; }
-            const uint64_t gtag = static_cast<uint64_t>(sm.st.epoch % 0x7fffffffu + 1u) << 32;
-            const int K = T.ntiles < static_cast<int>(gridDim.x) ? T.ntiles : static_cast<int>(gridDim.x);
-            const int gcells = gw * gh;
-            for (int c = lt + K * warp; lt < K && c < gcells; c += K * kWarps) {
-                const int px = gx0 + c % gw, py = gy0 + c / gw;
-                uint32_t payload;
-                if constexpr (Tr::kHalf) {
-                    const H v = half_lik<H>(T).warp_at(fv, px, py);
-                    payload = static_cast<uint32_t>(*reinterpret_cast<const unsigned short *>(&v));
-                } else {
-                    payload = warp_disk_sum(fv, px, py);
-                }
-                if (lane == 0) st_relaxed_u64(&T.gtab[PF_IDX(c, kTableMax)], gtag | payload);
-            }
-        }
+        // the window for the rest of the tile (ordered by the barrier of phase 1b)
+        if (gt && tid == 0) { sm.win_x0 = gx0; sm.win_y0 = gy0; sm.win_w = gw; sm.win_h = gh; }
     }
 
     // ------------------------------------------------------------ 1a. local scan of e
     acc_t loc[kItems];
+    acc_t mex = static_cast<acc_t>(0);   // running max of the preceding lanes of the warp
     // bounding box of the ancestors with non-negligible weight (absolute pixel units)
     float bx0 = FLT_MAX, bx1 = -FLT_MAX, by0 = FLT_MAX, by1 = -FLT_MAX;
     const int eb = tid * kItems;  // blocked arrangement: thread tid owns elements eb .. eb+kItems-1
@@ -1017,7 +1012,8 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
         const lik_t *__restrict__ Lin = static_cast<const lik_t *>(T.pl[in]);
         const pos_t *__restrict__ Xin = static_cast<const pos_t *>(T.px[in]);
         const pos_t *__restrict__ Yin = static_cast<const pos_t *>(T.py[in]);
-        const acc_t M = kF64 ? static_cast<acc_t>(sm.st.M) : static_cast<acc_t>(sm.st.M_f);
+        const acc_t M = Lp.shard ? static_cast<acc_t>(Lp.g_M)
+                                 : (kF64 ? static_cast<acc_t>(sm.st.M) : static_cast<acc_t>(sm.st.M_f));
         lik_t lv[kItems];
         pos_t xv[kItems], yv[kItems];
         if (eb + kItems <= cnt) {
@@ -1081,28 +1077,10 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
 #pragma unroll
             for (int m = 0; m < kItems; ++m) loc[m] = off + loc[m];
         }
-        // running max across threads: makes the tile-local prefix non-decreasing
-        acc_t mx = loc[kItems - 1];
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const acc_t y = __shfl_up_sync(0xffffffffu, mx, o);
-            if (lane >= o) mx = fmax(mx, y);
-        }
-        if (lane == 31) sm.warp_max[warp] = mx;
-        acc_t mex = __shfl_up_sync(0xffffffffu, mx, 1);
-        __syncthreads();
-        acc_t wmax = static_cast<acc_t>(0);
-#pragma unroll
-        for (int w = 0; w < kWarps; ++w) {
-            const acc_t v = sm.warp_max[w];
-            if (w < warp) wmax = fmax(wmax, v);
-        }
-        if (lane == 0) mex = wmax; else mex = fmax(mex, wmax);
-#pragma unroll
-        for (int m = 0; m < kItems; ++m) loc[m] = fmax(loc[m], mex);
-        // The tile aggregate is the clamped prefix at its last particle; the thread that
-        // holds it publishes it (tile 0: as the inclusive prefix) and leaves it for thread
-        // 0, which reads it after the next barrier.
+        // The tile aggregate is the prefix at its last particle; the thread that holds it
+        // publishes it at once (tile 0: as the inclusive prefix) and leaves it for thread 0,
+        // which reads it after the next barrier.  (Every prefix of the tile is later clamped
+        // to the exact boundary excl + aggregate.)
         {
             const int el = cnt - 1;
             if (el / kItems == tid) {
@@ -1115,6 +1093,16 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
                 sm.agg_x = ax;
             }
         }
+        // running max across threads, which makes the tile-local prefix non-decreasing: the
+        // warp part here, the block part after the next barrier (phase 1d)
+        acc_t mx = loc[kItems - 1];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const acc_t y = __shfl_up_sync(0xffffffffu, mx, o);
+            if (lane >= o) mx = fmax(mx, y);
+        }
+        if (lane == 31) sm.warp_max[warp] = mx;
+        mex = __shfl_up_sync(0xffffffffu, mx, 1);
     } else if (kPull && t > 0) {
         // The pull kernel's gather: offspring j = k0 + e takes the first particle a whose
         // CDF value reaches v_j (word j mod 4 of Philox(j / 4, t - 1, 1, tracker)); the
@@ -1195,6 +1183,23 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
                 by1 = fmaxf(by1, __shfl_xor_sync(0xffffffffu, by1, o));
             }
             if (lane == 0) { sm.box[warp][0] = bx0; sm.box[warp][1] = bx1; sm.box[warp][2] = by0; sm.box[warp][3] = by1; }
+        }
+        // the tracker table's share of this tile (after the aggregate is out)
+        if (gt) {
+            const uint64_t gtag = static_cast<uint64_t>(sm.st.epoch % 0x7fffffffu + 1u) << 32;
+            const int K = T.ntiles < static_cast<int>(gridDim.x) ? T.ntiles : static_cast<int>(gridDim.x);
+            const int gcells = gw * gh;
+            for (int c = lt + K * warp; lt < K && c < gcells; c += K * kWarps) {
+                const int px = gx0 + c % gw, py = gy0 + c / gw;
+                uint32_t payload;
+                if constexpr (Tr::kHalf) {
+                    const H v = half_lik<H>(T).warp_at(fv, px, py);
+                    payload = static_cast<uint32_t>(*reinterpret_cast<const unsigned short *>(&v));
+                } else {
+                    payload = warp_disk_sum(fv, px, py);
+                }
+                if (lane == 0) st_relaxed_u64(&T.gtab[PF_IDX(c, kTableMax)], gtag | payload);
+            }
         }
         // the resampling offset u0 of frame t - 1 (Philox tag 1, index 0), once per tile
         if (t > 0 && tid == 32) {
@@ -1306,10 +1311,22 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
     int Jr[kItems];           // J of the thread's elements (frames t > 0)
     int jb, je;               // the tile's offspring are j in [jb, je)
     if (!kPull && t > 0) {
-        // the step kernel's window phase ordered the tile aggregate (sm.agg_x) before this
-        // point; the CDF kernel has no window phase
+        // the step kernel's window phase ordered the tile aggregate (sm.agg_x) and the warps'
+        // running maxima before this point; the CDF kernel has no window phase
         if constexpr (kMode == kModeCdf) __syncthreads();
-        const acc_t invS = kF64 ? static_cast<acc_t>(sm.st.invS) : static_cast<acc_t>(sm.st.invS_f);
+        {   // the block part of the running max
+            acc_t wmax = static_cast<acc_t>(0);
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) {
+                const acc_t v = sm.warp_max[w];
+                if (w < warp) wmax = fmax(wmax, v);
+            }
+            if (lane == 0) mex = wmax; else mex = fmax(mex, wmax);
+#pragma unroll
+            for (int m = 0; m < kItems; ++m) loc[m] = fmax(loc[m], mex);
+        }
+        const acc_t invS = Lp.shard ? static_cast<acc_t>(Lp.g_invS)
+                                    : (kF64 ? static_cast<acc_t>(sm.st.invS) : static_cast<acc_t>(sm.st.invS_f));
 #ifdef PF_NAIVE_RESAMPLE
         const acc_t Sdiv = static_cast<acc_t>(sm.st.S);   // study build: a division per element
 #endif
@@ -1330,14 +1347,19 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
         else { excl = from_fixed_f(exclx); pend = from_fixed_f(endx); }
         if constexpr (kMode == kModeCdf) {
             acc_t *const cdf = static_cast<acc_t *>(T.cdf);
+            // a shard: its prefix starts at the other ranks' total before it and ends pinned
+            // at shard_hi, the value its successor starts from
+            const acc_t slo = static_cast<acc_t>(Lp.shard_lo), shi = static_cast<acc_t>(Lp.shard_hi);
+            if (Lp.shard) { excl = add_rn(excl, slo); pend = add_rn(pend, slo); }
 #pragma unroll
             for (int m = 0; m < kItems; ++m) {
                 const int e = eb + m;
                 if (e < cnt) {
                     const int k = k0 + e;
-                    const acc_t Pk = (e == cnt - 1) ? pend : fmin(add_rn(excl, loc[m]), pend);
+                    acc_t Pk = (e == cnt - 1) ? pend : fmin(add_rn(excl, loc[m]), pend);
+                    if (Lp.shard) Pk = (k == N - 1) ? shi : fmin(Pk, shi);
                     acc_t C = fmin(PF_NORM(Pk), static_cast<acc_t>(1));
-                    if (k == N - 1) C = static_cast<acc_t>(1);
+                    if (k == N - 1 && (!Lp.shard || Lp.shard_last)) C = static_cast<acc_t>(1);
                     cdf[PF_IDX(k, N)] = C;
                 }
             }
@@ -1349,16 +1371,44 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
 #else
         const acc_t nrm = invS;
 #endif
+        int jbl = 0, jprev0 = 0;   // the tile's first count; the count before the thread's first element
         if (T.resampler == kResampleStratified) {
             // (key_lo, key_hi, frame t - 1, tracker id) of the stratum offsets
             Strata<acc_t, true> str;
             str.init(N, static_cast<acc_t>(0.5), inv_n, sm.skeys);   // u0 = 1/2 only centres the estimate
-            strata_counts(str, loc, Jr, excl, pend, nrm, tid, lt, eb, cnt, k0, N, dbg_cdf, sm.jbeg, st);
+            strata_counts(str, loc, Jr, excl, pend, nrm, eb, cnt, k0, N, dbg_cdf, st);
+            jbl = (lt == 0) ? 0 : str.count_le(fmin(PF_NORM(excl), static_cast<acc_t>(1)));
+            // (see the systematic branch for the count before the thread's first element)
+            if (lane == 0 && tid != 0 && eb < cnt)
+                jprev0 = str.count_le(fmin(PF_NORM(fmin(add_rn(excl, mex), pend)), static_cast<acc_t>(1)));
+            if (tid == 0) jprev0 = jbl;
         } else {
             Strata<acc_t, false> str;
             str.init(N, u0, inv_n);
-            strata_counts(str, loc, Jr, excl, pend, nrm, tid, lt, eb, cnt, k0, N, dbg_cdf, sm.jbeg, st);
+            strata_counts(str, loc, Jr, excl, pend, nrm, eb, cnt, k0, N, dbg_cdf, st);
+            jbl = (lt == 0) ? 0 : str.count_le(fmin(PF_NORM(excl), static_cast<acc_t>(1)));
+            // The count before a warp's first element: that element's predecessor is the
+            // previous warp's last, whose clamped prefix is the running max of all preceding
+            // warps (the running max at lane 0 of this warp, mex), so the count is taken here
+            // from the same value, with the same arithmetic, as its owner takes it.
+            if (lane == 0 && tid != 0 && eb < cnt)
+                jprev0 = str.count_le(fmin(PF_NORM(fmin(add_rn(excl, mex), pend)), static_cast<acc_t>(1)));
+            if (tid == 0) jprev0 = jbl;
         }
+        // Every thread knows the tile's first count and the count before its first element,
+        // so the ancestor map's heads go in now (phase 1e fills the gaps): map[jp - jb] =
+        // 1 + element, jp the first offspring of each element that has offspring.
+        {
+            int jpt = __shfl_up_sync(0xffffffffu, Jr[kItems - 1], 1);
+            if (lane == 0) jpt = jprev0;
+#pragma unroll
+            for (int m = 0; m < kItems; ++m) {
+                const int jp = m ? Jr[m - 1] : jpt;
+                if (eb + m < cnt && Jr[m] > jp && jp - jbl < kMapMax)
+                    sm.map[PF_IDX(jp - jbl, kMapMax)] = static_cast<uint16_t>(eb + m + 1);
+            }
+        }
+        if (tid == 0) sm.jbeg = jbl;
         store_items(sm.J + eb, Jr);
         if (gt) fetch_table<P>(T, sm, wx0, wy0, ww, cells, fv, c1, c2D, den, st);
         __syncthreads();          // J, jbeg and the likelihood table are complete
@@ -1373,19 +1423,11 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
     const int nout = je - jb;
 
     // ------------------------------------------------------------ 1e. ancestor map
-    // map[j - jb] = 1 + tile element that is the ancestor of offspring j: a head at the
-    // first offspring of every element with offspring (the map was cleared at the start of
-    // the tile), then a block-wide running max fills the gaps.
+    // map[j - jb] = 1 + tile element that is the ancestor of offspring j: the heads (phase
+    // 1d; the map was cleared at the start of the tile), then a block-wide running max fills
+    // the gaps.
     const bool use_map = !kPull && (t > 0) && nout <= kMapMax;
     if (use_map) {
-        int jpt = __shfl_up_sync(0xffffffffu, Jr[kItems - 1], 1);   // J of element eb - 1
-        if (lane == 0) jpt = (tid == 0) ? jb : sm.J[eb - 1];
-#pragma unroll
-        for (int m = 0; m < kItems; ++m) {
-            const int jp = m ? Jr[m - 1] : jpt;
-            if (eb + m < cnt && Jr[m] > jp) sm.map[PF_IDX(jp - jb, kMapMax)] = static_cast<uint16_t>(eb + m + 1);
-        }
-        __syncthreads();
         // thread tid fills entries [tid*ch, tid*ch + ch), ch = 8 or 16 (16-byte vectors)
         const int nv = (nout > kThreads * 8) ? 2 : 1;
         uint4 *mv = reinterpret_cast<uint4 *>(sm.map) + tid * nv;
@@ -1430,6 +1472,7 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
     int32_t *__restrict__ dbg_anc = T.dbg_anc;
     const uint32_t tctr = static_cast<uint32_t>(t);
     const uint32_t trk_id = T.tracker_id, key_lo = T.key_lo, key_hi = T.key_hi;
+    const int jpair0 = static_cast<int>(T.j_base >> 1);   // global pair index of local pair 0
     Stats<acc_t> stats{neg_inf<acc_t>(), 0, 0, 0};
     const acc_t nxa_a = static_cast<acc_t>(nxi), nya_a = static_cast<acc_t>(nyi);
     const int axi = nxi, ayi = nyi;
@@ -1441,8 +1484,9 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
     const float shx = static_cast<float>(axi_anc - nxi), shy = static_cast<float>(ayi_anc - nyi);
     const float ix0 = T.init_xf - static_cast<float>(nxi), iy0 = T.init_yf - static_cast<float>(nyi);
 
-    // bounding box of the thread's new positions (for the next step's tracker table):
-    // absolute in REF64 / F32, anchor offsets in half2 lanes in F16 / BF16
+    // bounding box of the thread's new positions (for the next step's tracker table, when
+    // the tracker is large enough to use one): absolute in REF64 / F32, anchor offsets in
+    // half2 lanes in F16 / BF16
     acc_t pbx0 = static_cast<acc_t>(FLT_MAX), pbx1 = static_cast<acc_t>(-FLT_MAX);
     acc_t pby0 = static_cast<acc_t>(FLT_MAX), pby1 = static_cast<acc_t>(-FLT_MAX);
     using HB2 = typename HalfOps<H>::h2;
@@ -1487,8 +1531,9 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
                 }
             }
         }
-        // one Philox block per particle pair: words (x, y) for j0, (z, w) for j1
-        const uint4 wd = philox4x32_10(make_uint4(static_cast<uint32_t>(q), tctr, 0u, trk_id), key_lo, key_hi);
+        // one Philox block per particle pair: words (x, y) for j0, (z, w) for j1 (a shard's
+        // pairs are numbered globally)
+        const uint4 wd = philox4x32_10(make_uint4(static_cast<uint32_t>(q + jpair0), tctr, 0u, trk_id), key_lo, key_hi);
 
         if constexpr (!Tr::kHalf) {
             // ---------------- REF64 / F32: absolute positions, exact-integer likelihood
@@ -1541,8 +1586,10 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
                 Xout[PF_IDX(j1, N)] = x1; Yout[j1] = y1; Lout[j1] = L1;
             }
             stats_add2<false>(stats, v0, L0, x0 - nxa_a, y0 - nya_a, v1, L1, x1 - nxa_a, y1 - nya_a);
-            if (v0) { pbx0 = fmin(pbx0, x0); pbx1 = fmax(pbx1, x0); pby0 = fmin(pby0, y0); pby1 = fmax(pby1, y0); }
-            if (v1) { pbx0 = fmin(pbx0, x1); pbx1 = fmax(pbx1, x1); pby0 = fmin(pby0, y1); pby1 = fmax(pby1, y1); }
+            if (track_box) {
+                if (v0) { pbx0 = fmin(pbx0, x0); pbx1 = fmax(pbx1, x0); pby0 = fmin(pby0, y0); pby1 = fmax(pby1, y0); }
+                if (v1) { pbx0 = fmin(pbx0, x1); pbx1 = fmax(pbx1, x1); pby0 = fmin(pby0, y1); pby1 = fmax(pby1, y1); }
+            }
         } else {
             // ---------------- F16 / BF16: half2 lanes = particles (j0, j1), offsets from the anchor
             using OPS = HalfOps<H>;
@@ -1586,8 +1633,10 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
             stats_add2<true>(stats, v0, OPS::to_f(l0), OPS::lo(ox), OPS::lo(oy), v1, OPS::to_f(l1), OPS::hi(ox), OPS::hi(oy));
             // (a lane outside [jb, je) holds a draw around a valid ancestor: inside the reach
             // of the next step's table all the same)
-            hbx0 = __hmin2(hbx0, ox); hbx1 = __hmax2(hbx1, ox);
-            hby0 = __hmin2(hby0, oy); hby1 = __hmax2(hby1, oy);
+            if (track_box) {
+                hbx0 = __hmin2(hbx0, ox); hbx1 = __hmax2(hbx1, ox);
+                hby0 = __hmin2(hby0, oy); hby1 = __hmax2(hby1, oy);
+            }
         }
     };
     {
@@ -1617,14 +1666,16 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
         bb = make_float4(static_cast<float>(floor(pbx0)), static_cast<float>(ceil(pbx1)),
                          static_cast<float>(floor(pby0)), static_cast<float>(ceil(pby1)));
     }
-    warp_box(bb, sm);
+    if (track_box) warp_box(bb, sm);
     const Stats<acc_t> tot = block_stats<P>(stats, sm);
     if (tid == 0) {
-        bb = merge_warp_boxes(sm);
         TilePartial *p = &T.part[PF_IDX(lt, T.ntiles)];
-        const uint64_t btg = partial_tag(sm.st.epoch);
-        st_relaxed_v2(&p->b[0], btg | __float_as_uint(bb.x), btg | __float_as_uint(bb.y));
-        st_relaxed_v2(&p->b[2], btg | __float_as_uint(bb.z), btg | __float_as_uint(bb.w));
+        if (track_box) {
+            bb = merge_warp_boxes(sm);
+            const uint64_t btg = partial_tag(sm.st.epoch);
+            st_relaxed_v2(&p->b[0], btg | __float_as_uint(bb.x), btg | __float_as_uint(bb.y));
+            st_relaxed_v2(&p->b[2], btg | __float_as_uint(bb.z), btg | __float_as_uint(bb.w));
+        }
         uint32_t prev;
         if constexpr (kF64) {
             p->d[0] = tot.m;
@@ -1642,7 +1693,7 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
         sm.last = (prev == static_cast<uint32_t>(T.ntiles - 1)) ? 1u : 0u;
     }
     __syncthreads();
-    if (sm.last) finalize_tracker<P>(T, st, sm, Lp.est_out ? Lp.est_out + 2 * ti : nullptr);
+    if (sm.last) finalize_tracker<P>(T, st, sm, Lp.est_out ? Lp.est_out + 2 * ti : nullptr, track_box);
 }
 
 // CTAs per SM the register allocation must allow: 1024 threads per SM (64 registers a
@@ -1801,6 +1852,58 @@ int launch_step(int precision, const StepLaunch &L, int grid, void *stream) {
 int launch_pull(int precision, const StepLaunch &L, int grid, bool with_cdf, void *stream) {
     const int rc = with_cdf ? launch_mode<kModeCdf>(precision, L, grid, stream) : 0;
     return rc != 0 ? rc : launch_mode<kModePull>(precision, L, grid, stream);
+}
+
+int launch_cdf(int precision, const StepLaunch &L, int grid, void *stream) {
+    return launch_mode<kModeCdf>(precision, L, grid, stream);
+}
+
+// A shard's offspring run (see pf_internal.h): one thread per element of the shard's CDF,
+// the count at its predecessor (J(c_lo) before the first) and at itself over the global
+// strata, and the element's position copied to every offspring slot in between.
+template <typename A>
+__global__ void shard_expand_kernel(const A *C, const A *x, const A *y, int64_t n, int64_t n_global, int64_t t,
+                                    uint32_t key_lo, uint32_t key_hi, uint32_t tracker, A c_lo, A *sx, A *sy,
+                                    int64_t cap, int64_t *run, uint32_t *status) {
+    const uint32_t w0 = philox4x32_10(make_uint4(0u, static_cast<uint32_t>(t - 1), 1u, tracker), key_lo, key_hi).x;
+    const A u0 = sizeof(A) == 8 ? static_cast<A>(uniform_f64(w0)) : static_cast<A>(uniform_f32(w0));
+    const A inv_n = sizeof(A) == 8 ? static_cast<A>(1.0 / static_cast<double>(n_global))
+                                   : static_cast<A>(1.0f / static_cast<float>(n_global));
+    Strata<A, false> str;
+    str.init(static_cast<int>(n_global), u0, inv_n);
+    const int64_t jb = str.count_le(c_lo);
+    for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < n;
+         k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t j0 = k == 0 ? jb : str.count_le(C[k - 1]);
+        const int64_t j1 = str.count_le(C[k]);
+        const A xa = x[k], ya = y[k];
+        for (int64_t j = j0; j < j1; ++j) {
+            const int64_t i = j - jb;
+            if (i >= 0 && i < cap) { sx[i] = xa; sy[i] = ya; }
+            else atomicOr(status, 1u);
+        }
+        if (k == 0) run[0] = jb;
+        if (k == n - 1) run[1] = j1;
+    }
+}
+
+int launch_shard_expand(int precision, const void *cdf, const void *x, const void *y, int64_t n, int64_t n_global,
+                        int64_t t, uint32_t key_lo, uint32_t key_hi, uint32_t tracker, double c_lo, void *sx,
+                        void *sy, int64_t cap, int64_t *run, uint32_t *status, void *stream) {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const unsigned blocks = static_cast<unsigned>(std::min<int64_t>((n + 255) / 256, 4096));
+    if (precision == 0)
+        shard_expand_kernel<double><<<blocks, 256, 0, s>>>(
+            static_cast<const double *>(cdf), static_cast<const double *>(x), static_cast<const double *>(y), n, n_global,
+            t, key_lo, key_hi, tracker, c_lo, static_cast<double *>(sx), static_cast<double *>(sy), cap, run, status);
+    else if (precision == 1)
+        shard_expand_kernel<float><<<blocks, 256, 0, s>>>(
+            static_cast<const float *>(cdf), static_cast<const float *>(x), static_cast<const float *>(y), n, n_global,
+            t, key_lo, key_hi, tracker, static_cast<float>(c_lo), static_cast<float *>(sx), static_cast<float *>(sy),
+            cap, run, status);
+    else
+        return -1;
+    return static_cast<int>(cudaGetLastError());
 }
 
 int launch_wait_probe(void *d_desc, void *d_state, uint32_t limit, void *stream) {
