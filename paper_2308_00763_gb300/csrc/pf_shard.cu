@@ -185,6 +185,8 @@ extern "C" pf_status pf_shard_create(const pf_config *cfg, int32_t rank, int32_t
     h->h_frame->active = 1;
     err = cudaMemcpyAsync(h->d_trk, &T, sizeof T, cudaMemcpyHostToDevice, h->stream);
     if (err == cudaSuccess)
+        err = cudaMemcpyAsync(h->d_frame, h->h_frame, sizeof(FrameRef), cudaMemcpyHostToDevice, h->stream);
+    if (err == cudaSuccess)
         err = cudaMemcpyAsync(T.state, h->h_state, sizeof(TrackerState), cudaMemcpyHostToDevice, h->stream);
     if (err == cudaSuccess) err = cudaMemsetAsync(h->d_ticket, 0, sizeof(uint32_t), h->stream);
     if (err == cudaSuccess) {
