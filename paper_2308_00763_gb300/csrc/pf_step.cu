@@ -882,6 +882,10 @@ __device__ __forceinline__ void strata_counts(const Str &str, const A (&loc)[kIt
 // pull kernel (resampling from T.cdf, phases 2-5), launched in that order; the pull kernel
 // also takes the Gumbel-max, Metropolis and rejection trackers (ancestors from T.anc).
 constexpr int kModeStep = 0, kModeCdf = 1, kModePull = 2;
+// The step kernel with the tracker table (phase 0) and the bounding box that sizes it: a
+// separate instantiation, launched for a tracker of at least two waves of tiles, so that the
+// common launch carries none of its code or registers.
+constexpr int kModeStepBig = 3;
 
 // One tile of a launch in mode kMode (trackers of the other modes are skipped).
 template <int P, int kMode>
@@ -980,11 +984,11 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
     // min(ntiles, grid) tiles build it, one cell per warp; every cell carries this launch's
     // tag, and a tile that finds a cell not yet built computes it itself (same operations,
     // same bits), so no tile waits for another.
-    const bool track_box = kMode == kModeStep && T.gtab != nullptr &&
+    const bool track_box = kMode == kModeStepBig && T.gtab != nullptr &&
                            T.ntiles >= 2 * static_cast<int>(gridDim.x);
     bool gt = false;
     int gx0 = 0, gy0 = 0, gw = 0, gh = 0;
-    if constexpr (kMode == kModeStep) {
+    if constexpr (kMode == kModeStepBig) {
         const float b0 = sm.st.bb_x0, b1 = sm.st.bb_x1, c0 = sm.st.bb_y0, c1b = sm.st.bb_y1;
         if (track_box && b0 <= b1 && c0 <= c1b && fabsf(b0) < 1.0e6f && fabsf(b1) < 1.0e6f &&
             fabsf(c0) < 1.0e6f && fabsf(c1b) < 1.0e6f) {
@@ -1751,6 +1755,7 @@ int configure_and_grid(int total_tiles) {
     if (sizeof(StepSmem<P>) + 1024 > 228 * 1024) return -1;
     const int bytes = static_cast<int>(sizeof(StepSmem<P>));
     if (cudaFuncSetAttribute(step_kernel<P, kModeStep>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess ||
+        cudaFuncSetAttribute(step_kernel<P, kModeStepBig>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess ||
         cudaFuncSetAttribute(step_kernel<P, kModeCdf>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess ||
         cudaFuncSetAttribute(step_kernel<P, kModePull>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess)
         return -1;
@@ -1846,6 +1851,9 @@ int launch_mode(int precision, const StepLaunch &L, int grid, void *stream) {
 }
 
 int launch_step(int precision, const StepLaunch &L, int grid, void *stream) {
+    // a single tracker of at least two waves of tiles takes the instantiation with the
+    // tracker table (the kernel checks the condition again per tile)
+    if (L.ntrk == 1 && L.total_tiles >= 2 * grid) return launch_mode<kModeStepBig>(precision, L, grid, stream);
     return launch_mode<kModeStep>(precision, L, grid, stream);
 }
 
