@@ -154,12 +154,14 @@ __device__ uint32_t wait_desc(const LookbackDesc *d, uint64_t tag, TrackerState 
                               uint32_t limit = kSpinLimit) {
     uint32_t ns = 8;
     for (uint32_t it = 0; it < limit; ++it) {
+        // all six words in one round trip (the predecessor has usually published only its
+        // aggregate when the tiles of a wave look back together)
         uint64_t a0, a1, i0, i1, w4, w5;
+        ld_relaxed_v2(&d->w[0], a0, a1);
         ld_relaxed_v2(&d->w[2], i0, i1);
         ld_relaxed_v2(&d->w[4], w4, w5);
         const uint64_t hm = ~kPayload48;
         if ((i0 & hm) == tag && (i1 & hm) == tag && (w5 & hm) == tag) { v = desc_value(i0, i1, w5); return 2u; }
-        ld_relaxed_v2(&d->w[0], a0, a1);
         if ((a0 & hm) == tag && (a1 & hm) == tag && (w4 & hm) == tag) { v = desc_value(a0, a1, w4); return 1u; }
         if ((it & 1023u) == 1023u && timed_out(st)) return 0u;   // another wait already gave up
         __nanosleep(ns);
@@ -877,6 +879,24 @@ __device__ __forceinline__ void strata_counts(const Str &str, const A (&loc)[kIt
     }
 }
 
+// The descriptor, state and frame reference of launch position ti (slot `slot`) into shared
+// memory, by the whole block (the caller synchronises).
+template <int P>
+__device__ __forceinline__ void load_descriptor(const StepLaunch &Lp, int slot, int ti, StepSmem<P> &sm) {
+    const uint32_t *src_t = reinterpret_cast<const uint32_t *>(Lp.trk + slot);
+    const uint32_t *src_s = reinterpret_cast<const uint32_t *>(Lp.states + slot);
+    const uint32_t *src_f = reinterpret_cast<const uint32_t *>(Lp.frames + ti);
+    uint32_t *dt = reinterpret_cast<uint32_t *>(&sm.trk);
+    uint32_t *ds = reinterpret_cast<uint32_t *>(&sm.st);
+    uint32_t *df = reinterpret_cast<uint32_t *>(&sm.fr);
+    constexpr int nt = sizeof(TrackerDev) / 4, ns = sizeof(TrackerState) / 4, nf = sizeof(FrameRef) / 4;
+    for (int i = threadIdx.x; i < nt + ns + nf; i += kThreads) {
+        if (i < nt) dt[i] = __ldg(src_t + i);
+        else if (i < nt + ns) ds[i - nt] = __ldcg(src_s + i - nt);
+        else df[i - nt - ns] = __ldcg(src_f + i - nt - ns);
+    }
+}
+
 // Kernel modes: the step kernel (systematic and stratified trackers, every phase), and for
 // multinomial trackers the CDF kernel (phase 1 up to the CDF, written to T.cdf) and the
 // pull kernel (resampling from T.cdf, phases 2-5), launched in that order; the pull kernel
@@ -918,18 +938,7 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
     // and kept for the CTA's later tiles of the same tracker (none of them changes
     // before the tracker's last tile of this launch has finished)
     if (ti != sm.cached) {
-        const uint32_t *src_t = reinterpret_cast<const uint32_t *>(Lp.trk + slot);
-        const uint32_t *src_s = reinterpret_cast<const uint32_t *>(st);
-        const uint32_t *src_f = reinterpret_cast<const uint32_t *>(Lp.frames + ti);
-        uint32_t *dt = reinterpret_cast<uint32_t *>(&sm.trk);
-        uint32_t *ds = reinterpret_cast<uint32_t *>(&sm.st);
-        uint32_t *df = reinterpret_cast<uint32_t *>(&sm.fr);
-        constexpr int nt = sizeof(TrackerDev) / 4, ns = sizeof(TrackerState) / 4, nf = sizeof(FrameRef) / 4;
-        for (int i = tid; i < nt + ns + nf; i += kThreads) {
-            if (i < nt) dt[i] = __ldg(src_t + i);
-            else if (i < nt + ns) ds[i - nt] = __ldcg(src_s + i - nt);
-            else df[i - nt - ns] = __ldcg(src_f + i - nt - ns);
-        }
+        load_descriptor(Lp, slot, ti, sm);
         __syncthreads();
         if (tid == 0) sm.cached = ti;
     }
@@ -1719,6 +1728,11 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<P>::value) step_kernel(con
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (threadIdx.x == 0) sm.cached = -1;
+    if (Lp.ntrk == 1) {
+        // one tracker: its descriptor and state load while the first ticket is drawn
+        load_descriptor(Lp, Lp.slot_of ? __ldg(&Lp.slot_of[0]) : 0, 0, sm);
+        if (threadIdx.x == 0) sm.cached = 0;
+    }
     for (;;) {
         if (threadIdx.x == 0) sm.ticket = atomicAdd(Lp.ticket, 1u);
         __syncthreads();
