@@ -243,16 +243,19 @@ __device__ __forceinline__ Stats<A> stats_merge(const Stats<A> &a, const Stats<A
     return r;
 }
 
-// Two particles at once (a particle whose flag is false is skipped): one rescale check.
+// Two particles at once (a particle whose flag is false is skipped).  The rescale to a new
+// maximum is applied without a branch: when the maximum does not move the factor is
+// wexp(0) = 1 exactly (and 1 while no particle has been seen), so the sums are unchanged,
+// the same bits as skipping it.
 template <bool F, typename A>
 __device__ __forceinline__ void stats_add2(Stats<A> &a, bool v0, A L0, A dx0, A dy0, bool v1, A L1, A dx1, A dy1) {
     const A l0 = v0 ? L0 : neg_inf<A>(), l1 = v1 ? L1 : neg_inf<A>();
     const A mx = l0 > l1 ? l0 : l1;
-    if (mx > a.m) {
-        const A sc = (a.m == neg_inf<A>()) ? static_cast<A>(0) : wexp<F>(a.m - mx);
-        a.s *= sc; a.sx *= sc; a.sy *= sc;
-        a.m = mx;
-    }
+    const A nm = mx > a.m ? mx : a.m;
+    const A sc = (nm == neg_inf<A>()) ? static_cast<A>(1)
+                                      : ((a.m == neg_inf<A>()) ? static_cast<A>(0) : wexp<F>(a.m - nm));
+    a.s *= sc; a.sx *= sc; a.sy *= sc;
+    a.m = nm;
     const A e0 = v0 ? wexp<F>(l0 - a.m) : static_cast<A>(0);
     const A e1 = v1 ? wexp<F>(l1 - a.m) : static_cast<A>(0);
     a.s += e0 + e1;
@@ -600,15 +603,28 @@ struct __align__(16) StepSmem {
 // (butterfly); warp 0 does the same over the warps' results.  Max, rescale and sums run
 // in a fixed order, so the result is deterministic.  The caller synchronises before
 // sm.red is written again.
+// Warp max / min of floats by redux.sync on an order-preserving integer image (the sign bit
+// kept, the other bits flipped for negative values); exact, -inf included (no NaN here).
+__device__ __forceinline__ int float_key(float x) {
+    const int b = __float_as_int(x);
+    return b ^ ((b >> 31) & 0x7fffffff);
+}
+__device__ __forceinline__ float key_float(int k) { return __int_as_float(k ^ ((k >> 31) & 0x7fffffff)); }
+__device__ __forceinline__ float warp_max(float x) { return key_float(__reduce_max_sync(0xffffffffu, float_key(x))); }
+__device__ __forceinline__ float warp_min(float x) { return key_float(__reduce_min_sync(0xffffffffu, float_key(x))); }
+__device__ __forceinline__ double warp_max(double x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double y = __shfl_xor_sync(0xffffffffu, x, o);
+        x = y > x ? y : x;
+    }
+    return x;
+}
+
 template <int P, typename A>
 __device__ __forceinline__ Stats<A> warp_stats(Stats<A> v) {
     constexpr bool F = Prec<P>::kHalf;
-    A m = v.m;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const A y = __shfl_xor_sync(0xffffffffu, m, o);
-        m = y > m ? y : m;
-    }
+    const A m = warp_max(v.m);
     if (m == neg_inf<A>()) return Stats<A>{m, 0, 0, 0};
     const A sc = (v.m == neg_inf<A>()) ? static_cast<A>(0) : wexp<F>(v.m - m);
     A s = mul_rn(v.s, sc), sx = mul_rn(v.sx, sc), sy = mul_rn(v.sy, sc);
@@ -625,13 +641,7 @@ __device__ __forceinline__ Stats<A> warp_stats(Stats<A> v) {
 // merge_warp_boxes after the next barrier.
 template <int P>
 __device__ __forceinline__ void warp_box(float4 b, StepSmem<P> &sm) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        b.x = fminf(b.x, __shfl_xor_sync(0xffffffffu, b.x, o));
-        b.y = fmaxf(b.y, __shfl_xor_sync(0xffffffffu, b.y, o));
-        b.z = fminf(b.z, __shfl_xor_sync(0xffffffffu, b.z, o));
-        b.w = fmaxf(b.w, __shfl_xor_sync(0xffffffffu, b.w, o));
-    }
+    b = make_float4(warp_min(b.x), warp_max(b.y), warp_min(b.z), warp_max(b.w));
     if ((threadIdx.x & 31) == 0) *reinterpret_cast<float4 *>(sm.box[threadIdx.x >> 5]) = b;
 }
 template <int P>
@@ -1028,14 +1038,22 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
         const acc_t M = Lp.shard ? static_cast<acc_t>(Lp.g_M)
                                  : (kF64 ? static_cast<acc_t>(sm.st.M) : static_cast<acc_t>(sm.st.M_f));
         lik_t lv[kItems];
-        pos_t xv[kItems], yv[kItems];
+        // the thread's kItems positions as raw 16-byte vectors: copied to shared memory as
+        // they are (the offspring loop reads its ancestors there), unpacked only where the
+        // window's bounding box needs a value
+        constexpr int kVp = static_cast<int>(sizeof(pos_t)) * kItems / 16;
+        uint4 xr[kVp], yr[kVp];
         if (eb + kItems <= cnt) {
             // kItems consecutive values of each array, 16-byte aligned (k0 and eb are
             // multiples of kItems = 8 and the buffers are 16-byte aligned)
             load_items(lv, Lin + k0 + eb);
-            load_items(xv, Xin + k0 + eb);
-            load_items(yv, Yin + k0 + eb);
+#pragma unroll
+            for (int k = 0; k < kVp; ++k) {
+                xr[k] = reinterpret_cast<const uint4 *>(Xin + k0 + eb)[k];
+                yr[k] = reinterpret_cast<const uint4 *>(Yin + k0 + eb)[k];
+            }
         } else {
+            pos_t xv[kItems], yv[kItems];
 #pragma unroll
             for (int m = 0; m < kItems; ++m) {
                 const int e = eb + m;
@@ -1043,10 +1061,16 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
                 xv[m] = (e < cnt) ? Xin[k0 + e] : pos_t{};
                 yv[m] = (e < cnt) ? Yin[k0 + e] : pos_t{};
             }
+#pragma unroll
+            for (int k = 0; k < kVp; ++k) { xr[k] = make_uint4(0u, 0u, 0u, 0u); yr[k] = xr[k]; }
+#pragma unroll
+            for (int m = 0; m < kItems; ++m) { Bits<pos_t>::put(xr, m, xv[m]); Bits<pos_t>::put(yr, m, yv[m]); }
         }
-        // the offspring loop reads its ancestors' positions from shared memory
-        store_items(sm.ax + eb, xv);
-        store_items(sm.ay + eb, yv);
+#pragma unroll
+        for (int k = 0; k < kVp; ++k) {
+            reinterpret_cast<uint4 *>(sm.ax + eb)[k] = xr[k];
+            reinterpret_cast<uint4 *>(sm.ay + eb)[k] = yr[k];
+        }
         // clear the ancestor map (its heads are written after the strata are counted)
 #pragma unroll
         for (int i = 0; i < kMapMax / 8 / kThreads; ++i)
@@ -1060,8 +1084,8 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
             acc_t v = static_cast<acc_t>(0);
             if (e < cnt) v = wexp<Tr::kHalf>(to_acc(lv[m]) - M);
             if (!gt && v > static_cast<acc_t>(9.3132257461547852e-10)) {   // weight above 2^-30 of the max
-                const float xa = static_cast<float>(to_acc(xv[m])) + sx;
-                const float ya = static_cast<float>(to_acc(yv[m])) + sy;
+                const float xa = static_cast<float>(to_acc(Bits<pos_t>::get(xr, m))) + sx;
+                const float ya = static_cast<float>(to_acc(Bits<pos_t>::get(yr, m))) + sy;
                 bx0 = fminf(bx0, xa); bx1 = fmaxf(bx1, xa);
                 by0 = fminf(by0, ya); by1 = fmaxf(by1, ya);
             }
@@ -1187,16 +1211,7 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
     // lookback, so that the predecessors publish meanwhile.  (The pull kernel sizes it by
     // the gathered ancestors; the CDF kernel has none.)
     if constexpr (kMode != kModeCdf) {
-        if (!gt) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                bx0 = fminf(bx0, __shfl_xor_sync(0xffffffffu, bx0, o));
-                bx1 = fmaxf(bx1, __shfl_xor_sync(0xffffffffu, bx1, o));
-                by0 = fminf(by0, __shfl_xor_sync(0xffffffffu, by0, o));
-                by1 = fmaxf(by1, __shfl_xor_sync(0xffffffffu, by1, o));
-            }
-            if (lane == 0) { sm.box[warp][0] = bx0; sm.box[warp][1] = bx1; sm.box[warp][2] = by0; sm.box[warp][3] = by1; }
-        }
+        if (!gt) warp_box(make_float4(bx0, bx1, by0, by1), sm);
         // the tracker table's share of this tile (after the aggregate is out)
         if (gt) {
             const uint64_t gtag = static_cast<uint64_t>(sm.st.epoch % 0x7fffffffu + 1u) << 32;
