@@ -573,6 +573,10 @@ struct __align__(16) StepSmem {
     union {
         uint16_t pre[kRoiMax];      // integer form: row prefix sums of the staged region
         lik_t term[Tr::kHalf ? kRoiMax : 1];   // half form: per-pixel Eq. 4 terms of the staged region
+        // F16 half accumulation, staged regions of up to kRoiMax / 2 pixels: the terms of
+        // pixels x and x + 1 of a row side by side, so one half2 addition advances the sums
+        // of two neighbouring cells
+        __half2 term2[P == 2 ? kRoiMax / 2 : 1];
     } u;
     alignas(16) uint16_t map[kMapMax];   // ancestor (tile element + 1) of each offspring
     alignas(16) int warp_imax[kWarps];
@@ -1289,8 +1293,24 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
         // stage the frame region the window's templates cover (clamped to the frame);
         // warp w takes rows w, w + kWarps, ...; its lanes walk the row
         const int rx0 = wx0 - r, ry0 = wy0 - r, rw = ww + 2 * r, rh = wh + 2 * r;
+        bool paired = false;
+        if constexpr (P == 2) paired = hk.half_acc && rw * rh <= kRoiMax / 2;
         for (int yy = warp; yy < rh; yy += kWarps) {
             const uint8_t *row = fv.p + static_cast<int64_t>(clampi(ry0 + yy, 0, fv.H - 1)) * fv.pitch;
+            if constexpr (P == 2) {
+                if (paired) {
+                    // term2[x] = (term x, term x + 1): the right neighbour from the next lane
+                    // (lane 31 loads it; x + 1 = rw reads the clamped pixel after the row)
+                    for (int x0 = 0; x0 < rw; x0 += 32) {
+                        const int xx = x0 + lane;
+                        const H tx = hk.term(__ldg(row + clampi(rx0 + xx, 0, fv.W - 1)));
+                        H tn = __shfl_down_sync(0xffffffffu, tx, 1);
+                        if (lane == 31) tn = hk.term(__ldg(row + clampi(rx0 + xx + 1, 0, fv.W - 1)));
+                        if (xx < rw) sm.u.term2[PF_IDX(yy * rw + xx, kRoiMax / 2)] = __halves2half2(tx, tn);
+                    }
+                    continue;
+                }
+            }
             if constexpr (Tr::kHalf) {
                 for (int xx = lane; xx < rw; xx += 32)
                     sm.u.term[PF_IDX(yy * rw + xx, kRoiMax)] = hk.term(__ldg(row + clampi(rx0 + xx, 0, fv.W - 1)));
@@ -1315,8 +1335,31 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
             }
         }
         __syncthreads();
+        if (paired) {
+            // two neighbouring cells (cx, cx + 1) a thread, one in each half2 lane: each lane
+            // performs its cell's additions of from_terms in the same order (an odd row's
+            // last pair computes a cell past the row and drops it)
+            const int hpr = (ww + 1) >> 1;
+            for (int pi = tid; pi < hpr * wh; pi += kThreads) {
+                const int cy = pi / hpr, cx = 2 * (pi - cy * hpr);
+                __half2 acc = __float2half2_rn(0.0f);
+                for (int i = 0; i <= 2 * r; ++i) {
+                    const int hw = sm.w[i];
+                    const int b = (cy + i) * rw + cx + r;
+                    __half2 rs = __float2half2_rn(0.0f);
+#pragma unroll 4
+                    for (int dx = -hw; dx <= hw; ++dx) rs = __hadd2(rs, sm.u.term2[PF_IDX(b + dx, kRoiMax / 2)]);
+                    acc = __hadd2(acc, rs);
+                }
+                const int c = cy * ww + cx;
+                const __half2 a2 = acc;
+                lik_t *tab = sm.table;
+                tab[PF_IDX(c, kTableMax)] = *reinterpret_cast<const lik_t *>(&a2);
+                if (cx + 1 < ww) tab[PF_IDX(c + 1, kTableMax)] = reinterpret_cast<const lik_t *>(&a2)[1];
+            }
+        }
         const int wdiv = kMode != kModeCdf ? ww : 1;    // (no table in the CDF kernel)
-        for (int c = tid, cy = tid / wdiv, cx = tid - (tid / wdiv) * wdiv; c < cells; c += kThreads) {
+        for (int c = paired ? cells : tid, cy = tid / wdiv, cx = tid - (tid / wdiv) * wdiv; c < cells; c += kThreads) {
             if constexpr (Tr::kHalf) {
                 sm.table[PF_IDX(c, kTableMax)] = hk.from_terms(sm.u.term, rw, sm.w, r, cx, cy);
             } else {
