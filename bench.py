@@ -73,6 +73,9 @@ def _args():
     p.add_argument("--core-peaks", action="store_true",
                    help="measure the CUDA-core throughputs (FP32/FP16x2/BF16x2/FP64 FMA, ex2, IMAD, logic, "
                         "shared loads) with the microbenchmark; one JSON object")
+    p.add_argument("--profile-target", nargs=5, metavar=("PREC", "N", "SIZE", "RADIUS", "FRAMES"),
+                   help="profiling target: step one PREC tracker of N particles through FRAMES frames of a "
+                        "SIZE x SIZE synthetic video with disk radius RADIUS, then exit (no timing)")
     p.add_argument("--gumbel", type=int, default=0, metavar="N",
                    help="Gumbel-max study only: time Gumbel-max, systematic and multinomial resampling of "
                         "an N-particle tracker (N <= 2^16) in --precision on the headline video; one JSON object")
@@ -884,6 +887,24 @@ def _tpb_sweep():
     return 0
 
 
+def _profile_target(prec, n, size, radius, frames):
+    """A few frames of one tracker, for an ncu capture of the step kernel at a given size."""
+    import torch
+    import paper_2308_00763_gb300 as pf
+    from paper_2308_00763_gb300 import synth
+    n, size, radius, frames = int(n), int(size), int(radius), int(frames)
+    v = synth.make_video(size, size, frames, radius, noise=NOISE_, seed=SEED_)
+    fr = torch.from_numpy(v.frames).cuda()
+    f = pf.Filter(size, size, n, radius, prec, init=tuple(v.centres[0]), seed=SEED_)
+    for t in range(frames):
+        f.step(fr[t])
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_target": prec, "N": n, "size": size, "radius": radius, "frames": frames,
+                      "last_estimate": f.estimates(frames - 1, 1).tolist()[0]}))
+    f.close()
+    return 0
+
+
 def main():
     args = _args()
     if args.tpb_child:
@@ -892,6 +913,8 @@ def main():
         return _tpb_sweep()
     if args.core_peaks:
         return _run_core_peaks()
+    if args.profile_target:
+        return _profile_target(*args.profile_target)
     if args.gumbel:
         import torch
         print(json.dumps(_gumbel_max(torch.device("cuda"), torch.cuda.Stream(), {args.precision: (args.gumbel,)})))
