@@ -249,7 +249,11 @@ pf_status pf_set_state(pf_filter *f, const void *host_buf, size_t bytes);
  * ancestor index a_j of every particle j of that step (int32[N]; undefined at frame
  * 0), `which` = 1 the CDF C_k of the previous frame as the step computed it (double[N]
  * for REF64, float[N] otherwise; PF_ERR_ARG for the schemes that build no CDF: Gumbel-max,
- * Metropolis, rejection).  Synchronises.  host_buf: host pointer of `bytes`.
+ * Metropolis, rejection), `which` = 2 the likelihood-table window of every tile of the
+ * step (x0, y0, width, height in pixels as int32, width 0 when the tile built none; the
+ * tracker has ntiles <= ceil(N / 1024) tiles, so `bytes` >= 16 * ceil(N / 1024) always
+ * suffices; the 4-word entries of the ntiles tiles are written, the rest of the buffer is
+ * left as it was).  Synchronises.  host_buf: host pointer of `bytes`.
  * Errors: PF_ERR_STATE (no debug arrays), PF_ERR_ARG, PF_ERR_CUDA. */
 pf_status pf_get_debug(pf_filter *f, int32_t which, void *host_buf, size_t bytes);
 

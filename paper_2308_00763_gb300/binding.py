@@ -719,6 +719,11 @@ class Filter:
     def debug(self, which):
         if which == 0:
             return pf_get_debug(self.h, 0, self.N, np.int32)
+        if which == 2:   # per-tile windows (x0, y0, width, height): rows of the tiles the step used
+            w = np.full(4 * (-(-self.N // 1024)), -1, np.int32)
+            _check(lib().pf_get_debug(self.h, 2, w.ctypes.data_as(_P), w.nbytes), "pf_get_debug")
+            w = w.reshape(-1, 4)
+            return w[w[:, 2] >= 0]
         return pf_get_debug(self.h, 1, self.N, np.float64 if self.precision == PF_REF64 else np.float32)
 
     def close(self):

@@ -134,6 +134,7 @@ struct TrackerDev {
     void *px[2], *py[2], *pl[2];
     int32_t *dbg_anc;          // NULL unless PF_FLAG_DEBUG_ARRAYS
     void *dbg_cdf;
+    int32_t *dbg_win;          // NULL unless PF_FLAG_DEBUG_ARRAYS: each tile's table window [4 * ntiles]
     void *cdf;                 // multinomial: the normalised CDF of the previous frame [N] (FP64 / FP32)
     int32_t *anc;              // Gumbel-max, Metropolis, rejection: the ancestor of every offspring [N]
     LookbackDesc *look;

@@ -202,7 +202,7 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
     const size_t pb = pos_bytes(e.prec);
     const size_t cdf_b = e.prec == PF_REF64 ? 8 : 4;
     Arena a;
-    struct Off { size_t px[2], py[2], pl[2], look, part, done, state, est, stat, dbga, dbgc, cdf, gtab; };
+    struct Off { size_t px[2], py[2], pl[2], look, part, done, state, est, stat, dbga, dbgc, dbgw, cdf, gtab; };
     std::vector<Off> off(n);
     // the trackers' states form one array (the kernel indexes it by tracker)
     const size_t states_off = a.take(sizeof(TrackerState) * n);
@@ -244,6 +244,7 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
         if (c.flags & PF_FLAG_DEBUG_ARRAYS) {
             o.dbga = a.take(sizeof(int32_t) * N);
             if (!multi) o.dbgc = a.take(cdf_b * N);
+            o.dbgw = a.take(sizeof(int32_t) * 4 * static_cast<size_t>(nt));
         }
         if (multi) o.cdf = a.take((given ? sizeof(int32_t) : cdf_b) * N + 16);
         if (given) {
@@ -317,6 +318,7 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
         if (e.cfg[i].flags & PF_FLAG_DEBUG_ARRAYS) {
             T.dbg_anc = reinterpret_cast<int32_t *>(e.d_arena + o.dbga);
             T.dbg_cdf = e.d_arena + o.dbgc;
+            T.dbg_win = reinterpret_cast<int32_t *>(e.d_arena + o.dbgw);
         }
         if (e.cfg[i].resampler == PF_RESAMPLE_MULTINOMIAL) {
             // written by the CDF kernel, read by the pull kernel and by pf_get_debug
@@ -835,6 +837,14 @@ pf_status pf_get_debug(pf_filter *f, int32_t which, void *host_buf, size_t bytes
     const TrackerDev &T = e.h_trk[0];
     if (!T.dbg_anc) return PF_ERR_STATE;
     if (which == 1 && !T.dbg_cdf) return PF_ERR_ARG;   // Gumbel-max, Metropolis, rejection: no CDF
+    if (which == 2) {   // per-tile windows
+        const size_t wb = sizeof(int32_t) * 4 * static_cast<size_t>(T.ntiles);
+        if (bytes < wb) return PF_ERR_ARG;
+        cudaError_t err = cudaStreamSynchronize(e.stream);
+        if (err == cudaSuccess) err = cudaMemcpy(host_buf, T.dbg_win, wb, cudaMemcpyDeviceToHost);
+        if (err != cudaSuccess) { cudaGetLastError(); return e.fail(PF_ERR_CUDA); }
+        return PF_OK;
+    }
     const size_t elem = which == 0 ? 4 : (e.prec == PF_REF64 ? 8 : 4);
     if (which < 0 || which > 1 || bytes < elem * static_cast<size_t>(T.N)) return PF_ERR_ARG;
     cudaError_t err = cudaStreamSynchronize(e.stream);

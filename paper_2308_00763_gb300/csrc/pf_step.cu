@@ -641,12 +641,13 @@ __device__ __forceinline__ Stats<A> warp_stats(Stats<A> v) {
     return Stats<A>{m, s, sx, sy};
 }
 
-// Warp-level min / max of a bounding box (x0, x1, y0, y1); lane 0 leaves it in sm.box for
-// merge_warp_boxes after the next barrier.
+// Warp-level min / max of a bounding box (x0, x1, y0, y1), returned to every lane; lane 0
+// also leaves it in sm.box for merge_warp_boxes after the next barrier.
 template <int P>
-__device__ __forceinline__ void warp_box(float4 b, StepSmem<P> &sm) {
+__device__ __forceinline__ float4 warp_box(float4 b, StepSmem<P> &sm) {
     b = make_float4(warp_min(b.x), warp_max(b.y), warp_min(b.z), warp_max(b.w));
     if ((threadIdx.x & 31) == 0) *reinterpret_cast<float4 *>(sm.box[threadIdx.x >> 5]) = b;
+    return b;
 }
 template <int P>
 __device__ __forceinline__ float4 merge_warp_boxes(const StepSmem<P> &sm) {
@@ -1215,7 +1216,10 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
     // lookback, so that the predecessors publish meanwhile.  (The pull kernel sizes it by
     // the gathered ancestors; the CDF kernel has none.)
     if constexpr (kMode != kModeCdf) {
-        if (!gt) warp_box(make_float4(bx0, bx1, by0, by1), sm);
+        if (!gt) {   // thread 0 merges the other warps' boxes into its warp's after the barrier
+            const float4 wb = warp_box(make_float4(bx0, bx1, by0, by1), sm);
+            bx0 = wb.x; bx1 = wb.y; by0 = wb.z; by1 = wb.w;
+        }
         // the tracker table's share of this tile (after the aggregate is out)
         if (gt) {
             const uint64_t gtag = static_cast<uint64_t>(sm.st.epoch % 0x7fffffffu + 1u) << 32;
@@ -1281,6 +1285,10 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
     const int wx0 = no_table ? 0 : sm.win_x0, wy0 = no_table ? 0 : sm.win_y0;
     const int ww = no_table ? 0 : sm.win_w, wh = no_table ? 0 : sm.win_h;
     const int cells = ww * wh;
+    if (kMode != kModeCdf && T.dbg_win && tid == 0) {   // test hook: the tile's window
+        int32_t *dw = T.dbg_win + PF_IDX(4 * lt, 4 * T.ntiles);
+        dw[0] = wx0; dw[1] = wy0; dw[2] = ww; dw[3] = wh;
+    }
     HalfLik<H> hk;
     if constexpr (Tr::kHalf) hk = half_lik<H>(T);
 
