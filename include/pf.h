@@ -280,8 +280,9 @@ pf_status pf_debug_philox(const uint32_t *ctrs, int64_t n, uint64_t seed, uint32
  * Everything else the step needs (lookback descriptors, per-tile sums, counters, the
  * tracker descriptor) lives in one array (about 170 KiB) in the library's device memory, present
  * on every GPU from the moment the library is loaded until the process exits; it limits
- * num_particles to 2^22 (PF_ERR_ARG beyond).  The first call on each device looks up that
- * array's address, so make it before any stream capture.  All calls share the array; a
+ * num_particles to 2^22 (PF_ERR_ARG beyond).  The call waits for its step and reads the
+ * state back, so it cannot be captured into a CUDA graph (PF_ERR_ARG while cuda_stream is
+ * capturing).  All calls share the array; a
  * small kernel of each call writes the descriptor and clears what must start at zero;
  * calls whose GPU work overlaps (other streams, other threads) race on it and must be
  * serialised by the caller.  No device or pinned memory is allocated.

@@ -151,11 +151,17 @@ extern "C" pf_status pf_step_frame_noalloc(const pf_config *cfg, const pf_state_
                 if (overlaps(bufs[a], bufs[b], nb)) return PF_ERR_ARG;
     }
 
+    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    // the call waits for its step and reads the new state back: it cannot be captured
+    {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(stream, &cs) != cudaSuccess) { cudaGetLastError(); return PF_ERR_CUDA; }
+        if (cs != cudaStreamCaptureStatusNone) return PF_ERR_ARG;
+    }
     int dev = 0;
     unsigned char *scr = nullptr;
     pf_status s = scratch_for_current_device(&dev, &scr);
     if (s != PF_OK) return s;
-    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
     constexpr ScratchLayout LY = layout();
 
     // descriptor of the tracker: the caller's buffers are the ping-pong slots of frame t

@@ -185,3 +185,30 @@ def test_noalloc_rejects_misaligned_buffers(pf):
                                         ctypes.c_void_p(base + 4), ctypes.c_void_p(base + 16 * 32),
                                         ctypes.c_void_p(base + 16 * 48), ctypes.byref(out), None)
     assert rc == pf.PF_ERR_ARG
+
+
+def test_noalloc_rejects_stream_capture(pf):
+    """The call waits for its step and reads the state back, so it refuses a capturing stream
+    (before it touches the device) and the stream stays usable."""
+    import torch
+    N = 1000
+    cfg = pf.make_config(64, 64, N, 3, "f32")
+    hdr = pf.PfStateHeader(magic=0x31534650, precision=cfg.precision, num_particles=N, t=0)
+    frame = torch.zeros((64, 64), dtype=torch.uint8, device="cuda")
+    bufs = [torch.zeros(N + 16, dtype=torch.float32, device="cuda") for _ in range(3)]
+    out = pf.PfStateHeader()
+    P = ctypes.c_void_p
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g, stream=s):
+        rc = pf.lib().pf_step_frame_noalloc(ctypes.byref(cfg), ctypes.byref(hdr), None, None, None,
+                                            P(frame.data_ptr()), 64, P(bufs[0].data_ptr()), P(bufs[1].data_ptr()),
+                                            P(bufs[2].data_ptr()), ctypes.byref(out), P(s.cuda_stream))
+        bufs[0].add_(1.0)    # something to capture
+    assert rc == pf.PF_ERR_ARG
+    rc = pf.lib().pf_step_frame_noalloc(ctypes.byref(cfg), ctypes.byref(hdr), None, None, None,
+                                        P(frame.data_ptr()), 64, P(bufs[0].data_ptr()), P(bufs[1].data_ptr()),
+                                        P(bufs[2].data_ptr()), ctypes.byref(out), P(s.cuda_stream))
+    assert rc == pf.PF_OK and out.t == 1
+    torch.cuda.synchronize()
