@@ -1395,10 +1395,14 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
         if constexpr (kMode == kModeCdf) __syncthreads();
         {   // the block part of the running max
             acc_t wmax = static_cast<acc_t>(0);
+            if constexpr (kF64) {
 #pragma unroll
-            for (int w = 0; w < kWarps; ++w) {
-                const acc_t v = sm.warp_max[w];
-                if (w < warp) wmax = fmax(wmax, v);
+                for (int w = 0; w < kWarps; ++w) {
+                    const acc_t v = sm.warp_max[w];
+                    if (w < warp) wmax = fmax(wmax, v);
+                }
+            } else {   // lane w < warp holds warp w's maximum (prefixes are >= 0): one redux
+                wmax = warp_max(lane < warp ? sm.warp_max[lane] : static_cast<acc_t>(0));
             }
             if (lane == 0) mex = wmax; else mex = fmax(mex, wmax);
 #pragma unroll
@@ -1524,11 +1528,8 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
         int run = __shfl_up_sync(0xffffffffu, xm, 1);
         if (lane == 0) run = 0;
         __syncthreads();
-#pragma unroll
-        for (int w = 0; w < kWarps; ++w) {
-            const int v = sm.warp_imax[w];
-            if (w < warp) run = max(run, v);
-        }
+        // the maxima of the preceding warps: lane w < warp holds warp w's (entries are >= 0)
+        run = max(run, __reduce_max_sync(0xffffffffu, lane < warp ? sm.warp_imax[lane] : 0));
         uint32_t w4[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
