@@ -649,15 +649,14 @@ __device__ __forceinline__ float4 warp_box(float4 b, StepSmem<P> &sm) {
     if ((threadIdx.x & 31) == 0) *reinterpret_cast<float4 *>(sm.box[threadIdx.x >> 5]) = b;
     return b;
 }
+// The block's box from the warps' boxes in sm.box, by one whole warp (lane w reads warp w's),
+// returned to every lane of that warp.
 template <int P>
 __device__ __forceinline__ float4 merge_warp_boxes(const StepSmem<P> &sm) {
-    float4 b = *reinterpret_cast<const float4 *>(sm.box[0]);
-#pragma unroll
-    for (int w = 1; w < kWarps; ++w) {
-        const float4 v = *reinterpret_cast<const float4 *>(sm.box[w]);
-        b.x = fminf(b.x, v.x); b.y = fmaxf(b.y, v.y); b.z = fminf(b.z, v.z); b.w = fmaxf(b.w, v.w);
-    }
-    return b;
+    const int lane = threadIdx.x & 31;
+    const float4 b = lane < kWarps ? *reinterpret_cast<const float4 *>(sm.box[lane])
+                                   : make_float4(FLT_MAX, -FLT_MAX, FLT_MAX, -FLT_MAX);
+    return make_float4(warp_min(b.x), warp_max(b.y), warp_min(b.z), warp_max(b.w));
 }
 
 template <int P, typename A>
@@ -759,8 +758,8 @@ __device__ void finalize_tracker(const TrackerDev &T, TrackerState *st, StepSmem
     }
     if (track_box) warp_box(bb, sm);
     v = block_stats<P>(v, sm);
+    if (track_box && threadIdx.x < 32) bb = merge_warp_boxes(sm);
     if (threadIdx.x == 0) {
-        if (track_box) bb = merge_warp_boxes(sm);
         const Stats<acc_t> r = v;
         // The new state is built from the copy in shared memory (this launch's starting
         // state, which no tile changes) and written with stores only: no load round trip.
@@ -1216,10 +1215,7 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
     // lookback, so that the predecessors publish meanwhile.  (The pull kernel sizes it by
     // the gathered ancestors; the CDF kernel has none.)
     if constexpr (kMode != kModeCdf) {
-        if (!gt) {   // thread 0 merges the other warps' boxes into its warp's after the barrier
-            const float4 wb = warp_box(make_float4(bx0, bx1, by0, by1), sm);
-            bx0 = wb.x; bx1 = wb.y; by0 = wb.z; by1 = wb.w;
-        }
+        if (!gt) warp_box(make_float4(bx0, bx1, by0, by1), sm);   // warp 0 merges them after the barrier
         // the tracker table's share of this tile (after the aggregate is out)
         if (gt) {
             const uint64_t gtag = static_cast<uint64_t>(sm.st.epoch % 0x7fffffffu + 1u) << 32;
@@ -1246,13 +1242,11 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
             sm.skeys[2] = static_cast<uint32_t>(t - 1); sm.skeys[3] = T.tracker_id;
         }
         __syncthreads();
+        if (!gt && warp == 0) {   // the block's box, in every lane of warp 0
+            const float4 b = merge_warp_boxes(sm);
+            bx0 = b.x; bx1 = b.y; by0 = b.z; by1 = b.w;
+        }
         if (!gt && tid == 0) {
-#pragma unroll
-            for (int w = 1; w < kWarps; ++w) {
-                const float4 v = *reinterpret_cast<const float4 *>(sm.box[w]);
-                bx0 = fminf(bx0, v.x); bx1 = fmaxf(bx1, v.y);
-                by0 = fminf(by0, v.z); by1 = fmaxf(by1, v.w);
-            }
             // Every draw lies within kDrawMax sigma: if that window takes a single pass of
             // the block, no offspring needs the direct route; otherwise kWindowSigmas
             // (the tracker's window policy may force either).
@@ -1748,10 +1742,10 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
     }
     if (track_box) warp_box(bb, sm);
     const Stats<acc_t> tot = block_stats<P>(stats, sm);
+    if (track_box && warp == 0) bb = merge_warp_boxes(sm);
     if (tid == 0) {
         TilePartial *p = &T.part[PF_IDX(lt, T.ntiles)];
         if (track_box) {
-            bb = merge_warp_boxes(sm);
             const uint64_t btg = partial_tag(sm.st.epoch);
             st_relaxed_v2(&p->b[0], btg | __float_as_uint(bb.x), btg | __float_as_uint(bb.y));
             st_relaxed_v2(&p->b[2], btg | __float_as_uint(bb.z), btg | __float_as_uint(bb.w));
