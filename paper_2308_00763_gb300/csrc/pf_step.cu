@@ -759,71 +759,71 @@ __device__ void finalize_tracker(const TrackerDev &T, TrackerState *st, StepSmem
     if (track_box) warp_box(bb, sm);
     v = block_stats<P>(v, sm);
     if (track_box && threadIdx.x < 32) bb = merge_warp_boxes(sm);
-    if (threadIdx.x == 0) {
-        const Stats<acc_t> r = v;
-        // The new state is built from the copy in shared memory (this launch's starting
-        // state, which no tile changes) and written with stores only: no load round trip.
+    if (threadIdx.x < 32) {
+        // The new state, from the block's statistics (thread 0's, broadcast) and this launch's
+        // starting state (the copy in shared memory, which no tile changes), written field by
+        // field with stores only by four lanes in parallel: lane 0 the x estimate and
+        // anchors, lane 1 the y ones, lane 2 the weight scalars, lane 3 the rest.  The status
+        // word is not written (another tile may have raised it).
+        const int lane = threadIdx.x;
+        Stats<acc_t> r;
+        r.m = __shfl_sync(0xffffffffu, v.m, 0);
+        r.s = __shfl_sync(0xffffffffu, v.s, 0);
+        r.sx = __shfl_sync(0xffffffffu, v.sx, 0);
+        r.sy = __shfl_sync(0xffffffffu, v.sy, 0);
         const TrackerState &o = sm.st;
-        TrackerState n = o;
-        const acc_t inv = static_cast<acc_t>(1) / r.s;
-        double ex, ey;
-        if constexpr (kF64) {
-            ex = o.nx + r.sx / r.s;
-            ey = o.ny + r.sy / r.s;
-            if (isfinite(ex) && fabs(ex) < 1.0e6) n.nx = floor(ex) + ((ex - floor(ex)) >= 0.5 ? 1.0 : 0.0);
-            if (isfinite(ey) && fabs(ey) < 1.0e6) n.ny = floor(ey) + ((ey - floor(ey)) >= 0.5 ? 1.0 : 0.0);
-            n.nxi = static_cast<int32_t>(n.nx);
-            n.nyi = static_cast<int32_t>(n.ny);
-        } else {
-            // FP32 quotient; the next anchor in FP32 / integers (FP64 only to widen the
-            // results the host reads)
-            const float qx = r.sx / r.s, qy = r.sy / r.s;
-            const float fx = static_cast<float>(o.nxi) + qx, fy = static_cast<float>(o.nyi) + qy;
-            if (isfinite(fx) && fabsf(fx) < 1.0e6f) n.nxi = __float2int_rd(fx + 0.5f);
-            if (isfinite(fy) && fabsf(fy) < 1.0e6f) n.nyi = __float2int_rd(fy + 0.5f);
-            n.nx = static_cast<double>(n.nxi);
-            n.ny = static_cast<double>(n.nyi);
-            ex = o.nx + static_cast<double>(qx);
-            ey = o.ny + static_cast<double>(qy);
-        }
-        n.M = static_cast<double>(r.m);
-        n.S = static_cast<double>(r.s);
-        n.invS = static_cast<double>(inv);
-        n.ax = o.nx;
-        n.ay = o.ny;
-        n.M_f = static_cast<float>(r.m);
-        n.invS_f = static_cast<float>(inv);
-        n.axi = o.nxi;
-        n.ayi = o.nyi;
-        n.est_x = ex;
-        n.est_y = ey;
-        // the box of the new positions sizes the next step's tracker table (unknown if the
-        // launch did not track it, or empty)
-        const bool box_ok = track_box && bb.x <= bb.y && bb.z <= bb.w;
-        n.bb_x0 = box_ok ? bb.x : __int_as_float(0x7fc00000);
-        n.bb_x1 = box_ok ? bb.y : __int_as_float(0x7fc00000);
-        n.bb_y0 = box_ok ? bb.z : __int_as_float(0x7fc00000);
-        n.bb_y1 = box_ok ? bb.w : __int_as_float(0x7fc00000);
-        n.t = o.t + 1;
-        n.epoch = o.epoch + 1u;
         const int64_t slot = (o.t >= 0 && o.t < 0x7fffffffll)
                                  ? static_cast<int64_t>(static_cast<uint32_t>(o.t) % static_cast<uint32_t>(T.est_cap))
                                  : o.t % T.est_cap;
-        *reinterpret_cast<double2 *>(T.est_ring + 2 * slot) = make_double2(ex, ey);
-        *reinterpret_cast<double2 *>(T.stat_ring + 2 * slot) = make_double2(n.M, n.S);
-        if (est_out) *reinterpret_cast<double2 *>(est_out) = make_double2(ex, ey);
-        // every field but the sticky status word (another tile may have raised it)
-        st->t = n.t;
-        st->epoch = n.epoch;
-        constexpr int kHead = static_cast<int>(offsetof(TrackerState, M));
-        static_assert(kHead == 16 && sizeof(TrackerState) % 16 == 0, "TrackerState layout");
-        const uint4 *src = reinterpret_cast<const uint4 *>(reinterpret_cast<const char *>(&n) + kHead);
-        uint4 *dst = reinterpret_cast<uint4 *>(reinterpret_cast<char *>(st) + kHead);
-#pragma unroll
-        for (int k = 0; k < static_cast<int>(sizeof(TrackerState) - kHead) / 16; ++k) dst[k] = src[k];
-        // every tile of this launch has counted; the next launch sees the reset after the
-        // kernel boundary
-        *T.done = 0u;
+        if (lane < 2) {
+            const bool ly = lane == 1;
+            const acc_t rs = ly ? r.sy : r.sx;
+            const double on = ly ? o.ny : o.nx;        // the anchor the positions were written against
+            const int32_t oni = ly ? o.nyi : o.nxi;
+            double e, nn;
+            int32_t ni;
+            if constexpr (kF64) {
+                e = on + rs / r.s;
+                nn = on;
+                if (isfinite(e) && fabs(e) < 1.0e6) nn = floor(e) + ((e - floor(e)) >= 0.5 ? 1.0 : 0.0);
+                ni = static_cast<int32_t>(nn);
+            } else {
+                // FP32 quotient; the next anchor in FP32 / integers (FP64 only to widen the
+                // results the host reads)
+                const float q = rs / r.s;
+                const float fq = static_cast<float>(oni) + q;
+                ni = oni;
+                if (isfinite(fq) && fabsf(fq) < 1.0e6f) ni = __float2int_rd(fq + 0.5f);
+                nn = static_cast<double>(ni);
+                e = on + static_cast<double>(q);
+            }
+            if (ly) { st->ay = on; st->ayi = oni; st->ny = nn; st->nyi = ni; st->est_y = e; }
+            else { st->ax = on; st->axi = oni; st->nx = nn; st->nxi = ni; st->est_x = e; }
+            T.est_ring[2 * slot + lane] = e;
+            if (est_out) est_out[lane] = e;
+        } else if (lane == 2) {
+            const acc_t inv = static_cast<acc_t>(1) / r.s;
+            st->M = static_cast<double>(r.m);
+            st->S = static_cast<double>(r.s);
+            st->invS = static_cast<double>(inv);
+            st->M_f = static_cast<float>(r.m);
+            st->invS_f = static_cast<float>(inv);
+            T.stat_ring[2 * slot] = static_cast<double>(r.m);
+            T.stat_ring[2 * slot + 1] = static_cast<double>(r.s);
+        } else if (lane == 3) {
+            // the box of the new positions sizes the next step's tracker table (unknown if
+            // the launch did not track it, or empty)
+            const bool box_ok = track_box && bb.x <= bb.y && bb.z <= bb.w;
+            st->bb_x0 = box_ok ? bb.x : __int_as_float(0x7fc00000);
+            st->bb_x1 = box_ok ? bb.y : __int_as_float(0x7fc00000);
+            st->bb_y0 = box_ok ? bb.z : __int_as_float(0x7fc00000);
+            st->bb_y1 = box_ok ? bb.w : __int_as_float(0x7fc00000);
+            st->t = o.t + 1;
+            st->epoch = o.epoch + 1u;
+            // every tile of this launch has counted; the next launch sees the reset after the
+            // kernel boundary
+            *T.done = 0u;
+        }
     }
 }
 
