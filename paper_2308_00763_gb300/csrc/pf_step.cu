@@ -202,7 +202,7 @@ __device__ void wait_partial(const TilePartial *p, uint64_t tag, TrackerState *s
             return;
         if ((it & 1023u) == 1023u && timed_out(st)) return;
         __nanosleep(ns);
-        if (ns < 256) ns <<= 1;
+        if (ns < 64) ns <<= 1;
     }
     atomicOr(&st->status, kStatusTimeout);
 }
@@ -1762,7 +1762,10 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
             const uint64_t tg = partial_tag(sm.st.epoch);
             st_relaxed_v2(&p->w[0], tg | __float_as_uint(tot.m), tg | __float_as_uint(tot.s));
             st_relaxed_v2(&p->w[2], tg | __float_as_uint(tot.sx), tg | __float_as_uint(tot.sy));
-            prev = atom_add_relaxed(T.done, 1u);
+            // the tracker's last tile finalises, waiting for every partial's tag: no tile waits
+            // for a counter's round trip (the tiles before it hold lower tickets, so they are
+            // running or done)
+            prev = static_cast<uint32_t>(lt);
         }
         sm.last = (prev == static_cast<uint32_t>(T.ntiles - 1)) ? 1u : 0u;
     }
