@@ -273,6 +273,12 @@ def _rmse(a, b):
     return float(math.sqrt(np.mean(np.sum((np.asarray(a) - np.asarray(b)) ** 2, axis=1))))
 
 
+def _config(args, ws):
+    """The workload description both arms print (the reference arm times the same workload)."""
+    return {"workload": WORKLOAD_SHORT, "precision": args.precision, "resampler": args.resampler,
+            "l2": "flushed between timed steps", "parallelism": "replicas" if ws > 1 else "single GPU"}
+
+
 # ---------------------------------------------------------------------------- reference arm
 def run_reference(args):
     ws, rank, _ = _dist()
@@ -299,7 +305,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": val, "unit": METRIC, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "step": "oracle sample: " + sample},
+        "data": "synthetic", "config": _config(args, 1),
         "cpu_baseline": {"value": val, "unit": METRIC, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": val, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "gpu_launches": 0,
@@ -427,8 +433,7 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": DTYPE_NAME[hp], "data": "synthetic",
-        "config": {"workload": WORKLOAD_SHORT, "precision": hp, "resampler": args.resampler,
-                   "l2": "flushed between timed steps", "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "config": _config(args, ws),
         # the step kernel against HBM on the scan-and-search design's bytes per particle-step
         # (20 / 32 / 64 B: read x, y, write x, y, write L, scan L -> C, search C); the fused
         # kernel itself moves 12 / 24 / 48 B (fused_frac)
