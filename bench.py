@@ -495,8 +495,22 @@ def run_ours(args):
         # the detail first (stderr), the headline last on stdout, compact
         sys.stderr.write("bench detail: " + json.dumps(detail) + "\n")
         sys.stderr.flush()
-        print(json.dumps(line, separators=(",", ":")))
+        print(json.dumps(_rounded(line), separators=(",", ":")))
     return 0
+
+
+def _rounded(obj, keep=("value", "ms_per_step")):
+    """The headline line with its floats at five significant digits (it must stay short;
+    `value` and `ms_per_step` at the top level keep full precision)."""
+    def r(x, top=False, key=None):
+        if isinstance(x, float) and not (top and key in keep):
+            return float("%.5g" % x)
+        if isinstance(x, dict):
+            return {k: r(v, False, k) for k, v in x.items()}
+        if isinstance(x, list):
+            return [r(v) for v in x]
+        return x
+    return {k: r(v, True, k) for k, v in obj.items()}
 
 
 def _cpu_baseline(v, tracks):
