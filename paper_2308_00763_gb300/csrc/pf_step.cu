@@ -1176,6 +1176,35 @@ __device__ void run_tile(const StepLaunch &Lp, int g, StepSmem<P> &sm) {
                     hi[h + i] = (eb + h + i < cnt) ? N : 0;
                 }
             }
+            // A coarse table of the CDF in shared memory (the staging area is free until the
+            // likelihood table): cs[i] = C at the last index of block i of 2^lb entries, 2^lb
+            // the smallest power of two that gives at most kCoarse blocks.  The first block
+            // whose last value reaches u holds the answer (C is non-decreasing), so a search
+            // is a search of the table and then lb global steps inside that block, with the
+            // same result as a search of the whole CDF.
+            constexpr int kCoarse = static_cast<int>(sizeof(sm.u) / sizeof(acc_t));
+            int lb = 0;
+            while (((static_cast<int64_t>(N) + (1ll << lb) - 1) >> lb) > kCoarse) ++lb;
+            const int nb = static_cast<int>((static_cast<int64_t>(N) + (1ll << lb) - 1) >> lb);
+            acc_t *cs = reinterpret_cast<acc_t *>(&sm.u);
+            for (int i = tid; i < nb; i += kThreads) {
+                const int64_t last = ((static_cast<int64_t>(i) + 1) << lb) - 1;
+                cs[PF_IDX(i, kCoarse)] = __ldg(cdf + (last < N ? last : N - 1));
+            }
+            __syncthreads();
+#pragma unroll
+            for (int m = 0; m < kItems; ++m) {
+                if (hi[m] > 0) {
+                    int a = 0, b = nb - 1;        // first block whose last value reaches u
+                    while (a < b) {
+                        const int mid = (a + b) >> 1;
+                        if (cs[PF_IDX(mid, kCoarse)] >= uq[m]) b = mid; else a = mid + 1;
+                    }
+                    const int64_t bl = static_cast<int64_t>(a) << lb, bh = ((static_cast<int64_t>(a) + 1) << lb) - 1;
+                    lo[m] = static_cast<int>(bl);
+                    hi[m] = static_cast<int>(bh < N ? bh : N - 1);
+                }
+            }
         }
         for (bool more = true; more;) {           // first k with C_k >= u, in [lo, hi]
             more = false;
