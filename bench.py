@@ -61,6 +61,9 @@ def _args():
     p.add_argument("--serve-overload", type=float, default=20.0,
                    help="also replay the served workload with every stream's particle count scaled by this "
                         "factor (capped at 2^24) so that admission refuses streams; 0 = skip")
+    p.add_argument("--no-sweep", action="store_true",
+                   help="no effect: the sweep runs only with --systems (kept so that older profile command "
+                        "lines run unchanged)")
     p.add_argument("--systems", action="store_true",
                    help="also run the precision/size sweep, the paper's workload, the resampler and Gumbel-max "
                         "studies (printed in the detail line on stderr)")
