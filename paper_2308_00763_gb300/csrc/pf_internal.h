@@ -198,7 +198,8 @@ int launch_shard_expand(int precision, const void *cdf, const void *x, const voi
 constexpr int kGumbelOffspring = 8;       // Gumbel-max: offspring per CTA
 constexpr int kGumbelThreads = 256;
 constexpr int kMetropolisThreads = 256;   // Metropolis: one offspring per thread
-constexpr int kRejectionThreads = 256;    // rejection: one offspring per thread
+constexpr int kRejectionThreads = 256;    // rejection: threads per CTA
+constexpr int kRejectionOffspring = 2048; // rejection: offspring per CTA (a pool its threads share)
 struct AncestorLaunch {
     const TrackerDev *trk;     // device array indexed by slot
     const FrameRef *frames;    // device array indexed by slot

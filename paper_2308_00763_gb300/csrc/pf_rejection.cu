@@ -14,8 +14,12 @@
 // candidate is kept (the loop is bounded whatever the weights).  The test runs in FP64 for
 // REF64 and FP32 for the others (L widened exactly from its stored type).
 //
-// Layout: one thread per offspring, 256 offspring per CTA; a warp runs until its last
-// lane accepts, so its cost follows the largest of 32 geometric try counts.
+// Layout: CTA b takes kRejectionOffspring consecutive offspring as a pool its
+// kRejectionThreads threads share: each loop iteration is one try of every lane's current
+// offspring, and a lane whose offspring is decided takes the next undecided one from a
+// shared counter.  A warp therefore stays busy until the pool is empty instead of waiting,
+// for each group of 32 offspring, for the largest of 32 geometric try counts; every
+// offspring's tries and decision are those of its own Philox stream either way.
 #include <math.h>
 
 #include "pf_ancestor.cuh"
@@ -33,6 +37,7 @@ __global__ void __launch_bounds__(kRejectionThreads) rejection_kernel(const Ance
     using lik_t = typename Prec<P>::lik_t;
     using acc_t = typename Prec<P>::acc_t;
     constexpr bool kF64 = sizeof(acc_t) == 8;
+    __shared__ unsigned int s_next;   // next undecided offspring of the pool (local index)
     const int b = static_cast<int>(blockIdx.x);
     const int g = ancestor_tracker(G, b);
     const int slot = __ldg(G.slots + g);
@@ -41,26 +46,36 @@ __global__ void __launch_bounds__(kRejectionThreads) rejection_kernel(const Ance
     const int64_t t = st->t;
     if (t <= 0 || (st->status & kStatusTimeout) || !G.frames[slot].active) return;
     const int N = static_cast<int>(T.N);
-    const int j = (b - __ldg(G.cta_prefix + g)) * kRejectionThreads + static_cast<int>(threadIdx.x);
-    if (j >= N) return;
+    const int64_t j0 = static_cast<int64_t>(b - __ldg(G.cta_prefix + g)) * kRejectionOffspring;
+    const int pool = static_cast<int>(N - j0 < kRejectionOffspring ? N - j0 : kRejectionOffspring);
+    if (threadIdx.x == 0) s_next = kRejectionThreads;
+    __syncthreads();
     const lik_t *__restrict__ L = static_cast<const lik_t *>(T.pl[static_cast<int>((t + 1) & 1)]);
     const acc_t M = kF64 ? static_cast<acc_t>(st->M) : static_cast<acc_t>(st->M_f);
     const uint32_t tctr = static_cast<uint32_t>(t - 1);
-    const uint32_t tag = 6u + (static_cast<uint32_t>(j) << 8);
     const uint32_t key_lo = T.key_lo, key_hi = T.key_hi, trk_id = T.tracker_id;
     const uint32_t n = static_cast<uint32_t>(N);
     const int R = T.steps;
 
-    int k = j;
-    for (int i = 0; i < R; i += 2) {
-        const uint4 w = philox4x32_10(make_uint4(static_cast<uint32_t>(i >> 1), tctr, tag, trk_id), key_lo, key_hi);
-        if (i > 0) k = static_cast<int>(__umulhi(w.x, n));
-        if (log_uniform(w.y, acc_t{}) <= to_acc(L[k]) - M) break;
-        if (i + 1 >= R) break;
-        k = static_cast<int>(__umulhi(w.z, n));
-        if (log_uniform(w.w, acc_t{}) <= to_acc(L[k]) - M) break;
+    int e = static_cast<int>(threadIdx.x);   // the lane's offspring (pool index); >= pool: none
+    int i = 0, k = 0;                        // its next try and current candidate
+    uint4 w = make_uint4(0u, 0u, 0u, 0u);    // the Philox block of tries i & ~1, i | 1
+    while (e < pool) {
+        const int jj = static_cast<int>(j0) + e;
+        if ((i & 1) == 0)
+            w = philox4x32_10(make_uint4(static_cast<uint32_t>(i >> 1), tctr, 6u + (static_cast<uint32_t>(jj) << 8), trk_id),
+                              key_lo, key_hi);
+        const uint32_t wk = (i & 1) ? w.z : w.x, wu = (i & 1) ? w.w : w.y;
+        k = (i == 0) ? jj : static_cast<int>(__umulhi(wk, n));
+        const bool done = log_uniform(wu, acc_t{}) <= to_acc(L[k]) - M || i + 1 >= R;
+        if (done) {
+            T.anc[jj] = k;
+            e = static_cast<int>(atomicAdd(&s_next, 1u));
+            i = 0;
+        } else {
+            ++i;
+        }
     }
-    T.anc[j] = k;
 }
 
 template <int P>

@@ -249,7 +249,7 @@ static pf_status engine_init(Engine &e, const pf_config *cfgs, int n, void *stre
         if (multi) o.cdf = a.take((given ? sizeof(int32_t) : cdf_b) * N + 16);
         if (given) {
             const int s = c.resampler == PF_RESAMPLE_GUMBEL ? 0 : c.resampler == PF_RESAMPLE_METROPOLIS ? 1 : 2;
-            const int per = s == 0 ? kGumbelOffspring : s == 1 ? kMetropolisThreads : kRejectionThreads;
+            const int per = s == 0 ? kGumbelOffspring : s == 1 ? kMetropolisThreads : kRejectionOffspring;
             const int64_t ctas = aprefix[s].back() + (N + per - 1) / per;
             if (ctas > 0x7fffffff) return PF_ERR_ARG;
             atab[s].push_back(i);
