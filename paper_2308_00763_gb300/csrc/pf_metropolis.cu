@@ -15,7 +15,8 @@
 // type).
 //
 // Layout: one thread per offspring, 256 offspring per CTA.  The proposals do not depend on
-// the chain's state, so the random gathers L[k'] of successive steps are independent loads
+// the chain's state, so the random gathers L[k'] of successive steps are independent loads:
+// a thread issues eight steps' gathers together, then takes their accept tests in order
 // (L of a tracker is 2-8 bytes per particle and stays in L2 here); the state's own L_k is
 // kept in a register.  The pull kernel gathers the ancestors written here.
 #include <math.h>
@@ -53,19 +54,30 @@ __global__ void __launch_bounds__(kMetropolisThreads) metropolis_kernel(const An
 
     int k = j;
     acc_t lk = to_acc(L[j]);
-    for (int s = 0; s < B; s += 2) {
-        const uint4 w = philox4x32_10(make_uint4(static_cast<uint32_t>(s >> 1), tctr, tag, trk_id), key_lo, key_hi);
-        const int k1 = static_cast<int>(__umulhi(w.x, n));
-        const int k2 = static_cast<int>(__umulhi(w.z, n));
-        const acc_t l1 = to_acc(L[k1]);
-        const acc_t l2 = (s + 1 < B) ? to_acc(L[k2]) : acc_t{};
-        if (log_uniform(w.y, acc_t{}) <= l1 - lk) {
-            k = k1;
-            lk = l1;
+    // eight steps at a time: their proposals (four Philox blocks) and gathers first, all
+    // eight loads in flight, then the eight accept tests in step order
+    for (int s = 0; s < B; s += 8) {
+        uint32_t wk[8], wu[8];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            uint4 w = make_uint4(0u, 0u, 0u, 0u);
+            if (s + 2 * h < B)
+                w = philox4x32_10(make_uint4(static_cast<uint32_t>((s >> 1) + h), tctr, tag, trk_id), key_lo, key_hi);
+            wk[2 * h] = w.x; wu[2 * h] = w.y; wk[2 * h + 1] = w.z; wu[2 * h + 1] = w.w;
         }
-        if (s + 1 < B && log_uniform(w.w, acc_t{}) <= l2 - lk) {
-            k = k2;
-            lk = l2;
+        int kq[8];
+        acc_t lq[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            kq[q] = static_cast<int>(__umulhi(wk[q], n));
+            lq[q] = (s + q < B) ? to_acc(L[kq[q]]) : acc_t{};
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            if (s + q < B && log_uniform(wu[q], acc_t{}) <= lq[q] - lk) {
+                k = kq[q];
+                lk = lq[q];
+            }
         }
     }
     T.anc[j] = k;
