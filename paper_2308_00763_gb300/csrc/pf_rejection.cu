@@ -15,9 +15,9 @@
 // REF64 and FP32 for the others (L widened exactly from its stored type).
 //
 // Layout: CTA b takes kRejectionOffspring consecutive offspring as a pool its
-// kRejectionThreads threads share: each loop iteration is one try of every lane's current
-// offspring, and a lane whose offspring is decided takes the next undecided one from a
-// shared counter.  A warp therefore stays busy until the pool is empty instead of waiting,
+// kRejectionThreads threads share: each loop iteration is eight tries of every lane's
+// current offspring (their gathers in flight together), and a lane whose offspring is
+// decided takes the next undecided one from a shared counter.  A warp therefore stays busy until the pool is empty instead of waiting,
 // for each group of 32 offspring, for the largest of 32 geometric try counts; every
 // offspring's tries and decision are those of its own Philox stream either way.
 #include <math.h>
@@ -55,25 +55,44 @@ __global__ void __launch_bounds__(kRejectionThreads) rejection_kernel(const Ance
     const uint32_t tctr = static_cast<uint32_t>(t - 1);
     const uint32_t key_lo = T.key_lo, key_hi = T.key_hi, trk_id = T.tracker_id;
     const uint32_t n = static_cast<uint32_t>(N);
-    const int R = T.steps;
+    const int R = T.steps > 0 ? T.steps : 1;   // >= 1: every offspring is decided within R tries
 
     int e = static_cast<int>(threadIdx.x);   // the lane's offspring (pool index); >= pool: none
-    int i = 0, k = 0;                        // its next try and current candidate
-    uint4 w = make_uint4(0u, 0u, 0u, 0u);    // the Philox block of tries i & ~1, i | 1
+    int i = 0;                               // its next try (a multiple of 8)
     while (e < pool) {
         const int jj = static_cast<int>(j0) + e;
-        if ((i & 1) == 0)
-            w = philox4x32_10(make_uint4(static_cast<uint32_t>(i >> 1), tctr, 6u + (static_cast<uint32_t>(jj) << 8), trk_id),
-                              key_lo, key_hi);
-        const uint32_t wk = (i & 1) ? w.z : w.x, wu = (i & 1) ? w.w : w.y;
-        k = (i == 0) ? jj : static_cast<int>(__umulhi(wk, n));
-        const bool done = log_uniform(wu, acc_t{}) <= to_acc(L[k]) - M || i + 1 >= R;
-        if (done) {
-            T.anc[jj] = k;
+        const uint32_t tag = 6u + (static_cast<uint32_t>(jj) << 8);
+        // eight tries at a time: proposals (four Philox blocks) and gathers first, all eight
+        // loads in flight, then the tests in try order; the first accepted try (or the last
+        // try allowed) decides, later loads of the batch go unused
+        uint32_t wk[8], wu[8];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            uint4 w = make_uint4(0u, 0u, 0u, 0u);
+            if (i + 2 * h < R)
+                w = philox4x32_10(make_uint4(static_cast<uint32_t>((i >> 1) + h), tctr, tag, trk_id), key_lo, key_hi);
+            wk[2 * h] = w.x; wu[2 * h] = w.y; wk[2 * h + 1] = w.z; wu[2 * h + 1] = w.w;
+        }
+        int kq[8];
+        acc_t lq[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            kq[q] = (i + q == 0) ? jj : static_cast<int>(__umulhi(wk[q], n));
+            lq[q] = (i + q < R) ? to_acc(L[kq[q]]) : acc_t{};
+        }
+        int dec = -1;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if (dec < 0 && i + q < R && (log_uniform(wu[q], acc_t{}) <= lq[q] - M || i + q + 1 >= R)) dec = q;
+        if (dec >= 0) {
+            int kd = kq[0];
+#pragma unroll
+            for (int q = 1; q < 8; ++q) if (q == dec) kd = kq[q];
+            T.anc[jj] = kd;
             e = static_cast<int>(atomicAdd(&s_next, 1u));
             i = 0;
         } else {
-            ++i;
+            i += 8;
         }
     }
 }
